@@ -1,0 +1,153 @@
+/*
+ * gbr.h -- C ABI of the B300 (sm_103a) library for the per-RK-stage right-hand
+ * side of arXiv 2303.10785: MEG6 gradient-based reconstruction with the
+ * improved MP limiter, curvilinear HLLC, alpha-damping viscous flux,
+ * freestream-preserving conservative metrics and the geometric-conservation
+ * term on moving meshes, advanced by SSP-RK3.
+ *
+ * Conventions (every entry point):
+ *  - Plain pointers and sizes only.  Host pointers are borrowed for the call.
+ *  - The caller owns the device workspace (any allocator, e.g. a torch tensor);
+ *    the context keeps using it until gbr_destroy.  The library itself calls no
+ *    device allocator.  gbr_workspace_bytes gives the exact size.
+ *  - Work is enqueued on the caller's CUDA stream passed to gbr_create.
+ *  - No exception or abort crosses the ABI: every call returns a gbr_status.
+ *    Errors detected on the device (non-finite state, non-positive density) are
+ *    sticky and surface at gbr_sync.
+ *  - Not thread-safe per context; independent contexts are independent.
+ *
+ * Array layouts (doubles, C order, i fastest):
+ *  nodes    [ndim][Nk][Nj][Ni] with N_d = n_d + 1 on a periodic axis (node n_d
+ *           closes the period: node(n_d) = node(0) + constant period vector) and
+ *           N_d = n_d + 1 + 2*ghost_nodes on a non-periodic axis (ghost node
+ *           layers first).  2D: [2][Nj][Ni].
+ *  state    [nv][nk][nj][ni], nv = ndim + 2, conserved (rho, rho u.., E).
+ *  faces    direction d: [..][n with n_d -> n_d + 1]; face index f = 0..n_d is the
+ *           interface i+1/2 with i = f - 1.
+ */
+#ifndef GBR_H
+#define GBR_H
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GBR_ABI_VERSION 1
+
+typedef struct gbr_ctx gbr_ctx;
+
+typedef enum {
+  GBR_OK = 0,
+  GBR_EINVAL = 1,      /* invalid argument (message in gbr_last_error / gbr_last_global_error) */
+  GBR_ENOMEM = 2,      /* workspace smaller than gbr_workspace_bytes */
+  GBR_ECUDA = 3,       /* a CUDA runtime call failed */
+  GBR_ENONFINITE = 4,  /* the device saw a non-finite state or non-positive density */
+  GBR_ETIMEOUT = 5,    /* gbr_sync deadline passed before the stream drained */
+  GBR_ESTATE = 6       /* call out of order (e.g. stepping before metrics) */
+} gbr_status;
+
+enum { GBR_BC_ZEROGRAD = 1, GBR_BC_INFLOW = 2 };
+
+typedef struct {
+  int ndim;            /* 2 or 3 */
+  int n[3];            /* cells per axis (n[2] = 1 in 2D) */
+  int periodic[3];     /* 1 = periodic axis */
+  int ghost_nodes;     /* node layers supplied beyond each non-periodic side (>= 10) */
+  int bc[3][2];        /* non-periodic sides: GBR_BC_ZEROGRAD, or GBR_BC_INFLOW on the x-low side */
+  double gamma;        /* ratio of specific heats (Sec. 2: 1.4) */
+  double prandtl;      /* Sec. 2: 0.71 */
+  double reynolds;     /* <= 0: Euler, no viscous flux; mu_ref = 1/reynolds */
+  double sutherland_s; /* S / T_ref of Sutherland's law; <= 0: constant viscosity */
+  double t_ref;        /* Sutherland reference temperature in T = p/rho units */
+  double alpha_damping;/* alpha^D of Eq. (AD-eqn1), paper value 4 */
+  double mp_alpha, mp_beta, mp_eps; /* App. E limiter constants (4, 4, 1e-20) */
+  int moving;          /* 1: reserve grid-velocity, time-metric and GCL storage */
+} gbr_params;
+
+/* Prescribed sinusoidal node motion (Sec. 7.2 families):
+ * x_a(m, t) = origin_a + m_a h_a + amp_a sin(2 pi omega t) prod_b S_ab(m_b h_b),
+ * S_ab(s) = sin(k_ab s) if k_ab != 0 else 1;  velocities are the analytic
+ * time derivative.  m is the (unwrapped) node index. */
+typedef struct {
+  double origin[3], h[3], amp[3], omega, k[3][3];
+} gbr_motion;
+
+/* Field identifiers for gbr_get_field (read-back of intermediate results). */
+enum {
+  GBR_FIELD_CELL_METRICS = 0, /* [nd][nd][cells] hat metrics (Eq. GCL_metrics) */
+  GBR_FIELD_CELL_DET = 1,     /* [cells] 1/J (Eq. Jac-matrix) */
+  GBR_FIELD_CELL_TIME = 2,    /* [nd][cells] hat time metrics */
+  GBR_FIELD_FACE_HAT = 3,     /* [nd][faces of dir] interface hat metrics (Eq. interp-formulae) */
+  GBR_FIELD_FACE_UNHAT = 4,   /* [nd][nd][faces of dir] interface unhatted metrics (viscous) */
+  GBR_FIELD_FACE_TIME = 5,    /* [faces of dir] interface hat time metric */
+  GBR_FIELD_GCL = 6,          /* [cells] (1/J)_t (Eq. Jacb2) */
+  GBR_FIELD_FACE_FLUX = 7     /* [nv][faces of dir] F^ - F^v of the last right-hand side */
+};
+
+/* Exact device workspace size for these parameters; 0 if they are invalid. */
+size_t gbr_workspace_bytes(const gbr_params* p);
+
+/* Create a context on `d_workspace` (>= gbr_workspace_bytes) and upload the
+ * node coordinates (and, if given, node velocities) -- Sec. 3: the solution
+ * lives at the centroid of each cell's vertices.  stream: a cudaStream_t or
+ * NULL for the legacy default stream.  Errors: EINVAL (bad params or periodic
+ * closure), ENOMEM (workspace too small), ECUDA. */
+gbr_status gbr_create(const gbr_params* p, const double* nodes, const double* node_vel, void* d_workspace,
+                      size_t ws_bytes, void* stream, gbr_ctx** out);
+
+/* Sec. 4 + Sec. 6: conservative metrics with the MEG6 interface derivative,
+ * the Jacobian, their interface interpolation, and for a moving mesh the time
+ * metrics xi_t = -(x_t xi_x + ...) and (1/J)_t of Eq. (Jacb2). */
+gbr_status gbr_compute_metrics(gbr_ctx* c);
+
+/* Replace the node coordinates (and velocities) and recompute all metrics
+ * (Sec. 4: recomputed after each change of a dynamic mesh).  Host arrays. */
+gbr_status gbr_move_mesh(gbr_ctx* c, const double* nodes, const double* node_vel);
+
+/* Prescribe an analytic motion evaluated on the device; gbr_rk_step then
+ * recomputes the geometry at every stage time t, t+dt, t+dt/2 (reading A19).
+ * Sets the solution time to t0 and computes the metrics at t0. */
+gbr_status gbr_set_motion(gbr_ctx* c, const gbr_motion* m, double t0);
+
+/* Conserved state in/out; on_device = 1: q is a device pointer. */
+gbr_status gbr_set_state(gbr_ctx* c, const double* q, int on_device);
+gbr_status gbr_get_state(gbr_ctx* c, double* q, int on_device);
+
+/* Jet-type boundary data: x-low inflow primitives [nv][nk][nj] (host), and a
+ * sponge source -sigma (Q - q_amb) with sigma per cell (host, NULL removes it). */
+gbr_status gbr_set_inflow(gbr_ctx* c, const double* prim);
+gbr_status gbr_set_sponge(gbr_ctx* c, const double* sigma, const double* q_amb);
+
+/* dQ/dt = L(Q) = J (Res - (1/J)_t Q) [+ sponge] of the current state (Sec. 3,
+ * Sec. 4 time split, Sec. 5).  dqdt: device array [nv][cells]. */
+gbr_status gbr_rhs(gbr_ctx* c, double* dqdt);
+
+/* App. B CFL time step of the current state; kept on the device.  dt_out:
+ * host pointer (the call then waits for the result) or NULL. */
+gbr_status gbr_compute_dt(gbr_ctx* c, double cfl, double* dt_out);
+
+/* One SSP-RK3 step (App. B).  cfl_or_neg_dt > 0: CFL number (dt computed on
+ * the device from the state at t^n); < 0: fixed dt = -cfl_or_neg_dt.  Moves
+ * the mesh per stage when a motion is set.  Asynchronous. */
+gbr_status gbr_rk_step(gbr_ctx* c, double cfl_or_neg_dt);
+
+/* Wait for the stream (polling, up to timeout_s seconds; <= 0: no limit), then
+ * report sticky device errors (ENONFINITE) or ETIMEOUT. */
+gbr_status gbr_sync(gbr_ctx* c, double timeout_s);
+
+/* Solution time and the last time step (waits for the stream). */
+gbr_status gbr_get_time(gbr_ctx* c, double* t, double* dt);
+
+/* Copy an intermediate field to a host array (see GBR_FIELD_*); dir selects the
+ * face direction for face fields.  Waits for the stream. */
+gbr_status gbr_get_field(gbr_ctx* c, int which, int dir, double* host_out);
+
+const char* gbr_last_error(const gbr_ctx* c);
+const char* gbr_last_global_error(void);
+void gbr_destroy(gbr_ctx* c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

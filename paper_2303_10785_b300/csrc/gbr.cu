@@ -1,0 +1,963 @@
+// sm_103a library: kernels and the C ABI declared in include/gbr.h.
+//
+// Per RK stage (all FP64, every step of the path in these kernels):
+//   k_prim -> k_halo (one launch per axis) -> k_grad1 -> k_grad2 ->
+//   k_face (one launch per direction) -> k_update (divergence, GCL term,
+//   sponge, SSP-RK3 combination)
+// Geometry (set-up, or every stage of a moving mesh):
+//   k_motion -> k_centroid -> k_coordd -> k_metrics -> k_face_metrics -> k_gcl
+// Time step: k_dt (block min with warp shuffles + atomicMin on the bits of a
+// positive double) -> k_dt_final.  dt and t stay on the device.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/gbr.h"
+#include "gbr_kernels.cuh"
+
+using namespace gbr;
+
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kFaceBlock = 128;
+
+enum { S_DT = 0, S_T = 1, S_DTMIN = 2, S_NSCAL = 8 };
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+#define BOX_THREAD(B)                                                   \
+  const long long _t = (long long)blockIdx.x * blockDim.x + threadIdx.x; \
+  if (_t >= box_size(B)) return;                                       \
+  int i, j, k;                                                          \
+  box_coord(B, _t, i, j, k);
+
+__global__ void k_motion(Layout L, Motion M, const double* scal, double stage_c, double* nodes, double* nvel,
+                         Box b) {
+  BOX_THREAD(b);
+  const double tau = scal[S_T] + stage_c * scal[S_DT];
+  const double ph = 2.0 * M.omega * tau;  // sin(2 pi omega tau) = sinpi(2 omega tau)
+  const double st = sinpi(ph);
+  const double ct = 2.0 * 3.14159265358979323846 * M.omega * cospi(ph);
+  body_motion(L, M, st, ct, nodes, nvel, i, j, k);
+}
+
+__global__ void k_centroid(GeoArgs G, Box b) {
+  BOX_THREAD(b);
+  body_centroid(G, i, j, k);
+}
+
+__global__ void k_coordd(GeoArgs G, Box b0, Box b1, Box b2) {
+  const int d = blockIdx.y;
+  const Box b = d == 0 ? b0 : (d == 1 ? b1 : b2);
+  BOX_THREAD(b);
+  body_coord_derivative(G, d, i, j, k);
+}
+
+__global__ void k_metrics(GeoArgs G, Box b) {
+  BOX_THREAD(b);
+  body_metrics(G, i, j, k);
+}
+
+__global__ void k_face_metrics(GeoArgs G, Box b0, Box b1, Box b2) {
+  const int d = blockIdx.y;
+  const Box b = d == 0 ? b0 : (d == 1 ? b1 : b2);
+  BOX_THREAD(b);
+  body_face_metrics(G, d, i, j, k);
+}
+
+__global__ void k_gcl(GeoArgs G, Box b) {
+  BOX_THREAD(b);
+  body_gcl(G, i, j, k);
+}
+
+template <int ND>
+__global__ void k_prim(RhsArgs A, Box b) {
+  BOX_THREAD(b);
+  body_prim<ND>(A, i, j, k);
+}
+
+template <int ND>
+__global__ void k_halo(RhsArgs A, int d, Box b) {
+  BOX_THREAD(b);
+  body_halo<ND>(A, d, i, j, k);
+}
+
+template <int ND>
+__global__ void k_grad1(RhsArgs A, Box b0, Box b1, Box b2) {
+  const int e = blockIdx.y;
+  const Box b = e == 0 ? b0 : (e == 1 ? b1 : b2);
+  BOX_THREAD(b);
+  body_grad1<ND>(A, e, i, j, k);
+}
+
+template <int ND>
+__global__ void k_grad2(RhsArgs A, Box b0, Box b1, Box b2) {
+  const int e = blockIdx.y;
+  const Box b = e == 0 ? b0 : (e == 1 ? b1 : b2);
+  BOX_THREAD(b);
+  body_grad2<ND>(A, e, i, j, k);
+}
+
+template <int ND, bool VISC, bool MOV>
+__global__ void __launch_bounds__(kFaceBlock) k_face(RhsArgs A, int d, Box b) {
+  BOX_THREAD(b);
+  body_face<ND, VISC, MOV>(A, d, i, j, k);
+}
+
+template <int ND, bool MOV>
+__global__ void k_update(UpdArgs U, Box b, int* err) {
+  BOX_THREAD(b);
+  if (body_update<ND, MOV>(U, i, j, k)) atomicOr(err, 1);
+}
+
+template <int ND>
+__global__ void k_dt(DtArgs D, Box b, unsigned long long* minbits) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 1.0e300;
+  if (t < box_size(b)) {
+    int i, j, k;
+    box_coord(b, t, i, j, k);
+    v = body_dt<ND>(D, i, j, k);
+  }
+  for (int off = 16; off > 0; off >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, off));
+  __shared__ double wmin[kBlock / 32];
+  if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = (threadIdx.x < blockDim.x / 32) ? wmin[threadIdx.x] : 1.0e300;
+    for (int off = 16; off > 0; off >>= 1) w = fmin(w, __shfl_xor_sync(0xffffffffu, w, off));
+    // positive doubles order like their bit patterns
+    if (threadIdx.x == 0) atomicMin(minbits, (unsigned long long)__double_as_longlong(w));
+  }
+}
+
+__global__ void k_dt_init(unsigned long long* minbits) { *minbits = (unsigned long long)__double_as_longlong(1.0e300); }
+
+__global__ void k_dt_final(double* scal, const unsigned long long* minbits, double cfl) {
+  scal[S_DT] = cfl * __longlong_as_double((long long)*minbits);
+}
+
+__global__ void k_set_scalar(double* scal, int idx, double v) { scal[idx] = v; }
+__global__ void k_advance_time(double* scal) { scal[S_T] += scal[S_DT]; }
+
+// ---------------------------------------------------------------------------
+// workspace plan
+// ---------------------------------------------------------------------------
+struct Plan {
+  size_t off[64];
+  size_t len[64];
+  int count = 0;
+  size_t total = 0;
+  int add(size_t bytes) {
+    total = (total + 255) & ~(size_t)255;
+    off[count] = total;
+    len[count] = bytes;
+    total += bytes;
+    return count++;
+  }
+};
+
+enum Slot {
+  SL_Q0, SL_Q1, SL_Q2, SL_PRIM, SL_TEMP, SL_G1, SL_G2, SL_FLUX, SL_NODES, SL_NVEL, SL_XC, SL_VC, SL_XD, SL_MH,
+  SL_DET, SL_MU, SL_MT, SL_FH, SL_FU, SL_FT, SL_GCL, SL_JAC, SL_SIGMA, SL_INFLOW, SL_SCAL, SL_ERR, SL_COUNT
+};
+
+struct Sizes {
+  size_t bytes[SL_COUNT];
+};
+
+bool valid_params(const gbr_params* p, std::string& why) {
+  if (!p) { why = "null params"; return false; }
+  if (p->ndim != 2 && p->ndim != 3) { why = "ndim must be 2 or 3"; return false; }
+  for (int d = 0; d < p->ndim; ++d) {
+    if (p->n[d] < 1) { why = "empty axis"; return false; }
+    if (p->periodic[d] && p->n[d] < H) { why = "a periodic axis needs at least 6 cells"; return false; }
+    if (!p->periodic[d] && p->ghost_nodes < E) { why = "a non-periodic axis needs ghost_nodes >= 10"; return false; }
+    if (!p->periodic[d]) {
+      for (int s = 0; s < 2; ++s) {
+        int bc = p->bc[d][s];
+        if (bc != GBR_BC_ZEROGRAD && bc != GBR_BC_INFLOW) { why = "unknown boundary condition"; return false; }
+        if (bc == GBR_BC_INFLOW && !(d == 0 && s == 0)) { why = "inflow is supported on the x-low side only"; return false; }
+      }
+    }
+  }
+  if (!(p->gamma > 1.0)) { why = "gamma must exceed 1"; return false; }
+  if (p->reynolds > 0.0 && !(p->prandtl > 0.0)) { why = "prandtl must be positive"; return false; }
+  if (p->sutherland_s > 0.0 && !(p->t_ref > 0.0)) { why = "t_ref must be positive"; return false; }
+  long long cells = (long long)p->n[0] * p->n[1] * (p->ndim == 3 ? p->n[2] : 1);
+  if (cells > (1LL << 34)) { why = "grid too large"; return false; }
+  return true;
+}
+
+Layout layout_of(const gbr_params* p) {
+  int n[3] = {p->n[0], p->n[1], p->ndim == 3 ? p->n[2] : 1};
+  return make_layout(p->ndim, n, p->periodic);
+}
+
+Plan plan_of(const gbr_params* p, const Layout& L) {
+  Plan P;
+  const size_t D = sizeof(double);
+  const int nv = L.nv, nd = L.nd;
+  const bool visc = p->reynolds > 0.0;
+  const bool mov = p->moving != 0;
+  size_t fsum = 0;
+  for (int d = 0; d < nd; ++d) fsum += (size_t)L.fcount[d];
+  P.add(D * nv * L.ncells);                       // SL_Q0
+  P.add(D * nv * L.ncells);                       // SL_Q1
+  P.add(D * nv * L.ncells);                       // SL_Q2
+  P.add(D * nv * L.pcount);                       // SL_PRIM
+  P.add(visc ? D * L.pcount : 0);                 // SL_TEMP
+  P.add(D * nd * (nv + (visc ? 1 : 0)) * L.pcount);  // SL_G1
+  P.add(D * nd * nv * L.pcount);                  // SL_G2
+  P.add(D * nv * fsum);                           // SL_FLUX
+  P.add(D * nd * L.ncount);                       // SL_NODES
+  P.add(mov ? D * nd * L.ncount : 0);             // SL_NVEL
+  P.add(D * nd * L.ecount);                       // SL_XC
+  P.add(mov ? D * nd * L.ecount : 0);             // SL_VC
+  P.add(D * 9 * L.ecount);                        // SL_XD
+  P.add(D * 9 * L.ecount);                        // SL_MH
+  P.add(D * L.ecount);                            // SL_DET
+  P.add(visc ? D * 9 * L.ecount : 0);             // SL_MU
+  P.add(mov ? D * 3 * L.ecount : 0);              // SL_MT
+  P.add(D * nd * fsum);                           // SL_FH
+  P.add(visc ? D * nd * nd * fsum : 0);           // SL_FU
+  P.add(mov ? D * fsum : 0);                      // SL_FT
+  P.add(mov ? D * L.ncells : 0);                  // SL_GCL
+  P.add(D * L.ncells);                            // SL_JAC
+  P.add(D * L.ncells);                            // SL_SIGMA
+  P.add(D * nv * L.n[1] * L.n[2]);                // SL_INFLOW
+  P.add(D * S_NSCAL);                             // SL_SCAL
+  P.add(sizeof(int) * 4);                         // SL_ERR
+  P.total = (P.total + 255) & ~(size_t)255;
+  return P;
+}
+
+thread_local std::string g_global_error;
+
+Box make_box(const Layout& L, const int lo[3], const int hi[3]) {
+  Box b;
+  for (int d = 0; d < 3; ++d) {
+    if (d < L.nd) { b.lo[d] = lo[d]; b.hi[d] = hi[d]; }
+    else { b.lo[d] = 0; b.hi[d] = 1; }
+  }
+  return b;
+}
+
+// box with per-axis pads: [lo_pad below 0, n + hi_pad)
+Box pad_box(const Layout& L, int lo_pad, int hi_pad) {
+  int lo[3], hi[3];
+  for (int d = 0; d < 3; ++d) { lo[d] = -lo_pad; hi[d] = L.n[d] + hi_pad; }
+  return make_box(L, lo, hi);
+}
+
+unsigned grid_of(const Box& b, int block) {
+  long long n = box_size(b);
+  return (unsigned)((n + block - 1) / block);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct gbr_ctx {
+  gbr_params p;
+  Layout L;
+  Phys ph;
+  cudaStream_t stream;
+  char* ws;
+  size_t ws_bytes;
+  Plan plan;
+  double* q[3];
+  double *prim, *temp, *g1[3], *g2[3], *flux[3];
+  double *nodes, *nvel, *xc, *vc, *xd, *mh, *det, *mu, *mt, *fh[3], *fu[3], *ft[3], *gcl, *jac;
+  double *sigma, *inflow, *scal;
+  int* err;
+  bool visc, mov, have_sponge, have_motion, metrics_ready;
+  double qamb[5];
+  Motion motion;
+  double last_fixed_dt;
+  std::string last_error;
+};
+
+namespace {
+
+gbr_status fail(gbr_ctx* c, gbr_status s, const std::string& m) {
+  if (c) c->last_error = m;
+  g_global_error = m;
+  return s;
+}
+
+gbr_status cuda_check(gbr_ctx* c, cudaError_t e, const char* what) {
+  if (e != cudaSuccess) return fail(c, GBR_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return GBR_OK;
+}
+
+#define CK(expr, what)                                       \
+  do {                                                       \
+    gbr_status _s = cuda_check(c, (expr), what);             \
+    if (_s != GBR_OK) return _s;                             \
+  } while (0)
+#define CKL(what) CK(cudaGetLastError(), what)
+
+GeoArgs geo_args(gbr_ctx* c) {
+  GeoArgs G;
+  G.L = c->L;
+  G.nodes = c->nodes;
+  G.nvel = c->nvel;
+  G.xc = c->xc;
+  G.vc = c->vc;
+  G.xd = c->xd;
+  G.mh = c->mh;
+  G.det = c->det;
+  G.mu = c->mu;
+  G.mt = c->mt;
+  for (int d = 0; d < 3; ++d) { G.fh[d] = c->fh[d]; G.fu[d] = c->fu[d]; G.ft[d] = c->ft[d]; }
+  G.gcl = c->gcl;
+  G.jac = c->jac;
+  G.viscous = c->visc;
+  G.moving = c->mov;
+  return G;
+}
+
+// Unwrap periodic axes (node n = node 0 + period vector) and copy the supplied
+// ghost layers of non-periodic axes into the extended node box [-E, n+E].
+gbr_status build_extended(gbr_ctx* c, const double* src, bool shift, std::vector<double>& out) {
+  const Layout& L = c->L;
+  const int nd = L.nd;
+  const int G = c->p.ghost_nodes;
+  int Nn[3], off[3];
+  for (int d = 0; d < 3; ++d) {
+    if (d >= nd) { Nn[d] = 1; off[d] = 0; continue; }
+    Nn[d] = c->p.periodic[d] ? L.n[d] + 1 : L.n[d] + 1 + 2 * G;
+    off[d] = c->p.periodic[d] ? 0 : G;
+  }
+  const size_t NN = (size_t)Nn[0] * Nn[1] * Nn[2];
+  auto sid = [&](int a, int s0, int s1, int s2) { return (size_t)a * NN + ((size_t)s2 * Nn[1] + s1) * Nn[0] + s0; };
+  double per[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  if (shift) {
+    double scale = 0.0;
+    for (size_t m = 0; m < (size_t)nd * NN; ++m) scale = std::fmax(scale, std::fabs(src[m]));
+    for (int d = 0; d < nd; ++d) {
+      if (!c->p.periodic[d]) continue;
+      int s0[3] = {off[0], off[1], off[2]}, s1[3] = {off[0], off[1], off[2]};
+      s1[d] = L.n[d];
+      for (int a = 0; a < nd; ++a) per[d][a] = src[sid(a, s1[0], s1[1], s1[2])] - src[sid(a, s0[0], s0[1], s0[2])];
+      for (int s2 = 0; s2 < Nn[2]; ++s2)
+        for (int s1i = 0; s1i < Nn[1]; ++s1i)
+          for (int s0i = 0; s0i < Nn[0]; ++s0i) {
+            int s[3] = {s0i, s1i, s2};
+            if (s[d] != 0) continue;
+            int t[3] = {s0i, s1i, s2};
+            t[d] = L.n[d];
+            for (int a = 0; a < nd; ++a) {
+              double diff = src[sid(a, t[0], t[1], t[2])] - src[sid(a, s[0], s[1], s[2])];
+              if (std::fabs(diff - per[d][a]) > 1e-12 * (scale + 1.0))
+                return fail(c, GBR_EINVAL, "periodic axis is not closed by a constant period vector");
+            }
+          }
+    }
+  }
+  out.assign((size_t)nd * L.ncount, 0.0);
+  for (int mk = -L.he[2]; mk < L.nn[2] - L.he[2]; ++mk)
+    for (int mj = -L.he[1]; mj < L.nn[1] - L.he[1]; ++mj)
+      for (int mi = -L.he[0]; mi < L.nn[0] - L.he[0]; ++mi) {
+        int m[3] = {mi, mj, mk}, s[3];
+        int wraps[3] = {0, 0, 0};
+        for (int d = 0; d < 3; ++d) {
+          if (d >= nd) { s[d] = 0; continue; }
+          if (c->p.periodic[d]) {
+            int n = L.n[d];
+            int base = ((m[d] % n) + n) % n;
+            wraps[d] = (m[d] - base) / n;
+            s[d] = base;
+          } else {
+            s[d] = m[d] + off[d];
+          }
+        }
+        const long long id = nidx(L, mi, mj, mk);
+        for (int a = 0; a < nd; ++a) {
+          double v = src[sid(a, s[0], s[1], s[2])];
+          if (shift)
+            for (int d = 0; d < nd; ++d) v += wraps[d] * per[d][a];
+          out[(size_t)a * L.ncount + id] = v;
+        }
+      }
+  return GBR_OK;
+}
+
+gbr_status upload_nodes(gbr_ctx* c, const double* nodes, const double* vel) {
+  std::vector<double> ext, extv;
+  gbr_status s = build_extended(c, nodes, true, ext);
+  if (s != GBR_OK) return s;
+  CK(cudaMemcpyAsync(c->nodes, ext.data(), ext.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream), "upload nodes");
+  if (c->mov) {
+    if (vel) {
+      s = build_extended(c, vel, false, extv);
+      if (s != GBR_OK) return s;
+    } else {
+      extv.assign(ext.size(), 0.0);
+    }
+    CK(cudaMemcpyAsync(c->nvel, extv.data(), extv.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+       "upload node velocities");
+  }
+  CK(cudaStreamSynchronize(c->stream), "upload sync");  // host vectors go out of scope
+  return GBR_OK;
+}
+
+// Index boxes of every launch (shared by all launch sites).
+struct GeoBoxes {
+  Box ext;      // centroids: cells [-E, n+E)
+  Box coordd[3];  // D_d of the coordinates: [-5, n+5) along d, [-E, n+E) elsewhere
+  Box metrics;  // cells [-5, n+5)
+  Box faces[3]; // interfaces i+1/2, i in [-1, n-1] along d, interior elsewhere
+  Box inner;    // interior cells
+  Box nodes;    // extended nodes [-E, n+E]
+};
+
+GeoBoxes geo_boxes(const Layout& L) {
+  GeoBoxes B;
+  B.ext = pad_box(L, E, E);
+  for (int d = 0; d < 3; ++d) {
+    int lo[3], hi[3];
+    for (int e = 0; e < 3; ++e) { lo[e] = -E; hi[e] = L.n[e] + E; }
+    lo[d] = -5;
+    hi[d] = L.n[d] + 5;
+    B.coordd[d] = make_box(L, lo, hi);
+    int flo[3] = {0, 0, 0}, fhi[3] = {L.n[0], L.n[1], L.n[2]};
+    flo[d] = -1;
+    fhi[d] = L.n[d];
+    B.faces[d] = make_box(L, flo, fhi);
+  }
+  B.metrics = pad_box(L, 5, 5);
+  B.inner = pad_box(L, 0, 0);
+  int lo[3], hi[3];
+  for (int d = 0; d < 3; ++d) { lo[d] = -E; hi[d] = L.n[d] + E + 1; }
+  B.nodes = make_box(L, lo, hi);
+  return B;
+}
+
+struct RhsBoxes {
+  Box inner;
+  Box halo[3];   // cross-section of axis d: padded on axes < d, interior on axes > d
+  Box grad1[3];  // [-3, n+3) along e, [-1, n+1) elsewhere
+  Box grad2[3];  // [-2, n+2) along e, interior elsewhere
+  Box faces[3];
+};
+
+RhsBoxes rhs_boxes(const Layout& L) {
+  RhsBoxes B;
+  B.inner = pad_box(L, 0, 0);
+  for (int d = 0; d < 3; ++d) {
+    int lo[3], hi[3];
+    for (int e = 0; e < 3; ++e) {
+      lo[e] = (e < d) ? -H : 0;
+      hi[e] = (e < d) ? L.n[e] + H : L.n[e];
+    }
+    lo[d] = 0;
+    hi[d] = 1;
+    B.halo[d] = make_box(L, lo, hi);
+    int lo1[3], hi1[3], lo2[3], hi2[3];
+    for (int a = 0; a < 3; ++a) {
+      lo1[a] = -1; hi1[a] = L.n[a] + 1;
+      lo2[a] = 0; hi2[a] = L.n[a];
+    }
+    lo1[d] = -3; hi1[d] = L.n[d] + 3;
+    lo2[d] = -2; hi2[d] = L.n[d] + 2;
+    B.grad1[d] = make_box(L, lo1, hi1);
+    B.grad2[d] = make_box(L, lo2, hi2);
+    int flo[3] = {0, 0, 0}, fhi[3] = {L.n[0], L.n[1], L.n[2]};
+    flo[d] = -1;
+    fhi[d] = L.n[d];
+    B.faces[d] = make_box(L, flo, fhi);
+  }
+  return B;
+}
+
+gbr_status run_geometry(gbr_ctx* c) {
+  const Layout& L = c->L;
+  GeoArgs G = geo_args(c);
+  cudaStream_t st = c->stream;
+  const GeoBoxes B = geo_boxes(L);
+  k_centroid<<<grid_of(B.ext, kBlock), kBlock, 0, st>>>(G, B.ext);
+  CKL("k_centroid");
+  unsigned gmax = 0;
+  for (int d = 0; d < L.nd; ++d) gmax = std::max(gmax, grid_of(B.coordd[d], kBlock));
+  k_coordd<<<dim3(gmax, L.nd), kBlock, 0, st>>>(G, B.coordd[0], B.coordd[1], B.coordd[2]);
+  CKL("k_coordd");
+  k_metrics<<<grid_of(B.metrics, kBlock), kBlock, 0, st>>>(G, B.metrics);
+  CKL("k_metrics");
+  gmax = 0;
+  for (int d = 0; d < L.nd; ++d) gmax = std::max(gmax, grid_of(B.faces[d], kBlock));
+  k_face_metrics<<<dim3(gmax, L.nd), kBlock, 0, st>>>(G, B.faces[0], B.faces[1], B.faces[2]);
+  CKL("k_face_metrics");
+  k_gcl<<<grid_of(B.inner, kBlock), kBlock, 0, st>>>(G, B.inner);
+  CKL("k_gcl");
+  return GBR_OK;
+}
+
+gbr_status run_motion(gbr_ctx* c, double stage_c) {
+  const Box bn = geo_boxes(c->L).nodes;
+  k_motion<<<grid_of(bn, kBlock), kBlock, 0, c->stream>>>(c->L, c->motion, c->scal, stage_c, c->nodes, c->nvel, bn);
+  CKL("k_motion");
+  return GBR_OK;
+}
+
+RhsArgs rhs_args(gbr_ctx* c, const double* q) {
+  RhsArgs A;
+  A.L = c->L;
+  A.ph = c->ph;
+  A.q = q;
+  A.prim = c->prim;
+  A.temp = c->temp;
+  for (int d = 0; d < 3; ++d) {
+    A.g1[d] = c->g1[d];
+    A.g2[d] = c->g2[d];
+    A.fh[d] = c->fh[d];
+    A.fu[d] = c->fu[d];
+    A.ft[d] = c->ft[d];
+    A.flux[d] = c->flux[d];
+  }
+  A.inflow = c->inflow;
+  for (int d = 0; d < 3; ++d)
+    for (int s = 0; s < 2; ++s) A.bc[d][s] = c->p.bc[d][s];
+  A.viscous = c->visc;
+  return A;
+}
+
+template <int ND>
+gbr_status launch_face(gbr_ctx* c, const RhsArgs& A, int d, const Box& b) {
+  const unsigned g = grid_of(b, kFaceBlock);
+  cudaStream_t st = c->stream;
+  if (c->visc) {
+    if (c->mov) k_face<ND, true, true><<<g, kFaceBlock, 0, st>>>(A, d, b);
+    else k_face<ND, true, false><<<g, kFaceBlock, 0, st>>>(A, d, b);
+  } else {
+    if (c->mov) k_face<ND, false, true><<<g, kFaceBlock, 0, st>>>(A, d, b);
+    else k_face<ND, false, false><<<g, kFaceBlock, 0, st>>>(A, d, b);
+  }
+  CKL("k_face");
+  return GBR_OK;
+}
+
+// one evaluation of L(qs): out = L (mode 0) or the RK combination (mode 1)
+template <int ND>
+gbr_status run_rhs_nd(gbr_ctx* c, const double* qs, const double* q0, double* out, int mode, double ca, double cb,
+                      double cc) {
+  const Layout& L = c->L;
+  cudaStream_t st = c->stream;
+  RhsArgs A = rhs_args(c, qs);
+  const RhsBoxes B = rhs_boxes(L);
+  const Box bi = B.inner;
+  k_prim<ND><<<grid_of(bi, kBlock), kBlock, 0, st>>>(A, bi);
+  CKL("k_prim");
+  for (int d = 0; d < ND; ++d) {
+    k_halo<ND><<<grid_of(B.halo[d], kBlock), kBlock, 0, st>>>(A, d, B.halo[d]);
+    CKL("k_halo");
+  }
+  unsigned g1 = 0, g2 = 0;
+  for (int e = 0; e < ND; ++e) {
+    g1 = std::max(g1, grid_of(B.grad1[e], kBlock));
+    g2 = std::max(g2, grid_of(B.grad2[e], kBlock));
+  }
+  k_grad1<ND><<<dim3(g1, ND), kBlock, 0, st>>>(A, B.grad1[0], B.grad1[1], B.grad1[2]);
+  CKL("k_grad1");
+  k_grad2<ND><<<dim3(g2, ND), kBlock, 0, st>>>(A, B.grad2[0], B.grad2[1], B.grad2[2]);
+  CKL("k_grad2");
+  for (int d = 0; d < ND; ++d) {
+    gbr_status s = launch_face<ND>(c, A, d, B.faces[d]);
+    if (s != GBR_OK) return s;
+  }
+  UpdArgs U;
+  U.L = L;
+  for (int d = 0; d < 3; ++d) U.flux[d] = c->flux[d];
+  U.qs = qs;
+  U.q0 = q0;
+  U.out = out;
+  U.jac = c->jac;
+  U.gcl = c->gcl;
+  U.sigma = c->have_sponge ? c->sigma : nullptr;
+  for (int v = 0; v < 5; ++v) U.qamb[v] = c->qamb[v];
+  U.dt = c->scal + S_DT;
+  U.ca = ca;
+  U.cb = cb;
+  U.cc = cc;
+  U.mode = mode;
+  if (c->mov) k_update<ND, true><<<grid_of(bi, kBlock), kBlock, 0, st>>>(U, bi, c->err);
+  else k_update<ND, false><<<grid_of(bi, kBlock), kBlock, 0, st>>>(U, bi, c->err);
+  CKL("k_update");
+  return GBR_OK;
+}
+
+gbr_status run_rhs(gbr_ctx* c, const double* qs, const double* q0, double* out, int mode, double ca, double cb,
+                   double cc) {
+  return c->L.nd == 3 ? run_rhs_nd<3>(c, qs, q0, out, mode, ca, cb, cc)
+                      : run_rhs_nd<2>(c, qs, q0, out, mode, ca, cb, cc);
+}
+
+gbr_status run_dt(gbr_ctx* c, double cfl) {
+  const Layout& L = c->L;
+  DtArgs D;
+  D.L = L;
+  D.ph = c->ph;
+  D.q = c->q[0];
+  D.mh = c->mh;
+  D.mt = c->mov ? c->mt : nullptr;
+  D.jac = c->jac;
+  Box bi = pad_box(L, 0, 0);
+  unsigned long long* bits = reinterpret_cast<unsigned long long*>(c->scal + S_DTMIN);
+  k_dt_init<<<1, 1, 0, c->stream>>>(bits);
+  CKL("k_dt_init");
+  if (L.nd == 3) k_dt<3><<<grid_of(bi, kBlock), kBlock, 0, c->stream>>>(D, bi, bits);
+  else k_dt<2><<<grid_of(bi, kBlock), kBlock, 0, c->stream>>>(D, bi, bits);
+  CKL("k_dt");
+  k_dt_final<<<1, 1, 0, c->stream>>>(c->scal, bits, cfl);
+  CKL("k_dt_final");
+  return GBR_OK;
+}
+
+void carve(gbr_ctx* c) {
+  const Plan& P = c->plan;
+  const Layout& L = c->L;
+  auto ptr = [&](int slot) -> double* { return P.len[slot] ? (double*)(c->ws + P.off[slot]) : nullptr; };
+  for (int s = 0; s < 3; ++s) c->q[s] = ptr(SL_Q0 + s);
+  c->prim = ptr(SL_PRIM);
+  c->temp = ptr(SL_TEMP);
+  const int nv = L.nv, nd = L.nd;
+  const int n1 = nv + (c->visc ? 1 : 0);
+  size_t foff = 0;
+  for (int d = 0; d < 3; ++d) {
+    c->g1[d] = (d < nd) ? ptr(SL_G1) + (size_t)d * n1 * L.pcount : nullptr;
+    c->g2[d] = (d < nd) ? ptr(SL_G2) + (size_t)d * nv * L.pcount : nullptr;
+    c->flux[d] = (d < nd) ? ptr(SL_FLUX) + (size_t)nv * foff : nullptr;
+    c->fh[d] = (d < nd) ? ptr(SL_FH) + (size_t)nd * foff : nullptr;
+    c->fu[d] = (d < nd && c->visc) ? ptr(SL_FU) + (size_t)nd * nd * foff : nullptr;
+    c->ft[d] = (d < nd && c->mov) ? ptr(SL_FT) + foff : nullptr;
+    if (d < nd) foff += (size_t)L.fcount[d];
+  }
+  c->nodes = ptr(SL_NODES);
+  c->nvel = ptr(SL_NVEL);
+  c->xc = ptr(SL_XC);
+  c->vc = ptr(SL_VC);
+  c->xd = ptr(SL_XD);
+  c->mh = ptr(SL_MH);
+  c->det = ptr(SL_DET);
+  c->mu = ptr(SL_MU);
+  c->mt = ptr(SL_MT);
+  c->gcl = ptr(SL_GCL);
+  c->jac = ptr(SL_JAC);
+  c->sigma = ptr(SL_SIGMA);
+  c->inflow = ptr(SL_INFLOW);
+  c->scal = ptr(SL_SCAL);
+  c->err = (int*)(c->ws + P.off[SL_ERR]);
+}
+
+Phys phys_of(const gbr_params* p) {
+  Phys ph;
+  ph.gamma = p->gamma;
+  ph.gm1 = p->gamma - 1.0;
+  ph.igm1 = 1.0 / (p->gamma - 1.0);
+  ph.viscous = p->reynolds > 0.0;
+  ph.mu_ref = ph.viscous ? 1.0 / p->reynolds : 0.0;
+  ph.sutherland = p->sutherland_s > 0.0;
+  ph.suth_s = p->sutherland_s;
+  ph.it_ref = p->t_ref > 0.0 ? 1.0 / p->t_ref : 1.0;
+  ph.half_alpha_d = 0.5 * p->alpha_damping;
+  ph.mp_alpha = p->mp_alpha;
+  ph.mp_beta = p->mp_beta;
+  ph.mp_eps = p->mp_eps;
+  ph.kfac = ph.viscous ? p->gamma / ((p->gamma - 1.0) * p->prandtl) : 0.0;
+  ph.dt_visc_fac = ph.viscous ? std::fmax(4.0 / 3.0, p->gamma / p->prandtl) : 0.0;
+  return ph;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+size_t gbr_workspace_bytes(const gbr_params* p) {
+  std::string why;
+  if (!valid_params(p, why)) { g_global_error = why; return 0; }
+  Layout L = layout_of(p);
+  return plan_of(p, L).total;
+}
+
+gbr_status gbr_create(const gbr_params* p, const double* nodes, const double* node_vel, void* d_workspace,
+                      size_t ws_bytes, void* stream, gbr_ctx** out) {
+  if (!out) return fail(nullptr, GBR_EINVAL, "null output pointer");
+  *out = nullptr;
+  std::string why;
+  if (!valid_params(p, why)) return fail(nullptr, GBR_EINVAL, why);
+  if (!nodes) return fail(nullptr, GBR_EINVAL, "null node array");
+  if (!d_workspace) return fail(nullptr, GBR_EINVAL, "null workspace");
+  if (((uintptr_t)d_workspace & 255) != 0) return fail(nullptr, GBR_EINVAL, "workspace must be 256-byte aligned");
+  Layout L = layout_of(p);
+  Plan P = plan_of(p, L);
+  if (ws_bytes < P.total) return fail(nullptr, GBR_ENOMEM, "workspace smaller than gbr_workspace_bytes");
+  gbr_ctx* c = new gbr_ctx();
+  c->p = *p;
+  if (p->ndim == 2) c->p.n[2] = 1;
+  c->L = L;
+  c->ph = phys_of(p);
+  c->stream = (cudaStream_t)stream;
+  c->ws = (char*)d_workspace;
+  c->ws_bytes = ws_bytes;
+  c->plan = P;
+  c->visc = p->reynolds > 0.0;
+  c->mov = p->moving != 0;
+  c->have_sponge = false;
+  c->have_motion = false;
+  c->metrics_ready = false;
+  c->last_fixed_dt = 0.0;
+  for (int v = 0; v < 5; ++v) c->qamb[v] = 0.0;
+  carve(c);
+  cudaError_t e = cudaMemsetAsync(c->ws, 0, P.total, c->stream);
+  if (e != cudaSuccess) {
+    gbr_status s = fail(c, GBR_ECUDA, std::string("clear workspace: ") + cudaGetErrorString(e));
+    delete c;
+    return s;
+  }
+  gbr_status s = upload_nodes(c, nodes, node_vel);
+  if (s != GBR_OK) {
+    g_global_error = c->last_error;
+    delete c;
+    return s;
+  }
+  *out = c;
+  return GBR_OK;
+}
+
+gbr_status gbr_compute_metrics(gbr_ctx* c) {
+  if (!c) return fail(nullptr, GBR_EINVAL, "null context");
+  gbr_status s = run_geometry(c);
+  if (s != GBR_OK) return s;
+  c->metrics_ready = true;
+  return GBR_OK;
+}
+
+gbr_status gbr_move_mesh(gbr_ctx* c, const double* nodes, const double* node_vel) {
+  if (!c || !nodes) return fail(c, GBR_EINVAL, "null argument");
+  if (node_vel && !c->mov) return fail(c, GBR_EINVAL, "node velocities need params.moving = 1");
+  c->have_motion = false;
+  gbr_status s = upload_nodes(c, nodes, node_vel);
+  if (s != GBR_OK) return s;
+  return gbr_compute_metrics(c);
+}
+
+gbr_status gbr_set_motion(gbr_ctx* c, const gbr_motion* m, double t0) {
+  if (!c || !m) return fail(c, GBR_EINVAL, "null argument");
+  if (!c->mov) return fail(c, GBR_EINVAL, "a motion needs params.moving = 1");
+  for (int d = 0; d < c->L.nd; ++d)
+    if (!c->p.periodic[d]) return fail(c, GBR_EINVAL, "analytic motion needs periodic axes");
+  Motion M;
+  for (int a = 0; a < 3; ++a) {
+    M.origin[a] = m->origin[a];
+    M.h[a] = m->h[a];
+    M.amp[a] = m->amp[a];
+    for (int b = 0; b < 3; ++b) M.k[a][b] = m->k[a][b];
+  }
+  M.omega = m->omega;
+  c->motion = M;
+  c->have_motion = true;
+  k_set_scalar<<<1, 1, 0, c->stream>>>(c->scal, S_T, t0);
+  CKL("k_set_scalar");
+  gbr_status s = run_motion(c, 0.0);
+  if (s != GBR_OK) return s;
+  return gbr_compute_metrics(c);
+}
+
+gbr_status gbr_set_state(gbr_ctx* c, const double* q, int on_device) {
+  if (!c || !q) return fail(c, GBR_EINVAL, "null argument");
+  const size_t bytes = sizeof(double) * c->L.nv * c->L.ncells;
+  CK(cudaMemcpyAsync(c->q[0], q, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream),
+     "set state");
+  if (!on_device) CK(cudaStreamSynchronize(c->stream), "set state sync");
+  return GBR_OK;
+}
+
+gbr_status gbr_get_state(gbr_ctx* c, double* q, int on_device) {
+  if (!c || !q) return fail(c, GBR_EINVAL, "null argument");
+  const size_t bytes = sizeof(double) * c->L.nv * c->L.ncells;
+  CK(cudaMemcpyAsync(q, c->q[0], bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream),
+     "get state");
+  if (!on_device) CK(cudaStreamSynchronize(c->stream), "get state sync");
+  return GBR_OK;
+}
+
+gbr_status gbr_set_inflow(gbr_ctx* c, const double* prim) {
+  if (!c || !prim) return fail(c, GBR_EINVAL, "null argument");
+  const size_t bytes = sizeof(double) * c->L.nv * c->L.n[1] * c->L.n[2];
+  CK(cudaMemcpyAsync(c->inflow, prim, bytes, cudaMemcpyHostToDevice, c->stream), "set inflow");
+  CK(cudaStreamSynchronize(c->stream), "set inflow sync");
+  return GBR_OK;
+}
+
+gbr_status gbr_set_sponge(gbr_ctx* c, const double* sigma, const double* q_amb) {
+  if (!c) return fail(c, GBR_EINVAL, "null context");
+  if (!sigma) { c->have_sponge = false; return GBR_OK; }
+  if (!q_amb) return fail(c, GBR_EINVAL, "null ambient state");
+  CK(cudaMemcpyAsync(c->sigma, sigma, sizeof(double) * c->L.ncells, cudaMemcpyHostToDevice, c->stream), "set sponge");
+  CK(cudaStreamSynchronize(c->stream), "set sponge sync");
+  for (int v = 0; v < c->L.nv; ++v) c->qamb[v] = q_amb[v];
+  c->have_sponge = true;
+  return GBR_OK;
+}
+
+gbr_status gbr_rhs(gbr_ctx* c, double* dqdt) {
+  if (!c || !dqdt) return fail(c, GBR_EINVAL, "null argument");
+  if (!c->metrics_ready) return fail(c, GBR_ESTATE, "metrics not computed");
+  return run_rhs(c, c->q[0], c->q[0], dqdt, 0, 0.0, 0.0, 1.0);
+}
+
+gbr_status gbr_compute_dt(gbr_ctx* c, double cfl, double* dt_out) {
+  if (!c) return fail(c, GBR_EINVAL, "null context");
+  if (!(cfl > 0.0)) return fail(c, GBR_EINVAL, "cfl must be positive");
+  if (!c->metrics_ready) return fail(c, GBR_ESTATE, "metrics not computed");
+  gbr_status s = run_dt(c, cfl);
+  if (s != GBR_OK) return s;
+  if (dt_out) {
+    CK(cudaMemcpyAsync(dt_out, c->scal + S_DT, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "read dt");
+    CK(cudaStreamSynchronize(c->stream), "read dt sync");
+  }
+  return GBR_OK;
+}
+
+gbr_status gbr_rk_step(gbr_ctx* c, double cfl_or_neg_dt) {
+  if (!c) return fail(c, GBR_EINVAL, "null context");
+  if (!c->metrics_ready) return fail(c, GBR_ESTATE, "metrics not computed");
+  if (!(cfl_or_neg_dt != 0.0) || std::isnan(cfl_or_neg_dt)) return fail(c, GBR_EINVAL, "cfl_or_neg_dt must be nonzero");
+  gbr_status s;
+  // geometry at t^n (moving mesh), then the time step from Q^n
+  if (c->have_motion) {
+    if ((s = run_motion(c, 0.0)) != GBR_OK) return s;
+    if ((s = run_geometry(c)) != GBR_OK) return s;
+  }
+  if (cfl_or_neg_dt > 0.0) {
+    if ((s = run_dt(c, cfl_or_neg_dt)) != GBR_OK) return s;
+  } else {
+    k_set_scalar<<<1, 1, 0, c->stream>>>(c->scal, S_DT, -cfl_or_neg_dt);
+    CKL("k_set_scalar");
+  }
+  // App. B: Q1 = Qn + dt L(Qn); Q2 = 3/4 Qn + 1/4 Q1 + 1/4 dt L(Q1); Qn+1 = 1/3 Qn + 2/3 Q2 + 2/3 dt L(Q2)
+  if ((s = run_rhs(c, c->q[0], c->q[0], c->q[1], 1, 1.0, 0.0, 1.0)) != GBR_OK) return s;
+  if (c->have_motion) {
+    if ((s = run_motion(c, 1.0)) != GBR_OK) return s;
+    if ((s = run_geometry(c)) != GBR_OK) return s;
+  }
+  if ((s = run_rhs(c, c->q[1], c->q[0], c->q[2], 1, 0.75, 0.25, 0.25)) != GBR_OK) return s;
+  if (c->have_motion) {
+    if ((s = run_motion(c, 0.5)) != GBR_OK) return s;
+    if ((s = run_geometry(c)) != GBR_OK) return s;
+  }
+  if ((s = run_rhs(c, c->q[2], c->q[0], c->q[0], 1, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0)) != GBR_OK) return s;
+  k_advance_time<<<1, 1, 0, c->stream>>>(c->scal);
+  CKL("k_advance_time");
+  return GBR_OK;
+}
+
+gbr_status gbr_sync(gbr_ctx* c, double timeout_s) {
+  if (!c) return fail(c, GBR_EINVAL, "null context");
+  auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaStreamQuery(c->stream);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) return cuda_check(c, e, "stream query");
+    double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (timeout_s > 0.0 && el > timeout_s) return fail(c, GBR_ETIMEOUT, "stream did not drain before the deadline");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  int err = 0;
+  CK(cudaMemcpy(&err, c->err, sizeof(int), cudaMemcpyDeviceToHost), "read error flag");
+  if (err) return fail(c, GBR_ENONFINITE, "non-finite state or non-positive density on the device");
+  return GBR_OK;
+}
+
+gbr_status gbr_get_time(gbr_ctx* c, double* t, double* dt) {
+  if (!c) return fail(c, GBR_EINVAL, "null context");
+  double s[2];
+  CK(cudaMemcpyAsync(s, c->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "read time");
+  CK(cudaStreamSynchronize(c->stream), "read time sync");
+  if (dt) *dt = s[S_DT];
+  if (t) *t = s[S_T];
+  return GBR_OK;
+}
+
+gbr_status gbr_get_field(gbr_ctx* c, int which, int dir, double* out) {
+  if (!c || !out) return fail(c, GBR_EINVAL, "null argument");
+  const Layout& L = c->L;
+  const int nd = L.nd;
+  if (dir < 0 || dir >= nd) dir = 0;
+  CK(cudaStreamSynchronize(c->stream), "get field sync");
+  auto fetch = [&](const double* src, size_t count, std::vector<double>& h) -> gbr_status {
+    h.resize(count);
+    CK(cudaMemcpy(h.data(), src, count * sizeof(double), cudaMemcpyDeviceToHost), "get field copy");
+    return GBR_OK;
+  };
+  std::vector<double> h;
+  gbr_status s;
+  auto cells_from_ext = [&](const std::vector<double>& src, size_t off, double* dst) {
+    size_t m = 0;
+    for (int k = 0; k < L.n[2]; ++k)
+      for (int j = 0; j < L.n[1]; ++j)
+        for (int i = 0; i < L.n[0]; ++i) dst[m++] = src[off + eidx(L, i, j, k)];
+  };
+  switch (which) {
+    case GBR_FIELD_CELL_METRICS:
+      if ((s = fetch(c->mh, 9 * L.ecount, h)) != GBR_OK) return s;
+      for (int e = 0; e < nd; ++e)
+        for (int a = 0; a < nd; ++a) cells_from_ext(h, (size_t)(e * 3 + a) * L.ecount, out + (size_t)(e * nd + a) * L.ncells);
+      return GBR_OK;
+    case GBR_FIELD_CELL_DET:
+      if ((s = fetch(c->det, L.ecount, h)) != GBR_OK) return s;
+      cells_from_ext(h, 0, out);
+      return GBR_OK;
+    case GBR_FIELD_CELL_TIME:
+      if (!c->mov) return fail(c, GBR_ESTATE, "not a moving mesh");
+      if ((s = fetch(c->mt, 3 * L.ecount, h)) != GBR_OK) return s;
+      for (int e = 0; e < nd; ++e) cells_from_ext(h, (size_t)e * L.ecount, out + (size_t)e * L.ncells);
+      return GBR_OK;
+    case GBR_FIELD_FACE_HAT:
+      if ((s = fetch(c->fh[dir], (size_t)nd * L.fcount[dir], h)) != GBR_OK) return s;
+      std::memcpy(out, h.data(), h.size() * sizeof(double));
+      return GBR_OK;
+    case GBR_FIELD_FACE_UNHAT:
+      if (!c->visc) return fail(c, GBR_ESTATE, "not a viscous case");
+      if ((s = fetch(c->fu[dir], (size_t)nd * nd * L.fcount[dir], h)) != GBR_OK) return s;
+      std::memcpy(out, h.data(), h.size() * sizeof(double));
+      return GBR_OK;
+    case GBR_FIELD_FACE_TIME:
+      if (!c->mov) return fail(c, GBR_ESTATE, "not a moving mesh");
+      if ((s = fetch(c->ft[dir], (size_t)L.fcount[dir], h)) != GBR_OK) return s;
+      std::memcpy(out, h.data(), h.size() * sizeof(double));
+      return GBR_OK;
+    case GBR_FIELD_GCL:
+      if (!c->mov) return fail(c, GBR_ESTATE, "not a moving mesh");
+      if ((s = fetch(c->gcl, (size_t)L.ncells, h)) != GBR_OK) return s;
+      std::memcpy(out, h.data(), h.size() * sizeof(double));
+      return GBR_OK;
+    case GBR_FIELD_FACE_FLUX:
+      if ((s = fetch(c->flux[dir], (size_t)L.nv * L.fcount[dir], h)) != GBR_OK) return s;
+      std::memcpy(out, h.data(), h.size() * sizeof(double));
+      return GBR_OK;
+    default:
+      return fail(c, GBR_EINVAL, "unknown field");
+  }
+}
+
+const char* gbr_last_error(const gbr_ctx* c) { return c ? c->last_error.c_str() : g_global_error.c_str(); }
+const char* gbr_last_global_error(void) { return g_global_error.c_str(); }
+
+void gbr_destroy(gbr_ctx* c) { delete c; }
+
+}  // extern "C"

@@ -1,0 +1,780 @@
+// Device-side layouts and per-element bodies of the sm_103a library.
+//
+// Every kernel of the library is a thin __global__ wrapper that maps a thread
+// to one element (cell, face or cross-section cell) of a box and calls one of
+// the bodies below.  All arithmetic is FP64.  Equation and section numbers
+// refer to arXiv 2303.10785.
+#pragma once
+#include <cmath>
+#include <cstdint>
+
+#ifdef __CUDACC__
+#define GBR_HD __host__ __device__ __forceinline__
+#else
+#define GBR_HD inline
+#endif
+
+namespace gbr {
+
+constexpr int H = 6;   // halo of primitive-derived arrays: an interface needs cells i-5..i+6
+constexpr int E = 10;  // geometry extension: metric derivative (reach 5) of products that are themselves
+                       // metric derivatives (reach 5)
+
+// ---------------------------------------------------------------------------
+// Layouts
+// ---------------------------------------------------------------------------
+struct Layout {
+  int nd, nv;
+  int n[3];
+  int per[3];
+  int hp[3];          // halo per axis (H on active axes)
+  int pn[3];          // padded extents
+  long long ps[3];    // padded strides
+  long long pcount;
+  int he[3];          // geometry extension per axis (E on active axes)
+  int en[3];
+  long long es[3];
+  long long ecount;
+  int fn[3][3];       // face-array extents for direction d
+  long long fs[3][3]; // face-array strides
+  long long fcount[3];
+  long long ncells;
+  int nn[3];          // extended node extents (n + 2E + 1 on active axes)
+  long long ns[3];
+  long long ncount;
+};
+
+inline Layout make_layout(int nd, const int* n, const int* periodic) {
+  Layout L;
+  L.nd = nd;
+  L.nv = nd + 2;
+  for (int d = 0; d < 3; ++d) {
+    bool act = d < nd;
+    L.n[d] = act ? n[d] : 1;
+    L.per[d] = act ? periodic[d] : 1;
+    L.hp[d] = act ? H : 0;
+    L.pn[d] = L.n[d] + 2 * L.hp[d];
+    L.he[d] = act ? E : 0;
+    L.en[d] = L.n[d] + 2 * L.he[d];
+    L.nn[d] = act ? L.n[d] + 2 * E + 1 : 1;
+  }
+  L.ps[0] = 1;
+  L.ps[1] = L.pn[0];
+  L.ps[2] = (long long)L.pn[0] * L.pn[1];
+  L.pcount = L.ps[2] * L.pn[2];
+  L.es[0] = 1;
+  L.es[1] = L.en[0];
+  L.es[2] = (long long)L.en[0] * L.en[1];
+  L.ecount = L.es[2] * L.en[2];
+  L.ns[0] = 1;
+  L.ns[1] = L.nn[0];
+  L.ns[2] = (long long)L.nn[0] * L.nn[1];
+  L.ncount = L.ns[2] * L.nn[2];
+  L.ncells = (long long)L.n[0] * L.n[1] * L.n[2];
+  for (int d = 0; d < 3; ++d) {
+    for (int e = 0; e < 3; ++e) L.fn[d][e] = L.n[e] + ((e == d && d < nd) ? 1 : 0);
+    L.fs[d][0] = 1;
+    L.fs[d][1] = L.fn[d][0];
+    L.fs[d][2] = (long long)L.fn[d][0] * L.fn[d][1];
+    L.fcount[d] = L.fs[d][2] * L.fn[d][2];
+  }
+  return L;
+}
+
+GBR_HD long long pidx(const Layout& L, int i, int j, int k) {
+  return (long long)(i + L.hp[0]) + (long long)(j + L.hp[1]) * L.ps[1] + (long long)(k + L.hp[2]) * L.ps[2];
+}
+GBR_HD long long eidx(const Layout& L, int i, int j, int k) {
+  return (long long)(i + L.he[0]) + (long long)(j + L.he[1]) * L.es[1] + (long long)(k + L.he[2]) * L.es[2];
+}
+GBR_HD long long nidx(const Layout& L, int i, int j, int k) {
+  return (long long)(i + L.he[0]) + (long long)(j + L.he[1]) * L.ns[1] + (long long)(k + L.he[2]) * L.ns[2];
+}
+GBR_HD long long cidx(const Layout& L, int i, int j, int k) {
+  return (long long)i + (long long)j * L.n[0] + (long long)k * L.n[0] * L.n[1];
+}
+// interface i+1/2 along d (i in [-1, n_d - 1]) of the cross-section cell (j, k)
+GBR_HD long long fidx(const Layout& L, int d, int i, int j, int k) {
+  int c[3] = {i, j, k};
+  c[d] += 1;
+  return (long long)c[0] + (long long)c[1] * L.fs[d][1] + (long long)c[2] * L.fs[d][2];
+}
+
+struct Box {
+  int lo[3], hi[3];
+};
+GBR_HD long long box_size(const Box& b) {
+  return (long long)(b.hi[0] - b.lo[0]) * (b.hi[1] - b.lo[1]) * (b.hi[2] - b.lo[2]);
+}
+GBR_HD void box_coord(const Box& b, long long t, int& i, int& j, int& k) {
+  const long long nx = b.hi[0] - b.lo[0], ny = b.hi[1] - b.lo[1];
+  i = b.lo[0] + (int)(t % nx);
+  t /= nx;
+  j = b.lo[1] + (int)(t % ny);
+  k = b.lo[2] + (int)(t / ny);
+}
+
+struct Phys {
+  double gamma, gm1, igm1;
+  double mu_ref, suth_s, it_ref;
+  double half_alpha_d;       // alpha^D / 2
+  double mp_alpha, mp_beta, mp_eps;
+  double kfac;               // kappa = mu * kfac, kfac = gamma / ((gamma - 1) Pr)
+  double dt_visc_fac;        // max(4/3, gamma/Pr) of the viscous time-step bound (reading A20)
+  int viscous, sutherland;
+};
+
+// ---------------------------------------------------------------------------
+// Math helpers
+// ---------------------------------------------------------------------------
+GBR_HD double grsqrt(double x) {
+#ifdef __CUDA_ARCH__
+  return rsqrt(x);
+#else
+  return 1.0 / std::sqrt(x);
+#endif
+}
+GBR_HD double gfma(double a, double b, double c) {
+#ifdef __CUDA_ARCH__
+  return fma(a, b, c);
+#else
+  return a * b + c;
+#endif
+}
+GBR_HD double gmin(double a, double b) { return a < b ? a : b; }
+GBR_HD double gmax(double a, double b) { return a > b ? a : b; }
+// App. E: minmod(a, b) = 1/2 (sign a + sign b) min(|a|, |b|), i.e. the smaller-magnitude
+// argument when both have the same sign, else 0.
+GBR_HD double minmod(double a, double b) {
+  const double m = gmin(std::fabs(a), std::fabs(b));
+  return (a > 0.0 && b > 0.0) ? m : ((a < 0.0 && b < 0.0) ? -m : 0.0);
+}
+
+// Composite stencils of the MEG6 interface operators (Sec. 6): the interface
+// value I(f)_{i+1/2} = avg of the van Leer left/right states built from E6
+// gradients and the gradient-based second derivative, and the derivative
+// D(f)_i = I(f)_{i+1/2} - I(f)_{i-1/2}.  The D weights 2282, -546, 89, -3, -1
+// (over 2880) are the ones printed in the Sec. 6 proof; the I weights follow
+// from the same three formulas: 1821, -461, 85, -4, -1 (over 2880) on
+// (f_i + f_{i+1}), (f_{i-1} + f_{i+2}), ... .
+constexpr double kD1 = 2282.0 / 2880.0, kD2 = -546.0 / 2880.0, kD3 = 89.0 / 2880.0, kD4 = -3.0 / 2880.0,
+                 kD5 = -1.0 / 2880.0;
+constexpr double kI0 = 1821.0 / 2880.0, kI1 = -461.0 / 2880.0, kI2 = 85.0 / 2880.0, kI3 = -4.0 / 2880.0,
+                 kI4 = -1.0 / 2880.0;
+
+GBR_HD double stencil_D(const double* f, long long e, long long s) {
+  double r = kD1 * (f[e + s] - f[e - s]);
+  r = gfma(kD2, f[e + 2 * s] - f[e - 2 * s], r);
+  r = gfma(kD3, f[e + 3 * s] - f[e - 3 * s], r);
+  r = gfma(kD4, f[e + 4 * s] - f[e - 4 * s], r);
+  r = gfma(kD5, f[e + 5 * s] - f[e - 5 * s], r);
+  return r;
+}
+// interface between e and e + s
+GBR_HD double stencil_I(const double* f, long long e, long long s) {
+  double r = kI0 * (f[e] + f[e + s]);
+  r = gfma(kI1, f[e - s] + f[e + 2 * s], r);
+  r = gfma(kI2, f[e - 2 * s] + f[e + 3 * s], r);
+  r = gfma(kI3, f[e - 3 * s] + f[e + 4 * s], r);
+  r = gfma(kI4, f[e - 4 * s] + f[e + 5 * s], r);
+  return r;
+}
+// product stencil: D applied to the pointwise product a * b
+GBR_HD double stencil_D_prod(const double* a, const double* b, long long e, long long s) {
+  const double c[5] = {kD1, kD2, kD3, kD4, kD5};
+  double r = 0.0;
+  for (int m = 1; m <= 5; ++m) r = gfma(c[m - 1], a[e + m * s] * b[e + m * s] - a[e - m * s] * b[e - m * s], r);
+  return r;
+}
+
+// E6 first derivative (Eq. E6_grads, read with differences)
+GBR_HD double stencil_E6(const double* f, long long e, long long s) {
+  double r = (3.0 / 4.0) * (f[e + s] - f[e - s]);
+  r = gfma(-3.0 / 20.0, f[e + 2 * s] - f[e - 2 * s], r);
+  r = gfma(1.0 / 60.0, f[e + 3 * s] - f[e - 3 * s], r);
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Geometry bodies (Sec. 3, Sec. 4, Sec. 6)
+// ---------------------------------------------------------------------------
+struct GeoArgs {
+  Layout L;
+  const double* nodes;  // [nd][ncount]  extended nodes
+  const double* nvel;   // [nd][ncount]  extended node velocities (moving) or null
+  double* xc;           // [nd][ecount]  centroids
+  double* vc;           // [nd][ecount]  centroid velocities
+  double* xd;           // [9][ecount]   xd[a*3+d] = D_d x_a
+  double* mh;           // [9][ecount]   hat metrics mh[e*3+a]
+  double* det;          // [ecount]      1/J
+  double* mu;           // [9][ecount]   unhatted metrics (viscous)
+  double* mt;           // [3][ecount]   hat time metrics (moving)
+  double* fh[3];        // [nd][fcount]
+  double* fu[3];        // [nd*nd][fcount]
+  double* ft[3];        // [fcount]
+  double* gcl;          // [ncells]
+  double* jac;          // [ncells]  J = 1/(1/J)
+  int viscous, moving;
+};
+
+// Sec. 3: cell centroid = average of the cell's vertices
+GBR_HD void body_centroid(const GeoArgs& G, int i, int j, int k) {
+  const Layout& L = G.L;
+  const int nd = L.nd;
+  const long long e = eidx(L, i, j, k);
+  const double inv = (nd == 3) ? 0.125 : 0.25;
+  for (int a = 0; a < nd; ++a) {
+    const double* X = G.nodes + a * L.ncount;
+    double s = 0.0, sv = 0.0;
+    for (int ck = 0; ck < (nd == 3 ? 2 : 1); ++ck)
+      for (int cj = 0; cj < 2; ++cj)
+        for (int ci = 0; ci < 2; ++ci) {
+          const long long m = nidx(L, i + ci, j + cj, k + ck);
+          s = s + X[m];
+          if (G.moving) sv = sv + G.nvel[a * L.ncount + m];
+        }
+    G.xc[a * L.ecount + e] = s * inv;
+    if (G.moving) G.vc[a * L.ecount + e] = sv * inv;
+  }
+}
+
+// Sec. 6 step 2: consistent derivative of the coordinates, xd[a][d] = D_d(x_a)
+GBR_HD void body_coord_derivative(const GeoArgs& G, int d, int i, int j, int k) {
+  const Layout& L = G.L;
+  const long long e = eidx(L, i, j, k);
+  for (int a = 0; a < L.nd; ++a) G.xd[(a * 3 + d) * L.ecount + e] = stencil_D(G.xc + a * L.ecount, e, L.es[d]);
+}
+
+// Eq. (GCL_metrics) (3D) or its z = zeta reduction (2D), Eq. (Jac-matrix),
+// unhatted metrics (viscous) and Sec. 4 time metrics (moving).
+GBR_HD void body_metrics(const GeoArgs& G, int i, int j, int k) {
+  const Layout& L = G.L;
+  const long long EC = L.ecount;
+  const long long e = eidx(L, i, j, k);
+  const int nd = L.nd;
+  double m[3][3];
+  double det;
+  if (nd == 3) {
+    for (int ee = 0; ee < 3; ++ee) {
+      const int f = (ee + 1) % 3, g = (ee + 2) % 3;
+      for (int a = 0; a < 3; ++a) {
+        const int b = (a + 1) % 3, c = (a + 2) % 3;
+        // e.g. xi^_x = (y_eta z)_zeta - (y_zeta z)_eta
+        const double t1 = stencil_D_prod(G.xd + (b * 3 + f) * EC, G.xc + c * EC, e, L.es[g]);
+        const double t2 = stencil_D_prod(G.xd + (b * 3 + g) * EC, G.xc + c * EC, e, L.es[f]);
+        m[ee][a] = t1 - t2;
+      }
+    }
+    const double xx = G.xd[0 * EC + e], xe = G.xd[1 * EC + e], xz = G.xd[2 * EC + e];
+    const double yx = G.xd[3 * EC + e], ye = G.xd[4 * EC + e], yz = G.xd[5 * EC + e];
+    const double zx = G.xd[6 * EC + e], ze = G.xd[7 * EC + e], zz = G.xd[8 * EC + e];
+    det = xx * (ye * zz - ze * yz) - yx * (xe * zz - ze * xz) + zx * (xe * yz - ye * xz);
+  } else {
+    const double xx = G.xd[0 * EC + e], xe = G.xd[1 * EC + e];
+    const double yx = G.xd[3 * EC + e], ye = G.xd[4 * EC + e];
+    m[0][0] = ye;
+    m[0][1] = -xe;
+    m[1][0] = -yx;
+    m[1][1] = xx;
+    det = xx * ye - xe * yx;
+  }
+  for (int ee = 0; ee < nd; ++ee)
+    for (int a = 0; a < nd; ++a) G.mh[(ee * 3 + a) * EC + e] = m[ee][a];
+  G.det[e] = det;
+  if (G.viscous) {
+    const double idet = 1.0 / det;
+    for (int ee = 0; ee < nd; ++ee)
+      for (int a = 0; a < nd; ++a) G.mu[(ee * 3 + a) * EC + e] = m[ee][a] * idet;
+  }
+  if (G.moving) {
+    for (int ee = 0; ee < nd; ++ee) {
+      double s = 0.0;
+      for (int a = 0; a < nd; ++a) s = gfma(G.vc[a * EC + e], m[ee][a], s);
+      G.mt[ee * EC + e] = -s;
+    }
+  }
+}
+
+// Sec. 6 step 3: interface values of whole metric products, interface i+1/2 along d
+GBR_HD void body_face_metrics(const GeoArgs& G, int d, int i, int j, int k) {
+  const Layout& L = G.L;
+  const long long EC = L.ecount, FC = L.fcount[d];
+  const long long e = eidx(L, i, j, k), s = L.es[d];
+  const long long f = fidx(L, d, i, j, k);
+  const int nd = L.nd;
+  for (int a = 0; a < nd; ++a) G.fh[d][a * FC + f] = stencil_I(G.mh + (d * 3 + a) * EC, e, s);
+  if (G.viscous)
+    for (int ee = 0; ee < nd; ++ee)
+      for (int a = 0; a < nd; ++a) G.fu[d][(ee * nd + a) * FC + f] = stencil_I(G.mu + (ee * 3 + a) * EC, e, s);
+  if (G.moving) G.ft[d][f] = stencil_I(G.mt + d * EC, e, s);
+}
+
+// Eq. (Jacb2) with the same interface difference as the flux divergence; J for the update
+GBR_HD void body_gcl(const GeoArgs& G, int i, int j, int k) {
+  const Layout& L = G.L;
+  const long long c = cidx(L, i, j, k);
+  if (G.moving) {
+    double s = 0.0;
+    for (int d = 0; d < L.nd; ++d) {
+      const long long fhi = fidx(L, d, i, j, k);
+      s = s + (G.ft[d][fhi] - G.ft[d][fhi - L.fs[d][d]]);
+    }
+    G.gcl[c] = -s;
+  }
+  G.jac[c] = 1.0 / G.det[eidx(L, i, j, k)];
+}
+
+// Sec. 7.2 motion families evaluated at extended node index (i, j, k)
+struct Motion {
+  double origin[3], h[3], amp[3], omega, k[3][3];
+};
+GBR_HD void body_motion(const Layout& L, const Motion& M, double st, double ct, double* nodes, double* nvel, int i,
+                        int j, int k) {
+  const int m[3] = {i, j, k};
+  const long long id = nidx(L, i, j, k);
+  for (int a = 0; a < L.nd; ++a) {
+    double S = 1.0;
+    for (int b = 0; b < L.nd; ++b)
+      if (M.k[a][b] != 0.0) S *= sin(M.k[a][b] * (m[b] * M.h[b]));
+    nodes[a * L.ncount + id] = M.origin[a] + m[a] * M.h[a] + M.amp[a] * st * S;
+    nvel[a * L.ncount + id] = M.amp[a] * ct * S;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Right-hand-side bodies (Sec. 3, Sec. 5)
+// ---------------------------------------------------------------------------
+struct RhsArgs {
+  Layout L;
+  Phys ph;
+  const double* q;      // [nv][ncells] conserved state of the stage
+  double* prim;         // [nv][pcount] primitives with halo
+  double* temp;         // [pcount] T = p/rho (viscous)
+  double* g1[3];        // [nv (+1 T)][pcount] first derivatives along d
+  double* g2[3];        // [nv][pcount] second derivatives along d
+  const double* fh[3];
+  const double* fu[3];
+  const double* ft[3];
+  double* flux[3];      // [nv][fcount] F^ - F^v at interfaces
+  const double* inflow; // [nv][nk][nj]
+  int bc[3][2];
+  int viscous;
+};
+
+// Sec. 2: primitives P = [rho, u.., p] (and T = p/rho, R = 1) at interior cells
+template <int ND>
+GBR_HD void body_prim(const RhsArgs& A, int i, int j, int k) {
+  constexpr int NV = ND + 2;
+  const Layout& L = A.L;
+  const long long c = cidx(L, i, j, k), p = pidx(L, i, j, k);
+  const long long NC = L.ncells, PC = L.pcount;
+  const double rho = A.q[c];
+  const double ir = 1.0 / rho;
+  double ke = 0.0;
+  A.prim[p] = rho;
+  for (int a = 0; a < ND; ++a) {
+    const double m = A.q[(1 + a) * NC + c];
+    const double u = m * ir;
+    A.prim[(1 + a) * PC + p] = u;
+    ke = gfma(m, u, ke);
+  }
+  const double pr = A.ph.gm1 * (A.q[(NV - 1) * NC + c] - 0.5 * ke);
+  A.prim[(NV - 1) * PC + p] = pr;
+  if (A.viscous) A.temp[p] = pr * ir;
+}
+
+// ghost layers along axis d for the cross-section cell (i, j, k) (coordinate d ignored):
+// periodic copy, zero gradient, or Dirichlet inflow on the x-low side
+template <int ND>
+GBR_HD void body_halo(const RhsArgs& A, int d, int i, int j, int k) {
+  constexpr int NV = ND + 2;
+  const Layout& L = A.L;
+  const long long PC = L.pcount, s = L.ps[d];
+  int c0[3] = {i, j, k};
+  c0[d] = 0;
+  const long long base = pidx(L, c0[0], c0[1], c0[2]);  // cell 0 along d
+  const int n = L.n[d];
+  const int nf = NV + (A.viscous ? 1 : 0);
+  for (int f = 0; f < nf; ++f) {
+    double* F = (f < NV) ? A.prim + f * PC : A.temp;
+    for (int g = 1; g <= H; ++g) {
+      const long long lo = base - g * s, hi = base + (n - 1 + g) * s;
+      if (L.per[d]) {
+        F[lo] = F[base + (n - g) * s];
+        F[hi] = F[base + (g - 1) * s];
+      } else {
+        if (A.bc[d][0] == 2) {
+          const long long ib = ((long long)k * L.n[1] + j);
+          if (f < NV) {
+            F[lo] = A.inflow[f * L.n[1] * L.n[2] + ib];
+          } else {
+            F[lo] = A.inflow[(NV - 1) * L.n[1] * L.n[2] + ib] / A.inflow[ib];
+          }
+        } else {
+          F[lo] = F[base];
+        }
+        F[hi] = F[base + (n - 1) * s];
+      }
+    }
+  }
+}
+
+// Sec. 5.1 step 1: E6 first derivatives along e (primitives and T)
+template <int ND>
+GBR_HD void body_grad1(const RhsArgs& A, int e, int i, int j, int k) {
+  constexpr int NV = ND + 2;
+  const Layout& L = A.L;
+  const long long PC = L.pcount, p = pidx(L, i, j, k), s = L.ps[e];
+  for (int c = 0; c < NV; ++c) A.g1[e][c * PC + p] = stencil_E6(A.prim + c * PC, p, s);
+  if (A.viscous) A.g1[e][NV * PC + p] = stencil_E6(A.temp, p, s);
+}
+
+// Sec. 5.1 step 1: f''_i = 2 (f_{i+1} - 2 f_i + f_{i-1}) - 0.5 (f'_{i+1} - f'_{i-1})
+template <int ND>
+GBR_HD void body_grad2(const RhsArgs& A, int e, int i, int j, int k) {
+  constexpr int NV = ND + 2;
+  const Layout& L = A.L;
+  const long long PC = L.pcount, p = pidx(L, i, j, k), s = L.ps[e];
+  for (int c = 0; c < NV; ++c) {
+    const double* f = A.prim + c * PC;
+    const double* f1 = A.g1[e] + c * PC;
+    A.g2[e][c * PC + p] = 2.0 * (f[p + s] - 2.0 * f[p] + f[p - s]) - 0.5 * (f1[p + s] - f1[p - s]);
+  }
+}
+
+// App. A projection x -> R^{-1} x for the face eigenvectors (unit normal nu,
+// face rho*a = ra and a^2).  Row order: U - a, U (x2 or x3), U + a.
+template <int ND>
+GBR_HD void project(const double* nu, double ra, double a2, const double* x, double* W) {
+  if (ND == 3) {
+    const double s = gfma(nu[0], x[1], gfma(nu[1], x[2], nu[2] * x[3]));
+    const double t = ra * s;
+    const double e = gfma(a2, x[0], -x[4]);
+    W[0] = x[4] - t;
+    W[1] = gfma(nu[0], e, gfma(nu[1], x[3], -nu[2] * x[2]));
+    W[2] = gfma(nu[2], e, gfma(nu[0], x[2], -nu[1] * x[1]));
+    W[3] = gfma(-nu[1], e, gfma(nu[0], x[3], -nu[2] * x[1]));
+    W[4] = x[4] + t;
+  } else {
+    const double s = gfma(nu[0], x[1], nu[1] * x[2]);
+    const double t = ra * s;
+    W[0] = x[3] - t;
+    W[1] = gfma(a2, x[0], -x[3]);
+    W[2] = gfma(nu[0], x[2], -nu[1] * x[1]);
+    W[3] = x[3] + t;
+  }
+}
+
+// App. A back-projection d -> R d
+template <int ND>
+GBR_HD void back_project(const double* nu, double ira, double ia2, const double* dl, double* out) {
+  if (ND == 3) {
+    const double h = 0.5 * (dl[0] + dl[4]);
+    const double q = 0.5 * (dl[4] - dl[0]) * ira;
+    out[0] = ia2 * (h + gfma(nu[0], dl[1], gfma(nu[2], dl[2], -nu[1] * dl[3])));
+    out[1] = gfma(nu[0], q, gfma(-nu[1], dl[2], -nu[2] * dl[3]));
+    out[2] = gfma(nu[1], q, gfma(-nu[2], dl[1], nu[0] * dl[2]));
+    out[3] = gfma(nu[2], q, gfma(nu[1], dl[1], nu[0] * dl[3]));
+    out[4] = h;
+  } else {
+    const double h = 0.5 * (dl[0] + dl[3]);
+    const double q = 0.5 * (dl[3] - dl[0]) * ira;
+    out[0] = ia2 * (h + dl[1]);
+    out[1] = gfma(nu[0], q, -nu[1] * dl[2]);
+    out[2] = gfma(nu[1], q, nu[0] * dl[2]);
+    out[3] = h;
+  }
+}
+
+// App. E limiter written relative to the base cell value W_base:
+//   f  = W_face - W_base,  dm = W_base - W_up,  dp = W_down - W_base,
+//   du, db, dd = curvatures d of the up, base and down cells.
+// Returns the limited W_face - W_base.
+GBR_HD double mp_relative(double f, double dm, double dp, double du, double db, double dd, const Phys& ph) {
+  const double mmp = minmod(dp, ph.mp_beta * dm);  // W^MP - W_base
+  if (f * (f - mmp) <= ph.mp_eps) return f;
+  const double dmp = minmod(db, dd);  // d^M_{i+1/2}
+  const double dmm = minmod(du, db);  // d^M_{i-1/2}
+  const double md = 0.5 * dp - 0.5 * dmp;
+  const double ul = ph.mp_alpha * dm;
+  const double lc = gfma(4.0 / 3.0, dmm, 0.5 * dm);
+  const double lo = gmax(gmin(gmin(0.0, dp), md), gmin(gmin(0.0, ul), lc));
+  const double hi = gmin(gmax(gmax(0.0, dp), md), gmax(gmax(0.0, ul), lc));
+  return f + minmod(lo - f, hi - f);
+}
+
+// Sec. 5.1.1 HLLC with grid motion; P = [rho, u.., p]
+template <int ND>
+GBR_HD void hllc(const double* PL, const double* PR, const double* nh, double nn2, double inn, double nt,
+                 const Phys& ph, double* F) {
+  constexpr int NV = ND + 2;
+  const double nn = nn2 * inn;
+  const double inn2 = inn * inn;
+  double r[2], ir[2], u[2][ND], p[2], U[2], En[2], c[2];
+  const double* Ps[2] = {PL, PR};
+  for (int s = 0; s < 2; ++s) {
+    r[s] = Ps[s][0];
+    ir[s] = 1.0 / r[s];
+    double q2 = 0.0, un = nt;
+    for (int a = 0; a < ND; ++a) {
+      u[s][a] = Ps[s][1 + a];
+      q2 = gfma(u[s][a], u[s][a], q2);
+      un = gfma(nh[a], u[s][a], un);
+    }
+    U[s] = un;
+    p[s] = Ps[s][NV - 1];
+    En[s] = gfma(p[s], ph.igm1, 0.5 * r[s] * q2);
+    c[s] = sqrt(ph.gamma * p[s] * ir[s]);
+  }
+  const double SL = gmin(gfma(-c[0], nn, U[0]), gfma(-c[1], nn, U[1]));
+  const double SR = gmax(gfma(c[0], nn, U[0]), gfma(c[1], nn, U[1]));
+  const double aL = r[0] * (SL - U[0]), aR = r[1] * (SR - U[1]);
+  const double Ss = (aR * U[1] - aL * U[0] + (p[0] - p[1]) * nn2) / (aR - aL);
+  // branches of Sec. 5.1.1: S^L >= 0 -> F^L; S^L < 0 <= S* -> F*L; S* < 0 < S^R -> F*R; else F^R
+  const int s = (SL >= 0.0 || Ss >= 0.0) ? 0 : 1;
+  const double S = s == 0 ? SL : SR;
+  const bool star = !(SL >= 0.0) && (s == 0 || SR > 0.0);
+  const double Us = U[s], rs = r[s], ps = p[s], Es = En[s];
+  F[0] = rs * Us;
+  for (int a = 0; a < ND; ++a) F[1 + a] = gfma(rs * u[s][a], Us, nh[a] * ps);
+  F[NV - 1] = gfma(Es + ps, Us, -nt * ps);
+  if (star) {
+    const double A = S - Us;
+    const double rA = rs * A;
+    const double fac = rA / (S - Ss);
+    const double dS = Ss - Us;
+    const double w = dS * inn2;
+    F[0] += S * (fac - rs);
+    for (int a = 0; a < ND; ++a) F[1 + a] += S * (fac * gfma(nh[a], w, u[s][a]) - rs * u[s][a]);
+    const double eb = Es * ir[s] + dS * gfma(Ss - nt, inn2, ps / rA);
+    F[NV - 1] += S * gfma(fac, eb, -Es);
+  }
+}
+
+// One interface i+1/2 along d: Sec. 5.1 steps 2-6 and Sec. 5.2 steps 1-4.
+// The characteristic quantities are formed from projected differences of
+// neighbouring cells and the limited states are returned relative to the base
+// cell (P^L = P_i + R dW_L), which is the same arithmetic as projecting the
+// cell values themselves, in a different rounding order.
+template <int ND, bool VISC, bool MOV>
+GBR_HD void body_face(const RhsArgs& A, int d, int i, int j, int k) {
+  constexpr int NV = ND + 2;
+  const Layout& L = A.L;
+  const Phys& ph = A.ph;
+  const long long PC = L.pcount, s = L.ps[d];
+  const long long p1 = pidx(L, i, j, k);
+  const long long pp[4] = {p1 - s, p1, p1 + s, p1 + 2 * s};
+  const long long FC = L.fcount[d];
+  const long long f = fidx(L, d, i, j, k);
+  const double* P = A.prim;
+
+  double nh[ND];
+  double nn2 = 0.0;
+  for (int a = 0; a < ND; ++a) {
+    nh[a] = A.fh[d][a * FC + f];
+    nn2 = gfma(nh[a], nh[a], nn2);
+  }
+  const double nt = MOV ? A.ft[d][f] : 0.0;
+  const double inn = grsqrt(nn2);
+  double nu[ND];
+  for (int a = 0; a < ND; ++a) nu[a] = nh[a] * inn;
+  // face state of the eigenvectors: mean of rho and p of cells i, i+1 (reading A6)
+  const double rb = 0.5 * (P[pp[1]] + P[pp[2]]);
+  const double pb = 0.5 * (P[(NV - 1) * PC + pp[1]] + P[(NV - 1) * PC + pp[2]]);
+  const double irb = 1.0 / rb;
+  const double a2 = ph.gamma * pb * irb;
+  const double ia = grsqrt(a2);
+  const double ra = rb * (a2 * ia);
+  const double ira = irb * ia;
+  const double ia2 = ia * ia;
+
+  double Wd[3][NV], W1[2][NV], W2[4][NV];
+  {
+    double x[NV];
+    for (int m = 0; m < 3; ++m) {
+      for (int c = 0; c < NV; ++c) x[c] = P[c * PC + pp[m + 1]] - P[c * PC + pp[m]];
+      project<ND>(nu, ra, a2, x, Wd[m]);
+    }
+    for (int m = 0; m < 2; ++m) {
+      for (int c = 0; c < NV; ++c) x[c] = A.g1[d][c * PC + pp[m + 1]];
+      project<ND>(nu, ra, a2, x, W1[m]);
+    }
+    for (int m = 0; m < 4; ++m) {
+      for (int c = 0; c < NV; ++c) x[c] = A.g2[d][c * PC + pp[m]];
+      project<ND>(nu, ra, a2, x, W2[m]);
+    }
+  }
+  double dL[NV], dR[NV];
+  for (int c = 0; c < NV; ++c) {
+    const double fL = gfma(0.5, W1[0][c], W2[1][c] * (1.0 / 12.0));   // W^L - W_i   (Eq. legendre_polys)
+    const double fR = gfma(-0.5, W1[1][c], W2[2][c] * (1.0 / 12.0));  // W^R - W_{i+1}
+    dL[c] = mp_relative(fL, Wd[0][c], Wd[1][c], W2[0][c], W2[1][c], W2[2][c], ph);
+    dR[c] = mp_relative(fR, -Wd[2][c], -Wd[1][c], W2[3][c], W2[2][c], W2[1][c], ph);
+  }
+  double PL[NV], PR[NV];
+  back_project<ND>(nu, ira, ia2, dL, PL);
+  back_project<ND>(nu, ira, ia2, dR, PR);
+  for (int c = 0; c < NV; ++c) {
+    PL[c] += P[c * PC + pp[1]];
+    PR[c] += P[c * PC + pp[2]];
+  }
+  double F[NV];
+  hllc<ND>(PL, PR, nh, nn2, inn, nt, ph, F);
+
+  if (VISC) {
+    // Sec. 5.2 alpha-damping on [u.., T]
+    double gx[ND + 1][ND];
+    double phif[ND + 1];
+    const double* fu = A.fu[d];
+    for (int v = 0; v <= ND; ++v) {
+      const double* val = (v < ND) ? P + (1 + v) * PC : A.temp;
+      const int gi = (v < ND) ? (1 + v) : NV;
+      double gc[ND];
+      const double gd1 = A.g1[d][gi * PC + pp[1]], gd2 = A.g1[d][gi * PC + pp[2]];
+      const double phiL = gfma(0.5, gd1, val[pp[1]]);   // Eq. (AD-eqn2), beta^D = 0
+      const double phiR = gfma(-0.5, gd2, val[pp[2]]);
+      for (int e = 0; e < ND; ++e) {
+        if (e == d) {
+          gc[e] = gfma(ph.half_alpha_d, phiR - phiL, 0.5 * (gd1 + gd2));  // Eq. (AD-eqn1)
+        } else {
+          gc[e] = 0.5 * (A.g1[e][gi * PC + pp[1]] + A.g1[e][gi * PC + pp[2]]);  // reading A11
+        }
+      }
+      phif[v] = 0.5 * (phiL + phiR);
+      for (int a = 0; a < ND; ++a) {  // Eq. (AD-eqn3)
+        double sacc = 0.0;
+        for (int e = 0; e < ND; ++e) sacc = gfma(fu[(e * ND + a) * FC + f], gc[e], sacc);
+        gx[v][a] = sacc;
+      }
+    }
+    double mu = ph.mu_ref;
+    if (ph.sutherland) {
+      const double th = phif[ND] * ph.it_ref;
+      mu = ph.mu_ref * (th * sqrt(th)) * ((1.0 + ph.suth_s) / (th + ph.suth_s));
+    }
+    const double lam = (-2.0 / 3.0) * mu;
+    const double kap = mu * ph.kfac;
+    double div = 0.0;
+    for (int a = 0; a < ND; ++a) div += gx[a][a];
+    double tau[ND][ND];
+    for (int a = 0; a < ND; ++a)
+      for (int b = 0; b < ND; ++b) {
+        tau[a][b] = mu * (gx[a][b] + gx[b][a]);  // Eq. (shear-str)
+        if (a == b) tau[a][b] = gfma(lam, div, tau[a][b]);
+      }
+    double beta[ND];
+    for (int a = 0; a < ND; ++a) {
+      double sacc = kap * gx[ND][a];
+      for (int b = 0; b < ND; ++b) sacc = gfma(phif[b], tau[a][b], sacc);  // Eq. (thermal-work)
+      beta[a] = sacc;
+    }
+    for (int a = 0; a < ND; ++a) {
+      double sacc = 0.0;
+      for (int b = 0; b < ND; ++b) sacc = gfma(nh[b], tau[a][b], sacc);
+      F[1 + a] -= sacc;
+    }
+    double sacc = 0.0;
+    for (int b = 0; b < ND; ++b) sacc = gfma(nh[b], beta[b], sacc);
+    F[NV - 1] -= sacc;
+  }
+  for (int c = 0; c < NV; ++c) A.flux[d][c * FC + f] = F[c];
+}
+
+// Sec. 3 divergence, Sec. 4 time split, App. B stage combination.
+struct UpdArgs {
+  Layout L;
+  const double* flux[3];
+  const double* qs;     // state of this stage
+  const double* q0;     // Q^n
+  double* out;          // new state (mode 1) or L(Q) (mode 0)
+  const double* jac;
+  const double* gcl;
+  const double* sigma;  // sponge (or null)
+  double qamb[5];
+  const double* dt;     // device scalar
+  double ca, cb, cc;    // out = ca q0 + cb qs + cc dt L
+  int mode;             // 0: out = L, 1: RK combination
+};
+
+template <int ND, bool MOV>
+GBR_HD bool body_update(const UpdArgs& U, int i, int j, int k) {
+  constexpr int NV = ND + 2;
+  const Layout& L = U.L;
+  const long long c = cidx(L, i, j, k), NC = L.ncells;
+  const double J = U.jac[c];
+  bool bad = false;
+  const double dtc = (U.mode == 1) ? (*U.dt) * U.cc : 0.0;
+  for (int v = 0; v < NV; ++v) {
+    double res = 0.0;
+    for (int d = 0; d < ND; ++d) {
+      const long long fhi = fidx(L, d, i, j, k);
+      const long long FC = L.fcount[d];
+      res = res - (U.flux[d][v * FC + fhi] - U.flux[d][v * FC + fhi - L.fs[d][d]]);
+    }
+    const double qv = U.qs[v * NC + c];
+    double Lv = MOV ? J * gfma(-U.gcl[c], qv, res) : J * res;
+    if (U.sigma) Lv = gfma(-U.sigma[c], qv - U.qamb[v], Lv);
+    if (U.mode == 0) {
+      U.out[v * NC + c] = Lv;
+      bad |= !(Lv == Lv) || std::fabs(Lv) > 1.79e308;
+    } else {
+      const double o = gfma(U.ca, U.q0[v * NC + c], gfma(U.cb, qv, dtc * Lv));
+      U.out[v * NC + c] = o;
+      bad |= !(o == o) || std::fabs(o) > 1.79e308 || (v == 0 && !(o > 0.0));
+    }
+  }
+  return bad;
+}
+
+// App. B: per-cell min over directions of 1/(|U| + c |grad xi|), plus the
+// viscous bound of reading A20.
+struct DtArgs {
+  Layout L;
+  Phys ph;
+  const double* q;
+  const double* mh;   // ext layout
+  const double* mt;   // ext layout (moving) or null
+  const double* jac;
+};
+
+template <int ND>
+GBR_HD double body_dt(const DtArgs& D, int i, int j, int k) {
+  constexpr int NV = ND + 2;
+  const Layout& L = D.L;
+  const Phys& ph = D.ph;
+  const long long c = cidx(L, i, j, k), NC = L.ncells, e = eidx(L, i, j, k), EC = L.ecount;
+  const double rho = D.q[c];
+  const double ir = 1.0 / rho;
+  double u[ND], ke = 0.0;
+  for (int a = 0; a < ND; ++a) {
+    u[a] = D.q[(1 + a) * NC + c] * ir;
+    ke = gfma(D.q[(1 + a) * NC + c], u[a], ke);
+  }
+  const double pr = ph.gm1 * (D.q[(NV - 1) * NC + c] - 0.5 * ke);
+  const double cs = sqrt(ph.gamma * pr * ir);
+  const double J = D.jac[c];
+  double best = 1.0e300;
+  double nu_eff = 0.0;
+  if (ph.viscous) {
+    double mu = ph.mu_ref;
+    if (ph.sutherland) {
+      const double th = pr * ir * ph.it_ref;
+      mu = ph.mu_ref * (th * sqrt(th)) * ((1.0 + ph.suth_s) / (th + ph.suth_s));
+    }
+    nu_eff = ph.dt_visc_fac * mu * ir;
+  }
+  for (int ee = 0; ee < ND; ++ee) {
+    double Uc = D.mt ? D.mt[ee * EC + e] * J : 0.0;
+    double g2 = 0.0;
+    for (int a = 0; a < ND; ++a) {
+      const double m = D.mh[(ee * 3 + a) * EC + e] * J;
+      Uc = gfma(m, u[a], Uc);
+      g2 = gfma(m, m, g2);
+    }
+    best = gmin(best, 1.0 / (std::fabs(Uc) + cs * sqrt(g2)));
+    if (ph.viscous) best = gmin(best, 1.0 / (nu_eff * g2));
+  }
+  return best;
+}
+
+}  // namespace gbr

@@ -1,0 +1,283 @@
+"""Thin ctypes binding of the C ABI in include/gbr.h (argument marshalling only).
+
+Every step of the right-hand side runs in the in-tree CUDA library
+``libgbr.so`` (sm_103a).  PyTorch supplies device memory (the workspace and
+state tensors) and the CUDA stream; it does no arithmetic of the method.
+Importing this module without the built library raises immediately: there is
+no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgbr.so")
+
+GBR_OK, GBR_EINVAL, GBR_ENOMEM, GBR_ECUDA, GBR_ENONFINITE, GBR_ETIMEOUT, GBR_ESTATE = range(7)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENONFINITE", "ETIMEOUT", "ESTATE"]
+(GBR_FIELD_CELL_METRICS, GBR_FIELD_CELL_DET, GBR_FIELD_CELL_TIME, GBR_FIELD_FACE_HAT, GBR_FIELD_FACE_UNHAT,
+ GBR_FIELD_FACE_TIME, GBR_FIELD_GCL, GBR_FIELD_FACE_FLUX) = range(8)
+
+
+class gbr_params(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int),
+        ("n", ctypes.c_int * 3),
+        ("periodic", ctypes.c_int * 3),
+        ("ghost_nodes", ctypes.c_int),
+        ("bc", (ctypes.c_int * 2) * 3),
+        ("gamma", ctypes.c_double),
+        ("prandtl", ctypes.c_double),
+        ("reynolds", ctypes.c_double),
+        ("sutherland_s", ctypes.c_double),
+        ("t_ref", ctypes.c_double),
+        ("alpha_damping", ctypes.c_double),
+        ("mp_alpha", ctypes.c_double),
+        ("mp_beta", ctypes.c_double),
+        ("mp_eps", ctypes.c_double),
+        ("moving", ctypes.c_int),
+    ]
+
+
+class gbr_motion(ctypes.Structure):
+    _fields_ = [
+        ("origin", ctypes.c_double * 3),
+        ("h", ctypes.c_double * 3),
+        ("amp", ctypes.c_double * 3),
+        ("omega", ctypes.c_double),
+        ("k", (ctypes.c_double * 3) * 3),
+    ]
+
+
+class GbrError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+_lib = None
+_P = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library {LIB_PATH} is not built (run __graft_entry__.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    L.gbr_workspace_bytes.argtypes = [ctypes.POINTER(gbr_params)]
+    L.gbr_workspace_bytes.restype = ctypes.c_size_t
+    L.gbr_create.argtypes = [ctypes.POINTER(gbr_params), _P, _P, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]
+    L.gbr_compute_metrics.argtypes = [_vp]
+    L.gbr_move_mesh.argtypes = [_vp, _P, _P]
+    L.gbr_set_motion.argtypes = [_vp, ctypes.POINTER(gbr_motion), ctypes.c_double]
+    L.gbr_set_state.argtypes = [_vp, _vp, ctypes.c_int]
+    L.gbr_get_state.argtypes = [_vp, _vp, ctypes.c_int]
+    L.gbr_set_inflow.argtypes = [_vp, _P]
+    L.gbr_set_sponge.argtypes = [_vp, _P, _P]
+    L.gbr_rhs.argtypes = [_vp, _vp]
+    L.gbr_compute_dt.argtypes = [_vp, ctypes.c_double, _P]
+    L.gbr_rk_step.argtypes = [_vp, ctypes.c_double]
+    L.gbr_sync.argtypes = [_vp, ctypes.c_double]
+    L.gbr_get_time.argtypes = [_vp, _P, _P]
+    L.gbr_get_field.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _P]
+    L.gbr_last_error.argtypes = [_vp]
+    L.gbr_last_error.restype = ctypes.c_char_p
+    L.gbr_last_global_error.restype = ctypes.c_char_p
+    L.gbr_destroy.argtypes = [_vp]
+    for name in ("gbr_create", "gbr_compute_metrics", "gbr_move_mesh", "gbr_set_motion", "gbr_set_state",
+                 "gbr_get_state", "gbr_set_inflow", "gbr_set_sponge", "gbr_rhs", "gbr_compute_dt", "gbr_rk_step",
+                 "gbr_sync", "gbr_get_time", "gbr_get_field"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names declared in include/gbr.h that the library must export."""
+    return ["gbr_workspace_bytes", "gbr_create", "gbr_compute_metrics", "gbr_move_mesh", "gbr_set_motion",
+            "gbr_set_state", "gbr_get_state", "gbr_set_inflow", "gbr_set_sponge", "gbr_rhs", "gbr_compute_dt",
+            "gbr_rk_step", "gbr_sync", "gbr_get_time", "gbr_get_field", "gbr_last_error", "gbr_last_global_error",
+            "gbr_destroy"]
+
+
+def make_params(case):
+    p = gbr_params()
+    nd = int(case["ndim"])
+    p.ndim = nd
+    n = list(case["n"]) + [1] * 3
+    per = list(case.get("periodic", (1, 1, 1))) + [1] * 3
+    for d in range(3):
+        p.n[d] = int(n[d]) if d < nd else 1
+        p.periodic[d] = int(per[d])
+    p.ghost_nodes = int(case.get("ghost_nodes", 10))
+    bc = case.get("bc", ((1, 1), (1, 1), (1, 1)))
+    for d in range(3):
+        for s in range(2):
+            p.bc[d][s] = int(bc[d][s])
+    for key in ("gamma", "prandtl", "reynolds", "sutherland_s", "t_ref", "alpha_damping", "mp_alpha", "mp_beta",
+                "mp_eps"):
+        setattr(p, key, float(case[key]))
+    p.moving = int(case.get("moving", 0))
+    return p
+
+
+def make_motion(m):
+    """gbr_motion from an ``inputs.SinusoidalMotion``."""
+    g = gbr_motion()
+    for a in range(m.nd):
+        g.origin[a] = m.origin[a]
+        g.h[a] = m.h[a]
+        g.amp[a] = m.amp[a]
+        for b in range(m.nd):
+            g.k[a][b] = m.k[a][b]
+    g.omega = m.omega
+    return g
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_P)
+
+
+class Solver:
+    """One grid on one GPU.  ``case`` is a dict from ``inputs.case_params``."""
+
+    def __init__(self, case, nodes, node_vel=None, device="cuda", stream=None, moving=None):
+        import torch
+
+        self.torch = torch
+        self.L = lib()
+        self.case = dict(case)
+        if moving is not None:
+            self.case["moving"] = int(moving)
+        elif node_vel is not None:
+            self.case["moving"] = 1
+        self.nd = int(case["ndim"])
+        self.nv = self.nd + 2
+        self.n = tuple(int(v) for v in case["n"][: self.nd])
+        self.params = make_params(self.case)
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = self.L.gbr_workspace_bytes(ctypes.byref(self.params))
+        if nbytes == 0:
+            raise GbrError(GBR_EINVAL, self.L.gbr_last_global_error().decode())
+        self.workspace_bytes = int(nbytes)
+        self.workspace = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) & ~255
+        self.h = _vp()
+        nodes = _f64(nodes)
+        node_vel = _f64(node_vel)
+        rc = self.L.gbr_create(ctypes.byref(self.params), _ptr(nodes), _ptr(node_vel), _vp(aligned),
+                               ctypes.c_size_t(self.workspace_bytes), _vp(self.stream.cuda_stream), ctypes.byref(self.h))
+        if rc:
+            raise GbrError(rc, self.L.gbr_last_global_error().decode())
+        self._check(self.L.gbr_compute_metrics(self.h))
+
+    def _check(self, rc):
+        if rc:
+            raise GbrError(rc, self.L.gbr_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.L.gbr_destroy(self.h)
+            self.h = _vp()
+
+    def __del__(self):
+        self.close()
+
+    @property
+    def cell_shape(self):
+        return tuple(reversed(self.n))
+
+    def face_shape(self, d):
+        n = list(self.n)
+        n[d] += 1
+        return tuple(reversed(n))
+
+    # ---- state
+    def set_state(self, q):
+        t = self.torch
+        if isinstance(q, t.Tensor) and q.is_cuda:
+            q = q.contiguous().to(t.float64)
+            self._check(self.L.gbr_set_state(self.h, _vp(q.data_ptr()), 1))
+            self.stream.synchronize()
+        else:
+            q = _f64(q)
+            assert q.shape == (self.nv,) + self.cell_shape, q.shape
+            self._check(self.L.gbr_set_state(self.h, _vp(q.ctypes.data), 0))
+
+    def get_state(self):
+        out = np.empty((self.nv,) + self.cell_shape)
+        self._check(self.L.gbr_get_state(self.h, _vp(out.ctypes.data), 0))
+        return out
+
+    def state_into(self, tensor):
+        self._check(self.L.gbr_get_state(self.h, _vp(tensor.data_ptr()), 1))
+
+    # ---- method
+    def rhs(self, out=None):
+        t = self.torch
+        if out is None:
+            out = t.empty((self.nv,) + self.cell_shape, dtype=t.float64, device=self.device)
+        self._check(self.L.gbr_rhs(self.h, _vp(out.data_ptr())))
+        return out
+
+    def dt(self, cfl):
+        v = ctypes.c_double()
+        self._check(self.L.gbr_compute_dt(self.h, float(cfl), ctypes.byref(v)))
+        return v.value
+
+    def rk_step(self, cfl_or_neg_dt):
+        self._check(self.L.gbr_rk_step(self.h, float(cfl_or_neg_dt)))
+
+    def sync(self, timeout=60.0):
+        self._check(self.L.gbr_sync(self.h, float(timeout)))
+
+    def time(self):
+        t = ctypes.c_double()
+        dt = ctypes.c_double()
+        self._check(self.L.gbr_get_time(self.h, ctypes.byref(t), ctypes.byref(dt)))
+        return t.value, dt.value
+
+    def move_mesh(self, nodes, node_vel=None):
+        nodes = _f64(nodes)
+        node_vel = _f64(node_vel)
+        self._check(self.L.gbr_move_mesh(self.h, _ptr(nodes), _ptr(node_vel)))
+
+    def set_motion(self, motion, t0=0.0):
+        self._motion = make_motion(motion)
+        self._check(self.L.gbr_set_motion(self.h, ctypes.byref(self._motion), float(t0)))
+
+    def set_inflow(self, prim):
+        prim = _f64(prim)
+        self._check(self.L.gbr_set_inflow(self.h, _ptr(prim)))
+
+    def set_sponge(self, sigma, q_amb):
+        sigma = _f64(sigma)
+        q_amb = _f64(q_amb)
+        self._check(self.L.gbr_set_sponge(self.h, _ptr(sigma), _ptr(q_amb)))
+
+    # ---- read-back for tests
+    def field(self, which, d=0):
+        nd = self.nd
+        shapes = {
+            GBR_FIELD_CELL_METRICS: (nd, nd) + self.cell_shape,
+            GBR_FIELD_CELL_DET: self.cell_shape,
+            GBR_FIELD_CELL_TIME: (nd,) + self.cell_shape,
+            GBR_FIELD_FACE_HAT: (nd,) + self.face_shape(d),
+            GBR_FIELD_FACE_UNHAT: (nd, nd) + self.face_shape(d),
+            GBR_FIELD_FACE_TIME: self.face_shape(d),
+            GBR_FIELD_GCL: self.cell_shape,
+            GBR_FIELD_FACE_FLUX: (self.nv,) + self.face_shape(d),
+        }
+        out = np.empty(shapes[which])
+        self._check(self.L.gbr_get_field(self.h, which, d, _ptr(out)))
+        return out
