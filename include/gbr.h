@@ -143,6 +143,13 @@ gbr_status gbr_get_time(gbr_ctx* c, double* t, double* dt);
  * face direction for face fields.  Waits for the stream. */
 gbr_status gbr_get_field(gbr_ctx* c, int which, int dir, double* host_out);
 
+/* Measurement hook (no counterpart in the paper): waits for the stream,
+ * returns the summed CUDA-event time of the face-flux launches recorded since
+ * the previous call (face_ms), their count, and the number of kernels the
+ * context launched, then resets the tallies.  enable = 1 records events around
+ * every face-flux launch from now on; 0 stops recording.  Out pointers may be NULL. */
+gbr_status gbr_profile(gbr_ctx* c, int enable, double* face_ms, long long* face_launches, long long* launches);
+
 const char* gbr_last_error(const gbr_ctx* c);
 const char* gbr_last_global_error(void);
 void gbr_destroy(gbr_ctx* c);

@@ -76,6 +76,7 @@ def _lib(counting=False):
     lib.orc_mp_limit.argtypes = [ctypes.c_double] * 10
     lib.orc_mp_limit.restype = ctypes.c_double
     lib.orc_count_get.argtypes = [ctypes.POINTER(ctypes.c_ulonglong)] * 4
+    lib.orc_count_get_phase.argtypes = [ctypes.c_int] + [ctypes.POINTER(ctypes.c_ulonglong)] * 4
     _LIBS[key] = lib
     return lib
 
@@ -275,15 +276,22 @@ def mp_limit(wface, w_up, w_base, w_down, d_up, d_base, d_down, alpha=4.0, beta=
     return float(_lib().orc_mp_limit(wface, w_up, w_base, w_down, d_up, d_base, d_down, alpha, beta, eps))
 
 
+PHASES = {"misc": 0, "prim": 1, "grad": 2, "face": 3, "res": 4, "geom": 5}
+
+
 def flop_counts(fn):
-    """Run ``fn()`` (which must use ``Oracle(..., counting=True)``) and return the operation tallies."""
+    """Run ``fn()`` (which must use ``Oracle(..., counting=True)``) and return the operation
+    tallies per phase of the method (add/sub, mul, div, sqrt; flops = their sum)."""
     lib = _lib(True)
     lib.orc_count_reset()
     fn()
-    vals = [ctypes.c_ulonglong() for _ in range(4)]
-    lib.orc_count_get(*[ctypes.byref(v) for v in vals])
-    add, mul, div, sq = (v.value for v in vals)
-    return {"add": add, "mul": mul, "div": div, "sqrt": sq, "flops": add + mul + div + sq}
+    out = {}
+    for name, ph in list(PHASES.items()) + [("all", -1)]:
+        vals = [ctypes.c_ulonglong() for _ in range(4)]
+        lib.orc_count_get_phase(ph, *[ctypes.byref(v) for v in vals])
+        add, mul, div, sq = (v.value for v in vals)
+        out[name] = {"add": add, "mul": mul, "div": div, "sqrt": sq, "flops": add + mul + div + sq}
+    return out
 
 
 def threads():

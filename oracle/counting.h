@@ -13,7 +13,9 @@
 struct OrcCounters {
   unsigned long long add, mul, div, sqrt;
 };
-extern OrcCounters orc_counters;
+// Tallies are kept per phase of the method (see orc.cpp: ORC_PHASE_*).
+extern OrcCounters orc_counters[8];
+extern int orc_phase;
 
 struct CReal {
   double v;
@@ -21,10 +23,10 @@ struct CReal {
   CReal(double x) : v(x) {}  // implicit: literals promote
 };
 
-inline CReal operator+(CReal a, CReal b) { orc_counters.add++; return CReal(a.v + b.v); }
-inline CReal operator-(CReal a, CReal b) { orc_counters.add++; return CReal(a.v - b.v); }
-inline CReal operator*(CReal a, CReal b) { orc_counters.mul++; return CReal(a.v * b.v); }
-inline CReal operator/(CReal a, CReal b) { orc_counters.div++; return CReal(a.v / b.v); }
+inline CReal operator+(CReal a, CReal b) { orc_counters[orc_phase].add++; return CReal(a.v + b.v); }
+inline CReal operator-(CReal a, CReal b) { orc_counters[orc_phase].add++; return CReal(a.v - b.v); }
+inline CReal operator*(CReal a, CReal b) { orc_counters[orc_phase].mul++; return CReal(a.v * b.v); }
+inline CReal operator/(CReal a, CReal b) { orc_counters[orc_phase].div++; return CReal(a.v / b.v); }
 inline CReal operator-(CReal a) { return CReal(-a.v); }
 inline CReal& operator+=(CReal& a, CReal b) { a = a + b; return a; }
 inline CReal& operator-=(CReal& a, CReal b) { a = a - b; return a; }

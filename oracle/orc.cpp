@@ -46,8 +46,10 @@
 #ifdef ORC_COUNTING
 #include "counting.h"
 typedef CReal real;
-OrcCounters orc_counters = {0, 0, 0, 0};
-static inline real Sqrt(real a) { orc_counters.sqrt++; return CReal(std::sqrt(a.v)); }
+OrcCounters orc_counters[8] = {};
+int orc_phase = 0;
+static inline real Sqrt(real a) { orc_counters[orc_phase].sqrt++; return CReal(std::sqrt(a.v)); }
+#define ORC_PHASE(x) (orc_phase = (x))
 static inline real Fabs(real a) { return CReal(std::fabs(a.v)); }
 static inline double Dbl(real a) { return a.v; }
 #else
@@ -55,7 +57,11 @@ typedef double real;
 static inline real Sqrt(real a) { return std::sqrt(a); }
 static inline real Fabs(real a) { return std::fabs(a); }
 static inline double Dbl(real a) { return a; }
+#define ORC_PHASE(x) ((void)0)
 #endif
+// phases of the counting build: 0 time step / RK combination, 1 primitives,
+// 2 gradients, 3 interface fluxes, 4 divergence and source terms, 5 geometry
+enum { PH_MISC = 0, PH_PRIM = 1, PH_GRAD = 2, PH_FACE = 3, PH_RES = 4, PH_GEOM = 5 };
 
 static std::string g_err;
 static int fail(const std::string& m) { g_err = m; return 1; }
@@ -510,6 +516,7 @@ int orc_solver::centroids_from_nodes(const double* nodes, const double* vel, Fie
 // Sec. 4 and Sec. 6: conservative metrics, Jacobian, time metrics, face
 // interpolation and the GCL term.  xc/vc: centroids (velocities) on ext.
 int orc_solver::build_geometry(const Field* xc, const Field* vc) {
+  ORC_PHASE(PH_GEOM);
   const int sch = p.metric_scheme;
   Field xd[3][3];  // xd[a][d] = d x_a / d xi_d
   for (int a = 0; a < nd; ++a)
@@ -608,6 +615,7 @@ int orc_solver::build_geometry(const Field* xc, const Field* vc) {
       g.gcl.at(i, j, k) = -s;
     }
   }
+  ORC_PHASE(PH_MISC);
   return 0;
 }
 
@@ -766,6 +774,7 @@ int orc_solver::rhs(const double* q, double* Lout, double* resout, int fdir, dou
   Field P[5];
   for (int c = 0; c < nv; ++c) P[c] = Field(pad);
   // primitive variables at the cell centres (Sec. 2)
+  ORC_PHASE(PH_PRIM);
   const real gm1 = p.gamma - 1.0;
   FOR_BOX(inner) {
     size_t id = inner.idx(i, j, k);
@@ -792,6 +801,7 @@ int orc_solver::rhs(const double* q, double* Lout, double* resout, int fdir, dou
     FOR_BOX(pad) { T.at(i, j, k) = P[nv - 1].at(i, j, k) / P[0].at(i, j, k); }  // T = p/rho (R = 1, A14)
   }
   // Sec. 5.1 step 1: gradients along each computational direction
+  ORC_PHASE(PH_GRAD);
   Field P1[3][5], P2[3][5], T1[3];
   for (int d = 0; d < nd; ++d) {
     for (int c = 0; c < nv; ++c) {
@@ -801,6 +811,7 @@ int orc_solver::rhs(const double* q, double* Lout, double* resout, int fdir, dou
     if (viscous) T1[d] = op_e6(T, d);
   }
   // interface fluxes G = F^ - F^v for faces i+1/2, i = -1..n-1
+  ORC_PHASE(PH_FACE);
   Field Gf[3][5];
   for (int d = 0; d < nd; ++d) {
     Box fb = inner;
@@ -825,6 +836,7 @@ int orc_solver::rhs(const double* q, double* Lout, double* resout, int fdir, dou
     }
   }
   // Sec. 3: Res = -sum_d [(F^ - F^v)_{+1/2} - (F^ - F^v)_{-1/2}]; time split of Sec. 4
+  ORC_PHASE(PH_RES);
   for (int c = 0; c < nv; ++c) {
     FOR_BOX(inner) {
       size_t id = inner.idx(i, j, k);
@@ -840,6 +852,7 @@ int orc_solver::rhs(const double* q, double* Lout, double* resout, int fdir, dou
       }
     }
   }
+  ORC_PHASE(PH_MISC);
   return 0;
 }
 
@@ -1075,14 +1088,23 @@ double orc_mp_limit(double wface, double w_up, double w_base, double w_down, dou
 
 void orc_count_reset(void) {
 #ifdef ORC_COUNTING
-  orc_counters = OrcCounters{0, 0, 0, 0};
+  for (int m = 0; m < 8; ++m) orc_counters[m] = OrcCounters{0, 0, 0, 0};
+  orc_phase = PH_MISC;
 #endif
 }
 void orc_count_get(unsigned long long* add, unsigned long long* mul, unsigned long long* div, unsigned long long* sq) {
-#ifdef ORC_COUNTING
-  *add = orc_counters.add; *mul = orc_counters.mul; *div = orc_counters.div; *sq = orc_counters.sqrt;
-#else
+  orc_count_get_phase(-1, add, mul, div, sq);
+}
+void orc_count_get_phase(int phase, unsigned long long* add, unsigned long long* mul, unsigned long long* div,
+                         unsigned long long* sq) {
   *add = *mul = *div = *sq = 0;
+#ifdef ORC_COUNTING
+  for (int m = 0; m < 8; ++m) {
+    if (phase >= 0 && m != phase) continue;
+    *add += orc_counters[m].add; *mul += orc_counters[m].mul; *div += orc_counters[m].div; *sq += orc_counters[m].sqrt;
+  }
+#else
+  (void)phase;
 #endif
 }
 int orc_is_counting(void) {

@@ -83,6 +83,10 @@ double orc_mp_limit(double wface, double w_up, double w_base, double w_down,
 void orc_count_reset(void);
 void orc_count_get(unsigned long long* add, unsigned long long* mul,
                    unsigned long long* div, unsigned long long* sqrt_);
+/* phase: 0 time step / RK combination, 1 primitives, 2 gradients, 3 interface
+   fluxes, 4 divergence and source terms, 5 geometry; -1 = all */
+void orc_count_get_phase(int phase, unsigned long long* add, unsigned long long* mul,
+                         unsigned long long* div, unsigned long long* sqrt_);
 int  orc_is_counting(void);
 int  orc_threads(void);
 

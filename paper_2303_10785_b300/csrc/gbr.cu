@@ -286,6 +286,11 @@ struct gbr_ctx {
   Motion motion;
   double last_fixed_dt;
   std::string last_error;
+  // profiling: kernel launches issued, CUDA events around each face-flux launch
+  long long launches;
+  bool prof;
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used;
 };
 
 namespace {
@@ -306,7 +311,11 @@ gbr_status cuda_check(gbr_ctx* c, cudaError_t e, const char* what) {
     gbr_status _s = cuda_check(c, (expr), what);             \
     if (_s != GBR_OK) return _s;                             \
   } while (0)
-#define CKL(what) CK(cudaGetLastError(), what)
+#define CKL(what)                  \
+  do {                             \
+    ++c->launches;                 \
+    CK(cudaGetLastError(), what);  \
+  } while (0)
 
 GeoArgs geo_args(gbr_ctx* c) {
   GeoArgs G;
@@ -533,10 +542,24 @@ RhsArgs rhs_args(gbr_ctx* c, const double* q) {
   return A;
 }
 
+gbr_status prof_event(gbr_ctx* c) {
+  if (c->ev_used == c->ev.size()) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e), "event create");
+    c->ev.push_back(e);
+  }
+  CK(cudaEventRecord(c->ev[c->ev_used++], c->stream), "event record");
+  return GBR_OK;
+}
+
 template <int ND>
 gbr_status launch_face(gbr_ctx* c, const RhsArgs& A, int d, const Box& b) {
   const unsigned g = grid_of(b, kFaceBlock);
   cudaStream_t st = c->stream;
+  if (c->prof) {
+    gbr_status s0 = prof_event(c);
+    if (s0 != GBR_OK) return s0;
+  }
   if (c->visc) {
     if (c->mov) k_face<ND, true, true><<<g, kFaceBlock, 0, st>>>(A, d, b);
     else k_face<ND, true, false><<<g, kFaceBlock, 0, st>>>(A, d, b);
@@ -545,6 +568,7 @@ gbr_status launch_face(gbr_ctx* c, const RhsArgs& A, int d, const Box& b) {
     else k_face<ND, false, false><<<g, kFaceBlock, 0, st>>>(A, d, b);
   }
   CKL("k_face");
+  if (c->prof) return prof_event(c);
   return GBR_OK;
 }
 
@@ -720,6 +744,9 @@ gbr_status gbr_create(const gbr_params* p, const double* nodes, const double* no
   c->have_motion = false;
   c->metrics_ready = false;
   c->last_fixed_dt = 0.0;
+  c->launches = 0;
+  c->prof = false;
+  c->ev_used = 0;
   for (int v = 0; v < 5; ++v) c->qamb[v] = 0.0;
   carve(c);
   cudaError_t e = cudaMemsetAsync(c->ws, 0, P.total, c->stream);
@@ -955,9 +982,31 @@ gbr_status gbr_get_field(gbr_ctx* c, int which, int dir, double* out) {
   }
 }
 
+gbr_status gbr_profile(gbr_ctx* c, int enable, double* face_ms, long long* face_launches, long long* launches) {
+  if (!c) return fail(nullptr, GBR_EINVAL, "null context");
+  CK(cudaStreamSynchronize(c->stream), "profile sync");
+  double total = 0.0;
+  for (size_t m = 0; m + 1 < c->ev_used; m += 2) {
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, c->ev[m], c->ev[m + 1]), "event elapsed");
+    total += ms;
+  }
+  if (face_ms) *face_ms = total;
+  if (face_launches) *face_launches = (long long)(c->ev_used / 2);
+  if (launches) *launches = c->launches;
+  c->ev_used = 0;
+  c->launches = 0;
+  c->prof = enable != 0;
+  return GBR_OK;
+}
+
 const char* gbr_last_error(const gbr_ctx* c) { return c ? c->last_error.c_str() : g_global_error.c_str(); }
 const char* gbr_last_global_error(void) { return g_global_error.c_str(); }
 
-void gbr_destroy(gbr_ctx* c) { delete c; }
+void gbr_destroy(gbr_ctx* c) {
+  if (!c) return;
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  delete c;
+}
 
 }  // extern "C"

@@ -84,6 +84,8 @@ def lib():
     L.gbr_sync.argtypes = [_vp, ctypes.c_double]
     L.gbr_get_time.argtypes = [_vp, _P, _P]
     L.gbr_get_field.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _P]
+    L.gbr_profile.argtypes = [_vp, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    L.gbr_profile.restype = ctypes.c_int
     L.gbr_last_error.argtypes = [_vp]
     L.gbr_last_error.restype = ctypes.c_char_p
     L.gbr_last_global_error.restype = ctypes.c_char_p
@@ -100,8 +102,8 @@ def exported_symbols():
     """Names declared in include/gbr.h that the library must export."""
     return ["gbr_workspace_bytes", "gbr_create", "gbr_compute_metrics", "gbr_move_mesh", "gbr_set_motion",
             "gbr_set_state", "gbr_get_state", "gbr_set_inflow", "gbr_set_sponge", "gbr_rhs", "gbr_compute_dt",
-            "gbr_rk_step", "gbr_sync", "gbr_get_time", "gbr_get_field", "gbr_last_error", "gbr_last_global_error",
-            "gbr_destroy"]
+            "gbr_rk_step", "gbr_sync", "gbr_get_time", "gbr_get_field", "gbr_profile", "gbr_last_error",
+            "gbr_last_global_error", "gbr_destroy"]
 
 
 def make_params(case):
@@ -264,6 +266,14 @@ class Solver:
         sigma = _f64(sigma)
         q_amb = _f64(q_amb)
         self._check(self.L.gbr_set_sponge(self.h, _ptr(sigma), _ptr(q_amb)))
+
+    def profile(self, enable=True):
+        """(face-kernel ms, face launches, kernel launches) since the last call; then (re)arms recording."""
+        ms = ctypes.c_double()
+        nf = ctypes.c_longlong()
+        nl = ctypes.c_longlong()
+        self._check(self.L.gbr_profile(self.h, int(enable), ctypes.byref(ms), ctypes.byref(nf), ctypes.byref(nl)))
+        return ms.value, nf.value, nl.value
 
     # ---- read-back for tests
     def field(self, which, d=0):

@@ -1,0 +1,364 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (FP64): right-hand sides within 1e-12 of the cancellation scale of
+each conserved component (reading A27: the flux-difference scale, since the
+freestream RHS is ~0); states within 1e-12 (relative to max |Q| per component)
+after one RK3 stage/step and 1e-10 after 100 steps of a smooth case.  Sizes are
+ragged (not multiples of the 128/256-thread blocks) and span many blocks.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2303_10785_b300 import gbr
+from paper_2303_10785_b300 import inputs as I
+from _util import cancellation_scale
+
+pytestmark = pytest.mark.gpu
+
+GAMMA = 1.4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+
+
+def rel_state(a, b):
+    nv = a.shape[0]
+    return (np.abs(a - b).reshape(nv, -1).max(axis=1) / np.abs(b).reshape(nv, -1).max(axis=1)).max()
+
+
+def rhs_err(orc, solver, q):
+    Lg = solver.rhs().cpu().numpy()
+    Lo = orc.rhs(q)
+    scale = cancellation_scale(orc, q)
+    return (np.abs(Lg - Lo).reshape(q.shape[0], -1).max(axis=1) / scale).max()
+
+
+# ---------------------------------------------------------------------------
+# cases
+# ---------------------------------------------------------------------------
+def case_2d_vortex(n=64):
+    case = I.case_params(2, (n, n))
+    nodes = I.nodes_wavy_2d(n)
+    xc = I.centroids(nodes, (n, n), (1, 1))
+    return case, nodes, None, I.prim_to_cons(I.vortex_prim(xc[0], xc[1]), GAMMA)
+
+
+def case_2d_viscous_random():
+    n = (45, 33)
+    case = I.case_params(2, n, reynolds=300.0, sutherland_s=0.3768)
+    nodes = I.nodes_random(n, (9.0, 6.6), frac=0.2)
+    xc = I.centroids(nodes, n, (1, 1))
+    q = I.prim_to_cons(I.vortex_prim(xc[0], xc[1], center=(4.5, 3.3), L=9.0, strength=3.0), GAMMA)
+    return case, nodes, None, q
+
+
+def case_3d_tgv(n=(40, 36, 28)):
+    case = I.case_params(3, n, reynolds=1600.0)
+    L = (2 * np.pi,) * 3
+    nodes = I.nodes_random(n, L, frac=0.15)
+    xc = I.centroids(nodes, n, (1, 1, 1))
+    return case, nodes, None, I.prim_to_cons(I.tgv_prim(*xc), GAMMA)
+
+
+def case_3d_inviscid_ragged():
+    n = (37, 29, 21)
+    case = I.case_params(3, n)
+    nodes = I.nodes_random(n, (1.0, 0.8, 0.6), frac=0.2)
+    xc = I.centroids(nodes, n, (1, 1, 1))
+    P = I.tgv_prim(xc[0] * 2 * np.pi, xc[1] * 2 * np.pi / 0.8, xc[2] * 2 * np.pi / 0.6, mach=0.5)
+    return case, nodes, None, I.prim_to_cons(P, GAMMA)
+
+
+def case_2d_moving():
+    m = I.motion_dynamic_2d(n=48, L=10.0, amp=0.3)
+    case = I.case_params(2, (48, 48), moving=1)
+    t = 0.13
+    nodes, vel = m.nodes(t), m.velocity(t)
+    xc = I.centroids(nodes, (48, 48), (1, 1))
+    return case, nodes, vel, I.prim_to_cons(I.vortex_prim(xc[0], xc[1]), GAMMA)
+
+
+def case_3d_moving_viscous():
+    m = I.motion_deforming_3d(n=24, L=18.0)
+    case = I.case_params(3, (24, 24, 24), moving=1, reynolds=500.0)
+    nodes, vel = m.nodes(0.07), m.velocity(0.07)
+    xc = I.centroids(nodes, (24, 24, 24), (1, 1, 1))
+    s = 2 * np.pi / 18.0
+    return case, nodes, vel, I.prim_to_cons(I.tgv_prim(xc[0] * s, xc[1] * s, xc[2] * s), GAMMA)
+
+
+def case_jet(n=(40, 22, 18)):
+    ni, nj, nk = n
+    case = I.case_params(3, n, periodic=(0, 0, 0), bc=((2, 1), (1, 1), (1, 1)), reynolds=1e4, sutherland_s=0.3768)
+    nodes = I.nodes_jet(ni, nj, nk, Lx=4.0, h0=0.08, ratio=1.05)
+    xc = I.centroids(nodes, n, (0, 0, 0))
+    inflow = np.ascontiguousarray(I.jet_inflow_prim(xc[1][:, :, 0], xc[2][:, :, 0], delta=0.1))
+    P = I.uniform_prim((nk, nj, ni), 3, vel=(0.0, 0.0, 0.0))
+    P[4] = 1.0
+    P[:, :, :, :6] = inflow[:, :, :, None]
+    sigma = I.jet_sponge_sigma(n, lateral=4)
+    qamb = np.array([1.0, 0.0, 0.0, 0.0, 1.0 / 0.4])
+    extra = dict(inflow=inflow, sigma=sigma, qamb=qamb)
+    return case, nodes, None, I.prim_to_cons(P, GAMMA), extra
+
+
+def build_pair(case, nodes, vel, extra=None):
+    orc = O.Oracle(case, nodes, vel)
+    s = gbr.Solver(case, nodes, vel)
+    if extra:
+        orc.set_inflow(extra["inflow"])
+        s.set_inflow(extra["inflow"])
+        orc.set_sponge(extra["sigma"], extra["qamb"])
+        s.set_sponge(extra["sigma"], extra["qamb"])
+    return orc, s
+
+
+CASES = {
+    "2d_vortex": case_2d_vortex,
+    "2d_viscous_random": case_2d_viscous_random,
+    "3d_tgv": case_3d_tgv,
+    "3d_inviscid_ragged": case_3d_inviscid_ragged,
+    "2d_moving": case_2d_moving,
+    "3d_moving_viscous": case_3d_moving_viscous,
+}
+
+
+# ---------------------------------------------------------------------------
+# geometry
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["3d_tgv", "2d_moving", "3d_moving_viscous"])
+def test_metrics_match_oracle(name):
+    case, nodes, vel, q = CASES[name]()
+    orc, s = build_pair(case, nodes, vel)
+    nd = case["ndim"]
+    mh_o, det_o = orc.cell_metrics()
+    mh_g = s.field(gbr.GBR_FIELD_CELL_METRICS)
+    det_g = s.field(gbr.GBR_FIELD_CELL_DET)
+    assert np.abs(det_g - det_o).max() < 1e-13 * np.abs(det_o).max()
+    assert np.abs(mh_g - mh_o).max() < 1e-13 * np.abs(mh_o).max()
+    for d in range(nd):
+        fh_o, fu_o, ft_o = orc.face_metrics(d)
+        fh_g = s.field(gbr.GBR_FIELD_FACE_HAT, d)
+        assert np.abs(fh_g - fh_o).max() < 1e-13 * np.abs(fh_o).max()
+        if case["reynolds"] > 0:
+            fu_g = s.field(gbr.GBR_FIELD_FACE_UNHAT, d)
+            assert np.abs(fu_g - fu_o).max() < 1e-12 * np.abs(fu_o).max()
+        if vel is not None:
+            ft_g = s.field(gbr.GBR_FIELD_FACE_TIME, d)
+            assert np.abs(ft_g - ft_o).max() < 1e-12 * np.abs(ft_o).max()
+    if vel is not None:
+        g_o = orc.gcl()
+        g_g = s.field(gbr.GBR_FIELD_GCL)
+        assert np.abs(g_g - g_o).max() < 1e-11 * np.abs(g_o).max()
+    s.close()
+
+
+# ---------------------------------------------------------------------------
+# right-hand side and steps
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_rhs_matches_oracle(name):
+    case, nodes, vel, q = CASES[name]()
+    orc, s = build_pair(case, nodes, vel)
+    s.set_state(q)
+    assert rhs_err(orc, s, q) < 1e-12
+    s.close()
+
+
+def test_jet_rhs_with_inflow_and_sponge():
+    case, nodes, vel, q, extra = case_jet()
+    orc, s = build_pair(case, nodes, vel, extra)
+    s.set_state(q)
+    assert rhs_err(orc, s, q) < 1e-12
+    # a few fixed-dt steps through the ghost/sponge path
+    qo = q.copy()
+    for _ in range(3):
+        qo = orc.rk3(qo, 2e-3)
+        s.rk_step(-2e-3)
+    s.sync()
+    assert rel_state(s.get_state(), qo) < 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["2d_vortex", "3d_tgv", "3d_inviscid_ragged"])
+def test_face_fluxes_match_oracle(name):
+    case, nodes, vel, q = CASES[name]()
+    orc, s = build_pair(case, nodes, vel)
+    s.set_state(q)
+    s.rhs()
+    for d in range(case["ndim"]):
+        go = orc.face_flux(q, d)
+        gg = s.field(gbr.GBR_FIELD_FACE_FLUX, d)
+        sc = np.abs(go).reshape(go.shape[0], -1).max(axis=1)
+        assert (np.abs(gg - go).reshape(go.shape[0], -1).max(axis=1) / sc).max() < 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["2d_vortex", "2d_viscous_random", "3d_tgv"])
+def test_one_step_and_dt_match_oracle(name):
+    case, nodes, vel, q = CASES[name]()
+    orc, s = build_pair(case, nodes, vel)
+    s.set_state(q)
+    dt_g = s.dt(0.4)
+    dt_o = orc.dt(q, 0.4)
+    assert abs(dt_g - dt_o) <= 1e-13 * dt_o
+    s.rk_step(0.4)
+    s.sync()
+    assert rel_state(s.get_state(), orc.rk3(q, dt_o)) < 1e-12
+    t, dt = s.time()
+    assert abs(t - dt_o) <= 1e-13 * dt_o and abs(dt - dt_o) <= 1e-13 * dt_o
+    s.close()
+
+
+def test_hundred_steps_isentropic_vortex_wavy_mesh():
+    # 64 x 64 vortex on the wavy periodic mesh, CFL 0.4 (the small 2D workload)
+    case, nodes, vel, q = case_2d_vortex(64)
+    orc, s = build_pair(case, nodes, vel)
+    s.set_state(q)
+    qo = q.copy()
+    for _ in range(100):
+        qo = orc.rk3(qo, orc.dt(qo, 0.4))
+        s.rk_step(0.4)
+    s.sync()
+    assert rel_state(s.get_state(), qo) < 1e-10
+    s.close()
+
+
+def test_moving_mesh_steps_match_oracle():
+    # analytic motion on the device vs host node sets at the stage times
+    m = I.motion_dynamic_2d(n=64, L=10.0, amp=0.1)
+    case = I.case_params(2, (64, 64), moving=1)
+    nodes, vel = m.nodes(0.0), m.velocity(0.0)
+    xc = I.centroids(nodes, (64, 64), (1, 1))
+    q = I.prim_to_cons(I.vortex_prim(xc[0], xc[1]), GAMMA)
+    orc, s = build_pair(case, nodes, vel)
+    s.set_motion(m, 0.0)
+    s.set_state(q)
+    t, dt = 0.0, 0.01
+    qo = q.copy()
+    for _ in range(20):
+        ts = (t, t + dt, t + 0.5 * dt)
+        qo = orc.rk3(qo, dt, [m.nodes(x) for x in ts], [m.velocity(x) for x in ts])
+        s.rk_step(-dt)
+        t += dt
+    s.sync()
+    assert rel_state(s.get_state(), qo) < 1e-10
+    tg, _ = s.time()
+    assert abs(tg - t) < 1e-12
+    s.close()
+
+
+def test_freestream_preserved_on_gpu_static_and_moving():
+    n = (20, 20, 20)
+    case = I.case_params(3, n)
+    nodes = I.nodes_random(n, (4.0, 4.0, 4.0), frac=0.2)
+    q = I.prim_to_cons(I.uniform_prim((20, 20, 20), 3), GAMMA)
+    orc, s = build_pair(case, nodes, None)
+    s.set_state(q)
+    scale = cancellation_scale(orc, q)
+    L = s.rhs().cpu().numpy()
+    assert (np.abs(L).reshape(5, -1).max(axis=1) / scale).max() < 1e-13
+    s.close()
+    m = I.motion_deforming_3d(n=16, L=12.0)
+    case = I.case_params(3, (16, 16, 16), moving=1)
+    q = I.prim_to_cons(I.uniform_prim((16, 16, 16), 3), GAMMA)
+    s = gbr.Solver(case, m.nodes(0.0), m.velocity(0.0))
+    s.set_motion(m, 0.0)
+    s.set_state(q)
+    for _ in range(5):
+        s.rk_step(-0.01)
+    s.sync()
+    qg = s.get_state()
+    assert np.abs(qg[2] / qg[0]).max() < 1e-13 and np.abs(qg - q).max() < 1e-12
+    s.close()
+
+
+def test_full_size_taylor_green_rhs_matches_oracle():
+    # the benchmark workload: 128^3 viscous TGV on the 0.1 h perturbed mesh, full-grid comparison
+    n = 128
+    case = I.case_params(3, (n, n, n), reynolds=1600.0)
+    nodes = I.nodes_tgv_3d(n, 0.1)
+    xc = I.centroids(nodes, (n, n, n), (1, 1, 1))
+    q = I.prim_to_cons(I.tgv_prim(*xc), GAMMA)
+    orc, s = build_pair(case, nodes, None)
+    s.set_state(q)
+    assert rhs_err(orc, s, q) < 1e-12
+    s.close()
+
+
+def test_deterministic_and_checkpoint_resume_bitwise():
+    case, nodes, vel, q = case_3d_tgv((24, 20, 18))
+    a = gbr.Solver(case, nodes)
+    a.set_state(q)
+    for _ in range(6):
+        a.rk_step(0.3)
+    qa = a.get_state()
+    b = gbr.Solver(case, nodes)
+    b.set_state(q)
+    for _ in range(3):
+        b.rk_step(0.3)
+    mid = b.get_state()
+    b.close()
+    c = gbr.Solver(case, nodes)
+    c.set_state(mid)
+    for _ in range(3):
+        c.rk_step(0.3)
+    assert np.array_equal(c.get_state(), qa)
+    a.close()
+    c.close()
+
+
+def test_nonfinite_state_is_reported():
+    case, nodes, vel, q = case_2d_vortex(32)
+    s = gbr.Solver(case, nodes)
+    bad = q.copy()
+    bad[3, 5, 7] = np.nan
+    s.set_state(bad)
+    s.rk_step(-1e-3)
+    with pytest.raises(gbr.GbrError) as ei:
+        s.sync()
+    assert ei.value.status == gbr.GBR_ENONFINITE
+    s.close()
+
+
+def test_sync_deadline_reports_timeout_then_drains():
+    n = (96, 96, 96)
+    case = I.case_params(3, n, reynolds=1600.0)
+    nodes = I.nodes_tgv_3d(96, 0.1)
+    xc = I.centroids(nodes, n, (1, 1, 1))
+    s = gbr.Solver(case, nodes)
+    s.set_state(I.prim_to_cons(I.tgv_prim(*xc), GAMMA))
+    for _ in range(3):
+        s.rk_step(0.3)
+    with pytest.raises(gbr.GbrError) as ei:
+        s.sync(timeout=1e-6)
+    assert ei.value.status == gbr.GBR_ETIMEOUT
+    s.sync(timeout=120.0)
+    s.close()
+
+
+def test_periodic_closure_violation_rejected():
+    nodes = I.nodes_uniform((8, 8), (1.0, 1.0))
+    nodes[0, 3, -1] += 0.01
+    with pytest.raises(gbr.GbrError) as ei:
+        gbr.Solver(I.case_params(2, (8, 8)), nodes)
+    assert ei.value.status == gbr.GBR_EINVAL
+
+
+def test_minimum_periodic_size():
+    n = (6, 6, 6)
+    case = I.case_params(3, n, reynolds=100.0)
+    nodes = I.nodes_random(n, (1.0, 1.0, 1.0), frac=0.1)
+    xc = I.centroids(nodes, n, (1, 1, 1))
+    q = I.prim_to_cons(I.tgv_prim(xc[0] * 2 * math.pi, xc[1] * 2 * math.pi, xc[2] * 2 * math.pi), GAMMA)
+    orc, s = build_pair(case, nodes, None)
+    s.set_state(q)
+    assert rhs_err(orc, s, q) < 1e-12
+    s.close()
