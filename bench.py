@@ -95,7 +95,7 @@ class ClockSampler:
         sm = [float(r[0]) for r in self.rows if r[0].replace(".", "", 1).isdigit()]
         mx = [float(r[1]) for r in self.rows if r[1].replace(".", "", 1).isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if "Active" in r[3 + i]})
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(self.rows)}
 
@@ -208,34 +208,36 @@ def run_gpu(args):
     value = world * 3 * cells * args.steps / (ms / 1e3)
 
     # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
-    h_in = torch.from_numpy(np.ascontiguousarray(q)).pin_memory()
-    h_out = torch.empty_like(h_in).pin_memory()
-    import ctypes
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.from_numpy(np.ascontiguousarray(q)).pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        import ctypes
 
-    L = solver.L
-    for _ in range(2):
-        solver._check(L.gbr_set_state(solver.h, ctypes.c_void_p(h_in.data_ptr()), 0))
-        solver.rk_step(CFL)
-        solver._check(L.gbr_get_state(solver.h, ctypes.c_void_p(h_out.data_ptr()), 0))
-    barrier()
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    e2e_steps = max(1, min(args.steps, 10))
-    for _ in range(e2e_steps):
-        solver._check(L.gbr_set_state(solver.h, ctypes.c_void_p(h_in.data_ptr()), 0))
-        solver.rk_step(CFL)
-        solver._check(L.gbr_get_state(solver.h, ctypes.c_void_p(h_out.data_ptr()), 0))
-    solver.sync()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
+        L = solver.L
+        for _ in range(2):
+            solver._check(L.gbr_set_state(solver.h, ctypes.c_void_p(h_in.data_ptr()), 0))
+            solver.rk_step(CFL)
+            solver._check(L.gbr_get_state(solver.h, ctypes.c_void_p(h_out.data_ptr()), 0))
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        e2e_steps = max(1, min(args.steps, 10))
+        for _ in range(e2e_steps):
+            solver._check(L.gbr_set_state(solver.h, ctypes.c_void_p(h_in.data_ptr()), 0))
+            solver.rk_step(CFL)
+            solver._check(L.gbr_get_state(solver.h, ctypes.c_void_p(h_out.data_ptr()), 0))
+        solver.sync()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            import torch.distributed as dist
 
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    nbytes = int(q.size * 8)
-    e2e = {"value": world * 3 * cells * e2e_steps / e2e_s, "unit": METRIC, "h2d_bytes_per_step": nbytes,
-           "d2h_bytes_per_step": nbytes, "steps": e2e_steps}
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        nbytes = int(q.size * 8)
+        e2e = {"value": world * 3 * cells * e2e_steps / e2e_s, "unit": METRIC, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": e2e_steps}
 
     # ---- roofline of the interface-flux kernel (FP64 ALU bound)
     fl = load_flops()["tgv3d_viscous"]["face_flops_per_face"]
@@ -267,11 +269,17 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbr", choices=["gbr", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--edge", type=int, default=128, help="cells per edge (profiling runs use smaller grids)")
     args = ap.parse_args()
+    global N_CELLS_EDGE, WORKLOAD
+    if args.edge != N_CELLS_EDGE:
+        N_CELLS_EDGE = args.edge
+        WORKLOAD = f"tgv3d_viscous_{args.edge}^3_perturbed"
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
