@@ -7,6 +7,7 @@
 #pragma once
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #ifdef __CUDACC__
 #define GBR_HD __host__ __device__ __forceinline__
@@ -141,13 +142,54 @@ GBR_HD double gfma(double a, double b, double c) {
   return a * b + c;
 #endif
 }
-GBR_HD double gmin(double a, double b) { return a < b ? a : b; }
-GBR_HD double gmax(double a, double b) { return a > b ? a : b; }
+// Comparisons, min/max, |x| and minmod on the bit patterns of doubles.  On a
+// B300 the FP64 pipe issues 2 instructions/clk/SM while the integer pipe issues
+// 64, so the limiter's and the Riemann solver's branch logic is kept off the
+// FP64 pipe.  The key below is monotone in the value and maps +0 and -0 to the
+// same key, so key(a) < key(b) is exactly a < b for every non-NaN pair.
+GBR_HD long long dbits(double x) {
+#ifdef __CUDA_ARCH__
+  return __double_as_longlong(x);
+#else
+  long long r;
+  std::memcpy(&r, &x, sizeof r);
+  return r;
+#endif
+}
+GBR_HD double bitsd(long long b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double(b);
+#else
+  double r;
+  std::memcpy(&r, &b, sizeof r);
+  return r;
+#endif
+}
+constexpr long long kMag = 0x7fffffffffffffffLL;
+constexpr long long kSign = (long long)0x8000000000000000ULL;
+GBR_HD long long okey(double x) {
+  const long long b = dbits(x);
+  return b < 0 ? -(b & kMag) : b;
+}
+GBR_HD bool dlt(double a, double b) { return okey(a) < okey(b); }
+GBR_HD bool dle(double a, double b) { return okey(a) <= okey(b); }
+GBR_HD bool is_pos(double x) { return dbits(x) > 0; }                       // x > 0
+GBR_HD bool is_neg(double x) { return (dbits(x) & kMag) != 0 && dbits(x) < 0; }  // x < 0
+GBR_HD double gmin(double a, double b) { return dlt(a, b) ? a : b; }  // same as a < b ? a : b
+GBR_HD double gmax(double a, double b) { return dlt(b, a) ? a : b; }  // same as a > b ? a : b
+GBR_HD double gabs(double x) { return bitsd(dbits(x) & kMag); }
 // App. E: minmod(a, b) = 1/2 (sign a + sign b) min(|a|, |b|), i.e. the smaller-magnitude
 // argument when both have the same sign, else 0.
 GBR_HD double minmod(double a, double b) {
-  const double m = gmin(std::fabs(a), std::fabs(b));
-  return (a > 0.0 && b > 0.0) ? m : ((a < 0.0 && b < 0.0) ? -m : 0.0);
+  const long long ba = dbits(a), bb = dbits(b);
+  const long long ma = ba & kMag, mb = bb & kMag;
+  const long long m = ma < mb ? ma : mb;  // |a| < |b| ? |a| : |b|
+  const int sa = ba > 0 ? 1 : ((ba < 0 && ma != 0) ? -1 : 0);
+  const int sb = bb > 0 ? 1 : ((bb < 0 && mb != 0) ? -1 : 0);
+  const int sum = sa + sb;
+  if (sum == 2) return bitsd(m);
+  if (sum == -2) return bitsd(m | kSign);
+  return sum < 0 ? -0.0 : 0.0;  // one argument is zero: the product with the sign sum keeps its sign
 }
 
 // Composite stencils of the MEG6 interface operators (Sec. 6): the interface
@@ -492,7 +534,7 @@ GBR_HD void back_project(const double* nu, double ira, double ia2, const double*
 // Returns the limited W_face - W_base.
 GBR_HD double mp_relative(double f, double dm, double dp, double du, double db, double dd, const Phys& ph) {
   const double mmp = minmod(dp, ph.mp_beta * dm);  // W^MP - W_base
-  if (f * (f - mmp) <= ph.mp_eps) return f;
+  if (dle(f * (f - mmp), ph.mp_eps)) return f;
   const double dmp = minmod(db, dd);  // d^M_{i+1/2}
   const double dmm = minmod(du, db);  // d^M_{i-1/2}
   const double md = 0.5 * dp - 0.5 * dmp;
@@ -510,43 +552,50 @@ GBR_HD void hllc(const double* PL, const double* PR, const double* nh, double nn
   constexpr int NV = ND + 2;
   const double nn = nn2 * inn;
   const double inn2 = inn * inn;
-  double r[2], ir[2], u[2][ND], p[2], U[2], En[2], c[2];
-  const double* Ps[2] = {PL, PR};
-  for (int s = 0; s < 2; ++s) {
-    r[s] = Ps[s][0];
-    ir[s] = 1.0 / r[s];
-    double q2 = 0.0, un = nt;
-    for (int a = 0; a < ND; ++a) {
-      u[s][a] = Ps[s][1 + a];
-      q2 = gfma(u[s][a], u[s][a], q2);
-      un = gfma(nh[a], u[s][a], un);
-    }
-    U[s] = un;
-    p[s] = Ps[s][NV - 1];
-    En[s] = gfma(p[s], ph.igm1, 0.5 * r[s] * q2);
-    c[s] = sqrt(ph.gamma * p[s] * ir[s]);
+  // left and right states (kept in scalars: no runtime-indexed arrays)
+  const double rl = PL[0], rr = PR[0];
+  const double irl = 1.0 / rl, irr = 1.0 / rr;
+  const double pl = PL[NV - 1], pr = PR[NV - 1];
+  double q2l = 0.0, q2r = 0.0, Ul = nt, Ur = nt;
+  #pragma unroll
+  for (int a = 0; a < ND; ++a) {
+    q2l = gfma(PL[1 + a], PL[1 + a], q2l);
+    q2r = gfma(PR[1 + a], PR[1 + a], q2r);
+    Ul = gfma(nh[a], PL[1 + a], Ul);  // contravariant velocity, Sec. 2
+    Ur = gfma(nh[a], PR[1 + a], Ur);
   }
-  const double SL = gmin(gfma(-c[0], nn, U[0]), gfma(-c[1], nn, U[1]));
-  const double SR = gmax(gfma(c[0], nn, U[0]), gfma(c[1], nn, U[1]));
-  const double aL = r[0] * (SL - U[0]), aR = r[1] * (SR - U[1]);
-  const double Ss = (aR * U[1] - aL * U[0] + (p[0] - p[1]) * nn2) / (aR - aL);
+  const double El = gfma(pl, ph.igm1, 0.5 * rl * q2l), Er = gfma(pr, ph.igm1, 0.5 * rr * q2r);
+  const double xl = ph.gamma * pl * irl, xr = ph.gamma * pr * irr;
+  const double cl = xl * grsqrt(xl), cr = xr * grsqrt(xr);  // speeds of sound
+  const double SL = gmin(gfma(-cl, nn, Ul), gfma(-cr, nn, Ur));
+  const double SR = gmax(gfma(cl, nn, Ul), gfma(cr, nn, Ur));
+  const double aL = rl * (SL - Ul), aR = rr * (SR - Ur);
+  const double Ss = (aR * Ur - aL * Ul + (pl - pr) * nn2) / (aR - aL);
   // branches of Sec. 5.1.1: S^L >= 0 -> F^L; S^L < 0 <= S* -> F*L; S* < 0 < S^R -> F*R; else F^R
-  const int s = (SL >= 0.0 || Ss >= 0.0) ? 0 : 1;
-  const double S = s == 0 ? SL : SR;
-  const bool star = !(SL >= 0.0) && (s == 0 || SR > 0.0);
-  const double Us = U[s], rs = r[s], ps = p[s], Es = En[s];
+  const bool left = !is_neg(SL) || !is_neg(Ss);
+  const bool star = is_neg(SL) && (left || is_pos(SR));
+  const double rs = left ? rl : rr, irs = left ? irl : irr, ps = left ? pl : pr;
+  const double Us = left ? Ul : Ur, Es = left ? El : Er, S = left ? SL : SR;
+  double us[ND];
+  #pragma unroll
+  for (int a = 0; a < ND; ++a) us[a] = left ? PL[1 + a] : PR[1 + a];
   F[0] = rs * Us;
-  for (int a = 0; a < ND; ++a) F[1 + a] = gfma(rs * u[s][a], Us, nh[a] * ps);
+  #pragma unroll
+  for (int a = 0; a < ND; ++a) F[1 + a] = gfma(rs * us[a], Us, nh[a] * ps);
   F[NV - 1] = gfma(Es + ps, Us, -nt * ps);
   if (star) {
-    const double A = S - Us;
-    const double rA = rs * A;
-    const double fac = rA / (S - Ss);
+    // Q*K = rho (S - U)/(S - S*) [1, u + n^ (S* - U)/|n^|^2, E/rho + (S* - U)((S* - xi_t)/|n^|^2 + p/(rho (S - U)))]
+    const double rA = rs * (S - Us);
+    const double B = S - Ss;
+    const double inv = 1.0 / (rA * B);
+    const double fac = rA * rA * inv;      // rho (S - U) / (S - S*)
+    const double p_rA = ps * B * inv;      // p / (rho (S - U))
     const double dS = Ss - Us;
     const double w = dS * inn2;
     F[0] += S * (fac - rs);
-    for (int a = 0; a < ND; ++a) F[1 + a] += S * (fac * gfma(nh[a], w, u[s][a]) - rs * u[s][a]);
-    const double eb = Es * ir[s] + dS * gfma(Ss - nt, inn2, ps / rA);
+    #pragma unroll
+    for (int a = 0; a < ND; ++a) F[1 + a] += S * (fac * gfma(nh[a], w, us[a]) - rs * us[a]);
+    const double eb = Es * irs + dS * gfma(Ss - nt, inn2, p_rA);
     F[NV - 1] += S * gfma(fac, eb, -Es);
   }
 }
@@ -570,6 +619,7 @@ GBR_HD void body_face(const RhsArgs& A, int d, int i, int j, int k) {
 
   double nh[ND];
   double nn2 = 0.0;
+  #pragma unroll
   for (int a = 0; a < ND; ++a) {
     nh[a] = A.fh[d][a * FC + f];
     nn2 = gfma(nh[a], nh[a], nn2);
@@ -577,6 +627,7 @@ GBR_HD void body_face(const RhsArgs& A, int d, int i, int j, int k) {
   const double nt = MOV ? A.ft[d][f] : 0.0;
   const double inn = grsqrt(nn2);
   double nu[ND];
+  #pragma unroll
   for (int a = 0; a < ND; ++a) nu[a] = nh[a] * inn;
   // face state of the eigenvectors: mean of rho and p of cells i, i+1 (reading A6)
   const double rb = 0.5 * (P[pp[1]] + P[pp[2]]);
@@ -591,20 +642,27 @@ GBR_HD void body_face(const RhsArgs& A, int d, int i, int j, int k) {
   double Wd[3][NV], W1[2][NV], W2[4][NV];
   {
     double x[NV];
+    #pragma unroll
     for (int m = 0; m < 3; ++m) {
+      #pragma unroll
       for (int c = 0; c < NV; ++c) x[c] = P[c * PC + pp[m + 1]] - P[c * PC + pp[m]];
       project<ND>(nu, ra, a2, x, Wd[m]);
     }
+    #pragma unroll
     for (int m = 0; m < 2; ++m) {
+      #pragma unroll
       for (int c = 0; c < NV; ++c) x[c] = A.g1[d][c * PC + pp[m + 1]];
       project<ND>(nu, ra, a2, x, W1[m]);
     }
+    #pragma unroll
     for (int m = 0; m < 4; ++m) {
+      #pragma unroll
       for (int c = 0; c < NV; ++c) x[c] = A.g2[d][c * PC + pp[m]];
       project<ND>(nu, ra, a2, x, W2[m]);
     }
   }
   double dL[NV], dR[NV];
+  #pragma unroll
   for (int c = 0; c < NV; ++c) {
     const double fL = gfma(0.5, W1[0][c], W2[1][c] * (1.0 / 12.0));   // W^L - W_i   (Eq. legendre_polys)
     const double fR = gfma(-0.5, W1[1][c], W2[2][c] * (1.0 / 12.0));  // W^R - W_{i+1}
@@ -614,6 +672,7 @@ GBR_HD void body_face(const RhsArgs& A, int d, int i, int j, int k) {
   double PL[NV], PR[NV];
   back_project<ND>(nu, ira, ia2, dL, PL);
   back_project<ND>(nu, ira, ia2, dR, PR);
+  #pragma unroll
   for (int c = 0; c < NV; ++c) {
     PL[c] += P[c * PC + pp[1]];
     PR[c] += P[c * PC + pp[2]];
@@ -626,6 +685,7 @@ GBR_HD void body_face(const RhsArgs& A, int d, int i, int j, int k) {
     double gx[ND + 1][ND];
     double phif[ND + 1];
     const double* fu = A.fu[d];
+    #pragma unroll
     for (int v = 0; v <= ND; ++v) {
       const double* val = (v < ND) ? P + (1 + v) * PC : A.temp;
       const int gi = (v < ND) ? (1 + v) : NV;
@@ -633,6 +693,7 @@ GBR_HD void body_face(const RhsArgs& A, int d, int i, int j, int k) {
       const double gd1 = A.g1[d][gi * PC + pp[1]], gd2 = A.g1[d][gi * PC + pp[2]];
       const double phiL = gfma(0.5, gd1, val[pp[1]]);   // Eq. (AD-eqn2), beta^D = 0
       const double phiR = gfma(-0.5, gd2, val[pp[2]]);
+      #pragma unroll
       for (int e = 0; e < ND; ++e) {
         if (e == d) {
           gc[e] = gfma(ph.half_alpha_d, phiR - phiL, 0.5 * (gd1 + gd2));  // Eq. (AD-eqn1)
@@ -641,8 +702,10 @@ GBR_HD void body_face(const RhsArgs& A, int d, int i, int j, int k) {
         }
       }
       phif[v] = 0.5 * (phiL + phiR);
+      #pragma unroll
       for (int a = 0; a < ND; ++a) {  // Eq. (AD-eqn3)
         double sacc = 0.0;
+        #pragma unroll
         for (int e = 0; e < ND; ++e) sacc = gfma(fu[(e * ND + a) * FC + f], gc[e], sacc);
         gx[v][a] = sacc;
       }
@@ -655,28 +718,37 @@ GBR_HD void body_face(const RhsArgs& A, int d, int i, int j, int k) {
     const double lam = (-2.0 / 3.0) * mu;
     const double kap = mu * ph.kfac;
     double div = 0.0;
+    #pragma unroll
     for (int a = 0; a < ND; ++a) div += gx[a][a];
     double tau[ND][ND];
+    #pragma unroll
     for (int a = 0; a < ND; ++a)
+      #pragma unroll
       for (int b = 0; b < ND; ++b) {
         tau[a][b] = mu * (gx[a][b] + gx[b][a]);  // Eq. (shear-str)
         if (a == b) tau[a][b] = gfma(lam, div, tau[a][b]);
       }
     double beta[ND];
+    #pragma unroll
     for (int a = 0; a < ND; ++a) {
       double sacc = kap * gx[ND][a];
+      #pragma unroll
       for (int b = 0; b < ND; ++b) sacc = gfma(phif[b], tau[a][b], sacc);  // Eq. (thermal-work)
       beta[a] = sacc;
     }
+    #pragma unroll
     for (int a = 0; a < ND; ++a) {
       double sacc = 0.0;
+      #pragma unroll
       for (int b = 0; b < ND; ++b) sacc = gfma(nh[b], tau[a][b], sacc);
       F[1 + a] -= sacc;
     }
     double sacc = 0.0;
+    #pragma unroll
     for (int b = 0; b < ND; ++b) sacc = gfma(nh[b], beta[b], sacc);
     F[NV - 1] -= sacc;
   }
+  #pragma unroll
   for (int c = 0; c < NV; ++c) A.flux[d][c * FC + f] = F[c];
 }
 

@@ -209,7 +209,9 @@ def test_face_fluxes_match_oracle(name):
     for d in range(case["ndim"]):
         go = orc.face_flux(q, d)
         gg = s.field(gbr.GBR_FIELD_FACE_FLUX, d)
-        assert rel_state(gg, go) < 1e-12
+        # flux-vector scale: a component that nearly vanishes on these faces (e.g. the mass flux
+        # through zeta faces when w = 0) carries the round-off of the acoustic terms of the others
+        assert np.abs(gg - go).max() < 1e-12 * np.abs(go).max()
     s.close()
 
 
