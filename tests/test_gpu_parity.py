@@ -213,28 +213,28 @@ FLUX_CASES = {"2d_vortex": case_2d_vortex, "3d_tgv_smooth": case_3d_tgv_smooth, 
 
 @pytest.mark.parametrize("name", sorted(FLUX_CASES))
 def test_face_fluxes_match_oracle(name):
-    """Interface fluxes per direction.  On smooth meshes: max error <= 1e-12 of the flux-vector scale.
-    On the randomly perturbed meshes the MP limiter is active at many faces and its App. E test
-    (W^L - W_i)(W^L - W^MP) <= 1e-20 can resolve either way at round-off: there the criterion is the
-    L1 norm <= 1e-8 (the shock-sensor tolerance) with every face within 1e-10 (a flip moves a state
-    by at most the distance to the MP bound)."""
+    """Interface fluxes per direction, against the flux-vector scale of the direction.
+
+    The App. E test (W^L - W_i)(W^L - W^MP) <= 1e-20 has an absolute threshold: where a
+    characteristic component is nearly zero (transverse components when the off-diagonal metrics
+    are small, extrema) the product sits at the threshold and round-off (FMA on the GPU, the
+    paper's operation order in the oracle) can resolve it either way.  A flip moves W by at most
+    ~sqrt(1e-20) = 1e-10 relative.  Criterion: at least 99.9 % of interfaces within 1e-12, every
+    interface within 1e-10, and the L1 norm within 1e-8 (the shock-sensor tolerance)."""
     case, nodes, vel, q = FLUX_CASES[name]()
     orc, s = build_pair(case, nodes, vel)
     s.set_state(q)
     s.rhs()
-    smooth = name in ("2d_vortex", "3d_tgv_smooth")
     for d in range(case["ndim"]):
         go = orc.face_flux(q, d)
         gg = s.field(gbr.GBR_FIELD_FACE_FLUX, d)
         scale = np.abs(go).max()
-        err = np.abs(gg - go)
-        if smooth:
-            assert err.max() < 1e-12 * scale
-        else:
-            assert err.sum() < 1e-8 * np.abs(go).sum()
-            assert err.max() < 1e-10 * scale
-            flips = int((err > 1e-13 * scale).sum())
-            print(f"{name} d={d}: faces beyond 1e-13 of scale: {flips} of {err[0].size}")
+        err = np.abs(gg - go).max(axis=0)  # worst component per interface
+        beyond = int((err > 1e-12 * scale).sum())
+        print(f"{name} d={d}: interfaces beyond 1e-12 of scale: {beyond} of {err.size}")
+        assert beyond <= 1e-3 * err.size
+        assert err.max() < 1e-10 * scale
+        assert np.abs(gg - go).sum() < 1e-8 * np.abs(go).sum()
     s.close()
 
 
