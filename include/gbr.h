@@ -150,6 +150,30 @@ gbr_status gbr_get_field(gbr_ctx* c, int which, int dir, double* host_out);
  * every face-flux launch from now on; 0 stops recording.  Out pointers may be NULL. */
 gbr_status gbr_profile(gbr_ctx* c, int enable, double* face_ms, long long* face_launches, long long* launches);
 
+/* Right-hand side with no device allocation anywhere (the paper has no
+ * counterpart; this is a calling convention).  For callers that cannot call
+ * cudaMalloc or own a workspace -- code running inside another framework's
+ * memory pool or under a fixed device-memory budget, or code that must not
+ * allocate after start-up.  Computes the metrics of `nodes` (and, with
+ * node_vel and params.moving = 1, the time metrics and (1/J)_t) and writes
+ * dqdt = L(q) exactly as gbr_create + gbr_compute_metrics + gbr_set_state +
+ * gbr_rhs would.
+ *  nodes, node_vel: host arrays as for gbr_create; q, dqdt: device arrays
+ *  [nv][cells]; stream: cudaStream_t or NULL; msg/msg_len: optional
+ *  caller buffer for an error message (no allocation).
+ * All scratch lives in one file-scope device array of 64 MiB that every GPU
+ * loading this library holds until the process exits; grids whose scratch
+ * would exceed it are rejected with GBR_EINVAL before any device work.  Only
+ * periodic and zero-gradient sides are accepted (no inflow data, no sponge).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture.  Calls share the array and it keeps
+ * the last call's contents: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Asynchronous on `stream` after the host-to-device copy of the nodes. */
+gbr_status gbr_rhs_static(const gbr_params* p, const double* nodes, const double* node_vel, const double* q,
+                          double* dqdt, void* stream, char* msg, size_t msg_len);
+
 const char* gbr_last_error(const gbr_ctx* c);
 const char* gbr_last_global_error(void);
 void gbr_destroy(gbr_ctx* c);

@@ -1010,3 +1010,285 @@ void gbr_destroy(gbr_ctx* c) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Right-hand side without any allocation (gbr_rhs_static, include/gbr.h)
+//
+// For callers that cannot allocate device memory: code that runs inside
+// another framework's memory pool or under a hard device-memory budget, code
+// that must not allocate after start-up, or code that cannot own a workspace.
+// All scratch of the right-hand side (geometry, primitives, derivatives,
+// interface fluxes) lives in the file-scope device array below, which every
+// GPU that loads this library holds until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kStaticScratchBytes = (size_t)64 << 20;  // 64 MiB per device
+constexpr int kMaxStaticDevices = 64;
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+namespace {
+
+void* g_static_scratch_addr[kMaxStaticDevices];  // device address of g_static_scratch, per device
+
+gbr_status static_report(gbr_status s, const char* m, char* msg, size_t msg_len) {
+  if (msg && msg_len > 0) {
+    size_t n = std::strlen(m);
+    if (n >= msg_len) n = msg_len - 1;
+    std::memcpy(msg, m, n);
+    msg[n] = 0;
+  }
+  return s;
+}
+
+const char* static_param_error(const gbr_params* p) {
+  if (p->ndim != 2 && p->ndim != 3) return "ndim must be 2 or 3";
+  for (int d = 0; d < p->ndim; ++d) {
+    if (p->n[d] < 1) return "empty axis";
+    if (p->periodic[d] && p->n[d] < H) return "a periodic axis needs at least 6 cells";
+    if (!p->periodic[d]) {
+      if (p->ghost_nodes < E) return "a non-periodic axis needs ghost_nodes >= 10";
+      for (int s = 0; s < 2; ++s)
+        if (p->bc[d][s] != GBR_BC_ZEROGRAD) return "only periodic and zero-gradient sides are supported here";
+    }
+  }
+  if (!(p->gamma > 1.0)) return "gamma must exceed 1";
+  if (p->reynolds > 0.0 && !(p->prandtl > 0.0)) return "prandtl must be positive";
+  if (p->sutherland_s > 0.0 && !(p->t_ref > 0.0)) return "t_ref must be positive";
+  return nullptr;
+}
+
+struct RawNodes {
+  int Nn[3], off[3];
+  long long count;  // nodes per coordinate
+};
+
+RawNodes raw_nodes_of(const gbr_params* p, const Layout& L) {
+  RawNodes R;
+  R.count = 1;
+  for (int d = 0; d < 3; ++d) {
+    if (d >= L.nd) { R.Nn[d] = 1; R.off[d] = 0; continue; }
+    R.Nn[d] = p->periodic[d] ? L.n[d] + 1 : L.n[d] + 1 + 2 * p->ghost_nodes;
+    R.off[d] = p->periodic[d] ? 0 : p->ghost_nodes;
+    R.count *= R.Nn[d];
+  }
+  return R;
+}
+
+// period vectors of the periodic axes, with the closing-face check; reads the host nodes only
+const char* static_period_vectors(const gbr_params* p, const Layout& L, const RawNodes& R, const double* src,
+                                  double per[3][3]) {
+  const int nd = L.nd;
+  const long long NN = R.count;
+  auto sid = [&](int a, int s0, int s1, int s2) {
+    return (size_t)a * NN + ((size_t)s2 * R.Nn[1] + s1) * R.Nn[0] + s0;
+  };
+  double scale = 0.0;
+  for (long long m = 0; m < (long long)nd * NN; ++m) scale = std::fmax(scale, std::fabs(src[m]));
+  for (int d = 0; d < 3; ++d)
+    for (int a = 0; a < 3; ++a) per[d][a] = 0.0;
+  for (int d = 0; d < nd; ++d) {
+    if (!p->periodic[d]) continue;
+    int s0[3] = {R.off[0], R.off[1], R.off[2]}, s1[3] = {R.off[0], R.off[1], R.off[2]};
+    s1[d] = L.n[d];
+    for (int a = 0; a < nd; ++a) per[d][a] = src[sid(a, s1[0], s1[1], s1[2])] - src[sid(a, s0[0], s0[1], s0[2])];
+    for (int s2 = 0; s2 < R.Nn[2]; ++s2)
+      for (int s1i = 0; s1i < R.Nn[1]; ++s1i)
+        for (int s0i = 0; s0i < R.Nn[0]; ++s0i) {
+          int s[3] = {s0i, s1i, s2};
+          if (s[d] != 0) continue;
+          int t[3] = {s0i, s1i, s2};
+          t[d] = L.n[d];
+          for (int a = 0; a < nd; ++a) {
+            double diff = src[sid(a, t[0], t[1], t[2])] - src[sid(a, s[0], s[1], s[2])];
+            if (std::fabs(diff - per[d][a]) > 1e-12 * (scale + 1.0))
+              return "periodic axis is not closed by a constant period vector";
+          }
+        }
+  }
+  return nullptr;
+}
+
+struct ExtendArgs {
+  Layout L;
+  RawNodes R;
+  int periodic[3];
+  double per[3][3];
+  int shift;  // 1: coordinates (add period vectors), 0: velocities
+  const double* raw;
+  double* ext;
+};
+
+// extended node box [-E, n+E]: unwrapped periodic images / supplied ghost layers
+__global__ void k_extend_nodes(ExtendArgs X, Box b) {
+  BOX_THREAD(b);
+  const Layout& L = X.L;
+  const int m[3] = {i, j, k};
+  int s[3], wraps[3] = {0, 0, 0};
+  for (int d = 0; d < 3; ++d) {
+    if (d >= L.nd) { s[d] = 0; continue; }
+    if (X.periodic[d]) {
+      const int n = L.n[d];
+      const int base = ((m[d] % n) + n) % n;
+      wraps[d] = (m[d] - base) / n;
+      s[d] = base;
+    } else {
+      s[d] = m[d] + X.R.off[d];
+    }
+  }
+  const long long id = nidx(L, i, j, k);
+  const long long src = ((long long)s[2] * X.R.Nn[1] + s[1]) * X.R.Nn[0] + s[0];
+  for (int a = 0; a < L.nd; ++a) {
+    double v = X.raw[a * X.R.count + src];
+    if (X.shift)
+      for (int d = 0; d < L.nd; ++d) v += wraps[d] * X.per[d][a];
+    X.ext[a * L.ncount + id] = v;
+  }
+}
+
+template <int ND, bool VISC, bool MOV>
+void static_face_launches(const RhsArgs& A, const RhsBoxes& B, cudaStream_t st) {
+  for (int d = 0; d < ND; ++d)
+    k_face<ND, VISC, MOV><<<grid_of(B.faces[d], kFaceBlock), kFaceBlock, 0, st>>>(A, d, B.faces[d]);
+}
+
+// the launch sequence of one right-hand side (geometry first), errors as cudaError_t only
+template <int ND>
+cudaError_t static_rhs_launches(gbr_ctx& c, const double* q, double* dqdt, cudaStream_t st) {
+  const Layout& L = c.L;
+  const GeoArgs G = geo_args(&c);
+  const GeoBoxes GB = geo_boxes(L);
+  k_centroid<<<grid_of(GB.ext, kBlock), kBlock, 0, st>>>(G, GB.ext);
+  unsigned gmax = 0;
+  for (int d = 0; d < ND; ++d) gmax = std::max(gmax, grid_of(GB.coordd[d], kBlock));
+  k_coordd<<<dim3(gmax, ND), kBlock, 0, st>>>(G, GB.coordd[0], GB.coordd[1], GB.coordd[2]);
+  k_metrics<<<grid_of(GB.metrics, kBlock), kBlock, 0, st>>>(G, GB.metrics);
+  gmax = 0;
+  for (int d = 0; d < ND; ++d) gmax = std::max(gmax, grid_of(GB.faces[d], kBlock));
+  k_face_metrics<<<dim3(gmax, ND), kBlock, 0, st>>>(G, GB.faces[0], GB.faces[1], GB.faces[2]);
+  k_gcl<<<grid_of(GB.inner, kBlock), kBlock, 0, st>>>(G, GB.inner);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+
+  const RhsArgs A = rhs_args(&c, q);
+  const RhsBoxes B = rhs_boxes(L);
+  k_prim<ND><<<grid_of(B.inner, kBlock), kBlock, 0, st>>>(A, B.inner);
+  for (int d = 0; d < ND; ++d) k_halo<ND><<<grid_of(B.halo[d], kBlock), kBlock, 0, st>>>(A, d, B.halo[d]);
+  unsigned g1 = 0, g2 = 0;
+  for (int d = 0; d < ND; ++d) {
+    g1 = std::max(g1, grid_of(B.grad1[d], kBlock));
+    g2 = std::max(g2, grid_of(B.grad2[d], kBlock));
+  }
+  k_grad1<ND><<<dim3(g1, ND), kBlock, 0, st>>>(A, B.grad1[0], B.grad1[1], B.grad1[2]);
+  k_grad2<ND><<<dim3(g2, ND), kBlock, 0, st>>>(A, B.grad2[0], B.grad2[1], B.grad2[2]);
+  if (c.visc) {
+    if (c.mov) static_face_launches<ND, true, true>(A, B, st);
+    else static_face_launches<ND, true, false>(A, B, st);
+  } else {
+    if (c.mov) static_face_launches<ND, false, true>(A, B, st);
+    else static_face_launches<ND, false, false>(A, B, st);
+  }
+  UpdArgs U;
+  U.L = L;
+  for (int d = 0; d < 3; ++d) U.flux[d] = c.flux[d];
+  U.qs = q;
+  U.q0 = q;
+  U.out = dqdt;
+  U.jac = c.jac;
+  U.gcl = c.gcl;
+  U.sigma = nullptr;
+  for (int v = 0; v < 5; ++v) U.qamb[v] = 0.0;
+  U.dt = c.scal + S_DT;
+  U.ca = 0.0;
+  U.cb = 0.0;
+  U.cc = 1.0;
+  U.mode = 0;
+  if (c.mov) k_update<ND, true><<<grid_of(B.inner, kBlock), kBlock, 0, st>>>(U, B.inner, c.err);
+  else k_update<ND, false><<<grid_of(B.inner, kBlock), kBlock, 0, st>>>(U, B.inner, c.err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" gbr_status gbr_rhs_static(const gbr_params* p, const double* nodes, const double* node_vel,
+                                     const double* q, double* dqdt, void* stream, char* msg, size_t msg_len) {
+  if (!p || !nodes || !q || !dqdt) return static_report(GBR_EINVAL, "null argument", msg, msg_len);
+  if (const char* why = static_param_error(p)) return static_report(GBR_EINVAL, why, msg, msg_len);
+  if (node_vel && !p->moving) return static_report(GBR_EINVAL, "node velocities need params.moving = 1", msg, msg_len);
+  const Layout L = layout_of(p);
+  const Plan P = plan_of(p, L);
+  const RawNodes R = raw_nodes_of(p, L);
+  const size_t raw_bytes = (((size_t)L.nd * R.count * sizeof(double)) + 255) & ~(size_t)255;
+  const size_t need = P.total + raw_bytes * (node_vel ? 2 : 1);
+  if (need > kStaticScratchBytes)
+    return static_report(GBR_EINVAL, "grid too large for the 64 MiB static scratch of gbr_rhs_static", msg, msg_len);
+  double per[3][3];
+  if (const char* why = static_period_vectors(p, L, R, nodes, per)) return static_report(GBR_EINVAL, why, msg, msg_len);
+
+  // set-up, once per device, with that device current: the device address of the static array
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return static_report(GBR_ECUDA, "cudaGetDevice failed", msg, msg_len);
+  if (dev < 0 || dev >= kMaxStaticDevices) return static_report(GBR_EINVAL, "device index out of range", msg, msg_len);
+  if (!g_static_scratch_addr[dev]) {
+    void* addr = nullptr;
+    if (cudaGetSymbolAddress(&addr, g_static_scratch) != cudaSuccess || !addr)
+      return static_report(GBR_ECUDA, "cudaGetSymbolAddress of the static scratch failed", msg, msg_len);
+    g_static_scratch_addr[dev] = addr;
+  }
+
+  gbr_ctx c;  // host-side view of the scratch; holds no heap memory on this path
+  c.p = *p;
+  if (p->ndim == 2) c.p.n[2] = 1;
+  c.L = L;
+  c.ph = phys_of(p);
+  c.stream = (cudaStream_t)stream;
+  c.ws = (char*)g_static_scratch_addr[dev];
+  c.ws_bytes = kStaticScratchBytes;
+  c.plan = P;
+  c.visc = p->reynolds > 0.0;
+  c.mov = node_vel != nullptr;
+  c.have_sponge = false;
+  c.have_motion = false;
+  c.metrics_ready = false;
+  c.launches = 0;
+  c.prof = false;
+  c.ev_used = 0;
+  for (int v = 0; v < 5; ++v) c.qamb[v] = 0.0;
+  carve(&c);
+  if (!c.mov) {  // a static mesh leaves the moving-mesh slots out of the plan
+    c.nvel = nullptr;
+    c.vc = nullptr;
+  }
+  cudaStream_t st = c.stream;
+  double* raw = (double*)(c.ws + P.total);
+  double* rawv = (double*)(c.ws + P.total + raw_bytes);
+  const size_t copy_bytes = (size_t)L.nd * R.count * sizeof(double);
+  // the error flag and the scalars must start at zero; every other slot is rewritten before it is read
+  if (cudaMemsetAsync(c.err, 0, sizeof(int) * 4, st) != cudaSuccess ||
+      cudaMemsetAsync(c.scal, 0, sizeof(double) * S_NSCAL, st) != cudaSuccess ||
+      cudaMemcpyAsync(raw, nodes, copy_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      (c.mov && cudaMemcpyAsync(rawv, node_vel, copy_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess))
+    return static_report(GBR_ECUDA, "copy to the static scratch failed", msg, msg_len);
+  ExtendArgs X;
+  X.L = L;
+  X.R = R;
+  for (int d = 0; d < 3; ++d) {
+    X.periodic[d] = (d < L.nd) ? p->periodic[d] : 1;
+    for (int a = 0; a < 3; ++a) X.per[d][a] = per[d][a];
+  }
+  const Box bn = geo_boxes(L).nodes;
+  X.shift = 1;
+  X.raw = raw;
+  X.ext = c.nodes;
+  k_extend_nodes<<<grid_of(bn, kBlock), kBlock, 0, st>>>(X, bn);
+  if (c.mov) {
+    X.shift = 0;
+    X.raw = rawv;
+    X.ext = c.nvel;
+    k_extend_nodes<<<grid_of(bn, kBlock), kBlock, 0, st>>>(X, bn);
+  }
+  cudaError_t e = L.nd == 3 ? static_rhs_launches<3>(c, q, dqdt, st) : static_rhs_launches<2>(c, q, dqdt, st);
+  if (e != cudaSuccess) return static_report(GBR_ECUDA, cudaGetErrorString(e), msg, msg_len);
+  return GBR_OK;
+}

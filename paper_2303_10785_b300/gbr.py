@@ -86,6 +86,8 @@ def lib():
     L.gbr_get_field.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _P]
     L.gbr_profile.argtypes = [_vp, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     L.gbr_profile.restype = ctypes.c_int
+    L.gbr_rhs_static.argtypes = [ctypes.POINTER(gbr_params), _P, _P, _vp, _vp, _vp, ctypes.c_char_p, ctypes.c_size_t]
+    L.gbr_rhs_static.restype = ctypes.c_int
     L.gbr_last_error.argtypes = [_vp]
     L.gbr_last_error.restype = ctypes.c_char_p
     L.gbr_last_global_error.restype = ctypes.c_char_p
@@ -102,8 +104,8 @@ def exported_symbols():
     """Names declared in include/gbr.h that the library must export."""
     return ["gbr_workspace_bytes", "gbr_create", "gbr_compute_metrics", "gbr_move_mesh", "gbr_set_motion",
             "gbr_set_state", "gbr_get_state", "gbr_set_inflow", "gbr_set_sponge", "gbr_rhs", "gbr_compute_dt",
-            "gbr_rk_step", "gbr_sync", "gbr_get_time", "gbr_get_field", "gbr_profile", "gbr_last_error",
-            "gbr_last_global_error", "gbr_destroy"]
+            "gbr_rk_step", "gbr_sync", "gbr_get_time", "gbr_get_field", "gbr_profile", "gbr_rhs_static",
+            "gbr_last_error", "gbr_last_global_error", "gbr_destroy"]
 
 
 def make_params(case):
