@@ -25,8 +25,16 @@ using namespace gbr;
 
 namespace {
 
+// Launch shape of the interface kernel (tuning knobs, set at compile time).
+#ifndef GBR_FACE_BLOCK
+#define GBR_FACE_BLOCK 128
+#endif
+#ifndef GBR_FACE_MIN_BLOCKS
+#define GBR_FACE_MIN_BLOCKS 1
+#endif
+
 constexpr int kBlock = 256;
-constexpr int kFaceBlock = 128;
+constexpr int kFaceBlock = GBR_FACE_BLOCK;
 
 enum { S_DT = 0, S_T = 1, S_DTMIN = 2, S_NSCAL = 8 };
 
@@ -107,7 +115,7 @@ __global__ void k_grad2(RhsArgs A, Box b0, Box b1, Box b2) {
 }
 
 template <int ND, bool VISC, bool MOV>
-__global__ void __launch_bounds__(kFaceBlock) k_face(RhsArgs A, int d, Box b) {
+__global__ void __launch_bounds__(GBR_FACE_BLOCK, GBR_FACE_MIN_BLOCKS) k_face(RhsArgs A, int d, Box b) {
   BOX_THREAD(b);
   body_face<ND, VISC, MOV>(A, d, i, j, k);
 }

@@ -146,10 +146,16 @@ GBR_HD double gfma(double a, double b, double c) {
 // B300 the FP64 pipe issues 2 instructions/clk/SM while the integer pipe issues
 // 64, so the limiter's and the Riemann solver's branch logic is kept off the
 // FP64 pipe.  The key below is monotone in the value and maps +0 and -0 to the
-// same key, so key(a) < key(b) is exactly a < b for every non-NaN pair.
+// same key, so key(a) < key(b) is exactly a < b for every non-NaN pair.  On the
+// device the double -> bits move is an opaque register move: a plain
+// reinterpret lets the compiler fold "bits & mask" or a select of reinterpreted
+// values back into FP64 |x| / negate / select instructions, which run on the
+// FP64 pipe again.
 GBR_HD long long dbits(double x) {
 #ifdef __CUDA_ARCH__
-  return __double_as_longlong(x);
+  long long r;
+  asm("mov.b64 %0, %1;" : "=l"(r) : "d"(x));
+  return r;
 #else
   long long r;
   std::memcpy(&r, &x, sizeof r);
@@ -167,30 +173,32 @@ GBR_HD double bitsd(long long b) {
 }
 constexpr long long kMag = 0x7fffffffffffffffLL;
 constexpr long long kSign = (long long)0x8000000000000000ULL;
-GBR_HD long long okey(double x) {
-  const long long b = dbits(x);
-  return b < 0 ? -(b & kMag) : b;
+// order key of a bit pattern
+GBR_HD long long bkey(long long b) { return b < 0 ? -(b & kMag) : b; }
+GBR_HD long long okey(double x) { return bkey(dbits(x)); }
+// min / max of two bit patterns by value, exactly like a < b ? a : b and
+// a > b ? a : b on the doubles (a tie returns the second argument)
+GBR_HD long long bmin(long long a, long long b) { return bkey(a) < bkey(b) ? a : b; }
+GBR_HD long long bmax(long long a, long long b) { return bkey(b) < bkey(a) ? a : b; }
+// App. E: minmod(a, b) = 1/2 (sign a + sign b) min(|a|, |b|), i.e. the smaller-magnitude
+// argument when both have the same sign, else a zero; when one argument is zero
+// the product with the sign sum keeps that sum's sign (-0 for a negative sum).
+GBR_HD long long bminmod(long long a, long long b) {
+  const long long ma = a & kMag, mb = b & kMag;
+  const long long m = ma < mb ? ma : mb;  // |a| < |b| ? |a| : |b|
+  const int sa = a > 0 ? 1 : ((a < 0 && ma != 0) ? -1 : 0);
+  const int sb = b > 0 ? 1 : ((b < 0 && mb != 0) ? -1 : 0);
+  const int sum = sa + sb;
+  return sum == 2 ? m : (sum == -2 ? (m | kSign) : (sum < 0 ? kSign : 0LL));
 }
 GBR_HD bool dlt(double a, double b) { return okey(a) < okey(b); }
 GBR_HD bool dle(double a, double b) { return okey(a) <= okey(b); }
 GBR_HD bool is_pos(double x) { return dbits(x) > 0; }                       // x > 0
 GBR_HD bool is_neg(double x) { return (dbits(x) & kMag) != 0 && dbits(x) < 0; }  // x < 0
-GBR_HD double gmin(double a, double b) { return dlt(a, b) ? a : b; }  // same as a < b ? a : b
-GBR_HD double gmax(double a, double b) { return dlt(b, a) ? a : b; }  // same as a > b ? a : b
+GBR_HD double gmin(double a, double b) { return bitsd(bmin(dbits(a), dbits(b))); }  // a < b ? a : b
+GBR_HD double gmax(double a, double b) { return bitsd(bmax(dbits(a), dbits(b))); }  // a > b ? a : b
 GBR_HD double gabs(double x) { return bitsd(dbits(x) & kMag); }
-// App. E: minmod(a, b) = 1/2 (sign a + sign b) min(|a|, |b|), i.e. the smaller-magnitude
-// argument when both have the same sign, else 0.
-GBR_HD double minmod(double a, double b) {
-  const long long ba = dbits(a), bb = dbits(b);
-  const long long ma = ba & kMag, mb = bb & kMag;
-  const long long m = ma < mb ? ma : mb;  // |a| < |b| ? |a| : |b|
-  const int sa = ba > 0 ? 1 : ((ba < 0 && ma != 0) ? -1 : 0);
-  const int sb = bb > 0 ? 1 : ((bb < 0 && mb != 0) ? -1 : 0);
-  const int sum = sa + sb;
-  if (sum == 2) return bitsd(m);
-  if (sum == -2) return bitsd(m | kSign);
-  return sum < 0 ? -0.0 : 0.0;  // one argument is zero: the product with the sign sum keeps its sign
-}
+GBR_HD double minmod(double a, double b) { return bitsd(bminmod(dbits(a), dbits(b))); }
 
 // Composite stencils of the MEG6 interface operators (Sec. 6): the interface
 // value I(f)_{i+1/2} = avg of the van Leer left/right states built from E6
@@ -531,18 +539,31 @@ GBR_HD void back_project(const double* nu, double ira, double ia2, const double*
 // App. E limiter written relative to the base cell value W_base:
 //   f  = W_face - W_base,  dm = W_base - W_up,  dp = W_down - W_base,
 //   du, db, dd = curvatures d of the up, base and down cells.
-// Returns the limited W_face - W_base.
-GBR_HD double mp_relative(double f, double dm, double dp, double du, double db, double dd, const Phys& ph) {
-  const double mmp = minmod(dp, ph.mp_beta * dm);  // W^MP - W_base
-  if (dle(f * (f - mmp), ph.mp_eps)) return f;
-  const double dmp = minmod(db, dd);  // d^M_{i+1/2}
-  const double dmm = minmod(du, db);  // d^M_{i-1/2}
-  const double md = 0.5 * dp - 0.5 * dmp;
-  const double ul = ph.mp_alpha * dm;
-  const double lc = gfma(4.0 / 3.0, dmm, 0.5 * dm);
-  const double lo = gmax(gmin(gmin(0.0, dp), md), gmin(gmin(0.0, ul), lc));
-  const double hi = gmin(gmax(gmax(0.0, dp), md), gmax(gmax(0.0, ul), lc));
-  return f + minmod(lo - f, hi - f);
+// mp_keep is the test (W^L - W_base)(W^L - W^MP) <= eps that leaves the state
+// unchanged; mp_bound returns the limited W_face - W_base when it fails.  The
+// products and sums are FP64; every comparison, min, max, minmod and the
+// median work on the bit patterns (integer pipe) and select one of their
+// arguments exactly.
+GBR_HD bool mp_keep(double f, double dm, double dp, const Phys& ph) {
+  const long long bf = dbits(f);
+  const long long bmp = bminmod(dbits(dp), dbits(ph.mp_beta * dm));  // W^MP - W_base
+  // exactly non-positive product when f lies between 0 and W^MP - W_base
+  const long long kf = bkey(bf), km = bkey(bmp), ke = okey(ph.mp_eps);
+  const bool between = (km >= 0) ? (kf >= 0 && kf <= km) : (kf <= 0 && kf >= km);
+  return (between && ke >= 0) || okey(f * (f - bitsd(bmp))) <= ke;
+}
+GBR_HD double mp_bound(double f, double dm, double dp, double du, double db, double dd, const Phys& ph) {
+  const double dmp = bitsd(bminmod(dbits(db), dbits(dd)));  // d^M_{i+1/2}
+  const double dmm = bitsd(bminmod(dbits(du), dbits(db)));  // d^M_{i-1/2}
+  const long long bdp = dbits(dp), bf = dbits(f);
+  const long long md = dbits(0.5 * (dp - dmp));                // W^MD - W_base
+  const long long ul = dbits(ph.mp_alpha * dm);                // W^UL - W_base
+  const long long lc = dbits(gfma(4.0 / 3.0, dmm, 0.5 * dm));  // W^LC - W_base
+  // W^min, W^max relative to W_base (W_base itself maps to 0)
+  const long long lo = bmax(bmin(bmin(0LL, bdp), md), bmin(bmin(0LL, ul), lc));
+  const long long hi = bmin(bmax(bmax(0LL, bdp), md), bmax(bmax(0LL, ul), lc));
+  // W^L + minmod(W^min - W^L, W^max - W^L) is the median of (W^L, W^min, W^max)
+  return bitsd(bmax(bmin(bf, lo), bmin(bmax(bf, lo), hi)));
 }
 
 // Sec. 5.1.1 HLLC with grid motion; P = [rho, u.., p]
@@ -554,7 +575,8 @@ GBR_HD void hllc(const double* PL, const double* PR, const double* nh, double nn
   const double inn2 = inn * inn;
   // left and right states (kept in scalars: no runtime-indexed arrays)
   const double rl = PL[0], rr = PR[0];
-  const double irl = 1.0 / rl, irr = 1.0 / rr;
+  const double irlr = 1.0 / (rl * rr);  // one reciprocal for both densities
+  const double irl = rr * irlr, irr = rl * irlr;
   const double pl = PL[NV - 1], pr = PR[NV - 1];
   double q2l = 0.0, q2r = 0.0, Ul = nt, Ur = nt;
   #pragma unroll
@@ -632,42 +654,62 @@ GBR_HD void body_face(const RhsArgs& A, int d, int i, int j, int k) {
   // face state of the eigenvectors: mean of rho and p of cells i, i+1 (reading A6)
   const double rb = 0.5 * (P[pp[1]] + P[pp[2]]);
   const double pb = 0.5 * (P[(NV - 1) * PC + pp[1]] + P[(NV - 1) * PC + pp[2]]);
-  const double irb = 1.0 / rb;
-  const double a2 = ph.gamma * pb * irb;
-  const double ia = grsqrt(a2);
-  const double ra = rb * (a2 * ia);
-  const double ira = irb * ia;
+  // a = sqrt(gamma p / rho): with t = 1/sqrt(gamma p rho), rho a = gamma p rho t, 1/(rho a) = t,
+  // a = gamma p t and 1/a = rho t -- one reciprocal square root, no division
+  const double gp = ph.gamma * pb;
+  const double t = grsqrt(gp * rb);
+  const double ira = t;
+  const double ra = gp * rb * t;
+  const double a_ = gp * t;
+  const double a2 = a_ * a_;
+  const double ia = rb * t;
   const double ia2 = ia * ia;
 
-  double Wd[3][NV], W1[2][NV], W2[4][NV];
+  // projected differences dW = R^-1 (P_{m+1} - P_m) of the four cells i-1 .. i+2
+  double Wd[3][NV];
+  #pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    double x[NV];
+    #pragma unroll
+    for (int c = 0; c < NV; ++c) x[c] = P[c * PC + pp[m + 1]] - P[c * PC + pp[m]];
+    project<ND>(nu, ra, a2, x, Wd[m]);
+  }
+  // Eq. (legendre_polys) unlimited states relative to the base cells, projected
+  // after combining: W^L - W_i = R^-1 (f'_i / 2 + f''_i / 12),
+  // W^R - W_{i+1} = R^-1 (-f'_{i+1} / 2 + f''_{i+1} / 12)
+  double dL[NV], dR[NV];
   {
     double x[NV];
     #pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      #pragma unroll
-      for (int c = 0; c < NV; ++c) x[c] = P[c * PC + pp[m + 1]] - P[c * PC + pp[m]];
-      project<ND>(nu, ra, a2, x, Wd[m]);
-    }
+    for (int c = 0; c < NV; ++c) x[c] = gfma(0.5, A.g1[d][c * PC + pp[1]], A.g2[d][c * PC + pp[1]] * (1.0 / 12.0));
+    project<ND>(nu, ra, a2, x, dL);
     #pragma unroll
-    for (int m = 0; m < 2; ++m) {
-      #pragma unroll
-      for (int c = 0; c < NV; ++c) x[c] = A.g1[d][c * PC + pp[m + 1]];
-      project<ND>(nu, ra, a2, x, W1[m]);
-    }
+    for (int c = 0; c < NV; ++c) x[c] = gfma(-0.5, A.g1[d][c * PC + pp[2]], A.g2[d][c * PC + pp[2]] * (1.0 / 12.0));
+    project<ND>(nu, ra, a2, x, dR);
+  }
+  // App. E: the curvatures are projected only where some characteristic field
+  // fails the test (in smooth flow whole warps skip this block)
+  unsigned limit = 0;
+  #pragma unroll
+  for (int c = 0; c < NV; ++c) {
+    limit |= mp_keep(dL[c], Wd[0][c], Wd[1][c], ph) ? 0u : (1u << c);
+    limit |= mp_keep(dR[c], -Wd[2][c], -Wd[1][c], ph) ? 0u : (1u << (NV + c));
+  }
+  if (limit) {
+    double W2[4][NV];
     #pragma unroll
     for (int m = 0; m < 4; ++m) {
+      double x[NV];
       #pragma unroll
       for (int c = 0; c < NV; ++c) x[c] = A.g2[d][c * PC + pp[m]];
       project<ND>(nu, ra, a2, x, W2[m]);
     }
-  }
-  double dL[NV], dR[NV];
-  #pragma unroll
-  for (int c = 0; c < NV; ++c) {
-    const double fL = gfma(0.5, W1[0][c], W2[1][c] * (1.0 / 12.0));   // W^L - W_i   (Eq. legendre_polys)
-    const double fR = gfma(-0.5, W1[1][c], W2[2][c] * (1.0 / 12.0));  // W^R - W_{i+1}
-    dL[c] = mp_relative(fL, Wd[0][c], Wd[1][c], W2[0][c], W2[1][c], W2[2][c], ph);
-    dR[c] = mp_relative(fR, -Wd[2][c], -Wd[1][c], W2[3][c], W2[2][c], W2[1][c], ph);
+    #pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      if (limit & (1u << c)) dL[c] = mp_bound(dL[c], Wd[0][c], Wd[1][c], W2[0][c], W2[1][c], W2[2][c], ph);
+      if (limit & (1u << (NV + c)))
+        dR[c] = mp_bound(dR[c], -Wd[2][c], -Wd[1][c], W2[3][c], W2[2][c], W2[1][c], ph);
+    }
   }
   double PL[NV], PR[NV];
   back_project<ND>(nu, ira, ia2, dL, PL);
