@@ -1,14 +1,22 @@
 """Benchmark: cell-RK-stage updates/s of the FP64 MEG6 + HLLC + alpha-damping
 right-hand side with SSP-RK3 on one B300, plus the roofline of the dominant
-kernel (the interface-flux kernel) and the CPU oracle as the baseline.
+kernel (the interface-flux kernel) and of the whole step, and the CPU oracle as
+the baseline.
 
-Workload: 3D viscous Taylor-Green vortex, Re = 1600, M = 0.1, Pr = 0.71, on a
-128^3 periodic [0, 2 pi]^3 mesh with a 0.1 h sinusoidal node perturbation, CFL
-0.2 (dt computed on the device every step).  A step is one full SSP-RK3 step
-(three right-hand sides, time step, stage combinations); the working set
-(~3 GB) is far larger than L2, so no flush is needed between steps.
+Workloads (--workload):
+  tgv (default)  3D viscous Taylor-Green vortex, Re = 1600, M = 0.1, Pr = 0.71,
+                 on a 128^3 periodic [0, 2 pi]^3 mesh with a 0.1 h sinusoidal
+                 node perturbation, CFL 0.2 (dt computed on the device every step).
+  jet            480 x 170 x 170 (13.9 M cells) jet-like box: uniform in x on
+                 [0, 20 D], stretched (ratio 1.02) away from the axis, quiescent
+                 ambient, sonic top-hat inflow with a 1 % random velocity
+                 perturbation drawn per step (counter-based hash of seed, step,
+                 cell), Sutherland viscosity, Re_D = 1e5, sponge, fixed dt = 2e-3.
+A step is one full SSP-RK3 step (three right-hand sides, stage combinations and,
+for tgv, the time step); the working sets (~3 GB, ~20 GB) are far larger than
+L2, so no flush is needed between steps.
 
-python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload tgv|jet]
 Under torchrun (N > 1) each rank advances its own copy of the workload (the
 jobs are independent: replicas, weak scaling); rank 0 prints one JSON line.
 """
@@ -28,12 +36,16 @@ sys.path.insert(0, ROOT)
 
 N_CELLS_EDGE = 128
 CFL = 0.2
-WORKLOAD = "tgv3d_viscous_128^3_perturbed"
+JET_DT = 2e-3
+JET_SEED = 2303
 METRIC = "cell-RK-stage updates/s"
 # FP64 peak used as the roofline denominator of this ALU-bound path: 148 SMs x
 # 2 DFMA/clk/SM x 2 flop x 2.032 GHz = 1.20 TFLOP/s nominal at the maximum SM
 # clock (the pool's FP64 figure is 1.25 TFLOP/s; derivation in the design doc).
 FP64_PEAK_TFLOPS = 1.25
+HBM_PEAK_GBS = 6491.5
+# minimum HBM traffic of a 3D FP64 cell-stage: state and cell geometry, stage average
+BYTES_PER_CELL_STAGE_3D = 186.7
 
 
 def load_flops():
@@ -41,15 +53,69 @@ def load_flops():
         return json.load(f)
 
 
-def workload():
-    from paper_2303_10785_b300 import inputs as I
+class Workload:
+    """Inputs and per-step driving of one benchmark workload."""
 
-    n = N_CELLS_EDGE
-    case = I.case_params(3, (n, n, n), reynolds=1600.0, prandtl=0.71)
-    nodes = I.nodes_tgv_3d(n, 0.1)
-    xc = I.centroids(nodes, (n, n, n), (1, 1, 1))
-    q = I.prim_to_cons(I.tgv_prim(*xc, mach=0.1), case["gamma"])
-    return case, nodes, q
+    def __init__(self, kind, edge=N_CELLS_EDGE):
+        from paper_2303_10785_b300 import inputs as I
+
+        self.kind = kind
+        self.inflow = self.sponge = None
+        if kind == "tgv":
+            n = (edge,) * 3
+            self.case = I.case_params(3, n, reynolds=1600.0, prandtl=0.71)
+            self.nodes = I.nodes_tgv_3d(edge, 0.1)
+            xc = I.centroids(self.nodes, n, (1, 1, 1))
+            self.q = I.prim_to_cons(I.tgv_prim(*xc, mach=0.1), self.case["gamma"])
+            self.name = f"tgv3d_viscous_{edge}^3_perturbed"
+            self.flops_key = "tgv3d_viscous"
+            self.config = {"cells": edge ** 3, "cfl": CFL, "reynolds": 1600.0, "mach": 0.1}
+            self.ws_note = "working set ~3 GB >> 126 MB L2, no flush"
+        else:
+            n = (480, 170, 170)
+            self.case, self.nodes, self.q, self.inflow, sigma, qamb = I.jet_case(n)
+            self.sponge = (sigma, qamb)
+            self.name = "jet3d_viscous_480x170x170_stretched"
+            self.flops_key = "jet3d_viscous"
+            self.config = {"cells": n[0] * n[1] * n[2], "dt": JET_DT, "reynolds_d": 1e5, "sutherland": True,
+                           "inflow_perturbation": "1 % velocity, SplitMix64(seed, step, cell, component)"}
+            self.ws_note = "working set ~20 GB >> 126 MB L2, no flush"
+        self.n = n
+        self.cells = n[0] * n[1] * n[2]
+        self.faces_per_rhs = sum((n[0] + (d == 0)) * (n[1] + (d == 1)) * (n[2] + (d == 2)) for d in range(3))
+        self.planes = None
+
+    def attach(self, solver, n_steps):
+        """Boundary data on the solver; for the jet, the inflow planes of n_steps steps on the device."""
+        if self.inflow is None:
+            return
+        import torch
+
+        from paper_2303_10785_b300 import inputs as I
+
+        solver.set_sponge(*self.sponge)
+        planes = np.stack([I.jet_inflow_step(self.inflow, JET_SEED, s) for s in range(n_steps)])
+        self.planes = torch.from_numpy(planes).to(solver.device)
+        torch.cuda.synchronize(solver.device)
+
+    def step(self, solver, i):
+        """One SSP-RK3 step number i (all work queued on the solver's stream)."""
+        if self.planes is not None:
+            solver.set_inflow(self.planes[i % self.planes.shape[0]])
+            solver.rk_step(-JET_DT)
+        else:
+            solver.rk_step(CFL)
+
+    def oracle_sample(self):
+        """A bounded sample of the workload for the CPU oracle: (case, nodes, q, inflow, sponge, cells, text)."""
+        from paper_2303_10785_b300 import inputs as I
+
+        if self.kind == "tgv":
+            return self.case, self.nodes, self.q, None, None, self.cells, f"the full {self.n[0]}^3 workload"
+        m = (40, 170, 170)
+        case, nodes, q, inflow, sigma, qamb = I.jet_case(m, Lx=20.0 * m[0] / 480)
+        return (case, nodes, q, I.jet_inflow_step(inflow, JET_SEED, 0), (sigma, qamb), m[0] * m[1] * m[2],
+                "the first 40 of the 480 x-cells of the jet grid (full 170 x 170 cross-section, inflow, sponge)")
 
 
 class ClockSampler:
@@ -112,51 +178,62 @@ def _oracle_stage(orc, q):
     return q + 1e-3 * orc.rhs(q)
 
 
-def cpu_baseline(samples=1):
-    """The oracle as it stands on the host cores: right-hand sides of the full 128^3 workload."""
+def _oracle_for(wl):
     import oracle as O
 
-    case, nodes, q = workload()
+    case, nodes, q, inflow, sponge, cells, text = wl.oracle_sample()
     orc = O.Oracle(case, nodes)
+    if inflow is not None:
+        orc.set_inflow(inflow)
+        orc.set_sponge(*sponge)
+    return orc, q, cells, text
+
+
+def cpu_baseline(wl, seconds=10.0, max_samples=40):
+    """The oracle as it stands on the host cores: RK stages of a bounded sample of the workload,
+    repeated until about `seconds` of CPU work (at least two)."""
+    import oracle as O
+
+    orc, q, cells, text = _oracle_for(wl)
+    samples = 0
     t0 = time.perf_counter()
-    for _ in range(samples):
+    while samples < 2 or (time.perf_counter() - t0 < seconds and samples < max_samples):
         _oracle_stage(orc, q)
+        samples += 1
     el = time.perf_counter() - t0
-    cells = N_CELLS_EDGE ** 3
     return {"value": cells * samples / el, "unit": METRIC, "cores": O.threads(), "kind": "oracle",
-            "sample": f"{samples} RK stage(s) (right-hand side + stage combination) of the full 128^3 "
-                      f"workload, geometry set-up excluded, {el:.1f} s"}
+            "sample": f"{samples} RK stage(s) (right-hand side + stage combination) of {text}, "
+                      f"geometry set-up excluded, {el:.1f} s"}
 
 
-def run_reference(args):
-    """Reference arm: the CPU oracle as it stands, one RK stage of the full workload per step."""
+def run_reference(args, wl):
+    """Reference arm: the CPU oracle as it stands, one RK stage of the workload's sample per step."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
     import oracle as O
 
-    case, nodes, q = workload()
-    orc = O.Oracle(case, nodes)
+    orc, q, cells, text = _oracle_for(wl)
     for _ in range(args.warmup):
         _oracle_stage(orc, q)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         _oracle_stage(orc, q)
     el = time.perf_counter() - t0
-    value = N_CELLS_EDGE ** 3 * args.steps / el
-    sample = f"{args.steps} RK stage(s) of the full 128^3 workload on the host cores (one stage per step)"
+    value = cells * args.steps / el
+    sample = f"{args.steps} RK stage(s) of {text} on the host cores (one stage per step)"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": N_CELLS_EDGE ** 3, "cfl": CFL, "reynolds": 1600.0},
+        "config": dict({"workload": wl.name}, **wl.config),
         "cpu_baseline": {"value": value, "unit": METRIC, "cores": O.threads(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def run_gpu(args):
+def run_gpu(args, wl):
     import torch
 
     from paper_2303_10785_b300 import gbr
@@ -168,10 +245,11 @@ def run_gpu(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    case, nodes, q = workload()
-    solver = gbr.Solver(case, nodes, device=dev)
+    solver = gbr.Solver(wl.case, wl.nodes, device=dev)
     stream = solver.stream
-    cells = N_CELLS_EDGE ** 3
+    cells = wl.cells
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 10))
+    wl.attach(solver, args.warmup + args.steps + 2 + e2e_steps)
 
     def barrier():
         if world > 1:
@@ -180,9 +258,11 @@ def run_gpu(args):
             dist.barrier()
 
     # ---- device-resident throughput
-    solver.set_state(q)
+    solver.set_state(wl.q)
+    step = 0
     for _ in range(args.warmup):
-        solver.rk_step(CFL)
+        wl.step(solver, step)
+        step += 1
     solver.sync()
     solver.profile(True)
     barrier()
@@ -192,7 +272,8 @@ def run_gpu(args):
     with ClockSampler(local) as clocks:
         ev0.record(stream)
         for _ in range(args.steps):
-            solver.rk_step(CFL)
+            wl.step(solver, step)
+            step += 1
         ev1.record(stream)
         torch.cuda.synchronize(dev)
     barrier()
@@ -209,23 +290,24 @@ def run_gpu(args):
 
     # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
     e2e = None
-    if not args.no_e2e:
-        h_in = torch.from_numpy(np.ascontiguousarray(q)).pin_memory()
+    if e2e_steps:
+        h_in = torch.from_numpy(np.ascontiguousarray(wl.q)).pin_memory()
         h_out = torch.empty_like(h_in).pin_memory()
         import ctypes
 
         L = solver.L
         for _ in range(2):
             solver._check(L.gbr_set_state(solver.h, ctypes.c_void_p(h_in.data_ptr()), 0))
-            solver.rk_step(CFL)
+            wl.step(solver, step)
+            step += 1
             solver._check(L.gbr_get_state(solver.h, ctypes.c_void_p(h_out.data_ptr()), 0))
         barrier()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        e2e_steps = max(1, min(args.steps, 10))
         for _ in range(e2e_steps):
             solver._check(L.gbr_set_state(solver.h, ctypes.c_void_p(h_in.data_ptr()), 0))
-            solver.rk_step(CFL)
+            wl.step(solver, step)
+            step += 1
             solver._check(L.gbr_get_state(solver.h, ctypes.c_void_p(h_out.data_ptr()), 0))
         solver.sync()
         e2e_s = time.perf_counter() - t0
@@ -235,13 +317,14 @@ def run_gpu(args):
             t = torch.tensor([e2e_s], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_s = float(t.item())
-        nbytes = int(q.size * 8)
+        nbytes = int(wl.q.size * 8)
         e2e = {"value": world * 3 * cells * e2e_steps / e2e_s, "unit": METRIC, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": e2e_steps}
 
-    # ---- roofline of the interface-flux kernel (FP64 ALU bound)
-    fl = load_flops()["tgv3d_viscous"]["face_flops_per_face"]
-    faces_per_launch = (N_CELLS_EDGE + 1) * N_CELLS_EDGE * N_CELLS_EDGE
+    # ---- roofline of the interface-flux kernel (FP64 ALU bound) and of the whole step
+    counts = load_flops()[wl.flops_key]
+    fl = counts["face_flops_per_face"]
+    faces_per_launch = wl.faces_per_rhs / 3.0
     avg_launch_s = (face_ms / 1e3) / max(face_launches, 1)
     achieved = fl * faces_per_launch / avg_launch_s / 1e12
     roofline = {"kernel": "k_face<3,visc>", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
@@ -249,6 +332,13 @@ def run_gpu(args):
                 "flops_per_face": fl, "faces_per_launch": faces_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
                 "face_share_of_step": face_ms / ms if ms > 0 else None,
                 "peak_note": "FP64 derived from the pool's unit counts and clock (nominal 1.25 TFLOP/s)"}
+    f_cell = counts["step_flops_per_cell_stage"]
+    per_gpu = value / world
+    t_flop = f_cell / (FP64_PEAK_TFLOPS * 1e12)
+    t_byte = BYTES_PER_CELL_STAGE_3D / (HBM_PEAK_GBS * 1e9)
+    step_roofline = {"flops_per_cell_stage": f_cell, "bytes_per_cell_stage": BYTES_PER_CELL_STAGE_3D,
+                     "bound": "alu" if t_flop >= t_byte else "hbm", "achieved_tflops": f_cell * per_gpu / 1e12,
+                     "frac": max(t_flop, t_byte) * per_gpu}
     if rank != 0:
         solver.close()
         return
@@ -256,12 +346,12 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": cells, "cfl": CFL, "reynolds": 1600.0, "mach": 0.1,
-                   "parallelism": f"replicas{world}", "l2": "working set ~3 GB >> 126 MB L2, no flush"},
-        "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clocks.summary(),
+        "config": dict({"workload": wl.name}, **wl.config, parallelism=f"replicas{world}", l2=wl.ws_note),
+        "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "step_roofline": step_roofline,
+        "clocks": clocks.summary(),
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(2)
+        line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)
     solver.close()
 
@@ -269,23 +359,23 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default 60 for tgv, 20 for jet)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbr", choices=["gbr", "reference"])
+    ap.add_argument("--workload", default="tgv", choices=["tgv", "jet"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--edge", type=int, default=128, help="cells per edge (profiling runs use smaller grids)")
+    ap.add_argument("--edge", type=int, default=N_CELLS_EDGE, help="tgv cells per edge (profiling runs use smaller grids)")
     args = ap.parse_args()
-    global N_CELLS_EDGE, WORKLOAD
-    if args.edge != N_CELLS_EDGE:
-        N_CELLS_EDGE = args.edge
-        WORKLOAD = f"tgv3d_viscous_{args.edge}^3_perturbed"
+    if args.steps is None:
+        args.steps = 60 if args.workload == "tgv" else 20
     if args.warmup < 3:
         args.warmup = 3
+    wl = Workload(args.workload, args.edge)
     if args.impl == "reference":
-        run_reference(args)
+        run_reference(args, wl)
     else:
-        run_gpu(args)
+        run_gpu(args, wl)
 
 
 if __name__ == "__main__":

@@ -114,9 +114,14 @@ gbr_status gbr_set_motion(gbr_ctx* c, const gbr_motion* m, double t0);
 gbr_status gbr_set_state(gbr_ctx* c, const double* q, int on_device);
 gbr_status gbr_get_state(gbr_ctx* c, double* q, int on_device);
 
-/* Jet-type boundary data: x-low inflow primitives [nv][nk][nj] (host), and a
- * sponge source -sigma (Q - q_amb) with sigma per cell (host, NULL removes it). */
-gbr_status gbr_set_inflow(gbr_ctx* c, const double* prim);
+/* Jet-type boundary data (reading A23): x-low inflow primitives [nv][nk][nj]
+ * imposed in the x-low ghost cells of every following stage, and a sponge source
+ * -sigma (Q - q_amb) with sigma per cell (host, NULL removes it).
+ * gbr_set_inflow: on_device = 0: prim is host memory, copied before the call
+ * returns; on_device = 1: prim is device memory, copied in stream order on the
+ * context's stream (the caller keeps it alive until that copy has run), so a
+ * time-dependent inflow can be changed between steps without a host round trip. */
+gbr_status gbr_set_inflow(gbr_ctx* c, const double* prim, int on_device);
 gbr_status gbr_set_sponge(gbr_ctx* c, const double* sigma, const double* q_amb);
 
 /* dQ/dt = L(Q) = J (Res - (1/J)_t Q) [+ sponge] of the current state (Sec. 3,

@@ -243,12 +243,13 @@ class Oracle:
         return q
 
 
-def op1d(kind, f):
-    """Periodic line operators: 'e6', 'second', 'face', 'D', 'e4'."""
+def op1d(kind, f, counting=False):
+    """Periodic line operators: 'e6', 'second', 'face', 'D', 'e4' (counting=True: run in the
+    operation-counting build, for flop_counts)."""
     k = {"e6": 0, "second": 1, "face": 2, "D": 3, "e4": 4}[kind]
     f = _f64(f)
     out = np.zeros_like(f)
-    _lib().orc_op1d(k, f.size, _ptr(f), _ptr(out))
+    _lib(counting).orc_op1d(k, f.size, _ptr(f), _ptr(out))
     return out
 
 

@@ -830,11 +830,13 @@ gbr_status gbr_get_state(gbr_ctx* c, double* q, int on_device) {
   return GBR_OK;
 }
 
-gbr_status gbr_set_inflow(gbr_ctx* c, const double* prim) {
+gbr_status gbr_set_inflow(gbr_ctx* c, const double* prim, int on_device) {
   if (!c || !prim) return fail(c, GBR_EINVAL, "null argument");
   const size_t bytes = sizeof(double) * c->L.nv * c->L.n[1] * c->L.n[2];
-  CK(cudaMemcpyAsync(c->inflow, prim, bytes, cudaMemcpyHostToDevice, c->stream), "set inflow");
-  CK(cudaStreamSynchronize(c->stream), "set inflow sync");
+  CK(cudaMemcpyAsync(c->inflow, prim, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     c->stream),
+     "set inflow");
+  if (!on_device) CK(cudaStreamSynchronize(c->stream), "set inflow sync");
   return GBR_OK;
 }
 

@@ -76,7 +76,7 @@ def lib():
     L.gbr_set_motion.argtypes = [_vp, ctypes.POINTER(gbr_motion), ctypes.c_double]
     L.gbr_set_state.argtypes = [_vp, _vp, ctypes.c_int]
     L.gbr_get_state.argtypes = [_vp, _vp, ctypes.c_int]
-    L.gbr_set_inflow.argtypes = [_vp, _P]
+    L.gbr_set_inflow.argtypes = [_vp, _vp, ctypes.c_int]
     L.gbr_set_sponge.argtypes = [_vp, _P, _P]
     L.gbr_rhs.argtypes = [_vp, _vp]
     L.gbr_compute_dt.argtypes = [_vp, ctypes.c_double, _P]
@@ -261,8 +261,14 @@ class Solver:
         self._check(self.L.gbr_set_motion(self.h, ctypes.byref(self._motion), float(t0)))
 
     def set_inflow(self, prim):
-        prim = _f64(prim)
-        self._check(self.L.gbr_set_inflow(self.h, _ptr(prim)))
+        """x-low inflow primitives [nv][nk][nj]: a host array, or a CUDA tensor copied in stream order."""
+        t = self.torch
+        if isinstance(prim, t.Tensor) and prim.is_cuda:
+            assert prim.dtype == t.float64 and prim.is_contiguous()
+            self._check(self.L.gbr_set_inflow(self.h, _vp(prim.data_ptr()), 1))
+        else:
+            prim = _f64(prim)
+            self._check(self.L.gbr_set_inflow(self.h, _vp(prim.ctypes.data), 0))
 
     def set_sponge(self, sigma, q_amb):
         sigma = _f64(sigma)

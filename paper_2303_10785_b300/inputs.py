@@ -339,6 +339,20 @@ def jet_inflow_prim(yc, zc, gamma=1.4, p_exit=1.5, rho_exit=1.8, radius=0.5, del
     return np.stack([rho, u, z, z, p])
 
 
+def jet_inflow_step(base, seed, step, amp=0.01):
+    """Inflow primitives of time step `step`: the base inflow [nv][nk][nj] with a random
+    velocity of amplitude amp * u_base added to u, v, w, u_base the local axial inflow
+    velocity (so the quiescent ambient part of the plane stays at rest).  The random numbers
+    are SplitMix64 of (seed, step, cell, component) mapped to [-1, 1)."""
+    base = np.asarray(base, dtype=np.float64)
+    nv, nk, nj = base.shape
+    cell = np.arange(nk * nj, dtype=np.uint64).reshape(nk, nj)
+    out = base.copy()
+    for c in (1, 2, 3):
+        out[c] = base[c] + amp * base[1] * hash_uniform(seed, np.uint64(step), cell, np.uint64(c))
+    return out
+
+
 def jet_sponge_sigma(n, sigma_max=2.0, x_frac=0.15, lateral=10):
     """sigma = sigma_max s^2 over the last x_frac of the x cells and the outer lateral cells."""
     ni, nj, nk = n
@@ -354,3 +368,27 @@ def jet_sponge_sigma(n, sigma_max=2.0, x_frac=0.15, lateral=10):
     sz = lat(np.arange(nk), nk)
     S = np.maximum(np.maximum(sx[None, None, :], sy[None, :, None]), sz[:, None, None])
     return np.ascontiguousarray(sigma_max * S * S)
+
+
+
+def jet_case(n=(480, 170, 170), Lx=20.0, h0=0.02, ratio=1.02, re_d=1e5, gamma=1.4, sutherland_s=0.3768,
+             lateral=10):
+    """The under-expanded jet-like workload: the stretched box of nodes_jet, quiescent ambient
+    rho = p = 1 at rest, the sonic top-hat inflow of jet_inflow_prim in the x-low ghost cells,
+    zero-gradient elsewhere, the sponge of jet_sponge_sigma, Sutherland viscosity with
+    T_ref = T_e and mu(T_e) = rho_e u_e D / Re_D (D = 1).
+    Returns (case, nodes, q, inflow, sigma, q_amb)."""
+    ni, nj, nk = n
+    Te = 2.0 / (gamma + 1.0)
+    ue = math.sqrt(gamma * Te)
+    case = case_params(3, n, periodic=(0, 0, 0), bc=((2, 1), (1, 1), (1, 1)), reynolds=re_d / (1.8 * ue),
+                       sutherland_s=sutherland_s, t_ref=Te, gamma=gamma)
+    nodes = nodes_jet(ni, nj, nk, Lx=Lx, h0=h0, ratio=ratio)
+    xc = centroids(nodes, n, (0, 0, 0))
+    inflow = np.ascontiguousarray(jet_inflow_prim(xc[1][:, :, 0], xc[2][:, :, 0], gamma))
+    P = np.zeros((5, nk, nj, ni))
+    P[0] = 1.0
+    P[4] = 1.0
+    sigma = jet_sponge_sigma(n, lateral=lateral)
+    q_amb = np.array([1.0, 0.0, 0.0, 0.0, 1.0 / (gamma - 1.0)])
+    return case, nodes, prim_to_cons(P, gamma), inflow, sigma, q_amb

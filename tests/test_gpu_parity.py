@@ -200,6 +200,35 @@ def test_jet_rhs_with_inflow_and_sponge():
     s.close()
 
 
+def test_jet_steps_with_perturbed_inflow_from_device_memory():
+    """The jet workload's time-dependent inflow: 1 % random velocity per step, the planes
+    generated up front and handed to the library from device memory between steps."""
+    import torch
+
+    case, nodes, vel, q, extra = case_jet()
+    orc, s = build_pair(case, nodes, vel, extra)
+    s.set_state(q)
+    planes = [I.jet_inflow_step(extra["inflow"], 11, step) for step in range(4)]
+    dev = torch.from_numpy(np.stack(planes)).cuda()
+    torch.cuda.synchronize()
+    qo = q.copy()
+    for step in range(4):
+        orc.set_inflow(planes[step])
+        qo = orc.rk3(qo, 2e-3)
+        s.set_inflow(dev[step])
+        s.rk_step(-2e-3)
+    s.sync()
+    assert rel_state(s.get_state(), qo) < 1e-12
+    # the perturbation reached the state: the unperturbed inflow gives another result
+    s.set_state(q)
+    s.set_inflow(extra["inflow"])
+    for _ in range(4):
+        s.rk_step(-2e-3)
+    s.sync()
+    assert rel_state(s.get_state(), qo) > 1e-6
+    s.close()
+
+
 def case_3d_tgv_smooth(n=32):
     case = I.case_params(3, (n, n, n), reynolds=1600.0)
     nodes = I.nodes_tgv_3d(n, 0.1)
