@@ -46,6 +46,10 @@ FP64_PEAK_TFLOPS = 1.25
 HBM_PEAK_GBS = 6491.5
 # minimum HBM traffic of a 3D FP64 cell-stage: state and cell geometry, stage average
 BYTES_PER_CELL_STAGE_3D = 186.7
+# DRAM bytes (read + write) per interface of the 3D viscous interface kernel, from one ncu
+# capture of a 96^3 launch (dram__bytes_read.sum + dram__bytes_write.sum = 321.9 MB for
+# 893,952 interfaces); traffic grows in proportion to the interfaces of a launch.
+FACE_DRAM_BYTES_PER_INTERFACE = 321.9e6 / 893952
 
 
 def load_flops():
@@ -70,7 +74,6 @@ class Workload:
             self.name = f"tgv3d_viscous_{edge}^3_perturbed"
             self.flops_key = "tgv3d_viscous"
             self.config = {"cells": edge ** 3, "cfl": CFL, "reynolds": 1600.0, "mach": 0.1}
-            self.ws_note = "working set ~3 GB >> 126 MB L2, no flush"
         else:
             n = (480, 170, 170)
             self.case, self.nodes, self.q, self.inflow, sigma, qamb = I.jet_case(n)
@@ -79,7 +82,6 @@ class Workload:
             self.flops_key = "jet3d_viscous"
             self.config = {"cells": n[0] * n[1] * n[2], "dt": JET_DT, "reynolds_d": 1e5, "sutherland": True,
                            "inflow_perturbation": "1 % velocity, SplitMix64(seed, step, cell, component)"}
-            self.ws_note = "working set ~20 GB >> 126 MB L2, no flush"
         self.n = n
         self.cells = n[0] * n[1] * n[2]
         self.faces_per_rhs = sum((n[0] + (d == 0)) * (n[1] + (d == 1)) * (n[2] + (d == 2)) for d in range(3))
@@ -328,7 +330,9 @@ def run_gpu(args, wl):
     avg_launch_s = (face_ms / 1e3) / max(face_launches, 1)
     achieved = fl * faces_per_launch / avg_launch_s / 1e12
     roofline = {"kernel": "k_face<3,visc>", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": FACE_DRAM_BYTES_PER_INTERFACE * faces_per_launch,
+                "traffic_note": "bytes per launch, scaled from a 96^3 ncu capture by interfaces",
                 "flops_per_face": fl, "faces_per_launch": faces_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
                 "face_share_of_step": face_ms / ms if ms > 0 else None,
                 "peak_note": "FP64 derived from the pool's unit counts and clock (nominal 1.25 TFLOP/s)"}
@@ -346,7 +350,8 @@ def run_gpu(args, wl):
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict({"workload": wl.name}, **wl.config, parallelism=f"replicas{world}", l2=wl.ws_note),
+        "config": dict({"workload": wl.name}, **wl.config, parallelism=f"replicas{world}",
+                       l2=f"workspace {solver.workspace_bytes / 1e9:.1f} GB >> 126 MB L2, no flush"),
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "step_roofline": step_roofline,
         "clocks": clocks.summary(),
     }

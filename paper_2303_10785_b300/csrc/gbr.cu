@@ -702,7 +702,7 @@ Phys phys_of(const gbr_params* p) {
   ph.sutherland = p->sutherland_s > 0.0;
   ph.suth_s = p->sutherland_s;
   ph.it_ref = p->t_ref > 0.0 ? 1.0 / p->t_ref : 1.0;
-  ph.half_alpha_d = 0.5 * p->alpha_damping;
+  ph.alpha_d = p->alpha_damping;
   ph.mp_alpha = p->mp_alpha;
   ph.mp_beta = p->mp_beta;
   ph.mp_eps = p->mp_eps;

@@ -118,7 +118,7 @@ GBR_HD void box_coord(const Box& b, long long t, int& i, int& j, int& k) {
 struct Phys {
   double gamma, gm1, igm1;
   double mu_ref, suth_s, it_ref;
-  double half_alpha_d;       // alpha^D / 2
+  double alpha_d;            // alpha^D
   double mp_alpha, mp_beta, mp_eps;
   double kfac;               // kappa = mu * kfac, kfac = gamma / ((gamma - 1) Pr)
   double dt_visc_fac;        // max(4/3, gamma/Pr) of the viscous time-step bound (reading A20)
@@ -575,9 +575,10 @@ GBR_HD void hllc(const double* PL, const double* PR, const double* nh, double nn
   const double inn2 = inn * inn;
   // left and right states (kept in scalars: no runtime-indexed arrays)
   const double rl = PL[0], rr = PR[0];
-  const double irlr = 1.0 / (rl * rr);  // one reciprocal for both densities
-  const double irl = rr * irlr, irr = rl * irlr;
   const double pl = PL[NV - 1], pr = PR[NV - 1];
+  // t = 1/sqrt(gamma p rho) = 1/(rho c): c = gamma p t and 1/rho = gamma p t^2, no division
+  const double gpl = ph.gamma * pl, gpr = ph.gamma * pr;
+  const double tl = grsqrt(gpl * rl), tr = grsqrt(gpr * rr);
   double q2l = 0.0, q2r = 0.0, Ul = nt, Ur = nt;
   #pragma unroll
   for (int a = 0; a < ND; ++a) {
@@ -587,8 +588,7 @@ GBR_HD void hllc(const double* PL, const double* PR, const double* nh, double nn
     Ur = gfma(nh[a], PR[1 + a], Ur);
   }
   const double El = gfma(pl, ph.igm1, 0.5 * rl * q2l), Er = gfma(pr, ph.igm1, 0.5 * rr * q2r);
-  const double xl = ph.gamma * pl * irl, xr = ph.gamma * pr * irr;
-  const double cl = xl * grsqrt(xl), cr = xr * grsqrt(xr);  // speeds of sound
+  const double cl = gpl * tl, cr = gpr * tr;  // speeds of sound
   const double SL = gmin(gfma(-cl, nn, Ul), gfma(-cr, nn, Ur));
   const double SR = gmax(gfma(cl, nn, Ul), gfma(cr, nn, Ur));
   const double aL = rl * (SL - Ul), aR = rr * (SR - Ur);
@@ -596,7 +596,7 @@ GBR_HD void hllc(const double* PL, const double* PR, const double* nh, double nn
   // branches of Sec. 5.1.1: S^L >= 0 -> F^L; S^L < 0 <= S* -> F*L; S* < 0 < S^R -> F*R; else F^R
   const bool left = !is_neg(SL) || !is_neg(Ss);
   const bool star = is_neg(SL) && (left || is_pos(SR));
-  const double rs = left ? rl : rr, irs = left ? irl : irr, ps = left ? pl : pr;
+  const double rs = left ? rl : rr, ps = left ? pl : pr;
   const double Us = left ? Ul : Ur, Es = left ? El : Er, S = left ? SL : SR;
   double us[ND];
   #pragma unroll
@@ -617,7 +617,8 @@ GBR_HD void hllc(const double* PL, const double* PR, const double* nh, double nn
     F[0] += S * (fac - rs);
     #pragma unroll
     for (int a = 0; a < ND; ++a) F[1 + a] += S * (fac * gfma(nh[a], w, us[a]) - rs * us[a]);
-    const double eb = Es * irs + dS * gfma(Ss - nt, inn2, p_rA);
+    const double ts = left ? tl : tr, gps = left ? gpl : gpr;
+    const double eb = gfma(Es * gps, ts * ts, dS * gfma(Ss - nt, inn2, p_rA));  // E/rho + ...
     F[NV - 1] += S * gfma(fac, eb, -Es);
   }
 }
@@ -723,72 +724,81 @@ GBR_HD void body_face(const RhsArgs& A, int d, int i, int j, int k) {
   hllc<ND>(PL, PR, nh, nn2, inn, nt, ph, F);
 
   if (VISC) {
-    // Sec. 5.2 alpha-damping on [u.., T]
-    double gx[ND + 1][ND];
+    // Sec. 5.2 alpha-damping on [u.., T].  gc2[v][e] = 2 d(phi_v)/d(xi_e) at the interface:
+    // Eq. (AD-eqn1) along the sweep, the sum of the two cells' gradients across it (reading
+    // A11); the factor 1/2 is folded into mu, lambda and kappa below.
+    double gc2[ND + 1][ND];
     double phif[ND + 1];
-    const double* fu = A.fu[d];
     #pragma unroll
     for (int v = 0; v <= ND; ++v) {
       const double* val = (v < ND) ? P + (1 + v) * PC : A.temp;
       const int gi = (v < ND) ? (1 + v) : NV;
-      double gc[ND];
       const double gd1 = A.g1[d][gi * PC + pp[1]], gd2 = A.g1[d][gi * PC + pp[2]];
       const double phiL = gfma(0.5, gd1, val[pp[1]]);   // Eq. (AD-eqn2), beta^D = 0
       const double phiR = gfma(-0.5, gd2, val[pp[2]]);
       #pragma unroll
       for (int e = 0; e < ND; ++e) {
         if (e == d) {
-          gc[e] = gfma(ph.half_alpha_d, phiR - phiL, 0.5 * (gd1 + gd2));  // Eq. (AD-eqn1)
+          gc2[v][e] = gfma(ph.alpha_d, phiR - phiL, gd1 + gd2);  // 2 x Eq. (AD-eqn1)
         } else {
-          gc[e] = 0.5 * (A.g1[e][gi * PC + pp[1]] + A.g1[e][gi * PC + pp[2]]);  // reading A11
+          gc2[v][e] = A.g1[e][gi * PC + pp[1]] + A.g1[e][gi * PC + pp[2]];
         }
       }
       phif[v] = 0.5 * (phiL + phiR);
+    }
+    // The flux needs only tau n^ and beta . n^ (Eq. shear-str, thermal-work), so the chain rule
+    // d/dx_a = sum_e (d xi_e/d x_a) d/d xi_e (Eq. AD-eqn3) is contracted with n^ first:
+    //   m_e = sum_b xi_e,x_b n^_b,  s_e = sum_b n^_b du_b/d xi_e,
+    //   (grad u n^)_a = sum_e m_e du_a/dxi_e,  (grad u^T n^)_a = sum_e xi_e,x_a s_e,
+    //   div u = sum_a sum_e xi_e,x_a du_a/dxi_e,  grad T . n^ = sum_e m_e dT/dxi_e,
+    //   beta . n^ = kappa grad T . n^ + u . (tau n^)   (tau symmetric)
+    const double* fu = A.fu[d];
+    double xe[ND][ND];  // xe[e][a] = d xi_e / d x_a at the interface
+    #pragma unroll
+    for (int e = 0; e < ND; ++e)
       #pragma unroll
-      for (int a = 0; a < ND; ++a) {  // Eq. (AD-eqn3)
-        double sacc = 0.0;
-        #pragma unroll
-        for (int e = 0; e < ND; ++e) sacc = gfma(fu[(e * ND + a) * FC + f], gc[e], sacc);
-        gx[v][a] = sacc;
+      for (int a = 0; a < ND; ++a) xe[e][a] = fu[(e * ND + a) * FC + f];
+    double m[ND], sv[ND];
+    #pragma unroll
+    for (int e = 0; e < ND; ++e) {
+      double acc = xe[e][0] * nh[0], acs = nh[0] * gc2[0][e];
+      #pragma unroll
+      for (int b = 1; b < ND; ++b) {
+        acc = gfma(xe[e][b], nh[b], acc);
+        acs = gfma(nh[b], gc2[b][e], acs);
       }
+      m[e] = acc;
+      sv[e] = acs;
     }
     double mu = ph.mu_ref;
     if (ph.sutherland) {
       const double th = phif[ND] * ph.it_ref;
       mu = ph.mu_ref * (th * sqrt(th)) * ((1.0 + ph.suth_s) / (th + ph.suth_s));
     }
-    const double lam = (-2.0 / 3.0) * mu;
-    const double kap = mu * ph.kfac;
-    double div = 0.0;
-    #pragma unroll
-    for (int a = 0; a < ND; ++a) div += gx[a][a];
-    double tau[ND][ND];
+    const double hmu = 0.5 * mu;
+    double div2 = 0.0;
     #pragma unroll
     for (int a = 0; a < ND; ++a)
       #pragma unroll
-      for (int b = 0; b < ND; ++b) {
-        tau[a][b] = mu * (gx[a][b] + gx[b][a]);  // Eq. (shear-str)
-        if (a == b) tau[a][b] = gfma(lam, div, tau[a][b]);
+      for (int e = 0; e < ND; ++e) div2 = gfma(xe[e][a], gc2[a][e], div2);
+    const double hlamdiv = (-1.0 / 3.0) * mu * div2;  // lambda div u, lambda = -2/3 mu
+    double bn = 0.0;
+    #pragma unroll
+    for (int a = 0; a < ND; ++a) {
+      double t1 = 0.0, t2 = 0.0;
+      #pragma unroll
+      for (int e = 0; e < ND; ++e) {
+        t1 = gfma(m[e], gc2[a][e], t1);
+        t2 = gfma(xe[e][a], sv[e], t2);
       }
-    double beta[ND];
-    #pragma unroll
-    for (int a = 0; a < ND; ++a) {
-      double sacc = kap * gx[ND][a];
-      #pragma unroll
-      for (int b = 0; b < ND; ++b) sacc = gfma(phif[b], tau[a][b], sacc);  // Eq. (thermal-work)
-      beta[a] = sacc;
+      const double taun = gfma(hmu, t1 + t2, hlamdiv * nh[a]);  // (tau n^)_a
+      F[1 + a] -= taun;
+      bn = gfma(phif[a], taun, bn);
     }
+    double gTn = 0.0;
     #pragma unroll
-    for (int a = 0; a < ND; ++a) {
-      double sacc = 0.0;
-      #pragma unroll
-      for (int b = 0; b < ND; ++b) sacc = gfma(nh[b], tau[a][b], sacc);
-      F[1 + a] -= sacc;
-    }
-    double sacc = 0.0;
-    #pragma unroll
-    for (int b = 0; b < ND; ++b) sacc = gfma(nh[b], beta[b], sacc);
-    F[NV - 1] -= sacc;
+    for (int e = 0; e < ND; ++e) gTn = gfma(m[e], gc2[ND][e], gTn);
+    F[NV - 1] -= gfma(0.5 * mu * ph.kfac, gTn, bn);
   }
   #pragma unroll
   for (int c = 0; c < NV; ++c) A.flux[d][c * FC + f] = F[c];
