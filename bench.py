@@ -43,7 +43,20 @@ METRIC = "cell-RK-stage updates/s"
 # 2 DFMA/clk/SM x 2 flop x 2.032 GHz = 1.20 TFLOP/s nominal at the maximum SM
 # clock (the pool's FP64 figure is 1.25 TFLOP/s; derivation in the design doc).
 FP64_PEAK_TFLOPS = 1.25
-HBM_PEAK_GBS = 6491.5
+# FP32 FFMA peak, nominal: 148 SMs x 128 FMA/clk x 2 flop x 2.032 GHz
+FP32_PEAK_TFLOPS = 77.0
+
+
+def measured_hbm_gbs():
+    """HBM copy bandwidth measured on this machine (MEASURED_PEAKS.json), else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
+HBM_PEAK_GBS, HBM_PEAK_KIND = measured_hbm_gbs()
 # minimum HBM traffic of a 3D FP64 cell-stage: state and cell geometry, stage average
 BYTES_PER_CELL_STAGE_3D = 186.7
 # DRAM bytes (read + write) per interface of the 3D viscous interface kernel, from one ncu
@@ -57,13 +70,28 @@ def load_flops():
         return json.load(f)
 
 
+def face_alg_bytes(wl):
+    """Algorithmic HBM bytes per interface of one sweep: every array element the interface kernel
+    needs, read once (the cells of a sweep are shared by its interfaces), and the flux written once."""
+    nd = 3
+    nv = nd + 2
+    visc = wl.case.get("reynolds", 0.0) > 0.0
+    er = 4 if wl.precision == "mixed" else 8
+    cells = er * (nv + nv + nv)                                   # primitives, P' and P'' along the sweep
+    if visc:
+        cells += er * (1 + 1 + (nd - 1) * (nd + 1))               # T, T', tangential [u, T]' of two directions
+    metrics = 8 * (nd + (nd * nd if visc else 0) + (1 if wl.case.get("moving", 0) else 0))
+    return cells + metrics + er * nv
+
+
 class Workload:
     """Inputs and per-step driving of one benchmark workload."""
 
-    def __init__(self, kind, edge=N_CELLS_EDGE):
+    def __init__(self, kind, edge=N_CELLS_EDGE, precision="fp64"):
         from paper_2303_10785_b300 import inputs as I
 
         self.kind = kind
+        self.precision = precision
         self.inflow = self.sponge = None
         if kind == "tgv":
             n = (edge,) * 3
@@ -82,6 +110,9 @@ class Workload:
             self.flops_key = "jet3d_viscous"
             self.config = {"cells": n[0] * n[1] * n[2], "dt": JET_DT, "reynolds_d": 1e5, "sutherland": True,
                            "inflow_perturbation": "1 % velocity, SplitMix64(seed, step, cell, component)"}
+        self.case = dict(self.case, precision=precision)
+        if precision != "fp64":
+            self.name += "_" + precision
         self.n = n
         self.cells = n[0] * n[1] * n[2]
         self.faces_per_rhs = sum((n[0] + (d == 0)) * (n[1] + (d == 1)) * (n[2] + (d == 2)) for d in range(3))
@@ -323,34 +354,51 @@ def run_gpu(args, wl):
         e2e = {"value": world * 3 * cells * e2e_steps / e2e_s, "unit": METRIC, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": e2e_steps}
 
-    # ---- roofline of the interface-flux kernel (FP64 ALU bound) and of the whole step
+    # ---- roofline of the interface-flux kernel and of the whole step
     counts = load_flops()[wl.flops_key]
     fl = counts["face_flops_per_face"]
     faces_per_launch = wl.faces_per_rhs / 3.0
     avg_launch_s = (face_ms / 1e3) / max(face_launches, 1)
-    achieved = fl * faces_per_launch / avg_launch_s / 1e12
-    roofline = {"kernel": "k_face<3,visc>", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": FACE_DRAM_BYTES_PER_INTERFACE * faces_per_launch,
-                "traffic_note": "bytes per launch, scaled from a 96^3 ncu capture by interfaces",
-                "flops_per_face": fl, "faces_per_launch": faces_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
-                "face_share_of_step": face_ms / ms if ms > 0 else None,
-                "peak_note": "FP64 derived from the pool's unit counts and clock (nominal 1.25 TFLOP/s)"}
+    mixed = wl.precision == "mixed"
+    fp_peak = FP32_PEAK_TFLOPS if mixed else FP64_PEAK_TFLOPS
+    alg_bytes = face_alg_bytes(wl)
+    t_alu = fl / (fp_peak * 1e12)
+    t_hbm = alg_bytes / (HBM_PEAK_GBS * 1e9)
+    common = {"kernel": "k_face<3,visc>", "flops_per_face": fl, "alg_bytes_per_face": alg_bytes,
+              "faces_per_launch": faces_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
+              "face_share_of_step": face_ms / ms if ms > 0 else None}
+    if t_alu >= t_hbm:
+        achieved = fl * faces_per_launch / avg_launch_s / 1e12
+        roofline = dict({"bound": "alu", "achieved": achieved, "peak": fp_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp_peak}, **common)
+        roofline["peak_note"] = ("FP32 FFMA nominal from unit counts and the maximum SM clock" if mixed else
+                                 "FP64 derived from the pool's unit counts and clock (nominal 1.25 TFLOP/s)")
+    else:
+        achieved = alg_bytes * faces_per_launch / avg_launch_s / 1e9
+        roofline = dict({"bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                         "frac": achieved / HBM_PEAK_GBS}, **common)
+        roofline["peak_note"] = f"HBM copy bandwidth, {HBM_PEAK_KIND} (MEASURED_PEAKS.json)"
+    if mixed:
+        roofline["traffic"] = None
+    else:
+        roofline["traffic"] = FACE_DRAM_BYTES_PER_INTERFACE * faces_per_launch
+        roofline["traffic_note"] = "bytes per launch, scaled from a 96^3 ncu capture by interfaces"
     f_cell = counts["step_flops_per_cell_stage"]
     per_gpu = value / world
-    t_flop = f_cell / (FP64_PEAK_TFLOPS * 1e12)
+    t_flop = f_cell / (fp_peak * 1e12)
     t_byte = BYTES_PER_CELL_STAGE_3D / (HBM_PEAK_GBS * 1e9)
     step_roofline = {"flops_per_cell_stage": f_cell, "bytes_per_cell_stage": BYTES_PER_CELL_STAGE_3D,
                      "bound": "alu" if t_flop >= t_byte else "hbm", "achieved_tflops": f_cell * per_gpu / 1e12,
-                     "frac": max(t_flop, t_byte) * per_gpu}
+                     "frac": max(t_flop, t_byte) * per_gpu, "fp_peak_tflops": fp_peak,
+                     "hbm_peak_gbs": HBM_PEAK_GBS}
     if rank != 0:
         solver.close()
         return
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict({"workload": wl.name}, **wl.config, parallelism=f"replicas{world}",
+        "vs_baseline": None, "dtype": "f32+f64" if wl.precision == "mixed" else "f64", "data": "synthetic",
+        "config": dict({"workload": wl.name}, **wl.config, precision=wl.precision, parallelism=f"replicas{world}",
                        l2=f"workspace {solver.workspace_bytes / 1e9:.1f} GB >> 126 MB L2, no flush"),
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "step_roofline": step_roofline,
         "clocks": clocks.summary(),
@@ -368,6 +416,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbr", choices=["gbr", "reference"])
     ap.add_argument("--workload", default="tgv", choices=["tgv", "jet"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="mixed: FP32 reconstruction and fluxes, FP64 state, metrics, GCL and RK accumulation")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--edge", type=int, default=N_CELLS_EDGE, help="tgv cells per edge (profiling runs use smaller grids)")
@@ -376,7 +426,7 @@ def main():
         args.steps = 60 if args.workload == "tgv" else 20
     if args.warmup < 3:
         args.warmup = 3
-    wl = Workload(args.workload, args.edge)
+    wl = Workload(args.workload, args.edge, args.precision)
     if args.impl == "reference":
         run_reference(args, wl)
     else:

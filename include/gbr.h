@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define GBR_ABI_VERSION 1
+#define GBR_ABI_VERSION 2
 
 typedef struct gbr_ctx gbr_ctx;
 
@@ -49,6 +49,15 @@ typedef enum {
 
 enum { GBR_BC_ZEROGRAD = 1, GBR_BC_INFLOW = 2 };
 
+/* Arithmetic of the right-hand side (gbr_params.precision):
+ * GBR_PREC_FP64:  every step in FP64 (the paper's path).
+ * GBR_PREC_MIXED: primitives, gradients, characteristic reconstruction, limiter,
+ *                 HLLC and viscous fluxes computed and stored in FP32; the conserved
+ *                 state, the metrics and 1/J, the GCL term, the flux divergence and
+ *                 the RK accumulation in FP64.  Not in the paper (which compares FP32
+ *                 and FP64 runs only as a whole). */
+enum { GBR_PREC_FP64 = 0, GBR_PREC_MIXED = 1 };
+
 typedef struct {
   int ndim;            /* 2 or 3 */
   int n[3];            /* cells per axis (n[2] = 1 in 2D) */
@@ -63,6 +72,7 @@ typedef struct {
   double alpha_damping;/* alpha^D of Eq. (AD-eqn1), paper value 4 */
   double mp_alpha, mp_beta, mp_eps; /* App. E limiter constants (4, 4, 1e-20) */
   int moving;          /* 1: reserve grid-velocity, time-metric and GCL storage */
+  int precision;       /* GBR_PREC_FP64 or GBR_PREC_MIXED */
 } gbr_params;
 
 /* Prescribed sinusoidal node motion (Sec. 7.2 families):
@@ -169,7 +179,8 @@ gbr_status gbr_profile(gbr_ctx* c, int enable, double* face_ms, long long* face_
  * All scratch lives in one file-scope device array of 64 MiB that every GPU
  * loading this library holds until the process exits; grids whose scratch
  * would exceed it are rejected with GBR_EINVAL before any device work.  Only
- * periodic and zero-gradient sides are accepted (no inflow data, no sponge).
+ * periodic and zero-gradient sides are accepted (no inflow data, no sponge),
+ * and only params.precision = GBR_PREC_FP64.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current) and caches it; make that
  * first call before any stream capture.  Calls share the array and it keeps

@@ -86,42 +86,42 @@ __global__ void k_gcl(GeoArgs G, Box b) {
   body_gcl(G, i, j, k);
 }
 
-template <int ND>
-__global__ void k_prim(RhsArgs A, Box b) {
+template <int ND, class R = double>
+__global__ void k_prim(RhsArgsT<R> A, Box b) {
   BOX_THREAD(b);
   body_prim<ND>(A, i, j, k);
 }
 
-template <int ND>
-__global__ void k_halo(RhsArgs A, int d, Box b) {
+template <int ND, class R = double>
+__global__ void k_halo(RhsArgsT<R> A, int d, Box b) {
   BOX_THREAD(b);
   body_halo<ND>(A, d, i, j, k);
 }
 
-template <int ND>
-__global__ void k_grad1(RhsArgs A, Box b0, Box b1, Box b2) {
+template <int ND, class R = double>
+__global__ void k_grad1(RhsArgsT<R> A, Box b0, Box b1, Box b2) {
   const int e = blockIdx.y;
   const Box b = e == 0 ? b0 : (e == 1 ? b1 : b2);
   BOX_THREAD(b);
   body_grad1<ND>(A, e, i, j, k);
 }
 
-template <int ND>
-__global__ void k_grad2(RhsArgs A, Box b0, Box b1, Box b2) {
+template <int ND, class R = double>
+__global__ void k_grad2(RhsArgsT<R> A, Box b0, Box b1, Box b2) {
   const int e = blockIdx.y;
   const Box b = e == 0 ? b0 : (e == 1 ? b1 : b2);
   BOX_THREAD(b);
   body_grad2<ND>(A, e, i, j, k);
 }
 
-template <int ND, bool VISC, bool MOV>
-__global__ void __launch_bounds__(GBR_FACE_BLOCK, GBR_FACE_MIN_BLOCKS) k_face(RhsArgs A, int d, Box b) {
+template <int ND, bool VISC, bool MOV, class R = double>
+__global__ void __launch_bounds__(GBR_FACE_BLOCK, GBR_FACE_MIN_BLOCKS) k_face(RhsArgsT<R> A, int d, Box b) {
   BOX_THREAD(b);
   body_face<ND, VISC, MOV>(A, d, i, j, k);
 }
 
-template <int ND, bool MOV>
-__global__ void k_update(UpdArgs U, Box b, int* err) {
+template <int ND, bool MOV, class R = double>
+__global__ void k_update(UpdArgsT<R> U, Box b, int* err) {
   BOX_THREAD(b);
   if (body_update<ND, MOV>(U, i, j, k)) atomicOr(err, 1);
 }
@@ -200,6 +200,7 @@ bool valid_params(const gbr_params* p, std::string& why) {
   if (!(p->gamma > 1.0)) { why = "gamma must exceed 1"; return false; }
   if (p->reynolds > 0.0 && !(p->prandtl > 0.0)) { why = "prandtl must be positive"; return false; }
   if (p->sutherland_s > 0.0 && !(p->t_ref > 0.0)) { why = "t_ref must be positive"; return false; }
+  if (p->precision != GBR_PREC_FP64 && p->precision != GBR_PREC_MIXED) { why = "unknown precision"; return false; }
   long long cells = (long long)p->n[0] * p->n[1] * (p->ndim == 3 ? p->n[2] : 1);
   if (cells > (1LL << 34)) { why = "grid too large"; return false; }
   return true;
@@ -209,6 +210,9 @@ Layout layout_of(const gbr_params* p) {
   int n[3] = {p->n[0], p->n[1], p->ndim == 3 ? p->n[2] : 1};
   return make_layout(p->ndim, n, p->periodic);
 }
+
+// bytes of one element of the arrays computed in the path's type
+size_t elem_r(const gbr_params* p) { return p->precision == GBR_PREC_MIXED ? sizeof(float) : sizeof(double); }
 
 Plan plan_of(const gbr_params* p, const Layout& L) {
   Plan P;
@@ -221,11 +225,12 @@ Plan plan_of(const gbr_params* p, const Layout& L) {
   P.add(D * nv * L.ncells);                       // SL_Q0
   P.add(D * nv * L.ncells);                       // SL_Q1
   P.add(D * nv * L.ncells);                       // SL_Q2
-  P.add(D * nv * L.pcount);                       // SL_PRIM
-  P.add(visc ? D * L.pcount : 0);                 // SL_TEMP
-  P.add(D * nd * (nv + (visc ? 1 : 0)) * L.pcount);  // SL_G1
-  P.add(D * nd * nv * L.pcount);                  // SL_G2
-  P.add(D * nv * fsum);                           // SL_FLUX
+  const size_t ER = elem_r(p);                    // primitives, gradients, fluxes: the path's type
+  P.add(ER * nv * L.pcount);                      // SL_PRIM
+  P.add(visc ? ER * L.pcount : 0);                // SL_TEMP
+  P.add(ER * nd * (nv + (visc ? 1 : 0)) * L.pcount);  // SL_G1
+  P.add(ER * nd * nv * L.pcount);                 // SL_G2
+  P.add(ER * nv * fsum);                          // SL_FLUX
   P.add(D * nd * L.ncount);                       // SL_NODES
   P.add(mov ? D * nd * L.ncount : 0);             // SL_NVEL
   P.add(D * nd * L.ecount);                       // SL_XC
@@ -285,7 +290,7 @@ struct gbr_ctx {
   size_t ws_bytes;
   Plan plan;
   double* q[3];
-  double *prim, *temp, *g1[3], *g2[3], *flux[3];
+  void *prim, *temp, *g1[3], *g2[3], *flux[3];  // element type double (FP64) or float (mixed)
   double *nodes, *nvel, *xc, *vc, *xd, *mh, *det, *mu, *mt, *fh[3], *fu[3], *ft[3], *gcl, *jac;
   double *sigma, *inflow, *scal;
   int* err;
@@ -528,20 +533,22 @@ gbr_status run_motion(gbr_ctx* c, double stage_c) {
   return GBR_OK;
 }
 
-RhsArgs rhs_args(gbr_ctx* c, const double* q) {
-  RhsArgs A;
+template <class R>
+RhsArgsT<R> rhs_args_r(gbr_ctx* c, const double* q) {
+  RhsArgsT<R> A;
   A.L = c->L;
   A.ph = c->ph;
+  A.pr = phys_r<R>(c->ph);
   A.q = q;
-  A.prim = c->prim;
-  A.temp = c->temp;
+  A.prim = static_cast<R*>(c->prim);
+  A.temp = static_cast<R*>(c->temp);
   for (int d = 0; d < 3; ++d) {
-    A.g1[d] = c->g1[d];
-    A.g2[d] = c->g2[d];
+    A.g1[d] = static_cast<R*>(c->g1[d]);
+    A.g2[d] = static_cast<R*>(c->g2[d]);
     A.fh[d] = c->fh[d];
     A.fu[d] = c->fu[d];
     A.ft[d] = c->ft[d];
-    A.flux[d] = c->flux[d];
+    A.flux[d] = static_cast<R*>(c->flux[d]);
   }
   A.inflow = c->inflow;
   for (int d = 0; d < 3; ++d)
@@ -549,6 +556,7 @@ RhsArgs rhs_args(gbr_ctx* c, const double* q) {
   A.viscous = c->visc;
   return A;
 }
+RhsArgs rhs_args(gbr_ctx* c, const double* q) { return rhs_args_r<double>(c, q); }
 
 gbr_status prof_event(gbr_ctx* c) {
   if (c->ev_used == c->ev.size()) {
@@ -560,8 +568,8 @@ gbr_status prof_event(gbr_ctx* c) {
   return GBR_OK;
 }
 
-template <int ND>
-gbr_status launch_face(gbr_ctx* c, const RhsArgs& A, int d, const Box& b) {
+template <int ND, class R>
+gbr_status launch_face(gbr_ctx* c, const RhsArgsT<R>& A, int d, const Box& b) {
   const unsigned g = grid_of(b, kFaceBlock);
   cudaStream_t st = c->stream;
   if (c->prof) {
@@ -569,11 +577,11 @@ gbr_status launch_face(gbr_ctx* c, const RhsArgs& A, int d, const Box& b) {
     if (s0 != GBR_OK) return s0;
   }
   if (c->visc) {
-    if (c->mov) k_face<ND, true, true><<<g, kFaceBlock, 0, st>>>(A, d, b);
-    else k_face<ND, true, false><<<g, kFaceBlock, 0, st>>>(A, d, b);
+    if (c->mov) k_face<ND, true, true, R><<<g, kFaceBlock, 0, st>>>(A, d, b);
+    else k_face<ND, true, false, R><<<g, kFaceBlock, 0, st>>>(A, d, b);
   } else {
-    if (c->mov) k_face<ND, false, true><<<g, kFaceBlock, 0, st>>>(A, d, b);
-    else k_face<ND, false, false><<<g, kFaceBlock, 0, st>>>(A, d, b);
+    if (c->mov) k_face<ND, false, true, R><<<g, kFaceBlock, 0, st>>>(A, d, b);
+    else k_face<ND, false, false, R><<<g, kFaceBlock, 0, st>>>(A, d, b);
   }
   CKL("k_face");
   if (c->prof) return prof_event(c);
@@ -581,18 +589,18 @@ gbr_status launch_face(gbr_ctx* c, const RhsArgs& A, int d, const Box& b) {
 }
 
 // one evaluation of L(qs): out = L (mode 0) or the RK combination (mode 1)
-template <int ND>
+template <int ND, class R>
 gbr_status run_rhs_nd(gbr_ctx* c, const double* qs, const double* q0, double* out, int mode, double ca, double cb,
                       double cc) {
   const Layout& L = c->L;
   cudaStream_t st = c->stream;
-  RhsArgs A = rhs_args(c, qs);
+  const RhsArgsT<R> A = rhs_args_r<R>(c, qs);
   const RhsBoxes B = rhs_boxes(L);
   const Box bi = B.inner;
-  k_prim<ND><<<grid_of(bi, kBlock), kBlock, 0, st>>>(A, bi);
+  k_prim<ND, R><<<grid_of(bi, kBlock), kBlock, 0, st>>>(A, bi);
   CKL("k_prim");
   for (int d = 0; d < ND; ++d) {
-    k_halo<ND><<<grid_of(B.halo[d], kBlock), kBlock, 0, st>>>(A, d, B.halo[d]);
+    k_halo<ND, R><<<grid_of(B.halo[d], kBlock), kBlock, 0, st>>>(A, d, B.halo[d]);
     CKL("k_halo");
   }
   unsigned g1 = 0, g2 = 0;
@@ -600,17 +608,17 @@ gbr_status run_rhs_nd(gbr_ctx* c, const double* qs, const double* q0, double* ou
     g1 = std::max(g1, grid_of(B.grad1[e], kBlock));
     g2 = std::max(g2, grid_of(B.grad2[e], kBlock));
   }
-  k_grad1<ND><<<dim3(g1, ND), kBlock, 0, st>>>(A, B.grad1[0], B.grad1[1], B.grad1[2]);
+  k_grad1<ND, R><<<dim3(g1, ND), kBlock, 0, st>>>(A, B.grad1[0], B.grad1[1], B.grad1[2]);
   CKL("k_grad1");
-  k_grad2<ND><<<dim3(g2, ND), kBlock, 0, st>>>(A, B.grad2[0], B.grad2[1], B.grad2[2]);
+  k_grad2<ND, R><<<dim3(g2, ND), kBlock, 0, st>>>(A, B.grad2[0], B.grad2[1], B.grad2[2]);
   CKL("k_grad2");
   for (int d = 0; d < ND; ++d) {
-    gbr_status s = launch_face<ND>(c, A, d, B.faces[d]);
+    gbr_status s = launch_face<ND, R>(c, A, d, B.faces[d]);
     if (s != GBR_OK) return s;
   }
-  UpdArgs U;
+  UpdArgsT<R> U;
   U.L = L;
-  for (int d = 0; d < 3; ++d) U.flux[d] = c->flux[d];
+  for (int d = 0; d < 3; ++d) U.flux[d] = static_cast<const R*>(c->flux[d]);
   U.qs = qs;
   U.q0 = q0;
   U.out = out;
@@ -623,16 +631,19 @@ gbr_status run_rhs_nd(gbr_ctx* c, const double* qs, const double* q0, double* ou
   U.cb = cb;
   U.cc = cc;
   U.mode = mode;
-  if (c->mov) k_update<ND, true><<<grid_of(bi, kBlock), kBlock, 0, st>>>(U, bi, c->err);
-  else k_update<ND, false><<<grid_of(bi, kBlock), kBlock, 0, st>>>(U, bi, c->err);
+  if (c->mov) k_update<ND, true, R><<<grid_of(bi, kBlock), kBlock, 0, st>>>(U, bi, c->err);
+  else k_update<ND, false, R><<<grid_of(bi, kBlock), kBlock, 0, st>>>(U, bi, c->err);
   CKL("k_update");
   return GBR_OK;
 }
 
 gbr_status run_rhs(gbr_ctx* c, const double* qs, const double* q0, double* out, int mode, double ca, double cb,
                    double cc) {
-  return c->L.nd == 3 ? run_rhs_nd<3>(c, qs, q0, out, mode, ca, cb, cc)
-                      : run_rhs_nd<2>(c, qs, q0, out, mode, ca, cb, cc);
+  if (c->p.precision == GBR_PREC_MIXED)
+    return c->L.nd == 3 ? run_rhs_nd<3, float>(c, qs, q0, out, mode, ca, cb, cc)
+                        : run_rhs_nd<2, float>(c, qs, q0, out, mode, ca, cb, cc);
+  return c->L.nd == 3 ? run_rhs_nd<3, double>(c, qs, q0, out, mode, ca, cb, cc)
+                      : run_rhs_nd<2, double>(c, qs, q0, out, mode, ca, cb, cc);
 }
 
 gbr_status run_dt(gbr_ctx* c, double cfl) {
@@ -661,15 +672,18 @@ void carve(gbr_ctx* c) {
   const Layout& L = c->L;
   auto ptr = [&](int slot) -> double* { return P.len[slot] ? (double*)(c->ws + P.off[slot]) : nullptr; };
   for (int s = 0; s < 3; ++s) c->q[s] = ptr(SL_Q0 + s);
-  c->prim = ptr(SL_PRIM);
-  c->temp = ptr(SL_TEMP);
+  // arrays of the path's type: offsets in bytes of that type
+  const size_t ER = elem_r(&c->p);
+  auto rptr = [&](int slot, size_t elems) -> void* { return P.len[slot] ? c->ws + P.off[slot] + ER * elems : nullptr; };
+  c->prim = rptr(SL_PRIM, 0);
+  c->temp = rptr(SL_TEMP, 0);
   const int nv = L.nv, nd = L.nd;
   const int n1 = nv + (c->visc ? 1 : 0);
   size_t foff = 0;
   for (int d = 0; d < 3; ++d) {
-    c->g1[d] = (d < nd) ? ptr(SL_G1) + (size_t)d * n1 * L.pcount : nullptr;
-    c->g2[d] = (d < nd) ? ptr(SL_G2) + (size_t)d * nv * L.pcount : nullptr;
-    c->flux[d] = (d < nd) ? ptr(SL_FLUX) + (size_t)nv * foff : nullptr;
+    c->g1[d] = (d < nd) ? rptr(SL_G1, (size_t)d * n1 * L.pcount) : nullptr;
+    c->g2[d] = (d < nd) ? rptr(SL_G2, (size_t)d * nv * L.pcount) : nullptr;
+    c->flux[d] = (d < nd) ? rptr(SL_FLUX, (size_t)nv * foff) : nullptr;
     c->fh[d] = (d < nd) ? ptr(SL_FH) + (size_t)nd * foff : nullptr;
     c->fu[d] = (d < nd && c->visc) ? ptr(SL_FU) + (size_t)nd * nd * foff : nullptr;
     c->ft[d] = (d < nd && c->mov) ? ptr(SL_FT) + foff : nullptr;
@@ -983,10 +997,19 @@ gbr_status gbr_get_field(gbr_ctx* c, int which, int dir, double* out) {
       if ((s = fetch(c->gcl, (size_t)L.ncells, h)) != GBR_OK) return s;
       std::memcpy(out, h.data(), h.size() * sizeof(double));
       return GBR_OK;
-    case GBR_FIELD_FACE_FLUX:
-      if ((s = fetch(c->flux[dir], (size_t)L.nv * L.fcount[dir], h)) != GBR_OK) return s;
+    case GBR_FIELD_FACE_FLUX: {
+      const size_t n = (size_t)L.nv * L.fcount[dir];
+      if (c->p.precision == GBR_PREC_MIXED) {
+        std::vector<float> hf(n);
+        CK(cudaMemcpyAsync(hf.data(), c->flux[dir], n * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "fetch");
+        CK(cudaStreamSynchronize(c->stream), "fetch sync");
+        for (size_t m = 0; m < n; ++m) out[m] = hf[m];
+        return GBR_OK;
+      }
+      if ((s = fetch(static_cast<const double*>(c->flux[dir]), n, h)) != GBR_OK) return s;
       std::memcpy(out, h.data(), h.size() * sizeof(double));
       return GBR_OK;
+    }
     default:
       return fail(c, GBR_EINVAL, "unknown field");
   }
@@ -1066,6 +1089,7 @@ const char* static_param_error(const gbr_params* p) {
   if (!(p->gamma > 1.0)) return "gamma must exceed 1";
   if (p->reynolds > 0.0 && !(p->prandtl > 0.0)) return "prandtl must be positive";
   if (p->sutherland_s > 0.0 && !(p->t_ref > 0.0)) return "t_ref must be positive";
+  if (p->precision != GBR_PREC_FP64) return "only the FP64 path is supported here";
   return nullptr;
 }
 
@@ -1201,7 +1225,7 @@ cudaError_t static_rhs_launches(gbr_ctx& c, const double* q, double* dqdt, cudaS
   }
   UpdArgs U;
   U.L = L;
-  for (int d = 0; d < 3; ++d) U.flux[d] = c.flux[d];
+  for (int d = 0; d < 3; ++d) U.flux[d] = static_cast<const double*>(c.flux[d]);
   U.qs = q;
   U.q0 = q;
   U.out = dqdt;

@@ -237,14 +237,6 @@ GBR_HD double stencil_D_prod(const double* a, const double* b, long long e, long
   return r;
 }
 
-// E6 first derivative (Eq. E6_grads, read with differences)
-GBR_HD double stencil_E6(const double* f, long long e, long long s) {
-  double r = (3.0 / 4.0) * (f[e + s] - f[e - s]);
-  r = gfma(-3.0 / 20.0, f[e + 2 * s] - f[e - 2 * s], r);
-  r = gfma(1.0 / 60.0, f[e + 3 * s] - f[e - 3 * s], r);
-  return r;
-}
-
 // ---------------------------------------------------------------------------
 // Geometry bodies (Sec. 3, Sec. 4, Sec. 6)
 // ---------------------------------------------------------------------------
@@ -394,26 +386,107 @@ GBR_HD void body_motion(const Layout& L, const Motion& M, double st, double ct, 
 // ---------------------------------------------------------------------------
 // Right-hand-side bodies (Sec. 3, Sec. 5)
 // ---------------------------------------------------------------------------
-struct RhsArgs {
+// ---------------------------------------------------------------------------
+// Right-hand side bodies, templated on the compute type R of the reconstruction:
+// R = double is the FP64 path; R = float is the mixed path, where primitives,
+// gradients, characteristic reconstruction, limiter, Riemann and viscous fluxes
+// run and are stored in FP32, while the conserved state, the metrics and 1/J
+// (computed in FP64 by the geometry bodies), the GCL term, the flux divergence
+// and the RK accumulation stay FP64.  Every literal in the templated bodies is
+// written as R(...) so that the float path does no FP64 arithmetic.
+// ---------------------------------------------------------------------------
+template <class R>
+struct PhysR {
+  R gamma, igm1;
+  R mu_ref, suth_s, it_ref;
+  R alpha_d;                 // alpha^D
+  R mp_alpha, mp_beta, mp_eps;
+  R kfac;
+  int sutherland;
+};
+template <class R>
+inline PhysR<R> phys_r(const Phys& ph) {
+  PhysR<R> r;
+  r.gamma = R(ph.gamma);
+  r.igm1 = R(ph.igm1);
+  r.mu_ref = R(ph.mu_ref);
+  r.suth_s = R(ph.suth_s);
+  r.it_ref = R(ph.it_ref);
+  r.alpha_d = R(ph.alpha_d);
+  r.mp_alpha = R(ph.mp_alpha);
+  r.mp_beta = R(ph.mp_beta);
+  r.mp_eps = R(ph.mp_eps);
+  r.kfac = R(ph.kfac);
+  r.sutherland = ph.sutherland;
+  return r;
+}
+
+template <class R>
+struct RhsArgsT {
   Layout L;
   Phys ph;
+  PhysR<R> pr;
   const double* q;      // [nv][ncells] conserved state of the stage
-  double* prim;         // [nv][pcount] primitives with halo
-  double* temp;         // [pcount] T = p/rho (viscous)
-  double* g1[3];        // [nv (+1 T)][pcount] first derivatives along d
-  double* g2[3];        // [nv][pcount] second derivatives along d
-  const double* fh[3];
-  const double* fu[3];
-  const double* ft[3];
-  double* flux[3];      // [nv][fcount] F^ - F^v at interfaces
+  R* prim;              // [nv][pcount] primitives with halo
+  R* temp;              // [pcount] T = p/rho (viscous)
+  R* g1[3];             // [nv (+1 T)][pcount] first derivatives along d
+  R* g2[3];             // [nv][pcount] second derivatives along d
+  const double* fh[3];  // [nd][fcount] hat metrics n^ at interfaces
+  const double* fu[3];  // [nd][nd][fcount] unhatted metrics d xi_e / d x_a at interfaces
+  const double* ft[3];  // [fcount] hat xi_t at interfaces (moving)
+  R* flux[3];           // [nv][fcount] F^ - F^v at interfaces
   const double* inflow; // [nv][nk][nj]
   int bc[3][2];
   int viscous;
 };
+using RhsArgs = RhsArgsT<double>;
 
-// Sec. 2: primitives P = [rho, u.., p] (and T = p/rho, R = 1) at interior cells
-template <int ND>
-GBR_HD void body_prim(const RhsArgs& A, int i, int j, int k) {
+// single-precision helpers of the mixed path (plain compares: FP32 min/max are cheap)
+GBR_HD float grsqrt(float x) {
+#ifdef __CUDA_ARCH__
+  return rsqrtf(x);
+#else
+  return 1.0f / std::sqrt(x);
+#endif
+}
+GBR_HD float gfma(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+  return fmaf(a, b, c);
+#else
+  return a * b + c;
+#endif
+}
+GBR_HD bool is_pos(float x) { return x > 0.0f; }
+GBR_HD bool is_neg(float x) { return x < 0.0f; }
+GBR_HD float gmin(float a, float b) { return a < b ? a : b; }
+GBR_HD float gmax(float a, float b) { return a > b ? a : b; }
+GBR_HD float minmod(float a, float b) {  // App. E
+  if (a > 0.0f && b > 0.0f) return a < b ? a : b;
+  if (a < 0.0f && b < 0.0f) return a > b ? a : b;
+  return 0.0f;
+}
+GBR_HD float gsqrt(float x) {
+#ifdef __CUDA_ARCH__
+  return sqrtf(x);
+#else
+  return std::sqrt(x);
+#endif
+}
+GBR_HD double gsqrt(double x) { return sqrt(x); }
+
+// E6 first derivative (Eq. E6_grads, read with differences)
+template <class R>
+GBR_HD R stencil_E6(const R* f, long long e, long long s) {
+  R r = R(3.0 / 4.0) * (f[e + s] - f[e - s]);
+  r = gfma(R(-3.0 / 20.0), f[e + 2 * s] - f[e - 2 * s], r);
+  r = gfma(R(1.0 / 60.0), f[e + 3 * s] - f[e - 3 * s], r);
+  return r;
+}
+
+// Sec. 2: primitives P = [rho, u.., p] (and T = p/rho, R = 1) at interior cells,
+// evaluated in FP64 from the FP64 state and stored in R
+template <int ND, class R>
+GBR_HD void body_prim(const RhsArgsT<R>& A, int i, int j, int k) {
   constexpr int NV = ND + 2;
   const Layout& L = A.L;
   const long long c = cidx(L, i, j, k), p = pidx(L, i, j, k);
@@ -421,22 +494,22 @@ GBR_HD void body_prim(const RhsArgs& A, int i, int j, int k) {
   const double rho = A.q[c];
   const double ir = 1.0 / rho;
   double ke = 0.0;
-  A.prim[p] = rho;
+  A.prim[p] = R(rho);
   for (int a = 0; a < ND; ++a) {
     const double m = A.q[(1 + a) * NC + c];
     const double u = m * ir;
-    A.prim[(1 + a) * PC + p] = u;
+    A.prim[(1 + a) * PC + p] = R(u);
     ke = gfma(m, u, ke);
   }
   const double pr = A.ph.gm1 * (A.q[(NV - 1) * NC + c] - 0.5 * ke);
-  A.prim[(NV - 1) * PC + p] = pr;
-  if (A.viscous) A.temp[p] = pr * ir;
+  A.prim[(NV - 1) * PC + p] = R(pr);
+  if (A.viscous) A.temp[p] = R(pr * ir);
 }
 
 // ghost layers along axis d for the cross-section cell (i, j, k) (coordinate d ignored):
 // periodic copy, zero gradient, or Dirichlet inflow on the x-low side
-template <int ND>
-GBR_HD void body_halo(const RhsArgs& A, int d, int i, int j, int k) {
+template <int ND, class R>
+GBR_HD void body_halo(const RhsArgsT<R>& A, int d, int i, int j, int k) {
   constexpr int NV = ND + 2;
   const Layout& L = A.L;
   const long long PC = L.pcount, s = L.ps[d];
@@ -446,7 +519,7 @@ GBR_HD void body_halo(const RhsArgs& A, int d, int i, int j, int k) {
   const int n = L.n[d];
   const int nf = NV + (A.viscous ? 1 : 0);
   for (int f = 0; f < nf; ++f) {
-    double* F = (f < NV) ? A.prim + f * PC : A.temp;
+    R* F = (f < NV) ? A.prim + f * PC : A.temp;
     for (int g = 1; g <= H; ++g) {
       const long long lo = base - g * s, hi = base + (n - 1 + g) * s;
       if (L.per[d]) {
@@ -456,9 +529,9 @@ GBR_HD void body_halo(const RhsArgs& A, int d, int i, int j, int k) {
         if (A.bc[d][0] == 2) {
           const long long ib = ((long long)k * L.n[1] + j);
           if (f < NV) {
-            F[lo] = A.inflow[f * L.n[1] * L.n[2] + ib];
+            F[lo] = R(A.inflow[f * L.n[1] * L.n[2] + ib]);
           } else {
-            F[lo] = A.inflow[(NV - 1) * L.n[1] * L.n[2] + ib] / A.inflow[ib];
+            F[lo] = R(A.inflow[(NV - 1) * L.n[1] * L.n[2] + ib] / A.inflow[ib]);
           }
         } else {
           F[lo] = F[base];
@@ -470,8 +543,8 @@ GBR_HD void body_halo(const RhsArgs& A, int d, int i, int j, int k) {
 }
 
 // Sec. 5.1 step 1: E6 first derivatives along e (primitives and T)
-template <int ND>
-GBR_HD void body_grad1(const RhsArgs& A, int e, int i, int j, int k) {
+template <int ND, class R>
+GBR_HD void body_grad1(const RhsArgsT<R>& A, int e, int i, int j, int k) {
   constexpr int NV = ND + 2;
   const Layout& L = A.L;
   const long long PC = L.pcount, p = pidx(L, i, j, k), s = L.ps[e];
@@ -480,34 +553,34 @@ GBR_HD void body_grad1(const RhsArgs& A, int e, int i, int j, int k) {
 }
 
 // Sec. 5.1 step 1: f''_i = 2 (f_{i+1} - 2 f_i + f_{i-1}) - 0.5 (f'_{i+1} - f'_{i-1})
-template <int ND>
-GBR_HD void body_grad2(const RhsArgs& A, int e, int i, int j, int k) {
+template <int ND, class R>
+GBR_HD void body_grad2(const RhsArgsT<R>& A, int e, int i, int j, int k) {
   constexpr int NV = ND + 2;
   const Layout& L = A.L;
   const long long PC = L.pcount, p = pidx(L, i, j, k), s = L.ps[e];
   for (int c = 0; c < NV; ++c) {
-    const double* f = A.prim + c * PC;
-    const double* f1 = A.g1[e] + c * PC;
-    A.g2[e][c * PC + p] = 2.0 * (f[p + s] - 2.0 * f[p] + f[p - s]) - 0.5 * (f1[p + s] - f1[p - s]);
+    const R* f = A.prim + c * PC;
+    const R* f1 = A.g1[e] + c * PC;
+    A.g2[e][c * PC + p] = R(2) * (f[p + s] - R(2) * f[p] + f[p - s]) - R(0.5) * (f1[p + s] - f1[p - s]);
   }
 }
 
 // App. A projection x -> R^{-1} x for the face eigenvectors (unit normal nu,
 // face rho*a = ra and a^2).  Row order: U - a, U (x2 or x3), U + a.
-template <int ND>
-GBR_HD void project(const double* nu, double ra, double a2, const double* x, double* W) {
+template <int ND, class R>
+GBR_HD void project(const R* nu, R ra, R a2, const R* x, R* W) {
   if (ND == 3) {
-    const double s = gfma(nu[0], x[1], gfma(nu[1], x[2], nu[2] * x[3]));
-    const double t = ra * s;
-    const double e = gfma(a2, x[0], -x[4]);
+    const R s = gfma(nu[0], x[1], gfma(nu[1], x[2], nu[2] * x[3]));
+    const R t = ra * s;
+    const R e = gfma(a2, x[0], -x[4]);
     W[0] = x[4] - t;
     W[1] = gfma(nu[0], e, gfma(nu[1], x[3], -nu[2] * x[2]));
     W[2] = gfma(nu[2], e, gfma(nu[0], x[2], -nu[1] * x[1]));
     W[3] = gfma(-nu[1], e, gfma(nu[0], x[3], -nu[2] * x[1]));
     W[4] = x[4] + t;
   } else {
-    const double s = gfma(nu[0], x[1], nu[1] * x[2]);
-    const double t = ra * s;
+    const R s = gfma(nu[0], x[1], nu[1] * x[2]);
+    const R t = ra * s;
     W[0] = x[3] - t;
     W[1] = gfma(a2, x[0], -x[3]);
     W[2] = gfma(nu[0], x[2], -nu[1] * x[1]);
@@ -516,19 +589,19 @@ GBR_HD void project(const double* nu, double ra, double a2, const double* x, dou
 }
 
 // App. A back-projection d -> R d
-template <int ND>
-GBR_HD void back_project(const double* nu, double ira, double ia2, const double* dl, double* out) {
+template <int ND, class R>
+GBR_HD void back_project(const R* nu, R ira, R ia2, const R* dl, R* out) {
   if (ND == 3) {
-    const double h = 0.5 * (dl[0] + dl[4]);
-    const double q = 0.5 * (dl[4] - dl[0]) * ira;
+    const R h = R(0.5) * (dl[0] + dl[4]);
+    const R q = R(0.5) * (dl[4] - dl[0]) * ira;
     out[0] = ia2 * (h + gfma(nu[0], dl[1], gfma(nu[2], dl[2], -nu[1] * dl[3])));
     out[1] = gfma(nu[0], q, gfma(-nu[1], dl[2], -nu[2] * dl[3]));
     out[2] = gfma(nu[1], q, gfma(-nu[2], dl[1], nu[0] * dl[2]));
     out[3] = gfma(nu[2], q, gfma(nu[1], dl[1], nu[0] * dl[3]));
     out[4] = h;
   } else {
-    const double h = 0.5 * (dl[0] + dl[3]);
-    const double q = 0.5 * (dl[3] - dl[0]) * ira;
+    const R h = R(0.5) * (dl[0] + dl[3]);
+    const R q = R(0.5) * (dl[3] - dl[0]) * ira;
     out[0] = ia2 * (h + dl[1]);
     out[1] = gfma(nu[0], q, -nu[1] * dl[2]);
     out[2] = gfma(nu[1], q, nu[0] * dl[2]);
@@ -540,11 +613,11 @@ GBR_HD void back_project(const double* nu, double ira, double ia2, const double*
 //   f  = W_face - W_base,  dm = W_base - W_up,  dp = W_down - W_base,
 //   du, db, dd = curvatures d of the up, base and down cells.
 // mp_keep is the test (W^L - W_base)(W^L - W^MP) <= eps that leaves the state
-// unchanged; mp_bound returns the limited W_face - W_base when it fails.  The
-// products and sums are FP64; every comparison, min, max, minmod and the
-// median work on the bit patterns (integer pipe) and select one of their
+// unchanged; mp_bound returns the limited W_face - W_base when it fails.
+// FP64: the products and sums are FP64; every comparison, min, max, minmod and
+// the median work on the bit patterns (integer pipe) and select one of their
 // arguments exactly.
-GBR_HD bool mp_keep(double f, double dm, double dp, const Phys& ph) {
+GBR_HD bool mp_keep(double f, double dm, double dp, const PhysR<double>& ph) {
   const long long bf = dbits(f);
   const long long bmp = bminmod(dbits(dp), dbits(ph.mp_beta * dm));  // W^MP - W_base
   // exactly non-positive product when f lies between 0 and W^MP - W_base
@@ -552,7 +625,7 @@ GBR_HD bool mp_keep(double f, double dm, double dp, const Phys& ph) {
   const bool between = (km >= 0) ? (kf >= 0 && kf <= km) : (kf <= 0 && kf >= km);
   return (between && ke >= 0) || okey(f * (f - bitsd(bmp))) <= ke;
 }
-GBR_HD double mp_bound(double f, double dm, double dp, double du, double db, double dd, const Phys& ph) {
+GBR_HD double mp_bound(double f, double dm, double dp, double du, double db, double dd, const PhysR<double>& ph) {
   const double dmp = bitsd(bminmod(dbits(db), dbits(dd)));  // d^M_{i+1/2}
   const double dmm = bitsd(bminmod(dbits(du), dbits(db)));  // d^M_{i-1/2}
   const long long bdp = dbits(dp), bf = dbits(f);
@@ -565,21 +638,35 @@ GBR_HD double mp_bound(double f, double dm, double dp, double du, double db, dou
   // W^L + minmod(W^min - W^L, W^max - W^L) is the median of (W^L, W^min, W^max)
   return bitsd(bmax(bmin(bf, lo), bmin(bmax(bf, lo), hi)));
 }
+// FP32 (mixed path): the same steps with plain single-precision compares
+GBR_HD bool mp_keep(float f, float dm, float dp, const PhysR<float>& ph) {
+  const float mmp = minmod(dp, ph.mp_beta * dm);
+  return f * (f - mmp) <= ph.mp_eps;
+}
+GBR_HD float mp_bound(float f, float dm, float dp, float du, float db, float dd, const PhysR<float>& ph) {
+  const float dmp = minmod(db, dd);
+  const float dmm = minmod(du, db);
+  const float md = 0.5f * (dp - dmp);
+  const float ul = ph.mp_alpha * dm;
+  const float lc = gfma(4.0f / 3.0f, dmm, 0.5f * dm);
+  const float lo = gmax(gmin(gmin(0.0f, dp), md), gmin(gmin(0.0f, ul), lc));
+  const float hi = gmin(gmax(gmax(0.0f, dp), md), gmax(gmax(0.0f, ul), lc));
+  return gmax(gmin(f, lo), gmin(gmax(f, lo), hi));
+}
 
 // Sec. 5.1.1 HLLC with grid motion; P = [rho, u.., p]
-template <int ND>
-GBR_HD void hllc(const double* PL, const double* PR, const double* nh, double nn2, double inn, double nt,
-                 const Phys& ph, double* F) {
+template <int ND, class R>
+GBR_HD void hllc(const R* PL, const R* PR, const R* nh, R nn2, R inn, R nt, const PhysR<R>& ph, R* F) {
   constexpr int NV = ND + 2;
-  const double nn = nn2 * inn;
-  const double inn2 = inn * inn;
+  const R nn = nn2 * inn;
+  const R inn2 = inn * inn;
   // left and right states (kept in scalars: no runtime-indexed arrays)
-  const double rl = PL[0], rr = PR[0];
-  const double pl = PL[NV - 1], pr = PR[NV - 1];
+  const R rl = PL[0], rr = PR[0];
+  const R pl = PL[NV - 1], pr = PR[NV - 1];
   // t = 1/sqrt(gamma p rho) = 1/(rho c): c = gamma p t and 1/rho = gamma p t^2, no division
-  const double gpl = ph.gamma * pl, gpr = ph.gamma * pr;
-  const double tl = grsqrt(gpl * rl), tr = grsqrt(gpr * rr);
-  double q2l = 0.0, q2r = 0.0, Ul = nt, Ur = nt;
+  const R gpl = ph.gamma * pl, gpr = ph.gamma * pr;
+  const R tl = grsqrt(gpl * rl), tr = grsqrt(gpr * rr);
+  R q2l = R(0), q2r = R(0), Ul = nt, Ur = nt;
   #pragma unroll
   for (int a = 0; a < ND; ++a) {
     q2l = gfma(PL[1 + a], PL[1 + a], q2l);
@@ -587,18 +674,18 @@ GBR_HD void hllc(const double* PL, const double* PR, const double* nh, double nn
     Ul = gfma(nh[a], PL[1 + a], Ul);  // contravariant velocity, Sec. 2
     Ur = gfma(nh[a], PR[1 + a], Ur);
   }
-  const double El = gfma(pl, ph.igm1, 0.5 * rl * q2l), Er = gfma(pr, ph.igm1, 0.5 * rr * q2r);
-  const double cl = gpl * tl, cr = gpr * tr;  // speeds of sound
-  const double SL = gmin(gfma(-cl, nn, Ul), gfma(-cr, nn, Ur));
-  const double SR = gmax(gfma(cl, nn, Ul), gfma(cr, nn, Ur));
-  const double aL = rl * (SL - Ul), aR = rr * (SR - Ur);
-  const double Ss = (aR * Ur - aL * Ul + (pl - pr) * nn2) / (aR - aL);
+  const R El = gfma(pl, ph.igm1, R(0.5) * rl * q2l), Er = gfma(pr, ph.igm1, R(0.5) * rr * q2r);
+  const R cl = gpl * tl, cr = gpr * tr;  // speeds of sound
+  const R SL = gmin(gfma(-cl, nn, Ul), gfma(-cr, nn, Ur));
+  const R SR = gmax(gfma(cl, nn, Ul), gfma(cr, nn, Ur));
+  const R aL = rl * (SL - Ul), aR = rr * (SR - Ur);
+  const R Ss = (aR * Ur - aL * Ul + (pl - pr) * nn2) / (aR - aL);
   // branches of Sec. 5.1.1: S^L >= 0 -> F^L; S^L < 0 <= S* -> F*L; S* < 0 < S^R -> F*R; else F^R
   const bool left = !is_neg(SL) || !is_neg(Ss);
   const bool star = is_neg(SL) && (left || is_pos(SR));
-  const double rs = left ? rl : rr, ps = left ? pl : pr;
-  const double Us = left ? Ul : Ur, Es = left ? El : Er, S = left ? SL : SR;
-  double us[ND];
+  const R rs = left ? rl : rr, ps = left ? pl : pr;
+  const R Us = left ? Ul : Ur, Es = left ? El : Er, S = left ? SL : SR;
+  R us[ND];
   #pragma unroll
   for (int a = 0; a < ND; ++a) us[a] = left ? PL[1 + a] : PR[1 + a];
   F[0] = rs * Us;
@@ -607,18 +694,18 @@ GBR_HD void hllc(const double* PL, const double* PR, const double* nh, double nn
   F[NV - 1] = gfma(Es + ps, Us, -nt * ps);
   if (star) {
     // Q*K = rho (S - U)/(S - S*) [1, u + n^ (S* - U)/|n^|^2, E/rho + (S* - U)((S* - xi_t)/|n^|^2 + p/(rho (S - U)))]
-    const double rA = rs * (S - Us);
-    const double B = S - Ss;
-    const double inv = 1.0 / (rA * B);
-    const double fac = rA * rA * inv;      // rho (S - U) / (S - S*)
-    const double p_rA = ps * B * inv;      // p / (rho (S - U))
-    const double dS = Ss - Us;
-    const double w = dS * inn2;
+    const R rA = rs * (S - Us);
+    const R B = S - Ss;
+    const R inv = R(1) / (rA * B);
+    const R fac = rA * rA * inv;      // rho (S - U) / (S - S*)
+    const R p_rA = ps * B * inv;      // p / (rho (S - U))
+    const R dS = Ss - Us;
+    const R w = dS * inn2;
     F[0] += S * (fac - rs);
     #pragma unroll
     for (int a = 0; a < ND; ++a) F[1 + a] += S * (fac * gfma(nh[a], w, us[a]) - rs * us[a]);
-    const double ts = left ? tl : tr, gps = left ? gpl : gpr;
-    const double eb = gfma(Es * gps, ts * ts, dS * gfma(Ss - nt, inn2, p_rA));  // E/rho + ...
+    const R ts = left ? tl : tr, gps = left ? gpl : gpr;
+    const R eb = gfma(Es * gps, ts * ts, dS * gfma(Ss - nt, inn2, p_rA));  // E/rho + ...
     F[NV - 1] += S * gfma(fac, eb, -Es);
   }
 }
@@ -628,49 +715,49 @@ GBR_HD void hllc(const double* PL, const double* PR, const double* nh, double nn
 // neighbouring cells and the limited states are returned relative to the base
 // cell (P^L = P_i + R dW_L), which is the same arithmetic as projecting the
 // cell values themselves, in a different rounding order.
-template <int ND, bool VISC, bool MOV>
-GBR_HD void body_face(const RhsArgs& A, int d, int i, int j, int k) {
+template <int ND, bool VISC, bool MOV, class R>
+GBR_HD void body_face(const RhsArgsT<R>& A, int d, int i, int j, int k) {
   constexpr int NV = ND + 2;
   const Layout& L = A.L;
-  const Phys& ph = A.ph;
+  const PhysR<R>& ph = A.pr;
   const long long PC = L.pcount, s = L.ps[d];
   const long long p1 = pidx(L, i, j, k);
   const long long pp[4] = {p1 - s, p1, p1 + s, p1 + 2 * s};
   const long long FC = L.fcount[d];
   const long long f = fidx(L, d, i, j, k);
-  const double* P = A.prim;
+  const R* P = A.prim;
 
-  double nh[ND];
-  double nn2 = 0.0;
+  R nh[ND];
+  R nn2 = R(0);
   #pragma unroll
   for (int a = 0; a < ND; ++a) {
-    nh[a] = A.fh[d][a * FC + f];
+    nh[a] = R(A.fh[d][a * FC + f]);
     nn2 = gfma(nh[a], nh[a], nn2);
   }
-  const double nt = MOV ? A.ft[d][f] : 0.0;
-  const double inn = grsqrt(nn2);
-  double nu[ND];
+  const R nt = MOV ? R(A.ft[d][f]) : R(0);
+  const R inn = grsqrt(nn2);
+  R nu[ND];
   #pragma unroll
   for (int a = 0; a < ND; ++a) nu[a] = nh[a] * inn;
   // face state of the eigenvectors: mean of rho and p of cells i, i+1 (reading A6)
-  const double rb = 0.5 * (P[pp[1]] + P[pp[2]]);
-  const double pb = 0.5 * (P[(NV - 1) * PC + pp[1]] + P[(NV - 1) * PC + pp[2]]);
+  const R rb = R(0.5) * (P[pp[1]] + P[pp[2]]);
+  const R pb = R(0.5) * (P[(NV - 1) * PC + pp[1]] + P[(NV - 1) * PC + pp[2]]);
   // a = sqrt(gamma p / rho): with t = 1/sqrt(gamma p rho), rho a = gamma p rho t, 1/(rho a) = t,
   // a = gamma p t and 1/a = rho t -- one reciprocal square root, no division
-  const double gp = ph.gamma * pb;
-  const double t = grsqrt(gp * rb);
-  const double ira = t;
-  const double ra = gp * rb * t;
-  const double a_ = gp * t;
-  const double a2 = a_ * a_;
-  const double ia = rb * t;
-  const double ia2 = ia * ia;
+  const R gp = ph.gamma * pb;
+  const R t = grsqrt(gp * rb);
+  const R ira = t;
+  const R ra = gp * rb * t;
+  const R a_ = gp * t;
+  const R a2 = a_ * a_;
+  const R ia = rb * t;
+  const R ia2 = ia * ia;
 
   // projected differences dW = R^-1 (P_{m+1} - P_m) of the four cells i-1 .. i+2
-  double Wd[3][NV];
+  R Wd[3][NV];
   #pragma unroll
   for (int m = 0; m < 3; ++m) {
-    double x[NV];
+    R x[NV];
     #pragma unroll
     for (int c = 0; c < NV; ++c) x[c] = P[c * PC + pp[m + 1]] - P[c * PC + pp[m]];
     project<ND>(nu, ra, a2, x, Wd[m]);
@@ -678,14 +765,16 @@ GBR_HD void body_face(const RhsArgs& A, int d, int i, int j, int k) {
   // Eq. (legendre_polys) unlimited states relative to the base cells, projected
   // after combining: W^L - W_i = R^-1 (f'_i / 2 + f''_i / 12),
   // W^R - W_{i+1} = R^-1 (-f'_{i+1} / 2 + f''_{i+1} / 12)
-  double dL[NV], dR[NV];
+  R dL[NV], dR[NV];
   {
-    double x[NV];
+    R x[NV];
     #pragma unroll
-    for (int c = 0; c < NV; ++c) x[c] = gfma(0.5, A.g1[d][c * PC + pp[1]], A.g2[d][c * PC + pp[1]] * (1.0 / 12.0));
+    for (int c = 0; c < NV; ++c)
+      x[c] = gfma(R(0.5), A.g1[d][c * PC + pp[1]], A.g2[d][c * PC + pp[1]] * R(1.0 / 12.0));
     project<ND>(nu, ra, a2, x, dL);
     #pragma unroll
-    for (int c = 0; c < NV; ++c) x[c] = gfma(-0.5, A.g1[d][c * PC + pp[2]], A.g2[d][c * PC + pp[2]] * (1.0 / 12.0));
+    for (int c = 0; c < NV; ++c)
+      x[c] = gfma(R(-0.5), A.g1[d][c * PC + pp[2]], A.g2[d][c * PC + pp[2]] * R(1.0 / 12.0));
     project<ND>(nu, ra, a2, x, dR);
   }
   // App. E: the curvatures are projected only where some characteristic field
@@ -697,10 +786,10 @@ GBR_HD void body_face(const RhsArgs& A, int d, int i, int j, int k) {
     limit |= mp_keep(dR[c], -Wd[2][c], -Wd[1][c], ph) ? 0u : (1u << (NV + c));
   }
   if (limit) {
-    double W2[4][NV];
+    R W2[4][NV];
     #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      double x[NV];
+      R x[NV];
       #pragma unroll
       for (int c = 0; c < NV; ++c) x[c] = A.g2[d][c * PC + pp[m]];
       project<ND>(nu, ra, a2, x, W2[m]);
@@ -712,7 +801,7 @@ GBR_HD void body_face(const RhsArgs& A, int d, int i, int j, int k) {
         dR[c] = mp_bound(dR[c], -Wd[2][c], -Wd[1][c], W2[3][c], W2[2][c], W2[1][c], ph);
     }
   }
-  double PL[NV], PR[NV];
+  R PL[NV], PR[NV];
   back_project<ND>(nu, ira, ia2, dL, PL);
   back_project<ND>(nu, ira, ia2, dR, PR);
   #pragma unroll
@@ -720,22 +809,22 @@ GBR_HD void body_face(const RhsArgs& A, int d, int i, int j, int k) {
     PL[c] += P[c * PC + pp[1]];
     PR[c] += P[c * PC + pp[2]];
   }
-  double F[NV];
+  R F[NV];
   hllc<ND>(PL, PR, nh, nn2, inn, nt, ph, F);
 
   if (VISC) {
     // Sec. 5.2 alpha-damping on [u.., T].  gc2[v][e] = 2 d(phi_v)/d(xi_e) at the interface:
     // Eq. (AD-eqn1) along the sweep, the sum of the two cells' gradients across it (reading
     // A11); the factor 1/2 is folded into mu, lambda and kappa below.
-    double gc2[ND + 1][ND];
-    double phif[ND + 1];
+    R gc2[ND + 1][ND];
+    R phif[ND + 1];
     #pragma unroll
     for (int v = 0; v <= ND; ++v) {
-      const double* val = (v < ND) ? P + (1 + v) * PC : A.temp;
+      const R* val = (v < ND) ? P + (1 + v) * PC : A.temp;
       const int gi = (v < ND) ? (1 + v) : NV;
-      const double gd1 = A.g1[d][gi * PC + pp[1]], gd2 = A.g1[d][gi * PC + pp[2]];
-      const double phiL = gfma(0.5, gd1, val[pp[1]]);   // Eq. (AD-eqn2), beta^D = 0
-      const double phiR = gfma(-0.5, gd2, val[pp[2]]);
+      const R gd1 = A.g1[d][gi * PC + pp[1]], gd2 = A.g1[d][gi * PC + pp[2]];
+      const R phiL = gfma(R(0.5), gd1, val[pp[1]]);   // Eq. (AD-eqn2), beta^D = 0
+      const R phiR = gfma(R(-0.5), gd2, val[pp[2]]);
       #pragma unroll
       for (int e = 0; e < ND; ++e) {
         if (e == d) {
@@ -744,7 +833,7 @@ GBR_HD void body_face(const RhsArgs& A, int d, int i, int j, int k) {
           gc2[v][e] = A.g1[e][gi * PC + pp[1]] + A.g1[e][gi * PC + pp[2]];
         }
       }
-      phif[v] = 0.5 * (phiL + phiR);
+      phif[v] = R(0.5) * (phiL + phiR);
     }
     // The flux needs only tau n^ and beta . n^ (Eq. shear-str, thermal-work), so the chain rule
     // d/dx_a = sum_e (d xi_e/d x_a) d/d xi_e (Eq. AD-eqn3) is contracted with n^ first:
@@ -753,15 +842,15 @@ GBR_HD void body_face(const RhsArgs& A, int d, int i, int j, int k) {
     //   div u = sum_a sum_e xi_e,x_a du_a/dxi_e,  grad T . n^ = sum_e m_e dT/dxi_e,
     //   beta . n^ = kappa grad T . n^ + u . (tau n^)   (tau symmetric)
     const double* fu = A.fu[d];
-    double xe[ND][ND];  // xe[e][a] = d xi_e / d x_a at the interface
+    R xe[ND][ND];  // xe[e][a] = d xi_e / d x_a at the interface
     #pragma unroll
     for (int e = 0; e < ND; ++e)
       #pragma unroll
-      for (int a = 0; a < ND; ++a) xe[e][a] = fu[(e * ND + a) * FC + f];
-    double m[ND], sv[ND];
+      for (int a = 0; a < ND; ++a) xe[e][a] = R(fu[(e * ND + a) * FC + f]);
+    R m[ND], sv[ND];
     #pragma unroll
     for (int e = 0; e < ND; ++e) {
-      double acc = xe[e][0] * nh[0], acs = nh[0] * gc2[0][e];
+      R acc = xe[e][0] * nh[0], acs = nh[0] * gc2[0][e];
       #pragma unroll
       for (int b = 1; b < ND; ++b) {
         acc = gfma(xe[e][b], nh[b], acc);
@@ -770,44 +859,46 @@ GBR_HD void body_face(const RhsArgs& A, int d, int i, int j, int k) {
       m[e] = acc;
       sv[e] = acs;
     }
-    double mu = ph.mu_ref;
+    R mu = ph.mu_ref;
     if (ph.sutherland) {
-      const double th = phif[ND] * ph.it_ref;
-      mu = ph.mu_ref * (th * sqrt(th)) * ((1.0 + ph.suth_s) / (th + ph.suth_s));
+      const R th = phif[ND] * ph.it_ref;
+      mu = ph.mu_ref * (th * gsqrt(th)) * ((R(1) + ph.suth_s) / (th + ph.suth_s));
     }
-    const double hmu = 0.5 * mu;
-    double div2 = 0.0;
+    const R hmu = R(0.5) * mu;
+    R div2 = R(0);
     #pragma unroll
     for (int a = 0; a < ND; ++a)
       #pragma unroll
       for (int e = 0; e < ND; ++e) div2 = gfma(xe[e][a], gc2[a][e], div2);
-    const double hlamdiv = (-1.0 / 3.0) * mu * div2;  // lambda div u, lambda = -2/3 mu
-    double bn = 0.0;
+    const R hlamdiv = R(-1.0 / 3.0) * mu * div2;  // lambda div u, lambda = -2/3 mu
+    R bn = R(0);
     #pragma unroll
     for (int a = 0; a < ND; ++a) {
-      double t1 = 0.0, t2 = 0.0;
+      R t1 = R(0), t2 = R(0);
       #pragma unroll
       for (int e = 0; e < ND; ++e) {
         t1 = gfma(m[e], gc2[a][e], t1);
         t2 = gfma(xe[e][a], sv[e], t2);
       }
-      const double taun = gfma(hmu, t1 + t2, hlamdiv * nh[a]);  // (tau n^)_a
+      const R taun = gfma(hmu, t1 + t2, hlamdiv * nh[a]);  // (tau n^)_a
       F[1 + a] -= taun;
       bn = gfma(phif[a], taun, bn);
     }
-    double gTn = 0.0;
+    R gTn = R(0);
     #pragma unroll
     for (int e = 0; e < ND; ++e) gTn = gfma(m[e], gc2[ND][e], gTn);
-    F[NV - 1] -= gfma(0.5 * mu * ph.kfac, gTn, bn);
+    F[NV - 1] -= gfma(R(0.5) * mu * ph.kfac, gTn, bn);
   }
   #pragma unroll
   for (int c = 0; c < NV; ++c) A.flux[d][c * FC + f] = F[c];
 }
 
-// Sec. 3 divergence, Sec. 4 time split, App. B stage combination.
-struct UpdArgs {
+// Sec. 3 divergence, Sec. 4 time split, App. B stage combination (FP64; the
+// interface fluxes are read in the path's type R and accumulated in FP64).
+template <class R>
+struct UpdArgsT {
   Layout L;
-  const double* flux[3];
+  const R* flux[3];
   const double* qs;     // state of this stage
   const double* q0;     // Q^n
   double* out;          // new state (mode 1) or L(Q) (mode 0)
@@ -819,9 +910,10 @@ struct UpdArgs {
   double ca, cb, cc;    // out = ca q0 + cb qs + cc dt L
   int mode;             // 0: out = L, 1: RK combination
 };
+using UpdArgs = UpdArgsT<double>;
 
-template <int ND, bool MOV>
-GBR_HD bool body_update(const UpdArgs& U, int i, int j, int k) {
+template <int ND, bool MOV, class R>
+GBR_HD bool body_update(const UpdArgsT<R>& U, int i, int j, int k) {
   constexpr int NV = ND + 2;
   const Layout& L = U.L;
   const long long c = cidx(L, i, j, k), NC = L.ncells;
@@ -833,7 +925,7 @@ GBR_HD bool body_update(const UpdArgs& U, int i, int j, int k) {
     for (int d = 0; d < ND; ++d) {
       const long long fhi = fidx(L, d, i, j, k);
       const long long FC = L.fcount[d];
-      res = res - (U.flux[d][v * FC + fhi] - U.flux[d][v * FC + fhi - L.fs[d][d]]);
+      res = res - ((double)U.flux[d][v * FC + fhi] - (double)U.flux[d][v * FC + fhi - L.fs[d][d]]);
     }
     const double qv = U.qs[v * NC + c];
     double Lv = MOV ? J * gfma(-U.gcl[c], qv, res) : J * res;

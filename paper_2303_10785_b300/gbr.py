@@ -18,6 +18,7 @@ GBR_OK, GBR_EINVAL, GBR_ENOMEM, GBR_ECUDA, GBR_ENONFINITE, GBR_ETIMEOUT, GBR_EST
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENONFINITE", "ETIMEOUT", "ESTATE"]
 (GBR_FIELD_CELL_METRICS, GBR_FIELD_CELL_DET, GBR_FIELD_CELL_TIME, GBR_FIELD_FACE_HAT, GBR_FIELD_FACE_UNHAT,
  GBR_FIELD_FACE_TIME, GBR_FIELD_GCL, GBR_FIELD_FACE_FLUX) = range(8)
+GBR_PREC_FP64, GBR_PREC_MIXED = 0, 1
 
 
 class gbr_params(ctypes.Structure):
@@ -37,6 +38,7 @@ class gbr_params(ctypes.Structure):
         ("mp_beta", ctypes.c_double),
         ("mp_eps", ctypes.c_double),
         ("moving", ctypes.c_int),
+        ("precision", ctypes.c_int),
     ]
 
 
@@ -126,6 +128,7 @@ def make_params(case):
                 "mp_eps"):
         setattr(p, key, float(case[key]))
     p.moving = int(case.get("moving", 0))
+    p.precision = {"fp64": GBR_PREC_FP64, "mixed": GBR_PREC_MIXED}[case.get("precision", "fp64")]
     return p
 
 

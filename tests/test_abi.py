@@ -45,9 +45,14 @@ def test_workspace_bytes(lib):
     assert lib.gbr_workspace_bytes(ctypes.byref(p3)) < nb
     p4 = gbr.make_params(I.case_params(3, (32, 24, 16), reynolds=100.0, moving=1))
     assert lib.gbr_workspace_bytes(ctypes.byref(p4)) > nb
+    # the mixed path stores primitives, gradients and fluxes in FP32
+    p5 = gbr.make_params(I.case_params(3, (32, 24, 16), reynolds=100.0, precision="mixed"))
+    assert p5.precision == gbr.GBR_PREC_MIXED
+    assert 0 < lib.gbr_workspace_bytes(ctypes.byref(p5)) < nb
 
 
-@pytest.mark.parametrize("bad", [dict(ndim=4), dict(n=(4, 8, 8)), dict(gamma=1.0), dict(ghost=True)])
+@pytest.mark.parametrize("bad", [dict(ndim=4), dict(n=(4, 8, 8)), dict(gamma=1.0), dict(ghost=True),
+                                 dict(precision=7)])
 def test_invalid_params_rejected(lib, bad):
     kw = dict(reynolds=0.0)
     nd = bad.get("ndim", 3)
@@ -60,6 +65,8 @@ def test_invalid_params_rejected(lib, bad):
         case["periodic"] = (0, 1, 1)
         case["ghost_nodes"] = 4
     p = gbr.make_params(case)
+    if "precision" in bad:
+        p.precision = bad["precision"]
     assert lib.gbr_workspace_bytes(ctypes.byref(p)) == 0
     out = ctypes.c_void_p()
     dummy = (ctypes.c_double * 8)()
