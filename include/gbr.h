@@ -190,6 +190,58 @@ gbr_status gbr_profile(gbr_ctx* c, int enable, double* face_ms, long long* face_
 gbr_status gbr_rhs_static(const gbr_params* p, const double* nodes, const double* node_vel, const double* q,
                           double* dqdt, void* stream, char* msg, size_t msg_len);
 
+/* ---------------------------------------------------------------------------
+ * Batched stepping (not in the paper, whose solver runs one job per GPU).
+ * A batch advances many contexts together: per kind of member (ndim, viscous,
+ * precision) every phase of an SSP-RK3 step is one launch over a
+ * block -> (member, tile) work list, and the whole step (time steps on the
+ * device, three stages, time advance) is captured as one CUDA graph, replayed
+ * until the membership changes.  Each member keeps its own state, metrics, time
+ * step and error flag; its results are bitwise those of gbr_rk_step on it alone.
+ * Members must be static-mesh contexts created on the batch's stream; while a
+ * member, a context is advanced only through the batch (other calls on it stay
+ * in stream order).  Device tables live in a caller-owned workspace of
+ * gbr_batch_workspace_bytes(max_members) bytes (256-byte aligned).
+ * Not thread-safe per batch. */
+typedef struct gbr_batch gbr_batch;
+
+size_t gbr_batch_workspace_bytes(int max_members);
+gbr_status gbr_batch_create(int max_members, void* d_workspace, size_t ws_bytes, void* stream, gbr_batch** out);
+/* use_graph: capture and replay each step as a CUDA graph (default 1); autotune:
+ * per kind and size class (log2 of the kind's cells), time the candidate
+ * interface-kernel block sizes (64, 128, 256 interfaces per tile) and gradient
+ * sweeps (two passes, or one fused pass) on the live members' right-hand side
+ * and keep the fastest (default 1; the members' states are not changed). */
+gbr_status gbr_batch_set_options(gbr_batch* b, int use_graph, int autotune);
+/* cfl_or_neg_dt as for gbr_rk_step: > 0 CFL number, < 0 fixed step. */
+gbr_status gbr_batch_add(gbr_batch* b, gbr_ctx* c, double cfl_or_neg_dt);
+gbr_status gbr_batch_remove(gbr_batch* b, gbr_ctx* c);
+/* Queue n_steps SSP-RK3 steps of every member (asynchronous; rebuilds the
+ * tables, tuning and graph first when the membership changed). */
+gbr_status gbr_batch_step(gbr_batch* b, int n_steps);
+/* Drain the stream (GBR_ETIMEOUT after timeout_s > 0) and check every member's
+ * error flag: GBR_ENONFINITE names the first bad member (*bad_member, or -1). */
+gbr_status gbr_batch_sync(gbr_batch* b, double timeout_s, int* bad_member);
+/* Members, kinds, kernel launches per step and launches issued so far. */
+gbr_status gbr_batch_info(gbr_batch* b, int* members, int* kinds, long long* launches_per_step, long long* launches);
+/* The chosen tuning of kind `kind` (0 .. kinds-1). */
+gbr_status gbr_batch_tuning(gbr_batch* b, int kind, int* nd, int* viscous, int* precision, int* face_block,
+                            int* fused_grad);
+const char* gbr_batch_last_error(const gbr_batch* b);
+void gbr_batch_destroy(gbr_batch* b);
+
+/* Device-memory arena for admitting jobs by HBM footprint (not in the paper):
+ * host bookkeeping of a caller-owned, 256-byte aligned device range; first fit
+ * in address order, 256-byte granules, free neighbours merged.  No device
+ * access.  gbr_arena_alloc returns GBR_ENOMEM when no free range is large
+ * enough (the caller keeps the job queued).  Not thread-safe. */
+typedef struct gbr_arena gbr_arena;
+gbr_status gbr_arena_create(void* d_base, size_t bytes, gbr_arena** out);
+gbr_status gbr_arena_alloc(gbr_arena* a, size_t bytes, void** ptr);
+gbr_status gbr_arena_free(gbr_arena* a, void* ptr);
+gbr_status gbr_arena_stats(const gbr_arena* a, size_t* used, size_t* free_total, size_t* largest_free, int* blocks);
+void gbr_arena_destroy(gbr_arena* a);
+
 const char* gbr_last_error(const gbr_ctx* c);
 const char* gbr_last_global_error(void);
 void gbr_destroy(gbr_ctx* c);

@@ -1326,3 +1326,5 @@ extern "C" gbr_status gbr_rhs_static(const gbr_params* p, const double* nodes, c
   if (e != cudaSuccess) return static_report(GBR_ECUDA, cudaGetErrorString(e), msg, msg_len);
   return GBR_OK;
 }
+
+#include "gbr_batch.cuh"

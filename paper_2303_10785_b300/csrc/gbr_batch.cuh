@@ -1,0 +1,880 @@
+// Batched stepping of many contexts and the device-memory arena used to admit them.
+//
+// Included at the end of gbr.cu (one translation unit: it uses the context
+// layout, the launch helpers and the kernel bodies).  Not in the paper, whose
+// solver runs one job per GPU; the arithmetic of every member is exactly that of
+// gbr_rk_step on the member alone (same bodies, same data, same order).
+//
+// Design:
+// * Members are grouped by kind: (ndim, viscous, precision).  Per kind, each
+//   phase of an SSP-RK3 step is ONE launch over a work list of items
+//   (member, sub-box, first block, blocks): the block -> (member, tile) map.
+// * Phase kernels are persistent: the grid is the number of co-resident CTAs (or
+//   fewer), and CTA b takes the contiguous block range [b*chunk, (b+1)*chunk)
+//   of the work list, finding its first item by binary search and walking on.
+// * Primitives and all ghost layers are produced by one pass over the padded box
+//   (body_prim_halo), so a stage is prim+halo, gradients, interfaces, update.
+// * The whole step (time step on the device, three stages, time advance, for
+//   every kind) is captured once into a CUDA graph and replayed until the
+//   membership changes.
+// * Per kind, an autotuner picks the interface kernel's block size (interfaces
+//   per tile: 64, 128 or 256) and the gradient sweep (two passes, or one fused
+//   pass that recomputes the neighbours' first derivatives) by timing the
+//   stage-1 right-hand side of the live members; results are cached per kind and
+//   size class (log2 of the kind's cells).
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// device tables
+// ---------------------------------------------------------------------------
+template <class R>
+struct BatchJob {
+  RhsArgsT<R> A;        // A.q unused: the stage input comes from q[stage]
+  UpdArgsT<R> U[4];     // SSP-RK3 stage combinations 0..2; 3: L(Q^n) into Q^(1) (autotuning)
+  DtArgs D;
+  const double* q[3];   // Q^n, Q^(1), Q^(2)
+  Box pad, inner, grad1[3], grad2[3], faces[3];
+  double* scal;
+  unsigned long long* dtbits;
+  int* err;
+  double cfl;           // > 0: CFL number; < 0: fixed time step -cfl
+};
+
+struct WorkItem {
+  int job, sub, first, blocks;  // blocks [first, first + blocks) of the launch cover sub-box `sub` of `job`
+};
+
+enum { WL_PAD = 0, WL_GRAD1, WL_GRAD2, WL_FACE, WL_INNER, WL_DT, WL_COUNT };
+
+// Runs f(item, local block) for the contiguous block range of this CTA.
+template <class F>
+__device__ __forceinline__ void for_work(const WorkItem* items, int n_items, int total, F f) {
+  const int chunk = (total + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int b0 = (int)blockIdx.x * chunk;
+  const int b1 = min(total, b0 + chunk);
+  if (b0 >= b1) return;
+  int lo = 0, hi = n_items - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (items[mid].first <= b0) lo = mid;
+    else hi = mid - 1;
+  }
+  int m = lo;
+  for (int blk = b0; blk < b1; ++blk) {
+    while (m + 1 < n_items && blk >= items[m].first + items[m].blocks) ++m;
+    f(items[m], blk - items[m].first);
+  }
+}
+
+#define BATCH_CELL(BOX)                                                        \
+  const long long _t = (long long)lb * blockDim.x + threadIdx.x;              \
+  if (_t >= box_size(BOX)) return;                                             \
+  int i, j, k;                                                                 \
+  box_coord(BOX, _t, i, j, k);
+
+template <int ND, class R>
+__global__ void __launch_bounds__(kBlock) kb_prim_halo(const BatchJob<R>* jobs, const WorkItem* items, int n,
+                                                        int total, int stage) {
+  for_work(items, n, total, [&](const WorkItem& it, int lb) {
+    const BatchJob<R>& J = jobs[it.job];
+    BATCH_CELL(J.pad);
+    body_prim_halo<ND>(J.A, J.q[stage], i, j, k);
+  });
+}
+
+template <int ND, class R>
+__global__ void __launch_bounds__(kBlock) kb_grad1(const BatchJob<R>* jobs, const WorkItem* items, int n, int total) {
+  for_work(items, n, total, [&](const WorkItem& it, int lb) {
+    const BatchJob<R>& J = jobs[it.job];
+    BATCH_CELL(J.grad1[it.sub]);
+    body_grad1<ND>(J.A, it.sub, i, j, k);
+  });
+}
+
+template <int ND, class R>
+__global__ void __launch_bounds__(kBlock) kb_grad2(const BatchJob<R>* jobs, const WorkItem* items, int n, int total) {
+  for_work(items, n, total, [&](const WorkItem& it, int lb) {
+    const BatchJob<R>& J = jobs[it.job];
+    BATCH_CELL(J.grad2[it.sub]);
+    body_grad2<ND>(J.A, it.sub, i, j, k);
+  });
+}
+
+// fused gradient sweep over the first-derivative box: f' everywhere, f'' where the
+// second-derivative box needs it, from f' of the neighbours recomputed in registers
+template <int ND, class R>
+__global__ void __launch_bounds__(kBlock) kb_grad12(const BatchJob<R>* jobs, const WorkItem* items, int n,
+                                                     int total) {
+  for_work(items, n, total, [&](const WorkItem& it, int lb) {
+    const BatchJob<R>& J = jobs[it.job];
+    BATCH_CELL(J.grad1[it.sub]);
+    body_grad12<ND>(J.A, it.sub, J.grad2[it.sub], i, j, k);
+  });
+}
+
+template <int ND, bool VISC, class R, int BS>
+__global__ void __launch_bounds__(BS) kb_face(const BatchJob<R>* jobs, const WorkItem* items, int n, int total) {
+  for_work(items, n, total, [&](const WorkItem& it, int lb) {
+    const BatchJob<R>& J = jobs[it.job];
+    BATCH_CELL(J.faces[it.sub]);
+    body_face<ND, VISC, false>(J.A, it.sub, i, j, k);
+  });
+}
+
+template <int ND, class R>
+__global__ void __launch_bounds__(kBlock) kb_update(const BatchJob<R>* jobs, const WorkItem* items, int n, int total,
+                                                     int stage) {
+  for_work(items, n, total, [&](const WorkItem& it, int lb) {
+    const BatchJob<R>& J = jobs[it.job];
+    BATCH_CELL(J.inner);
+    if (body_update<ND, false>(J.U[stage], i, j, k)) atomicOr(J.err, 1);
+  });
+}
+
+template <int ND, class R>
+__global__ void __launch_bounds__(kBlock) kb_dt(const BatchJob<R>* jobs, const WorkItem* items, int n, int total) {
+  __shared__ double wmin[kBlock / 32];
+  for_work(items, n, total, [&](const WorkItem& it, int lb) {
+    const BatchJob<R>& J = jobs[it.job];
+    const long long t = (long long)lb * blockDim.x + threadIdx.x;
+    double v = 1.0e300;
+    if (t < box_size(J.inner)) {
+      int i, j, k;
+      box_coord(J.inner, t, i, j, k);
+      v = body_dt<ND>(J.D, i, j, k);
+    }
+    for (int off = 16; off > 0; off >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, off));
+    __syncthreads();  // wmin of the previous block of this CTA has been read
+    if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double w = (threadIdx.x < blockDim.x / 32) ? wmin[threadIdx.x] : 1.0e300;
+      for (int off = 16; off > 0; off >>= 1) w = fmin(w, __shfl_xor_sync(0xffffffffu, w, off));
+      if (threadIdx.x == 0) atomicMin(J.dtbits, (unsigned long long)__double_as_longlong(w));
+    }
+  });
+}
+
+// per member: 0 = reset the time-step minimum (CFL) or set the fixed step, 1 = dt from the minimum,
+// 2 = advance the time
+template <class R>
+__global__ void kb_scalar(const BatchJob<R>* jobs, int n, int what) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n) return;
+  const BatchJob<R>& J = jobs[m];
+  if (what == 0) {
+    if (J.cfl > 0.0) *J.dtbits = (unsigned long long)__double_as_longlong(1.0e300);
+    else J.scal[S_DT] = -J.cfl;
+  } else if (what == 1) {
+    if (J.cfl > 0.0) J.scal[S_DT] = J.cfl * __longlong_as_double((long long)*J.dtbits);
+  } else {
+    J.scal[S_T] += J.scal[S_DT];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+constexpr int kFaceBlockOptions[3] = {64, 128, 256};
+
+struct KindKey {
+  int nd, visc, prec;
+  bool operator==(const KindKey& o) const { return nd == o.nd && visc == o.visc && prec == o.prec; }
+};
+
+struct Tuning {
+  int face_block = 128;  // interfaces per tile
+  int fused_grad = 0;    // 1: one fused gradient sweep
+};
+
+struct Kind {
+  KindKey key;
+  std::vector<gbr_ctx*> members;
+  std::vector<double> cfl;
+  size_t job_bytes = 0;
+  char* d_jobs = nullptr;  // BatchJob<R>[members]
+  WorkItem* d_items[WL_COUNT] = {};
+  std::vector<WorkItem> items[WL_COUNT];
+  int total[WL_COUNT] = {};
+  long long cells = 0;
+  Tuning tune;
+};
+
+}  // namespace
+
+struct gbr_batch {
+  cudaStream_t stream;        // the members' stream: graphs and direct launches run here
+  cudaStream_t cur = nullptr; // stream the enqueue functions issue to (the capture stream while capturing)
+  cudaStream_t cap = nullptr; // private non-blocking stream the step graph is recorded on (the legacy
+                              // default stream cannot be captured)
+  char* ws;
+  size_t ws_bytes;
+  int max_members;
+  std::vector<gbr_ctx*> members;
+  std::vector<double> cfl;
+  std::vector<Kind> kinds;
+  bool dirty = true;
+  int use_graph = 1;
+  int autotune = 1;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long launches_per_step = 0;
+  long long launches = 0;
+  int sms = 0;
+  std::vector<std::pair<long long, Tuning>> tune_cache;  // key: kind code * 64 + size class
+  std::string last_error;
+};
+
+namespace {
+
+gbr_status bfail(gbr_batch* b, gbr_status s, const std::string& m) {
+  if (b) b->last_error = m;
+  g_global_error = m;
+  return s;
+}
+
+#define BK(expr, what)                                                                         \
+  do {                                                                                         \
+    cudaError_t _e = (expr);                                                                   \
+    if (_e != cudaSuccess) return bfail(b, GBR_ECUDA, std::string(what) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+size_t batch_job_bytes() { return std::max(sizeof(BatchJob<double>), sizeof(BatchJob<float>)); }
+
+size_t batch_ws_bytes(int max_members) {
+  // per kind (at most 8) alignment slack, per member one job record and at most 1 + 3 + 3 + 3 + 1 + 1 items
+  const size_t per_member = ((batch_job_bytes() + 255) & ~(size_t)255) + 12 * sizeof(WorkItem);
+  return 8 * (size_t)WL_COUNT * 256 + 8 * 256 + (size_t)max_members * (per_member + 256);
+}
+
+template <class R>
+BatchJob<R> make_job(gbr_ctx* c, double cfl) {
+  BatchJob<R> J;
+  std::memset(&J, 0, sizeof J);
+  const Layout& L = c->L;
+  J.A = rhs_args_r<R>(c, c->q[0]);
+  const double ca[3] = {1.0, 0.75, 1.0 / 3.0}, cb[3] = {0.0, 0.25, 2.0 / 3.0}, cc[3] = {1.0, 0.25, 2.0 / 3.0};
+  for (int s = 0; s < 4; ++s) {
+    UpdArgsT<R>& U = J.U[s];
+    U.L = L;
+    for (int d = 0; d < 3; ++d) U.flux[d] = static_cast<const R*>(c->flux[d]);
+    U.jac = c->jac;
+    U.gcl = c->gcl;
+    U.sigma = c->have_sponge ? c->sigma : nullptr;
+    for (int v = 0; v < 5; ++v) U.qamb[v] = c->qamb[v];
+    U.dt = c->scal + S_DT;
+    if (s < 3) {
+      // the same stage combinations as gbr_rk_step
+      U.qs = c->q[s];
+      U.q0 = c->q[0];
+      U.out = (s == 2) ? c->q[0] : c->q[s + 1];
+      U.ca = ca[s];
+      U.cb = cb[s];
+      U.cc = cc[s];
+      U.mode = 1;
+    } else {
+      U.qs = c->q[0];
+      U.q0 = c->q[0];
+      U.out = c->q[1];
+      U.ca = U.cb = 0.0;
+      U.cc = 1.0;
+      U.mode = 0;
+    }
+  }
+  J.D.L = L;
+  J.D.ph = c->ph;
+  J.D.q = c->q[0];
+  J.D.mh = c->mh;
+  J.D.mt = nullptr;
+  J.D.jac = c->jac;
+  for (int s = 0; s < 3; ++s) J.q[s] = c->q[s];
+  const RhsBoxes B = rhs_boxes(L);
+  J.pad = pad_box(L, H, H);
+  J.inner = B.inner;
+  for (int d = 0; d < 3; ++d) {
+    J.grad1[d] = B.grad1[d];
+    J.grad2[d] = B.grad2[d];
+    J.faces[d] = B.faces[d];
+  }
+  J.scal = c->scal;
+  J.dtbits = reinterpret_cast<unsigned long long*>(c->scal + S_DTMIN);
+  J.err = c->err;
+  J.cfl = cfl;
+  return J;
+}
+
+void add_items(std::vector<WorkItem>& v, int& total, int job, int sub, const Box& box, int block) {
+  const int blocks = (int)((box_size(box) + block - 1) / block);
+  if (blocks <= 0) return;
+  v.push_back(WorkItem{job, sub, total, blocks});
+  total += blocks;
+}
+
+void build_items(Kind& K) {
+  for (int w = 0; w < WL_COUNT; ++w) {
+    K.items[w].clear();
+    K.total[w] = 0;
+  }
+  for (size_t m = 0; m < K.members.size(); ++m) {
+    gbr_ctx* c = K.members[m];
+    const Layout& L = c->L;
+    const RhsBoxes B = rhs_boxes(L);
+    const int jm = (int)m;
+    add_items(K.items[WL_PAD], K.total[WL_PAD], jm, 0, pad_box(L, H, H), kBlock);
+    for (int d = 0; d < L.nd; ++d) {
+      add_items(K.items[WL_GRAD1], K.total[WL_GRAD1], jm, d, B.grad1[d], kBlock);
+      add_items(K.items[WL_GRAD2], K.total[WL_GRAD2], jm, d, B.grad2[d], kBlock);
+      add_items(K.items[WL_FACE], K.total[WL_FACE], jm, d, B.faces[d], K.tune.face_block);
+    }
+    add_items(K.items[WL_INNER], K.total[WL_INNER], jm, 0, B.inner, kBlock);
+    if (K.cfl[m] > 0.0) add_items(K.items[WL_DT], K.total[WL_DT], jm, 0, B.inner, kBlock);
+  }
+}
+
+// co-resident CTAs of a kernel, the grid of its persistent launch
+template <class KernelT>
+int resident_ctas(gbr_batch* b, KernelT kernel, int block) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+  return per_sm * b->sms;
+}
+
+template <class KernelT>
+unsigned persistent_grid(gbr_batch* b, KernelT kernel, int block, int total) {
+  return (unsigned)std::max(1, std::min(total, resident_ctas(b, kernel, block)));
+}
+
+template <int ND, bool VISC, class R, int BS>
+gbr_status launch_face_kind(gbr_batch* b, const Kind& K, const BatchJob<R>* jobs) {
+  auto kern = kb_face<ND, VISC, R, BS>;
+  const unsigned g = persistent_grid(b, kern, BS, K.total[WL_FACE]);
+  kern<<<g, BS, 0, b->cur>>>(jobs, K.d_items[WL_FACE], (int)K.items[WL_FACE].size(), K.total[WL_FACE]);
+  BK(cudaGetLastError(), "kb_face");
+  return GBR_OK;
+}
+
+// the right-hand side of `stage` (0..3, 3 = autotuning evaluation) for one kind
+template <int ND, bool VISC, class R>
+gbr_status enqueue_rhs(gbr_batch* b, const Kind& K, int stage, long long& launches) {
+  const BatchJob<R>* jobs = reinterpret_cast<const BatchJob<R>*>(K.d_jobs);
+  cudaStream_t st = b->cur;
+  const int qin = stage == 3 ? 0 : stage;
+  {
+    auto kern = kb_prim_halo<ND, R>;
+    kern<<<persistent_grid(b, kern, kBlock, K.total[WL_PAD]), kBlock, 0, st>>>(
+        jobs, K.d_items[WL_PAD], (int)K.items[WL_PAD].size(), K.total[WL_PAD], qin);
+    BK(cudaGetLastError(), "kb_prim_halo");
+  }
+  if (K.tune.fused_grad) {
+    auto kern = kb_grad12<ND, R>;
+    kern<<<persistent_grid(b, kern, kBlock, K.total[WL_GRAD1]), kBlock, 0, st>>>(
+        jobs, K.d_items[WL_GRAD1], (int)K.items[WL_GRAD1].size(), K.total[WL_GRAD1]);
+    BK(cudaGetLastError(), "kb_grad12");
+    launches += 2;
+  } else {
+    auto k1 = kb_grad1<ND, R>;
+    k1<<<persistent_grid(b, k1, kBlock, K.total[WL_GRAD1]), kBlock, 0, st>>>(
+        jobs, K.d_items[WL_GRAD1], (int)K.items[WL_GRAD1].size(), K.total[WL_GRAD1]);
+    BK(cudaGetLastError(), "kb_grad1");
+    auto k2 = kb_grad2<ND, R>;
+    k2<<<persistent_grid(b, k2, kBlock, K.total[WL_GRAD2]), kBlock, 0, st>>>(
+        jobs, K.d_items[WL_GRAD2], (int)K.items[WL_GRAD2].size(), K.total[WL_GRAD2]);
+    BK(cudaGetLastError(), "kb_grad2");
+    launches += 3;
+  }
+  gbr_status s;
+  switch (K.tune.face_block) {
+    case 64: s = launch_face_kind<ND, VISC, R, 64>(b, K, jobs); break;
+    case 256: s = launch_face_kind<ND, VISC, R, 256>(b, K, jobs); break;
+    default: s = launch_face_kind<ND, VISC, R, 128>(b, K, jobs); break;
+  }
+  if (s != GBR_OK) return s;
+  {
+    auto kern = kb_update<ND, R>;
+    kern<<<persistent_grid(b, kern, kBlock, K.total[WL_INNER]), kBlock, 0, st>>>(
+        jobs, K.d_items[WL_INNER], (int)K.items[WL_INNER].size(), K.total[WL_INNER], stage);
+    BK(cudaGetLastError(), "kb_update");
+  }
+  launches += 2;
+  return GBR_OK;
+}
+
+template <int ND, bool VISC, class R>
+gbr_status enqueue_step_kind(gbr_batch* b, const Kind& K, long long& launches) {
+  const BatchJob<R>* jobs = reinterpret_cast<const BatchJob<R>*>(K.d_jobs);
+  cudaStream_t st = b->cur;
+  const int n = (int)K.members.size();
+  const unsigned gs = (unsigned)((n + 127) / 128);
+  kb_scalar<R><<<gs, 128, 0, st>>>(jobs, n, 0);
+  BK(cudaGetLastError(), "kb_scalar");
+  launches += 2;
+  if (K.total[WL_DT] > 0) {
+    auto kern = kb_dt<ND, R>;
+    kern<<<persistent_grid(b, kern, kBlock, K.total[WL_DT]), kBlock, 0, st>>>(
+        jobs, K.d_items[WL_DT], (int)K.items[WL_DT].size(), K.total[WL_DT]);
+    BK(cudaGetLastError(), "kb_dt");
+    ++launches;
+  }
+  kb_scalar<R><<<gs, 128, 0, st>>>(jobs, n, 1);
+  BK(cudaGetLastError(), "kb_scalar");
+  for (int stage = 0; stage < 3; ++stage) {
+    gbr_status s = enqueue_rhs<ND, VISC, R>(b, K, stage, launches);
+    if (s != GBR_OK) return s;
+  }
+  kb_scalar<R><<<gs, 128, 0, st>>>(jobs, n, 2);
+  BK(cudaGetLastError(), "kb_scalar");
+  ++launches;
+  return GBR_OK;
+}
+
+// dispatch on the kind's template parameters
+template <class Fn>
+gbr_status dispatch_kind(const KindKey& k, Fn fn) {
+  if (k.nd == 3) {
+    if (k.visc) return k.prec ? fn.template run<3, true, float>() : fn.template run<3, true, double>();
+    return k.prec ? fn.template run<3, false, float>() : fn.template run<3, false, double>();
+  }
+  if (k.visc) return k.prec ? fn.template run<2, true, float>() : fn.template run<2, true, double>();
+  return k.prec ? fn.template run<2, false, float>() : fn.template run<2, false, double>();
+}
+
+struct StepFn {
+  gbr_batch* b;
+  const Kind* K;
+  long long* launches;
+  template <int ND, bool VISC, class R>
+  gbr_status run() { return enqueue_step_kind<ND, VISC, R>(b, *K, *launches); }
+};
+
+struct RhsFn {
+  gbr_batch* b;
+  const Kind* K;
+  long long* launches;
+  template <int ND, bool VISC, class R>
+  gbr_status run() { return enqueue_rhs<ND, VISC, R>(b, *K, 3, *launches); }
+};
+
+struct UploadFn {
+  gbr_batch* b;
+  Kind* K;
+  std::vector<char>* host;
+  template <int ND, bool VISC, class R>
+  gbr_status run() {
+    const size_t n = K->members.size();
+    host->assign(n * sizeof(BatchJob<R>), 0);
+    for (size_t m = 0; m < n; ++m) {
+      BatchJob<R> J = make_job<R>(K->members[m], K->cfl[m]);
+      std::memcpy(host->data() + m * sizeof(BatchJob<R>), &J, sizeof J);
+    }
+    K->job_bytes = host->size();
+    return GBR_OK;
+  }
+};
+
+int kind_code(const KindKey& k) { return (k.nd - 2) * 4 + k.visc * 2 + k.prec; }
+
+int size_class(long long cells) {
+  int c = 0;
+  while (cells > 1) {
+    cells >>= 1;
+    ++c;
+  }
+  return c;
+}
+
+// lay out the kinds' tables in the batch workspace and copy them to the device
+gbr_status upload_kinds(gbr_batch* b) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    off = (off + 255) & ~(size_t)255;
+    char* p = b->ws + off;
+    off += bytes;
+    return p;
+  };
+  std::vector<char> host;
+  for (Kind& K : b->kinds) {
+    build_items(K);
+    UploadFn up{b, &K, &host};
+    gbr_status s = dispatch_kind(K.key, up);
+    if (s != GBR_OK) return s;
+    K.d_jobs = take(K.job_bytes);
+    if (off > b->ws_bytes) return bfail(b, GBR_ENOMEM, "batch workspace too small");
+    BK(cudaMemcpyAsync(K.d_jobs, host.data(), K.job_bytes, cudaMemcpyHostToDevice, b->stream), "upload jobs");
+    for (int w = 0; w < WL_COUNT; ++w) {
+      const size_t bytes = std::max<size_t>(1, K.items[w].size()) * sizeof(WorkItem);
+      K.d_items[w] = reinterpret_cast<WorkItem*>(take(bytes));
+      if (off > b->ws_bytes) return bfail(b, GBR_ENOMEM, "batch workspace too small");
+      if (!K.items[w].empty())
+        BK(cudaMemcpyAsync(K.d_items[w], K.items[w].data(), K.items[w].size() * sizeof(WorkItem),
+                           cudaMemcpyHostToDevice, b->stream),
+           "upload work list");
+    }
+    // the host vectors are reused: finish the copies before the next kind overwrites them
+    BK(cudaStreamSynchronize(b->stream), "upload sync");
+  }
+  return GBR_OK;
+}
+
+gbr_status enqueue_step(gbr_batch* b, long long& launches) {
+  for (const Kind& K : b->kinds) {
+    StepFn fn{b, &K, &launches};
+    gbr_status s = dispatch_kind(K.key, fn);
+    if (s != GBR_OK) return s;
+  }
+  return GBR_OK;
+}
+
+// time the stage-1 right-hand side of one kind under each tuning; keep the fastest
+gbr_status autotune_kind(gbr_batch* b, Kind& K) {
+  const long long key = (long long)kind_code(K.key) * 64 + size_class(K.cells);
+  for (auto& e : b->tune_cache)
+    if (e.first == key) {
+      K.tune = e.second;
+      return GBR_OK;
+    }
+  cudaEvent_t e0, e1;
+  BK(cudaEventCreate(&e0), "event");
+  BK(cudaEventCreate(&e1), "event");
+  Tuning best;
+  float best_ms = 1e30f;
+  std::vector<char> host;
+  for (int fb : kFaceBlockOptions) {
+    for (int fused = 0; fused < 2; ++fused) {
+      K.tune.face_block = fb;
+      K.tune.fused_grad = fused;
+      build_items(K);
+      // face work list for this block size
+      const size_t bytes = K.items[WL_FACE].size() * sizeof(WorkItem);
+      BK(cudaMemcpyAsync(K.d_items[WL_FACE], K.items[WL_FACE].data(), bytes, cudaMemcpyHostToDevice, b->stream),
+         "upload work list");
+      long long dummy = 0;
+      RhsFn fn{b, &K, &dummy};
+      b->cur = b->stream;
+      gbr_status s = dispatch_kind(K.key, fn);  // warm-up
+      if (s != GBR_OK) return s;
+      BK(cudaEventRecord(e0, b->stream), "event");
+      for (int r = 0; r < 3; ++r)
+        if ((s = dispatch_kind(K.key, fn)) != GBR_OK) return s;
+      BK(cudaEventRecord(e1, b->stream), "event");
+      BK(cudaEventSynchronize(e1), "event sync");
+      float ms = 0.f;
+      BK(cudaEventElapsedTime(&ms, e0, e1), "event time");
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = K.tune;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  K.tune = best;
+  b->tune_cache.push_back({key, best});
+  return GBR_OK;
+}
+
+gbr_status rebuild(gbr_batch* b) {
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  if (b->graph) {
+    cudaGraphDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  b->kinds.clear();
+  for (size_t m = 0; m < b->members.size(); ++m) {
+    gbr_ctx* c = b->members[m];
+    KindKey key{c->L.nd, c->visc ? 1 : 0, c->p.precision == GBR_PREC_MIXED ? 1 : 0};
+    Kind* K = nullptr;
+    for (Kind& x : b->kinds)
+      if (x.key == key) K = &x;
+    if (!K) {
+      b->kinds.push_back(Kind());
+      K = &b->kinds.back();
+      K->key = key;
+    }
+    K->members.push_back(c);
+    K->cfl.push_back(b->cfl[m]);
+    K->cells += c->L.ncells;
+  }
+  for (Kind& K : b->kinds) {
+    const long long key = (long long)kind_code(K.key) * 64 + size_class(K.cells);
+    for (auto& e : b->tune_cache)
+      if (e.first == key) K.tune = e.second;
+  }
+  gbr_status s = upload_kinds(b);
+  if (s != GBR_OK) return s;
+  if (b->autotune) {
+    for (Kind& K : b->kinds)
+      if ((s = autotune_kind(b, K)) != GBR_OK) return s;
+    if ((s = upload_kinds(b)) != GBR_OK) return s;
+  }
+  long long launches = 0;
+  if (b->use_graph && !b->members.empty()) {
+    if (!b->cap) BK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "capture stream");
+    b->cur = b->cap;
+    BK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    s = enqueue_step(b, launches);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+    b->cur = b->stream;
+    if (s != GBR_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    BK(e, "end capture");
+    b->graph = g;
+    BK(cudaGraphInstantiate(&b->exec, b->graph, 0), "graph instantiate");
+  } else {
+    // count the launches of one step without running it
+    for (const Kind& K : b->kinds) {
+      const int per_stage = K.tune.fused_grad ? 4 : 5;
+      launches += 3 + (K.total[WL_DT] > 0 ? 1 : 0) + 3 * per_stage;
+    }
+  }
+  b->launches_per_step = launches;
+  b->dirty = false;
+  return GBR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t gbr_batch_workspace_bytes(int max_members) {
+  if (max_members < 1) return 0;
+  return batch_ws_bytes(max_members);
+}
+
+gbr_status gbr_batch_create(int max_members, void* d_workspace, size_t ws_bytes, void* stream, gbr_batch** out) {
+  if (!out) return bfail(nullptr, GBR_EINVAL, "null output pointer");
+  *out = nullptr;
+  if (max_members < 1) return bfail(nullptr, GBR_EINVAL, "max_members must be positive");
+  if (!d_workspace || ((uintptr_t)d_workspace & 255)) return bfail(nullptr, GBR_EINVAL, "workspace must be 256-byte aligned");
+  if (ws_bytes < batch_ws_bytes(max_members)) return bfail(nullptr, GBR_ENOMEM, "batch workspace too small");
+  gbr_batch* b = new gbr_batch();
+  b->stream = (cudaStream_t)stream;
+  b->cur = b->stream;
+  b->ws = (char*)d_workspace;
+  b->ws_bytes = ws_bytes;
+  b->max_members = max_members;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || b->sms < 1) {
+    delete b;
+    return bfail(nullptr, GBR_ECUDA, "device query failed");
+  }
+  *out = b;
+  return GBR_OK;
+}
+
+gbr_status gbr_batch_set_options(gbr_batch* b, int use_graph, int autotune) {
+  if (!b) return bfail(b, GBR_EINVAL, "null batch");
+  b->use_graph = use_graph ? 1 : 0;
+  b->autotune = autotune ? 1 : 0;
+  b->dirty = true;
+  return GBR_OK;
+}
+
+gbr_status gbr_batch_add(gbr_batch* b, gbr_ctx* c, double cfl_or_neg_dt) {
+  if (!b || !c) return bfail(b, GBR_EINVAL, "null argument");
+  if (!(cfl_or_neg_dt != 0.0) || std::isnan(cfl_or_neg_dt)) return bfail(b, GBR_EINVAL, "cfl_or_neg_dt must be nonzero");
+  if ((int)b->members.size() >= b->max_members) return bfail(b, GBR_ENOMEM, "batch is full");
+  if (!c->metrics_ready) return bfail(b, GBR_ESTATE, "metrics not computed");
+  if (c->mov || c->have_motion) return bfail(b, GBR_EINVAL, "moving meshes are stepped with gbr_rk_step, not in a batch");
+  if (c->stream != b->stream) return bfail(b, GBR_EINVAL, "the context must use the batch's stream");
+  for (gbr_ctx* x : b->members)
+    if (x == c) return bfail(b, GBR_EINVAL, "context already in the batch");
+  b->members.push_back(c);
+  b->cfl.push_back(cfl_or_neg_dt);
+  b->dirty = true;
+  return GBR_OK;
+}
+
+gbr_status gbr_batch_remove(gbr_batch* b, gbr_ctx* c) {
+  if (!b || !c) return bfail(b, GBR_EINVAL, "null argument");
+  for (size_t m = 0; m < b->members.size(); ++m)
+    if (b->members[m] == c) {
+      b->members.erase(b->members.begin() + m);
+      b->cfl.erase(b->cfl.begin() + m);
+      b->dirty = true;
+      return GBR_OK;
+    }
+  return bfail(b, GBR_EINVAL, "context is not in the batch");
+}
+
+gbr_status gbr_batch_step(gbr_batch* b, int n_steps) {
+  if (!b) return bfail(b, GBR_EINVAL, "null batch");
+  if (n_steps < 0) return bfail(b, GBR_EINVAL, "n_steps must be non-negative");
+  if (b->members.empty() || n_steps == 0) return GBR_OK;
+  gbr_status s;
+  if (b->dirty && (s = rebuild(b)) != GBR_OK) return s;
+  for (int r = 0; r < n_steps; ++r) {
+    if (b->exec) {
+      BK(cudaGraphLaunch(b->exec, b->stream), "graph launch");
+    } else {
+      long long dummy = 0;
+      b->cur = b->stream;
+      if ((s = enqueue_step(b, dummy)) != GBR_OK) return s;
+    }
+    b->launches += b->launches_per_step;
+  }
+  return GBR_OK;
+}
+
+gbr_status gbr_batch_sync(gbr_batch* b, double timeout_s, int* bad_member) {
+  if (!b) return bfail(b, GBR_EINVAL, "null batch");
+  if (bad_member) *bad_member = -1;
+  auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaStreamQuery(b->stream);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) return bfail(b, GBR_ECUDA, std::string("stream query: ") + cudaGetErrorString(e));
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (timeout_s > 0.0 && el > timeout_s) return bfail(b, GBR_ETIMEOUT, "stream did not drain before the deadline");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  for (size_t m = 0; m < b->members.size(); ++m) {
+    int err = 0;
+    BK(cudaMemcpy(&err, b->members[m]->err, sizeof(int), cudaMemcpyDeviceToHost), "read error flag");
+    if (err) {
+      if (bad_member) *bad_member = (int)m;
+      return bfail(b, GBR_ENONFINITE, "member " + std::to_string(m) + ": non-finite state or non-positive density");
+    }
+  }
+  return GBR_OK;
+}
+
+gbr_status gbr_batch_info(gbr_batch* b, int* members, int* kinds, long long* launches_per_step, long long* launches) {
+  if (!b) return bfail(b, GBR_EINVAL, "null batch");
+  if (b->dirty && !b->members.empty()) {
+    gbr_status s = rebuild(b);
+    if (s != GBR_OK) return s;
+  }
+  if (members) *members = (int)b->members.size();
+  if (kinds) *kinds = (int)b->kinds.size();
+  if (launches_per_step) *launches_per_step = b->launches_per_step;
+  if (launches) *launches = b->launches;
+  return GBR_OK;
+}
+
+gbr_status gbr_batch_tuning(gbr_batch* b, int kind, int* nd, int* viscous, int* precision, int* face_block,
+                            int* fused_grad) {
+  if (!b) return bfail(b, GBR_EINVAL, "null batch");
+  if (kind < 0 || kind >= (int)b->kinds.size()) return bfail(b, GBR_EINVAL, "no such kind");
+  const Kind& K = b->kinds[kind];
+  if (nd) *nd = K.key.nd;
+  if (viscous) *viscous = K.key.visc;
+  if (precision) *precision = K.key.prec;
+  if (face_block) *face_block = K.tune.face_block;
+  if (fused_grad) *fused_grad = K.tune.fused_grad;
+  return GBR_OK;
+}
+
+const char* gbr_batch_last_error(const gbr_batch* b) { return b ? b->last_error.c_str() : g_global_error.c_str(); }
+
+void gbr_batch_destroy(gbr_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Device-memory arena: host bookkeeping of a caller-owned device range, used to
+// admit jobs by their HBM footprint (gbr_workspace_bytes).  First fit over the
+// free holes in address order, 256-byte granules, neighbours merged on free.
+// Nothing here touches the device.
+// ---------------------------------------------------------------------------
+#include <map>
+
+struct gbr_arena {
+  uintptr_t base;
+  size_t bytes;
+  std::map<size_t, size_t> free_;  // offset -> length
+  std::map<size_t, size_t> used_;  // offset -> length
+  std::string last_error;
+};
+
+extern "C" {
+
+gbr_status gbr_arena_create(void* d_base, size_t bytes, gbr_arena** out) {
+  if (!out) return bfail(nullptr, GBR_EINVAL, "null output pointer");
+  *out = nullptr;
+  if (!d_base || ((uintptr_t)d_base & 255)) return bfail(nullptr, GBR_EINVAL, "arena base must be 256-byte aligned");
+  bytes &= ~(size_t)255;
+  if (bytes == 0) return bfail(nullptr, GBR_EINVAL, "empty arena");
+  gbr_arena* a = new gbr_arena();
+  a->base = (uintptr_t)d_base;
+  a->bytes = bytes;
+  a->free_[0] = bytes;
+  *out = a;
+  return GBR_OK;
+}
+
+gbr_status gbr_arena_alloc(gbr_arena* a, size_t bytes, void** ptr) {
+  if (!a || !ptr) return bfail(nullptr, GBR_EINVAL, "null argument");
+  *ptr = nullptr;
+  if (bytes == 0) return bfail(nullptr, GBR_EINVAL, "zero-byte allocation");
+  const size_t need = (bytes + 255) & ~(size_t)255;
+  for (auto it = a->free_.begin(); it != a->free_.end(); ++it) {
+    if (it->second < need) continue;
+    const size_t off = it->first, len = it->second;
+    a->free_.erase(it);
+    if (len > need) a->free_[off + need] = len - need;
+    a->used_[off] = need;
+    *ptr = (void*)(a->base + off);
+    return GBR_OK;
+  }
+  a->last_error = "no free range of " + std::to_string(need) + " bytes";
+  return GBR_ENOMEM;
+}
+
+gbr_status gbr_arena_free(gbr_arena* a, void* ptr) {
+  if (!a || !ptr) return bfail(nullptr, GBR_EINVAL, "null argument");
+  const uintptr_t p = (uintptr_t)ptr;
+  if (p < a->base || p >= a->base + a->bytes) return bfail(nullptr, GBR_EINVAL, "pointer outside the arena");
+  const size_t off = p - a->base;
+  auto u = a->used_.find(off);
+  if (u == a->used_.end()) return bfail(nullptr, GBR_EINVAL, "pointer not allocated from this arena");
+  size_t start = off, len = u->second;
+  a->used_.erase(u);
+  auto next = a->free_.lower_bound(start);
+  if (next != a->free_.end() && next->first == start + len) {
+    len += next->second;
+    next = a->free_.erase(next);
+  }
+  if (next != a->free_.begin()) {
+    auto prev = std::prev(next);
+    if (prev->first + prev->second == start) {
+      start = prev->first;
+      len += prev->second;
+      a->free_.erase(prev);
+    }
+  }
+  a->free_[start] = len;
+  return GBR_OK;
+}
+
+gbr_status gbr_arena_stats(const gbr_arena* a, size_t* used, size_t* free_total, size_t* largest_free, int* blocks) {
+  if (!a) return bfail(nullptr, GBR_EINVAL, "null arena");
+  size_t u = 0, f = 0, big = 0;
+  for (auto& e : a->used_) u += e.second;
+  for (auto& e : a->free_) {
+    f += e.second;
+    big = std::max(big, e.second);
+  }
+  if (used) *used = u;
+  if (free_total) *free_total = f;
+  if (largest_free) *largest_free = big;
+  if (blocks) *blocks = (int)a->used_.size();
+  return GBR_OK;
+}
+
+void gbr_arena_destroy(gbr_arena* a) { delete a; }
+
+}  // extern "C"

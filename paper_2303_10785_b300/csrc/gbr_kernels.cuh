@@ -483,27 +483,67 @@ GBR_HD R stencil_E6(const R* f, long long e, long long s) {
   return r;
 }
 
-// Sec. 2: primitives P = [rho, u.., p] (and T = p/rho, R = 1) at interior cells,
-// evaluated in FP64 from the FP64 state and stored in R
+// Sec. 2: primitives P = [rho, u.., p] (and T = p/rho, R = 1) of state cell c stored at padded
+// index p, evaluated in FP64 from the FP64 state and stored in R
 template <int ND, class R>
-GBR_HD void body_prim(const RhsArgsT<R>& A, int i, int j, int k) {
+GBR_HD void prim_store(const RhsArgsT<R>& A, const double* q, long long c, long long p) {
   constexpr int NV = ND + 2;
   const Layout& L = A.L;
-  const long long c = cidx(L, i, j, k), p = pidx(L, i, j, k);
   const long long NC = L.ncells, PC = L.pcount;
-  const double rho = A.q[c];
+  const double rho = q[c];
   const double ir = 1.0 / rho;
   double ke = 0.0;
   A.prim[p] = R(rho);
   for (int a = 0; a < ND; ++a) {
-    const double m = A.q[(1 + a) * NC + c];
+    const double m = q[(1 + a) * NC + c];
     const double u = m * ir;
     A.prim[(1 + a) * PC + p] = R(u);
     ke = gfma(m, u, ke);
   }
-  const double pr = A.ph.gm1 * (A.q[(NV - 1) * NC + c] - 0.5 * ke);
+  const double pr = A.ph.gm1 * (q[(NV - 1) * NC + c] - 0.5 * ke);
   A.prim[(NV - 1) * PC + p] = R(pr);
   if (A.viscous) A.temp[p] = R(pr * ir);
+}
+
+// primitives at interior cells
+template <int ND, class R>
+GBR_HD void body_prim(const RhsArgsT<R>& A, int i, int j, int k) {
+  prim_store<ND>(A, A.q, cidx(A.L, i, j, k), pidx(A.L, i, j, k));
+}
+
+// Primitives on the whole padded box in one pass (interior and ghost layers): a ghost cell takes
+// the primitives of its source cell found axis by axis -- periodic wrap, zero-gradient clamp, or
+// the x-low inflow data -- which is exactly what the axis-by-axis ghost copies of body_halo
+// produce (corners included), with the same arithmetic per value.
+template <int ND, class R>
+GBR_HD void body_prim_halo(const RhsArgsT<R>& A, const double* q, int i, int j, int k) {
+  constexpr int NV = ND + 2;
+  const Layout& L = A.L;
+  int c[3] = {i, j, k};
+  bool inflow = false;
+  #pragma unroll
+  for (int a = 0; a < ND; ++a) {
+    const int n = L.n[a];
+    if (c[a] < 0) {
+      if (L.per[a]) {
+        c[a] += n;
+      } else {
+        inflow = inflow || (a == 0 && A.bc[0][0] == 2);
+        c[a] = 0;
+      }
+    } else if (c[a] >= n) {
+      c[a] = L.per[a] ? c[a] - n : n - 1;
+    }
+  }
+  const long long p = pidx(L, i, j, k);
+  if (inflow) {
+    const long long PC = L.pcount, plane = (long long)L.n[1] * L.n[2];
+    const long long ib = (long long)c[2] * L.n[1] + c[1];
+    for (int f = 0; f < NV; ++f) A.prim[f * PC + p] = R(A.inflow[f * plane + ib]);
+    if (A.viscous) A.temp[p] = R(A.inflow[(NV - 1) * plane + ib] / A.inflow[ib]);
+    return;
+  }
+  prim_store<ND>(A, q, cidx(L, c[0], c[1], c[2]), p);
 }
 
 // ghost layers along axis d for the cross-section cell (i, j, k) (coordinate d ignored):
@@ -563,6 +603,27 @@ GBR_HD void body_grad2(const RhsArgsT<R>& A, int e, int i, int j, int k) {
     const R* f1 = A.g1[e] + c * PC;
     A.g2[e][c * PC + p] = R(2) * (f[p + s] - R(2) * f[p] + f[p - s]) - R(0.5) * (f1[p + s] - f1[p - s]);
   }
+}
+
+// Both derivatives along e in one pass over the first-derivative box: f' at the cell (stored),
+// and, inside the second-derivative box `b2`, f'' from f' of the two neighbours recomputed with
+// the same stencil -- the values are those of body_grad1 followed by body_grad2.
+template <int ND, class R>
+GBR_HD void body_grad12(const RhsArgsT<R>& A, int e, const Box& b2, int i, int j, int k) {
+  constexpr int NV = ND + 2;
+  const Layout& L = A.L;
+  const long long PC = L.pcount, p = pidx(L, i, j, k), s = L.ps[e];
+  const bool second = i >= b2.lo[0] && i < b2.hi[0] && j >= b2.lo[1] && j < b2.hi[1] && k >= b2.lo[2] &&
+                      k < b2.hi[2];
+  for (int c = 0; c < NV; ++c) {
+    const R* f = A.prim + c * PC;
+    A.g1[e][c * PC + p] = stencil_E6(f, p, s);
+    if (second) {
+      const R f1p = stencil_E6(f, p + s, s), f1m = stencil_E6(f, p - s, s);
+      A.g2[e][c * PC + p] = R(2) * (f[p + s] - R(2) * f[p] + f[p - s]) - R(0.5) * (f1p - f1m);
+    }
+  }
+  if (A.viscous) A.g1[e][NV * PC + p] = stencil_E6(A.temp, p, s);
 }
 
 // App. A projection x -> R^{-1} x for the face eigenvectors (unit normal nu,

@@ -90,6 +90,30 @@ def lib():
     L.gbr_profile.restype = ctypes.c_int
     L.gbr_rhs_static.argtypes = [ctypes.POINTER(gbr_params), _P, _P, _vp, _vp, _vp, ctypes.c_char_p, ctypes.c_size_t]
     L.gbr_rhs_static.restype = ctypes.c_int
+    _ll = ctypes.c_longlong
+    _ip = ctypes.POINTER(ctypes.c_int)
+    L.gbr_batch_workspace_bytes.argtypes = [ctypes.c_int]
+    L.gbr_batch_workspace_bytes.restype = ctypes.c_size_t
+    L.gbr_batch_create.argtypes = [ctypes.c_int, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]
+    L.gbr_batch_set_options.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
+    L.gbr_batch_add.argtypes = [_vp, _vp, ctypes.c_double]
+    L.gbr_batch_remove.argtypes = [_vp, _vp]
+    L.gbr_batch_step.argtypes = [_vp, ctypes.c_int]
+    L.gbr_batch_sync.argtypes = [_vp, ctypes.c_double, _ip]
+    L.gbr_batch_info.argtypes = [_vp, _ip, _ip, ctypes.POINTER(_ll), ctypes.POINTER(_ll)]
+    L.gbr_batch_tuning.argtypes = [_vp, ctypes.c_int, _ip, _ip, _ip, _ip, _ip]
+    L.gbr_batch_last_error.argtypes = [_vp]
+    L.gbr_batch_last_error.restype = ctypes.c_char_p
+    L.gbr_batch_destroy.argtypes = [_vp]
+    L.gbr_arena_create.argtypes = [_vp, ctypes.c_size_t, ctypes.POINTER(_vp)]
+    L.gbr_arena_alloc.argtypes = [_vp, ctypes.c_size_t, ctypes.POINTER(_vp)]
+    L.gbr_arena_free.argtypes = [_vp, _vp]
+    L.gbr_arena_stats.argtypes = [_vp] + [ctypes.POINTER(ctypes.c_size_t)] * 3 + [_ip]
+    L.gbr_arena_destroy.argtypes = [_vp]
+    for name in ("gbr_batch_create", "gbr_batch_set_options", "gbr_batch_add", "gbr_batch_remove", "gbr_batch_step",
+                 "gbr_batch_sync", "gbr_batch_info", "gbr_batch_tuning", "gbr_arena_create", "gbr_arena_alloc",
+                 "gbr_arena_free", "gbr_arena_stats"):
+        getattr(L, name).restype = ctypes.c_int
     L.gbr_last_error.argtypes = [_vp]
     L.gbr_last_error.restype = ctypes.c_char_p
     L.gbr_last_global_error.restype = ctypes.c_char_p
@@ -107,7 +131,10 @@ def exported_symbols():
     return ["gbr_workspace_bytes", "gbr_create", "gbr_compute_metrics", "gbr_move_mesh", "gbr_set_motion",
             "gbr_set_state", "gbr_get_state", "gbr_set_inflow", "gbr_set_sponge", "gbr_rhs", "gbr_compute_dt",
             "gbr_rk_step", "gbr_sync", "gbr_get_time", "gbr_get_field", "gbr_profile", "gbr_rhs_static",
-            "gbr_last_error", "gbr_last_global_error", "gbr_destroy"]
+            "gbr_batch_workspace_bytes", "gbr_batch_create", "gbr_batch_set_options", "gbr_batch_add",
+            "gbr_batch_remove", "gbr_batch_step", "gbr_batch_sync", "gbr_batch_info", "gbr_batch_tuning",
+            "gbr_batch_last_error", "gbr_batch_destroy", "gbr_arena_create", "gbr_arena_alloc", "gbr_arena_free",
+            "gbr_arena_stats", "gbr_arena_destroy", "gbr_last_error", "gbr_last_global_error", "gbr_destroy"]
 
 
 def make_params(case):
@@ -156,7 +183,9 @@ def _ptr(a):
 class Solver:
     """One grid on one GPU.  ``case`` is a dict from ``inputs.case_params``."""
 
-    def __init__(self, case, nodes, node_vel=None, device="cuda", stream=None, moving=None):
+    def __init__(self, case, nodes, node_vel=None, device="cuda", stream=None, moving=None, workspace=None):
+        """workspace: optional (device pointer, bytes) owned by the caller (e.g. from an ``Arena``);
+        by default a torch tensor of ``workspace_bytes`` is allocated."""
         import torch
 
         self.torch = torch
@@ -176,9 +205,15 @@ class Solver:
         if nbytes == 0:
             raise GbrError(GBR_EINVAL, self.L.gbr_last_global_error().decode())
         self.workspace_bytes = int(nbytes)
-        self.workspace = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
-        base = self.workspace.data_ptr()
-        aligned = (base + 255) & ~255
+        if workspace is None:
+            self.workspace = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
+            base = self.workspace.data_ptr()
+            aligned = (base + 255) & ~255
+        else:
+            aligned, avail = int(workspace[0]), int(workspace[1])
+            if avail < self.workspace_bytes:
+                raise GbrError(GBR_ENOMEM, "external workspace smaller than gbr_workspace_bytes")
+            self.workspace = None
         self.h = _vp()
         nodes = _f64(nodes)
         node_vel = _f64(node_vel)
@@ -302,3 +337,110 @@ class Solver:
         out = np.empty(shapes[which])
         self._check(self.L.gbr_get_field(self.h, which, d, _ptr(out)))
         return out
+
+
+class Batch:
+    """Many static-mesh ``Solver``s advanced together (one launch per phase and kind, one CUDA graph
+    per step).  Members must use the batch's stream."""
+
+    def __init__(self, max_members, device="cuda", stream=None, use_graph=True, autotune=True):
+        import torch
+
+        self.L = lib()
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = int(self.L.gbr_batch_workspace_bytes(int(max_members)))
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        aligned = (self.workspace.data_ptr() + 255) & ~255
+        self.h = _vp()
+        rc = self.L.gbr_batch_create(int(max_members), _vp(aligned), ctypes.c_size_t(nbytes),
+                                     _vp(self.stream.cuda_stream), ctypes.byref(self.h))
+        if rc:
+            raise GbrError(rc, self.L.gbr_last_global_error().decode())
+        self._check(self.L.gbr_batch_set_options(self.h, int(use_graph), int(autotune)))
+        self.members = []
+
+    def _check(self, rc):
+        if rc:
+            raise GbrError(rc, self.L.gbr_batch_last_error(self.h).decode())
+
+    def add(self, solver, cfl_or_neg_dt):
+        self._check(self.L.gbr_batch_add(self.h, solver.h, float(cfl_or_neg_dt)))
+        self.members.append(solver)
+
+    def remove(self, solver):
+        self._check(self.L.gbr_batch_remove(self.h, solver.h))
+        self.members.remove(solver)
+
+    def step(self, n=1):
+        self._check(self.L.gbr_batch_step(self.h, int(n)))
+
+    def sync(self, timeout=60.0):
+        bad = ctypes.c_int(-1)
+        rc = self.L.gbr_batch_sync(self.h, float(timeout), ctypes.byref(bad))
+        if rc:
+            raise GbrError(rc, self.L.gbr_batch_last_error(self.h).decode())
+
+    def info(self):
+        m, k = ctypes.c_int(), ctypes.c_int()
+        lps, lt = ctypes.c_longlong(), ctypes.c_longlong()
+        self._check(self.L.gbr_batch_info(self.h, ctypes.byref(m), ctypes.byref(k), ctypes.byref(lps),
+                                          ctypes.byref(lt)))
+        return {"members": m.value, "kinds": k.value, "launches_per_step": lps.value, "launches": lt.value}
+
+    def tuning(self):
+        out = []
+        for kind in range(self.info()["kinds"]):
+            v = [ctypes.c_int() for _ in range(5)]
+            self._check(self.L.gbr_batch_tuning(self.h, kind, *[ctypes.byref(x) for x in v]))
+            out.append(dict(zip(("ndim", "viscous", "mixed", "face_block", "fused_grad"), (x.value for x in v))))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.L.gbr_batch_destroy(self.h)
+            self.h = _vp()
+
+    def __del__(self):
+        self.close()
+
+
+class Arena:
+    """First-fit bookkeeping of one device range (``gbr_arena_*``): jobs are admitted when their
+    workspace fits."""
+
+    def __init__(self, base, nbytes):
+        self.L = lib()
+        self.h = _vp()
+        rc = self.L.gbr_arena_create(_vp(int(base)), ctypes.c_size_t(int(nbytes)), ctypes.byref(self.h))
+        if rc:
+            raise GbrError(rc, self.L.gbr_last_global_error().decode())
+
+    def alloc(self, nbytes):
+        """Device pointer, or None when no free range fits."""
+        p = _vp()
+        rc = self.L.gbr_arena_alloc(self.h, ctypes.c_size_t(int(nbytes)), ctypes.byref(p))
+        if rc == GBR_ENOMEM:
+            return None
+        if rc:
+            raise GbrError(rc, self.L.gbr_last_global_error().decode())
+        return p.value
+
+    def free(self, ptr):
+        rc = self.L.gbr_arena_free(self.h, _vp(int(ptr)))
+        if rc:
+            raise GbrError(rc, self.L.gbr_last_global_error().decode())
+
+    def stats(self):
+        v = [ctypes.c_size_t() for _ in range(3)]
+        nb = ctypes.c_int()
+        self.L.gbr_arena_stats(self.h, *[ctypes.byref(x) for x in v], ctypes.byref(nb))
+        return {"used": v[0].value, "free": v[1].value, "largest_free": v[2].value, "blocks": nb.value}
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.L.gbr_arena_destroy(self.h)
+            self.h = _vp()
+
+    def __del__(self):
+        self.close()

@@ -1,0 +1,165 @@
+"""GPU: batched stepping (gbr_batch_*) against each member stepped alone with gbr_rk_step.
+
+The batch runs the same kernel bodies on the same data in the same order as the
+per-context path (the primitives and ghost layers in one pass instead of
+interior + axis-by-axis copies, which copy the same values), and the time step
+is an exact minimum, so every member's state and time must be bitwise equal to
+those of the member stepped alone -- whatever the batch composition, membership
+changes, graph replay or tuning.
+"""
+import numpy as np
+import pytest
+
+from paper_2303_10785_b300 import gbr
+from paper_2303_10785_b300 import inputs as I
+from test_gpu_parity import GAMMA, case_2d_viscous_random, case_2d_vortex, case_3d_inviscid_ragged, case_jet
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+
+
+def tgv(n, precision="fp64"):
+    case = I.case_params(3, (n, n, n), reynolds=1600.0, precision=precision)
+    nodes = I.nodes_tgv_3d(n, 0.1)
+    xc = I.centroids(nodes, (n, n, n), (1, 1, 1))
+    return case, nodes, I.prim_to_cons(I.tgv_prim(*xc, mach=0.1), GAMMA)
+
+
+def sod(precision="fp64"):
+    n = (40, 32)
+    case = I.case_params(2, n, precision=precision)
+    nodes = I.nodes_skewed_2d(n, (1.25, 1.0), skew_deg=25.0, jitter=0.1, seed=5)
+    xc = I.centroids(nodes, n, (1, 1))
+    rho, p = I.sod_slab_prim(xc[1], L=1.0)
+    P = np.stack([rho, np.zeros_like(rho), np.zeros_like(rho), p])
+    return case, nodes, I.prim_to_cons(P, GAMMA)
+
+
+def jobs():
+    """(case, nodes, q, cfl_or_neg_dt, extra): every kind the batch groups, CFL and fixed steps."""
+    out = []
+    c, n, _, q = case_2d_vortex(48)
+    out.append((c, n, q, 0.4, None))
+    out.append((dict(c, precision="mixed"), n, q, 0.4, None))
+    c, n, _, q = case_2d_viscous_random()
+    out.append((c, n, q, 0.3, None))
+    c, n, q = tgv(20)
+    out.append((c, n, q, 0.2, None))
+    c, n, q = tgv(24, "mixed")
+    out.append((c, n, q, 0.2, None))
+    c, n, _, q = case_3d_inviscid_ragged()
+    out.append((dict(c, precision="mixed"), n, q, -2e-3, None))
+    c, n, q = sod()
+    out.append((c, n, q, 0.3, None))
+    c, n, _, q, extra = case_jet()
+    out.append((c, n, q, -2e-3, extra))
+    return out
+
+
+def make(job):
+    case, nodes, q, _, extra = job
+    s = gbr.Solver(case, nodes)
+    if extra:
+        s.set_inflow(extra["inflow"])
+        s.set_sponge(extra["sigma"], extra["qamb"])
+    s.set_state(q)
+    return s
+
+
+def alone(job, steps):
+    s = make(job)
+    for _ in range(steps):
+        s.rk_step(job[3])
+    s.sync()
+    out = s.get_state(), s.time()
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("use_graph,autotune", [(True, True), (False, False)])
+def test_batch_results_bitwise_equal_to_members_alone(use_graph, autotune):
+    js = jobs()
+    steps = 4
+    refs = [alone(j, steps) for j in js]
+    b = gbr.Batch(len(js), use_graph=use_graph, autotune=autotune)
+    members = [make(j) for j in js]
+    for s, j in zip(members, js):
+        b.add(s, j[3])
+    b.step(steps)
+    b.sync()
+    info = b.info()
+    assert info["members"] == len(js) and info["kinds"] == 6
+    assert info["launches"] == steps * info["launches_per_step"]
+    for s, (qref, tref) in zip(members, refs):
+        assert np.array_equal(s.get_state(), qref)
+        assert s.time() == tref
+    for t in b.tuning():
+        assert t["face_block"] in (64, 128, 256) and t["fused_grad"] in (0, 1)
+    b.close()
+    for s in members:
+        s.close()
+
+
+def test_batch_membership_changes_between_steps():
+    js = jobs()[:5]
+    b = gbr.Batch(8)
+    s = [make(j) for j in js]
+    b.add(s[0], js[0][3])
+    b.add(s[3], js[3][3])
+    b.step(2)
+    b.add(s[1], js[1][3])   # joins after two steps
+    b.add(s[4], js[4][3])
+    b.step(1)
+    b.remove(s[0])           # leaves after three steps
+    b.add(s[2], js[2][3])
+    b.step(3)
+    b.sync()
+    done = {0: 3, 1: 4, 2: 3, 3: 6, 4: 4}
+    for m, steps in done.items():
+        qref, tref = alone(js[m], steps)
+        assert np.array_equal(s[m].get_state(), qref), m
+        assert s[m].time() == tref
+    b.close()
+    for x in s:
+        x.close()
+
+
+def test_batch_rejects_moving_mesh_and_foreign_stream():
+    import torch
+
+    b = gbr.Batch(2)
+    m = I.motion_dynamic_2d(n=32, L=10.0, amp=0.1)
+    mov = gbr.Solver(I.case_params(2, (32, 32), moving=1), m.nodes(0.0), m.velocity(0.0))
+    with pytest.raises(gbr.GbrError):
+        b.add(mov, 0.4)
+    c, n, _, q = case_2d_vortex(32)
+    other = gbr.Solver(c, n, stream=torch.cuda.Stream())
+    with pytest.raises(gbr.GbrError):
+        b.add(other, 0.4)
+    mov.close()
+    other.close()
+    b.close()
+
+
+def test_batch_reports_the_member_with_a_bad_state():
+    js = jobs()[:2]
+    b = gbr.Batch(2)
+    s = [make(j) for j in js]
+    q = js[1][2].copy()
+    q[0, 0, 0] = -1.0  # negative density in one cell of the second member
+    s[1].set_state(q)
+    for x, j in zip(s, js):
+        b.add(x, -1e-3)
+    b.step(1)
+    with pytest.raises(gbr.GbrError) as e:
+        b.sync()
+    assert e.value.status == gbr.GBR_ENONFINITE and "member 1" in str(e.value)
+    b.close()
+    for x in s:
+        x.close()
