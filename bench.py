@@ -409,13 +409,91 @@ def run_gpu(args, wl):
     solver.close()
 
 
+def run_serving(args):
+    """The serving stream: jobs of mixed kinds, sizes and precisions with Poisson arrivals at an
+    offered load of `--load` x the measured FP64 per-job capacity, served (1) by the plain FP64
+    per-job form (one job at a time through gbr_rk_step) and (2) by the continuous-batching server
+    (each job in its own precision); aggregate cell-RK-stage updates/s and time-to-N-steps p50/p99."""
+    import torch
+
+    from paper_2303_10785_b300 import inputs as I
+    from paper_2303_10785_b300 import serving
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    specs = I.serving_stream(args.jobs, seed=args.seed, rate=1.0)
+
+    def jobs_at(rate, precision=None):
+        out = []
+        for sp in specs:
+            case, nodes, q, cfl = I.serving_job_inputs(sp, precision)
+            out.append(serving.Job(sp["id"], case, nodes, q, sp["steps"], cfl, sp["arrival"] / rate))
+        return out
+
+    # FP64 per-job capacity on a sample of the stream's jobs (a few steps each, after a warm-up step)
+    sample = [sp for sp in specs[:: max(1, len(specs) // 8)]]
+    work = secs = 0.0
+    stream = torch.cuda.current_stream()
+    for sp in sample:
+        case, nodes, q, cfl = I.serving_job_inputs(sp, "fp64")
+        job = serving.Job(sp["id"], case, nodes, q, 4, cfl)
+        s = job.make_solver(stream)
+        s.rk_step(cfl)
+        s.sync()
+        t0 = time.perf_counter()
+        for _ in range(job.steps):
+            s.rk_step(cfl)
+        s.sync()
+        secs += time.perf_counter() - t0
+        work += job.work
+        s.close()
+    capacity = work / secs
+    mean_work = float(np.mean([I.serving_job_work(sp) for sp in specs]))
+    rate = args.load * capacity / mean_work
+
+    base = jobs_at(rate, "fp64")
+    serving.run_serial(base)
+    st_base = serving.latency_stats(base)
+    pool = int(args.pool_gb * 1e9)
+    srv = serving.Server(pool, max_active=args.slots, chunk_steps=args.chunk)
+    mix = jobs_at(rate)
+    with ClockSampler(local) as clocks:
+        srv.run(mix)
+    st_mix = serving.latency_stats(mix)
+    info = srv.batch.info()
+    tuning = srv.batch.tuning()
+    peak = {"active": srv.peak_active, "pool_bytes": srv.peak_pool}
+    srv.close()
+    errors = [j.error for j in mix + base if j.error]
+    line = {
+        "metric": METRIC, "value": st_mix["cell_rk_stage_updates_per_s"], "unit": METRIC, "n_gpus": 1,
+        "steps": None, "warmup": None, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 and f32+f64 per job", "data": "synthetic",
+        "config": {"workload": f"serving_stream_{args.jobs}_jobs", "seed": args.seed, "offered_load": args.load,
+                   "pool_gb": args.pool_gb, "slots": args.slots, "chunk_steps": args.chunk,
+                   "l2": "working sets of the large jobs >> 126 MB L2, no flush"},
+        "serving": {"batched_mixed": st_mix, "per_job_fp64": st_base, "fp64_capacity_per_job": capacity,
+                    "arrival_rate_jobs_per_s": rate, "throughput_ratio": st_mix["cell_rk_stage_updates_per_s"]
+                    / st_base["cell_rk_stage_updates_per_s"], "peak": peak, "tuning": tuning,
+                    "errors": errors},
+        "gpu_launches": info["launches"], "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None, help="timed steps (default 60 for tgv, 20 for jet)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbr", choices=["gbr", "reference"])
-    ap.add_argument("--workload", default="tgv", choices=["tgv", "jet"])
+    ap.add_argument("--workload", default="tgv", choices=["tgv", "jet", "serving"])
+    ap.add_argument("--jobs", type=int, default=64, help="serving: jobs in the stream")
+    ap.add_argument("--seed", type=int, default=0, help="serving: stream seed")
+    ap.add_argument("--load", type=float, default=1.2, help="serving: offered load / FP64 per-job capacity")
+    ap.add_argument("--pool-gb", type=float, default=64.0, help="serving: device pool for job workspaces")
+    ap.add_argument("--slots", type=int, default=64, help="serving: batch slots")
+    ap.add_argument("--chunk", type=int, default=8, help="serving: steps between looks at the queue")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="mixed: FP32 reconstruction and fluxes, FP64 state, metrics, GCL and RK accumulation")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -426,6 +504,10 @@ def main():
         args.steps = 60 if args.workload == "tgv" else 20
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "serving":
+        if dist_env()[1] == 0 and args.impl != "reference":
+            run_serving(args)
+        return
     wl = Workload(args.workload, args.edge, args.precision)
     if args.impl == "reference":
         run_reference(args, wl)

@@ -415,6 +415,7 @@ class Arena:
         rc = self.L.gbr_arena_create(_vp(int(base)), ctypes.c_size_t(int(nbytes)), ctypes.byref(self.h))
         if rc:
             raise GbrError(rc, self.L.gbr_last_global_error().decode())
+        self.capacity = int(nbytes) & ~255
 
     def alloc(self, nbytes):
         """Device pointer, or None when no free range fits."""

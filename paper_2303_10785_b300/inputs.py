@@ -392,3 +392,62 @@ def jet_case(n=(480, 170, 170), Lx=20.0, h0=0.02, ratio=1.02, re_d=1e5, gamma=1.
     sigma = jet_sponge_sigma(n, lateral=lateral)
     q_amb = np.array([1.0, 0.0, 0.0, 0.0, 1.0 / (gamma - 1.0)])
     return case, nodes, prim_to_cons(P, gamma), inflow, sigma, q_amb
+
+# ---------------------------------------------------------------------------
+# The serving stream: jobs of mixed kinds and sizes with Poisson arrivals
+# ---------------------------------------------------------------------------
+def serving_stream(n_jobs=256, seed=0, rate=1.0, edge2d=(32, 512), edge3d=(32, 128), steps=(50, 500),
+                   mixed_frac=0.5):
+    """Job specifications (dicts) of a serving stream.  Per job, from SplitMix64 of (seed, job, field):
+    2D or 3D with equal odds; the grid edge log-uniform in edge2d / edge3d; 2D jobs are the isentropic
+    vortex or a Sod slab, 3D jobs the viscous Taylor-Green vortex; an affine skew of U[0, 30] degrees
+    (2D) plus 10 % node jitter; steps uniform in `steps`; FP64 or mixed precision (mixed with
+    probability mixed_frac); arrivals a Poisson process of `rate` jobs per second."""
+    out = []
+    t = 0.0
+    for j in range(n_jobs):
+        u = [0.5 * (hash_uniform(seed, j, f) + 1.0) for f in range(8)]
+        t += -math.log(max(1.0 - float(u[0]), 1e-300)) / rate
+        nd = 2 if u[1] < 0.5 else 3
+        lo, hi = edge2d if nd == 2 else edge3d
+        edge = int(round(math.exp(math.log(lo) + float(u[2]) * (math.log(hi) - math.log(lo)))))
+        kind = ("vortex" if u[3] < 0.5 else "sod") if nd == 2 else "tgv"
+        n_steps = int(steps[0] + math.floor(float(u[4]) * (steps[1] - steps[0] + 1)))
+        out.append(dict(id=j, arrival=t, ndim=nd, edge=edge, kind=kind, steps=min(n_steps, steps[1]),
+                        precision="mixed" if u[5] < mixed_frac else "fp64", skew_deg=30.0 * float(u[6]),
+                        seed=int(1000 + j)))
+    return out
+
+
+def serving_job_inputs(spec, precision=None):
+    """(case, nodes, q, cfl) of one serving job (precision overrides the spec's)."""
+    prec = precision or spec["precision"]
+    e = spec["edge"]
+    if spec["ndim"] == 2:
+        n = (e, e)
+        if spec["kind"] == "vortex":
+            nodes = nodes_skewed_2d(n, (10.0, 10.0), skew_deg=spec["skew_deg"], jitter=0.1, seed=spec["seed"])
+            xc = centroids(nodes, n, (1, 1))
+            q = prim_to_cons(vortex_prim(xc[0], xc[1]), 1.4)
+            cfl = 0.4
+        else:
+            nodes = nodes_skewed_2d(n, (1.0, 1.0), skew_deg=spec["skew_deg"], jitter=0.1, seed=spec["seed"])
+            xc = centroids(nodes, n, (1, 1))
+            rho, p = sod_slab_prim(xc[1], L=1.0)
+            z = np.zeros_like(rho)
+            q = prim_to_cons(np.stack([rho, z, z, p]), 1.4)
+            cfl = 0.3
+        case = case_params(2, n, precision=prec)
+    else:
+        n = (e, e, e)
+        nodes = nodes_random(n, (2 * np.pi,) * 3, frac=0.1, seed=spec["seed"])
+        xc = centroids(nodes, n, (1, 1, 1))
+        q = prim_to_cons(tgv_prim(*xc, mach=0.1), 1.4)
+        case = case_params(3, n, reynolds=1600.0, precision=prec)
+        cfl = 0.2
+    return case, nodes, q, cfl
+
+
+def serving_job_work(spec):
+    """Cell-RK-stage updates of one job."""
+    return spec["edge"] ** spec["ndim"] * spec["steps"] * 3

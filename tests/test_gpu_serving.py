@@ -1,0 +1,55 @@
+"""GPU: continuous-batching serving.  Jobs of mixed kinds, sizes and precisions arrive while
+others run, wait for a batch slot and for device memory (admission by gbr_workspace_bytes in a
+pool that holds only a few of them), run in the mix, and leave; each result must equal -- bitwise --
+the same job run alone through gbr_rk_step, and the server reports time-to-N-steps percentiles."""
+import numpy as np
+import pytest
+
+from paper_2303_10785_b300 import gbr, serving
+from paper_2303_10785_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+
+
+def small_stream(n=14, seed=3, rate=400.0):
+    specs = I.serving_stream(n, seed=seed, rate=rate, edge2d=(24, 72), edge3d=(12, 24), steps=(3, 14))
+    jobs = []
+    for sp in specs:
+        case, nodes, q, cfl = I.serving_job_inputs(sp)
+        jobs.append(serving.Job(sp["id"], case, nodes, q, sp["steps"], cfl, sp["arrival"]))
+    return jobs
+
+
+def test_serving_results_equal_alone_and_in_the_mix():
+    jobs = small_stream()
+    alone = serving.run_serial([serving.Job(j.id, j.case, j.nodes, j.q, j.steps, j.cfl, 0.0) for j in jobs])
+    pool = int(2.5 * max(j.footprint() for j in jobs))
+    srv = serving.Server(pool, max_active=4, chunk_steps=3)
+    srv.run(jobs)
+    assert len(srv.done) == len(jobs) and not srv.queue and not srv.active
+    assert 1 < srv.peak_active <= 4 and srv.peak_pool <= pool
+    for j, a in zip(sorted(jobs, key=lambda x: x.id), sorted(alone, key=lambda x: x.id)):
+        assert j.error is None
+        assert np.array_equal(j.result, a.result), j.id
+        assert j.time == a.time
+    st = serving.latency_stats(jobs)
+    assert st["jobs"] == len(jobs) and 0 < st["p50_s"] <= st["p99_s"]
+    assert all(j.admitted >= j.arrival - 1e-9 and j.finished >= j.admitted for j in jobs)
+    srv.close()
+
+
+def test_serving_rejects_a_job_larger_than_the_pool():
+    jobs = small_stream(3)
+    big = max(jobs, key=lambda j: j.footprint())
+    srv = serving.Server(big.footprint() - 4096, max_active=2)
+    srv.run(jobs)
+    assert big.error and "larger than the device pool" in big.error
+    assert all(j.result is not None for j in jobs if j is not big)
+    srv.close()
