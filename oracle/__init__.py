@@ -35,6 +35,7 @@ class OrcParams(ctypes.Structure):
         ("mp_alpha", ctypes.c_double),
         ("mp_beta", ctypes.c_double),
         ("mp_eps", ctypes.c_double),
+        ("gradient_scheme", ctypes.c_int),
     ]
 
 
@@ -110,6 +111,7 @@ def make_params(case):
     for key in ("gamma", "prandtl", "reynolds", "sutherland_s", "t_ref", "alpha_damping", "mp_alpha", "mp_beta",
                 "mp_eps"):
         setattr(p, key, float(case[key]))
+    p.gradient_scheme = {"meg6": 0, "mig4": 1}[case.get("gradient_scheme", "meg6")]
     return p
 
 
@@ -244,9 +246,10 @@ class Oracle:
 
 
 def op1d(kind, f, counting=False):
-    """Periodic line operators: 'e6', 'second', 'face', 'D', 'e4' (counting=True: run in the
-    operation-counting build, for flop_counts)."""
-    k = {"e6": 0, "second": 1, "face": 2, "D": 3, "e4": 4}[kind]
+    """Line operators: 'e6', 'second', 'face', 'D', 'e4', 'ig4' on a periodic line, and 'ig4_open':
+    IG4 on an open line whose three end points at each side take the explicit end rows
+    (counting=True: run in the operation-counting build, for flop_counts)."""
+    k = {"e6": 0, "second": 1, "face": 2, "D": 3, "e4": 4, "ig4": 5, "ig4_open": 6}[kind]
     f = _f64(f)
     out = np.zeros_like(f)
     _lib(counting).orc_op1d(k, f.size, _ptr(f), _ptr(out))

@@ -172,6 +172,110 @@ static Field op_e4(const Field& f, int d) {
   return o;
 }
 
+// Eq. (IG4_grads), read with differences (A2), alpha = 5/14:
+//   alpha f'_{i-1} + f'_i + alpha f'_{i+1} = (2 + alpha)/3 (f_{i+1} - f_{i-1}) + (4 alpha - 1)/12 (f_{i+2} - f_{i-2})
+static const double kIG4Alpha = 5.0 / 14.0;
+
+static real ig4_rhs(const real* f, int i) {
+  const double a = kIG4Alpha;
+  return (2.0 + a) / 3.0 * (f[i + 1] - f[i - 1]) + (4.0 * a - 1.0) / 12.0 * (f[i + 2] - f[i - 2]);
+}
+
+// Thomas algorithm for sub-diagonal a, diagonal b, super-diagonal c, right side r (length m);
+// the first and last rows may be given with zero off-diagonals.
+static void thomas(const std::vector<real>& a, const std::vector<real>& b, const std::vector<real>& c,
+                   std::vector<real> r, std::vector<real>& x) {
+  const int m = (int)b.size();
+  std::vector<real> cp(m), rp(m);
+  cp[0] = c[0] / b[0];
+  rp[0] = r[0] / b[0];
+  for (int i = 1; i < m; ++i) {
+    const real den = b[i] - a[i] * cp[i - 1];
+    cp[i] = c[i] / den;
+    rp[i] = (r[i] - a[i] * rp[i - 1]) / den;
+  }
+  x.assign(m, real(0.0));
+  x[m - 1] = rp[m - 1];
+  for (int i = m - 2; i >= 0; --i) x[i] = rp[i] - cp[i] * x[i + 1];
+}
+
+// IG4 on a periodic line of n values: fp points at f_0 with f_{-2} .. f_{n+1} readable.
+// The cyclic system (corners alpha) is solved with the Sherman-Morrison formula: with
+// gamma = -b_0, A = T + u v^T, u = (gamma, 0.., alpha), v = (1, 0.., alpha/gamma); solve
+// T y = r and T z = u, then x = y - (v.y)/(1 + v.z) z.
+static void ig4_line_cyclic(const real* fp, int n, std::vector<real>& g) {
+  const double al = kIG4Alpha;
+  std::vector<real> a(n, real(al)), b(n, real(1.0)), c(n, real(al)), r(n), u(n, real(0.0));
+  for (int i = 0; i < n; ++i) r[i] = ig4_rhs(fp, i);
+  const real gamma = -b[0];
+  b[0] = b[0] - gamma;
+  b[n - 1] = b[n - 1] - al * al / gamma;
+  a[0] = 0.0;
+  c[n - 1] = 0.0;
+  u[0] = gamma;
+  u[n - 1] = al;
+  std::vector<real> y, z;
+  thomas(a, b, c, r, y);
+  thomas(a, b, c, u, z);
+  const real fac = (y[0] + al / gamma * y[n - 1]) / (1.0 + z[0] + al / gamma * z[n - 1]);
+  g.assign(n, real(0.0));
+  for (int i = 0; i < n; ++i) g[i] = y[i] - fac * z[i];
+}
+
+// IG4 on an open line of m >= 7 values: the three end points at each side take explicit
+// rows (reading A33, App. C with A22's index correction): second-order one-sided at the end
+// point, fourth-order biased next to it, fourth-order central (Eq. 4thorder-grads) third;
+// IG4 rows in between.
+static void ig4_line_open(const real* f, int m, std::vector<real>& g) {
+  const double al = kIG4Alpha;
+  std::vector<real> a(m, real(al)), b(m, real(1.0)), c(m, real(al)), r(m, real(0.0));
+  for (int t = 0; t < 3; ++t) {
+    a[t] = c[t] = a[m - 1 - t] = c[m - 1 - t] = 0.0;
+  }
+  r[0] = -1.5 * f[0] + 2.0 * f[1] - 0.5 * f[2];
+  r[1] = -0.25 * f[0] - (5.0 / 6.0) * f[1] + 1.5 * f[2] - 0.5 * f[3] + f[4] / 12.0;
+  r[2] = (2.0 / 3.0) * (f[3] - f[1]) - (f[4] - f[0]) / 12.0;
+  const int e = m - 1;
+  r[e] = 1.5 * f[e] - 2.0 * f[e - 1] + 0.5 * f[e - 2];
+  r[e - 1] = 0.25 * f[e] + (5.0 / 6.0) * f[e - 1] - 1.5 * f[e - 2] + 0.5 * f[e - 3] - f[e - 4] / 12.0;
+  r[e - 2] = (2.0 / 3.0) * (f[e - 1] - f[e - 3]) - (f[e] - f[e - 4]) / 12.0;
+  for (int i = 3; i < m - 3; ++i) r[i] = ig4_rhs(f, i);
+  thomas(a, b, c, r, g);
+}
+
+// IG4 first derivatives of a padded field along d (output box: f's box shrunk by 3 along d,
+// like op_e6).  Periodic axis: the cyclic system over the n cells, extended periodically;
+// open axis: the whole padded line with explicit end rows.
+static Field op_ig4(const Field& f, int d, bool periodic, int n) {
+  Field o(f.b.grow(d, -3, -3));
+  Box lines = o.b;
+  lines.lo[d] = 0;
+  lines.hi[d] = 1;
+  const int flo = f.b.lo[d], fhi = f.b.hi[d];
+  FOR_BOX(lines) {
+    int c[3] = {i, j, k};
+    std::vector<real> line(fhi - flo), g;
+    for (int m = flo; m < fhi; ++m) {
+      c[d] = m;
+      line[m - flo] = f.at(c[0], c[1], c[2]);
+    }
+    if (periodic) {
+      ig4_line_cyclic(line.data() - flo, n, g);
+      for (int m = o.b.lo[d]; m < o.b.hi[d]; ++m) {
+        c[d] = m;
+        o.at(c[0], c[1], c[2]) = g[((m % n) + n) % n];
+      }
+    } else {
+      ig4_line_open(line.data(), fhi - flo, g);
+      for (int m = o.b.lo[d]; m < o.b.hi[d]; ++m) {
+        c[d] = m;
+        o.at(c[0], c[1], c[2]) = g[m - flo];
+      }
+    }
+  }
+  return o;
+}
+
 // Sec. 5.1 step 1, second derivative shared by MEG6 and MIG4:
 // f''_i = 2 (f_{i+1} - 2 f_i + f_{i-1}) - 0.5 (f'_{i+1} - f'_{i-1})
 static Field op_second(const Field& f, const Field& f1, int d) {
@@ -803,12 +907,13 @@ int orc_solver::rhs(const double* q, double* Lout, double* resout, int fdir, dou
   // Sec. 5.1 step 1: gradients along each computational direction
   ORC_PHASE(PH_GRAD);
   Field P1[3][5], P2[3][5], T1[3];
+  const bool mig4 = p.gradient_scheme == 1;
   for (int d = 0; d < nd; ++d) {
     for (int c = 0; c < nv; ++c) {
-      P1[d][c] = op_e6(P[c], d);
+      P1[d][c] = mig4 ? op_ig4(P[c], d, p.periodic[d] != 0, p.n[d]) : op_e6(P[c], d);
       P2[d][c] = op_second(P[c], P1[d][c], d);
     }
-    if (viscous) T1[d] = op_e6(T, d);
+    if (viscous) T1[d] = mig4 ? op_ig4(T, d, p.periodic[d] != 0, p.n[d]) : op_e6(T, d);
   }
   // interface fluxes G = F^ - F^v for faces i+1/2, i = -1..n-1
   ORC_PHASE(PH_FACE);
@@ -1055,7 +1160,15 @@ void orc_op1d(int kind, int n, const double* f, double* out) {
     case 1: o = op_second(F, op_e6(F, 0), 0); break;
     case 2: o = op_interp(F, 0, 0); break;
     case 3: o = op_D(F, 0); break;
-    default: o = op_e4(F, 0); break;
+    case 4: o = op_e4(F, 0); break;
+    case 5: o = op_ig4(F, 0, true, n); break;
+    default: {
+      // open line: the values themselves, no wrap
+      std::vector<real> line(f, f + n), g;
+      ig4_line_open(line.data(), n, g);
+      for (int i = 0; i < n; ++i) out[i] = Dbl(g[i]);
+      return;
+    }
   }
   for (int i = 0; i < n; ++i) out[i] = Dbl(o.at(i, 0, 0));
 }

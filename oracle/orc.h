@@ -37,6 +37,9 @@ typedef struct {
   double t_ref;          /* reference temperature (T = p/rho units) for Sutherland */
   double alpha_damping;  /* alpha^D of Eq. (AD-eqn1); paper: 4 */
   double mp_alpha, mp_beta, mp_eps;  /* App. E limiter constants */
+  int gradient_scheme;   /* 0 = MEG6: explicit E6 gradients (Eq. E6_grads);
+                            1 = MIG4: implicit IG4 gradients (Eq. IG4_grads), cyclic on periodic
+                            axes, explicit end rows on open lines (reading A33) */
 } orc_params;
 
 typedef struct orc_solver orc_solver;
