@@ -87,11 +87,12 @@ def face_alg_bytes(wl):
 class Workload:
     """Inputs and per-step driving of one benchmark workload."""
 
-    def __init__(self, kind, edge=N_CELLS_EDGE, precision="fp64"):
+    def __init__(self, kind, edge=N_CELLS_EDGE, precision="fp64", scheme="meg6"):
         from paper_2303_10785_b300 import inputs as I
 
         self.kind = kind
         self.precision = precision
+        self.scheme = scheme
         self.inflow = self.sponge = None
         if kind == "tgv":
             n = (edge,) * 3
@@ -110,9 +111,11 @@ class Workload:
             self.flops_key = "jet3d_viscous"
             self.config = {"cells": n[0] * n[1] * n[2], "dt": JET_DT, "reynolds_d": 1e5, "sutherland": True,
                            "inflow_perturbation": "1 % velocity, SplitMix64(seed, step, cell, component)"}
-        self.case = dict(self.case, precision=precision)
+        self.case = dict(self.case, precision=precision, gradient_scheme=scheme)
         if precision != "fp64":
             self.name += "_" + precision
+        if scheme != "meg6":
+            self.name += "_" + scheme
         self.n = n
         self.cells = n[0] * n[1] * n[2]
         self.faces_per_rhs = sum((n[0] + (d == 0)) * (n[1] + (d == 1)) * (n[2] + (d == 2)) for d in range(3))
@@ -398,7 +401,8 @@ def run_gpu(args, wl):
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if wl.precision == "mixed" else "f64", "data": "synthetic",
-        "config": dict({"workload": wl.name}, **wl.config, precision=wl.precision, parallelism=f"replicas{world}",
+        "config": dict({"workload": wl.name}, **wl.config, precision=wl.precision, gradients=wl.scheme,
+                       parallelism=f"replicas{world}",
                        l2=f"workspace {solver.workspace_bytes / 1e9:.1f} GB >> 126 MB L2, no flush"),
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "step_roofline": step_roofline,
         "clocks": clocks.summary(),
@@ -494,6 +498,8 @@ def main():
     ap.add_argument("--pool-gb", type=float, default=64.0, help="serving: device pool for job workspaces")
     ap.add_argument("--slots", type=int, default=64, help="serving: batch slots")
     ap.add_argument("--chunk", type=int, default=8, help="serving: steps between looks at the queue")
+    ap.add_argument("--scheme", default="meg6", choices=["meg6", "mig4"],
+                    help="gradients: explicit E6 (MEG6) or implicit IG4 line solves (MIG4)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="mixed: FP32 reconstruction and fluxes, FP64 state, metrics, GCL and RK accumulation")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -508,7 +514,7 @@ def main():
         if dist_env()[1] == 0 and args.impl != "reference":
             run_serving(args)
         return
-    wl = Workload(args.workload, args.edge, args.precision)
+    wl = Workload(args.workload, args.edge, args.precision, args.scheme)
     if args.impl == "reference":
         run_reference(args, wl)
     else:

@@ -58,6 +58,17 @@ enum { GBR_BC_ZEROGRAD = 1, GBR_BC_INFLOW = 2 };
  *                 and FP64 runs only as a whole). */
 enum { GBR_PREC_FP64 = 0, GBR_PREC_MIXED = 1 };
 
+/* Gradients of the primitives (gbr_params.gradient_scheme), Sec. 5.1 step 1:
+ * GBR_GRAD_MEG6: explicit sixth-order E6 (Eq. E6_grads).
+ * GBR_GRAD_MIG4: implicit fourth-order IG4 (Eq. IG4_grads, alpha = 5/14): one
+ *                tridiagonal solve per grid line -- cyclic on periodic axes; on
+ *                open axes over the padded line, whose three end points at each
+ *                side take explicit rows (second-order one-sided, fourth-order
+ *                biased, fourth-order central).  The metrics keep the E6-based
+ *                operators of Sec. 6 (the paper builds them from IG4 for MIG4).
+ *                Not available in gbr_rhs_static or in a batch. */
+enum { GBR_GRAD_MEG6 = 0, GBR_GRAD_MIG4 = 1 };
+
 typedef struct {
   int ndim;            /* 2 or 3 */
   int n[3];            /* cells per axis (n[2] = 1 in 2D) */
@@ -73,6 +84,7 @@ typedef struct {
   double mp_alpha, mp_beta, mp_eps; /* App. E limiter constants (4, 4, 1e-20) */
   int moving;          /* 1: reserve grid-velocity, time-metric and GCL storage */
   int precision;       /* GBR_PREC_FP64 or GBR_PREC_MIXED */
+  int gradient_scheme; /* GBR_GRAD_MEG6 or GBR_GRAD_MIG4 */
 } gbr_params;
 
 /* Prescribed sinusoidal node motion (Sec. 7.2 families):

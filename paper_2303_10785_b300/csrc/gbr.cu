@@ -106,6 +106,19 @@ __global__ void k_grad1(RhsArgsT<R> A, Box b0, Box b1, Box b2) {
   body_grad1<ND>(A, e, i, j, k);
 }
 
+// MIG4: one thread per (line, field); blockIdx.y is the field (primitives, then T)
+template <int ND, class R = double>
+__global__ void k_ig4(RhsArgsT<R> A, int e, Box lines, const double* table) {
+  constexpr int NV = ND + 2;
+  BOX_THREAD(lines);
+  const int f = blockIdx.y;
+  const long long PC = A.L.pcount;
+  const R* src = (f < NV) ? A.prim + f * PC : A.temp;
+  ig4_line(A.L, table, e, src, A.g1[e] + f * PC, i, j, k);
+}
+
+__global__ void k_ig4_factor(double* table, int n, int periodic) { ig4_factor(table, n, periodic != 0); }
+
 template <int ND, class R = double>
 __global__ void k_grad2(RhsArgsT<R> A, Box b0, Box b1, Box b2) {
   const int e = blockIdx.y;
@@ -175,7 +188,7 @@ struct Plan {
 
 enum Slot {
   SL_Q0, SL_Q1, SL_Q2, SL_PRIM, SL_TEMP, SL_G1, SL_G2, SL_FLUX, SL_NODES, SL_NVEL, SL_XC, SL_VC, SL_XD, SL_MH,
-  SL_DET, SL_MU, SL_MT, SL_FH, SL_FU, SL_FT, SL_GCL, SL_JAC, SL_SIGMA, SL_INFLOW, SL_SCAL, SL_ERR, SL_COUNT
+  SL_DET, SL_MU, SL_MT, SL_FH, SL_FU, SL_FT, SL_GCL, SL_JAC, SL_SIGMA, SL_INFLOW, SL_SCAL, SL_ERR, SL_IG4, SL_COUNT
 };
 
 struct Sizes {
@@ -201,6 +214,12 @@ bool valid_params(const gbr_params* p, std::string& why) {
   if (p->reynolds > 0.0 && !(p->prandtl > 0.0)) { why = "prandtl must be positive"; return false; }
   if (p->sutherland_s > 0.0 && !(p->t_ref > 0.0)) { why = "t_ref must be positive"; return false; }
   if (p->precision != GBR_PREC_FP64 && p->precision != GBR_PREC_MIXED) { why = "unknown precision"; return false; }
+  if (p->gradient_scheme != GBR_GRAD_MEG6 && p->gradient_scheme != GBR_GRAD_MIG4) {
+    why = "unknown gradient scheme";
+    return false;
+  }
+  for (int d = 0; d < p->ndim; ++d)
+    if (p->gradient_scheme == GBR_GRAD_MIG4 && p->n[d] < 4) { why = "MIG4 needs at least 4 cells per axis"; return false; }
   long long cells = (long long)p->n[0] * p->n[1] * (p->ndim == 3 ? p->n[2] : 1);
   if (cells > (1LL << 34)) { why = "grid too large"; return false; }
   return true;
@@ -249,6 +268,10 @@ Plan plan_of(const gbr_params* p, const Layout& L) {
   P.add(D * nv * L.n[1] * L.n[2]);                // SL_INFLOW
   P.add(D * S_NSCAL);                             // SL_SCAL
   P.add(sizeof(int) * 4);                         // SL_ERR
+  long long ig4 = 0;                               // SL_IG4: MIG4 line-solve factors per direction
+  if (p->gradient_scheme == GBR_GRAD_MIG4)
+    for (int d = 0; d < nd; ++d) ig4 += ig4_table_len(L.n[d], L.per[d] != 0);
+  P.add(D * ig4);
   P.total = (P.total + 255) & ~(size_t)255;
   return P;
 }
@@ -293,6 +316,7 @@ struct gbr_ctx {
   void *prim, *temp, *g1[3], *g2[3], *flux[3];  // element type double (FP64) or float (mixed)
   double *nodes, *nvel, *xc, *vc, *xd, *mh, *det, *mu, *mt, *fh[3], *fu[3], *ft[3], *gcl, *jac;
   double *sigma, *inflow, *scal;
+  double* ig4[3];  // MIG4 line-solve factors per direction (or null)
   int* err;
   bool visc, mov, have_sponge, have_motion, metrics_ready;
   double qamb[5];
@@ -608,8 +632,19 @@ gbr_status run_rhs_nd(gbr_ctx* c, const double* qs, const double* q0, double* ou
     g1 = std::max(g1, grid_of(B.grad1[e], kBlock));
     g2 = std::max(g2, grid_of(B.grad2[e], kBlock));
   }
-  k_grad1<ND, R><<<dim3(g1, ND), kBlock, 0, st>>>(A, B.grad1[0], B.grad1[1], B.grad1[2]);
-  CKL("k_grad1");
+  if (c->p.gradient_scheme == GBR_GRAD_MIG4) {
+    const int nf = L.nv + (c->visc ? 1 : 0);
+    for (int e = 0; e < ND; ++e) {
+      Box lines = B.grad1[e];
+      lines.lo[e] = 0;
+      lines.hi[e] = 1;
+      k_ig4<ND, R><<<dim3(grid_of(lines, 128), nf), 128, 0, st>>>(A, e, lines, c->ig4[e]);
+      CKL("k_ig4");
+    }
+  } else {
+    k_grad1<ND, R><<<dim3(g1, ND), kBlock, 0, st>>>(A, B.grad1[0], B.grad1[1], B.grad1[2]);
+    CKL("k_grad1");
+  }
   k_grad2<ND, R><<<dim3(g2, ND), kBlock, 0, st>>>(A, B.grad2[0], B.grad2[1], B.grad2[2]);
   CKL("k_grad2");
   for (int d = 0; d < ND; ++d) {
@@ -704,6 +739,16 @@ void carve(gbr_ctx* c) {
   c->inflow = ptr(SL_INFLOW);
   c->scal = ptr(SL_SCAL);
   c->err = (int*)(c->ws + P.off[SL_ERR]);
+  {
+    size_t toff = 0;
+    for (int d = 0; d < 3; ++d) {
+      c->ig4[d] = nullptr;
+      if (d < L.nd && P.len[SL_IG4]) {
+        c->ig4[d] = (double*)(c->ws + P.off[SL_IG4]) + toff;
+        toff += (size_t)ig4_table_len(L.n[d], L.per[d] != 0);
+      }
+    }
+  }
 }
 
 Phys phys_of(const gbr_params* p) {
@@ -776,6 +821,15 @@ gbr_status gbr_create(const gbr_params* p, const double* nodes, const double* no
     gbr_status s = fail(c, GBR_ECUDA, std::string("clear workspace: ") + cudaGetErrorString(e));
     delete c;
     return s;
+  }
+  if (p->gradient_scheme == GBR_GRAD_MIG4) {
+    for (int d = 0; d < L.nd; ++d) k_ig4_factor<<<1, 1, 0, c->stream>>>(c->ig4[d], L.n[d], L.per[d]);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      gbr_status s = fail(c, GBR_ECUDA, std::string("MIG4 factors: ") + cudaGetErrorString(e));
+      delete c;
+      return s;
+    }
   }
   gbr_status s = upload_nodes(c, nodes, node_vel);
   if (s != GBR_OK) {
@@ -1090,6 +1144,7 @@ const char* static_param_error(const gbr_params* p) {
   if (p->reynolds > 0.0 && !(p->prandtl > 0.0)) return "prandtl must be positive";
   if (p->sutherland_s > 0.0 && !(p->t_ref > 0.0)) return "t_ref must be positive";
   if (p->precision != GBR_PREC_FP64) return "only the FP64 path is supported here";
+  if (p->gradient_scheme != GBR_GRAD_MEG6) return "only MEG6 is supported here";
   return nullptr;
 }
 

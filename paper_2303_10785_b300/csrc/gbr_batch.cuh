@@ -683,6 +683,7 @@ gbr_status gbr_batch_add(gbr_batch* b, gbr_ctx* c, double cfl_or_neg_dt) {
   if ((int)b->members.size() >= b->max_members) return bfail(b, GBR_ENOMEM, "batch is full");
   if (!c->metrics_ready) return bfail(b, GBR_ESTATE, "metrics not computed");
   if (c->mov || c->have_motion) return bfail(b, GBR_EINVAL, "moving meshes are stepped with gbr_rk_step, not in a batch");
+  if (c->p.gradient_scheme != GBR_GRAD_MEG6) return bfail(b, GBR_EINVAL, "MIG4 contexts are stepped with gbr_rk_step, not in a batch");
   if (c->stream != b->stream) return bfail(b, GBR_EINVAL, "the context must use the batch's stream");
   for (gbr_ctx* x : b->members)
     if (x == c) return bfail(b, GBR_EINVAL, "context already in the batch");

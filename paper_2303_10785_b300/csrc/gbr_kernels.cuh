@@ -605,6 +605,130 @@ GBR_HD void body_grad2(const RhsArgsT<R>& A, int e, int i, int j, int k) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// MIG4 (Eq. IG4_grads, alpha = 5/14): alpha f'_{i-1} + f'_i + alpha f'_{i+1} =
+// (2 + alpha)/3 (f_{i+1} - f_{i-1}) + (4 alpha - 1)/12 (f_{i+2} - f_{i-2}).
+// The matrix is the same for every line of a direction, so its Thomas factors
+// are computed once (on the device, ig4_factor) and each line is one forward and
+// one backward sweep.  Periodic axis: the cyclic system over the n cells by the
+// Sherman-Morrison formula (gamma = -1: first diagonal 2, last 1 + alpha^2,
+// correction vector z solved once); open axis: the padded line of n + 2H cells
+// whose three end points at each side take explicit rows (second-order
+// one-sided, fourth-order biased, fourth-order central).
+// Table layout per direction (doubles): periodic: cp[n], inv[n], z[n], kinv;
+// open: cp[m], inv[m] with m = n + 2H.
+// ---------------------------------------------------------------------------
+constexpr double kIg4Alpha = 5.0 / 14.0;
+
+inline long long ig4_table_len(int n, bool periodic) { return periodic ? 3LL * n + 1 : 2LL * (n + 2 * H); }
+
+GBR_HD void ig4_factor(double* t, int n, bool periodic) {
+  const double al = kIg4Alpha;
+  if (periodic) {
+    double* cp = t;
+    double* inv = t + n;
+    double* z = t + 2 * n;
+    // modified diagonal: b_0 = 1 - gamma = 2, b_{n-1} = 1 - alpha^2 / gamma = 1 + alpha^2
+    double den = 2.0;
+    inv[0] = 1.0 / den;
+    cp[0] = al * inv[0];
+    for (int i = 1; i < n; ++i) {
+      const double b = (i == n - 1) ? 1.0 + al * al : 1.0;
+      const double c = (i == n - 1) ? 0.0 : al;
+      den = b - al * cp[i - 1];
+      inv[i] = 1.0 / den;
+      cp[i] = c * inv[i];
+    }
+    // z = T'^-1 u, u = (gamma, 0, .., 0, alpha)
+    z[0] = -1.0 * inv[0];
+    for (int i = 1; i < n; ++i) z[i] = ((i == n - 1 ? al : 0.0) - al * z[i - 1]) * inv[i];
+    for (int i = n - 2; i >= 0; --i) z[i] -= cp[i] * z[i + 1];
+    // x = y - (y_0 - alpha y_{n-1}) / (1 + z_0 - alpha z_{n-1}) z   (v = (1, 0, .., 0, alpha / gamma))
+    t[3 * n] = 1.0 / (1.0 + z[0] - al * z[n - 1]);
+  } else {
+    const int m = n + 2 * H;
+    double* cp = t;
+    double* inv = t + m;
+    for (int i = 0; i < m; ++i) {
+      const bool expl = i < 3 || i >= m - 3;
+      const double a = expl ? 0.0 : al, c = expl ? 0.0 : al;
+      const double den = 1.0 - (i > 0 ? a * cp[i - 1] : 0.0);
+      inv[i] = 1.0 / den;
+      cp[i] = c * inv[i];
+    }
+  }
+}
+
+// IG4 right side of row i from the values f_{i-2} .. f_{i+2} (stride s)
+template <class R>
+GBR_HD R ig4_rhs(const R* f, long long p, long long s) {
+  return R((2.0 + kIg4Alpha) / 3.0) * (f[p + s] - f[p - s]) + R((4.0 * kIg4Alpha - 1.0) / 12.0) * (f[p + 2 * s] - f[p - 2 * s]);
+}
+
+// One line of f' along e through padded cell (i, j, k) (coordinate e ignored): field f, output g
+template <class R>
+GBR_HD void ig4_line(const Layout& L, const double* t, int e, const R* f, R* g, int i, int j, int k) {
+  const R al = R(kIg4Alpha);
+  const long long s = L.ps[e];
+  int c0[3] = {i, j, k};
+  c0[e] = 0;
+  const long long base = pidx(L, c0[0], c0[1], c0[2]);  // cell 0 of the line
+  const int n = L.n[e];
+  if (L.per[e]) {
+    const double* cp = t;
+    const double* inv = t + n;
+    const double* z = t + 2 * n;
+    // forward sweep (rp kept in g), backward sweep (y in g)
+    R prev = R(0);
+    for (int m = 0; m < n; ++m) {
+      const long long p = base + m * s;
+      const R r = ig4_rhs(f, p, s);
+      prev = (m == 0) ? r * R(inv[0]) : (r - al * prev) * R(inv[m]);
+      g[p] = prev;
+    }
+    R y = prev;
+    for (int m = n - 2; m >= 0; --m) {
+      const long long p = base + m * s;
+      y = g[p] - R(cp[m]) * y;
+      g[p] = y;
+    }
+    const R fac = (y - al * g[base + (n - 1) * s]) * R(t[3 * n]);
+    for (int m = 0; m < n; ++m) {
+      const long long p = base + m * s;
+      g[p] = g[p] - fac * R(z[m]);
+    }
+    for (int m = 1; m <= 3; ++m) {  // periodic images of the derivative the gradient box needs
+      g[base - m * s] = g[base + (n - m) * s];
+      g[base + (n - 1 + m) * s] = g[base + (m - 1) * s];
+    }
+  } else {
+    const int M = n + 2 * H;
+    const double* cp = t;
+    const double* inv = t + M;
+    const long long b0 = base - H * s;  // padded cell -H: row 0
+    R prev = R(0);
+    for (int m = 0; m < M; ++m) {
+      const long long p = b0 + m * s;
+      R r;
+      if (m == 0) r = R(-1.5) * f[p] + R(2) * f[p + s] - R(0.5) * f[p + 2 * s];
+      else if (m == 1) r = R(-0.25) * f[p - s] - R(5.0 / 6.0) * f[p] + R(1.5) * f[p + s] - R(0.5) * f[p + 2 * s] + f[p + 3 * s] * R(1.0 / 12.0);
+      else if (m == 2 || m == M - 3) r = R(2.0 / 3.0) * (f[p + s] - f[p - s]) - (f[p + 2 * s] - f[p - 2 * s]) * R(1.0 / 12.0);
+      else if (m == M - 2) r = R(0.25) * f[p + s] + R(5.0 / 6.0) * f[p] - R(1.5) * f[p - s] + R(0.5) * f[p - 2 * s] - f[p - 3 * s] * R(1.0 / 12.0);
+      else if (m == M - 1) r = R(1.5) * f[p] - R(2) * f[p - s] + R(0.5) * f[p - 2 * s];
+      else r = ig4_rhs(f, p, s);
+      const bool expl = m < 3 || m >= M - 3;
+      prev = (m == 0 || expl) ? r * R(inv[m]) : (r - al * prev) * R(inv[m]);
+      g[p] = prev;
+    }
+    R y = prev;
+    for (int m = M - 2; m >= 0; --m) {
+      const long long p = b0 + m * s;
+      y = g[p] - R(cp[m]) * y;
+      g[p] = y;
+    }
+  }
+}
+
 // Both derivatives along e in one pass over the first-derivative box: f' at the cell (stored),
 // and, inside the second-derivative box `b2`, f'' from f' of the two neighbours recomputed with
 // the same stencil -- the values are those of body_grad1 followed by body_grad2.

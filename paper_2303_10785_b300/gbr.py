@@ -19,6 +19,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENONFINITE", "ETIMEOUT", "ES
 (GBR_FIELD_CELL_METRICS, GBR_FIELD_CELL_DET, GBR_FIELD_CELL_TIME, GBR_FIELD_FACE_HAT, GBR_FIELD_FACE_UNHAT,
  GBR_FIELD_FACE_TIME, GBR_FIELD_GCL, GBR_FIELD_FACE_FLUX) = range(8)
 GBR_PREC_FP64, GBR_PREC_MIXED = 0, 1
+GBR_GRAD_MEG6, GBR_GRAD_MIG4 = 0, 1
 
 
 class gbr_params(ctypes.Structure):
@@ -39,6 +40,7 @@ class gbr_params(ctypes.Structure):
         ("mp_eps", ctypes.c_double),
         ("moving", ctypes.c_int),
         ("precision", ctypes.c_int),
+        ("gradient_scheme", ctypes.c_int),
     ]
 
 
@@ -156,6 +158,7 @@ def make_params(case):
         setattr(p, key, float(case[key]))
     p.moving = int(case.get("moving", 0))
     p.precision = {"fp64": GBR_PREC_FP64, "mixed": GBR_PREC_MIXED}[case.get("precision", "fp64")]
+    p.gradient_scheme = {"meg6": GBR_GRAD_MEG6, "mig4": GBR_GRAD_MIG4}[case.get("gradient_scheme", "meg6")]
     return p
 
 

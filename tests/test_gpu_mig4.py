@@ -1,0 +1,95 @@
+"""GPU: MIG4 gradients (gbr_params.gradient_scheme = GBR_GRAD_MIG4) against the MIG4 oracle.
+
+The CUDA path solves each grid line's tridiagonal IG4 system with factors computed once per
+direction (cyclic by Sherman-Morrison on periodic axes, explicit end rows on open axes); the
+oracle builds and solves each line's system on its own.  Same tolerances as the MEG6 parity
+tests: right-hand sides within 1e-12 of the cancellation scale, states within 1e-12 after a
+step; the mixed path within its own FP32 tolerance."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2303_10785_b300 import gbr
+from _util import cancellation_scale
+from test_gpu_parity import CASES, case_jet, rel_state
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+
+
+def mig4(case, **kw):
+    return dict(case, gradient_scheme="mig4", **kw)
+
+
+def rhs_err(orc, s, q):
+    Lg = s.rhs().cpu().numpy()
+    Lo = orc.rhs(q)
+    return (np.abs(Lg - Lo).reshape(q.shape[0], -1).max(axis=1) / cancellation_scale(orc, q)).max()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_mig4_rhs_matches_oracle(name):
+    case, nodes, vel, q = CASES[name]()
+    orc = O.Oracle(mig4(case), nodes, vel)
+    s = gbr.Solver(mig4(case), nodes, vel)
+    s.set_state(q)
+    assert rhs_err(orc, s, q) < 1e-12
+    # and the gradients are not the E6 ones
+    meg6 = O.Oracle(case, nodes, vel)
+    assert np.abs(meg6.rhs(q) - s.rhs().cpu().numpy()).max() > 1e-9
+    s.close()
+
+
+def test_mig4_open_axes_jet_step_matches_oracle():
+    case, nodes, vel, q, extra = case_jet()
+    orc = O.Oracle(mig4(case), nodes, vel)
+    s = gbr.Solver(mig4(case), nodes, vel)
+    for obj in (orc, s):
+        obj.set_inflow(extra["inflow"])
+        obj.set_sponge(extra["sigma"], extra["qamb"])
+    s.set_state(q)
+    assert rhs_err(orc, s, q) < 1e-12
+    qo = orc.rk3(q, 2e-3)
+    s.rk_step(-2e-3)
+    s.sync()
+    assert rel_state(s.get_state(), qo) < 1e-12
+    s.close()
+
+
+def test_mig4_vortex_steps_match_oracle():
+    case, nodes, vel, q = CASES["2d_vortex"]()
+    orc = O.Oracle(mig4(case), nodes, vel)
+    s = gbr.Solver(mig4(case), nodes, vel)
+    s.set_state(q)
+    qo = q.copy()
+    for _ in range(10):
+        qo = orc.rk3(qo, orc.dt(qo, 0.4))
+        s.rk_step(0.4)
+    s.sync()
+    assert rel_state(s.get_state(), qo) < 1e-11
+    s.close()
+
+
+def test_mig4_mixed_precision_rhs():
+    case, nodes, vel, q = CASES["3d_tgv"]()
+    orc = O.Oracle(mig4(case), nodes, vel)
+    s = gbr.Solver(mig4(case, precision="mixed"), nodes, vel)
+    s.set_state(q)
+    assert rhs_err(orc, s, q) < 2e-5
+    s.close()
+
+
+def test_mig4_rejected_by_batch():
+    case, nodes, vel, q = CASES["2d_vortex"]()
+    s = gbr.Solver(mig4(case), nodes, vel)
+    b = gbr.Batch(1)
+    with pytest.raises(gbr.GbrError):
+        b.add(s, 0.4)
+    b.close()
+    s.close()
