@@ -1,9 +1,10 @@
 // sm_103a library: kernels and the C ABI declared in include/gbr.h.
 //
-// Per RK stage (all FP64, every step of the path in these kernels):
-//   k_prim -> k_halo (one launch per axis) -> k_grad1 -> k_grad2 ->
-//   k_face (one launch per direction) -> k_update (divergence, GCL term,
-//   sponge, SSP-RK3 combination)
+// Per RK stage (FP64, or the mixed path's FP32 where gbr_params.precision says;
+// every step of the path in these kernels):
+//   k_prim_halo (primitives and all ghost layers in one pass) -> k_grad1 (E6;
+//   MIG4: k_ig4, one launch per direction) -> k_grad2 -> k_face (one launch per
+//   direction) -> k_update (divergence, GCL term, sponge, SSP-RK3 combination)
 // Geometry (set-up, or every stage of a moving mesh):
 //   k_motion -> k_centroid -> k_coordd -> k_metrics -> k_face_metrics -> k_gcl
 // Time step: k_dt (block min with warp shuffles + atomicMin on the bits of a
@@ -25,12 +26,18 @@ using namespace gbr;
 
 namespace {
 
-// Launch shape of the interface kernel (tuning knobs, set at compile time).
+// Launch shape of the interface kernel (tuning knobs, set at compile time).  The FP64
+// instantiations are FP64-pipe bound (one 128-thread block per SM's register share is
+// enough); the FP32 ones are memory-latency bound and run 6 blocks per SM (80 registers,
+// measured 17 % faster than the unconstrained 128 registers on the 128^3 TGV).
 #ifndef GBR_FACE_BLOCK
 #define GBR_FACE_BLOCK 128
 #endif
 #ifndef GBR_FACE_MIN_BLOCKS
 #define GBR_FACE_MIN_BLOCKS 1
+#endif
+#ifndef GBR_FACE_MIN_BLOCKS_F32
+#define GBR_FACE_MIN_BLOCKS_F32 6
 #endif
 
 constexpr int kBlock = 256;
@@ -93,6 +100,12 @@ __global__ void k_prim(RhsArgsT<R> A, Box b) {
 }
 
 template <int ND, class R = double>
+__global__ void k_prim_halo(RhsArgsT<R> A, const double* q, Box b) {
+  BOX_THREAD(b);
+  body_prim_halo<ND>(A, q, i, j, k);
+}
+
+template <int ND, class R = double>
 __global__ void k_halo(RhsArgsT<R> A, int d, Box b) {
   BOX_THREAD(b);
   body_halo<ND>(A, d, i, j, k);
@@ -128,7 +141,8 @@ __global__ void k_grad2(RhsArgsT<R> A, Box b0, Box b1, Box b2) {
 }
 
 template <int ND, bool VISC, bool MOV, class R = double>
-__global__ void __launch_bounds__(GBR_FACE_BLOCK, GBR_FACE_MIN_BLOCKS) k_face(RhsArgsT<R> A, int d, Box b) {
+__global__ void __launch_bounds__(GBR_FACE_BLOCK, sizeof(R) == 4 ? GBR_FACE_MIN_BLOCKS_F32 : GBR_FACE_MIN_BLOCKS)
+    k_face(RhsArgsT<R> A, int d, Box b) {
   BOX_THREAD(b);
   body_face<ND, VISC, MOV>(A, d, i, j, k);
 }
@@ -621,12 +635,10 @@ gbr_status run_rhs_nd(gbr_ctx* c, const double* qs, const double* q0, double* ou
   const RhsArgsT<R> A = rhs_args_r<R>(c, qs);
   const RhsBoxes B = rhs_boxes(L);
   const Box bi = B.inner;
-  k_prim<ND, R><<<grid_of(bi, kBlock), kBlock, 0, st>>>(A, bi);
-  CKL("k_prim");
-  for (int d = 0; d < ND; ++d) {
-    k_halo<ND, R><<<grid_of(B.halo[d], kBlock), kBlock, 0, st>>>(A, d, B.halo[d]);
-    CKL("k_halo");
-  }
+  // primitives and all ghost layers in one pass over the padded box
+  const Box pad = pad_box(L, H, H);
+  k_prim_halo<ND, R><<<grid_of(pad, kBlock), kBlock, 0, st>>>(A, qs, pad);
+  CKL("k_prim_halo");
   unsigned g1 = 0, g2 = 0;
   for (int e = 0; e < ND; ++e) {
     g1 = std::max(g1, grid_of(B.grad1[e], kBlock));

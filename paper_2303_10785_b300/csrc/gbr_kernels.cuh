@@ -1106,12 +1106,15 @@ GBR_HD bool body_update(const UpdArgsT<R>& U, int i, int j, int k) {
   bool bad = false;
   const double dtc = (U.mode == 1) ? (*U.dt) * U.cc : 0.0;
   for (int v = 0; v < NV; ++v) {
-    double res = 0.0;
+    // flux differences in the fluxes' own type (for neighbouring FP32 fluxes within a factor 2 of
+    // each other the difference is exact), summed and converted to FP64 once
+    R rsum = R(0);
     for (int d = 0; d < ND; ++d) {
       const long long fhi = fidx(L, d, i, j, k);
       const long long FC = L.fcount[d];
-      res = res - ((double)U.flux[d][v * FC + fhi] - (double)U.flux[d][v * FC + fhi - L.fs[d][d]]);
+      rsum = rsum - (U.flux[d][v * FC + fhi] - U.flux[d][v * FC + fhi - L.fs[d][d]]);
     }
+    const double res = (double)rsum;
     const double qv = U.qs[v * NC + c];
     double Lv = MOV ? J * gfma(-U.gcl[c], qv, res) : J * res;
     if (U.sigma) Lv = gfma(-U.sigma[c], qv - U.qamb[v], Lv);
@@ -1164,6 +1167,9 @@ GBR_HD double body_dt(const DtArgs& D, int i, int j, int k) {
     }
     nu_eff = ph.dt_visc_fac * mu * ir;
   }
+  // min over directions of 1/(|U| + c |grad xi|) and 1/(nu_eff |grad xi|^2) as one division by the
+  // largest denominator: division is correctly rounded and monotone, so the result is the same value
+  double worst = 0.0;
   for (int ee = 0; ee < ND; ++ee) {
     double Uc = D.mt ? D.mt[ee * EC + e] * J : 0.0;
     double g2 = 0.0;
@@ -1172,10 +1178,10 @@ GBR_HD double body_dt(const DtArgs& D, int i, int j, int k) {
       Uc = gfma(m, u[a], Uc);
       g2 = gfma(m, m, g2);
     }
-    best = gmin(best, 1.0 / (std::fabs(Uc) + cs * sqrt(g2)));
-    if (ph.viscous) best = gmin(best, 1.0 / (nu_eff * g2));
+    worst = gmax(worst, gabs(Uc) + cs * sqrt(g2));
+    if (ph.viscous) worst = gmax(worst, nu_eff * g2);
   }
-  return best;
+  return gmin(best, 1.0 / worst);
 }
 
 }  // namespace gbr
