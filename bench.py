@@ -416,8 +416,9 @@ def run_gpu(args, wl):
 def run_serving(args):
     """The serving stream: jobs of mixed kinds, sizes and precisions with Poisson arrivals at an
     offered load of `--load` x the measured FP64 per-job capacity, served (1) by the plain FP64
-    per-job form (one job at a time through gbr_rk_step) and (2) by the continuous-batching server
-    (each job in its own precision); aggregate cell-RK-stage updates/s and time-to-N-steps p50/p99."""
+    per-job form (one job at a time through gbr_rk_step), (2) by the continuous-batching server
+    with each job in its own precision (the line's value) and (3) by the server with every job in
+    mixed precision; aggregate cell-RK-stage updates/s and time-to-N-steps p50/p99 of each."""
     import torch
 
     from paper_2303_10785_b300 import inputs as I
@@ -453,7 +454,8 @@ def run_serving(args):
         s.close()
     capacity = work / secs
     mean_work = float(np.mean([I.serving_job_work(sp) for sp in specs]))
-    rate = args.load * capacity / mean_work
+    # --load 0: a burst (every job arrives at t = 0), which measures the capacity of each form
+    rate = args.load * capacity / mean_work if args.load > 0 else float("inf")
 
     base = jobs_at(rate, "fp64")
     serving.run_serial(base)
@@ -468,7 +470,14 @@ def run_serving(args):
     tuning = srv.batch.tuning()
     peak = {"active": srv.peak_active, "pool_bytes": srv.peak_pool}
     srv.close()
-    errors = [j.error for j in mix + base if j.error]
+    # the same stream with every job in mixed precision
+    srv = serving.Server(pool, max_active=args.slots, chunk_steps=args.chunk)
+    allmix = jobs_at(rate, "mixed")
+    srv.run(allmix)
+    st_allmix = serving.latency_stats(allmix)
+    launches_allmix = srv.batch.info()["launches"]
+    srv.close()
+    errors = [j.error for j in mix + base + allmix if j.error]
     line = {
         "metric": METRIC, "value": st_mix["cell_rk_stage_updates_per_s"], "unit": METRIC, "n_gpus": 1,
         "steps": None, "warmup": None, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
@@ -476,11 +485,15 @@ def run_serving(args):
         "config": {"workload": f"serving_stream_{args.jobs}_jobs", "seed": args.seed, "offered_load": args.load,
                    "pool_gb": args.pool_gb, "slots": args.slots, "chunk_steps": args.chunk,
                    "l2": "working sets of the large jobs >> 126 MB L2, no flush"},
-        "serving": {"batched_mixed": st_mix, "per_job_fp64": st_base, "fp64_capacity_per_job": capacity,
-                    "arrival_rate_jobs_per_s": rate, "throughput_ratio": st_mix["cell_rk_stage_updates_per_s"]
+        "serving": {"batched_mixed": st_mix, "batched_all_mixed": st_allmix, "per_job_fp64": st_base,
+                    "fp64_capacity_per_job": capacity,
+                    "all_mixed_throughput_ratio": st_allmix["cell_rk_stage_updates_per_s"]
+                    / st_base["cell_rk_stage_updates_per_s"],
+                    "arrival_rate_jobs_per_s": rate if rate != float("inf") else "burst",
+                    "throughput_ratio": st_mix["cell_rk_stage_updates_per_s"]
                     / st_base["cell_rk_stage_updates_per_s"], "peak": peak, "tuning": tuning,
                     "errors": errors},
-        "gpu_launches": info["launches"], "clocks": clocks.summary(),
+        "gpu_launches": info["launches"] + launches_allmix, "clocks": clocks.summary(),
     }
     print(json.dumps(line), flush=True)
 
@@ -494,7 +507,8 @@ def main():
     ap.add_argument("--workload", default="tgv", choices=["tgv", "jet", "serving"])
     ap.add_argument("--jobs", type=int, default=64, help="serving: jobs in the stream")
     ap.add_argument("--seed", type=int, default=0, help="serving: stream seed")
-    ap.add_argument("--load", type=float, default=1.2, help="serving: offered load / FP64 per-job capacity")
+    ap.add_argument("--load", type=float, default=1.2,
+                    help="serving: offered load / FP64 per-job capacity (0: every job arrives at once)")
     ap.add_argument("--pool-gb", type=float, default=64.0, help="serving: device pool for job workspaces")
     ap.add_argument("--slots", type=int, default=64, help="serving: batch slots")
     ap.add_argument("--chunk", type=int, default=8, help="serving: steps between looks at the queue")

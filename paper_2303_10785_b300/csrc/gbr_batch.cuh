@@ -113,8 +113,10 @@ __global__ void __launch_bounds__(kBlock) kb_grad12(const BatchJob<R>* jobs, con
   });
 }
 
+// FP32 instantiations: 768 threads per SM (memory-latency bound, as k_face)
 template <int ND, bool VISC, class R, int BS>
-__global__ void __launch_bounds__(BS) kb_face(const BatchJob<R>* jobs, const WorkItem* items, int n, int total) {
+__global__ void __launch_bounds__(BS, sizeof(R) == 4 ? 768 / BS : 1)
+    kb_face(const BatchJob<R>* jobs, const WorkItem* items, int n, int total) {
   for_work(items, n, total, [&](const WorkItem& it, int lb) {
     const BatchJob<R>& J = jobs[it.job];
     BATCH_CELL(J.faces[it.sub]);
