@@ -246,10 +246,11 @@ class Oracle:
 
 
 def op1d(kind, f, counting=False):
-    """Line operators: 'e6', 'second', 'face', 'D', 'e4', 'ig4' on a periodic line, and 'ig4_open':
-    IG4 on an open line whose three end points at each side take the explicit end rows
+    """Line operators: 'e6', 'second', 'face', 'D', 'e4', 'ig4' on a periodic line; 'ig4_open':
+    IG4 on an open line whose three end points at each side take the explicit end rows; 'D_walls':
+    the metric derivative D on a line bounded by walls (App. C)
     (counting=True: run in the operation-counting build, for flop_counts)."""
-    k = {"e6": 0, "second": 1, "face": 2, "D": 3, "e4": 4, "ig4": 5, "ig4_open": 6}[kind]
+    k = {"e6": 0, "second": 1, "face": 2, "D": 3, "e4": 4, "ig4": 5, "ig4_open": 6, "D_walls": 7}[kind]
     f = _f64(f)
     out = np.zeros_like(f)
     _lib(counting).orc_op1d(k, f.size, _ptr(f), _ptr(out))

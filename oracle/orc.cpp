@@ -322,6 +322,91 @@ static Field op_interp(const Field& f, int d, int scheme) {
 // Sec. 6 step 2: consistent metric derivative D = delta o interp (MEG6).
 static Field op_D(const Field& f, int d) { return op_delta(op_interp(f, d, 0), d); }
 
+// ---------------------------------------------------------------------------
+// App. C (reading A35): an axis bounded by walls on both sides (no ghost nodes).
+// The field's box along d is the n cells [lo, hi); the first and last three
+// cells take one-sided derivatives, the interfaces next to the walls one-sided
+// states, so that D = delta o interp is defined on every cell and is the same
+// operator in every line (the metric identities of Sec. 6 still hold).
+// ---------------------------------------------------------------------------
+// first derivative on the whole box
+static Field op_e6_c(const Field& f, int d) {
+  Field o(f.b);
+  const int lo = f.b.lo[d], hi = f.b.hi[d];
+  FOR_BOX(o.b) {
+    int c[3] = {i, j, k};
+    const int m = c[d];
+    auto F = [&](int s) { return f.sh(i, j, k, d, s); };
+    real v;
+    if (m == lo) v = -1.5 * F(0) + 2.0 * F(1) - 0.5 * F(2);                       // 2nd order one-sided
+    else if (m == hi - 1) v = 1.5 * F(0) - 2.0 * F(-1) + 0.5 * F(-2);
+    else if (m == lo + 1)                                                           // 4th order biased (A22)
+      v = -0.25 * F(-1) - (5.0 / 6.0) * F(0) + 1.5 * F(1) - 0.5 * F(2) + F(3) / 12.0;
+    else if (m == hi - 2) v = 0.25 * F(1) + (5.0 / 6.0) * F(0) - 1.5 * F(-1) + 0.5 * F(-2) - F(-3) / 12.0;
+    else if (m == lo + 2 || m == hi - 3)                                            // 4th order central
+      v = (2.0 / 3.0) * (F(1) - F(-1)) - (F(2) - F(-2)) / 12.0;
+    else
+      v = (3.0 / 4.0) * (F(1) - F(-1)) - (3.0 / 20.0) * (F(2) - F(-2)) + (1.0 / 60.0) * (F(3) - F(-3));
+    o.at(i, j, k) = v;
+  }
+  return o;
+}
+
+// second derivative on the whole box: one-sided derivatives of f' in the two end cells,
+// the interior formula of Sec. 5.1 elsewhere (the third cell's printed sign is read as A22)
+static Field op_second_c(const Field& f, const Field& f1, int d) {
+  Field o(f.b);
+  const int lo = f.b.lo[d], hi = f.b.hi[d];
+  FOR_BOX(o.b) {
+    int c[3] = {i, j, k};
+    const int m = c[d];
+    auto G = [&](int s) { return f1.sh(i, j, k, d, s); };
+    real v;
+    if (m == lo) v = -1.5 * G(0) + 2.0 * G(1) - 0.5 * G(2);
+    else if (m == hi - 1) v = 1.5 * G(0) - 2.0 * G(-1) + 0.5 * G(-2);
+    else if (m == lo + 1) v = -0.25 * G(-1) - (5.0 / 6.0) * G(0) + 1.5 * G(1) - 0.5 * G(2) + G(3) / 12.0;
+    else if (m == hi - 2) v = 0.25 * G(1) + (5.0 / 6.0) * G(0) - 1.5 * G(-1) + 0.5 * G(-2) - G(-3) / 12.0;
+    else
+      v = 2.0 * (f.sh(i, j, k, d, 1) - 2.0 * f.at(i, j, k) + f.sh(i, j, k, d, -1)) - 0.5 * (G(1) - G(-1));
+    o.at(i, j, k) = v;
+  }
+  return o;
+}
+
+// interface values i+1/2 for i = lo-1 .. hi-1 (the two walls included): the wall interfaces take
+// the boundary cell's own state on that side; the interfaces between the first two and the last
+// two cells take the state of the inner cell only (App. C); the others the mean of both states
+static Field op_face_c(const Field& f, const Field& f1, const Field& f2, int d) {
+  Box ob = f.b;
+  const int lo = f.b.lo[d], hi = f.b.hi[d];
+  ob.lo[d] = lo - 1;
+  Field o(ob);
+  FOR_BOX(o.b) {
+    int c[3] = {i, j, k};
+    const int m = c[d];
+    auto left = [&]() {  // state of cell m at its + face
+      return f.at(i, j, k) + 0.5 * f1.at(i, j, k) + f2.at(i, j, k) / 12.0;
+    };
+    auto right = [&]() {  // state of cell m+1 at its - face
+      return f.sh(i, j, k, d, 1) - 0.5 * f1.sh(i, j, k, d, 1) + f2.sh(i, j, k, d, 1) / 12.0;
+    };
+    real v;
+    if (m == lo - 1) v = right();
+    else if (m == hi - 1) v = left();
+    else if (m == lo) v = right();
+    else if (m == hi - 2) v = left();
+    else v = 0.5 * (left() + right());
+    o.at(i, j, k) = v;
+  }
+  return o;
+}
+
+static Field op_interp_c(const Field& f, int d) {
+  Field f1 = op_e6_c(f, d);
+  Field f2 = op_second_c(f, f1, d);
+  return op_face_c(f, f1, f2, d);
+}
+
 static Field f_mul(const Field& a, const Field& b) {
   Field o(box_and(a.b, b.b));
   FOR_BOX(o.b) { o.at(i, j, k) = a.at(i, j, k) * b.at(i, j, k); }
@@ -516,6 +601,7 @@ struct orc_solver {
   orc_params p;
   int nd = 3, nv = 5;
   bool viscous = false;
+  bool closed[3] = {false, false, false};  // wall-bounded axis without ghost nodes (App. C)
   Box inner, pad, ext, cellgeo;
   Geom g;
   std::vector<double> inflow;  // [nv][nk][nj] primitives for an x-low inflow side
@@ -623,8 +709,11 @@ int orc_solver::build_geometry(const Field* xc, const Field* vc) {
   ORC_PHASE(PH_GEOM);
   const int sch = p.metric_scheme;
   Field xd[3][3];  // xd[a][d] = d x_a / d xi_d
+  // Sec. 6 operators, App. C on wall-bounded axes
+  auto Dop = [&](const Field& f, int d) { return closed[d] ? op_delta(op_interp_c(f, d), d) : op_D(f, d); };
+  auto Iop = [&](const Field& f, int d) { return closed[d] ? op_interp_c(f, d) : op_interp(f, d, sch); };
   for (int a = 0; a < nd; ++a)
-    for (int d = 0; d < nd; ++d) xd[a][d] = sch == 0 ? op_D(xc[a], d) : op_e4(xc[a], d);
+    for (int d = 0; d < nd; ++d) xd[a][d] = sch == 0 ? Dop(xc[a], d) : op_e4(xc[a], d);
 
   Field mh[3][3];
   Field det;
@@ -635,7 +724,7 @@ int orc_solver::build_geometry(const Field* xc, const Field* vc) {
         int b = (a + 1) % 3, c = (a + 2) % 3;
         if (sch == 0) {
           // Eq. (GCL_metrics): e.g. xi^_x = (y_eta z)_zeta - (y_zeta z)_eta
-          mh[e][a] = f_sub(op_D(f_mul(xd[b][f], xc[c]), gg), op_D(f_mul(xd[b][gg], xc[c]), f));
+          mh[e][a] = f_sub(Dop(f_mul(xd[b][f], xc[c]), gg), Dop(f_mul(xd[b][gg], xc[c]), f));
         } else {
           // App. D: e.g. xi^_x = y_eta z_zeta - y_zeta z_eta (cyclic form, reading A29)
           mh[e][a] = f_sub(f_mul(xd[b][f], xd[c][gg]), f_mul(xd[b][gg], xd[c][f]));
@@ -699,16 +788,16 @@ int orc_solver::build_geometry(const Field* xc, const Field* vc) {
     Box fb = inner;
     fb.lo[d] = -1;
     fb.hi[d] = p.n[d];
-    for (int a = 0; a < nd; ++a) g.fh[d][a] = f_crop(op_interp(g.mh[d][a], d, sch), fb);
+    for (int a = 0; a < nd; ++a) g.fh[d][a] = f_crop(Iop(g.mh[d][a], d), fb);
     if (viscous) {
       for (int e = 0; e < nd; ++e)
         for (int a = 0; a < nd; ++a) {
           Field m(cellgeo);  // unhatted cell metric xi_x = (xi_x/J) * J
           FOR_BOX(cellgeo) { m.at(i, j, k) = g.mh[e][a].at(i, j, k) / g.det.at(i, j, k); }
-          g.fu[d][e][a] = f_crop(op_interp(m, d, sch), fb);
+          g.fu[d][e][a] = f_crop(Iop(m, d), fb);
         }
     }
-    if (g.moving) g.ft[d] = f_crop(op_interp(g.mt[d], d, sch), fb);
+    if (g.moving) g.ft[d] = f_crop(Iop(g.mt[d], d), fb);
   }
   // Eq. (Jacb2) on the face values, the same difference as the flux divergence (A17)
   g.gcl = Field(inner);
@@ -762,6 +851,36 @@ void orc_solver::fill_ghosts(Field* P) const {
             src[d] = n - 1;
             f.at(hi[0], hi[1], hi[2]) = f.at(src[0], src[1], src[2]);
           }
+        }
+      }
+    }
+    // slip walls (reading A36): ghost layer g mirrors cell g - 1 (n - g on the high side) --
+    // density and pressure as they are, the velocity reflected about the unit normal of the
+    // wall face, taken at the cross-section (coordinates of earlier axes clamped to the cells)
+    for (int side = 0; side < 2; ++side) {
+      if (p.periodic[d] || p.bc[d][side] != ORC_BC_WALL) continue;
+      FOR_BOX(S) {
+        int fc[3] = {i, j, k};
+        for (int e = 0; e < nd; ++e)
+          if (e != d) fc[e] = fc[e] < 0 ? 0 : (fc[e] >= p.n[e] ? p.n[e] - 1 : fc[e]);
+        fc[d] = side == 0 ? -1 : n - 1;  // the wall interface
+        real nh[3] = {0.0, 0.0, 0.0}, nn = 0.0;
+        for (int a = 0; a < nd; ++a) {
+          nh[a] = g.fh[d][a].at(fc[0], fc[1], fc[2]);
+          nn = nn + nh[a] * nh[a];
+        }
+        const real inv = 1.0 / Sqrt(nn);
+        for (int a = 0; a < nd; ++a) nh[a] = nh[a] * inv;
+        for (int gl = 1; gl <= H; ++gl) {
+          int gc[3] = {i, j, k}, sc[3] = {i, j, k};
+          gc[d] = side == 0 ? -gl : n - 1 + gl;
+          sc[d] = side == 0 ? gl - 1 : n - gl;
+          real un = 0.0;
+          for (int a = 0; a < nd; ++a) un = un + P[1 + a].at(sc[0], sc[1], sc[2]) * nh[a];
+          P[0].at(gc[0], gc[1], gc[2]) = P[0].at(sc[0], sc[1], sc[2]);
+          P[nv - 1].at(gc[0], gc[1], gc[2]) = P[nv - 1].at(sc[0], sc[1], sc[2]);
+          for (int a = 0; a < nd; ++a)
+            P[1 + a].at(gc[0], gc[1], gc[2]) = P[1 + a].at(sc[0], sc[1], sc[2]) - 2.0 * un * nh[a];
         }
       }
     }
@@ -987,13 +1106,36 @@ int orc_create(const orc_params* prm, const double* nodes, const double* node_ve
   for (int d = 0; d < s->nd; ++d) {
     if (s->p.n[d] < H && s->p.periodic[d]) { delete s; return fail("periodic axis needs at least 6 cells"); }
     if (s->p.n[d] < 1) { delete s; return fail("empty axis"); }
-    if (!s->p.periodic[d] && s->p.ghost_nodes < E) { delete s; return fail("non-periodic axis needs >= 10 ghost node layers"); }
+    if (!s->p.periodic[d] && s->p.ghost_nodes != 0 && s->p.ghost_nodes < E) {
+      delete s;
+      return fail("non-periodic axis needs >= 10 ghost node layers, or none (App. C)");
+    }
+    if (!s->p.periodic[d] && s->p.ghost_nodes == 0 && s->p.n[d] < 2 * H) {
+      delete s;
+      return fail("an axis without ghost nodes needs at least 12 cells");
+    }
+    if (!s->p.periodic[d] && s->p.ghost_nodes == 0 && node_vel) {
+      delete s;
+      return fail("moving meshes need ghost nodes on non-periodic axes");
+    }
+    for (int side = 0; side < 2; ++side)
+      if (!s->p.periodic[d] && s->p.bc[d][side] == ORC_BC_WALL && s->p.n[d] < H) {
+        delete s;
+        return fail("a wall axis needs at least 6 cells");
+      }
   }
   s->viscous = prm->reynolds > 0.0;
   s->inner = make_box(s->nd, s->p.n, 0);
   s->pad = make_box(s->nd, s->p.n, H);
   s->ext = make_box(s->nd, s->p.n, E);
   s->cellgeo = make_box(s->nd, s->p.n, 5);
+  for (int d = 0; d < s->nd; ++d) {
+    s->closed[d] = !s->p.periodic[d] && s->p.ghost_nodes == 0;
+    if (s->closed[d]) {  // geometry exists on the cells only
+      s->ext.lo[d] = s->cellgeo.lo[d] = 0;
+      s->ext.hi[d] = s->cellgeo.hi[d] = s->p.n[d];
+    }
+  }
   s->inflow.assign((size_t)s->nv * s->p.n[1] * s->p.n[2], 0.0);
   if (nodes) {
     int rc = orc_set_nodes(s, nodes, node_vel);
@@ -1162,6 +1304,17 @@ void orc_op1d(int kind, int n, const double* f, double* out) {
     case 3: o = op_D(F, 0); break;
     case 4: o = op_e4(F, 0); break;
     case 5: o = op_ig4(F, 0, true, n); break;
+    case 7: {
+      // the App. C derivative D on a wall-bounded line: the values themselves, no wrap
+      Box cb;
+      cb.lo[0] = 0; cb.hi[0] = n;
+      cb.lo[1] = cb.lo[2] = 0; cb.hi[1] = cb.hi[2] = 1;
+      Field C(cb);
+      for (int i = 0; i < n; ++i) C.at(i, 0, 0) = f[i];
+      Field D = op_delta(op_interp_c(C, 0), 0);
+      for (int i = 0; i < n; ++i) out[i] = Dbl(D.at(i, 0, 0));
+      return;
+    }
     default: {
       // open line: the values themselves, no wrap
       std::vector<real> line(f, f + n), g;

@@ -21,14 +21,17 @@
 extern "C" {
 #endif
 
-enum { ORC_BC_PERIODIC = 0, ORC_BC_ZEROGRAD = 1, ORC_BC_INFLOW = 2 };
+enum { ORC_BC_PERIODIC = 0, ORC_BC_ZEROGRAD = 1, ORC_BC_INFLOW = 2, ORC_BC_WALL = 3 };
 
 typedef struct {
   int ndim;              /* 2 or 3 */
   int n[3];              /* cells per axis; n[2] = 1 when ndim == 2 */
   int periodic[3];       /* 1 = periodic axis */
-  int ghost_nodes;       /* node layers supplied beyond each non-periodic side (>= 10) */
-  int bc[3][2];          /* non-periodic sides: ORC_BC_ZEROGRAD or ORC_BC_INFLOW (x-low only) */
+  int ghost_nodes;       /* node layers supplied beyond each non-periodic side (>= 10), or 0:
+                            the non-periodic axes end at walls and their metrics take the
+                            one-sided formulas of App. C (reading A35) */
+  int bc[3][2];          /* non-periodic sides: ORC_BC_ZEROGRAD, ORC_BC_INFLOW (x-low only) or
+                            ORC_BC_WALL (slip wall, reading A36) */
   int metric_scheme;     /* 0 = conservative metrics with the MEG6 operator (Sec. 6),
                             1 = non-conservative metrics with E4 (App. D, negative control) */
   double gamma, prandtl;

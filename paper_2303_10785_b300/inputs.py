@@ -241,6 +241,27 @@ def nodes_jet(ni=480, nj=170, nk=170, Lx=20.0, h0=0.02, ratio=1.02, G=10):
     return nodes_from_functions((ni, nj, nk), (0, 0, 0), G, f)
 
 
+def nodes_channel(n, lengths, amp=0.0):
+    """Walls at x = 0 and x = Lx (no ghost nodes: the x axis is bounded), periodic in y (and z):
+    x = xi + amp sin(pi xi / Lx) sin(2 pi eta / Ly), y = eta + amp sin(2 pi xi / Lx) sin(2 pi eta / Ly)
+    (z likewise in 3D); the walls stay the planes x = 0 and x = Lx."""
+    nd = len(n)
+    h = [L / m for L, m in zip(lengths, n)]
+    Lx = lengths[0]
+
+    def f(*I):
+        X = [I[a] * h[a] for a in range(nd)]
+        wy = np.sin(2 * np.pi * X[1] / lengths[1])
+        if nd == 3:
+            wy = wy * np.cos(2 * np.pi * X[2] / lengths[2])
+        out = [X[0] + amp * np.sin(np.pi * X[0] / Lx) * wy]
+        for a in range(1, nd):
+            out.append(X[a] + amp * np.sin(2 * np.pi * X[0] / Lx) * wy)
+        return tuple(out)
+
+    return nodes_from_functions(tuple(n), (0,) + (1,) * (nd - 1), 0, f)
+
+
 # ---------------------------------------------------------------------------
 # Cell centroids for evaluating initial conditions (input preparation only)
 # ---------------------------------------------------------------------------
