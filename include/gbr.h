@@ -47,7 +47,11 @@ typedef enum {
   GBR_ESTATE = 6       /* call out of order (e.g. stepping before metrics) */
 } gbr_status;
 
-enum { GBR_BC_ZEROGRAD = 1, GBR_BC_INFLOW = 2 };
+/* Non-periodic sides: zero-gradient ghosts; Dirichlet inflow (x-low side only, gbr_set_inflow);
+ * slip wall: ghost layer g mirrors cell g - 1, density and pressure as they are, the velocity
+ * reflected about the unit normal of the wall interface (the paper's boundary-condition table
+ * is an image missing from its text; this is the standard reflecting wall). */
+enum { GBR_BC_ZEROGRAD = 1, GBR_BC_INFLOW = 2, GBR_BC_WALL = 3 };
 
 /* Arithmetic of the right-hand side (gbr_params.precision):
  * GBR_PREC_FP64:  every step in FP64 (the paper's path).
@@ -73,8 +77,12 @@ typedef struct {
   int ndim;            /* 2 or 3 */
   int n[3];            /* cells per axis (n[2] = 1 in 2D) */
   int periodic[3];     /* 1 = periodic axis */
-  int ghost_nodes;     /* node layers supplied beyond each non-periodic side (>= 10) */
-  int bc[3][2];        /* non-periodic sides: GBR_BC_ZEROGRAD, or GBR_BC_INFLOW on the x-low side */
+  int ghost_nodes;     /* node layers supplied beyond each non-periodic side (>= 10), or 0: the
+                          non-periodic axes end at the grid's last nodes and their metrics near
+                          the ends take the one-sided formulas of App. C (>= 12 cells; static
+                          meshes only) */
+  int bc[3][2];        /* non-periodic sides: GBR_BC_ZEROGRAD, GBR_BC_WALL, or GBR_BC_INFLOW on
+                          the x-low side */
   double gamma;        /* ratio of specific heats (Sec. 2: 1.4) */
   double prandtl;      /* Sec. 2: 0.71 */
   double reynolds;     /* <= 0: Euler, no viscous flux; mu_ref = 1/reynolds */

@@ -215,12 +215,23 @@ bool valid_params(const gbr_params* p, std::string& why) {
   for (int d = 0; d < p->ndim; ++d) {
     if (p->n[d] < 1) { why = "empty axis"; return false; }
     if (p->periodic[d] && p->n[d] < H) { why = "a periodic axis needs at least 6 cells"; return false; }
-    if (!p->periodic[d] && p->ghost_nodes < E) { why = "a non-periodic axis needs ghost_nodes >= 10"; return false; }
+    if (!p->periodic[d] && p->ghost_nodes != 0 && p->ghost_nodes < E) {
+      why = "a non-periodic axis needs ghost_nodes >= 10, or 0 (walls, App. C metrics)";
+      return false;
+    }
+    if (!p->periodic[d] && p->ghost_nodes == 0 && p->n[d] < 2 * H) {
+      why = "an axis without ghost nodes needs at least 12 cells";
+      return false;
+    }
     if (!p->periodic[d]) {
       for (int s = 0; s < 2; ++s) {
         int bc = p->bc[d][s];
-        if (bc != GBR_BC_ZEROGRAD && bc != GBR_BC_INFLOW) { why = "unknown boundary condition"; return false; }
+        if (bc != GBR_BC_ZEROGRAD && bc != GBR_BC_INFLOW && bc != GBR_BC_WALL) {
+          why = "unknown boundary condition";
+          return false;
+        }
         if (bc == GBR_BC_INFLOW && !(d == 0 && s == 0)) { why = "inflow is supported on the x-low side only"; return false; }
+        if (bc == GBR_BC_WALL && p->n[d] < H) { why = "a wall axis needs at least 6 cells"; return false; }
       }
     }
   }
@@ -228,6 +239,11 @@ bool valid_params(const gbr_params* p, std::string& why) {
   if (p->reynolds > 0.0 && !(p->prandtl > 0.0)) { why = "prandtl must be positive"; return false; }
   if (p->sutherland_s > 0.0 && !(p->t_ref > 0.0)) { why = "t_ref must be positive"; return false; }
   if (p->precision != GBR_PREC_FP64 && p->precision != GBR_PREC_MIXED) { why = "unknown precision"; return false; }
+  for (int d = 0; d < p->ndim; ++d)
+    if (!p->periodic[d] && p->ghost_nodes == 0 && p->moving) {
+      why = "moving meshes need ghost nodes on non-periodic axes";
+      return false;
+    }
   if (p->gradient_scheme != GBR_GRAD_MEG6 && p->gradient_scheme != GBR_GRAD_MIG4) {
     why = "unknown gradient scheme";
     return false;
@@ -241,7 +257,9 @@ bool valid_params(const gbr_params* p, std::string& why) {
 
 Layout layout_of(const gbr_params* p) {
   int n[3] = {p->n[0], p->n[1], p->ndim == 3 ? p->n[2] : 1};
-  return make_layout(p->ndim, n, p->periodic);
+  int closed[3];
+  for (int d = 0; d < 3; ++d) closed[d] = (d < p->ndim && !p->periodic[d] && p->ghost_nodes == 0) ? 1 : 0;
+  return make_layout(p->ndim, n, p->periodic, closed);
 }
 
 // bytes of one element of the arrays computed in the path's type
@@ -502,6 +520,17 @@ GeoBoxes geo_boxes(const Layout& L) {
   int lo[3], hi[3];
   for (int d = 0; d < 3; ++d) { lo[d] = -E; hi[d] = L.n[d] + E + 1; }
   B.nodes = make_box(L, lo, hi);
+  // closed (wall-bounded) axes: geometry exists on the cells only (App. C)
+  for (int a = 0; a < L.nd; ++a) {
+    if (!L.closed[a]) continue;
+    Box* cellb[] = {&B.ext, &B.coordd[0], &B.coordd[1], &B.coordd[2], &B.metrics};
+    for (Box* b : cellb) {
+      b->lo[a] = 0;
+      b->hi[a] = L.n[a];
+    }
+    B.nodes.lo[a] = 0;
+    B.nodes.hi[a] = L.n[a] + 1;
+  }
   return B;
 }
 
@@ -1157,6 +1186,8 @@ const char* static_param_error(const gbr_params* p) {
   if (p->sutherland_s > 0.0 && !(p->t_ref > 0.0)) return "t_ref must be positive";
   if (p->precision != GBR_PREC_FP64) return "only the FP64 path is supported here";
   if (p->gradient_scheme != GBR_GRAD_MEG6) return "only MEG6 is supported here";
+  for (int d = 0; d < p->ndim; ++d)
+    if (!p->periodic[d] && p->ghost_nodes == 0) return "non-periodic axes need ghost nodes here";
   return nullptr;
 }
 

@@ -40,12 +40,13 @@ struct Layout {
   long long fs[3][3]; // face-array strides
   long long fcount[3];
   long long ncells;
-  int nn[3];          // extended node extents (n + 2E + 1 on active axes)
+  int nn[3];          // extended node extents (n + 2E + 1 on active axes, n + 1 on closed ones)
   long long ns[3];
   long long ncount;
+  int closed[3];      // wall-bounded axis without ghost nodes: no geometry extension, App. C operators
 };
 
-inline Layout make_layout(int nd, const int* n, const int* periodic) {
+inline Layout make_layout(int nd, const int* n, const int* periodic, const int* closed) {
   Layout L;
   L.nd = nd;
   L.nv = nd + 2;
@@ -53,11 +54,12 @@ inline Layout make_layout(int nd, const int* n, const int* periodic) {
     bool act = d < nd;
     L.n[d] = act ? n[d] : 1;
     L.per[d] = act ? periodic[d] : 1;
+    L.closed[d] = act && !periodic[d] && closed[d];
     L.hp[d] = act ? H : 0;
     L.pn[d] = L.n[d] + 2 * L.hp[d];
-    L.he[d] = act ? E : 0;
+    L.he[d] = (act && !L.closed[d]) ? E : 0;
     L.en[d] = L.n[d] + 2 * L.he[d];
-    L.nn[d] = act ? L.n[d] + 2 * E + 1 : 1;
+    L.nn[d] = act ? L.n[d] + 2 * L.he[d] + 1 : 1;
   }
   L.ps[0] = 1;
   L.ps[1] = L.pn[0];
@@ -238,6 +240,56 @@ GBR_HD double stencil_D_prod(const double* a, const double* b, long long e, long
 }
 
 // ---------------------------------------------------------------------------
+// App. C on a wall-bounded (closed) axis of n cells, used for every cell of such an axis:
+// f' second-order one-sided at the end cells, fourth-order biased next to them (A22's index),
+// fourth-order central third, E6 inside; f'' one-sided from f' at the two end cells, the
+// interior formula elsewhere; interface values: the wall interfaces take the boundary cell's
+// own state, the interfaces between the first (last) two cells the inner cell's state, the
+// others the mean of both van Leer states.  `f(m)` reads cell m of the line.
+// ---------------------------------------------------------------------------
+template <class F>
+GBR_HD double appc_d1(const F& f, int m, int n) {
+  if (m == 0) return -1.5 * f(0) + 2.0 * f(1) - 0.5 * f(2);
+  if (m == n - 1) return 1.5 * f(n - 1) - 2.0 * f(n - 2) + 0.5 * f(n - 3);
+  if (m == 1) return -0.25 * f(0) - (5.0 / 6.0) * f(1) + 1.5 * f(2) - 0.5 * f(3) + f(4) * (1.0 / 12.0);
+  if (m == n - 2)
+    return 0.25 * f(n - 1) + (5.0 / 6.0) * f(n - 2) - 1.5 * f(n - 3) + 0.5 * f(n - 4) - f(n - 5) * (1.0 / 12.0);
+  if (m == 2 || m == n - 3) return (2.0 / 3.0) * (f(m + 1) - f(m - 1)) - (f(m + 2) - f(m - 2)) * (1.0 / 12.0);
+  double r = (3.0 / 4.0) * (f(m + 1) - f(m - 1));
+  r = gfma(-3.0 / 20.0, f(m + 2) - f(m - 2), r);
+  return gfma(1.0 / 60.0, f(m + 3) - f(m - 3), r);
+}
+template <class F>
+GBR_HD double appc_d2(const F& f, int m, int n) {
+  auto d1 = [&](int c) { return appc_d1(f, c, n); };
+  if (m == 0) return -1.5 * d1(0) + 2.0 * d1(1) - 0.5 * d1(2);
+  if (m == n - 1) return 1.5 * d1(n - 1) - 2.0 * d1(n - 2) + 0.5 * d1(n - 3);
+  if (m == 1) return -0.25 * d1(0) - (5.0 / 6.0) * d1(1) + 1.5 * d1(2) - 0.5 * d1(3) + d1(4) * (1.0 / 12.0);
+  if (m == n - 2)
+    return 0.25 * d1(n - 1) + (5.0 / 6.0) * d1(n - 2) - 1.5 * d1(n - 3) + 0.5 * d1(n - 4) - d1(n - 5) * (1.0 / 12.0);
+  return 2.0 * (f(m + 1) - 2.0 * f(m) + f(m - 1)) - 0.5 * (d1(m + 1) - d1(m - 1));
+}
+// interface m + 1/2, m in [-1, n - 1]
+template <class F>
+GBR_HD double appc_face(const F& f, int m, int n) {
+  auto plus = [&](int c) { return f(c) + 0.5 * appc_d1(f, c, n) + appc_d2(f, c, n) * (1.0 / 12.0); };
+  auto minus = [&](int c) { return f(c) - 0.5 * appc_d1(f, c, n) + appc_d2(f, c, n) * (1.0 / 12.0); };
+  if (m == -1 || m == 0) return minus(m + 1);
+  if (m == n - 1 || m == n - 2) return plus(m);
+  return 0.5 * (plus(m) + minus(m + 1));
+}
+template <class F>
+GBR_HD double appc_D(const F& f, int m, int n) { return appc_face(f, m, n) - appc_face(f, m - 1, n); }
+
+// cell index of (i, j, k) along d and the extended index of cell 0 of that line
+GBR_HD int line_pos(int d, int i, int j, int k) { return d == 0 ? i : (d == 1 ? j : k); }
+GBR_HD long long line_base(const Layout& L, int d, int i, int j, int k) {
+  int c[3] = {i, j, k};
+  c[d] = 0;
+  return eidx(L, c[0], c[1], c[2]);
+}
+
+// ---------------------------------------------------------------------------
 // Geometry bodies (Sec. 3, Sec. 4, Sec. 6)
 // ---------------------------------------------------------------------------
 struct GeoArgs {
@@ -284,7 +336,36 @@ GBR_HD void body_centroid(const GeoArgs& G, int i, int j, int k) {
 GBR_HD void body_coord_derivative(const GeoArgs& G, int d, int i, int j, int k) {
   const Layout& L = G.L;
   const long long e = eidx(L, i, j, k);
-  for (int a = 0; a < L.nd; ++a) G.xd[(a * 3 + d) * L.ecount + e] = stencil_D(G.xc + a * L.ecount, e, L.es[d]);
+  for (int a = 0; a < L.nd; ++a) {
+    const double* x = G.xc + a * L.ecount;
+    double v;
+    if (L.closed[d]) {
+      const long long b = line_base(L, d, i, j, k), s = L.es[d];
+      v = appc_D([&](int m) { return x[b + m * s]; }, line_pos(d, i, j, k), L.n[d]);
+    } else {
+      v = stencil_D(x, e, L.es[d]);
+    }
+    G.xd[(a * 3 + d) * L.ecount + e] = v;
+  }
+}
+
+// D along d of the product a * b (Sec. 6 step 2), App. C on a closed axis
+GBR_HD double metric_D_prod(const Layout& L, const double* a, const double* b, int d, int i, int j, int k) {
+  if (L.closed[d]) {
+    const long long base = line_base(L, d, i, j, k), s = L.es[d];
+    return appc_D([&](int m) { return a[base + m * s] * b[base + m * s]; }, line_pos(d, i, j, k), L.n[d]);
+  }
+  return stencil_D_prod(a, b, eidx(L, i, j, k), L.es[d]);
+}
+
+// interface value at i+1/2 along d of the cell field f (Sec. 6 step 3), App. C on a closed axis
+GBR_HD double metric_I(const Layout& L, const double* f, int d, int i, int j, int k) {
+  if (L.closed[d]) {
+    const long long base = line_base(L, d, i, j, k), s = L.es[d];
+    int c[3] = {i, j, k};
+    return appc_face([&](int m) { return f[base + m * s]; }, c[d], L.n[d]);
+  }
+  return stencil_I(f, eidx(L, i, j, k), L.es[d]);
 }
 
 // Eq. (GCL_metrics) (3D) or its z = zeta reduction (2D), Eq. (Jac-matrix),
@@ -302,8 +383,8 @@ GBR_HD void body_metrics(const GeoArgs& G, int i, int j, int k) {
       for (int a = 0; a < 3; ++a) {
         const int b = (a + 1) % 3, c = (a + 2) % 3;
         // e.g. xi^_x = (y_eta z)_zeta - (y_zeta z)_eta
-        const double t1 = stencil_D_prod(G.xd + (b * 3 + f) * EC, G.xc + c * EC, e, L.es[g]);
-        const double t2 = stencil_D_prod(G.xd + (b * 3 + g) * EC, G.xc + c * EC, e, L.es[f]);
+        const double t1 = metric_D_prod(L, G.xd + (b * 3 + f) * EC, G.xc + c * EC, g, i, j, k);
+        const double t2 = metric_D_prod(L, G.xd + (b * 3 + g) * EC, G.xc + c * EC, f, i, j, k);
         m[ee][a] = t1 - t2;
       }
     }
@@ -344,11 +425,13 @@ GBR_HD void body_face_metrics(const GeoArgs& G, int d, int i, int j, int k) {
   const long long e = eidx(L, i, j, k), s = L.es[d];
   const long long f = fidx(L, d, i, j, k);
   const int nd = L.nd;
-  for (int a = 0; a < nd; ++a) G.fh[d][a * FC + f] = stencil_I(G.mh + (d * 3 + a) * EC, e, s);
+  (void)e;
+  (void)s;
+  for (int a = 0; a < nd; ++a) G.fh[d][a * FC + f] = metric_I(L, G.mh + (d * 3 + a) * EC, d, i, j, k);
   if (G.viscous)
     for (int ee = 0; ee < nd; ++ee)
-      for (int a = 0; a < nd; ++a) G.fu[d][(ee * nd + a) * FC + f] = stencil_I(G.mu + (ee * 3 + a) * EC, e, s);
-  if (G.moving) G.ft[d][f] = stencil_I(G.mt + d * EC, e, s);
+      for (int a = 0; a < nd; ++a) G.fu[d][(ee * nd + a) * FC + f] = metric_I(L, G.mu + (ee * 3 + a) * EC, d, i, j, k);
+  if (G.moving) G.ft[d][f] = metric_I(L, G.mt + d * EC, d, i, j, k);
 }
 
 // Eq. (Jacb2) with the same interface difference as the flux divergence; J for the update
@@ -512,38 +595,100 @@ GBR_HD void body_prim(const RhsArgsT<R>& A, int i, int j, int k) {
 }
 
 // Primitives on the whole padded box in one pass (interior and ghost layers): a ghost cell takes
-// the primitives of its source cell found axis by axis -- periodic wrap, zero-gradient clamp, or
-// the x-low inflow data -- which is exactly what the axis-by-axis ghost copies of body_halo
-// produce (corners included), with the same arithmetic per value.
+// the primitives of its source cell found axis by axis -- periodic wrap, zero-gradient clamp,
+// slip-wall mirror, or the x-low inflow data -- which is exactly what the axis-by-axis ghost
+// copies of body_halo produce (corners included), with the same arithmetic per value.  A slip
+// wall (reading A36) mirrors cell g - 1 into ghost layer g and reflects the velocity about the
+// unit normal of the wall interface; several walls reflect in axis order, each normal taken at
+// the cross-section the axis-by-axis filling sees (earlier axes' coordinates clamped to the
+// cells, later axes' at the source cell).
 template <int ND, class R>
 GBR_HD void body_prim_halo(const RhsArgsT<R>& A, const double* q, int i, int j, int k) {
   constexpr int NV = ND + 2;
   const Layout& L = A.L;
   int c[3] = {i, j, k};
+  const int own[3] = {i, j, k};
   bool inflow = false;
+  int wall[3] = {0, 0, 0};
   #pragma unroll
   for (int a = 0; a < ND; ++a) {
     const int n = L.n[a];
     if (c[a] < 0) {
       if (L.per[a]) {
         c[a] += n;
+      } else if (a == 0 && A.bc[0][0] == 2) {
+        inflow = true;
+        c[a] = 0;
+      } else if (A.bc[a][0] == 3) {
+        wall[a] = -1;
+        c[a] = -c[a] - 1;
       } else {
-        inflow = inflow || (a == 0 && A.bc[0][0] == 2);
         c[a] = 0;
       }
     } else if (c[a] >= n) {
-      c[a] = L.per[a] ? c[a] - n : n - 1;
+      if (L.per[a]) {
+        c[a] -= n;
+      } else if (A.bc[a][1] == 3) {
+        wall[a] = 1;
+        c[a] = 2 * n - 1 - c[a];
+      } else {
+        c[a] = n - 1;
+      }
     }
   }
   const long long p = pidx(L, i, j, k);
-  if (inflow) {
-    const long long PC = L.pcount, plane = (long long)L.n[1] * L.n[2];
-    const long long ib = (long long)c[2] * L.n[1] + c[1];
-    for (int f = 0; f < NV; ++f) A.prim[f * PC + p] = R(A.inflow[f * plane + ib]);
-    if (A.viscous) A.temp[p] = R(A.inflow[(NV - 1) * plane + ib] / A.inflow[ib]);
+  const long long PC = L.pcount;
+  if (!inflow && !(wall[0] | wall[1] | wall[2])) {
+    prim_store<ND>(A, q, cidx(L, c[0], c[1], c[2]), p);
     return;
   }
-  prim_store<ND>(A, q, cidx(L, c[0], c[1], c[2]), p);
+  // the source state in FP64
+  double rho, u[3] = {0.0, 0.0, 0.0}, pr;
+  if (inflow) {
+    const long long plane = (long long)L.n[1] * L.n[2];
+    const long long ib = (long long)c[2] * L.n[1] + c[1];
+    rho = A.inflow[ib];
+    for (int a = 0; a < ND; ++a) u[a] = A.inflow[(1 + a) * plane + ib];
+    pr = A.inflow[(NV - 1) * plane + ib];
+  } else {
+    const long long cs = cidx(L, c[0], c[1], c[2]), NC = L.ncells;
+    rho = q[cs];
+    const double ir = 1.0 / rho;
+    double ke = 0.0;
+    for (int a = 0; a < ND; ++a) {
+      const double m = q[(1 + a) * NC + cs];
+      u[a] = m * ir;
+      ke = gfma(m, u[a], ke);
+    }
+    pr = A.ph.gm1 * (q[(NV - 1) * NC + cs] - 0.5 * ke);
+  }
+  #pragma unroll
+  for (int a = 0; a < ND; ++a) {
+    if (!wall[a]) continue;
+    int fc[3];
+    for (int b = 0; b < 3; ++b) {
+      if (b < a) fc[b] = own[b] < 0 ? 0 : (own[b] >= L.n[b] ? L.n[b] - 1 : own[b]);
+      else fc[b] = c[b];
+    }
+    fc[a] = wall[a] < 0 ? -1 : L.n[a] - 1;  // the wall interface
+    const long long FC = L.fcount[a], f = fidx(L, a, fc[0], fc[1], fc[2]);
+    double nh[3] = {0.0, 0.0, 0.0}, nn = 0.0;
+    for (int b = 0; b < ND; ++b) {
+      nh[b] = A.fh[a][b * FC + f];
+      nn = gfma(nh[b], nh[b], nn);
+    }
+    const double inv = 1.0 / sqrt(nn);
+    double un = 0.0;
+    for (int b = 0; b < ND; ++b) {
+      nh[b] *= inv;
+      un = gfma(u[b], nh[b], un);
+    }
+    for (int b = 0; b < ND; ++b) u[b] = gfma(-2.0 * un, nh[b], u[b]);
+  }
+  A.prim[p] = R(rho);
+  for (int a = 0; a < ND; ++a) A.prim[(1 + a) * PC + p] = R(u[a]);
+  A.prim[(NV - 1) * PC + p] = R(pr);
+  if (A.viscous) A.temp[p] = R(pr / rho);
 }
 
 // ghost layers along axis d for the cross-section cell (i, j, k) (coordinate d ignored):

@@ -19,6 +19,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENONFINITE", "ETIMEOUT", "ES
 (GBR_FIELD_CELL_METRICS, GBR_FIELD_CELL_DET, GBR_FIELD_CELL_TIME, GBR_FIELD_FACE_HAT, GBR_FIELD_FACE_UNHAT,
  GBR_FIELD_FACE_TIME, GBR_FIELD_GCL, GBR_FIELD_FACE_FLUX) = range(8)
 GBR_PREC_FP64, GBR_PREC_MIXED = 0, 1
+GBR_BC_ZEROGRAD, GBR_BC_INFLOW, GBR_BC_WALL = 1, 2, 3
 GBR_GRAD_MEG6, GBR_GRAD_MIG4 = 0, 1
 
 
