@@ -113,15 +113,29 @@ __global__ void __launch_bounds__(kBlock) kb_grad12(const BatchJob<R>* jobs, con
   });
 }
 
-// FP32 instantiations: 768 threads per SM (memory-latency bound, as k_face)
+// As k_face: FP64 with the limiter's bound work compacted over the block (every thread takes
+// part in each work block's barriers), FP32 one interface per thread at 768 threads per SM.
 template <int ND, bool VISC, class R, int BS>
 __global__ void __launch_bounds__(BS, sizeof(R) == 4 ? 768 / BS : 1)
     kb_face(const BatchJob<R>* jobs, const WorkItem* items, int n, int total) {
-  for_work(items, n, total, [&](const WorkItem& it, int lb) {
-    const BatchJob<R>& J = jobs[it.job];
-    BATCH_CELL(J.faces[it.sub]);
-    body_face<ND, VISC, false>(J.A, it.sub, i, j, k);
-  });
+  if constexpr (sizeof(R) == 8) {
+    __shared__ BoundSlot<ND, R> slots[BS];
+    __shared__ int count;
+    for_work(items, n, total, [&](const WorkItem& it, int lb) {
+      const BatchJob<R>& J = jobs[it.job];
+      const long long t = (long long)lb * blockDim.x + threadIdx.x;
+      const bool valid = t < box_size(J.faces[it.sub]);
+      int i = 0, j = 0, k = 0;
+      if (valid) box_coord(J.faces[it.sub], t, i, j, k);
+      face_block<ND, VISC, false>(J.A, it.sub, valid, i, j, k, slots, &count);
+    });
+  } else {
+    for_work(items, n, total, [&](const WorkItem& it, int lb) {
+      const BatchJob<R>& J = jobs[it.job];
+      BATCH_CELL(J.faces[it.sub]);
+      body_face<ND, VISC, false>(J.A, it.sub, i, j, k);
+    });
+  }
 }
 
 template <int ND, class R>

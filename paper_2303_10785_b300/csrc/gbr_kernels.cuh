@@ -1040,13 +1040,28 @@ GBR_HD void hllc(const R* PL, const R* PR, const R* nh, R nn2, R inn, R nt, cons
   }
 }
 
-// One interface i+1/2 along d: Sec. 5.1 steps 2-6 and Sec. 5.2 steps 1-4.
-// The characteristic quantities are formed from projected differences of
-// neighbouring cells and the limited states are returned relative to the base
-// cell (P^L = P_i + R dW_L), which is the same arithmetic as projecting the
-// cell values themselves, in a different rounding order.
-template <int ND, bool VISC, bool MOV, class R>
-GBR_HD void body_face(const RhsArgsT<R>& A, int d, int i, int j, int k) {
+// One interface i+1/2 along d: Sec. 5.1 steps 2-6 and Sec. 5.2 steps 1-4, in three stages so
+// that the kernel can hand the limiter's bound work of a whole block to as few warps as possible:
+// face_unlimited (face state, projected differences, unlimited states, the App. E test),
+// face_bounds (the curvatures' projection and the bounds of the fields that failed the test),
+// face_flux (back-projection, HLLC, viscous flux, store).
+// The characteristic quantities are formed from projected differences of neighbouring cells
+// and the limited states are returned relative to the base cell (P^L = P_i + R dW_L), which is
+// the same arithmetic as projecting the cell values themselves, in a different rounding order.
+template <int ND, class R>
+struct FaceCtx {
+  static constexpr int NV = ND + 2;
+  long long p1, f;      // padded index of cell i, interface index
+  R nh[ND], nu[ND];
+  R nn2, inn, nt;
+  R ra, a2, ira, ia2;   // face state of the eigenvectors
+  R Wd[3][NV];          // projected differences of cells i-1 .. i+2
+  R dL[NV], dR[NV];     // W^L - W_i, W^R - W_{i+1}
+  unsigned limit;       // bit c: left field c fails the App. E test; bit NV + c: right
+};
+
+template <int ND, bool MOV, class R>
+GBR_HD void face_unlimited(const RhsArgsT<R>& A, int d, int i, int j, int k, FaceCtx<ND, R>& C) {
   constexpr int NV = ND + 2;
   const Layout& L = A.L;
   const PhysR<R>& ph = A.pr;
@@ -1056,19 +1071,19 @@ GBR_HD void body_face(const RhsArgsT<R>& A, int d, int i, int j, int k) {
   const long long FC = L.fcount[d];
   const long long f = fidx(L, d, i, j, k);
   const R* P = A.prim;
-
-  R nh[ND];
+  C.p1 = p1;
+  C.f = f;
   R nn2 = R(0);
   #pragma unroll
   for (int a = 0; a < ND; ++a) {
-    nh[a] = R(A.fh[d][a * FC + f]);
-    nn2 = gfma(nh[a], nh[a], nn2);
+    C.nh[a] = R(A.fh[d][a * FC + f]);
+    nn2 = gfma(C.nh[a], C.nh[a], nn2);
   }
-  const R nt = MOV ? R(A.ft[d][f]) : R(0);
-  const R inn = grsqrt(nn2);
-  R nu[ND];
+  C.nn2 = nn2;
+  C.nt = MOV ? R(A.ft[d][f]) : R(0);
+  C.inn = grsqrt(nn2);
   #pragma unroll
-  for (int a = 0; a < ND; ++a) nu[a] = nh[a] * inn;
+  for (int a = 0; a < ND; ++a) C.nu[a] = C.nh[a] * C.inn;
   // face state of the eigenvectors: mean of rho and p of cells i, i+1 (reading A6)
   const R rb = R(0.5) * (P[pp[1]] + P[pp[2]]);
   const R pb = R(0.5) * (P[(NV - 1) * PC + pp[1]] + P[(NV - 1) * PC + pp[2]]);
@@ -1076,64 +1091,84 @@ GBR_HD void body_face(const RhsArgsT<R>& A, int d, int i, int j, int k) {
   // a = gamma p t and 1/a = rho t -- one reciprocal square root, no division
   const R gp = ph.gamma * pb;
   const R t = grsqrt(gp * rb);
-  const R ira = t;
-  const R ra = gp * rb * t;
+  C.ira = t;
+  C.ra = gp * rb * t;
   const R a_ = gp * t;
-  const R a2 = a_ * a_;
+  C.a2 = a_ * a_;
   const R ia = rb * t;
-  const R ia2 = ia * ia;
-
+  C.ia2 = ia * ia;
   // projected differences dW = R^-1 (P_{m+1} - P_m) of the four cells i-1 .. i+2
-  R Wd[3][NV];
   #pragma unroll
   for (int m = 0; m < 3; ++m) {
     R x[NV];
     #pragma unroll
     for (int c = 0; c < NV; ++c) x[c] = P[c * PC + pp[m + 1]] - P[c * PC + pp[m]];
-    project<ND>(nu, ra, a2, x, Wd[m]);
+    project<ND>(C.nu, C.ra, C.a2, x, C.Wd[m]);
   }
   // Eq. (legendre_polys) unlimited states relative to the base cells, projected
   // after combining: W^L - W_i = R^-1 (f'_i / 2 + f''_i / 12),
   // W^R - W_{i+1} = R^-1 (-f'_{i+1} / 2 + f''_{i+1} / 12)
-  R dL[NV], dR[NV];
   {
     R x[NV];
     #pragma unroll
     for (int c = 0; c < NV; ++c)
       x[c] = gfma(R(0.5), A.g1[d][c * PC + pp[1]], A.g2[d][c * PC + pp[1]] * R(1.0 / 12.0));
-    project<ND>(nu, ra, a2, x, dL);
+    project<ND>(C.nu, C.ra, C.a2, x, C.dL);
     #pragma unroll
     for (int c = 0; c < NV; ++c)
       x[c] = gfma(R(-0.5), A.g1[d][c * PC + pp[2]], A.g2[d][c * PC + pp[2]] * R(1.0 / 12.0));
-    project<ND>(nu, ra, a2, x, dR);
+    project<ND>(C.nu, C.ra, C.a2, x, C.dR);
   }
-  // App. E: the curvatures are projected only where some characteristic field
-  // fails the test (in smooth flow whole warps skip this block)
+  // App. E test per field and side
   unsigned limit = 0;
   #pragma unroll
   for (int c = 0; c < NV; ++c) {
-    limit |= mp_keep(dL[c], Wd[0][c], Wd[1][c], ph) ? 0u : (1u << c);
-    limit |= mp_keep(dR[c], -Wd[2][c], -Wd[1][c], ph) ? 0u : (1u << (NV + c));
+    limit |= mp_keep(C.dL[c], C.Wd[0][c], C.Wd[1][c], ph) ? 0u : (1u << c);
+    limit |= mp_keep(C.dR[c], -C.Wd[2][c], -C.Wd[1][c], ph) ? 0u : (1u << (NV + c));
   }
-  if (limit) {
-    R W2[4][NV];
+  C.limit = limit;
+}
+
+// App. E bounds of the fields that failed the test: the curvatures d of cells i-1 .. i+2 are
+// projected with the face's eigenvectors (only here), then each failing state is limited
+template <int ND, class R>
+GBR_HD void face_bounds(const RhsArgsT<R>& A, int d, const R* nu, R ra, R a2, long long p1, unsigned limit,
+                        const R (*Wd)[ND + 2], R* dL, R* dR) {
+  constexpr int NV = ND + 2;
+  const Layout& L = A.L;
+  const long long PC = L.pcount, s = L.ps[d];
+  const long long pp[4] = {p1 - s, p1, p1 + s, p1 + 2 * s};
+  R W2[4][NV];
+  #pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    R x[NV];
     #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      R x[NV];
-      #pragma unroll
-      for (int c = 0; c < NV; ++c) x[c] = A.g2[d][c * PC + pp[m]];
-      project<ND>(nu, ra, a2, x, W2[m]);
-    }
-    #pragma unroll
-    for (int c = 0; c < NV; ++c) {
-      if (limit & (1u << c)) dL[c] = mp_bound(dL[c], Wd[0][c], Wd[1][c], W2[0][c], W2[1][c], W2[2][c], ph);
-      if (limit & (1u << (NV + c)))
-        dR[c] = mp_bound(dR[c], -Wd[2][c], -Wd[1][c], W2[3][c], W2[2][c], W2[1][c], ph);
-    }
+    for (int c = 0; c < NV; ++c) x[c] = A.g2[d][c * PC + pp[m]];
+    project<ND>(nu, ra, a2, x, W2[m]);
   }
+  #pragma unroll
+  for (int c = 0; c < NV; ++c) {
+    if (limit & (1u << c)) dL[c] = mp_bound(dL[c], Wd[0][c], Wd[1][c], W2[0][c], W2[1][c], W2[2][c], A.pr);
+    if (limit & (1u << (NV + c))) dR[c] = mp_bound(dR[c], -Wd[2][c], -Wd[1][c], W2[3][c], W2[2][c], W2[1][c], A.pr);
+  }
+}
+
+template <int ND, bool VISC, bool MOV, class R>
+GBR_HD void face_flux(const RhsArgsT<R>& A, int d, int i, int j, int k, const FaceCtx<ND, R>& C) {
+  constexpr int NV = ND + 2;
+  const Layout& L = A.L;
+  const PhysR<R>& ph = A.pr;
+  const long long PC = L.pcount, s = L.ps[d];
+  const long long p1 = C.p1;
+  const long long pp[4] = {p1 - s, p1, p1 + s, p1 + 2 * s};
+  const long long FC = L.fcount[d];
+  const long long f = C.f;
+  const R* P = A.prim;
+  const R* nh = C.nh;
+  const R nn2 = C.nn2, inn = C.inn, nt = C.nt;
   R PL[NV], PR[NV];
-  back_project<ND>(nu, ira, ia2, dL, PL);
-  back_project<ND>(nu, ira, ia2, dR, PR);
+  back_project<ND>(C.nu, C.ira, C.ia2, C.dL, PL);
+  back_project<ND>(C.nu, C.ira, C.ia2, C.dR, PR);
   #pragma unroll
   for (int c = 0; c < NV; ++c) {
     PL[c] += P[c * PC + pp[1]];
@@ -1221,6 +1256,15 @@ GBR_HD void body_face(const RhsArgsT<R>& A, int d, int i, int j, int k) {
   }
   #pragma unroll
   for (int c = 0; c < NV; ++c) A.flux[d][c * FC + f] = F[c];
+}
+
+// the whole interface in one thread (host emulation and the batch kernels)
+template <int ND, bool VISC, bool MOV, class R>
+GBR_HD void body_face(const RhsArgsT<R>& A, int d, int i, int j, int k) {
+  FaceCtx<ND, R> C;
+  face_unlimited<ND, MOV>(A, d, i, j, k, C);
+  if (C.limit) face_bounds<ND>(A, d, C.nu, C.ra, C.a2, C.p1, C.limit, C.Wd, C.dL, C.dR);
+  face_flux<ND, VISC, MOV>(A, d, i, j, k, C);
 }
 
 // Sec. 3 divergence, Sec. 4 time split, App. B stage combination (FP64; the
