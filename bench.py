@@ -60,9 +60,9 @@ HBM_PEAK_GBS, HBM_PEAK_KIND = measured_hbm_gbs()
 # minimum HBM traffic of a 3D FP64 cell-stage: state and cell geometry, stage average
 BYTES_PER_CELL_STAGE_3D = 186.7
 # DRAM bytes (read + write) per interface of the 3D viscous interface kernel, from one ncu
-# capture of a 96^3 launch (dram__bytes_read.sum + dram__bytes_write.sum = 322.3 MB for
+# capture of a 96^3 launch (dram__bytes_read.sum + dram__bytes_write.sum = 322.8 MB for
 # 893,952 interfaces); traffic grows in proportion to the interfaces of a launch.
-FACE_DRAM_BYTES_PER_INTERFACE = 322.3e6 / 893952
+FACE_DRAM_BYTES_PER_INTERFACE = 322.8e6 / 893952
 
 
 def load_flops():
