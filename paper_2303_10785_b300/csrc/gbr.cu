@@ -227,14 +227,14 @@ __global__ void k_update(UpdArgsT<R> U, Box b, int* err) {
   if (body_update<ND, MOV>(U, i, j, k)) atomicOr(err, 1);
 }
 
-template <int ND>
+template <int ND, class R = double>
 __global__ void k_dt(DtArgs D, Box b, unsigned long long* minbits) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double v = 1.0e300;
   if (t < box_size(b)) {
     int i, j, k;
     box_coord(b, t, i, j, k);
-    v = body_dt<ND>(D, i, j, k);
+    v = body_dt<ND, R>(D, i, j, k);
   }
   for (int off = 16; off > 0; off >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, off));
   __shared__ double wmin[kBlock / 32];
@@ -809,8 +809,15 @@ gbr_status run_dt(gbr_ctx* c, double cfl) {
   unsigned long long* bits = reinterpret_cast<unsigned long long*>(c->scal + S_DTMIN);
   k_dt_init<<<1, 1, 0, c->stream>>>(bits);
   CKL("k_dt_init");
-  if (L.nd == 3) k_dt<3><<<grid_of(bi, kBlock), kBlock, 0, c->stream>>>(D, bi, bits);
-  else k_dt<2><<<grid_of(bi, kBlock), kBlock, 0, c->stream>>>(D, bi, bits);
+  const unsigned g = grid_of(bi, kBlock);
+  cudaStream_t st = c->stream;
+  if (c->p.precision == GBR_PREC_MIXED) {
+    if (L.nd == 3) k_dt<3, float><<<g, kBlock, 0, st>>>(D, bi, bits);
+    else k_dt<2, float><<<g, kBlock, 0, st>>>(D, bi, bits);
+  } else {
+    if (L.nd == 3) k_dt<3, double><<<g, kBlock, 0, st>>>(D, bi, bits);
+    else k_dt<2, double><<<g, kBlock, 0, st>>>(D, bi, bits);
+  }
   CKL("k_dt");
   k_dt_final<<<1, 1, 0, c->stream>>>(c->scal, bits, cfl);
   CKL("k_dt_final");

@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kBlock) kb_dt(const BatchJob<R>* jobs, const W
     if (t < box_size(J.inner)) {
       int i, j, k;
       box_coord(J.inner, t, i, j, k);
-      v = body_dt<ND>(J.D, i, j, k);
+      v = body_dt<ND, R>(J.D, i, j, k);
     }
     for (int off = 16; off > 0; off >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, off));
     __syncthreads();  // wmin of the previous block of this CTA has been read

@@ -480,7 +480,7 @@ GBR_HD void body_motion(const Layout& L, const Motion& M, double st, double ct, 
 // ---------------------------------------------------------------------------
 template <class R>
 struct PhysR {
-  R gamma, igm1;
+  R gamma, gm1, igm1;
   R mu_ref, suth_s, it_ref;
   R alpha_d;                 // alpha^D
   R mp_alpha, mp_beta, mp_eps;
@@ -491,6 +491,7 @@ template <class R>
 inline PhysR<R> phys_r(const Phys& ph) {
   PhysR<R> r;
   r.gamma = R(ph.gamma);
+  r.gm1 = R(ph.gm1);
   r.igm1 = R(ph.igm1);
   r.mu_ref = R(ph.mu_ref);
   r.suth_s = R(ph.suth_s);
@@ -543,6 +544,7 @@ GBR_HD bool is_pos(float x) { return x > 0.0f; }
 GBR_HD bool is_neg(float x) { return x < 0.0f; }
 GBR_HD float gmin(float a, float b) { return a < b ? a : b; }
 GBR_HD float gmax(float a, float b) { return a > b ? a : b; }
+GBR_HD float gabs(float x) { return x < 0.0f ? -x : x; }
 GBR_HD float minmod(float a, float b) {  // App. E
   if (a > 0.0f && b > 0.0f) return a < b ? a : b;
   if (a < 0.0f && b < 0.0f) return a > b ? a : b;
@@ -567,25 +569,27 @@ GBR_HD R stencil_E6(const R* f, long long e, long long s) {
 }
 
 // Sec. 2: primitives P = [rho, u.., p] (and T = p/rho, R = 1) of state cell c stored at padded
-// index p, evaluated in FP64 from the FP64 state and stored in R
+// index p, evaluated in the path's type R from the FP64 state (the mixed path rounds the state
+// to FP32 first: the stored primitives are FP32 either way, and the FP64 divide is what would
+// bound this pass)
 template <int ND, class R>
 GBR_HD void prim_store(const RhsArgsT<R>& A, const double* q, long long c, long long p) {
   constexpr int NV = ND + 2;
   const Layout& L = A.L;
   const long long NC = L.ncells, PC = L.pcount;
-  const double rho = q[c];
-  const double ir = 1.0 / rho;
-  double ke = 0.0;
-  A.prim[p] = R(rho);
+  const R rho = R(q[c]);
+  const R ir = R(1) / rho;
+  R ke = R(0);
+  A.prim[p] = rho;
   for (int a = 0; a < ND; ++a) {
-    const double m = q[(1 + a) * NC + c];
-    const double u = m * ir;
-    A.prim[(1 + a) * PC + p] = R(u);
+    const R m = R(q[(1 + a) * NC + c]);
+    const R u = m * ir;
+    A.prim[(1 + a) * PC + p] = u;
     ke = gfma(m, u, ke);
   }
-  const double pr = A.ph.gm1 * (q[(NV - 1) * NC + c] - 0.5 * ke);
-  A.prim[(NV - 1) * PC + p] = R(pr);
-  if (A.viscous) A.temp[p] = R(pr * ir);
+  const R pr = A.pr.gm1 * (R(q[(NV - 1) * NC + c]) - R(0.5) * ke);
+  A.prim[(NV - 1) * PC + p] = pr;
+  if (A.viscous) A.temp[p] = pr * ir;
 }
 
 // primitives at interior cells
@@ -1330,47 +1334,49 @@ struct DtArgs {
   const double* jac;
 };
 
-template <int ND>
+template <int ND, class R = double>
 GBR_HD double body_dt(const DtArgs& D, int i, int j, int k) {
+  // evaluated in the path's type R (the mixed path's FP32 time step differs from the FP64 one by
+  // FP32 round-off, far below the CFL number's own slack)
   constexpr int NV = ND + 2;
   const Layout& L = D.L;
   const Phys& ph = D.ph;
   const long long c = cidx(L, i, j, k), NC = L.ncells, e = eidx(L, i, j, k), EC = L.ecount;
-  const double rho = D.q[c];
-  const double ir = 1.0 / rho;
-  double u[ND], ke = 0.0;
+  const R rho = R(D.q[c]);
+  const R ir = R(1) / rho;
+  R u[ND], ke = R(0);
   for (int a = 0; a < ND; ++a) {
-    u[a] = D.q[(1 + a) * NC + c] * ir;
-    ke = gfma(D.q[(1 + a) * NC + c], u[a], ke);
+    const R m = R(D.q[(1 + a) * NC + c]);
+    u[a] = m * ir;
+    ke = gfma(m, u[a], ke);
   }
-  const double pr = ph.gm1 * (D.q[(NV - 1) * NC + c] - 0.5 * ke);
-  const double cs = sqrt(ph.gamma * pr * ir);
-  const double J = D.jac[c];
-  double best = 1.0e300;
-  double nu_eff = 0.0;
+  const R pr = R(ph.gm1) * (R(D.q[(NV - 1) * NC + c]) - R(0.5) * ke);
+  const R cs = gsqrt(R(ph.gamma) * pr * ir);
+  const R J = R(D.jac[c]);
+  R nu_eff = R(0);
   if (ph.viscous) {
-    double mu = ph.mu_ref;
+    R mu = R(ph.mu_ref);
     if (ph.sutherland) {
-      const double th = pr * ir * ph.it_ref;
-      mu = ph.mu_ref * (th * sqrt(th)) * ((1.0 + ph.suth_s) / (th + ph.suth_s));
+      const R th = pr * ir * R(ph.it_ref);
+      mu = R(ph.mu_ref) * (th * gsqrt(th)) * ((R(1) + R(ph.suth_s)) / (th + R(ph.suth_s)));
     }
-    nu_eff = ph.dt_visc_fac * mu * ir;
+    nu_eff = R(ph.dt_visc_fac) * mu * ir;
   }
   // min over directions of 1/(|U| + c |grad xi|) and 1/(nu_eff |grad xi|^2) as one division by the
   // largest denominator: division is correctly rounded and monotone, so the result is the same value
-  double worst = 0.0;
+  R worst = R(0);
   for (int ee = 0; ee < ND; ++ee) {
-    double Uc = D.mt ? D.mt[ee * EC + e] * J : 0.0;
-    double g2 = 0.0;
+    R Uc = D.mt ? R(D.mt[ee * EC + e]) * J : R(0);
+    R g2 = R(0);
     for (int a = 0; a < ND; ++a) {
-      const double m = D.mh[(ee * 3 + a) * EC + e] * J;
+      const R m = R(D.mh[(ee * 3 + a) * EC + e]) * J;
       Uc = gfma(m, u[a], Uc);
       g2 = gfma(m, m, g2);
     }
-    worst = gmax(worst, gabs(Uc) + cs * sqrt(g2));
+    worst = gmax(worst, gabs(Uc) + cs * gsqrt(g2));
     if (ph.viscous) worst = gmax(worst, nu_eff * g2);
   }
-  return gmin(best, 1.0 / worst);
+  return gmin(1.0e300, double(R(1) / worst));
 }
 
 }  // namespace gbr
