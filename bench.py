@@ -80,7 +80,8 @@ def face_alg_bytes(wl):
     cells = er * (nv + nv + nv)                                   # primitives, P' and P'' along the sweep
     if visc:
         cells += er * (1 + 1 + (nd - 1) * (nd + 1))               # T, T', tangential [u, T]' of two directions
-    metrics = 8 * (nd + (nd * nd if visc else 0) + (1 if wl.case.get("moving", 0) else 0))
+    # interface metrics: FP64, or the FP32 copies the mixed path reads
+    metrics = er * (nd + (nd * nd if visc else 0) + (1 if wl.case.get("moving", 0) else 0))
     return cells + metrics + er * nv
 
 

@@ -255,6 +255,10 @@ __global__ void k_dt_final(double* scal, const unsigned long long* minbits, doub
 }
 
 __global__ void k_set_scalar(double* scal, int idx, double v) { scal[idx] = v; }
+__global__ void k_to_f32(const double* src, float* dst, long long n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) dst[t] = (float)src[t];
+}
 __global__ void k_advance_time(double* scal) { scal[S_T] += scal[S_DT]; }
 
 // ---------------------------------------------------------------------------
@@ -276,7 +280,8 @@ struct Plan {
 
 enum Slot {
   SL_Q0, SL_Q1, SL_Q2, SL_PRIM, SL_TEMP, SL_G1, SL_G2, SL_FLUX, SL_NODES, SL_NVEL, SL_XC, SL_VC, SL_XD, SL_MH,
-  SL_DET, SL_MU, SL_MT, SL_FH, SL_FU, SL_FT, SL_GCL, SL_JAC, SL_SIGMA, SL_INFLOW, SL_SCAL, SL_ERR, SL_IG4, SL_COUNT
+  SL_DET, SL_MU, SL_MT, SL_FH, SL_FU, SL_FT, SL_GCL, SL_JAC, SL_SIGMA, SL_INFLOW, SL_SCAL, SL_ERR, SL_IG4, SL_FH32, SL_FU32,
+  SL_FT32, SL_COUNT
 };
 
 struct Sizes {
@@ -378,6 +383,11 @@ Plan plan_of(const gbr_params* p, const Layout& L) {
   if (p->gradient_scheme == GBR_GRAD_MIG4)
     for (int d = 0; d < nd; ++d) ig4 += ig4_table_len(L.n[d], L.per[d] != 0);
   P.add(D * ig4);
+  // mixed path: FP32 copies of the interface metrics the interface kernel reads
+  const bool f32 = p->precision == GBR_PREC_MIXED;
+  P.add(f32 ? sizeof(float) * nd * fsum : 0);                   // SL_FH32
+  P.add(f32 && visc ? sizeof(float) * nd * nd * fsum : 0);      // SL_FU32
+  P.add(f32 && mov ? sizeof(float) * fsum : 0);                 // SL_FT32
   P.total = (P.total + 255) & ~(size_t)255;
   return P;
 }
@@ -421,6 +431,7 @@ struct gbr_ctx {
   double* q[3];
   void *prim, *temp, *g1[3], *g2[3], *flux[3];  // element type double (FP64) or float (mixed)
   double *nodes, *nvel, *xc, *vc, *xd, *mh, *det, *mu, *mt, *fh[3], *fu[3], *ft[3], *gcl, *jac;
+  float *fh32[3], *fu32[3], *ft32[3];  // mixed path: FP32 copies of the interface metrics
   double *sigma, *inflow, *scal;
   double* ig4[3];  // MIG4 line-solve factors per direction (or null)
   int* err;
@@ -664,6 +675,18 @@ gbr_status run_geometry(gbr_ctx* c) {
   CKL("k_face_metrics");
   k_gcl<<<grid_of(B.inner, kBlock), kBlock, 0, st>>>(G, B.inner);
   CKL("k_gcl");
+  if (c->p.precision == GBR_PREC_MIXED) {
+    // FP32 copies of the interface metrics (whole slots: all directions at once)
+    const Plan& P = c->plan;
+    const int slots[3][2] = {{SL_FH, SL_FH32}, {SL_FU, SL_FU32}, {SL_FT, SL_FT32}};
+    for (auto& sl : slots) {
+      const long long n = (long long)(P.len[sl[1]] / sizeof(float));
+      if (n == 0) continue;
+      k_to_f32<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, st>>>(
+          (const double*)(c->ws + P.off[sl[0]]), (float*)(c->ws + P.off[sl[1]]), n);
+      CKL("k_to_f32");
+    }
+  }
   return GBR_OK;
 }
 
@@ -686,9 +709,15 @@ RhsArgsT<R> rhs_args_r(gbr_ctx* c, const double* q) {
   for (int d = 0; d < 3; ++d) {
     A.g1[d] = static_cast<R*>(c->g1[d]);
     A.g2[d] = static_cast<R*>(c->g2[d]);
-    A.fh[d] = c->fh[d];
-    A.fu[d] = c->fu[d];
-    A.ft[d] = c->ft[d];
+    if constexpr (sizeof(R) == 4) {
+      A.fh[d] = c->fh32[d];
+      A.fu[d] = c->fu32[d];
+      A.ft[d] = c->ft32[d];
+    } else {
+      A.fh[d] = c->fh[d];
+      A.fu[d] = c->fu[d];
+      A.ft[d] = c->ft[d];
+    }
     A.flux[d] = static_cast<R*>(c->flux[d]);
   }
   A.inflow = c->inflow;
@@ -844,6 +873,12 @@ void carve(gbr_ctx* c) {
     c->fh[d] = (d < nd) ? ptr(SL_FH) + (size_t)nd * foff : nullptr;
     c->fu[d] = (d < nd && c->visc) ? ptr(SL_FU) + (size_t)nd * nd * foff : nullptr;
     c->ft[d] = (d < nd && c->mov) ? ptr(SL_FT) + foff : nullptr;
+    auto fptr = [&](int slot, size_t elems) -> float* {
+      return P.len[slot] ? (float*)(c->ws + P.off[slot]) + elems : nullptr;
+    };
+    c->fh32[d] = (d < nd) ? fptr(SL_FH32, (size_t)nd * foff) : nullptr;
+    c->fu32[d] = (d < nd && c->visc) ? fptr(SL_FU32, (size_t)nd * nd * foff) : nullptr;
+    c->ft32[d] = (d < nd && c->mov) ? fptr(SL_FT32, foff) : nullptr;
     if (d < nd) foff += (size_t)L.fcount[d];
   }
   c->nodes = ptr(SL_NODES);

@@ -515,9 +515,9 @@ struct RhsArgsT {
   R* temp;              // [pcount] T = p/rho (viscous)
   R* g1[3];             // [nv (+1 T)][pcount] first derivatives along d
   R* g2[3];             // [nv][pcount] second derivatives along d
-  const double* fh[3];  // [nd][fcount] hat metrics n^ at interfaces
-  const double* fu[3];  // [nd][nd][fcount] unhatted metrics d xi_e / d x_a at interfaces
-  const double* ft[3];  // [fcount] hat xi_t at interfaces (moving)
+  const R* fh[3];       // [nd][fcount] hat metrics n^ at interfaces (FP32 copies on the mixed path)
+  const R* fu[3];       // [nd][nd][fcount] unhatted metrics d xi_e / d x_a at interfaces
+  const R* ft[3];       // [fcount] hat xi_t at interfaces (moving)
   R* flux[3];           // [nv][fcount] F^ - F^v at interfaces
   const double* inflow; // [nv][nk][nj]
   int bc[3][2];
@@ -1210,7 +1210,7 @@ GBR_HD void face_flux(const RhsArgsT<R>& A, int d, int i, int j, int k, const Fa
     //   (grad u n^)_a = sum_e m_e du_a/dxi_e,  (grad u^T n^)_a = sum_e xi_e,x_a s_e,
     //   div u = sum_a sum_e xi_e,x_a du_a/dxi_e,  grad T . n^ = sum_e m_e dT/dxi_e,
     //   beta . n^ = kappa grad T . n^ + u . (tau n^)   (tau symmetric)
-    const double* fu = A.fu[d];
+    const R* fu = A.fu[d];
     R xe[ND][ND];  // xe[e][a] = d xi_e / d x_a at the interface
     #pragma unroll
     for (int e = 0; e < ND; ++e)
