@@ -210,6 +210,46 @@ def dist_env():
     return world, rank, local
 
 
+def dist_max(value, device=None):
+    """Max of a float over the ranks of the default process group (the value itself alone).
+    The jobs of the ranks are independent (replicas or shards of the serving stream): this
+    timing reduction is the only collective."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard(items, rank, world):
+    """The items of one rank: every world-th item from position rank (a partition of the list)."""
+    return list(items[rank::world])
+
+
+def merge_serving(records):
+    """Whole-job serving statistics from per-rank records {"lat": [s...], "work": W, "makespan": s}:
+    time-to-N-steps percentiles over every rank's jobs, throughput = all work / slowest makespan."""
+    lat = np.concatenate([np.asarray(r["lat"], dtype=np.float64) for r in records])
+    work = float(sum(r["work"] for r in records))
+    span = max(r["makespan"] for r in records)
+    return {"jobs": int(lat.size), "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "makespan_s": span, "cell_rk_stage_updates_per_s": work / max(span, 1e-9)}
+
+
+def gather_objects(obj):
+    """Every rank's object, in rank order (the object itself alone)."""
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [obj]
+    out = [None] * dist.get_world_size()
+    dist.all_gather_object(out, obj)
+    return out
+
+
 def _oracle_stage(orc, q):
     """One SSP-RK3 stage of the oracle: a right-hand side and the first stage combination."""
     return q + 1e-3 * orc.rhs(q)
@@ -317,12 +357,7 @@ def run_gpu(args, wl):
     ms = ev0.elapsed_time(ev1)
     face_ms, face_launches, launches = solver.profile(False)
     solver.sync()
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = dist_max(ms, dev)
     value = world * 3 * cells * args.steps / (ms / 1e3)
 
     # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
@@ -347,13 +382,7 @@ def run_gpu(args, wl):
             step += 1
             solver._check(L.gbr_get_state(solver.h, ctypes.c_void_p(h_out.data_ptr()), 0))
         solver.sync()
-        e2e_s = time.perf_counter() - t0
-        if world > 1:
-            import torch.distributed as dist
-
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = dist_max(time.perf_counter() - t0, dev)
         nbytes = int(wl.q.size * 8)
         e2e = {"value": world * 3 * cells * e2e_steps / e2e_s, "unit": METRIC, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": e2e_steps}
@@ -427,7 +456,12 @@ def run_serving(args):
 
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
-    specs = I.serving_stream(args.jobs, seed=args.seed, rate=1.0)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    # each rank serves its own stream of --jobs jobs (independent jobs: weak scaling)
+    specs = I.serving_stream(args.jobs, seed=args.seed + rank, rate=1.0)
 
     def jobs_at(rate, precision=None):
         out = []
@@ -479,11 +513,26 @@ def run_serving(args):
     launches_allmix = srv.batch.info()["launches"]
     srv.close()
     errors = [j.error for j in mix + base + allmix if j.error]
+
+    def record(jobs, st):
+        return {"lat": [j.finished - j.arrival for j in jobs if j.finished is not None],
+                "work": float(sum(j.work for j in jobs if j.finished is not None)), "makespan": st["makespan_s"]}
+
+    recs = gather_objects({"mix": record(mix, st_mix), "base": record(base, st_base),
+                           "allmix": record(allmix, st_allmix), "errors": errors,
+                           "launches": info["launches"] + launches_allmix})
+    if world > 1:
+        st_mix = merge_serving([r["mix"] for r in recs])
+        st_base = merge_serving([r["base"] for r in recs])
+        st_allmix = merge_serving([r["allmix"] for r in recs])
+        errors = [e for r in recs for e in r["errors"]]
+    if rank != 0:
+        return
     line = {
-        "metric": METRIC, "value": st_mix["cell_rk_stage_updates_per_s"], "unit": METRIC, "n_gpus": 1,
+        "metric": METRIC, "value": st_mix["cell_rk_stage_updates_per_s"], "unit": METRIC, "n_gpus": world,
         "steps": None, "warmup": None, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64 and f32+f64 per job", "data": "synthetic",
-        "config": {"workload": f"serving_stream_{args.jobs}_jobs", "seed": args.seed, "offered_load": args.load,
+        "config": {"workload": f"serving_stream_{args.jobs}_jobs_per_gpu", "seed": args.seed, "offered_load": args.load,
                    "pool_gb": args.pool_gb, "slots": args.slots, "chunk_steps": args.chunk,
                    "l2": "working sets of the large jobs >> 126 MB L2, no flush"},
         "serving": {"batched_mixed": st_mix, "batched_all_mixed": st_allmix, "per_job_fp64": st_base,
@@ -494,7 +543,7 @@ def run_serving(args):
                     "throughput_ratio": st_mix["cell_rk_stage_updates_per_s"]
                     / st_base["cell_rk_stage_updates_per_s"], "peak": peak, "tuning": tuning,
                     "errors": errors},
-        "gpu_launches": info["launches"] + launches_allmix, "clocks": clocks.summary(),
+        "gpu_launches": sum(r["launches"] for r in recs), "clocks": clocks.summary(),
     }
     print(json.dumps(line), flush=True)
 
@@ -526,8 +575,11 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     if args.workload == "serving":
-        if dist_env()[1] == 0 and args.impl != "reference":
+        if args.impl != "reference":
             run_serving(args)
+        elif dist_env()[1] == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the serving stream has no CPU reference arm: "
+                              "the oracle evaluates one grid at a time"}), flush=True)
         return
     wl = Workload(args.workload, args.edge, args.precision, args.scheme)
     if args.impl == "reference":
