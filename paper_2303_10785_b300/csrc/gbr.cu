@@ -437,6 +437,7 @@ struct gbr_ctx {
   int* err;
   bool visc, mov, have_sponge, have_motion, metrics_ready;
   double qamb[5];
+  double pref = 0.0;  // mixed path: pressure offset of the FP32 primitives (a pressure of the initial state)
   Motion motion;
   double last_fixed_dt;
   std::string last_error;
@@ -724,6 +725,7 @@ RhsArgsT<R> rhs_args_r(gbr_ctx* c, const double* q) {
   for (int d = 0; d < 3; ++d)
     for (int s = 0; s < 2; ++s) A.bc[d][s] = c->p.bc[d][s];
   A.viscous = c->visc;
+  A.pref = (sizeof(R) == 4) ? c->pref : 0.0;
   return A;
 }
 RhsArgs rhs_args(gbr_ctx* c, const double* q) { return rhs_args_r<double>(c, q); }
@@ -1043,6 +1045,21 @@ gbr_status gbr_set_state(gbr_ctx* c, const double* q, int on_device) {
   CK(cudaMemcpyAsync(c->q[0], q, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream),
      "set state");
   if (!on_device) CK(cudaStreamSynchronize(c->stream), "set state sync");
+  if (c->p.precision == GBR_PREC_MIXED) {
+    // the FP32 primitives store p - pref with pref the pressure of the first cell (any constant is
+    // exact; one of the flow's own pressures keeps the stored differences' digits)
+    const int nv = c->L.nv;
+    double q0[5];
+    for (int v = 0; v < nv; ++v)
+      CK(cudaMemcpyAsync(q0 + v, c->q[0] + (size_t)v * c->L.ncells, sizeof(double), cudaMemcpyDeviceToHost,
+                         c->stream),
+         "read first cell");
+    CK(cudaStreamSynchronize(c->stream), "read first cell sync");
+    double ke = 0.0;
+    for (int a = 0; a < c->L.nd; ++a) ke += q0[1 + a] * q0[1 + a] / q0[0];
+    const double p0 = (c->p.gamma - 1.0) * (q0[nv - 1] - 0.5 * ke);
+    c->pref = std::isfinite(p0) ? p0 : 0.0;
+  }
   return GBR_OK;
 }
 

@@ -511,7 +511,8 @@ struct RhsArgsT {
   Phys ph;
   PhysR<R> pr;
   const double* q;      // [nv][ncells] conserved state of the stage
-  R* prim;              // [nv][pcount] primitives with halo
+  R* prim;              // [nv][pcount] primitives with halo; the pressure slot holds p - pref
+  double pref;          // pressure offset of the stored primitives (mixed path; 0 on the FP64 path)
   R* temp;              // [pcount] T = p/rho (viscous)
   R* g1[3];             // [nv (+1 T)][pcount] first derivatives along d
   R* g2[3];             // [nv][pcount] second derivatives along d
@@ -572,6 +573,9 @@ GBR_HD R stencil_E6(const R* f, long long e, long long s) {
 // index p, evaluated in the path's type R from the FP64 state (the mixed path rounds the state
 // to FP32 first: the stored primitives are FP32 either way, and the FP64 divide is what would
 // bound this pass)
+// The pressure is stored as p - pref: on the mixed path pref is a pressure of the flow (set with
+// the state), so that FP32 keeps the digits of the pressure differences; the energy offset
+// pref/(gamma-1) is taken off in FP64 before the rounding.  pref = 0 on the FP64 path.
 template <int ND, class R>
 GBR_HD void prim_store(const RhsArgsT<R>& A, const double* q, long long c, long long p) {
   constexpr int NV = ND + 2;
@@ -587,9 +591,10 @@ GBR_HD void prim_store(const RhsArgsT<R>& A, const double* q, long long c, long 
     A.prim[(1 + a) * PC + p] = u;
     ke = gfma(m, u, ke);
   }
-  const R pr = A.pr.gm1 * (R(q[(NV - 1) * NC + c]) - R(0.5) * ke);
-  A.prim[(NV - 1) * PC + p] = pr;
-  if (A.viscous) A.temp[p] = pr * ir;
+  const R Erel = R(q[(NV - 1) * NC + c] - A.pref * A.ph.igm1);
+  const R prel = A.pr.gm1 * (Erel - R(0.5) * ke);  // p - pref
+  A.prim[(NV - 1) * PC + p] = prel;
+  if (A.viscous) A.temp[p] = (prel + R(A.pref)) * ir;
 }
 
 // primitives at interior cells
@@ -691,7 +696,7 @@ GBR_HD void body_prim_halo(const RhsArgsT<R>& A, const double* q, int i, int j, 
   }
   A.prim[p] = R(rho);
   for (int a = 0; a < ND; ++a) A.prim[(1 + a) * PC + p] = R(u[a]);
-  A.prim[(NV - 1) * PC + p] = R(pr);
+  A.prim[(NV - 1) * PC + p] = R(pr - A.pref);
   if (A.viscous) A.temp[p] = R(pr / rho);
 }
 
@@ -989,14 +994,18 @@ GBR_HD float mp_bound(float f, float dm, float dp, float du, float db, float dd,
 }
 
 // Sec. 5.1.1 HLLC with grid motion; P = [rho, u.., p]
+// The states carry p - pref (pref = 0 on the FP64 path): the absolute pressure enters the sound
+// speeds, the energy and the energy flux; the pressure difference of S* and the momentum flux's
+// pressure term use p - pref (the dropped pref n^ has zero divergence by the metric identities).
 template <int ND, class R>
-GBR_HD void hllc(const R* PL, const R* PR, const R* nh, R nn2, R inn, R nt, const PhysR<R>& ph, R* F) {
+GBR_HD void hllc(const R* PL, const R* PR, const R* nh, R nn2, R inn, R nt, const PhysR<R>& ph, R pref, R* F) {
   constexpr int NV = ND + 2;
   const R nn = nn2 * inn;
   const R inn2 = inn * inn;
   // left and right states (kept in scalars: no runtime-indexed arrays)
   const R rl = PL[0], rr = PR[0];
-  const R pl = PL[NV - 1], pr = PR[NV - 1];
+  const R dpl = PL[NV - 1], dpr = PR[NV - 1];
+  const R pl = dpl + pref, pr = dpr + pref;
   // t = 1/sqrt(gamma p rho) = 1/(rho c): c = gamma p t and 1/rho = gamma p t^2, no division
   const R gpl = ph.gamma * pl, gpr = ph.gamma * pr;
   const R tl = grsqrt(gpl * rl), tr = grsqrt(gpr * rr);
@@ -1013,34 +1022,38 @@ GBR_HD void hllc(const R* PL, const R* PR, const R* nh, R nn2, R inn, R nt, cons
   const R SL = gmin(gfma(-cl, nn, Ul), gfma(-cr, nn, Ur));
   const R SR = gmax(gfma(cl, nn, Ul), gfma(cr, nn, Ur));
   const R aL = rl * (SL - Ul), aR = rr * (SR - Ur);
-  const R Ss = (aR * Ur - aL * Ul + (pl - pr) * nn2) / (aR - aL);
+  const R Ss = (aR * Ur - aL * Ul + (dpl - dpr) * nn2) / (aR - aL);
   // branches of Sec. 5.1.1: S^L >= 0 -> F^L; S^L < 0 <= S* -> F*L; S* < 0 < S^R -> F*R; else F^R
   const bool left = !is_neg(SL) || !is_neg(Ss);
   const bool star = is_neg(SL) && (left || is_pos(SR));
-  const R rs = left ? rl : rr, ps = left ? pl : pr;
+  const R rs = left ? rl : rr, ps = left ? pl : pr, dps = left ? dpl : dpr;
   const R Us = left ? Ul : Ur, Es = left ? El : Er, S = left ? SL : SR;
   R us[ND];
   #pragma unroll
   for (int a = 0; a < ND; ++a) us[a] = left ? PL[1 + a] : PR[1 + a];
   F[0] = rs * Us;
   #pragma unroll
-  for (int a = 0; a < ND; ++a) F[1 + a] = gfma(rs * us[a], Us, nh[a] * ps);
+  for (int a = 0; a < ND; ++a) F[1 + a] = gfma(rs * us[a], Us, nh[a] * dps);
   F[NV - 1] = gfma(Es + ps, Us, -nt * ps);
   if (star) {
     // Q*K = rho (S - U)/(S - S*) [1, u + n^ (S* - U)/|n^|^2, E/rho + (S* - U)((S* - xi_t)/|n^|^2 + p/(rho (S - U)))]
+    // The correction S (Q*K - QK) is formed with the factor (S* - U) taken out,
+    //   Q*K - QK = (S* - U)/(S - S*) [rho, rho u, E] + rho (S - U)/(S - S*) (S* - U) [0, n^/|n^|^2, (S* - xi_t)/|n^|^2 + p/(rho (S - U))],
+    // instead of as a difference of two O(rho) states multiplied by S ~ c: at low Mach numbers the
+    // difference would lose a factor c/|U| of the working precision.
     const R rA = rs * (S - Us);
     const R B = S - Ss;
     const R inv = R(1) / (rA * B);
-    const R fac = rA * rA * inv;      // rho (S - U) / (S - S*)
+    const R g = rA * inv;             // 1 / (S - S*)
+    const R fac = rA * g;             // rho (S - U) / (S - S*)
     const R p_rA = ps * B * inv;      // p / (rho (S - U))
     const R dS = Ss - Us;
-    const R w = dS * inn2;
-    F[0] += S * (fac - rs);
+    const R dg = dS * g;              // (S* - U) / (S - S*)
+    const R fw = fac * dS * inn2;
+    F[0] = gfma(S * rs, dg, F[0]);
     #pragma unroll
-    for (int a = 0; a < ND; ++a) F[1 + a] += S * (fac * gfma(nh[a], w, us[a]) - rs * us[a]);
-    const R ts = left ? tl : tr, gps = left ? gpl : gpr;
-    const R eb = gfma(Es * gps, ts * ts, dS * gfma(Ss - nt, inn2, p_rA));  // E/rho + ...
-    F[NV - 1] += S * gfma(fac, eb, -Es);
+    for (int a = 0; a < ND; ++a) F[1 + a] = gfma(S, gfma(rs * us[a], dg, fw * nh[a]), F[1 + a]);
+    F[NV - 1] = gfma(S * dS, gfma(fac, gfma(Ss - nt, inn2, p_rA), Es * g), F[NV - 1]);
   }
 }
 
@@ -1090,7 +1103,7 @@ GBR_HD void face_unlimited(const RhsArgsT<R>& A, int d, int i, int j, int k, Fac
   for (int a = 0; a < ND; ++a) C.nu[a] = C.nh[a] * C.inn;
   // face state of the eigenvectors: mean of rho and p of cells i, i+1 (reading A6)
   const R rb = R(0.5) * (P[pp[1]] + P[pp[2]]);
-  const R pb = R(0.5) * (P[(NV - 1) * PC + pp[1]] + P[(NV - 1) * PC + pp[2]]);
+  const R pb = gfma(R(0.5), P[(NV - 1) * PC + pp[1]] + P[(NV - 1) * PC + pp[2]], R(A.pref));
   // a = sqrt(gamma p / rho): with t = 1/sqrt(gamma p rho), rho a = gamma p rho t, 1/(rho a) = t,
   // a = gamma p t and 1/a = rho t -- one reciprocal square root, no division
   const R gp = ph.gamma * pb;
@@ -1179,7 +1192,7 @@ GBR_HD void face_flux(const RhsArgsT<R>& A, int d, int i, int j, int k, const Fa
     PR[c] += P[c * PC + pp[2]];
   }
   R F[NV];
-  hllc<ND>(PL, PR, nh, nn2, inn, nt, ph, F);
+  hllc<ND>(PL, PR, nh, nn2, inn, nt, ph, R(A.pref), F);
 
   if (VISC) {
     // Sec. 5.2 alpha-damping on [u.., T].  gc2[v][e] = 2 d(phi_v)/d(xi_e) at the interface:

@@ -4,10 +4,13 @@ The mixed path computes primitives, gradients, the characteristic reconstruction
 the limiter and the HLLC and viscous fluxes in FP32 and keeps the state, the
 metrics, 1/J, the GCL term, the flux divergence and the RK accumulation in FP64.
 Its results therefore differ from the FP64 oracle by FP32 round-off, not by the
-scheme.  Tolerances:
-* right-hand sides: 2e-5 of the cancellation scale (reading A27) -- about 300
-  FP32 ulps; the largest observed is ~4e-6, on the M = 0.1 Taylor-Green vortex
-  where p0 = 71 in FP32 carries O(1e-3) cell-to-cell pressure differences;
+scheme.  Two choices keep that round-off independent of the Mach number M: the FP32 primitives
+hold p - p_ref (p_ref a pressure of the initial state, so that FP32 does not spend its
+digits on the O(1/M^2) mean pressure), and the HLLC star correction S (Q*K - QK) is
+formed with (S* - U) factored out (no difference of two O(rho) states multiplied by S ~ c).
+Without them the error grows like 1/M.  Tolerances:
+* right-hand sides: 2e-6 of the cancellation scale (reading A27) -- about 30 FP32 ulps;
+  the largest observed is ~2e-7, the same from M = 0.02 to M = 0.5;
 * states after many steps: L-infinity 1e-5 relative to max |Q| per component;
 * freestream: right-hand side 1e-6 of the cancellation scale, velocity 1e-6 of
   the freestream speed after steps on a deforming mesh.
@@ -23,7 +26,7 @@ from test_gpu_parity import CASES, GAMMA, case_jet, rel_state
 
 pytestmark = pytest.mark.gpu
 
-RHS_TOL = 2e-5
+RHS_TOL = 2e-6
 STATE_TOL = 1e-5
 FREESTREAM_TOL = 1e-6
 
@@ -61,6 +64,25 @@ def test_mixed_rhs_matches_fp64_oracle(name):
     assert err < RHS_TOL, err
     # and it is not the FP64 path: FP32 round-off is visible
     assert err > 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("mach", [0.02, 0.1, 0.3])
+def test_mixed_rhs_error_does_not_grow_at_low_mach(mach):
+    # viscous Taylor-Green vortex on a randomly perturbed mesh: the FP32 error relative to the
+    # cancellation scale stays at a few ulps as M falls (it grew like 1/M with absolute FP32
+    # pressures or a star correction formed as a difference of states)
+    n = (20, 18, 16)
+    case = I.case_params(3, n, reynolds=1600.0)
+    nodes = I.nodes_random(n, (2 * np.pi,) * 3, frac=0.15)
+    xc = I.centroids(nodes, n, (1, 1, 1))
+    q = I.prim_to_cons(I.tgv_prim(*xc, mach=mach), GAMMA)
+    orc, s = pair(case, nodes, None)
+    s.set_state(q)
+    Lg = s.rhs().cpu().numpy()
+    scale = cancellation_scale(orc, q)
+    err = (np.abs(Lg - orc.rhs(q)).reshape(5, -1).max(axis=1) / scale).max()
+    assert err < RHS_TOL, err
     s.close()
 
 
