@@ -59,7 +59,10 @@ enum { GBR_BC_ZEROGRAD = 1, GBR_BC_INFLOW = 2, GBR_BC_WALL = 3 };
  *                 HLLC and viscous fluxes computed and stored in FP32; the conserved
  *                 state, the metrics and 1/J, the GCL term, the flux divergence and
  *                 the RK accumulation in FP64.  Not in the paper (which compares FP32
- *                 and FP64 runs only as a whole). */
+ *                 and FP64 runs only as a whole).  The FP32 primitives hold p - p_ref,
+ *                 p_ref the pressure of cell 0 of the state last given to gbr_set_state
+ *                 (any constant gives the same scheme; one near the mean pressure keeps
+ *                 the round-off independent of the Mach number). */
 enum { GBR_PREC_FP64 = 0, GBR_PREC_MIXED = 1 };
 
 /* Gradients of the primitives (gbr_params.gradient_scheme), Sec. 5.1 step 1:
@@ -140,7 +143,9 @@ gbr_status gbr_move_mesh(gbr_ctx* c, const double* nodes, const double* node_vel
  * Sets the solution time to t0 and computes the metrics at t0. */
 gbr_status gbr_set_motion(gbr_ctx* c, const gbr_motion* m, double t0);
 
-/* Conserved state in/out; on_device = 1: q is a device pointer. */
+/* Conserved state in/out; on_device = 1: q is a device pointer.  On a
+ * GBR_PREC_MIXED context gbr_set_state also sets the pressure offset p_ref of
+ * the FP32 primitives from cell 0 (0 if that pressure is not finite). */
 gbr_status gbr_set_state(gbr_ctx* c, const double* q, int on_device);
 gbr_status gbr_get_state(gbr_ctx* c, double* q, int on_device);
 
