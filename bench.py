@@ -60,9 +60,11 @@ HBM_PEAK_GBS, HBM_PEAK_KIND = measured_hbm_gbs()
 # minimum HBM traffic of a 3D FP64 cell-stage: state and cell geometry, stage average
 BYTES_PER_CELL_STAGE_3D = 186.7
 # DRAM bytes (read + write) per interface of the 3D viscous interface kernel, from one ncu
-# capture of a 96^3 launch (dram__bytes_read.sum + dram__bytes_write.sum = 322.8 MB for
-# 893,952 interfaces); traffic grows in proportion to the interfaces of a launch.
-FACE_DRAM_BYTES_PER_INTERFACE = 322.8e6 / 893952
+# capture of a launch (dram__bytes_read.sum + dram__bytes_write.sum): FP64, 325.1 MB for the
+# 893,952 interfaces of a 96^3 sweep; FP32 (mixed path), 329.6 MB for the 2,113,536 of a 128^3
+# sweep.  Traffic grows in proportion to the interfaces of a launch.
+FACE_DRAM_BYTES_PER_INTERFACE = 325.1e6 / 893952
+FACE_DRAM_BYTES_PER_INTERFACE_F32 = 329.6e6 / 2113536
 
 
 def load_flops():
@@ -77,7 +79,8 @@ def face_alg_bytes(wl):
     nv = nd + 2
     visc = wl.case.get("reynolds", 0.0) > 0.0
     er = 4 if wl.precision == "mixed" else 8
-    cells = er * (nv + nv + nv)                                   # primitives, P' and P'' along the sweep
+    # primitives and P' along the sweep, and P'' (the FP32 kernel forms P'' from P and P' itself)
+    cells = er * (nv + nv + (0 if wl.precision == "mixed" else nv))
     if visc:
         cells += er * (1 + 1 + (nd - 1) * (nd + 1))               # T, T', tangential [u, T]' of two directions
     # interface metrics: FP64, or the FP32 copies the mixed path reads
@@ -412,7 +415,8 @@ def run_gpu(args, wl):
                          "frac": achieved / HBM_PEAK_GBS}, **common)
         roofline["peak_note"] = f"HBM copy bandwidth, {HBM_PEAK_KIND} (MEASURED_PEAKS.json)"
     if mixed:
-        roofline["traffic"] = None
+        roofline["traffic"] = FACE_DRAM_BYTES_PER_INTERFACE_F32 * faces_per_launch
+        roofline["traffic_note"] = "bytes per launch, scaled from a 128^3 ncu capture by interfaces"
     else:
         roofline["traffic"] = FACE_DRAM_BYTES_PER_INTERFACE * faces_per_launch
         roofline["traffic_note"] = "bytes per launch, scaled from a 96^3 ncu capture by interfaces"

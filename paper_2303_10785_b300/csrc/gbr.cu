@@ -111,11 +111,20 @@ __global__ void k_halo(RhsArgsT<R> A, int d, Box b) {
   body_halo<ND>(A, d, i, j, k);
 }
 
+// Gradient passes: the ND directions of one chunk of cells are consecutive blocks, so the passes
+// over a chunk run close together in time and share its fields in L2 (one DRAM read of each
+// field instead of one per direction).
+#define GRAD_THREAD(B0, B1, B2)                                                   \
+  const int e = blockIdx.x % ND;                                                  \
+  const Box b = e == 0 ? B0 : (e == 1 ? B1 : B2);                                 \
+  const long long _t = (long long)(blockIdx.x / ND) * blockDim.x + threadIdx.x;   \
+  if (_t >= box_size(b)) return;                                                  \
+  int i, j, k;                                                                    \
+  box_coord(b, _t, i, j, k);
+
 template <int ND, class R = double>
 __global__ void k_grad1(RhsArgsT<R> A, Box b0, Box b1, Box b2) {
-  const int e = blockIdx.y;
-  const Box b = e == 0 ? b0 : (e == 1 ? b1 : b2);
-  BOX_THREAD(b);
+  GRAD_THREAD(b0, b1, b2);
   body_grad1<ND>(A, e, i, j, k);
 }
 
@@ -134,16 +143,14 @@ __global__ void k_ig4_factor(double* table, int n, int periodic) { ig4_factor(ta
 
 template <int ND, class R = double>
 __global__ void k_grad2(RhsArgsT<R> A, Box b0, Box b1, Box b2) {
-  const int e = blockIdx.y;
-  const Box b = e == 0 ? b0 : (e == 1 ? b1 : b2);
-  BOX_THREAD(b);
+  GRAD_THREAD(b0, b1, b2);
   body_grad2<ND>(A, e, i, j, k);
 }
 
 // Interfaces whose App. E test failed, handed from their thread to a worker thread of the block.
 template <int ND, class R>
 struct BoundSlot {
-  long long p1;
+  FaceIx<R> p1;
   unsigned limit;
   R nu[ND];
   R ra, a2;
@@ -202,23 +209,18 @@ __device__ __forceinline__ void face_block(const RhsArgsT<R>& A, int d, bool val
   if (valid) face_flux<ND, VISC, MOV>(A, d, i, j, k, C);
 }
 
-// FP64: bound work compacted over the block (FP64-pipe bound: -7 % on the 128^3 TGV);
-// FP32: one whole interface per thread (memory bound: the barriers cost more than they save)
+// Bound work compacted over the block in both precisions (FP64: FP64-pipe bound, -7 % on the
+// 128^3 TGV; FP32, where the bounds form the four cells' f'': -5 % against one interface per thread)
 template <int ND, bool VISC, bool MOV, class R = double>
 __global__ void __launch_bounds__(GBR_FACE_BLOCK, sizeof(R) == 4 ? GBR_FACE_MIN_BLOCKS_F32 : GBR_FACE_MIN_BLOCKS)
     k_face(RhsArgsT<R> A, int d, Box b) {
-  if constexpr (sizeof(R) == 8) {
-    __shared__ BoundSlot<ND, R> slots[GBR_FACE_BLOCK];
-    __shared__ int count;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = t < box_size(b);
-    int i = 0, j = 0, k = 0;
-    if (valid) box_coord(b, t, i, j, k);
-    face_block<ND, VISC, MOV>(A, d, valid, i, j, k, slots, &count);
-  } else {
-    BOX_THREAD(b);
-    body_face<ND, VISC, MOV>(A, d, i, j, k);
-  }
+  __shared__ BoundSlot<ND, R> slots[GBR_FACE_BLOCK];
+  __shared__ int count;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = t < box_size(b);
+  int i = 0, j = 0, k = 0;
+  if (valid) box_coord(b, t, i, j, k);
+  face_block<ND, VISC, MOV>(A, d, valid, i, j, k, slots, &count);
 }
 
 template <int ND, bool MOV, class R = double>
@@ -288,6 +290,8 @@ struct Sizes {
   size_t bytes[SL_COUNT];
 };
 
+Layout layout_of(const gbr_params* p);
+
 bool valid_params(const gbr_params* p, std::string& why) {
   if (!p) { why = "null params"; return false; }
   if (p->ndim != 2 && p->ndim != 3) { why = "ndim must be 2 or 3"; return false; }
@@ -331,6 +335,15 @@ bool valid_params(const gbr_params* p, std::string& why) {
     if (p->gradient_scheme == GBR_GRAD_MIG4 && p->n[d] < 4) { why = "MIG4 needs at least 4 cells per axis"; return false; }
   long long cells = (long long)p->n[0] * p->n[1] * (p->ndim == 3 ? p->n[2] : 1);
   if (cells > (1LL << 34)) { why = "grid too large"; return false; }
+  // the interface kernels address their arrays with 32-bit offsets: (fields + 1) x padded cells
+  // and 9 x interfaces of a direction stay below 2^32 (a larger grid would not fit in memory)
+  const Layout L = layout_of(p);
+  long long fmax = 0;
+  for (int d = 0; d < L.nd; ++d) fmax = std::max(fmax, L.fcount[d]);
+  if ((long long)(L.nv + 1) * L.pcount >= (1LL << 32) || 9LL * fmax >= (1LL << 32)) {
+    why = "grid too large (32-bit array offsets)";
+    return false;
+  }
   return true;
 }
 
@@ -359,7 +372,7 @@ Plan plan_of(const gbr_params* p, const Layout& L) {
   P.add(ER * nv * L.pcount);                      // SL_PRIM
   P.add(visc ? ER * L.pcount : 0);                // SL_TEMP
   P.add(ER * nd * (nv + (visc ? 1 : 0)) * L.pcount);  // SL_G1
-  P.add(ER * nd * nv * L.pcount);                 // SL_G2
+  P.add(p->precision == GBR_PREC_MIXED ? 0 : ER * nd * nv * L.pcount);  // SL_G2 (FP64 path only)
   P.add(ER * nv * fsum);                          // SL_FLUX
   P.add(D * nd * L.ncount);                       // SL_NODES
   P.add(mov ? D * nd * L.ncount : 0);             // SL_NVEL
@@ -726,6 +739,7 @@ RhsArgsT<R> rhs_args_r(gbr_ctx* c, const double* q) {
     for (int s = 0; s < 2; ++s) A.bc[d][s] = c->p.bc[d][s];
   A.viscous = c->visc;
   A.pref = (sizeof(R) == 4) ? c->pref : 0.0;
+  A.pref_r = R(A.pref);
   return A;
 }
 RhsArgs rhs_args(gbr_ctx* c, const double* q) { return rhs_args_r<double>(c, q); }
@@ -788,11 +802,13 @@ gbr_status run_rhs_nd(gbr_ctx* c, const double* qs, const double* q0, double* ou
       CKL("k_ig4");
     }
   } else {
-    k_grad1<ND, R><<<dim3(g1, ND), kBlock, 0, st>>>(A, B.grad1[0], B.grad1[1], B.grad1[2]);
+    k_grad1<ND, R><<<g1 * ND, kBlock, 0, st>>>(A, B.grad1[0], B.grad1[1], B.grad1[2]);
     CKL("k_grad1");
   }
-  k_grad2<ND, R><<<dim3(g2, ND), kBlock, 0, st>>>(A, B.grad2[0], B.grad2[1], B.grad2[2]);
-  CKL("k_grad2");
+  if constexpr (!kFaceFormsG2<R>) {
+    k_grad2<ND, R><<<g2 * ND, kBlock, 0, st>>>(A, B.grad2[0], B.grad2[1], B.grad2[2]);
+    CKL("k_grad2");
+  }
   for (int d = 0; d < ND; ++d) {
     gbr_status s = launch_face<ND, R>(c, A, d, B.faces[d]);
     if (s != GBR_OK) return s;
@@ -870,7 +886,7 @@ void carve(gbr_ctx* c) {
   size_t foff = 0;
   for (int d = 0; d < 3; ++d) {
     c->g1[d] = (d < nd) ? rptr(SL_G1, (size_t)d * n1 * L.pcount) : nullptr;
-    c->g2[d] = (d < nd) ? rptr(SL_G2, (size_t)d * nv * L.pcount) : nullptr;
+    c->g2[d] = (d < nd && c->p.precision != GBR_PREC_MIXED) ? rptr(SL_G2, (size_t)d * nv * L.pcount) : nullptr;
     c->flux[d] = (d < nd) ? rptr(SL_FLUX, (size_t)nv * foff) : nullptr;
     c->fh[d] = (d < nd) ? ptr(SL_FH) + (size_t)nd * foff : nullptr;
     c->fu[d] = (d < nd && c->visc) ? ptr(SL_FU) + (size_t)nd * nd * foff : nullptr;
@@ -1058,7 +1074,8 @@ gbr_status gbr_set_state(gbr_ctx* c, const double* q, int on_device) {
     double ke = 0.0;
     for (int a = 0; a < c->L.nd; ++a) ke += q0[1 + a] * q0[1 + a] / q0[0];
     const double p0 = (c->p.gamma - 1.0) * (q0[nv - 1] - 0.5 * ke);
-    c->pref = std::isfinite(p0) ? p0 : 0.0;
+    // rounded to FP32, so that the FP64 primitive pass and the FP32 kernels use the same number
+    c->pref = std::isfinite(p0) && std::fabs(p0) < 1e38 ? (double)(float)p0 : 0.0;
   }
   return GBR_OK;
 }
@@ -1445,8 +1462,8 @@ cudaError_t static_rhs_launches(gbr_ctx& c, const double* q, double* dqdt, cudaS
     g1 = std::max(g1, grid_of(B.grad1[d], kBlock));
     g2 = std::max(g2, grid_of(B.grad2[d], kBlock));
   }
-  k_grad1<ND><<<dim3(g1, ND), kBlock, 0, st>>>(A, B.grad1[0], B.grad1[1], B.grad1[2]);
-  k_grad2<ND><<<dim3(g2, ND), kBlock, 0, st>>>(A, B.grad2[0], B.grad2[1], B.grad2[2]);
+  k_grad1<ND><<<g1 * ND, kBlock, 0, st>>>(A, B.grad1[0], B.grad1[1], B.grad1[2]);
+  k_grad2<ND><<<g2 * ND, kBlock, 0, st>>>(A, B.grad2[0], B.grad2[1], B.grad2[2]);
   if (c.visc) {
     if (c.mov) static_face_launches<ND, true, true>(A, B, st);
     else static_face_launches<ND, true, false>(A, B, st);

@@ -113,29 +113,21 @@ __global__ void __launch_bounds__(kBlock) kb_grad12(const BatchJob<R>* jobs, con
   });
 }
 
-// As k_face: FP64 with the limiter's bound work compacted over the block (every thread takes
-// part in each work block's barriers), FP32 one interface per thread at 768 threads per SM.
+// As k_face: the limiter's bound work compacted over the block (every thread takes part in
+// each work block's barriers); FP32 at 768 threads per SM.
 template <int ND, bool VISC, class R, int BS>
 __global__ void __launch_bounds__(BS, sizeof(R) == 4 ? 768 / BS : 1)
     kb_face(const BatchJob<R>* jobs, const WorkItem* items, int n, int total) {
-  if constexpr (sizeof(R) == 8) {
-    __shared__ BoundSlot<ND, R> slots[BS];
-    __shared__ int count;
-    for_work(items, n, total, [&](const WorkItem& it, int lb) {
-      const BatchJob<R>& J = jobs[it.job];
-      const long long t = (long long)lb * blockDim.x + threadIdx.x;
-      const bool valid = t < box_size(J.faces[it.sub]);
-      int i = 0, j = 0, k = 0;
-      if (valid) box_coord(J.faces[it.sub], t, i, j, k);
-      face_block<ND, VISC, false>(J.A, it.sub, valid, i, j, k, slots, &count);
-    });
-  } else {
-    for_work(items, n, total, [&](const WorkItem& it, int lb) {
-      const BatchJob<R>& J = jobs[it.job];
-      BATCH_CELL(J.faces[it.sub]);
-      body_face<ND, VISC, false>(J.A, it.sub, i, j, k);
-    });
-  }
+  __shared__ BoundSlot<ND, R> slots[BS];
+  __shared__ int count;
+  for_work(items, n, total, [&](const WorkItem& it, int lb) {
+    const BatchJob<R>& J = jobs[it.job];
+    const long long t = (long long)lb * blockDim.x + threadIdx.x;
+    const bool valid = t < box_size(J.faces[it.sub]);
+    int i = 0, j = 0, k = 0;
+    if (valid) box_coord(J.faces[it.sub], t, i, j, k);
+    face_block<ND, VISC, false>(J.A, it.sub, valid, i, j, k, slots, &count);
+  });
 }
 
 template <int ND, class R>
@@ -382,7 +374,14 @@ gbr_status enqueue_rhs(gbr_batch* b, const Kind& K, int stage, long long& launch
         jobs, K.d_items[WL_PAD], (int)K.items[WL_PAD].size(), K.total[WL_PAD], qin);
     BK(cudaGetLastError(), "kb_prim_halo");
   }
-  if (K.tune.fused_grad) {
+  if constexpr (kFaceFormsG2<R>) {
+    // FP32: the interface kernel forms f'' itself
+    auto k1 = kb_grad1<ND, R>;
+    k1<<<persistent_grid(b, k1, kBlock, K.total[WL_GRAD1]), kBlock, 0, st>>>(
+        jobs, K.d_items[WL_GRAD1], (int)K.items[WL_GRAD1].size(), K.total[WL_GRAD1]);
+    BK(cudaGetLastError(), "kb_grad1");
+    launches += 2;
+  } else if (K.tune.fused_grad) {
     auto kern = kb_grad12<ND, R>;
     kern<<<persistent_grid(b, kern, kBlock, K.total[WL_GRAD1]), kBlock, 0, st>>>(
         jobs, K.d_items[WL_GRAD1], (int)K.items[WL_GRAD1].size(), K.total[WL_GRAD1]);
@@ -556,7 +555,8 @@ gbr_status autotune_kind(gbr_batch* b, Kind& K) {
   float best_ms = 1e30f;
   std::vector<char> host;
   for (int fb : kFaceBlockOptions) {
-    for (int fused = 0; fused < 2; ++fused) {
+    // the gradient sweep is a choice of the FP64 path only (FP32 forms f'' in the interface kernel)
+    for (int fused = 0; fused < (K.key.prec == GBR_PREC_MIXED ? 1 : 2); ++fused) {
       K.tune.face_block = fb;
       K.tune.fused_grad = fused;
       build_items(K);
@@ -645,7 +645,7 @@ gbr_status rebuild(gbr_batch* b) {
   } else {
     // count the launches of one step without running it
     for (const Kind& K : b->kinds) {
-      const int per_stage = K.tune.fused_grad ? 4 : 5;
+      const int per_stage = (K.tune.fused_grad || K.key.prec == GBR_PREC_MIXED) ? 4 : 5;
       launches += 3 + (K.total[WL_DT] > 0 ? 1 : 0) + 3 * per_stage;
     }
   }

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <type_traits>
 
 #ifdef __CUDACC__
 #define GBR_HD __host__ __device__ __forceinline__
@@ -101,6 +102,34 @@ GBR_HD long long fidx(const Layout& L, int d, int i, int j, int k) {
   int c[3] = {i, j, k};
   c[d] += 1;
   return (long long)c[0] + (long long)c[1] * L.fs[d][1] + (long long)c[2] * L.fs[d][2];
+}
+// The same indices in 32-bit unsigned arithmetic, for the interface kernels: every offset into
+// one of their arrays (field x padded cell, component x interface) is below 2^32, which
+// valid_params checks for every context (a grid with more cells would not fit in device
+// memory).  One widening multiply-add per address instead of 64-bit index arithmetic.
+GBR_HD unsigned pidx32(const Layout& L, int i, int j, int k) {
+  return (unsigned)(i + L.hp[0]) + (unsigned)(j + L.hp[1]) * (unsigned)L.ps[1] +
+         (unsigned)(k + L.hp[2]) * (unsigned)L.ps[2];
+}
+GBR_HD unsigned fidx32(const Layout& L, int d, int i, int j, int k) {
+  int c[3] = {i, j, k};
+  c[d] += 1;
+  return (unsigned)c[0] + (unsigned)c[1] * (unsigned)L.fs[d][1] + (unsigned)c[2] * (unsigned)L.fs[d][2];
+}
+// Index type of the interface kernels: 32-bit offsets in FP64 (1.4 % faster: the FP64 kernel issues
+// its integer work beside a busy FP64 pipe), 64-bit in FP32 (32-bit offsets measured 40 % slower
+// there).
+template <class R>
+using FaceIx = std::conditional_t<sizeof(R) == sizeof(double), unsigned, long long>;
+template <class I>
+GBR_HD I face_pidx(const Layout& L, int i, int j, int k) {
+  if constexpr (sizeof(I) == 4) return pidx32(L, i, j, k);
+  else return pidx(L, i, j, k);
+}
+template <class I>
+GBR_HD I face_fidx(const Layout& L, int d, int i, int j, int k) {
+  if constexpr (sizeof(I) == 4) return fidx32(L, d, i, j, k);
+  else return fidx(L, d, i, j, k);
 }
 
 struct Box {
@@ -513,6 +542,7 @@ struct RhsArgsT {
   const double* q;      // [nv][ncells] conserved state of the stage
   R* prim;              // [nv][pcount] primitives with halo; the pressure slot holds p - pref
   double pref;          // pressure offset of the stored primitives (mixed path; 0 on the FP64 path)
+  R pref_r;             // the same in the path's type (the mixed path's offset is an FP32 number)
   R* temp;              // [pcount] T = p/rho (viscous)
   R* g1[3];             // [nv (+1 T)][pcount] first derivatives along d
   R* g2[3];             // [nv][pcount] second derivatives along d
@@ -594,7 +624,7 @@ GBR_HD void prim_store(const RhsArgsT<R>& A, const double* q, long long c, long 
   const R Erel = R(q[(NV - 1) * NC + c] - A.pref * A.ph.igm1);
   const R prel = A.pr.gm1 * (Erel - R(0.5) * ke);  // p - pref
   A.prim[(NV - 1) * PC + p] = prel;
-  if (A.viscous) A.temp[p] = (prel + R(A.pref)) * ir;
+  if (A.viscous) A.temp[p] = (prel + A.pref_r) * ir;
 }
 
 // primitives at interior cells
@@ -747,6 +777,18 @@ GBR_HD void body_grad1(const RhsArgsT<R>& A, int e, int i, int j, int k) {
 }
 
 // Sec. 5.1 step 1: f''_i = 2 (f_{i+1} - 2 f_i + f_{i-1}) - 0.5 (f'_{i+1} - f'_{i-1})
+// The FP32 path forms f'' inside the interface kernel instead (from f and f' of the four cells
+// of the stencil, which it loads anyway): no f'' array and no pass.  The FP64 path stores f''
+// once per cell and direction, which costs fewer FP64 operations than forming it twice per
+// interface.
+template <class R>
+constexpr bool kFaceFormsG2 = sizeof(R) == sizeof(float);
+
+template <class R, class I>
+GBR_HD R second_deriv(const R* f, const R* f1, I p, I s) {
+  return R(2) * (f[p + s] - R(2) * f[p] + f[p - s]) - R(0.5) * (f1[p + s] - f1[p - s]);
+}
+
 template <int ND, class R>
 GBR_HD void body_grad2(const RhsArgsT<R>& A, int e, int i, int j, int k) {
   constexpr int NV = ND + 2;
@@ -755,7 +797,7 @@ GBR_HD void body_grad2(const RhsArgsT<R>& A, int e, int i, int j, int k) {
   for (int c = 0; c < NV; ++c) {
     const R* f = A.prim + c * PC;
     const R* f1 = A.g1[e] + c * PC;
-    A.g2[e][c * PC + p] = R(2) * (f[p + s] - R(2) * f[p] + f[p - s]) - R(0.5) * (f1[p + s] - f1[p - s]);
+    A.g2[e][c * PC + p] = second_deriv(f, f1, p, s);
   }
 }
 
@@ -1068,7 +1110,7 @@ GBR_HD void hllc(const R* PL, const R* PR, const R* nh, R nn2, R inn, R nt, cons
 template <int ND, class R>
 struct FaceCtx {
   static constexpr int NV = ND + 2;
-  long long p1, f;      // padded index of cell i, interface index
+  FaceIx<R> p1, f;      // padded index of cell i, interface index
   R nh[ND], nu[ND];
   R nn2, inn, nt;
   R ra, a2, ira, ia2;   // face state of the eigenvectors
@@ -1082,11 +1124,12 @@ GBR_HD void face_unlimited(const RhsArgsT<R>& A, int d, int i, int j, int k, Fac
   constexpr int NV = ND + 2;
   const Layout& L = A.L;
   const PhysR<R>& ph = A.pr;
-  const long long PC = L.pcount, s = L.ps[d];
-  const long long p1 = pidx(L, i, j, k);
-  const long long pp[4] = {p1 - s, p1, p1 + s, p1 + 2 * s};
-  const long long FC = L.fcount[d];
-  const long long f = fidx(L, d, i, j, k);
+  using I = FaceIx<R>;
+  const I PC = (I)L.pcount, s = (I)L.ps[d];
+  const I p1 = face_pidx<I>(L, i, j, k);
+  const I pp[4] = {p1 - s, p1, p1 + s, p1 + 2 * s};
+  const I FC = (I)L.fcount[d];
+  const I f = face_fidx<I>(L, d, i, j, k);
   const R* P = A.prim;
   C.p1 = p1;
   C.f = f;
@@ -1103,7 +1146,7 @@ GBR_HD void face_unlimited(const RhsArgsT<R>& A, int d, int i, int j, int k, Fac
   for (int a = 0; a < ND; ++a) C.nu[a] = C.nh[a] * C.inn;
   // face state of the eigenvectors: mean of rho and p of cells i, i+1 (reading A6)
   const R rb = R(0.5) * (P[pp[1]] + P[pp[2]]);
-  const R pb = gfma(R(0.5), P[(NV - 1) * PC + pp[1]] + P[(NV - 1) * PC + pp[2]], R(A.pref));
+  const R pb = gfma(R(0.5), P[(NV - 1) * PC + pp[1]] + P[(NV - 1) * PC + pp[2]], A.pref_r);
   // a = sqrt(gamma p / rho): with t = 1/sqrt(gamma p rho), rho a = gamma p rho t, 1/(rho a) = t,
   // a = gamma p t and 1/a = rho t -- one reciprocal square root, no division
   const R gp = ph.gamma * pb;
@@ -1125,7 +1168,20 @@ GBR_HD void face_unlimited(const RhsArgsT<R>& A, int d, int i, int j, int k, Fac
   // Eq. (legendre_polys) unlimited states relative to the base cells, projected
   // after combining: W^L - W_i = R^-1 (f'_i / 2 + f''_i / 12),
   // W^R - W_{i+1} = R^-1 (-f'_{i+1} / 2 + f''_{i+1} / 12)
-  {
+  if constexpr (kFaceFormsG2<R>) {
+    // FP32: f'' of cells i and i+1 formed here (the same formula as body_grad2) from the
+    // primitives and f' of cells i-1 .. i+2 -- two loads of f' per field instead of two of f''
+    R xl[NV], xr[NV];
+    #pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      const R* f = P + c * PC;
+      const R* f1 = A.g1[d] + c * PC;
+      xl[c] = gfma(R(0.5), f1[pp[1]], second_deriv(f, f1, pp[1], s) * R(1.0 / 12.0));
+      xr[c] = gfma(R(-0.5), f1[pp[2]], second_deriv(f, f1, pp[2], s) * R(1.0 / 12.0));
+    }
+    project<ND>(C.nu, C.ra, C.a2, xl, C.dL);
+    project<ND>(C.nu, C.ra, C.a2, xr, C.dR);
+  } else {
     R x[NV];
     #pragma unroll
     for (int c = 0; c < NV; ++c)
@@ -1147,20 +1203,28 @@ GBR_HD void face_unlimited(const RhsArgsT<R>& A, int d, int i, int j, int k, Fac
 }
 
 // App. E bounds of the fields that failed the test: the curvatures d of cells i-1 .. i+2 are
-// projected with the face's eigenvectors (only here), then each failing state is limited
+// projected with the face's eigenvectors (only here), then each failing state is limited.
+// FP32 forms the four f'' here (keeping those of cells i and i+1 from face_unlimited instead
+// measured 3 % slower: more live registers); FP64 reads them from the f'' array.
 template <int ND, class R>
-GBR_HD void face_bounds(const RhsArgsT<R>& A, int d, const R* nu, R ra, R a2, long long p1, unsigned limit,
+GBR_HD void face_bounds(const RhsArgsT<R>& A, int d, const R* nu, R ra, R a2, FaceIx<R> p1, unsigned limit,
                         const R (*Wd)[ND + 2], R* dL, R* dR) {
   constexpr int NV = ND + 2;
   const Layout& L = A.L;
-  const long long PC = L.pcount, s = L.ps[d];
-  const long long pp[4] = {p1 - s, p1, p1 + s, p1 + 2 * s};
+  using I = FaceIx<R>;
+  const I PC = (I)L.pcount, s = (I)L.ps[d];
+  const I pp[4] = {p1 - s, p1, p1 + s, p1 + 2 * s};
   R W2[4][NV];
   #pragma unroll
   for (int m = 0; m < 4; ++m) {
     R x[NV];
     #pragma unroll
-    for (int c = 0; c < NV; ++c) x[c] = A.g2[d][c * PC + pp[m]];
+    for (int c = 0; c < NV; ++c) {
+      if constexpr (kFaceFormsG2<R>)
+        x[c] = second_deriv(A.prim + c * PC, A.g1[d] + c * PC, pp[m], s);
+      else
+        x[c] = A.g2[d][c * PC + pp[m]];
+    }
     project<ND>(nu, ra, a2, x, W2[m]);
   }
   #pragma unroll
@@ -1175,11 +1239,12 @@ GBR_HD void face_flux(const RhsArgsT<R>& A, int d, int i, int j, int k, const Fa
   constexpr int NV = ND + 2;
   const Layout& L = A.L;
   const PhysR<R>& ph = A.pr;
-  const long long PC = L.pcount, s = L.ps[d];
-  const long long p1 = C.p1;
-  const long long pp[4] = {p1 - s, p1, p1 + s, p1 + 2 * s};
-  const long long FC = L.fcount[d];
-  const long long f = C.f;
+  using I = FaceIx<R>;
+  const I PC = (I)L.pcount, s = (I)L.ps[d];
+  const I p1 = C.p1;
+  const I pp[4] = {p1 - s, p1, p1 + s, p1 + 2 * s};
+  const I FC = (I)L.fcount[d];
+  const I f = C.f;
   const R* P = A.prim;
   const R* nh = C.nh;
   const R nn2 = C.nn2, inn = C.inn, nt = C.nt;
@@ -1192,7 +1257,7 @@ GBR_HD void face_flux(const RhsArgsT<R>& A, int d, int i, int j, int k, const Fa
     PR[c] += P[c * PC + pp[2]];
   }
   R F[NV];
-  hllc<ND>(PL, PR, nh, nn2, inn, nt, ph, R(A.pref), F);
+  hllc<ND>(PL, PR, nh, nn2, inn, nt, ph, A.pref_r, F);
 
   if (VISC) {
     // Sec. 5.2 alpha-damping on [u.., T].  gc2[v][e] = 2 d(phi_v)/d(xi_e) at the interface:
@@ -1275,7 +1340,7 @@ GBR_HD void face_flux(const RhsArgsT<R>& A, int d, int i, int j, int k, const Fa
   for (int c = 0; c < NV; ++c) A.flux[d][c * FC + f] = F[c];
 }
 
-// the whole interface in one thread (host emulation and the batch kernels)
+// the whole interface in one thread (host emulation)
 template <int ND, bool VISC, bool MOV, class R>
 GBR_HD void body_face(const RhsArgsT<R>& A, int d, int i, int j, int k) {
   FaceCtx<ND, R> C;
@@ -1303,6 +1368,12 @@ struct UpdArgsT {
 };
 using UpdArgs = UpdArgsT<double>;
 
+// |x| > 1.79e308 (overflow or NaN) and x <= 0 tested on the bit pattern (integer pipe; the
+// FP64 pipe is the scarce one on this GPU)
+constexpr long long kUpdHuge = 0x7FEFDCF158ADBB99LL;  // bit pattern of 1.79e308
+GBR_HD bool upd_not_finite(double x) { return (dbits(x) & kMag) > kUpdHuge; }
+GBR_HD bool upd_not_positive(double x) { return dbits(x) <= 0; }  // +0, negatives, -0
+
 template <int ND, bool MOV, class R>
 GBR_HD bool body_update(const UpdArgsT<R>& U, int i, int j, int k) {
   constexpr int NV = ND + 2;
@@ -1310,7 +1381,10 @@ GBR_HD bool body_update(const UpdArgsT<R>& U, int i, int j, int k) {
   const long long c = cidx(L, i, j, k), NC = L.ncells;
   const double J = U.jac[c];
   bool bad = false;
-  const double dtc = (U.mode == 1) ? (*U.dt) * U.cc : 0.0;
+  // RK combination out = ca q0 + cb qs + cc dt J r with r the residual: dt cc J is one factor per
+  // cell; the first SSP-RK3 stage (qs = q0, ca + cb = 1) is out = qs + dt J r and reads Q^n once
+  const bool first = U.qs == U.q0 && U.ca + U.cb == 1.0;
+  const double dtJ = (U.mode == 1) ? (*U.dt) * U.cc * J : 0.0;
   for (int v = 0; v < NV; ++v) {
     // flux differences in the fluxes' own type (for neighbouring FP32 fluxes within a factor 2 of
     // each other the difference is exact), summed and converted to FP64 once
@@ -1322,16 +1396,24 @@ GBR_HD bool body_update(const UpdArgsT<R>& U, int i, int j, int k) {
     }
     const double res = (double)rsum;
     const double qv = U.qs[v * NC + c];
-    double Lv = MOV ? J * gfma(-U.gcl[c], qv, res) : J * res;
-    if (U.sigma) Lv = gfma(-U.sigma[c], qv - U.qamb[v], Lv);
-    if (U.mode == 0) {
-      U.out[v * NC + c] = Lv;
-      bad |= !(Lv == Lv) || std::fabs(Lv) > 1.79e308;
-    } else {
+    const double r = MOV ? gfma(-U.gcl[c], qv, res) : res;  // residual before 1/J (GCL term, Eq. Jacb2)
+    if (U.mode == 0 || U.sigma) {
+      double Lv = J * r;
+      if (U.sigma) Lv = gfma(-U.sigma[c], qv - U.qamb[v], Lv);
+      if (U.mode == 0) {
+        U.out[v * NC + c] = Lv;
+        bad |= upd_not_finite(Lv);
+        continue;
+      }
+      const double dtc = (*U.dt) * U.cc;
       const double o = gfma(U.ca, U.q0[v * NC + c], gfma(U.cb, qv, dtc * Lv));
       U.out[v * NC + c] = o;
-      bad |= !(o == o) || std::fabs(o) > 1.79e308 || (v == 0 && !(o > 0.0));
+      bad |= upd_not_finite(o) || (v == 0 && upd_not_positive(o));
+      continue;
     }
+    const double o = first ? gfma(dtJ, r, qv) : gfma(U.ca, U.q0[v * NC + c], gfma(U.cb, qv, dtJ * r));
+    U.out[v * NC + c] = o;
+    bad |= upd_not_finite(o) || (v == 0 && upd_not_positive(o));
   }
   return bad;
 }
