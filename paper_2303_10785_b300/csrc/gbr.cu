@@ -130,7 +130,7 @@ __global__ void k_grad1(RhsArgsT<R> A, Box b0, Box b1, Box b2) {
 
 // MIG4: one thread per (line, field); blockIdx.y is the field (primitives, then T)
 template <int ND, class R = double>
-__global__ void k_ig4(RhsArgsT<R> A, int e, Box lines, const double* table) {
+__global__ void k_ig4(RhsArgsT<R> A, int e, Box lines, const R* table) {
   constexpr int NV = ND + 2;
   BOX_THREAD(lines);
   const int f = blockIdx.y;
@@ -140,6 +140,64 @@ __global__ void k_ig4(RhsArgsT<R> A, int e, Box lines, const double* table) {
 }
 
 __global__ void k_ig4_factor(double* table, int n, int periodic) { ig4_factor(table, n, periodic != 0); }
+
+// MIG4 with the lines staged in shared memory: a block of kIg4Lines threads takes kIg4Lines
+// neighbouring lines of one field (neighbours along axis a: x for y- and z-lines, y for
+// x-lines), loads their padded rows with coalesced reads (consecutive threads read consecutive
+// addresses: along the line for x-lines, across the lines otherwise), solves each line in its
+// own thread from shared memory (in place; rows of odd length, so the threads' accesses fall in
+// distinct banks), and stores the derivative rows back the same way.  The x-lines, which a thread
+// per line in global memory walks with a stride across the warp, become coalesced.
+constexpr int kIg4Lines = 32;
+
+template <int ND, class R>
+__global__ void __launch_bounds__(kIg4Lines) k_ig4s(RhsArgsT<R> A, int e, int a, Box lines, const R* table,
+                                                      int srow) {
+  constexpr int NV = ND + 2;
+  extern __shared__ __align__(16) unsigned char ig4_smem[];
+  R* F = reinterpret_cast<R*>(ig4_smem);
+  const Layout& L = A.L;
+  const int b = 3 - e - a;  // the third axis (extent 1 in 2D)
+  const int n = L.n[e], M = n + 2 * H;
+  const int na = lines.hi[a] - lines.lo[a];
+  const int tiles = (na + kIg4Lines - 1) / kIg4Lines;
+  const int ta = blockIdx.x % tiles, tb = blockIdx.x / tiles;
+  const int nl = min(kIg4Lines, na - ta * kIg4Lines);
+  int c[3];
+  c[e] = -H;
+  c[a] = lines.lo[a] + ta * kIg4Lines;
+  c[b] = lines.lo[b] + tb;
+  const long long base = pidx(L, c[0], c[1], c[2]);  // padded cell -H of the tile's first line
+  const long long sa = L.ps[a], se = L.ps[e];
+  const int f = blockIdx.y;
+  const long long PC = L.pcount;
+  const R* src = (f < NV) ? A.prim + f * PC : A.temp;
+  R* dst = A.g1[e] + f * PC;
+  const int tid = threadIdx.x;
+  if (e == 0) {
+    for (int l = 0; l < nl; ++l)
+      for (int m = tid; m < M; m += kIg4Lines) F[l * srow + m] = src[base + l * sa + m];
+  } else if (tid < nl) {
+    for (int m = 0; m < M; ++m) F[tid * srow + m] = src[base + tid + m * se];
+  }
+  __syncthreads();
+  if (tid < nl) ig4_solve(table, n, L.per[e] != 0, F + tid * srow + H, F + tid * srow + H, 1);
+  __syncthreads();
+  // rows written by the solve: the n cells and 3 images each side (periodic), the padded line (open)
+  const int m0 = L.per[e] ? H - 3 : 0, m1 = L.per[e] ? H + n + 3 : M;
+  if (e == 0) {
+    for (int l = 0; l < nl; ++l)
+      for (int m = m0 + tid; m < m1; m += kIg4Lines) dst[base + l * sa + m] = F[l * srow + m];
+  } else if (tid < nl) {
+    for (int m = m0; m < m1; ++m) dst[base + tid + m * se] = F[tid * srow + m];
+  }
+}
+
+// shared-memory row length (odd) and bytes of the staged MIG4 kernel for a line of n cells
+inline int ig4_srow(int n) { return (n + 2 * H) | 1; }
+template <class R>
+size_t ig4_smem_bytes(int n) { return sizeof(R) * (size_t)kIg4Lines * ig4_srow(n); }
+constexpr size_t kIg4SmemMax = 200 * 1024;
 
 template <int ND, class R = double>
 __global__ void k_grad2(RhsArgsT<R> A, Box b0, Box b1, Box b2) {
@@ -283,7 +341,7 @@ struct Plan {
 enum Slot {
   SL_Q0, SL_Q1, SL_Q2, SL_PRIM, SL_TEMP, SL_G1, SL_G2, SL_FLUX, SL_NODES, SL_NVEL, SL_XC, SL_VC, SL_XD, SL_MH,
   SL_DET, SL_MU, SL_MT, SL_FH, SL_FU, SL_FT, SL_GCL, SL_JAC, SL_SIGMA, SL_INFLOW, SL_SCAL, SL_ERR, SL_IG4, SL_FH32, SL_FU32,
-  SL_FT32, SL_COUNT
+  SL_FT32, SL_IG4F, SL_COUNT
 };
 
 struct Sizes {
@@ -401,6 +459,7 @@ Plan plan_of(const gbr_params* p, const Layout& L) {
   P.add(f32 ? sizeof(float) * nd * fsum : 0);                   // SL_FH32
   P.add(f32 && visc ? sizeof(float) * nd * nd * fsum : 0);      // SL_FU32
   P.add(f32 && mov ? sizeof(float) * fsum : 0);                 // SL_FT32
+  P.add(f32 ? sizeof(float) * ig4 : 0);                         // SL_IG4F: FP32 copies of the MIG4 factors
   P.total = (P.total + 255) & ~(size_t)255;
   return P;
 }
@@ -447,6 +506,7 @@ struct gbr_ctx {
   float *fh32[3], *fu32[3], *ft32[3];  // mixed path: FP32 copies of the interface metrics
   double *sigma, *inflow, *scal;
   double* ig4[3];  // MIG4 line-solve factors per direction (or null)
+  float* ig4f[3];  // mixed path: their FP32 copies (no conversions in the FP32 line solves)
   int* err;
   bool visc, mov, have_sponge, have_motion, metrics_ready;
   double qamb[5];
@@ -798,7 +858,23 @@ gbr_status run_rhs_nd(gbr_ctx* c, const double* qs, const double* q0, double* ou
       Box lines = B.grad1[e];
       lines.lo[e] = 0;
       lines.hi[e] = 1;
-      k_ig4<ND, R><<<dim3(grid_of(lines, 128), nf), 128, 0, st>>>(A, e, lines, c->ig4[e]);
+      const R* table;
+      if constexpr (sizeof(R) == sizeof(float)) table = c->ig4f[e];
+      else table = c->ig4[e];
+      const size_t smem = ig4_smem_bytes<R>(L.n[e]);
+      if (smem <= kIg4SmemMax) {
+        static bool attr_set = false;  // one opt-in per instantiation (above the 48 KB default)
+        if (!attr_set) {
+          cudaFuncSetAttribute(k_ig4s<ND, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIg4SmemMax);
+          attr_set = true;
+        }
+        const int a = (e == 0) ? 1 : 0, bx = 3 - e - a;
+        const int na = lines.hi[a] - lines.lo[a], nb = lines.hi[bx] - lines.lo[bx];
+        const unsigned tiles = (unsigned)((na + kIg4Lines - 1) / kIg4Lines) * (unsigned)nb;
+        k_ig4s<ND, R><<<dim3(tiles, nf), kIg4Lines, smem, st>>>(A, e, a, lines, table, ig4_srow(L.n[e]));
+      } else {
+        k_ig4<ND, R><<<dim3(grid_of(lines, 128), nf), 128, 0, st>>>(A, e, lines, table);
+      }
       CKL("k_ig4");
     }
   } else {
@@ -918,8 +994,10 @@ void carve(gbr_ctx* c) {
     size_t toff = 0;
     for (int d = 0; d < 3; ++d) {
       c->ig4[d] = nullptr;
+      c->ig4f[d] = nullptr;
       if (d < L.nd && P.len[SL_IG4]) {
         c->ig4[d] = (double*)(c->ws + P.off[SL_IG4]) + toff;
+        if (P.len[SL_IG4F]) c->ig4f[d] = (float*)(c->ws + P.off[SL_IG4F]) + toff;
         toff += (size_t)ig4_table_len(L.n[d], L.per[d] != 0);
       }
     }
@@ -998,7 +1076,13 @@ gbr_status gbr_create(const gbr_params* p, const double* nodes, const double* no
     return s;
   }
   if (p->gradient_scheme == GBR_GRAD_MIG4) {
-    for (int d = 0; d < L.nd; ++d) k_ig4_factor<<<1, 1, 0, c->stream>>>(c->ig4[d], L.n[d], L.per[d]);
+    for (int d = 0; d < L.nd; ++d) {
+      k_ig4_factor<<<1, 1, 0, c->stream>>>(c->ig4[d], L.n[d], L.per[d]);
+      if (c->ig4f[d]) {
+        const long long n = ig4_table_len(L.n[d], L.per[d] != 0);
+        k_to_f32<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, c->stream>>>(c->ig4[d], c->ig4f[d], n);
+      }
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) {
       gbr_status s = fail(c, GBR_ECUDA, std::string("MIG4 factors: ") + cudaGetErrorString(e));

@@ -861,68 +861,93 @@ GBR_HD R ig4_rhs(const R* f, long long p, long long s) {
   return R((2.0 + kIg4Alpha) / 3.0) * (f[p + s] - f[p - s]) + R((4.0 * kIg4Alpha - 1.0) / 12.0) * (f[p + 2 * s] - f[p - 2 * s]);
 }
 
-// One line of f' along e through padded cell (i, j, k) (coordinate e ignored): field f, output g
+// IG4 right side of a row from the window values f_{i-2}, f_{i-1}, f_{i+1}, f_{i+2} (the same
+// arithmetic as ig4_rhs)
 template <class R>
-GBR_HD void ig4_line(const Layout& L, const double* t, int e, const R* f, R* g, int i, int j, int k) {
+GBR_HD R ig4_rhs_w(R fm2, R fm1, R fp1, R fp2) {
+  return R((2.0 + kIg4Alpha) / 3.0) * (fp1 - fm1) + R((4.0 * kIg4Alpha - 1.0) / 12.0) * (fp2 - fm2);
+}
+
+// One IG4 line: f0 and g0 point at cell 0 of the line, s is the distance between its cells.
+// Every value of f is read once, into a register window around the row being formed, and read
+// before g is written at or below it, so g may overwrite f in place (the staged kernel's
+// shared-memory row).  Periodic: the n cells with the images of f at -2, -1, n, n + 1; g at
+// 0 .. n-1 and its images at -3 .. -1 and n .. n+2.  Open: the padded line -H .. n+H-1.
+template <class R>
+GBR_HD void ig4_solve(const R* t, int n, bool periodic, const R* f0, R* g0, long long s) {
   const R al = R(kIg4Alpha);
-  const long long s = L.ps[e];
-  int c0[3] = {i, j, k};
-  c0[e] = 0;
-  const long long base = pidx(L, c0[0], c0[1], c0[2]);  // cell 0 of the line
-  const int n = L.n[e];
-  if (L.per[e]) {
-    const double* cp = t;
-    const double* inv = t + n;
-    const double* z = t + 2 * n;
-    // forward sweep (rp kept in g), backward sweep (y in g)
+  if (periodic) {
+    const R* cp = t;
+    const R* inv = t + n;
+    const R* z = t + 2 * n;
+    // forward sweep (rp kept in g), window f_{m-2} .. f_{m+2}
+    R w0 = f0[-2 * s], w1 = f0[-s], w2 = f0[0], w3 = f0[s], w4 = f0[2 * s];
     R prev = R(0);
     for (int m = 0; m < n; ++m) {
-      const long long p = base + m * s;
-      const R r = ig4_rhs(f, p, s);
+      const R r = ig4_rhs_w(w0, w1, w3, w4);
       prev = (m == 0) ? r * R(inv[0]) : (r - al * prev) * R(inv[m]);
-      g[p] = prev;
+      w0 = w1;
+      w1 = w2;
+      w2 = w3;
+      w3 = w4;
+      if (m + 1 < n) w4 = f0[(m + 3) * s];
+      g0[m * s] = prev;
     }
+    // backward sweep (y in g)
     R y = prev;
     for (int m = n - 2; m >= 0; --m) {
-      const long long p = base + m * s;
-      y = g[p] - R(cp[m]) * y;
-      g[p] = y;
+      y = g0[m * s] - R(cp[m]) * y;
+      g0[m * s] = y;
     }
-    const R fac = (y - al * g[base + (n - 1) * s]) * R(t[3 * n]);
-    for (int m = 0; m < n; ++m) {
-      const long long p = base + m * s;
-      g[p] = g[p] - fac * R(z[m]);
-    }
+    const R fac = (y - al * g0[(n - 1) * s]) * R(t[3 * n]);
+    for (int m = 0; m < n; ++m) g0[m * s] = g0[m * s] - fac * R(z[m]);
     for (int m = 1; m <= 3; ++m) {  // periodic images of the derivative the gradient box needs
-      g[base - m * s] = g[base + (n - m) * s];
-      g[base + (n - 1 + m) * s] = g[base + (m - 1) * s];
+      g0[-m * s] = g0[(n - m) * s];
+      g0[(n - 1 + m) * s] = g0[(m - 1) * s];
     }
   } else {
     const int M = n + 2 * H;
-    const double* cp = t;
-    const double* inv = t + M;
-    const long long b0 = base - H * s;  // padded cell -H: row 0
+    const R* cp = t;
+    const R* inv = t + M;
+    const R* f = f0 - H * s;  // padded cell -H: row 0
+    R* g = g0 - H * s;
+    // window f_{m-3} .. f_{m+3} of row m (entries outside the line are never used)
+    R w0 = R(0), w1 = R(0), w2 = R(0), w3 = f[0], w4 = f[s], w5 = f[2 * s], w6 = f[3 * s];
     R prev = R(0);
     for (int m = 0; m < M; ++m) {
-      const long long p = b0 + m * s;
       R r;
-      if (m == 0) r = R(-1.5) * f[p] + R(2) * f[p + s] - R(0.5) * f[p + 2 * s];
-      else if (m == 1) r = R(-0.25) * f[p - s] - R(5.0 / 6.0) * f[p] + R(1.5) * f[p + s] - R(0.5) * f[p + 2 * s] + f[p + 3 * s] * R(1.0 / 12.0);
-      else if (m == 2 || m == M - 3) r = R(2.0 / 3.0) * (f[p + s] - f[p - s]) - (f[p + 2 * s] - f[p - 2 * s]) * R(1.0 / 12.0);
-      else if (m == M - 2) r = R(0.25) * f[p + s] + R(5.0 / 6.0) * f[p] - R(1.5) * f[p - s] + R(0.5) * f[p - 2 * s] - f[p - 3 * s] * R(1.0 / 12.0);
-      else if (m == M - 1) r = R(1.5) * f[p] - R(2) * f[p - s] + R(0.5) * f[p - 2 * s];
-      else r = ig4_rhs(f, p, s);
+      if (m == 0) r = R(-1.5) * w3 + R(2) * w4 - R(0.5) * w5;
+      else if (m == 1) r = R(-0.25) * w2 - R(5.0 / 6.0) * w3 + R(1.5) * w4 - R(0.5) * w5 + w6 * R(1.0 / 12.0);
+      else if (m == 2 || m == M - 3) r = R(2.0 / 3.0) * (w4 - w2) - (w5 - w1) * R(1.0 / 12.0);
+      else if (m == M - 2) r = R(0.25) * w4 + R(5.0 / 6.0) * w3 - R(1.5) * w2 + R(0.5) * w1 - w0 * R(1.0 / 12.0);
+      else if (m == M - 1) r = R(1.5) * w3 - R(2) * w2 + R(0.5) * w1;
+      else r = ig4_rhs_w(w1, w2, w4, w5);
       const bool expl = m < 3 || m >= M - 3;
       prev = (m == 0 || expl) ? r * R(inv[m]) : (r - al * prev) * R(inv[m]);
-      g[p] = prev;
+      w0 = w1;
+      w1 = w2;
+      w2 = w3;
+      w3 = w4;
+      w4 = w5;
+      w5 = w6;
+      if (m + 4 < M) w6 = f[(m + 4) * s];
+      g[m * s] = prev;
     }
     R y = prev;
     for (int m = M - 2; m >= 0; --m) {
-      const long long p = b0 + m * s;
-      y = g[p] - R(cp[m]) * y;
-      g[p] = y;
+      y = g[m * s] - R(cp[m]) * y;
+      g[m * s] = y;
     }
   }
+}
+
+// One line of f' along e through padded cell (i, j, k) (coordinate e ignored): field f, output g
+template <class R>
+GBR_HD void ig4_line(const Layout& L, const R* t, int e, const R* f, R* g, int i, int j, int k) {
+  int c0[3] = {i, j, k};
+  c0[e] = 0;
+  const long long base = pidx(L, c0[0], c0[1], c0[2]);  // cell 0 of the line
+  ig4_solve(t, L.n[e], L.per[e] != 0, f + base, g + base, L.ps[e]);
 }
 
 // Both derivatives along e in one pass over the first-derivative box: f' at the cell (stored),

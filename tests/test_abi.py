@@ -76,6 +76,16 @@ def test_invalid_params_rejected(lib, bad):
     assert lib.gbr_last_global_error()
 
 
+def test_grid_beyond_32bit_offsets_rejected(lib):
+    # the interface kernels address their arrays with 32-bit offsets: a grid whose (fields + 1) x
+    # padded cells reach 2^32 is rejected on the host (it would need ~1 TB of workspace anyway)
+    ok = gbr.make_params(I.case_params(3, (512, 512, 512)))
+    assert lib.gbr_workspace_bytes(ctypes.byref(ok)) > 0
+    big = gbr.make_params(I.case_params(3, (1024, 1024, 1024)))
+    assert lib.gbr_workspace_bytes(ctypes.byref(big)) == 0
+    assert b"32-bit" in lib.gbr_last_global_error()
+
+
 def test_small_workspace_is_enomem_before_any_device_work(lib):
     p = gbr.make_params(I.case_params(3, (16, 16, 16)))
     need = lib.gbr_workspace_bytes(ctypes.byref(p))
