@@ -93,3 +93,25 @@ def test_mig4_rejected_by_batch():
         b.add(s, 0.4)
     b.close()
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_mig4_long_lines_take_the_per_line_kernel(precision):
+    # x-lines of 800 cells do not fit the staged kernel's shared memory in FP64 (32 lines x 813
+    # doubles > 200 KB) and run one thread per line in global memory; the y-lines are staged.
+    # FP32 rows of 800 cells still fit.  Both precisions must match the oracle.
+    from paper_2303_10785_b300 import inputs as I
+
+    n = (800, 12)
+    case = mig4(I.case_params(2, n), precision=precision)
+    nodes = I.nodes_uniform(n, (40.0, 0.6))
+    xc = I.centroids(nodes, n, (1, 1))
+    kx, ky = 2 * np.pi / 40.0 * 3, 2 * np.pi / 0.6
+    wave = np.sin(kx * xc[0]) * np.cos(ky * xc[1])
+    P = np.stack([1.0 + 0.1 * wave, 0.5 + 0.05 * wave, 0.1 * np.cos(kx * xc[0]), 1.0 / (1.4 * 0.25) + 0.2 * wave])
+    q = I.prim_to_cons(P, 1.4)
+    orc = O.Oracle(dict(case, precision="fp64"), nodes)
+    s = gbr.Solver(case, nodes)
+    s.set_state(q)
+    assert rhs_err(orc, s, q) < (1e-12 if precision == "fp64" else 2e-6)
+    s.close()
