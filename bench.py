@@ -519,8 +519,9 @@ def run_serving(args):
     errors = [j.error for j in mix + base + allmix if j.error]
 
     def record(jobs, st):
-        return {"lat": [j.finished - j.arrival for j in jobs if j.finished is not None],
-                "work": float(sum(j.work for j in jobs if j.finished is not None)), "makespan": st["makespan_s"]}
+        done = [j for j in jobs if j.finished is not None and j.error is None]
+        return {"lat": [j.finished - j.arrival for j in done], "work": float(sum(j.work for j in done)),
+                "makespan": st["makespan_s"]}
 
     recs = gather_objects({"mix": record(mix, st_mix), "base": record(base, st_base),
                            "allmix": record(allmix, st_allmix), "errors": errors,

@@ -1085,7 +1085,10 @@ GBR_HD void hllc(const R* PL, const R* PR, const R* nh, R nn2, R inn, R nt, cons
     Ur = gfma(nh[a], PR[1 + a], Ur);
   }
   const R El = gfma(pl, ph.igm1, R(0.5) * rl * q2l), Er = gfma(pr, ph.igm1, R(0.5) * rr * q2r);
-  const R cl = gpl * tl, cr = gpr * tr;  // speeds of sound
+  // speeds of sound c = sqrt(gamma p / rho) = |gamma p| t: the absolute value keeps the formula's
+  // value for a reconstructed state whose density and pressure are both negative (the App. E bounds
+  // do not exclude one at a sawtooth of cell values)
+  const R cl = gabs(gpl) * tl, cr = gabs(gpr) * tr;
   const R SL = gmin(gfma(-cl, nn, Ul), gfma(-cr, nn, Ur));
   const R SR = gmax(gfma(cl, nn, Ul), gfma(cr, nn, Ur));
   const R aL = rl * (SL - Ul), aR = rr * (SR - Ur);

@@ -56,9 +56,10 @@ class gbr_motion(ctypes.Structure):
 
 
 class GbrError(RuntimeError):
-    def __init__(self, status, msg):
+    def __init__(self, status, msg, member=-1):
         super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
         self.status = status
+        self.member = member  # Batch.sync: index of the first member with a bad state (else -1)
 
 
 _lib = None
@@ -380,10 +381,12 @@ class Batch:
         self._check(self.L.gbr_batch_step(self.h, int(n)))
 
     def sync(self, timeout=60.0):
+        """Drain the stream; GbrError (ENONFINITE) names the first member whose state went bad in
+        .member (the others are unaffected: members share launches, not data)."""
         bad = ctypes.c_int(-1)
         rc = self.L.gbr_batch_sync(self.h, float(timeout), ctypes.byref(bad))
         if rc:
-            raise GbrError(rc, self.L.gbr_batch_last_error(self.h).decode())
+            raise GbrError(rc, self.L.gbr_batch_last_error(self.h).decode(), bad.value)
 
     def info(self):
         m, k = ctypes.c_int(), ctypes.c_int()

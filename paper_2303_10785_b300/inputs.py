@@ -453,8 +453,11 @@ def serving_job_inputs(spec, precision=None):
             cfl = 0.4
         else:
             nodes = nodes_skewed_2d(n, (1.0, 1.0), skew_deg=spec["skew_deg"], jitter=0.1, seed=spec["seed"])
-            xc = centroids(nodes, n, (1, 1))
-            rho, p = sod_slab_prim(xc[1], L=1.0)
+            # the slab is bounded by grid lines (logical coordinate eta), oblique to x on the skewed
+            # mesh; drawn on the jittered centroids instead, a row crossing the jump would hold a
+            # cell-to-cell sawtooth of the two states
+            eta = np.broadcast_to(((np.arange(e) + 0.5) / e)[:, None], n)
+            rho, p = sod_slab_prim(eta, L=1.0)
             z = np.zeros_like(rho)
             q = prim_to_cons(np.stack([rho, z, z, p]), 1.4)
             cfl = 0.3

@@ -62,13 +62,17 @@ class Job:
 
 
 def latency_stats(jobs):
-    lat = np.array([j.finished - j.arrival for j in jobs if j.finished is not None])
-    work = sum(j.work for j in jobs if j.finished is not None)
+    """Time-to-N-steps of the completed jobs and their aggregate throughput; failed jobs (a state
+    that went non-finite, a job that could not be admitted) are counted apart."""
+    done = [j for j in jobs if j.finished is not None and j.error is None]
+    lat = np.array([j.finished - j.arrival for j in done])
+    work = sum(j.work for j in done)
     if lat.size == 0:
         return {}
     start = min(j.arrival for j in jobs)
-    end = max(j.finished for j in jobs if j.finished is not None)
-    return {"jobs": int(lat.size), "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+    end = max(j.finished for j in done)
+    return {"jobs": int(lat.size), "failed": sum(1 for j in jobs if j.error is not None),
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "mean_s": float(lat.mean()), "makespan_s": end - start,
             "cell_rk_stage_updates_per_s": work / max(end - start, 1e-9)}
 
@@ -147,6 +151,30 @@ class Server:
             self.done.append(job)
         self.active = keep
 
+    def _fail(self, entry, why, now):
+        job, s, ptr, _ = entry
+        self.batch.remove(s)
+        s.close()
+        self.arena.free(ptr)
+        job.error = why
+        job.finished = now
+        self.done.append(job)
+        self.active.remove(entry)
+
+    def _sync_isolating(self, clock):
+        """Drain the batch; a member whose state went non-finite fails alone (its job is retired
+        with the error and its memory freed) and the others carry on."""
+        while True:
+            try:
+                self.batch.sync()
+                return
+            except gbr.GbrError as e:
+                if e.status != gbr.GBR_ENONFINITE or e.member < 0:
+                    raise
+                bad = self.batch.members[e.member]
+                entry = next(x for x in self.active if x[1] is bad)
+                self._fail(entry, f"job {entry[0].id}: {e}", clock())
+
     def run(self, jobs, clock=None, t0=None):
         """Serve `jobs` (their .arrival in seconds from the start); returns them when all are done."""
         clock = clock or time.perf_counter
@@ -167,7 +195,7 @@ class Server:
                 continue
             k = min(self.chunk, min(job.steps - n for job, _, _, n in self.active))
             self.batch.step(k)
-            self.batch.sync()
+            self._sync_isolating(clock)
             for entry in self.active:
                 entry[3] += k
             self._retire(clock)
@@ -205,9 +233,14 @@ def run_serial(jobs, device="cuda", precision=None, clock=None):
         s = job.make_solver(stream)
         for _ in range(job.steps):
             s.rk_step(job.cfl)
-        s.sync()
-        job.result = s.get_state()
-        job.time = s.time()[0]
+        try:
+            s.sync()
+            job.result = s.get_state()
+            job.time = s.time()[0]
+        except gbr.GbrError as e:  # this job's state went bad: it fails alone
+            if e.status != gbr.GBR_ENONFINITE:
+                raise
+            job.error = f"job {job.id}: {e}"
         job.finished = clock() - start
         s.close()
     return jobs

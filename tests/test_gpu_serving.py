@@ -53,3 +53,27 @@ def test_serving_rejects_a_job_larger_than_the_pool():
     assert big.error and "larger than the device pool" in big.error
     assert all(j.result is not None for j in jobs if j is not big)
     srv.close()
+
+
+def test_a_job_whose_state_goes_bad_fails_alone():
+    # one job starts from a state with a NaN (as an unstable job would end): the batch reports it,
+    # the server retires it with the error and frees its memory, and the other jobs finish with the
+    # states they reach alone; the plain per-job form isolates it the same way
+    jobs = small_stream(5, seed=11)
+    bad = jobs[2]
+    q = bad.q.copy()
+    q[0].flat[q[0].size // 2] = np.nan
+    bad.q = q
+    alone = serving.run_serial([serving.Job(j.id, j.case, j.nodes, j.q, j.steps, j.cfl, 0.0) for j in jobs])
+    assert [a.error is not None for a in alone] == [j is bad for j in jobs]
+    pool = int(4 * max(j.footprint() for j in jobs))
+    srv = serving.Server(pool, max_active=4, chunk_steps=2)
+    srv.run(jobs)
+    assert len(srv.done) == len(jobs) and not srv.active and srv.arena.stats()["used"] == 0
+    assert bad.error and "ENONFINITE" in bad.error and bad.result is None
+    for j, a in zip(jobs, alone):
+        if j is not bad:
+            assert j.error is None and np.array_equal(j.result, a.result), j.id
+    st = serving.latency_stats(jobs)
+    assert st["jobs"] == len(jobs) - 1 and st["failed"] == 1
+    srv.close()
