@@ -452,3 +452,21 @@ def test_minimum_periodic_size():
     s.set_state(q)
     assert rhs_err(orc, s, q) < 1e-12
     s.close()
+
+
+def test_nonphysical_reconstructed_states_match_oracle():
+    # a sharp Sod slab drawn on the jittered centroids of a 28-degree skewed 378^2 mesh: rows that
+    # cross the jump hold a cell-to-cell sawtooth, where the App. E bounds leave reconstructed
+    # states with negative density and pressure (reading A37); the sound speed must be the
+    # formula's sqrt(gamma p / rho) there, as in the oracle
+    n = (378, 378)
+    case = I.case_params(2, n)
+    nodes = I.nodes_skewed_2d(n, (1.0, 1.0), skew_deg=27.942954695675876, jitter=0.1, seed=1071)
+    xc = I.centroids(nodes, n, (1, 1))
+    rho, p = I.sod_slab_prim(xc[1], L=1.0)
+    z = np.zeros_like(rho)
+    q = I.prim_to_cons(np.stack([rho, z, z, p]), GAMMA)
+    orc, s = build_pair(case, nodes, None)
+    s.set_state(q)
+    assert rhs_err(orc, s, q) < 1e-12
+    s.close()
