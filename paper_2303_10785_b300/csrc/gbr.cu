@@ -398,7 +398,8 @@ bool valid_params(const gbr_params* p, std::string& why) {
   const Layout L = layout_of(p);
   long long fmax = 0;
   for (int d = 0; d < L.nd; ++d) fmax = std::max(fmax, L.fcount[d]);
-  if ((long long)(L.nv + 1) * L.pcount >= (1LL << 32) || 9LL * fmax >= (1LL << 32)) {
+  if ((long long)(L.nv + 1) * L.pcount >= (1LL << 32) || 9LL * fmax >= (1LL << 32) || L.ecount >= (1LL << 32) ||
+      L.ncount >= (1LL << 32)) {
     why = "grid too large (32-bit array offsets)";
     return false;
   }
