@@ -28,8 +28,9 @@ namespace {
 
 // Launch shape of the interface kernel (tuning knobs, set at compile time).  The FP64
 // instantiations are FP64-pipe bound (one 128-thread block per SM's register share is
-// enough); the FP32 ones are memory-latency bound and run 6 blocks per SM (80 registers,
-// measured 17 % faster than the unconstrained 128 registers on the 128^3 TGV).
+// enough); the FP32 ones are issue- and latency-bound and run 7 blocks per SM (72 registers;
+// measured on the 128^3 TGV: 6 blocks / 80 registers 5 % slower, 8 / 64 spills, unconstrained
+// 128 registers 17 % slower).
 #ifndef GBR_FACE_BLOCK
 #define GBR_FACE_BLOCK 128
 #endif
@@ -37,7 +38,7 @@ namespace {
 #define GBR_FACE_MIN_BLOCKS 1
 #endif
 #ifndef GBR_FACE_MIN_BLOCKS_F32
-#define GBR_FACE_MIN_BLOCKS_F32 6
+#define GBR_FACE_MIN_BLOCKS_F32 7
 #endif
 
 constexpr int kBlock = 256;

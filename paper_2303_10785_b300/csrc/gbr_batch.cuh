@@ -114,10 +114,11 @@ __global__ void __launch_bounds__(kBlock) kb_grad12(const BatchJob<R>* jobs, con
 }
 
 // As k_face: the limiter's bound work compacted over the block (every thread takes part in
-// each work block's barriers); FP32 at 768 threads per SM, FP64 at 384 (at most 168 registers:
-// 4 % faster than the unconstrained 234 on a batch of 64^3 TGV and 256^2 vortex jobs).
+// each work block's barriers); FP32 at 7 blocks of 128 threads per SM (as k_face), FP64 at 384
+// threads (at most 168 registers: 4 % faster than the unconstrained 234 on a batch of 64^3 TGV
+// and 256^2 vortex jobs).
 template <int ND, bool VISC, class R, int BS>
-__global__ void __launch_bounds__(BS, sizeof(R) == 4 ? 768 / BS : (BS < 384 ? 384 / BS : 1))
+__global__ void __launch_bounds__(BS, sizeof(R) == 4 ? 896 / BS : (BS < 384 ? 384 / BS : 1))
     kb_face(const BatchJob<R>* jobs, const WorkItem* items, int n, int total) {
   __shared__ BoundSlot<ND, R> slots[BS];
   __shared__ int count;
