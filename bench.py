@@ -61,10 +61,10 @@ HBM_PEAK_GBS, HBM_PEAK_KIND = measured_hbm_gbs()
 BYTES_PER_CELL_STAGE_3D = 186.7
 # DRAM bytes (read + write) per interface of the 3D viscous interface kernel, from one ncu
 # capture of a launch (dram__bytes_read.sum + dram__bytes_write.sum): FP64, 325.0 MB for the
-# 893,952 interfaces of a 96^3 sweep; FP32 (mixed path), 329.0 MB for the 2,113,536 of a 128^3
+# 893,952 interfaces of a 96^3 sweep; FP32 (mixed path), 330.2 MB for the 2,113,536 of a 128^3
 # sweep.  Traffic grows in proportion to the interfaces of a launch.
 FACE_DRAM_BYTES_PER_INTERFACE = 325.0e6 / 893952
-FACE_DRAM_BYTES_PER_INTERFACE_F32 = 329.0e6 / 2113536
+FACE_DRAM_BYTES_PER_INTERFACE_F32 = 330.2e6 / 2113536
 
 
 def load_flops():

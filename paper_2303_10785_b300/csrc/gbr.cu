@@ -288,6 +288,11 @@ __global__ void k_update(UpdArgsT<R> U, Box b, int* err) {
   if (body_update<ND, MOV>(U, i, j, k)) atomicOr(err, 1);
 }
 
+__global__ void k_dt_f32(DtArgs D, float* mh32, float* mt32, float* jac32, Box b) {
+  BOX_THREAD(b);
+  body_dt_f32(D, mh32, mt32, jac32, i, j, k);
+}
+
 template <int ND, class R = double>
 __global__ void k_dt(DtArgs D, Box b, unsigned long long* minbits) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -342,7 +347,7 @@ struct Plan {
 enum Slot {
   SL_Q0, SL_Q1, SL_Q2, SL_PRIM, SL_TEMP, SL_G1, SL_G2, SL_FLUX, SL_NODES, SL_NVEL, SL_XC, SL_VC, SL_XD, SL_MH,
   SL_DET, SL_MU, SL_MT, SL_FH, SL_FU, SL_FT, SL_GCL, SL_JAC, SL_SIGMA, SL_INFLOW, SL_SCAL, SL_ERR, SL_IG4, SL_FH32, SL_FU32,
-  SL_FT32, SL_IG4F, SL_COUNT
+  SL_FT32, SL_IG4F, SL_MH32, SL_MT32, SL_JAC32, SL_COUNT
 };
 
 struct Sizes {
@@ -462,6 +467,9 @@ Plan plan_of(const gbr_params* p, const Layout& L) {
   P.add(f32 && visc ? sizeof(float) * nd * nd * fsum : 0);      // SL_FU32
   P.add(f32 && mov ? sizeof(float) * fsum : 0);                 // SL_FT32
   P.add(f32 ? sizeof(float) * ig4 : 0);                         // SL_IG4F: FP32 copies of the MIG4 factors
+  P.add(f32 ? sizeof(float) * 9 * L.ncells : 0);               // SL_MH32: the time step's cell metrics
+  P.add(f32 && mov ? sizeof(float) * 3 * L.ncells : 0);        // SL_MT32
+  P.add(f32 ? sizeof(float) * L.ncells : 0);                   // SL_JAC32
   P.total = (P.total + 255) & ~(size_t)255;
   return P;
 }
@@ -506,6 +514,7 @@ struct gbr_ctx {
   void *prim, *temp, *g1[3], *g2[3], *flux[3];  // element type double (FP64) or float (mixed)
   double *nodes, *nvel, *xc, *vc, *xd, *mh, *det, *mu, *mt, *fh[3], *fu[3], *ft[3], *gcl, *jac;
   float *fh32[3], *fu32[3], *ft32[3];  // mixed path: FP32 copies of the interface metrics
+  float *mh32, *mt32, *jac32;          // mixed path: FP32 copies of the cell metrics (time step)
   double *sigma, *inflow, *scal;
   double* ig4[3];  // MIG4 line-solve factors per direction (or null)
   float* ig4f[3];  // mixed path: their FP32 copies (no conversions in the FP32 line solves)
@@ -732,6 +741,8 @@ RhsBoxes rhs_boxes(const Layout& L) {
   return B;
 }
 
+DtArgs dt_args(gbr_ctx* c);
+
 gbr_status run_geometry(gbr_ctx* c) {
   const Layout& L = c->L;
   GeoArgs G = geo_args(c);
@@ -762,6 +773,9 @@ gbr_status run_geometry(gbr_ctx* c) {
           (const double*)(c->ws + P.off[sl[0]]), (float*)(c->ws + P.off[sl[1]]), n);
       CKL("k_to_f32");
     }
+    // and of the cell metrics and J the time step reads
+    k_dt_f32<<<grid_of(B.inner, kBlock), kBlock, 0, st>>>(dt_args(c), c->mh32, c->mt32, c->jac32, B.inner);
+    CKL("k_dt_f32");
   }
   return GBR_OK;
 }
@@ -921,15 +935,23 @@ gbr_status run_rhs(gbr_ctx* c, const double* qs, const double* q0, double* out, 
                       : run_rhs_nd<2, double>(c, qs, q0, out, mode, ca, cb, cc);
 }
 
-gbr_status run_dt(gbr_ctx* c, double cfl) {
-  const Layout& L = c->L;
+DtArgs dt_args(gbr_ctx* c) {
   DtArgs D;
-  D.L = L;
+  D.L = c->L;
   D.ph = c->ph;
   D.q = c->q[0];
   D.mh = c->mh;
   D.mt = c->mov ? c->mt : nullptr;
   D.jac = c->jac;
+  D.mh32 = c->mh32;
+  D.mt32 = c->mov ? c->mt32 : nullptr;
+  D.jac32 = c->jac32;
+  return D;
+}
+
+gbr_status run_dt(gbr_ctx* c, double cfl) {
+  const Layout& L = c->L;
+  const DtArgs D = dt_args(c);
   Box bi = pad_box(L, 0, 0);
   unsigned long long* bits = reinterpret_cast<unsigned long long*>(c->scal + S_DTMIN);
   k_dt_init<<<1, 1, 0, c->stream>>>(bits);
@@ -988,6 +1010,12 @@ void carve(gbr_ctx* c) {
   c->mt = ptr(SL_MT);
   c->gcl = ptr(SL_GCL);
   c->jac = ptr(SL_JAC);
+  {
+    auto f32p = [&](int slot) -> float* { return P.len[slot] ? (float*)(c->ws + P.off[slot]) : nullptr; };
+    c->mh32 = f32p(SL_MH32);
+    c->mt32 = f32p(SL_MT32);
+    c->jac32 = f32p(SL_JAC32);
+  }
   c->sigma = ptr(SL_SIGMA);
   c->inflow = ptr(SL_INFLOW);
   c->scal = ptr(SL_SCAL);

@@ -292,12 +292,9 @@ BatchJob<R> make_job(gbr_ctx* c, double cfl) {
       U.mode = 0;
     }
   }
-  J.D.L = L;
-  J.D.ph = c->ph;
-  J.D.q = c->q[0];
-  J.D.mh = c->mh;
-  J.D.mt = nullptr;
-  J.D.jac = c->jac;
+  J.D = dt_args(c);
+  J.D.mt = nullptr;  // static members only
+  J.D.mt32 = nullptr;
   for (int s = 0; s < 3; ++s) J.q[s] = c->q[s];
   const RhsBoxes B = rhs_boxes(L);
   J.pad = pad_box(L, H, H);

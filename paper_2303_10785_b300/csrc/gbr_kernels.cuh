@@ -1458,7 +1458,23 @@ struct DtArgs {
   const double* mh;   // ext layout
   const double* mt;   // ext layout (moving) or null
   const double* jac;
+  // mixed path: FP32 copies on the interior cells ([9][cells], [3][cells], [cells]; the FP32
+  // time step then converts only the state), else null
+  const float* mh32;
+  const float* mt32;
+  const float* jac32;
 };
+
+// FP32 copies of the cell metrics the mixed path's time step reads (interior cells)
+GBR_HD void body_dt_f32(const DtArgs& D, float* mh32, float* mt32, float* jac32, int i, int j, int k) {
+  const Layout& L = D.L;
+  const long long c = cidx(L, i, j, k), NC = L.ncells, e = eidx(L, i, j, k), EC = L.ecount;
+  for (int ee = 0; ee < L.nd; ++ee) {
+    for (int a = 0; a < L.nd; ++a) mh32[(ee * 3 + a) * NC + c] = (float)D.mh[(ee * 3 + a) * EC + e];
+    if (D.mt) mt32[ee * NC + c] = (float)D.mt[ee * EC + e];
+  }
+  jac32[c] = (float)D.jac[c];
+}
 
 template <int ND, class R = double>
 GBR_HD double body_dt(const DtArgs& D, int i, int j, int k) {
@@ -1478,7 +1494,8 @@ GBR_HD double body_dt(const DtArgs& D, int i, int j, int k) {
   }
   const R pr = R(ph.gm1) * (R(D.q[(NV - 1) * NC + c]) - R(0.5) * ke);
   const R cs = gsqrt(R(ph.gamma) * pr * ir);
-  const R J = R(D.jac[c]);
+  constexpr bool F32 = sizeof(R) == sizeof(float);
+  const R J = (F32 && D.jac32) ? R(D.jac32[c]) : R(D.jac[c]);
   R nu_eff = R(0);
   if (ph.viscous) {
     R mu = R(ph.mu_ref);
@@ -1492,10 +1509,11 @@ GBR_HD double body_dt(const DtArgs& D, int i, int j, int k) {
   // largest denominator: division is correctly rounded and monotone, so the result is the same value
   R worst = R(0);
   for (int ee = 0; ee < ND; ++ee) {
-    R Uc = D.mt ? R(D.mt[ee * EC + e]) * J : R(0);
+    R Uc = D.mt ? ((F32 && D.mt32) ? R(D.mt32[ee * NC + c]) : R(D.mt[ee * EC + e])) * J : R(0);
     R g2 = R(0);
     for (int a = 0; a < ND; ++a) {
-      const R m = R(D.mh[(ee * 3 + a) * EC + e]) * J;
+      const R mv = (F32 && D.mh32) ? R(D.mh32[(ee * 3 + a) * NC + c]) : R(D.mh[(ee * 3 + a) * EC + e]);
+      const R m = mv * J;
       Uc = gfma(m, u[a], Uc);
       g2 = gfma(m, m, g2);
     }
