@@ -912,6 +912,7 @@ gbr_status run_rhs_nd(gbr_ctx* c, const double* qs, const double* q0, double* ou
   U.q0 = q0;
   U.out = out;
   U.jac = c->jac;
+  U.jac32 = c->jac32;
   U.gcl = c->gcl;
   U.sigma = c->have_sponge ? c->sigma : nullptr;
   for (int v = 0; v < 5; ++v) U.qamb[v] = c->qamb[v];
@@ -1592,6 +1593,7 @@ cudaError_t static_rhs_launches(gbr_ctx& c, const double* q, double* dqdt, cudaS
   U.q0 = q;
   U.out = dqdt;
   U.jac = c.jac;
+  U.jac32 = nullptr;
   U.gcl = c.gcl;
   U.sigma = nullptr;
   for (int v = 0; v < 5; ++v) U.qamb[v] = 0.0;

@@ -270,6 +270,7 @@ BatchJob<R> make_job(gbr_ctx* c, double cfl) {
     U.L = L;
     for (int d = 0; d < 3; ++d) U.flux[d] = static_cast<const R*>(c->flux[d]);
     U.jac = c->jac;
+    U.jac32 = c->jac32;
     U.gcl = c->gcl;
     U.sigma = c->have_sponge ? c->sigma : nullptr;
     for (int v = 0; v < 5; ++v) U.qamb[v] = c->qamb[v];

@@ -1390,6 +1390,7 @@ struct UpdArgsT {
   const double* q0;     // Q^n
   double* out;          // new state (mode 1) or L(Q) (mode 0)
   const double* jac;
+  const float* jac32;   // mixed path: FP32 copy of J (else null)
   const double* gcl;
   const double* sigma;  // sponge (or null)
   double qamb[5];
@@ -1410,11 +1411,32 @@ GBR_HD bool body_update(const UpdArgsT<R>& U, int i, int j, int k) {
   constexpr int NV = ND + 2;
   const Layout& L = U.L;
   const long long c = cidx(L, i, j, k), NC = L.ncells;
-  const double J = U.jac[c];
   bool bad = false;
   // RK combination out = ca q0 + cb qs + cc dt J r with r the residual: dt cc J is one factor per
   // cell; the first SSP-RK3 stage (qs = q0, ca + cb = 1) is out = qs + dt J r and reads Q^n once
   const bool first = U.qs == U.q0 && U.ca + U.cb == 1.0;
+  if constexpr (sizeof(R) == sizeof(float) && !MOV) {
+    // mixed path, static mesh, no sponge: the increment dt cc J r is formed in FP32 (r is an FP32
+    // sum; its relative error stays that of r) and only the state combination is FP64
+    if (U.mode == 1 && !U.sigma && U.jac32) {
+      const float dtJf = float((*U.dt) * U.cc) * U.jac32[c];
+      for (int v = 0; v < NV; ++v) {
+        R rsum = R(0);
+        for (int d = 0; d < ND; ++d) {
+          const long long fhi = fidx(L, d, i, j, k);
+          const long long FC = L.fcount[d];
+          rsum = rsum - (U.flux[d][v * FC + fhi] - U.flux[d][v * FC + fhi - L.fs[d][d]]);
+        }
+        const double inc = (double)(dtJf * rsum);
+        const double qv = U.qs[v * NC + c];
+        const double o = first ? qv + inc : gfma(U.ca, U.q0[v * NC + c], gfma(U.cb, qv, inc));
+        U.out[v * NC + c] = o;
+        bad |= upd_not_finite(o) || (v == 0 && upd_not_positive(o));
+      }
+      return bad;
+    }
+  }
+  const double J = U.jac[c];
   const double dtJ = (U.mode == 1) ? (*U.dt) * U.cc * J : 0.0;
   for (int v = 0; v < NV; ++v) {
     // flux differences in the fluxes' own type (for neighbouring FP32 fluxes within a factor 2 of
