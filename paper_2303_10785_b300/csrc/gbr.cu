@@ -100,8 +100,12 @@ __global__ void k_prim(RhsArgsT<R> A, Box b) {
   body_prim<ND>(A, i, j, k);
 }
 
+// Primitive and update passes: latency-bound streams, run at full occupancy (8 blocks of 256 threads
+// per SM, 32 registers): the mixed 128^3 TGV step 4.7 % faster than at 42 / 54 registers.
+constexpr int kStreamBlocks = 8;
+
 template <int ND, class R = double>
-__global__ void k_prim_halo(RhsArgsT<R> A, const double* q, Box b) {
+__global__ void __launch_bounds__(kBlock, kStreamBlocks) k_prim_halo(RhsArgsT<R> A, const double* q, Box b) {
   BOX_THREAD(b);
   body_prim_halo<ND>(A, q, i, j, k);
 }
@@ -283,7 +287,7 @@ __global__ void __launch_bounds__(GBR_FACE_BLOCK, sizeof(R) == 4 ? GBR_FACE_MIN_
 }
 
 template <int ND, bool MOV, class R = double>
-__global__ void k_update(UpdArgsT<R> U, Box b, int* err) {
+__global__ void __launch_bounds__(kBlock, kStreamBlocks) k_update(UpdArgsT<R> U, Box b, int* err) {
   BOX_THREAD(b);
   if (body_update<ND, MOV>(U, i, j, k)) atomicOr(err, 1);
 }

@@ -74,7 +74,7 @@ __device__ __forceinline__ void for_work(const WorkItem* items, int n_items, int
   box_coord(BOX, _t, i, j, k);
 
 template <int ND, class R>
-__global__ void __launch_bounds__(kBlock) kb_prim_halo(const BatchJob<R>* jobs, const WorkItem* items, int n,
+__global__ void __launch_bounds__(kBlock, kStreamBlocks) kb_prim_halo(const BatchJob<R>* jobs, const WorkItem* items, int n,
                                                         int total, int stage) {
   for_work(items, n, total, [&](const WorkItem& it, int lb) {
     const BatchJob<R>& J = jobs[it.job];
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(BS, sizeof(R) == 4 ? 896 / BS : (BS < 384 ? 38
 }
 
 template <int ND, class R>
-__global__ void __launch_bounds__(kBlock) kb_update(const BatchJob<R>* jobs, const WorkItem* items, int n, int total,
+__global__ void __launch_bounds__(kBlock, kStreamBlocks) kb_update(const BatchJob<R>* jobs, const WorkItem* items, int n, int total,
                                                      int stage) {
   for_work(items, n, total, [&](const WorkItem& it, int lb) {
     const BatchJob<R>& J = jobs[it.job];
