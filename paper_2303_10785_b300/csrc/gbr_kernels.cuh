@@ -789,7 +789,15 @@ constexpr bool kFaceFormsG2 = sizeof(R) == sizeof(float);
 
 template <class R, class I>
 GBR_HD R second_deriv(const R* f, const R* f1, I p, I s) {
-  return R(2) * (f[p + s] - R(2) * f[p] + f[p - s]) - R(0.5) * (f1[p + s] - f1[p - s]);
+  if constexpr (sizeof(R) == sizeof(double)) {
+    // FP64 (pipe-bound pass): five operations, 2 (f_{i+1} - 2 f_i + f_{i-1}) as one fused
+    // multiply-add on -0.5 (f'_{i+1} - f'_{i-1}) (-1.3 % step time)
+    const R c2 = gfma(R(-2), f[p], f[p + s]) + f[p - s];
+    return gfma(R(2), c2, R(-0.5) * (f1[p + s] - f1[p - s]));
+  } else {
+    // FP32 (inside the interface kernel, where the form above measured 1.3 % slower)
+    return R(2) * (f[p + s] - R(2) * f[p] + f[p - s]) - R(0.5) * (f1[p + s] - f1[p - s]);
+  }
 }
 
 template <int ND, class R>
@@ -968,7 +976,7 @@ GBR_HD void body_grad12(const RhsArgsT<R>& A, int e, const Box& b2, int i, int j
     A.g1[e][c * PC + p] = stencil_E6(f, p, s);
     if (second) {
       const R f1p = stencil_E6(f, p + s, s), f1m = stencil_E6(f, p - s, s);
-      A.g2[e][c * PC + p] = R(2) * (f[p + s] - R(2) * f[p] + f[p - s]) - R(0.5) * (f1p - f1m);
+      A.g2[e][c * PC + p] = gfma(R(2), gfma(R(-2), f[p], f[p + s]) + f[p - s], R(-0.5) * (f1p - f1m));  // as second_deriv
     }
   }
   if (A.viscous) A.g1[e][NV * PC + p] = stencil_E6(A.temp, p, s);
@@ -1406,6 +1414,22 @@ constexpr long long kUpdHuge = 0x7FEFDCF158ADBB99LL;  // bit pattern of 1.79e308
 GBR_HD bool upd_not_finite(double x) { return (dbits(x) & kMag) > kUpdHuge; }
 GBR_HD bool upd_not_positive(double x) { return dbits(x) <= 0; }  // +0, negatives, -0
 
+// -sum_d (F_{i+1/2} - F_{i-1/2}) of component v, written (F_lo - F_hi) + ... so the first term
+// needs no subtraction from zero: the same rounding as 0 - (F_hi - F_lo) - ..., one operation fewer
+template <int ND, class R>
+GBR_HD R upd_flux_sum(const UpdArgsT<R>& U, int v, int i, int j, int k) {
+  const Layout& L = U.L;
+  R r = R(0);
+  #pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    const long long fhi = fidx(L, d, i, j, k);
+    const long long FC = L.fcount[d];
+    const R t = U.flux[d][v * FC + fhi - L.fs[d][d]] - U.flux[d][v * FC + fhi];
+    r = (d == 0) ? t : r + t;
+  }
+  return r;
+}
+
 template <int ND, bool MOV, class R>
 GBR_HD bool body_update(const UpdArgsT<R>& U, int i, int j, int k) {
   constexpr int NV = ND + 2;
@@ -1421,12 +1445,7 @@ GBR_HD bool body_update(const UpdArgsT<R>& U, int i, int j, int k) {
     if (U.mode == 1 && !U.sigma && U.jac32) {
       const float dtJf = float((*U.dt) * U.cc) * U.jac32[c];
       for (int v = 0; v < NV; ++v) {
-        R rsum = R(0);
-        for (int d = 0; d < ND; ++d) {
-          const long long fhi = fidx(L, d, i, j, k);
-          const long long FC = L.fcount[d];
-          rsum = rsum - (U.flux[d][v * FC + fhi] - U.flux[d][v * FC + fhi - L.fs[d][d]]);
-        }
+        const R rsum = upd_flux_sum<ND>(U, v, i, j, k);
         const double inc = (double)(dtJf * rsum);
         const double qv = U.qs[v * NC + c];
         const double o = first ? qv + inc : gfma(U.ca, U.q0[v * NC + c], gfma(U.cb, qv, inc));
@@ -1441,12 +1460,7 @@ GBR_HD bool body_update(const UpdArgsT<R>& U, int i, int j, int k) {
   for (int v = 0; v < NV; ++v) {
     // flux differences in the fluxes' own type (for neighbouring FP32 fluxes within a factor 2 of
     // each other the difference is exact), summed and converted to FP64 once
-    R rsum = R(0);
-    for (int d = 0; d < ND; ++d) {
-      const long long fhi = fidx(L, d, i, j, k);
-      const long long FC = L.fcount[d];
-      rsum = rsum - (U.flux[d][v * FC + fhi] - U.flux[d][v * FC + fhi - L.fs[d][d]]);
-    }
+    R rsum = upd_flux_sum<ND>(U, v, i, j, k);
     const double res = (double)rsum;
     const double qv = U.qs[v * NC + c];
     const double r = MOV ? gfma(-U.gcl[c], qv, res) : res;  // residual before 1/J (GCL term, Eq. Jacb2)
