@@ -218,6 +218,8 @@ struct gbr_batch {
   cudaStream_t cur = nullptr; // stream the enqueue functions issue to (the capture stream while capturing)
   cudaStream_t cap = nullptr; // private non-blocking stream the step graph is recorded on (the legacy
                               // default stream cannot be captured)
+  std::vector<cudaStream_t> branch;  // one capture stream per kind: the kinds' steps are parallel
+                                     // branches of the step graph
   char* ws;
   size_t ws_bytes;
   int max_members;
@@ -631,6 +633,41 @@ gbr_status rebuild(gbr_batch* b) {
     if (!b->cap) BK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "capture stream");
     b->cur = b->cap;
     BK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    if (b->kinds.size() > 1) {
+      // the kinds share no data: each kind's step is a branch forked from and joined to the capture
+      // stream, so a kind whose launches do not fill the GPU overlaps the others
+      while (b->branch.size() < b->kinds.size()) {
+        cudaStream_t x = nullptr;
+        BK(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking), "branch stream");
+        b->branch.push_back(x);
+      }
+      std::vector<cudaEvent_t> ev(b->kinds.size() + 1, nullptr);
+      for (auto& x : ev) BK(cudaEventCreateWithFlags(&x, cudaEventDisableTiming), "branch event");
+      BK(cudaEventRecord(ev[0], b->cap), "fork");
+      for (size_t k = 0; k < b->kinds.size() && s == GBR_OK; ++k) {
+        BK(cudaStreamWaitEvent(b->branch[k], ev[0], 0), "fork wait");
+        b->cur = b->branch[k];
+        StepFn fn{b, &b->kinds[k], &launches};
+        s = dispatch_kind(b->kinds[k].key, fn);
+        BK(cudaEventRecord(ev[k + 1], b->branch[k]), "join");
+        BK(cudaStreamWaitEvent(b->cap, ev[k + 1], 0), "join wait");
+      }
+      b->cur = b->cap;
+      cudaGraph_t g0 = nullptr;
+      cudaError_t e0 = cudaStreamEndCapture(b->cap, &g0);
+      for (auto& x : ev) cudaEventDestroy(x);
+      b->cur = b->stream;
+      if (s != GBR_OK || e0 != cudaSuccess) {
+        if (g0) cudaGraphDestroy(g0);
+        if (s != GBR_OK) return s;
+        BK(e0, "end capture");
+      }
+      b->graph = g0;
+      BK(cudaGraphInstantiate(&b->exec, b->graph, 0), "graph instantiate");
+      b->launches_per_step = launches;
+      b->dirty = false;
+      return GBR_OK;
+    }
     s = enqueue_step(b, launches);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(b->cap, &g);
@@ -796,6 +833,7 @@ void gbr_batch_destroy(gbr_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->cap) cudaStreamDestroy(b->cap);
+  for (cudaStream_t x : b->branch) cudaStreamDestroy(x);
   delete b;
 }
 
