@@ -146,16 +146,26 @@ class Workload:
         else:
             solver.rk_step(CFL)
 
-    def oracle_sample(self):
-        """A bounded sample of the workload for the CPU oracle: (case, nodes, q, inflow, sponge, cells, text)."""
+    def oracle_sample(self, small=False):
+        """A bounded sample of the workload for the CPU oracle: (case, nodes, q, inflow, sponge, cells, text).
+        small: the sample a single thread times (a 64^3 Taylor-Green vortex of the same recipe, or the
+        first 10 x-cells of the jet)."""
         from paper_2303_10785_b300 import inputs as I
 
         if self.kind == "tgv":
+            if small:
+                e = 64
+                n = (e,) * 3
+                case = dict(self.case, n=n)
+                nodes = I.nodes_tgv_3d(e, 0.1)
+                xc = I.centroids(nodes, n, (1, 1, 1))
+                q = I.prim_to_cons(I.tgv_prim(*xc, mach=0.1), self.case["gamma"])
+                return case, nodes, q, None, None, e ** 3, "the same Taylor-Green recipe on 64^3"
             return self.case, self.nodes, self.q, None, None, self.cells, f"the full {self.n[0]}^3 workload"
-        m = (40, 170, 170)
+        m = (10, 170, 170) if small else (40, 170, 170)
         case, nodes, q, inflow, sigma, qamb = I.jet_case(m, Lx=20.0 * m[0] / 480)
         return (case, nodes, q, I.jet_inflow_step(inflow, JET_SEED, 0), (sigma, qamb), m[0] * m[1] * m[2],
-                "the first 40 of the 480 x-cells of the jet grid (full 170 x 170 cross-section, inflow, sponge)")
+                f"the first {m[0]} of the 480 x-cells of the jet grid (full 170 x 170 cross-section, inflow, sponge)")
 
 
 class ClockSampler:
@@ -258,10 +268,10 @@ def _oracle_stage(orc, q):
     return q + 1e-3 * orc.rhs(q)
 
 
-def _oracle_for(wl):
+def _oracle_for(wl, small=False):
     import oracle as O
 
-    case, nodes, q, inflow, sponge, cells, text = wl.oracle_sample()
+    case, nodes, q, inflow, sponge, cells, text = wl.oracle_sample(small)
     orc = O.Oracle(case, nodes)
     if inflow is not None:
         orc.set_inflow(inflow)
@@ -281,9 +291,22 @@ def cpu_baseline(wl, seconds=10.0, max_samples=40):
         _oracle_stage(orc, q)
         samples += 1
     el = time.perf_counter() - t0
-    return {"value": cells * samples / el, "unit": METRIC, "cores": O.threads(), "kind": "oracle",
-            "sample": f"{samples} RK stage(s) (right-hand side + stage combination) of {text}, "
-                      f"geometry set-up excluded, {el:.1f} s"}
+    cores = O.threads()
+    out = {"value": cells * samples / el, "unit": METRIC, "cores": cores, "kind": "oracle",
+           "sample": f"{samples} RK stage(s) (right-hand side + stage combination) of {text}, "
+                     f"geometry set-up excluded, {el:.1f} s"}
+    # the same oracle on one thread, on a smaller sample of the workload (one stage)
+    O.set_threads(1)
+    try:
+        orc1, q1, cells1, text1 = _oracle_for(wl, small=True)
+        t0 = time.perf_counter()
+        _oracle_stage(orc1, q1)
+        el1 = time.perf_counter() - t0
+        out["value_1_thread"] = cells1 / el1
+        out["sample_1_thread"] = f"1 RK stage of {text1} on 1 thread, {el1:.1f} s"
+    finally:
+        O.set_threads(cores)
+    return out
 
 
 def run_reference(args, wl):

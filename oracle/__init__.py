@@ -301,3 +301,8 @@ def flop_counts(fn):
 
 def threads():
     return int(_lib().orc_threads())
+
+
+def set_threads(n):
+    """Threads the oracle's loops use from now on (timing at one thread and at all cores)."""
+    _lib().orc_set_threads(int(n))

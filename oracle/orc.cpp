@@ -1094,6 +1094,13 @@ int orc_threads(void) {
   return 1;
 #endif
 }
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
 
 int orc_create(const orc_params* prm, const double* nodes, const double* node_vel, orc_solver** out) {
   *out = nullptr;

@@ -95,6 +95,7 @@ void orc_count_get_phase(int phase, unsigned long long* add, unsigned long long*
                          unsigned long long* div, unsigned long long* sqrt_);
 int  orc_is_counting(void);
 int  orc_threads(void);
+void orc_set_threads(int n); /* OpenMP threads of the following calls (n > 0) */
 
 #ifdef __cplusplus
 }
