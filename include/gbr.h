@@ -173,7 +173,9 @@ gbr_status gbr_compute_dt(gbr_ctx* c, double cfl, double* dt_out);
 gbr_status gbr_rk_step(gbr_ctx* c, double cfl_or_neg_dt);
 
 /* Wait for the stream (polling, up to timeout_s seconds; <= 0: no limit), then
- * report sticky device errors (ENONFINITE) or ETIMEOUT. */
+ * report sticky device errors: ENONFINITE, or ETIMEOUT when a kernel's bounded
+ * wait for a tile copy into shared memory ran out (the MIG4 line solves).
+ * ETIMEOUT also when the stream did not drain before the deadline. */
 gbr_status gbr_sync(gbr_ctx* c, double timeout_s);
 
 /* Solution time and the last time step (waits for the stream). */
@@ -189,6 +191,16 @@ gbr_status gbr_get_field(gbr_ctx* c, int which, int dir, double* host_out);
  * context launched, then resets the tallies.  enable = 1 records events around
  * every face-flux launch from now on; 0 stops recording.  Out pointers may be NULL. */
 gbr_status gbr_profile(gbr_ctx* c, int enable, double* face_ms, long long* face_launches, long long* launches);
+
+/* Self-check of the kernels' bounded waits (no counterpart in the paper).  The
+ * MIG4 line solves wait for a TMA tile copy on an mbarrier with a bounded
+ * number of polls; when they run out the block sets a sticky device flag and
+ * leaves.  This call runs that timeout path on purpose: one block waits, for
+ * `polls` polls (1 .. 65536, each suspending for at most about 1 us), on an
+ * mbarrier that nothing completes.  Asynchronous; the next gbr_sync returns
+ * GBR_ETIMEOUT, and the context stays usable (the flag stays set).
+ * Errors: EINVAL for a null context or polls out of range. */
+gbr_status gbr_check_bounded_wait(gbr_ctx* c, int polls);
 
 /* Right-hand side with no device allocation anywhere (the paper has no
  * counterpart; this is a calling convention).  For callers that cannot call

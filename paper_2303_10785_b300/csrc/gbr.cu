@@ -9,6 +9,7 @@
 //   k_motion -> k_centroid -> k_coordd -> k_metrics -> k_face_metrics -> k_gcl
 // Time step: k_dt (block min with warp shuffles + atomicMin on the bits of a
 // positive double) -> k_dt_final.  dt and t stay on the device.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -146,51 +147,78 @@ __global__ void k_ig4(RhsArgsT<R> A, int e, Box lines, const R* table) {
 
 __global__ void k_ig4_factor(double* table, int n, int periodic) { ig4_factor(table, n, periodic != 0); }
 
+// one element from global into shared memory without a register round trip (cp.async)
+template <class R>
+__device__ __forceinline__ void cp_async_elem(R* dst, const R* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(__cvta_generic_to_global(src)),
+               "n"((int)sizeof(R))
+               : "memory");
+}
+
 // MIG4 with the lines staged in shared memory: a block of kIg4Lines threads takes kIg4Lines
 // neighbouring lines of one field (neighbours along axis a: x for y- and z-lines, y for
-// x-lines), loads their padded rows with coalesced reads (consecutive threads read consecutive
-// addresses: along the line for x-lines, across the lines otherwise), solves each line in its
-// own thread from shared memory (in place; rows of odd length, so the threads' accesses fall in
-// distinct banks), and stores the derivative rows back the same way.  The x-lines, which a thread
-// per line in global memory walks with a stride across the warp, become coalesced.
+// x-lines), loads their padded rows with coalesced asynchronous copies (consecutive threads read
+// consecutive addresses: along the line for x-lines, across the lines otherwise; all of a tile's
+// copies are in flight together, where loads through registers left the kernel waiting on a few
+// at a time), solves each line in its own thread from shared memory (in place; rows of odd
+// length, so the threads' accesses fall in distinct banks), and stores the derivative rows back
+// with coalesced writes.  The x-lines, which a thread per line in global memory walks with a
+// stride across the warp, become coalesced.  The y- and z-lines take the TMA form below where
+// its alignment rules hold.
 constexpr int kIg4Lines = 32;
+// The FP32 solves read the factor table from shared memory (a uniform load per row that no longer
+// waits on L1); the FP64 solves, bound by the FP64 pipe, keep it in global memory, where it costs
+// no shared memory and so no resident blocks.
+template <class R>
+constexpr bool kIg4StageTable = sizeof(R) == sizeof(float);
 
 template <int ND, class R>
-__global__ void __launch_bounds__(kIg4Lines) k_ig4s(RhsArgsT<R> A, int e, int a, Box lines, const R* table,
-                                                      int srow) {
+__global__ void __launch_bounds__(kIg4Lines) k_ig4s(RhsArgsT<R> A, int e, Box lines, const R* table,
+                                                      int srow, int tlen) {
   constexpr int NV = ND + 2;
   extern __shared__ __align__(16) unsigned char ig4_smem[];
   R* F = reinterpret_cast<R*>(ig4_smem);
   const Layout& L = A.L;
-  const int b = 3 - e - a;  // the third axis (extent 1 in 2D)
-  const int n = L.n[e], M = n + 2 * H;
-  const int na = lines.hi[a] - lines.lo[a];
+  // (e, a, b) is (x, y, z), (y, x, z) or (z, x, y): selects, no arrays indexed at run time
+  const bool ex = (e == 0), ey = (e == 1);
+  const int n = ex ? L.n[0] : (ey ? L.n[1] : L.n[2]), M = n + 2 * H;
+  const int loa = ex ? lines.lo[1] : lines.lo[0], na = (ex ? lines.hi[1] : lines.hi[0]) - loa;
+  const int lob = (ex || ey) ? lines.lo[2] : lines.lo[1];
   const int tiles = (na + kIg4Lines - 1) / kIg4Lines;
   const int ta = blockIdx.x % tiles, tb = blockIdx.x / tiles;
   const int nl = min(kIg4Lines, na - ta * kIg4Lines);
-  int c[3];
-  c[e] = -H;
-  c[a] = lines.lo[a] + ta * kIg4Lines;
-  c[b] = lines.lo[b] + tb;
-  const long long base = pidx(L, c[0], c[1], c[2]);  // padded cell -H of the tile's first line
-  const long long sa = L.ps[a], se = L.ps[e];
+  const int ca = loa + ta * kIg4Lines, cb = lob + tb;
+  // padded cell -H of the tile's first line
+  const long long base = ex ? pidx(L, -H, ca, cb) : (ey ? pidx(L, ca, -H, cb) : pidx(L, ca, cb, -H));
+  const long long sa = ex ? L.ps[1] : 1, se = ex ? 1 : (ey ? L.ps[1] : L.ps[2]);
   const int f = blockIdx.y;
   const long long PC = L.pcount;
   const R* src = (f < NV) ? A.prim + f * PC : A.temp;
-  R* dst = A.g1[e] + f * PC;
+  R* dst = (ex ? A.g1[0] : (ey ? A.g1[1] : A.g1[2])) + f * PC;
+  const bool per = ex ? L.per[0] != 0 : (ey ? L.per[1] != 0 : L.per[2] != 0);
   const int tid = threadIdx.x;
-  if (e == 0) {
-    for (int l = 0; l < nl; ++l)
-      for (int m = tid; m < M; m += kIg4Lines) F[l * srow + m] = src[base + l * sa + m];
-  } else if (tid < nl) {
-    for (int m = 0; m < M; ++m) F[tid * srow + m] = src[base + tid + m * se];
+  // FP32: the factor table staged beside the rows (every line reads the same entry at each row)
+  const R* T = table;
+  if constexpr (kIg4StageTable<R>) {
+    R* Ts = F + kIg4Lines * srow;
+    for (int i = tid; i < tlen; i += kIg4Lines) Ts[i] = table[i];
+    T = Ts;
   }
+  // asynchronous element copies (cp.async): every load of the tile is in flight at once
+  if (ex) {
+    for (int l = 0; l < nl; ++l)
+      for (int m = tid; m < M; m += kIg4Lines) cp_async_elem(F + l * srow + m, src + base + l * sa + m);
+  } else if (tid < nl) {
+    for (int m = 0; m < M; ++m) cp_async_elem(F + tid * srow + m, src + base + tid + m * se);
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
-  if (tid < nl) ig4_solve(table, n, L.per[e] != 0, F + tid * srow + H, F + tid * srow + H, 1);
+  if (tid < nl) ig4_solve(T, n, per, F + tid * srow + H, F + tid * srow + H, 1);
   __syncthreads();
   // rows written by the solve: the n cells and 3 images each side (periodic), the padded line (open)
-  const int m0 = L.per[e] ? H - 3 : 0, m1 = L.per[e] ? H + n + 3 : M;
-  if (e == 0) {
+  const int m0 = per ? H - 3 : 0, m1 = per ? H + n + 3 : M;
+  if (ex) {
     for (int l = 0; l < nl; ++l)
       for (int m = m0 + tid; m < m1; m += kIg4Lines) dst[base + l * sa + m] = F[l * srow + m];
   } else if (tid < nl) {
@@ -201,8 +229,127 @@ __global__ void __launch_bounds__(kIg4Lines) k_ig4s(RhsArgsT<R> A, int e, int a,
 // shared-memory row length (odd) and bytes of the staged MIG4 kernel for a line of n cells
 inline int ig4_srow(int n) { return (n + 2 * H) | 1; }
 template <class R>
-size_t ig4_smem_bytes(int n) { return sizeof(R) * (size_t)kIg4Lines * ig4_srow(n); }
+size_t ig4_smem_bytes(int n, bool per) {
+  return sizeof(R) * ((size_t)kIg4Lines * ig4_srow(n) + (kIg4StageTable<R> ? (size_t)ig4_table_len(n, per) : 0));
+}
 constexpr size_t kIg4SmemMax = 200 * 1024;
+
+// The same solves with the tile brought in by one TMA bulk copy (cp.async.bulk.tensor): for y- and
+// z-lines the 32 neighbouring lines are the box {32 along x, the padded line along e} of the field,
+// a single asynchronous copy into shared memory (laid out [point][line]: the per-thread solve reads
+// consecutive words, no bank conflicts) completed on an mbarrier.  Tiles start at a padded x that is
+// a multiple of 4, so the copy's innermost coordinate is 16-byte aligned; the host uses this form
+// only when the row pitch is a multiple of 16 bytes and the padded line fits one box (<= 256).  The
+// wait is bounded: if the copy has not completed after kTmaSpin try_wait polls (each suspending
+// for at most about kTmaWaitNs), the block flags it in err[1] (gbr_sync reports a timeout), waits
+// once more, boundedly, for the copy to land, and leaves without writing its derivatives.
+constexpr int kTmaSpin = 1 << 16;
+constexpr unsigned kTmaWaitNs = 1000;  // suspend-time hint of one try_wait, ns
+template <class R>
+size_t ig4t_smem_bytes(int n, bool per) {
+  return sizeof(R) * ((size_t)kIg4Lines * (n + 2 * H) + (kIg4StageTable<R> ? (size_t)ig4_table_len(n, per) : 0)) + 128;
+}
+
+// bounded wait on phase 0 of the block's mbarrier: true once the copy has landed
+__device__ __forceinline__ bool tma_wait(unsigned bar, int spins) {
+  unsigned done = 0;
+  for (int it = 0; it < spins && !done; ++it)
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0, %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(bar), "r"(kTmaWaitNs)
+        : "memory");
+  return done != 0;
+}
+
+// The timeout path of the bounded wait, run on purpose: one block waits on an mbarrier that
+// expects an arrival nobody makes (no copy is issued, so nothing is in flight when it leaves) and
+// flags err[1] as a line-solve block whose tile never landed would.
+__global__ void k_wait_check(int polls, int* err) {
+  __shared__ __align__(8) unsigned long long mbar;
+  const unsigned bar = (unsigned)__cvta_generic_to_shared(&mbar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (!tma_wait(bar, polls) && threadIdx.x == 0) atomicOr(err + 1, 1);
+}
+
+template <int ND, class R>
+__global__ void __launch_bounds__(kIg4Lines) k_ig4t(RhsArgsT<R> A, int e, Box lines, const R* table, int tlen, int x0p,
+                                                     const __grid_constant__ CUtensorMap tm_prim,
+                                                     const __grid_constant__ CUtensorMap tm_temp, int* err) {
+  constexpr int NV = ND + 2;
+  extern __shared__ __align__(16) unsigned char ig4t_smem[];
+  __shared__ __align__(8) unsigned long long mbar;
+  // the copy's destination on a 128-byte boundary (the allocation carries 128 bytes of slack)
+  const unsigned s0 = (unsigned)__cvta_generic_to_shared(ig4t_smem);
+  const unsigned pad = (128u - (s0 & 127u)) & 127u;
+  R* F = reinterpret_cast<R*>(ig4t_smem + pad);
+  const unsigned dst = s0 + pad;
+  const Layout& L = A.L;
+  const int n = (e == 1) ? L.n[1] : L.n[2], M = n + 2 * H;
+  // the third axis b (extent 1 in 2D): z for y-lines, y for z-lines (selects, no indexed arrays)
+  const bool ey = (e == 1);
+  const int lob = ey ? lines.lo[2] : lines.lo[1], hpb = ey ? L.hp[2] : L.hp[1];
+  const int tiles = (lines.hi[0] + L.hp[0] - x0p + kIg4Lines - 1) / kIg4Lines;
+  const int tx = blockIdx.x % tiles, tb = blockIdx.x / tiles;
+  const int xs = x0p + tx * kIg4Lines;  // padded x of the tile's first line (a multiple of 4)
+  const int cb = lob + tb + hpb;        // padded coordinate of the tile along b
+  const int f = blockIdx.y;
+  const int tid = threadIdx.x;
+  const unsigned bar = (unsigned)__cvta_generic_to_shared(&mbar);
+  const unsigned bytes = (unsigned)(sizeof(R) * kIg4Lines * M);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    const int c1 = ey ? 0 : cb, c2 = ey ? cb : 0;  // the line starts at padded 0 along e
+    if (f < NV)
+      asm volatile(
+          "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+          "[%6];" ::"r"(dst),
+          "l"(reinterpret_cast<unsigned long long>(&tm_prim)), "r"(xs), "r"(c1), "r"(c2), "r"(f), "r"(bar)
+          : "memory");
+    else
+      asm volatile(
+          "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+          "[%5];" ::"r"(dst),
+          "l"(reinterpret_cast<unsigned long long>(&tm_temp)), "r"(xs), "r"(c1), "r"(c2), "r"(bar)
+          : "memory");
+  }
+  const R* T = table;
+  if constexpr (kIg4StageTable<R>) {  // FP32: the factor table, staged while the tile is in flight
+    R* Ts = F + kIg4Lines * M;
+    for (int i = tid; i < tlen; i += kIg4Lines) Ts[i] = table[i];
+    T = Ts;
+    __syncwarp();
+  }
+  if (!tma_wait(bar, kTmaSpin)) {
+    // the copy did not land in time: flag it, give the copy a last bounded chance to finish before
+    // the block's shared memory is released, and leave the derivatives of this tile unwritten
+    if (tid == 0) atomicOr(err + 1, 1);
+    tma_wait(bar, kTmaSpin);
+    return;
+  }
+  // this thread's line: cell x = xs - hp0 + tid, solved and stored when it lies in the lines box
+  const int cx = xs - L.hp[0] + tid;
+  if (cx < lines.lo[0] || cx >= lines.hi[0]) return;
+  R* col = F + tid + H * kIg4Lines;
+  const bool per = ey ? L.per[1] != 0 : L.per[2] != 0;
+  ig4_solve(T, n, per, col, col, (long long)kIg4Lines);
+  const int cl = lob + tb;
+  const long long base = ey ? pidx(L, cx, -H, cl) : pidx(L, cx, cl, -H);  // padded cell -H of this thread's line
+  const long long se = ey ? L.ps[1] : L.ps[2];
+  R* out = (ey ? A.g1[1] : A.g1[2]) + f * L.pcount;
+  // rows written by the solve: the n cells and 3 images each side (periodic), the padded line (open)
+  const int m0 = per ? H - 3 : 0, m1 = per ? H + n + 3 : M;
+  for (int m = m0; m < m1; ++m) out[base + m * se] = F[m * kIg4Lines + tid];
+}
 
 template <int ND, class R = double>
 __global__ void k_grad2(RhsArgsT<R> A, Box b0, Box b1, Box b2) {
@@ -522,6 +669,8 @@ struct gbr_ctx {
   double *sigma, *inflow, *scal;
   double* ig4[3];  // MIG4 line-solve factors per direction (or null)
   float* ig4f[3];  // mixed path: their FP32 copies (no conversions in the FP32 line solves)
+  CUtensorMap ig4_tm[3][2];  // MIG4 y/z lines: TMA maps of the primitives and the temperature
+  bool ig4_tma[3];           // the TMA form is used for this direction
   int* err;
   bool visc, mov, have_sponge, have_motion, metrics_ready;
   double qamb[5];
@@ -881,8 +1030,22 @@ gbr_status run_rhs_nd(gbr_ctx* c, const double* qs, const double* q0, double* ou
       const R* table;
       if constexpr (sizeof(R) == sizeof(float)) table = c->ig4f[e];
       else table = c->ig4[e];
-      const size_t smem = ig4_smem_bytes<R>(L.n[e]);
-      if (smem <= kIg4SmemMax) {
+      const bool per = L.per[e] != 0;
+      const int tlen = (int)ig4_table_len(L.n[e], per);
+      const size_t smem = ig4_smem_bytes<R>(L.n[e], per);
+      if (c->ig4_tma[e]) {
+        static bool attr_t = false;
+        if (!attr_t) {
+          cudaFuncSetAttribute(k_ig4t<ND, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIg4SmemMax);
+          attr_t = true;
+        }
+        const int bx = (e == 1) ? 2 : 1;
+        const int x0p = (lines.lo[0] + L.hp[0]) & ~3;
+        const int tiles = (lines.hi[0] + L.hp[0] - x0p + kIg4Lines - 1) / kIg4Lines;
+        const int nb = lines.hi[bx] - lines.lo[bx];
+        k_ig4t<ND, R><<<dim3((unsigned)(tiles * nb), nf), kIg4Lines, ig4t_smem_bytes<R>(L.n[e], per), st>>>(
+            A, e, lines, table, tlen, x0p, c->ig4_tm[e][0], c->ig4_tm[e][1], c->err);
+      } else if (smem <= kIg4SmemMax) {
         static bool attr_set = false;  // one opt-in per instantiation (above the 48 KB default)
         if (!attr_set) {
           cudaFuncSetAttribute(k_ig4s<ND, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIg4SmemMax);
@@ -891,7 +1054,7 @@ gbr_status run_rhs_nd(gbr_ctx* c, const double* qs, const double* q0, double* ou
         const int a = (e == 0) ? 1 : 0, bx = 3 - e - a;
         const int na = lines.hi[a] - lines.lo[a], nb = lines.hi[bx] - lines.lo[bx];
         const unsigned tiles = (unsigned)((na + kIg4Lines - 1) / kIg4Lines) * (unsigned)nb;
-        k_ig4s<ND, R><<<dim3(tiles, nf), kIg4Lines, smem, st>>>(A, e, a, lines, table, ig4_srow(L.n[e]));
+        k_ig4s<ND, R><<<dim3(tiles, nf), kIg4Lines, smem, st>>>(A, e, lines, table, ig4_srow(L.n[e]), tlen);
       } else {
         k_ig4<ND, R><<<dim3(grid_of(lines, 128), nf), 128, 0, st>>>(A, e, lines, table);
       }
@@ -1039,6 +1202,56 @@ void carve(gbr_ctx* c) {
   }
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against the driver library)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+
+// TMA maps of the MIG4 y- and z-line tiles (k_ig4t): the primitives as a 4D tensor {px, py, pz, nv}
+// and the temperature as a 3D one, each with the box {32 along x, the padded line along e}.  A
+// direction keeps the staged plain-load kernel when a TMA rule does not hold: the row pitch and
+// the base addresses must be multiples of 16 bytes, a box extent at most 256.
+void ig4_encode_maps(gbr_ctx* c) {
+  const Layout& L = c->L;
+  const size_t es = elem_r(&c->p);
+  EncodeTiledFn enc = encode_tiled();
+  for (int e = 0; e < 3; ++e) c->ig4_tma[e] = false;
+  const bool aligned = ((uintptr_t)c->prim % 16 == 0) && (!c->visc || (uintptr_t)c->temp % 16 == 0) &&
+                       ((size_t)L.pn[0] * es) % 16 == 0;
+  if (!enc || !aligned) return;
+  const CUtensorMapDataType dt = (es == 4) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  const cuuint64_t dims[4] = {(cuuint64_t)L.pn[0], (cuuint64_t)L.pn[1], (cuuint64_t)L.pn[2], (cuuint64_t)L.nv};
+  const cuuint64_t strides[3] = {(cuuint64_t)(L.ps[1] * es), (cuuint64_t)(L.ps[2] * es), (cuuint64_t)(L.pcount * es)};
+  const cuuint32_t ones[4] = {1, 1, 1, 1};
+  for (int e = 1; e < L.nd; ++e) {
+    const int M = L.n[e] + 2 * H;
+    if (M > 256) continue;
+    cuuint32_t box[4] = {(cuuint32_t)kIg4Lines, 1, 1, 1};
+    box[e] = (cuuint32_t)M;
+    bool ok = enc(&c->ig4_tm[e][0], dt, 4, c->prim, dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    if (ok && c->visc)
+      ok = enc(&c->ig4_tm[e][1], dt, 3, c->temp, dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    else if (ok)
+      c->ig4_tm[e][1] = c->ig4_tm[e][0];  // never read (no temperature field without viscosity)
+    c->ig4_tma[e] = ok;
+  }
+}
+
 Phys phys_of(const gbr_params* p) {
   Phys ph;
   ph.gamma = p->gamma;
@@ -1111,6 +1324,7 @@ gbr_status gbr_create(const gbr_params* p, const double* nodes, const double* no
     return s;
   }
   if (p->gradient_scheme == GBR_GRAD_MIG4) {
+    ig4_encode_maps(c);
     for (int d = 0; d < L.nd; ++d) {
       k_ig4_factor<<<1, 1, 0, c->stream>>>(c->ig4[d], L.n[d], L.per[d]);
       if (c->ig4f[d]) {
@@ -1292,9 +1506,10 @@ gbr_status gbr_sync(gbr_ctx* c, double timeout_s) {
     if (timeout_s > 0.0 && el > timeout_s) return fail(c, GBR_ETIMEOUT, "stream did not drain before the deadline");
     std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
-  int err = 0;
-  CK(cudaMemcpy(&err, c->err, sizeof(int), cudaMemcpyDeviceToHost), "read error flag");
-  if (err) return fail(c, GBR_ENONFINITE, "non-finite state or non-positive density on the device");
+  int err[2] = {0, 0};
+  CK(cudaMemcpy(err, c->err, sizeof(err), cudaMemcpyDeviceToHost), "read error flags");
+  if (err[0]) return fail(c, GBR_ENONFINITE, "non-finite state or non-positive density on the device");
+  if (err[1]) return fail(c, GBR_ETIMEOUT, "a tile copy into shared memory did not complete in time");
   return GBR_OK;
 }
 
@@ -1394,6 +1609,14 @@ gbr_status gbr_profile(gbr_ctx* c, int enable, double* face_ms, long long* face_
   c->ev_used = 0;
   c->launches = 0;
   c->prof = enable != 0;
+  return GBR_OK;
+}
+
+gbr_status gbr_check_bounded_wait(gbr_ctx* c, int polls) {
+  if (!c) return fail(nullptr, GBR_EINVAL, "null context");
+  if (polls < 1 || polls > kTmaSpin) return fail(c, GBR_EINVAL, "polls out of range");
+  k_wait_check<<<1, kIg4Lines, 0, c->stream>>>(polls, c->err);
+  CKL("k_wait_check");
   return GBR_OK;
 }
 

@@ -91,6 +91,7 @@ def lib():
     L.gbr_get_time.argtypes = [_vp, _P, _P]
     L.gbr_get_field.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _P]
     L.gbr_profile.argtypes = [_vp, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    L.gbr_check_bounded_wait.argtypes = [_vp, ctypes.c_int]
     L.gbr_profile.restype = ctypes.c_int
     L.gbr_rhs_static.argtypes = [ctypes.POINTER(gbr_params), _P, _P, _vp, _vp, _vp, ctypes.c_char_p, ctypes.c_size_t]
     L.gbr_rhs_static.restype = ctypes.c_int
@@ -134,7 +135,8 @@ def exported_symbols():
     """Names declared in include/gbr.h that the library must export."""
     return ["gbr_workspace_bytes", "gbr_create", "gbr_compute_metrics", "gbr_move_mesh", "gbr_set_motion",
             "gbr_set_state", "gbr_get_state", "gbr_set_inflow", "gbr_set_sponge", "gbr_rhs", "gbr_compute_dt",
-            "gbr_rk_step", "gbr_sync", "gbr_get_time", "gbr_get_field", "gbr_profile", "gbr_rhs_static",
+            "gbr_rk_step", "gbr_sync", "gbr_get_time", "gbr_get_field", "gbr_profile", "gbr_check_bounded_wait",
+            "gbr_rhs_static",
             "gbr_batch_workspace_bytes", "gbr_batch_create", "gbr_batch_set_options", "gbr_batch_add",
             "gbr_batch_remove", "gbr_batch_step", "gbr_batch_sync", "gbr_batch_info", "gbr_batch_tuning",
             "gbr_batch_last_error", "gbr_batch_destroy", "gbr_arena_create", "gbr_arena_alloc", "gbr_arena_free",
@@ -287,6 +289,11 @@ class Solver:
 
     def sync(self, timeout=60.0):
         self._check(self.L.gbr_sync(self.h, float(timeout)))
+
+    def check_bounded_wait(self, polls=64):
+        """Run the kernels' bounded-wait timeout path on purpose (a wait nothing completes): the
+        next sync raises GbrError with status GBR_ETIMEOUT."""
+        self._check(self.L.gbr_check_bounded_wait(self.h, int(polls)))
 
     def time(self):
         t = ctypes.c_double()

@@ -76,8 +76,11 @@ def test_mig4_vortex_steps_match_oracle():
     s.close()
 
 
-def test_mig4_mixed_precision_rhs():
-    case, nodes, vel, q = CASES["3d_tgv"]()
+@pytest.mark.parametrize("name", ["3d_tgv", "3d_inviscid_ragged", "2d_vortex"])
+def test_mig4_mixed_precision_rhs(name):
+    # 3d_tgv and 2d_vortex: y/z lines by TMA tiles (rows of 52 and 76 floats, multiples of 16
+    # bytes); 3d_inviscid_ragged: rows of 49 floats, the staged plain-copy kernel
+    case, nodes, vel, q = CASES[name]()
     orc = O.Oracle(mig4(case), nodes, vel)
     s = gbr.Solver(mig4(case, precision="mixed"), nodes, vel)
     s.set_state(q)
@@ -114,4 +117,33 @@ def test_mig4_long_lines_take_the_per_line_kernel(precision):
     s = gbr.Solver(case, nodes)
     s.set_state(q)
     assert rhs_err(orc, s, q) < (1e-12 if precision == "fp64" else 2e-6)
+    s.close()
+
+
+def test_mig4_mixed_open_axes_jet_rhs():
+    case, nodes, vel, q, extra = case_jet()
+    orc = O.Oracle(mig4(case), nodes, vel)
+    s = gbr.Solver(mig4(case, precision="mixed"), nodes, vel)
+    for obj in (orc, s):
+        obj.set_inflow(extra["inflow"])
+        obj.set_sponge(extra["sigma"], extra["qamb"])
+    s.set_state(q)
+    assert rhs_err(orc, s, q) < 2e-5
+    s.close()
+
+
+def test_bounded_wait_timeout_is_reported_and_context_stays_usable():
+    # the line solves' wait for a tile copy is bounded: when it runs out the block flags a sticky
+    # error and leaves; this runs that path on purpose (a wait that nothing completes)
+    case, nodes, vel, q = CASES["3d_tgv"]()
+    s = gbr.Solver(mig4(case), nodes, vel)
+    s.set_state(q)
+    with pytest.raises(gbr.GbrError):
+        s.check_bounded_wait(0)
+    s.check_bounded_wait(64)
+    with pytest.raises(gbr.GbrError) as err:
+        s.sync()
+    assert err.value.status == gbr.GBR_ETIMEOUT
+    orc = O.Oracle(mig4(case), nodes, vel)
+    assert rhs_err(orc, s, q) < 1e-12  # the context still computes
     s.close()
