@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kIg4Lines) k_ig4s(RhsArgsT<R> A, int e, Box li
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
-  if (tid < nl) ig4_solve(T, n, per, F + tid * srow + H, F + tid * srow + H, 1);
+  if (tid < nl) ig4_solve(T, n, per, F + tid * srow + H, F + tid * srow + H, 1, F + tid * srow, 1);
   __syncthreads();
   // rows written by the solve: the n cells and 3 images each side (periodic), the padded line (open)
   const int m0 = per ? H - 3 : 0, m1 = per ? H + n + 3 : M;
@@ -339,16 +339,16 @@ __global__ void __launch_bounds__(kIg4Lines) k_ig4t(RhsArgsT<R> A, int e, Box li
   // this thread's line: cell x = xs - hp0 + tid, solved and stored when it lies in the lines box
   const int cx = xs - L.hp[0] + tid;
   if (cx < lines.lo[0] || cx >= lines.hi[0]) return;
-  R* col = F + tid + H * kIg4Lines;
   const bool per = ey ? L.per[1] != 0 : L.per[2] != 0;
-  ig4_solve(T, n, per, col, col, (long long)kIg4Lines);
   const int cl = lob + tb;
   const long long base = ey ? pidx(L, cx, -H, cl) : pidx(L, cx, cl, -H);  // padded cell -H of this thread's line
   const long long se = ey ? L.ps[1] : L.ps[2];
-  R* out = (ey ? A.g1[1] : A.g1[2]) + f * L.pcount;
-  // rows written by the solve: the n cells and 3 images each side (periodic), the padded line (open)
-  const int m0 = per ? H - 3 : 0, m1 = per ? H + n + 3 : M;
-  for (int m = m0; m < m1; ++m) out[base + m * se] = F[m * kIg4Lines + tid];
+  R* out = (ey ? A.g1[1] : A.g1[2]) + f * L.pcount + base;
+  // forward sweep in the shared column, backward sweep stored straight to the derivative (the
+  // threads of the warp write neighbouring x: coalesced): the n cells and 3 images each side
+  // (periodic), the padded line (open)
+  R* col = F + tid + H * kIg4Lines;
+  ig4_solve(T, n, per, col, col, kIg4Lines, out, se);
 }
 
 template <int ND, class R = double>

@@ -822,12 +822,12 @@ GBR_HD void body_grad2(const RhsArgsT<R>& A, int e, int i, int j, int k) {
 // correction vector z solved once); open axis: the padded line of n + 2H cells
 // whose three end points at each side take explicit rows (second-order
 // one-sided, fourth-order biased, fourth-order central).
-// Table layout per direction (doubles): periodic: cp[n], inv[n], z[n], kinv;
+// Table layout per direction (doubles): periodic: cp[n], inv[n], z[n], kinv, P[n];
 // open: cp[m], inv[m] with m = n + 2H.
 // ---------------------------------------------------------------------------
 constexpr double kIg4Alpha = 5.0 / 14.0;
 
-inline long long ig4_table_len(int n, bool periodic) { return periodic ? 3LL * n + 1 : 2LL * (n + 2 * H); }
+inline long long ig4_table_len(int n, bool periodic) { return periodic ? 4LL * n + 1 : 2LL * (n + 2 * H); }
 
 GBR_HD void ig4_factor(double* t, int n, bool periodic) {
   const double al = kIg4Alpha;
@@ -852,6 +852,11 @@ GBR_HD void ig4_factor(double* t, int n, bool periodic) {
     for (int i = n - 2; i >= 0; --i) z[i] -= cp[i] * z[i + 1];
     // x = y - (y_0 - alpha y_{n-1}) / (1 + z_0 - alpha z_{n-1}) z   (v = (1, 0, .., 0, alpha / gamma))
     t[3 * n] = 1.0 / (1.0 + z[0] - al * z[n - 1]);
+    // weights of y_0 in the forward results: y_0 = sum_k P_k g_k, P_k = prod_{j<k} (-cp_j), so that
+    // y_0 (and the correction factor) is known before the backward sweep (ig4_solve)
+    double* P = t + 3 * n + 1;
+    P[0] = 1.0;
+    for (int i = 1; i < n; ++i) P[i] = -cp[i - 1] * P[i - 1];
   } else {
     const int m = n + 2 * H;
     double* cp = t;
@@ -879,51 +884,76 @@ GBR_HD R ig4_rhs_w(R fm2, R fm1, R fp1, R fp2) {
   return R((2.0 + kIg4Alpha) / 3.0) * (fp1 - fm1) + R((4.0 * kIg4Alpha - 1.0) / 12.0) * (fp2 - fm2);
 }
 
-// One IG4 line: f0 and g0 point at cell 0 of the line, s is the distance between its cells.
-// Every value of f is read once, into a register window around the row being formed, and read
-// before g is written at or below it, so g may overwrite f in place (the staged kernel's
-// shared-memory row).  Periodic: the n cells with the images of f at -2, -1, n, n + 1; g at
-// 0 .. n-1 and its images at -3 .. -1 and n .. n+2.  Open: the padded line -H .. n+H-1.
+// One IG4 line.  f: cell 0 of the line, w: cell 0 of a work column (may be f itself: in place),
+// both with distance S between cells; out: cell -H of the destination, distance so.  The forward
+// sweep reads each f into a register window before w is written at or below it, and also sums
+// y_0 = sum_k P_k g_k (periodic), so the Sherman-Morrison factor is known before the backward
+// sweep, which then forms each final value once and stores it (and the periodic images) at
+// out + (c + H) so for cell c; out may alias w (each row is read before it is overwritten).
+// In place on a periodic line (out aliasing w) the correction pass reads row m before it
+// writes it and writes images only at rows it has read or never reads.
+// Periodic: the n cells with the images of f at -2, -1, n, n + 1; the derivative at 0 .. n-1 and
+// its images at -3 .. -1 and n .. n+2.  Open: the padded line -H .. n+H-1.  y_0 is the backward
+// sweep's own end value summed in another order.
+// FP32 sums y_0 in the forward sweep (one pass less over the column); FP64, whose line solves are
+// bound by the FP64 pipe, does not spend the extra multiply-add per cell and forms y_0 by the
+// backward sweep in the work column before the correction.
 template <class R>
-GBR_HD void ig4_solve(const R* t, int n, bool periodic, const R* f0, R* g0, long long s) {
+constexpr bool kIg4SumY0 = sizeof(R) == sizeof(float);
+
+template <class R>
+GBR_HD void ig4_solve(const R* t, int n, bool periodic, const R* f, R* w, long long S, R* out, long long so) {
   const R al = R(kIg4Alpha);
   if (periodic) {
     const R* cp = t;
     const R* inv = t + n;
     const R* z = t + 2 * n;
-    // forward sweep (rp kept in g), window f_{m-2} .. f_{m+2}
-    R w0 = f0[-2 * s], w1 = f0[-s], w2 = f0[0], w3 = f0[s], w4 = f0[2 * s];
-    R prev = R(0);
+    const R* P = t + 3 * n + 1;
+    R w0 = f[-2 * S], w1 = f[-S], w2 = f[0], w3 = f[S], w4 = f[2 * S];
+    R prev = R(0), y0 = R(0);
     for (int m = 0; m < n; ++m) {
       const R r = ig4_rhs_w(w0, w1, w3, w4);
-      prev = (m == 0) ? r * R(inv[0]) : (r - al * prev) * R(inv[m]);
+      prev = (m == 0) ? r * inv[0] : (r - al * prev) * inv[m];
+      if constexpr (kIg4SumY0<R>) y0 = y0 + P[m] * prev;
       w0 = w1;
       w1 = w2;
       w2 = w3;
       w3 = w4;
-      if (m + 1 < n) w4 = f0[(m + 3) * s];
-      g0[m * s] = prev;
+      if (m + 1 < n) w4 = f[(m + 3) * S];
+      w[m * S] = prev;
     }
-    // backward sweep (y in g)
     R y = prev;
-    for (int m = n - 2; m >= 0; --m) {
-      y = g0[m * s] - R(cp[m]) * y;
-      g0[m * s] = y;
-    }
-    const R fac = (y - al * g0[(n - 1) * s]) * R(t[3 * n]);
-    for (int m = 0; m < n; ++m) g0[m * s] = g0[m * s] - fac * R(z[m]);
-    for (int m = 1; m <= 3; ++m) {  // periodic images of the derivative the gradient box needs
-      g0[-m * s] = g0[(n - m) * s];
-      g0[(n - 1 + m) * s] = g0[(m - 1) * s];
+    if constexpr (kIg4SumY0<R>) {
+      const R fac = (y0 - al * prev) * t[3 * n];
+      for (int m = n - 1; m >= 0; --m) {
+        if (m < n - 1) y = w[m * S] - cp[m] * y;
+        const R x = y - fac * z[m];
+        out[(m + H) * so] = x;
+        if (m >= n - 3) out[(m - n + H) * so] = x;  // images -3 .. -1
+        if (m <= 2) out[(m + n + H) * so] = x;      // images n .. n + 2
+      }
+    } else {
+      // backward sweep and correction in the work column, then the rows out (when out is not w)
+      for (int m = n - 2; m >= 0; --m) {
+        y = w[m * S] - cp[m] * y;
+        w[m * S] = y;
+      }
+      const R fac = (y - al * w[(n - 1) * S]) * t[3 * n];
+      for (int m = 0; m < n; ++m) w[m * S] = w[m * S] - fac * z[m];
+      for (int m = 1; m <= 3; ++m) {  // periodic images of the derivative the gradient box needs
+        w[-m * S] = w[(n - m) * S];
+        w[(n - 1 + m) * S] = w[(m - 1) * S];
+      }
+      if (out != w - H * S)
+        for (int c = -3; c < n + 3; ++c) out[(c + H) * so] = w[c * S];
     }
   } else {
     const int M = n + 2 * H;
     const R* cp = t;
     const R* inv = t + M;
-    const R* f = f0 - H * s;  // padded cell -H: row 0
-    R* g = g0 - H * s;
-    // window f_{m-3} .. f_{m+3} of row m (entries outside the line are never used)
-    R w0 = R(0), w1 = R(0), w2 = R(0), w3 = f[0], w4 = f[s], w5 = f[2 * s], w6 = f[3 * s];
+    const R* f0 = f - H * S;  // padded cell -H: row 0
+    R* w0r = w - H * S;
+    R w0 = R(0), w1 = R(0), w2 = R(0), w3 = f0[0], w4 = f0[S], w5 = f0[2 * S], w6 = f0[3 * S];
     R prev = R(0);
     for (int m = 0; m < M; ++m) {
       R r;
@@ -934,20 +964,21 @@ GBR_HD void ig4_solve(const R* t, int n, bool periodic, const R* f0, R* g0, long
       else if (m == M - 1) r = R(1.5) * w3 - R(2) * w2 + R(0.5) * w1;
       else r = ig4_rhs_w(w1, w2, w4, w5);
       const bool expl = m < 3 || m >= M - 3;
-      prev = (m == 0 || expl) ? r * R(inv[m]) : (r - al * prev) * R(inv[m]);
+      prev = (m == 0 || expl) ? r * inv[m] : (r - al * prev) * inv[m];
       w0 = w1;
       w1 = w2;
       w2 = w3;
       w3 = w4;
       w4 = w5;
       w5 = w6;
-      if (m + 4 < M) w6 = f[(m + 4) * s];
-      g[m * s] = prev;
+      if (m + 4 < M) w6 = f0[(m + 4) * S];
+      w0r[m * S] = prev;
     }
     R y = prev;
+    out[(M - 1) * so] = y;
     for (int m = M - 2; m >= 0; --m) {
-      y = g[m * s] - R(cp[m]) * y;
-      g[m * s] = y;
+      y = w0r[m * S] - cp[m] * y;
+      out[m * so] = y;
     }
   }
 }
@@ -958,7 +989,8 @@ GBR_HD void ig4_line(const Layout& L, const R* t, int e, const R* f, R* g, int i
   int c0[3] = {i, j, k};
   c0[e] = 0;
   const long long base = pidx(L, c0[0], c0[1], c0[2]);  // cell 0 of the line
-  ig4_solve(t, L.n[e], L.per[e] != 0, f + base, g + base, L.ps[e]);
+  const long long s = L.ps[e];
+  ig4_solve(t, L.n[e], L.per[e] != 0, f + base, g + base, s, g + base - H * s, s);
 }
 
 // Both derivatives along e in one pass over the first-derivative box: f' at the cell (stored),
