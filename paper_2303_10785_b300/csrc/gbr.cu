@@ -134,6 +134,141 @@ __global__ void k_grad1(RhsArgsT<R> A, Box b0, Box b1, Box b2) {
   body_grad1<ND>(A, e, i, j, k);
 }
 
+// E6 first derivatives of one field in all three directions, 3D (Eq. 11), by a block that owns a
+// 32 x 8 tile of (x, y) columns and marches along z through a chunk of planes.  Each column keeps
+// its seven values z-3 .. z+3 in registers (the z-derivative, one new load per plane); each plane
+// goes to shared memory with a ring of 3 cells around the tile (the x- and y-derivatives), written
+// from the columns' centre values plus the ring loads, double-buffered so that one barrier per
+// plane suffices.  Every value is read from global memory about once per plane (the ring and the
+// chunk ends aside) instead of once per stencil point, and the three derivatives are stored with
+// consecutive threads on consecutive x.  Outputs and arithmetic are those of body_grad1 on the
+// three first-derivative boxes (each cell of a box gets exactly its stencil_E6 value).  The
+// per-cell kernel was issue-bound on index arithmetic (53 instructions per derivative, 62 % of
+// the issue slots busy); running pointers and one ring load per thread and plane take the 128^3
+// mixed step from 1.929 to 1.874 ms.
+constexpr int kG1TX = 32, kG1TY = 8, kG1Ring = 3;
+constexpr int kG1SX = kG1TX + 2 * kG1Ring, kG1SY = kG1TY + 2 * kG1Ring;
+constexpr int kG1RingCount = kG1SX * kG1SY - kG1TX * kG1TY;  // 276
+
+// (row, column) in the plane tile of the r-th ring cell: the top rows, the sides of the middle
+// rows, the bottom rows
+__device__ __forceinline__ void g1_ring_pos(int r, int& sy, int& sx) {
+  constexpr int top = kG1Ring * kG1SX, side = 2 * kG1Ring;
+  if (r < top) {
+    sy = r / kG1SX;
+    sx = r % kG1SX;
+  } else if (r < top + kG1TY * side) {
+    const int q = r - top;
+    sy = kG1Ring + q / side;
+    const int c = q % side;
+    sx = c < kG1Ring ? c : kG1TX + c;
+  } else {
+    const int q = r - top - kG1TY * side;
+    sy = kG1Ring + kG1TY + q / kG1SX;
+    sx = q % kG1SX;
+  }
+}
+
+constexpr int kG1Waves = 3;
+
+// streaming multiprocessors of the current device (queried once)
+inline int device_sms() {
+  static int v = 0;
+  if (v < 1) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        v < 1)
+      v = 148;
+  }
+  return v;
+}
+
+template <class R>
+__global__ void __launch_bounds__(kG1TX * kG1TY) k_grad1t(RhsArgsT<R> A, Box U, Box bx, Box by, Box bz, int tiles_x,
+                                                          int tiles_y, int zchunk) {
+  constexpr int NV = 5;
+  constexpr int PL = kG1SX * kG1SY;  // one plane tile
+  __shared__ R plane[2 * PL];
+  const Layout& L = A.L;
+  const int tid = threadIdx.x, tx = tid % kG1TX, ty = tid / kG1TX;
+  const int t = blockIdx.x;
+  const int tlx = t % tiles_x, tly = (t / tiles_x) % tiles_y, chunk = t / (tiles_x * tiles_y);
+  const int x0 = U.lo[0] + tlx * kG1TX, y0 = U.lo[1] + tly * kG1TY;  // cell of tile point (0, 0)
+  const int x = x0 + tx, y = y0 + ty;
+  const int zs = U.lo[2] + chunk * zchunk, ze = min(zs + zchunk, U.hi[2]);
+  const int f = blockIdx.y;
+  const long long PC = L.pcount, sz = L.ps[2];
+  const R* src = (f < NV) ? A.prim + f * PC : A.temp;
+  // A value is loaded only where its (x, y) lies in the padded box (outside it no output needs
+  // it).  Along z no check is needed: the planes read, zs - 3 .. ze + 2 with zs >= -3 and
+  // ze <= n_z + 3, lie in the padded range -H .. n_z + H - 1.
+  auto inside = [&](int cx, int cy) {
+    return cx >= -L.hp[0] && cx < L.n[0] + L.hp[0] && cy >= -L.hp[1] && cy < L.n[1] + L.hp[1];
+  };
+  const bool col = inside(x, y);
+  const long long pcol = col ? pidx(L, x, y, 0) : 0;  // padded index of (x, y, 0)
+  // the ring cells this thread loads (at most two): shared-memory slot and running source pointer
+  int r_off[2];
+  bool r_ok[2];
+  const R* rq[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int r = tid + h * kG1TX * kG1TY;
+    int sy = 0, sx = 0;
+    r_ok[h] = false;
+    if (r < kG1RingCount) {
+      g1_ring_pos(r, sy, sx);
+      r_ok[h] = inside(x0 + sx - kG1Ring, y0 + sy - kG1Ring);
+    }
+    r_off[h] = (r < kG1RingCount) ? sy * kG1SX + sx : -1;
+    rq[h] = src + (r_ok[h] ? pidx(L, x0 + sx - kG1Ring, y0 + sy - kG1Ring, 0) : 0);
+  }
+  const bool ox = x >= bx.lo[0] && x < bx.hi[0] && y >= bx.lo[1] && y < bx.hi[1];
+  const bool oy = x >= by.lo[0] && x < by.hi[0] && y >= by.lo[1] && y < by.hi[1];
+  const bool oz = x >= bz.lo[0] && x < bz.hi[0] && y >= bz.lo[1] && y < bz.hi[1];
+  const int e = (ty + kG1Ring) * kG1SX + tx + kG1Ring;  // this column's cell in the plane tile
+  // loads run ahead of their use: the column's z+3 and the ring's plane z+2 are requested while
+  // plane z is formed, so no step waits on a load issued in the same step
+  const R* cq = src + pcol + (long long)(zs - 3) * sz;
+  R w[7], rv[2][3];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) w[k] = col ? cq[k * sz] : R(0);
+  cq += 6 * sz;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    rq[h] += (long long)zs * sz;
+    rv[h][0] = r_ok[h] ? rq[h][0] : R(0);
+    rv[h][1] = r_ok[h] ? rq[h][sz] : R(0);
+    rq[h] += 2 * sz;
+  }
+  long long p = pcol + (long long)zs * sz;
+  for (int z = zs; z < ze; ++z, p += sz) {
+    R* pl = plane + ((z - zs) & 1) * PL;
+    w[6] = col ? *cq : R(0);
+    cq += sz;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      rv[h][2] = r_ok[h] ? *rq[h] : R(0);
+      rq[h] += sz;
+    }
+    pl[e] = w[3];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      if (r_off[h] >= 0) pl[r_off[h]] = rv[h][0];
+    __syncthreads();
+    if (ox && z >= bx.lo[2] && z < bx.hi[2]) A.g1[0][f * PC + p] = stencil_E6(pl + e, 0, 1);
+    if (oy && z >= by.lo[2] && z < by.hi[2]) A.g1[1][f * PC + p] = stencil_E6(pl + e, 0, kG1SX);
+    if (oz && z >= bz.lo[2] && z < bz.hi[2]) A.g1[2][f * PC + p] = stencil_E6(w, 3, 1);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) w[k] = w[k + 1];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      rv[h][0] = rv[h][1];
+      rv[h][1] = rv[h][2];
+    }
+  }
+}
+
 // MIG4: one thread per (line, field); blockIdx.y is the field (primitives, then T)
 template <int ND, class R = double>
 __global__ void k_ig4(RhsArgsT<R> A, int e, Box lines, const R* table) {
@@ -1061,7 +1196,27 @@ gbr_status run_rhs_nd(gbr_ctx* c, const double* qs, const double* q0, double* ou
       CKL("k_ig4");
     }
   } else {
-    k_grad1<ND, R><<<g1 * ND, kBlock, 0, st>>>(A, B.grad1[0], B.grad1[1], B.grad1[2]);
+    if constexpr (ND == 3 && sizeof(R) == sizeof(float)) {
+      // one z-marching block per 32 x 8 tile of the union of the three boxes and chunk of planes
+      // (FP32; the FP64 pass is bound by the FP64 pipe, where the per-cell kernel measured faster)
+      Box U;
+      for (int d = 0; d < 3; ++d) {
+        U.lo[d] = std::min(B.grad1[0].lo[d], std::min(B.grad1[1].lo[d], B.grad1[2].lo[d]));
+        U.hi[d] = std::max(B.grad1[0].hi[d], std::max(B.grad1[1].hi[d], B.grad1[2].hi[d]));
+      }
+      const int nf = L.nv + (c->visc ? 1 : 0);
+      const int tiles_x = (U.hi[0] - U.lo[0] + kG1TX - 1) / kG1TX, tiles_y = (U.hi[1] - U.lo[1] + kG1TY - 1) / kG1TY;
+      const int nzu = U.hi[2] - U.lo[2];
+      // chunks of planes: about kG1Waves waves of resident blocks (8 per SM)
+      const int pairs = tiles_x * tiles_y * nf;
+      const int chunks = std::max(1, std::min(nzu, (kG1Waves * device_sms() * 8 + pairs - 1) / pairs));
+      const int zchunk = (nzu + chunks - 1) / chunks;
+      const unsigned blocks = (unsigned)(tiles_x * tiles_y * ((nzu + zchunk - 1) / zchunk));
+      k_grad1t<R><<<dim3(blocks, nf), kG1TX * kG1TY, 0, st>>>(A, U, B.grad1[0], B.grad1[1], B.grad1[2], tiles_x,
+                                                              tiles_y, zchunk);
+    } else {
+      k_grad1<ND, R><<<g1 * ND, kBlock, 0, st>>>(A, B.grad1[0], B.grad1[1], B.grad1[2]);
+    }
     CKL("k_grad1");
   }
   if constexpr (!kFaceFormsG2<R>) {
