@@ -170,6 +170,7 @@ __device__ __forceinline__ void g1_ring_pos(int r, int& sy, int& sx) {
 }
 
 constexpr int kG1Waves = 3;
+constexpr int kG1Fields = 1;  // fields per block (2 and 3, one barrier per plane for all, measured no faster)
 
 // streaming multiprocessors of the current device (queried once)
 inline int device_sms() {
@@ -183,12 +184,12 @@ inline int device_sms() {
   return v;
 }
 
-template <class R>
+template <class R, int FPB>
 __global__ void __launch_bounds__(kG1TX * kG1TY) k_grad1t(RhsArgsT<R> A, Box U, Box bx, Box by, Box bz, int tiles_x,
-                                                          int tiles_y, int zchunk) {
+                                                          int tiles_y, int zchunk, int nf) {
   constexpr int NV = 5;
   constexpr int PL = kG1SX * kG1SY;  // one plane tile
-  __shared__ R plane[2 * PL];
+  __shared__ R plane[2][FPB][PL];
   const Layout& L = A.L;
   const int tid = threadIdx.x, tx = tid % kG1TX, ty = tid / kG1TX;
   const int t = blockIdx.x;
@@ -196,9 +197,17 @@ __global__ void __launch_bounds__(kG1TX * kG1TY) k_grad1t(RhsArgsT<R> A, Box U, 
   const int x0 = U.lo[0] + tlx * kG1TX, y0 = U.lo[1] + tly * kG1TY;  // cell of tile point (0, 0)
   const int x = x0 + tx, y = y0 + ty;
   const int zs = U.lo[2] + chunk * zchunk, ze = min(zs + zchunk, U.hi[2]);
-  const int f = blockIdx.y;
   const long long PC = L.pcount, sz = L.ps[2];
-  const R* src = (f < NV) ? A.prim + f * PC : A.temp;
+  // fields f0 .. f0 + FPB - 1 of this block (the last block of an odd count repeats the last
+  // field: same values written twice)
+  const R* src[FPB];
+  long long fo[FPB];
+#pragma unroll
+  for (int q = 0; q < FPB; ++q) {
+    const int f = min(blockIdx.y * FPB + q, nf - 1);
+    src[q] = (f < NV) ? A.prim + f * PC : A.temp;
+    fo[q] = f * PC;
+  }
   // A value is loaded only where its (x, y) lies in the padded box (outside it no output needs
   // it).  Along z no check is needed: the planes read, zs - 3 .. ze + 2 with zs >= -3 and
   // ze <= n_z + 3, lie in the padded range -H .. n_z + H - 1.
@@ -207,10 +216,10 @@ __global__ void __launch_bounds__(kG1TX * kG1TY) k_grad1t(RhsArgsT<R> A, Box U, 
   };
   const bool col = inside(x, y);
   const long long pcol = col ? pidx(L, x, y, 0) : 0;  // padded index of (x, y, 0)
-  // the ring cells this thread loads (at most two): shared-memory slot and running source pointer
+  // the ring cells this thread loads (at most two): shared-memory slot and padded offset
   int r_off[2];
   bool r_ok[2];
-  const R* rq[2];
+  long long r_p[2];
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int r = tid + h * kG1TX * kG1TY;
@@ -221,7 +230,7 @@ __global__ void __launch_bounds__(kG1TX * kG1TY) k_grad1t(RhsArgsT<R> A, Box U, 
       r_ok[h] = inside(x0 + sx - kG1Ring, y0 + sy - kG1Ring);
     }
     r_off[h] = (r < kG1RingCount) ? sy * kG1SX + sx : -1;
-    rq[h] = src + (r_ok[h] ? pidx(L, x0 + sx - kG1Ring, y0 + sy - kG1Ring, 0) : 0);
+    r_p[h] = r_ok[h] ? pidx(L, x0 + sx - kG1Ring, y0 + sy - kG1Ring, 0) : 0;
   }
   const bool ox = x >= bx.lo[0] && x < bx.hi[0] && y >= bx.lo[1] && y < bx.hi[1];
   const bool oy = x >= by.lo[0] && x < by.hi[0] && y >= by.lo[1] && y < by.hi[1];
@@ -229,42 +238,52 @@ __global__ void __launch_bounds__(kG1TX * kG1TY) k_grad1t(RhsArgsT<R> A, Box U, 
   const int e = (ty + kG1Ring) * kG1SX + tx + kG1Ring;  // this column's cell in the plane tile
   // loads run ahead of their use: the column's z+3 and the ring's plane z+2 are requested while
   // plane z is formed, so no step waits on a load issued in the same step
-  const R* cq = src + pcol + (long long)(zs - 3) * sz;
-  R w[7], rv[2][3];
+  R w[FPB][7], rv[FPB][2][3];
+  long long oc = pcol + (long long)(zs - 3) * sz;  // column offset of the next load
+  long long orr = (long long)zs * sz;              // ring offset (plus r_p) of the next load
 #pragma unroll
-  for (int k = 0; k < 6; ++k) w[k] = col ? cq[k * sz] : R(0);
-  cq += 6 * sz;
+  for (int q = 0; q < FPB; ++q) {
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    rq[h] += (long long)zs * sz;
-    rv[h][0] = r_ok[h] ? rq[h][0] : R(0);
-    rv[h][1] = r_ok[h] ? rq[h][sz] : R(0);
-    rq[h] += 2 * sz;
-  }
-  long long p = pcol + (long long)zs * sz;
-  for (int z = zs; z < ze; ++z, p += sz) {
-    R* pl = plane + ((z - zs) & 1) * PL;
-    w[6] = col ? *cq : R(0);
-    cq += sz;
+    for (int k = 0; k < 6; ++k) w[q][k] = col ? src[q][oc + k * sz] : R(0);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      rv[h][2] = r_ok[h] ? *rq[h] : R(0);
-      rq[h] += sz;
+      rv[q][h][0] = r_ok[h] ? src[q][r_p[h] + orr] : R(0);
+      rv[q][h][1] = r_ok[h] ? src[q][r_p[h] + orr + sz] : R(0);
     }
-    pl[e] = w[3];
+  }
+  oc += 6 * sz;
+  orr += 2 * sz;
+  long long p = pcol + (long long)zs * sz;
+  for (int z = zs; z < ze; ++z, p += sz, oc += sz, orr += sz) {
+    const int buf = (z - zs) & 1;
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
-      if (r_off[h] >= 0) pl[r_off[h]] = rv[h][0];
+    for (int q = 0; q < FPB; ++q) {
+      w[q][6] = col ? src[q][oc] : R(0);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) rv[q][h][2] = r_ok[h] ? src[q][r_p[h] + orr] : R(0);
+      R* pl = plane[buf][q];
+      pl[e] = w[q][3];
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        if (r_off[h] >= 0) pl[r_off[h]] = rv[q][h][0];
+    }
     __syncthreads();
-    if (ox && z >= bx.lo[2] && z < bx.hi[2]) A.g1[0][f * PC + p] = stencil_E6(pl + e, 0, 1);
-    if (oy && z >= by.lo[2] && z < by.hi[2]) A.g1[1][f * PC + p] = stencil_E6(pl + e, 0, kG1SX);
-    if (oz && z >= bz.lo[2] && z < bz.hi[2]) A.g1[2][f * PC + p] = stencil_E6(w, 3, 1);
+    const bool zx = ox && z >= bx.lo[2] && z < bx.hi[2];
+    const bool zy = oy && z >= by.lo[2] && z < by.hi[2];
+    const bool zz = oz && z >= bz.lo[2] && z < bz.hi[2];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) w[k] = w[k + 1];
+    for (int q = 0; q < FPB; ++q) {
+      const R* pl = plane[buf][q];
+      if (zx) A.g1[0][fo[q] + p] = stencil_E6(pl + e, 0, 1);
+      if (zy) A.g1[1][fo[q] + p] = stencil_E6(pl + e, 0, kG1SX);
+      if (zz) A.g1[2][fo[q] + p] = stencil_E6(w[q], 3, 1);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      rv[h][0] = rv[h][1];
-      rv[h][1] = rv[h][2];
+      for (int k = 0; k < 6; ++k) w[q][k] = w[q][k + 1];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        rv[q][h][0] = rv[q][h][1];
+        rv[q][h][1] = rv[q][h][2];
+      }
     }
   }
 }
@@ -1208,12 +1227,13 @@ gbr_status run_rhs_nd(gbr_ctx* c, const double* qs, const double* q0, double* ou
       const int tiles_x = (U.hi[0] - U.lo[0] + kG1TX - 1) / kG1TX, tiles_y = (U.hi[1] - U.lo[1] + kG1TY - 1) / kG1TY;
       const int nzu = U.hi[2] - U.lo[2];
       // chunks of planes: about kG1Waves waves of resident blocks (8 per SM)
-      const int pairs = tiles_x * tiles_y * nf;
+      const int fb = (nf + kG1Fields - 1) / kG1Fields;  // field groups
+      const int pairs = tiles_x * tiles_y * fb;
       const int chunks = std::max(1, std::min(nzu, (kG1Waves * device_sms() * 8 + pairs - 1) / pairs));
       const int zchunk = (nzu + chunks - 1) / chunks;
       const unsigned blocks = (unsigned)(tiles_x * tiles_y * ((nzu + zchunk - 1) / zchunk));
-      k_grad1t<R><<<dim3(blocks, nf), kG1TX * kG1TY, 0, st>>>(A, U, B.grad1[0], B.grad1[1], B.grad1[2], tiles_x,
-                                                              tiles_y, zchunk);
+      k_grad1t<R, kG1Fields><<<dim3(blocks, fb), kG1TX * kG1TY, 0, st>>>(A, U, B.grad1[0], B.grad1[1], B.grad1[2],
+                                                                         tiles_x, tiles_y, zchunk, nf);
     } else {
       k_grad1<ND, R><<<g1 * ND, kBlock, 0, st>>>(A, B.grad1[0], B.grad1[1], B.grad1[2]);
     }
