@@ -149,6 +149,27 @@ gbr_status gbr_set_motion(gbr_ctx* c, const gbr_motion* m, double t0);
 gbr_status gbr_set_state(gbr_ctx* c, const double* q, int on_device);
 gbr_status gbr_get_state(gbr_ctx* c, double* q, int on_device);
 
+/* Pipelined host transfers of the conserved state (no counterpart in the paper;
+ * a calling convention for loops fed from host memory, e.g. one problem per
+ * step).  Both return at once.  gbr_set_state_async uploads host_q into the
+ * caller-owned device buffer d_stage on a copy stream of the context, and the
+ * context's stream takes it as the state at this point of its order (work
+ * enqueued before the call still sees the old state, work after it the new
+ * one); gbr_get_state_async snapshots the state at this point of the stream
+ * order into d_stage and downloads it to host_q on a second copy stream.  So
+ * the upload of the next state and the download of the last one overlap the
+ * steps in between.  On a GBR_PREC_MIXED context gbr_set_state_async sets
+ * p_ref from cell 0 of host_q as gbr_set_state does.
+ *  host_q: page-locked host memory (cudaHostAlloc / cudaHostRegister), [nv][cells]
+ *          doubles; set: read up to the next gbr_sync (keep it unchanged until
+ *          then), get: written by the time gbr_sync returns.
+ *  d_stage: device buffer of nv*cells doubles owned by the caller, one for the
+ *          uploads and another for the downloads, each reused across calls and
+ *          not touched by the caller until gbr_sync.
+ * Errors: EINVAL for a null argument or host memory that is not page-locked. */
+gbr_status gbr_set_state_async(gbr_ctx* c, const double* host_q, double* d_stage);
+gbr_status gbr_get_state_async(gbr_ctx* c, double* host_q, double* d_stage);
+
 /* Jet-type boundary data (reading A23): x-low inflow primitives [nv][nk][nj]
  * imposed in the x-low ghost cells of every following stage, and a sponge source
  * -sigma (Q - q_amb) with sigma per cell (host, NULL removes it).
@@ -172,7 +193,8 @@ gbr_status gbr_compute_dt(gbr_ctx* c, double cfl, double* dt_out);
  * the mesh per stage when a motion is set.  Asynchronous. */
 gbr_status gbr_rk_step(gbr_ctx* c, double cfl_or_neg_dt);
 
-/* Wait for the stream (polling, up to timeout_s seconds; <= 0: no limit), then
+/* Wait for the stream and the copy streams of the pipelined transfers (polling,
+ * up to timeout_s seconds; <= 0: no limit), then
  * report sticky device errors: ENONFINITE, or ETIMEOUT when a kernel's bounded
  * wait for a tile copy into shared memory ran out (the MIG4 line solves).
  * ETIMEOUT also when the stream did not drain before the deadline. */

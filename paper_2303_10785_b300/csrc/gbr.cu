@@ -836,6 +836,10 @@ struct gbr_ctx {
   long long launches;
   bool prof;
   std::vector<cudaEvent_t> ev;
+  // pipelined host transfers (gbr_set_state_async / gbr_get_state_async): one copy stream per
+  // direction and the events that order them against the context's stream (created on first use)
+  cudaStream_t cs_in = nullptr, cs_out = nullptr;
+  cudaEvent_t ev_in_ready = nullptr, ev_in_free = nullptr, ev_snap = nullptr, ev_out_free = nullptr;
   size_t ev_used;
 };
 
@@ -1597,6 +1601,78 @@ gbr_status gbr_get_state(gbr_ctx* c, double* q, int on_device) {
   return GBR_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// the copy streams and events of the pipelined transfers, created once per context
+gbr_status async_init(gbr_ctx* c) {
+  if (c->cs_in) return GBR_OK;
+  CK(cudaStreamCreateWithFlags(&c->cs_in, cudaStreamNonBlocking), "copy stream");
+  CK(cudaStreamCreateWithFlags(&c->cs_out, cudaStreamNonBlocking), "copy stream");
+  for (cudaEvent_t* e : {&c->ev_in_ready, &c->ev_in_free, &c->ev_snap, &c->ev_out_free})
+    CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "copy event");
+  return GBR_OK;
+}
+
+// host memory the copy engines can read or write without a staging copy of their own
+bool is_pinned(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
+// FP32 primitives' pressure offset from cell 0 of a host state (gbr_set_state's rule)
+void set_pref_from(gbr_ctx* c, const double* q) {
+  const int nv = c->L.nv;
+  double ke = 0.0;
+  for (int a = 0; a < c->L.nd; ++a) ke += q[(1 + a) * c->L.ncells] * q[(1 + a) * c->L.ncells] / q[0];
+  const double p0 = (c->p.gamma - 1.0) * (q[(size_t)(nv - 1) * c->L.ncells] - 0.5 * ke);
+  c->pref = std::isfinite(p0) && std::fabs(p0) < 1e38 ? (double)(float)p0 : 0.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+gbr_status gbr_set_state_async(gbr_ctx* c, const double* host_q, double* d_stage) {
+  if (!c || !host_q || !d_stage) return fail(c, GBR_EINVAL, "null argument");
+  if (!is_pinned(host_q)) return fail(c, GBR_EINVAL, "host state must be page-locked (pinned) memory");
+  gbr_status s = async_init(c);
+  if (s != GBR_OK) return s;
+  const size_t bytes = sizeof(double) * c->L.nv * c->L.ncells;
+  // upload into the staging buffer once the previous upload has been taken from it, then take it
+  // in the context's stream order
+  CK(cudaStreamWaitEvent(c->cs_in, c->ev_in_free, 0), "wait staging");
+  CK(cudaMemcpyAsync(d_stage, host_q, bytes, cudaMemcpyHostToDevice, c->cs_in), "upload state");
+  CK(cudaEventRecord(c->ev_in_ready, c->cs_in), "record upload");
+  CK(cudaStreamWaitEvent(c->stream, c->ev_in_ready, 0), "wait upload");
+  CK(cudaMemcpyAsync(c->q[0], d_stage, bytes, cudaMemcpyDeviceToDevice, c->stream), "take state");
+  CK(cudaEventRecord(c->ev_in_free, c->stream), "record staging free");
+  if (c->p.precision == GBR_PREC_MIXED) set_pref_from(c, host_q);
+  return GBR_OK;
+}
+
+gbr_status gbr_get_state_async(gbr_ctx* c, double* host_q, double* d_stage) {
+  if (!c || !host_q || !d_stage) return fail(c, GBR_EINVAL, "null argument");
+  if (!is_pinned(host_q)) return fail(c, GBR_EINVAL, "host state must be page-locked (pinned) memory");
+  gbr_status s = async_init(c);
+  if (s != GBR_OK) return s;
+  const size_t bytes = sizeof(double) * c->L.nv * c->L.ncells;
+  // snapshot in stream order (once the previous download has left the staging buffer), download
+  // on the copy stream while the context's stream goes on
+  CK(cudaStreamWaitEvent(c->stream, c->ev_out_free, 0), "wait staging");
+  CK(cudaMemcpyAsync(d_stage, c->q[0], bytes, cudaMemcpyDeviceToDevice, c->stream), "snapshot state");
+  CK(cudaEventRecord(c->ev_snap, c->stream), "record snapshot");
+  CK(cudaStreamWaitEvent(c->cs_out, c->ev_snap, 0), "wait snapshot");
+  CK(cudaMemcpyAsync(host_q, d_stage, bytes, cudaMemcpyDeviceToHost, c->cs_out), "download state");
+  CK(cudaEventRecord(c->ev_out_free, c->cs_out), "record download");
+  return GBR_OK;
+}
+
 gbr_status gbr_set_inflow(gbr_ctx* c, const double* prim, int on_device) {
   if (!c || !prim) return fail(c, GBR_EINVAL, "null argument");
   const size_t bytes = sizeof(double) * c->L.nv * c->L.n[1] * c->L.n[2];
@@ -1675,6 +1751,8 @@ gbr_status gbr_sync(gbr_ctx* c, double timeout_s) {
   auto t0 = std::chrono::steady_clock::now();
   for (;;) {
     cudaError_t e = cudaStreamQuery(c->stream);
+    if (e == cudaSuccess && c->cs_in) e = cudaStreamQuery(c->cs_in);
+    if (e == cudaSuccess && c->cs_out) e = cudaStreamQuery(c->cs_out);
     if (e == cudaSuccess) break;
     if (e != cudaErrorNotReady) return cuda_check(c, e, "stream query");
     double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1801,6 +1879,13 @@ const char* gbr_last_global_error(void) { return g_global_error.c_str(); }
 void gbr_destroy(gbr_ctx* c) {
   if (!c) return;
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : {c->ev_in_ready, c->ev_in_free, c->ev_snap, c->ev_out_free})
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t t : {c->cs_in, c->cs_out})
+    if (t) {
+      cudaStreamSynchronize(t);
+      cudaStreamDestroy(t);
+    }
   delete c;
 }
 

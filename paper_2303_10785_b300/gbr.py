@@ -92,6 +92,8 @@ def lib():
     L.gbr_get_field.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _P]
     L.gbr_profile.argtypes = [_vp, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     L.gbr_check_bounded_wait.argtypes = [_vp, ctypes.c_int]
+    L.gbr_set_state_async.argtypes = [_vp, _vp, _vp]
+    L.gbr_get_state_async.argtypes = [_vp, _vp, _vp]
     L.gbr_profile.restype = ctypes.c_int
     L.gbr_rhs_static.argtypes = [ctypes.POINTER(gbr_params), _P, _P, _vp, _vp, _vp, ctypes.c_char_p, ctypes.c_size_t]
     L.gbr_rhs_static.restype = ctypes.c_int
@@ -135,7 +137,8 @@ def exported_symbols():
     """Names declared in include/gbr.h that the library must export."""
     return ["gbr_workspace_bytes", "gbr_create", "gbr_compute_metrics", "gbr_move_mesh", "gbr_set_motion",
             "gbr_set_state", "gbr_get_state", "gbr_set_inflow", "gbr_set_sponge", "gbr_rhs", "gbr_compute_dt",
-            "gbr_rk_step", "gbr_sync", "gbr_get_time", "gbr_get_field", "gbr_profile", "gbr_check_bounded_wait",
+            "gbr_set_state_async", "gbr_get_state_async", "gbr_rk_step", "gbr_sync", "gbr_get_time", "gbr_get_field",
+            "gbr_profile", "gbr_check_bounded_wait",
             "gbr_rhs_static",
             "gbr_batch_workspace_bytes", "gbr_batch_create", "gbr_batch_set_options", "gbr_batch_add",
             "gbr_batch_remove", "gbr_batch_step", "gbr_batch_sync", "gbr_batch_info", "gbr_batch_tuning",
@@ -270,6 +273,26 @@ class Solver:
 
     def state_into(self, tensor):
         self._check(self.L.gbr_get_state(self.h, _vp(tensor.data_ptr()), 1))
+
+    def _stage(self, which):
+        # device staging buffers of the pipelined transfers ("in", "out"), allocated on first use
+        stages = self.__dict__.setdefault("_stages", {})
+        if which not in stages:
+            stages[which] = self.torch.empty((self.nv,) + self.cell_shape, dtype=self.torch.float64,
+                                             device=self.device)
+        return stages[which]
+
+    def set_state_async(self, host):
+        """Upload a pinned host tensor [nv][cells] (float64) on a copy stream; it becomes the state
+        at this point of the stream order.  Keep it unchanged until sync()."""
+        assert host.is_pinned() and host.dtype == self.torch.float64 and host.is_contiguous()
+        self._check(self.L.gbr_set_state_async(self.h, _vp(host.data_ptr()), _vp(self._stage("in").data_ptr())))
+
+    def get_state_async(self, host):
+        """Download the state at this point of the stream order into a pinned host tensor on a copy
+        stream; valid after sync()."""
+        assert host.is_pinned() and host.dtype == self.torch.float64 and host.is_contiguous()
+        self._check(self.L.gbr_get_state_async(self.h, _vp(host.data_ptr()), _vp(self._stage("out").data_ptr())))
 
     # ---- method
     def rhs(self, out=None):
