@@ -106,9 +106,10 @@ __global__ void k_prim(RhsArgsT<R> A, Box b) {
 constexpr int kStreamBlocks = 8;
 
 template <int ND, class R = double>
-__global__ void __launch_bounds__(kBlock, kStreamBlocks) k_prim_halo(RhsArgsT<R> A, const double* q, Box b) {
+__global__ void __launch_bounds__(kBlock, kStreamBlocks) k_prim_halo(RhsArgsT<R> A, const double* q,
+                                                                     const float* dq, Box b) {
   BOX_THREAD(b);
-  body_prim_halo<ND>(A, q, i, j, k);
+  body_prim_halo<ND>(A, q, dq, i, j, k);
 }
 
 template <int ND, class R = double>
@@ -1161,10 +1162,11 @@ gbr_status launch_face(gbr_ctx* c, const RhsArgsT<R>& A, int d, const Box& b) {
   return GBR_OK;
 }
 
-// one evaluation of L(qs): out = L (mode 0) or the RK combination (mode 1)
+// one evaluation of L(qs [+ dq_in]): out = L (mode 0) or the RK combination (mode 1), the latter
+// in increments when dq_in / dq_out are given (mixed path, body_update)
 template <int ND, class R>
 gbr_status run_rhs_nd(gbr_ctx* c, const double* qs, const double* q0, double* out, int mode, double ca, double cb,
-                      double cc) {
+                      double cc, const float* dq_in, float* dq_out) {
   const Layout& L = c->L;
   cudaStream_t st = c->stream;
   const RhsArgsT<R> A = rhs_args_r<R>(c, qs);
@@ -1172,7 +1174,7 @@ gbr_status run_rhs_nd(gbr_ctx* c, const double* qs, const double* q0, double* ou
   const Box bi = B.inner;
   // primitives and all ghost layers in one pass over the padded box
   const Box pad = pad_box(L, H, H);
-  k_prim_halo<ND, R><<<grid_of(pad, kBlock), kBlock, 0, st>>>(A, qs, pad);
+  k_prim_halo<ND, R><<<grid_of(pad, kBlock), kBlock, 0, st>>>(A, qs, dq_in, pad);
   CKL("k_prim_halo");
   unsigned g1 = 0, g2 = 0;
   for (int e = 0; e < ND; ++e) {
@@ -1267,6 +1269,8 @@ gbr_status run_rhs_nd(gbr_ctx* c, const double* qs, const double* q0, double* ou
   U.cb = cb;
   U.cc = cc;
   U.mode = mode;
+  U.dq_in = dq_in;
+  U.dq_out = dq_out;
   if (c->mov) k_update<ND, true, R><<<grid_of(bi, kBlock), kBlock, 0, st>>>(U, bi, c->err);
   else k_update<ND, false, R><<<grid_of(bi, kBlock), kBlock, 0, st>>>(U, bi, c->err);
   CKL("k_update");
@@ -1274,12 +1278,18 @@ gbr_status run_rhs_nd(gbr_ctx* c, const double* qs, const double* q0, double* ou
 }
 
 gbr_status run_rhs(gbr_ctx* c, const double* qs, const double* q0, double* out, int mode, double ca, double cb,
-                   double cc) {
+                   double cc, const float* dq_in = nullptr, float* dq_out = nullptr) {
   if (c->p.precision == GBR_PREC_MIXED)
-    return c->L.nd == 3 ? run_rhs_nd<3, float>(c, qs, q0, out, mode, ca, cb, cc)
-                        : run_rhs_nd<2, float>(c, qs, q0, out, mode, ca, cb, cc);
-  return c->L.nd == 3 ? run_rhs_nd<3, double>(c, qs, q0, out, mode, ca, cb, cc)
-                      : run_rhs_nd<2, double>(c, qs, q0, out, mode, ca, cb, cc);
+    return c->L.nd == 3 ? run_rhs_nd<3, float>(c, qs, q0, out, mode, ca, cb, cc, dq_in, dq_out)
+                        : run_rhs_nd<2, float>(c, qs, q0, out, mode, ca, cb, cc, dq_in, dq_out);
+  return c->L.nd == 3 ? run_rhs_nd<3, double>(c, qs, q0, out, mode, ca, cb, cc, nullptr, nullptr)
+                      : run_rhs_nd<2, double>(c, qs, q0, out, mode, ca, cb, cc, nullptr, nullptr);
+}
+
+// the SSP-RK3 stages as Q^n plus FP32 increments: mixed path, static mesh, no sponge, motion or
+// geometry change within the step (the same condition as the FP32 increment of body_update)
+bool rk_in_increments(const gbr_ctx* c) {
+  return c->p.precision == GBR_PREC_MIXED && !c->mov && !c->have_motion && !c->have_sponge && c->jac32;
 }
 
 DtArgs dt_args(gbr_ctx* c) {
@@ -1730,6 +1740,19 @@ gbr_status gbr_rk_step(gbr_ctx* c, double cfl_or_neg_dt) {
     CKL("k_set_scalar");
   }
   // App. B: Q1 = Qn + dt L(Qn); Q2 = 3/4 Qn + 1/4 Q1 + 1/4 dt L(Q1); Qn+1 = 1/3 Qn + 2/3 Q2 + 2/3 dt L(Q2)
+  if (rk_in_increments(c)) {
+    // mixed path on a static mesh without sponge: Q1 = Qn + D1, Q2 = Qn + D2 with FP32 increments
+    // D1, D2 kept in the stage buffers (body_update)
+    float* d1 = reinterpret_cast<float*>(c->q[1]);
+    float* d2 = reinterpret_cast<float*>(c->q[2]);
+    if ((s = run_rhs(c, c->q[0], c->q[0], nullptr, 1, 1.0, 0.0, 1.0, nullptr, d1)) != GBR_OK) return s;
+    if ((s = run_rhs(c, c->q[0], c->q[0], nullptr, 1, 0.75, 0.25, 0.25, d1, d2)) != GBR_OK) return s;
+    if ((s = run_rhs(c, c->q[0], c->q[0], c->q[0], 1, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, d2, nullptr)) != GBR_OK)
+      return s;
+    k_advance_time<<<1, 1, 0, c->stream>>>(c->scal);
+    CKL("k_advance_time");
+    return GBR_OK;
+  }
   if ((s = run_rhs(c, c->q[0], c->q[0], c->q[1], 1, 1.0, 0.0, 1.0)) != GBR_OK) return s;
   if (c->have_motion) {
     if ((s = run_motion(c, 1.0)) != GBR_OK) return s;
@@ -2089,6 +2112,8 @@ cudaError_t static_rhs_launches(gbr_ctx& c, const double* q, double* dqdt, cudaS
   U.cb = 0.0;
   U.cc = 1.0;
   U.mode = 0;
+  U.dq_in = nullptr;
+  U.dq_out = nullptr;
   if (c.mov) k_update<ND, true><<<grid_of(B.inner, kBlock), kBlock, 0, st>>>(U, B.inner, c.err);
   else k_update<ND, false><<<grid_of(B.inner, kBlock), kBlock, 0, st>>>(U, B.inner, c.err);
   return cudaGetLastError();

@@ -33,7 +33,8 @@ struct BatchJob {
   RhsArgsT<R> A;        // A.q unused: the stage input comes from q[stage]
   UpdArgsT<R> U[4];     // SSP-RK3 stage combinations 0..2; 3: L(Q^n) into Q^(1) (autotuning)
   DtArgs D;
-  const double* q[3];   // Q^n, Q^(1), Q^(2)
+  const double* q[3];   // Q^n, Q^(1), Q^(2) (increment form: Q^n for every stage)
+  const float* dq[3];   // increment form: null, D1, D2 (the stage state is q[s] + dq[s])
   Box pad, inner, grad1[3], grad2[3], faces[3];
   double* scal;
   unsigned long long* dtbits;
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(kBlock, kStreamBlocks) kb_prim_halo(const Batc
   for_work(items, n, total, [&](const WorkItem& it, int lb) {
     const BatchJob<R>& J = jobs[it.job];
     BATCH_CELL(J.pad);
-    body_prim_halo<ND>(J.A, J.q[stage], i, j, k);
+    body_prim_halo<ND>(J.A, J.q[stage], J.dq[stage], i, j, k);
   });
 }
 
@@ -299,6 +300,23 @@ BatchJob<R> make_job(gbr_ctx* c, double cfl) {
   J.D.mt = nullptr;  // static members only
   J.D.mt32 = nullptr;
   for (int s = 0; s < 3; ++s) J.q[s] = c->q[s];
+  if (rk_in_increments(c)) {
+    // the same increment form as gbr_rk_step: Q_s = Q^n + D_s, D1 and D2 in the stage buffers
+    float* d1 = reinterpret_cast<float*>(c->q[1]);
+    float* d2 = reinterpret_cast<float*>(c->q[2]);
+    for (int s = 0; s < 3; ++s) {
+      J.q[s] = c->q[0];
+      J.U[s].qs = c->q[0];
+    }
+    J.dq[1] = d1;
+    J.dq[2] = d2;
+    J.U[0].dq_out = d1;
+    J.U[0].out = nullptr;
+    J.U[1].dq_in = d1;
+    J.U[1].dq_out = d2;
+    J.U[1].out = nullptr;
+    J.U[2].dq_in = d2;
+  }
   const RhsBoxes B = rhs_boxes(L);
   J.pad = pad_box(L, H, H);
   J.inner = B.inner;

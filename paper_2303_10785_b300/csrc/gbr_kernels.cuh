@@ -609,22 +609,27 @@ GBR_HD R stencil_E6(const R* f, long long e, long long s) {
 // The pressure is stored as p - pref: on the mixed path pref is a pressure of the flow (set with
 // the state), so that FP32 keeps the digits of the pressure differences; the energy offset
 // pref/(gamma-1) is taken off in FP64 before the rounding.  pref = 0 on the FP64 path.
+// dq (mixed path, or null): the FP32 increment of the stage state over q, Q_s = q + dq (the
+// stage states of a step are kept as Q^n plus an FP32 increment, see body_update); added after
+// the rounding to FP32.
 template <int ND, class R>
-GBR_HD void prim_store(const RhsArgsT<R>& A, const double* q, long long c, long long p) {
+GBR_HD void prim_store(const RhsArgsT<R>& A, const double* q, const float* dq, long long c, long long p) {
   constexpr int NV = ND + 2;
   const Layout& L = A.L;
   const long long NC = L.ncells, PC = L.pcount;
-  const R rho = R(q[c]);
+  const R rho = dq ? R(q[c]) + R(dq[c]) : R(q[c]);
   const R ir = R(1) / rho;
   R ke = R(0);
   A.prim[p] = rho;
   for (int a = 0; a < ND; ++a) {
-    const R m = R(q[(1 + a) * NC + c]);
+    const long long o = (1 + a) * NC + c;
+    const R m = dq ? R(q[o]) + R(dq[o]) : R(q[o]);
     const R u = m * ir;
     A.prim[(1 + a) * PC + p] = u;
     ke = gfma(m, u, ke);
   }
-  const R Erel = R(q[(NV - 1) * NC + c] - A.pref * A.ph.igm1);
+  const long long oE = (NV - 1) * NC + c;
+  const R Erel = dq ? R(q[oE] - A.pref * A.ph.igm1) + R(dq[oE]) : R(q[oE] - A.pref * A.ph.igm1);
   const R prel = A.pr.gm1 * (Erel - R(0.5) * ke);  // p - pref
   A.prim[(NV - 1) * PC + p] = prel;
   if (A.viscous) A.temp[p] = (prel + A.pref_r) * ir;
@@ -633,7 +638,7 @@ GBR_HD void prim_store(const RhsArgsT<R>& A, const double* q, long long c, long 
 // primitives at interior cells
 template <int ND, class R>
 GBR_HD void body_prim(const RhsArgsT<R>& A, int i, int j, int k) {
-  prim_store<ND>(A, A.q, cidx(A.L, i, j, k), pidx(A.L, i, j, k));
+  prim_store<ND>(A, A.q, nullptr, cidx(A.L, i, j, k), pidx(A.L, i, j, k));
 }
 
 // Primitives on the whole padded box in one pass (interior and ghost layers): a ghost cell takes
@@ -645,7 +650,7 @@ GBR_HD void body_prim(const RhsArgsT<R>& A, int i, int j, int k) {
 // the cross-section the axis-by-axis filling sees (earlier axes' coordinates clamped to the
 // cells, later axes' at the source cell).
 template <int ND, class R>
-GBR_HD void body_prim_halo(const RhsArgsT<R>& A, const double* q, int i, int j, int k) {
+GBR_HD void body_prim_halo(const RhsArgsT<R>& A, const double* q, const float* dq, int i, int j, int k) {
   constexpr int NV = ND + 2;
   const Layout& L = A.L;
   int c[3] = {i, j, k};
@@ -681,7 +686,7 @@ GBR_HD void body_prim_halo(const RhsArgsT<R>& A, const double* q, int i, int j, 
   const long long p = pidx(L, i, j, k);
   const long long PC = L.pcount;
   if (!inflow && !(wall[0] | wall[1] | wall[2])) {
-    prim_store<ND>(A, q, cidx(L, c[0], c[1], c[2]), p);
+    prim_store<ND>(A, q, dq, cidx(L, c[0], c[1], c[2]), p);
     return;
   }
   // the source state in FP64
@@ -694,15 +699,16 @@ GBR_HD void body_prim_halo(const RhsArgsT<R>& A, const double* q, int i, int j, 
     pr = A.inflow[(NV - 1) * plane + ib];
   } else {
     const long long cs = cidx(L, c[0], c[1], c[2]), NC = L.ncells;
-    rho = q[cs];
+    auto qv = [&](int v) { return dq ? q[v * NC + cs] + (double)dq[v * NC + cs] : q[v * NC + cs]; };
+    rho = qv(0);
     const double ir = 1.0 / rho;
     double ke = 0.0;
     for (int a = 0; a < ND; ++a) {
-      const double m = q[(1 + a) * NC + cs];
+      const double m = qv(1 + a);
       u[a] = m * ir;
       ke = gfma(m, u[a], ke);
     }
-    pr = A.ph.gm1 * (q[(NV - 1) * NC + cs] - 0.5 * ke);
+    pr = A.ph.gm1 * (qv(NV - 1) - 0.5 * ke);
   }
   #pragma unroll
   for (int a = 0; a < ND; ++a) {
@@ -1437,6 +1443,9 @@ struct UpdArgsT {
   const double* dt;     // device scalar
   double ca, cb, cc;    // out = ca q0 + cb qs + cc dt L
   int mode;             // 0: out = L, 1: RK combination
+  // mixed path, static mesh, no sponge: the stage states as Q^n + FP32 increments (or null)
+  const float* dq_in;   // increment of this stage's state (null in the first stage)
+  float* dq_out;        // increment of the next stage's state (null in the last stage: out = Q^n+1)
 };
 using UpdArgs = UpdArgsT<double>;
 
@@ -1445,6 +1454,15 @@ using UpdArgs = UpdArgsT<double>;
 constexpr long long kUpdHuge = 0x7FEFDCF158ADBB99LL;  // bit pattern of 1.79e308
 GBR_HD bool upd_not_finite(double x) { return (dbits(x) & kMag) > kUpdHuge; }
 GBR_HD bool upd_not_positive(double x) { return dbits(x) <= 0; }  // +0, negatives, -0
+GBR_HD bool upd_not_finite_f(float x) {  // |x| above the largest float: infinity or NaN
+#ifdef __CUDA_ARCH__
+  return (__float_as_uint(x) & 0x7FFFFFFFu) > 0x7F7FFFFFu;
+#else
+  unsigned b;
+  std::memcpy(&b, &x, sizeof b);
+  return (b & 0x7FFFFFFFu) > 0x7F7FFFFFu;
+#endif
+}
 
 // -sum_d (F_{i+1/2} - F_{i-1/2}) of component v, written (F_lo - F_hi) + ... so the first term
 // needs no subtraction from zero: the same rounding as 0 - (F_hi - F_lo) - ..., one operation fewer
@@ -1474,6 +1492,26 @@ GBR_HD bool body_update(const UpdArgsT<R>& U, int i, int j, int k) {
   if constexpr (sizeof(R) == sizeof(float) && !MOV) {
     // mixed path, static mesh, no sponge: the increment dt cc J r is formed in FP32 (r is an FP32
     // sum; its relative error stays that of r) and only the state combination is FP64
+    if (U.mode == 1 && !U.sigma && U.jac32 && (U.dq_in || U.dq_out)) {
+      // SSP-RK3 with ca + cb = 1 in increments: Q_s = Q^n + D_s, D_1 = dt J r_0,
+      // D_2 = 1/4 D_1 + 1/4 dt J r_1, Q^n+1 = Q^n + 2/3 D_2 + 2/3 dt J r_2, each D in FP32 (its
+      // size is that of the step's change, far below Q), one FP64 addition per value and step
+      const float dtJf = float((*U.dt) * U.cc) * U.jac32[c];
+      const float cbf = float(U.cb);
+      for (int v = 0; v < NV; ++v) {
+        float dn = dtJf * upd_flux_sum<ND>(U, v, i, j, k);
+        if (U.dq_in) dn = gfma(cbf, U.dq_in[v * NC + c], dn);
+        if (U.dq_out) {
+          U.dq_out[v * NC + c] = dn;
+          bad |= upd_not_finite_f(dn);
+        } else {
+          const double o = U.q0[v * NC + c] + (double)dn;
+          U.out[v * NC + c] = o;
+          bad |= upd_not_finite(o) || (v == 0 && upd_not_positive(o));
+        }
+      }
+      return bad;
+    }
     if (U.mode == 1 && !U.sigma && U.jac32) {
       const float dtJf = float((*U.dt) * U.cc) * U.jac32[c];
       for (int v = 0; v < NV; ++v) {
