@@ -1286,10 +1286,10 @@ gbr_status run_rhs(gbr_ctx* c, const double* qs, const double* q0, double* out, 
                       : run_rhs_nd<2, double>(c, qs, q0, out, mode, ca, cb, cc, nullptr, nullptr);
 }
 
-// the SSP-RK3 stages as Q^n plus FP32 increments: mixed path, static mesh, no sponge, motion or
-// geometry change within the step (the same condition as the FP32 increment of body_update)
+// the SSP-RK3 stages as Q^n plus FP32 increments: mixed path on a static mesh (no GCL term, no
+// motion or geometry change within the step)
 bool rk_in_increments(const gbr_ctx* c) {
-  return c->p.precision == GBR_PREC_MIXED && !c->mov && !c->have_motion && !c->have_sponge && c->jac32;
+  return c->p.precision == GBR_PREC_MIXED && !c->mov && !c->have_motion && c->jac32;
 }
 
 DtArgs dt_args(gbr_ctx* c) {
@@ -1741,7 +1741,7 @@ gbr_status gbr_rk_step(gbr_ctx* c, double cfl_or_neg_dt) {
   }
   // App. B: Q1 = Qn + dt L(Qn); Q2 = 3/4 Qn + 1/4 Q1 + 1/4 dt L(Q1); Qn+1 = 1/3 Qn + 2/3 Q2 + 2/3 dt L(Q2)
   if (rk_in_increments(c)) {
-    // mixed path on a static mesh without sponge: Q1 = Qn + D1, Q2 = Qn + D2 with FP32 increments
+    // mixed path on a static mesh: Q1 = Qn + D1, Q2 = Qn + D2 with FP32 increments
     // D1, D2 kept in the stage buffers (body_update)
     float* d1 = reinterpret_cast<float*>(c->q[1]);
     float* d2 = reinterpret_cast<float*>(c->q[2]);

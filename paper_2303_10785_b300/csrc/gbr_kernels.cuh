@@ -1492,14 +1492,22 @@ GBR_HD bool body_update(const UpdArgsT<R>& U, int i, int j, int k) {
   if constexpr (sizeof(R) == sizeof(float) && !MOV) {
     // mixed path, static mesh, no sponge: the increment dt cc J r is formed in FP32 (r is an FP32
     // sum; its relative error stays that of r) and only the state combination is FP64
-    if (U.mode == 1 && !U.sigma && U.jac32 && (U.dq_in || U.dq_out)) {
-      // SSP-RK3 with ca + cb = 1 in increments: Q_s = Q^n + D_s, D_1 = dt J r_0,
-      // D_2 = 1/4 D_1 + 1/4 dt J r_1, Q^n+1 = Q^n + 2/3 D_2 + 2/3 dt J r_2, each D in FP32 (its
-      // size is that of the step's change, far below Q), one FP64 addition per value and step
+    if (U.mode == 1 && U.jac32 && (U.dq_in || U.dq_out)) {
+      // SSP-RK3 with ca + cb = 1 in increments: Q_s = Q^n + D_s, D_1 = dt L_0,
+      // D_2 = 1/4 D_1 + 1/4 dt L_1, Q^n+1 = Q^n + 2/3 D_2 + 2/3 dt L_2, each D in FP32 (its size
+      // is that of the step's change, far below Q), one FP64 addition per value and step;
+      // L = J r - sigma (Q_s - Q_amb) with the sponge
       const float dtJf = float((*U.dt) * U.cc) * U.jac32[c];
       const float cbf = float(U.cb);
+      const double sg = U.sigma ? U.sigma[c] : 0.0;
+      const float dtsg = (sg != 0.0) ? float((*U.dt) * U.cc * sg) : 0.0f;
       for (int v = 0; v < NV; ++v) {
         float dn = dtJf * upd_flux_sum<ND>(U, v, i, j, k);
+        if (sg != 0.0) {
+          float dev = float(U.q0[v * NC + c] - U.qamb[v]);
+          if (U.dq_in) dev += U.dq_in[v * NC + c];
+          dn = gfma(-dtsg, dev, dn);
+        }
         if (U.dq_in) dn = gfma(cbf, U.dq_in[v * NC + c], dn);
         if (U.dq_out) {
           U.dq_out[v * NC + c] = dn;
