@@ -588,10 +588,10 @@ __global__ void __launch_bounds__(GBR_FACE_BLOCK, sizeof(R) == 4 ? GBR_FACE_MIN_
   face_block<ND, VISC, MOV>(A, d, valid, i, j, k, slots, &count);
 }
 
-template <int ND, bool MOV, class R = double>
+template <int ND, bool MOV, class R = double, bool SP = true>
 __global__ void __launch_bounds__(kBlock, kStreamBlocks) k_update(UpdArgsT<R> U, Box b, int* err) {
   BOX_THREAD(b);
-  if (body_update<ND, MOV>(U, i, j, k)) atomicOr(err, 1);
+  if (body_update<ND, MOV, R, SP>(U, i, j, k)) atomicOr(err, 1);
 }
 
 __global__ void k_dt_f32(DtArgs D, float* mh32, float* mt32, float* jac32, Box b) {
@@ -1272,7 +1272,8 @@ gbr_status run_rhs_nd(gbr_ctx* c, const double* qs, const double* q0, double* ou
   U.dq_in = dq_in;
   U.dq_out = dq_out;
   if (c->mov) k_update<ND, true, R><<<grid_of(bi, kBlock), kBlock, 0, st>>>(U, bi, c->err);
-  else k_update<ND, false, R><<<grid_of(bi, kBlock), kBlock, 0, st>>>(U, bi, c->err);
+  else if (U.sigma) k_update<ND, false, R, true><<<grid_of(bi, kBlock), kBlock, 0, st>>>(U, bi, c->err);
+  else k_update<ND, false, R, false><<<grid_of(bi, kBlock), kBlock, 0, st>>>(U, bi, c->err);
   CKL("k_update");
   return GBR_OK;
 }

@@ -133,13 +133,13 @@ __global__ void __launch_bounds__(BS, sizeof(R) == 4 ? 896 / BS : (BS < 384 ? 38
   });
 }
 
-template <int ND, class R>
+template <int ND, class R, bool SP>
 __global__ void __launch_bounds__(kBlock, kStreamBlocks) kb_update(const BatchJob<R>* jobs, const WorkItem* items, int n, int total,
                                                      int stage) {
   for_work(items, n, total, [&](const WorkItem& it, int lb) {
     const BatchJob<R>& J = jobs[it.job];
     BATCH_CELL(J.inner);
-    if (body_update<ND, false>(J.U[stage], i, j, k)) atomicOr(J.err, 1);
+    if (body_update<ND, false, R, SP>(J.U[stage], i, j, k)) atomicOr(J.err, 1);
   });
 }
 
@@ -426,7 +426,10 @@ gbr_status enqueue_rhs(gbr_batch* b, const Kind& K, int stage, long long& launch
   }
   if (s != GBR_OK) return s;
   {
-    auto kern = kb_update<ND, R>;
+    // the sponge-capable instantiation only when a member of the kind has a sponge
+    bool sponge = false;
+    for (gbr_ctx* m : K.members) sponge |= m->have_sponge;
+    auto kern = sponge ? kb_update<ND, R, true> : kb_update<ND, R, false>;
     kern<<<persistent_grid(b, kern, kBlock, K.total[WL_INNER]), kBlock, 0, st>>>(
         jobs, K.d_items[WL_INNER], (int)K.items[WL_INNER].size(), K.total[WL_INNER], stage);
     BK(cudaGetLastError(), "kb_update");

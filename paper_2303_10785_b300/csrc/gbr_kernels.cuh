@@ -1480,7 +1480,9 @@ GBR_HD R upd_flux_sum(const UpdArgsT<R>& U, int v, int i, int j, int k) {
   return r;
 }
 
-template <int ND, bool MOV, class R>
+// SP: the launch may carry a sponge (false: U.sigma is null for every cell it updates; the FP32
+// increment loop then has no sponge path, which costs registers at 32 per thread)
+template <int ND, bool MOV, class R, bool SP = true>
 GBR_HD bool body_update(const UpdArgsT<R>& U, int i, int j, int k) {
   constexpr int NV = ND + 2;
   const Layout& L = U.L;
@@ -1499,24 +1501,36 @@ GBR_HD bool body_update(const UpdArgsT<R>& U, int i, int j, int k) {
       // L = J r - sigma (Q_s - Q_amb) with the sponge
       const float dtJf = float((*U.dt) * U.cc) * U.jac32[c];
       const float cbf = float(U.cb);
-      const double sg = U.sigma ? U.sigma[c] : 0.0;
-      const float dtsg = (sg != 0.0) ? float((*U.dt) * U.cc * sg) : 0.0f;
-      for (int v = 0; v < NV; ++v) {
-        float dn = dtJf * upd_flux_sum<ND>(U, v, i, j, k);
-        if (sg != 0.0) {
-          float dev = float(U.q0[v * NC + c] - U.qamb[v]);
-          if (U.dq_in) dev += U.dq_in[v * NC + c];
-          dn = gfma(-dtsg, dev, dn);
+      // the sponge loop apart (a separate instantiation: the loop without it keeps its registers)
+      auto stages = [&](auto sponge) {
+        constexpr bool WS = decltype(sponge)::value;
+        const double sg = WS ? U.sigma[c] : 0.0;
+        const float dtsg = WS ? float((*U.dt) * U.cc * sg) : 0.0f;
+        for (int v = 0; v < NV; ++v) {
+          float dn = dtJf * upd_flux_sum<ND>(U, v, i, j, k);
+          if constexpr (WS) {
+            if (sg != 0.0) {
+              float dev = float(U.q0[v * NC + c] - U.qamb[v]);
+              if (U.dq_in) dev += U.dq_in[v * NC + c];
+              dn = gfma(-dtsg, dev, dn);
+            }
+          }
+          if (U.dq_in) dn = gfma(cbf, U.dq_in[v * NC + c], dn);
+          if (U.dq_out) {
+            U.dq_out[v * NC + c] = dn;
+            bad |= upd_not_finite_f(dn);
+          } else {
+            const double o = U.q0[v * NC + c] + (double)dn;
+            U.out[v * NC + c] = o;
+            bad |= upd_not_finite(o) || (v == 0 && upd_not_positive(o));
+          }
         }
-        if (U.dq_in) dn = gfma(cbf, U.dq_in[v * NC + c], dn);
-        if (U.dq_out) {
-          U.dq_out[v * NC + c] = dn;
-          bad |= upd_not_finite_f(dn);
-        } else {
-          const double o = U.q0[v * NC + c] + (double)dn;
-          U.out[v * NC + c] = o;
-          bad |= upd_not_finite(o) || (v == 0 && upd_not_positive(o));
-        }
+      };
+      if constexpr (SP) {
+        if (U.sigma) stages(std::true_type{});
+        else stages(std::false_type{});
+      } else {
+        stages(std::false_type{});
       }
       return bad;
     }
