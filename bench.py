@@ -41,7 +41,7 @@ JET_SEED = 2303
 METRIC = "cell-RK-stage updates/s"
 # FP64 peak used as the roofline denominator of this ALU-bound path: 148 SMs x
 # 2 DFMA/clk/SM x 2 flop x 2.032 GHz = 1.20 TFLOP/s nominal at the maximum SM
-# clock (the pool's FP64 figure is 1.25 TFLOP/s; derivation in the design doc).
+# clock; the pool's nominal FP64 figure, 1.25 TFLOP/s, is the one used.
 FP64_PEAK_TFLOPS = 1.25
 # FP32 FFMA peak, nominal: 148 SMs x 128 FMA/clk x 2 flop x 2.032 GHz
 FP32_PEAK_TFLOPS = 77.0

@@ -139,7 +139,7 @@ gbr_status gbr_compute_metrics(gbr_ctx* c);
 gbr_status gbr_move_mesh(gbr_ctx* c, const double* nodes, const double* node_vel);
 
 /* Prescribe an analytic motion evaluated on the device; gbr_rk_step then
- * recomputes the geometry at every stage time t, t+dt, t+dt/2 (reading A19).
+ * recomputes the geometry at every stage time t, t+dt, t+dt/2.
  * Sets the solution time to t0 and computes the metrics at t0. */
 gbr_status gbr_set_motion(gbr_ctx* c, const gbr_motion* m, double t0);
 
@@ -170,7 +170,7 @@ gbr_status gbr_get_state(gbr_ctx* c, double* q, int on_device);
 gbr_status gbr_set_state_async(gbr_ctx* c, const double* host_q, double* d_stage);
 gbr_status gbr_get_state_async(gbr_ctx* c, double* host_q, double* d_stage);
 
-/* Jet-type boundary data (reading A23): x-low inflow primitives [nv][nk][nj]
+/* Jet-type boundary data: x-low inflow primitives [nv][nk][nj]
  * imposed in the x-low ghost cells of every following stage, and a sponge source
  * -sigma (Q - q_amb) with sigma per cell (host, NULL removes it).
  * gbr_set_inflow: on_device = 0: prim is host memory, copied before the call

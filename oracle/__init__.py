@@ -6,9 +6,8 @@ CPU-baseline leg of ``bench.py``; the product path never touches it.  It shares
 no code with the CUDA library.  The only module both sides use is
 ``paper_2303_10785_b300.inputs`` (seeded grids and initial states).
 
-Parity unpinned (listed in the design doc): the face state of the eigenvectors
-(A6), the MP-limiter constants (A8), the Sutherland constants (A13), the viscous
-time-step bound (A20) and the jet boundary/sponge forms (A23).
+Parity unpinned: the face state of the eigenvectors, the MP-limiter constants, the
+Sutherland constants, the viscous time-step bound and the jet boundary/sponge forms.
 """
 import ctypes
 import os

@@ -24,11 +24,11 @@
  *   App. B   SSP-RK3 and the CFL time step
  *   App. D   non-conservative metrics with the E4 derivative (negative control only)
  *
- * Readings of silent or garbled passages are listed in the design doc (A1-A28 there).
+ * Where the paper is silent or garbled, the reading taken is stated beside the code that uses it.
  * Parity unpinned (oracle-to-GPU parity only): the face state used for the
- * eigenvectors (A6), the MP-limiter constants alpha = beta = 4 (A8), the
- * Sutherland constants (A13), the viscous time-step term (A20) and the jet
- * boundary/sponge forms (A23).
+ * eigenvectors, the MP-limiter constants alpha = beta = 4, the
+ * Sutherland constants, the viscous time-step term and the jet
+ * boundary/sponge forms.
  */
 #include "orc.h"
 
@@ -66,7 +66,7 @@ enum { PH_MISC = 0, PH_PRIM = 1, PH_GRAD = 2, PH_FACE = 3, PH_RES = 4, PH_GEOM =
 static std::string g_err;
 static int fail(const std::string& m) { g_err = m; return 1; }
 
-static const int H = 6;   // ghost layers of the primitive state (reading A21)
+static const int H = 6;   // ghost layers of the primitive state
 static const int E = 10;  // geometry extension in cells beyond each side
 
 static inline real Min(real a, real b) { return (a < b) ? a : b; }
@@ -150,7 +150,7 @@ struct Field {
 // One-dimensional operators along axis d (Sec. 5.1 step 1, Sec. 6, App. D)
 // ---------------------------------------------------------------------------
 
-// Eq. (E6_grads), read with differences (A1):
+// Eq. (E6_grads), read with differences:
 // f'_i = 3/4 (f_{i+1} - f_{i-1}) - 3/20 (f_{i+2} - f_{i-2}) + 1/60 (f_{i+3} - f_{i-3})
 static Field op_e6(const Field& f, int d) {
   Field o(f.b.grow(d, -3, -3));
@@ -172,7 +172,7 @@ static Field op_e4(const Field& f, int d) {
   return o;
 }
 
-// Eq. (IG4_grads), read with differences (A2), alpha = 5/14:
+// Eq. (IG4_grads), read with differences, alpha = 5/14:
 //   alpha f'_{i-1} + f'_i + alpha f'_{i+1} = (2 + alpha)/3 (f_{i+1} - f_{i-1}) + (4 alpha - 1)/12 (f_{i+2} - f_{i-2})
 static const double kIG4Alpha = 5.0 / 14.0;
 
@@ -223,7 +223,7 @@ static void ig4_line_cyclic(const real* fp, int n, std::vector<real>& g) {
 }
 
 // IG4 on an open line of m >= 7 values: the three end points at each side take explicit
-// rows (reading A33, App. C with A22's index correction): second-order one-sided at the end
+// rows (App. C, with the second cell's printed stencil shifted back by one index): second-order one-sided at the end
 // point, fourth-order biased next to it, fourth-order central (Eq. 4thorder-grads) third;
 // IG4 rows in between.
 static void ig4_line_open(const real* f, int m, std::vector<real>& g) {
@@ -323,7 +323,7 @@ static Field op_interp(const Field& f, int d, int scheme) {
 static Field op_D(const Field& f, int d) { return op_delta(op_interp(f, d, 0), d); }
 
 // ---------------------------------------------------------------------------
-// App. C (reading A35): an axis bounded by walls on both sides (no ghost nodes).
+// App. C: an axis bounded by walls on both sides (no ghost nodes).
 // The field's box along d is the n cells [lo, hi); the first and last three
 // cells take one-sided derivatives, the interfaces next to the walls one-sided
 // states, so that D = delta o interp is defined on every cell and is the same
@@ -340,7 +340,7 @@ static Field op_e6_c(const Field& f, int d) {
     real v;
     if (m == lo) v = -1.5 * F(0) + 2.0 * F(1) - 0.5 * F(2);                       // 2nd order one-sided
     else if (m == hi - 1) v = 1.5 * F(0) - 2.0 * F(-1) + 0.5 * F(-2);
-    else if (m == lo + 1)                                                           // 4th order biased (A22)
+    else if (m == lo + 1)                                                           // 4th order biased (printed stencil shifted back by one index)
       v = -0.25 * F(-1) - (5.0 / 6.0) * F(0) + 1.5 * F(1) - 0.5 * F(2) + F(3) / 12.0;
     else if (m == hi - 2) v = 0.25 * F(1) + (5.0 / 6.0) * F(0) - 1.5 * F(-1) + 0.5 * F(-2) - F(-3) / 12.0;
     else if (m == lo + 2 || m == hi - 3)                                            // 4th order central
@@ -353,7 +353,7 @@ static Field op_e6_c(const Field& f, int d) {
 }
 
 // second derivative on the whole box: one-sided derivatives of f' in the two end cells,
-// the interior formula of Sec. 5.1 elsewhere (the third cell's printed sign is read as A22)
+// the interior formula of Sec. 5.1 elsewhere (the third cell takes the interior formula: the printed one is garbled)
 static Field op_second_c(const Field& f, const Field& f1, int d) {
   Field o(f.b);
   const int lo = f.b.lo[d], hi = f.b.hi[d];
@@ -441,7 +441,7 @@ static int nz_of(int nd, int left, int r, int c) {
 // App. A: right (R) and left (R^{-1}) eigenvectors of B_xi in primitive
 // variables P = [rho, u, v, w, p], with the normalised metric n~ = n^/|n^|
 // and the face density and speed of sound.  2D: the restriction to
-// P = [rho, u, v, p] (reading in the design doc: entropy row = n~x row1 - n~y row3).
+// P = [rho, u, v, p] (the entropy row is n~x row1 - n~y row3).
 static void eigen(int nd, const real* nh, real rho, real p, real gamma, real R[5][5], real L[5][5]) {
   real nn2 = 0.0;
   for (int a = 0; a < nd; ++a) nn2 = nn2 + nh[a] * nh[a];
@@ -726,7 +726,7 @@ int orc_solver::build_geometry(const Field* xc, const Field* vc) {
           // Eq. (GCL_metrics): e.g. xi^_x = (y_eta z)_zeta - (y_zeta z)_eta
           mh[e][a] = f_sub(Dop(f_mul(xd[b][f], xc[c]), gg), Dop(f_mul(xd[b][gg], xc[c]), f));
         } else {
-          // App. D: e.g. xi^_x = y_eta z_zeta - y_zeta z_eta (cyclic form, reading A29)
+          // App. D: e.g. xi^_x = y_eta z_zeta - y_zeta z_eta (the cyclic form; the printed zeta^_y swaps the indices)
           mh[e][a] = f_sub(f_mul(xd[b][f], xd[c][gg]), f_mul(xd[b][gg], xd[c][f]));
         }
       }
@@ -799,7 +799,7 @@ int orc_solver::build_geometry(const Field* xc, const Field* vc) {
     }
     if (g.moving) g.ft[d] = f_crop(Iop(g.mt[d], d), fb);
   }
-  // Eq. (Jacb2) on the face values, the same difference as the flux divergence (A17)
+  // Eq. (Jacb2) on the face values, the same difference as the flux divergence
   g.gcl = Field(inner);
   if (g.moving) {
     FOR_BOX(inner) {
@@ -815,7 +815,7 @@ int orc_solver::build_geometry(const Field* xc, const Field* vc) {
 real orc_solver::viscosity(real T) const {
   real mu_ref = 1.0 / p.reynolds;
   if (!(p.sutherland_s > 0.0)) return mu_ref;
-  // Sutherland's law (Sec. 2), reading A13: mu = mu_ref th^{3/2} (1 + S)/(th + S), th = T/T_ref
+  // Sutherland's law (Sec. 2), read as: mu = mu_ref th^{3/2} (1 + S)/(th + S), th = T/T_ref
   real th = T / p.t_ref;
   return mu_ref * (th * Sqrt(th)) * ((1.0 + p.sutherland_s) / (th + p.sutherland_s));
 }
@@ -854,7 +854,7 @@ void orc_solver::fill_ghosts(Field* P) const {
         }
       }
     }
-    // slip walls (reading A36): ghost layer g mirrors cell g - 1 (n - g on the high side) --
+    // slip walls: ghost layer g mirrors cell g - 1 (n - g on the high side) --
     // density and pressure as they are, the velocity reflected about the unit normal of the
     // wall face, taken at the cross-section (coordinates of earlier axes clamped to the cells)
     for (int side = 0; side < 2; ++side) {
@@ -902,7 +902,7 @@ void orc_solver::face_flux(int d, int i, int j, int k, const Field* P, const Fie
   real nt = g.moving ? g.ft[d].at(i, j, k) : real(0.0);
 
   // Step 2: characteristic projection with the face eigenvectors (App. A).
-  // Face state (reading A6): arithmetic mean of rho and p of cells i and i+1.
+  // Face state: arithmetic mean of rho and p of cells i and i+1.
   real rb = 0.5 * (P[0].at(CELL(1)) + P[0].at(CELL(2)));
   real pb = 0.5 * (P[nv - 1].at(CELL(1)) + P[nv - 1].at(CELL(2)));
   real R[5][5], Ri[5][5];
@@ -948,7 +948,7 @@ void orc_solver::face_flux(int d, int i, int j, int k, const Field* P, const Fie
       real phiR = val(2) - 0.5 * grd(d, 2);
       for (int e = 0; e < nd; ++e) {
         if (e == d) gc[e] = 0.5 * (grd(e, 1) + grd(e, 2)) + (p.alpha_damping / 2.0) * (phiR - phiL);  // Eq. (AD-eqn1)
-        else gc[e] = 0.5 * (grd(e, 1) + grd(e, 2));  // tangential: mean of the cell gradients (A11)
+        else gc[e] = 0.5 * (grd(e, 1) + grd(e, 2));  // tangential: mean of the cell gradients
       }
       phif[v] = 0.5 * (phiL + phiR);
       // Eq. (AD-eqn3): chain rule with the interpolated unhatted metrics
@@ -1021,7 +1021,7 @@ int orc_solver::rhs(const double* q, double* Lout, double* resout, int fdir, dou
   Field T;
   if (viscous) {
     T = Field(pad);
-    FOR_BOX(pad) { T.at(i, j, k) = P[nv - 1].at(i, j, k) / P[0].at(i, j, k); }  // T = p/rho (R = 1, A14)
+    FOR_BOX(pad) { T.at(i, j, k) = P[nv - 1].at(i, j, k) / P[0].at(i, j, k); }  // T = p/rho (gas constant R = 1)
   }
   // Sec. 5.1 step 1: gradients along each computational direction
   ORC_PHASE(PH_GRAD);
@@ -1071,7 +1071,7 @@ int orc_solver::rhs(const double* q, double* Lout, double* resout, int fdir, dou
         real J = 1.0 / g.det.at(i, j, k);
         real qc = q[(size_t)c * NC + id];
         real L = g.moving ? J * (res - g.gcl.at(i, j, k) * qc) : J * res;
-        if (!sigma.empty()) L = L - sigma[id] * (qc - qamb[c]);  // sponge source (A23)
+        if (!sigma.empty()) L = L - sigma[id] * (qc - qamb[c]);  // sponge source
         Lout[(size_t)c * NC + id] = Dbl(L);
       }
     }
@@ -1237,7 +1237,7 @@ int orc_primitives(orc_solver* s, const double* q, double* prim) {
 }
 
 // App. B: dt = CFL * min over cells and directions of 1/(|U| + c |grad xi|),
-// with the viscous bound of reading A20 when the flow is viscous.
+// with the viscous bound 1 / (nu_eff |grad xi|^2), nu_eff = max(4/3, gamma/Pr) mu / rho, when the flow is viscous.
 double orc_dt(orc_solver* s, const double* q, double cfl) {
   const int nd = s->nd, nv = s->nv;
   const size_t NC = s->inner.size();

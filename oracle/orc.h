@@ -29,9 +29,9 @@ typedef struct {
   int periodic[3];       /* 1 = periodic axis */
   int ghost_nodes;       /* node layers supplied beyond each non-periodic side (>= 10), or 0:
                             the non-periodic axes end at walls and their metrics take the
-                            one-sided formulas of App. C (reading A35) */
+                            one-sided formulas of App. C */
   int bc[3][2];          /* non-periodic sides: ORC_BC_ZEROGRAD, ORC_BC_INFLOW (x-low only) or
-                            ORC_BC_WALL (slip wall, reading A36) */
+                            ORC_BC_WALL (slip wall) */
   int metric_scheme;     /* 0 = conservative metrics with the MEG6 operator (Sec. 6),
                             1 = non-conservative metrics with E4 (App. D, negative control) */
   double gamma, prandtl;
@@ -42,7 +42,7 @@ typedef struct {
   double mp_alpha, mp_beta, mp_eps;  /* App. E limiter constants */
   int gradient_scheme;   /* 0 = MEG6: explicit E6 gradients (Eq. E6_grads);
                             1 = MIG4: implicit IG4 gradients (Eq. IG4_grads), cyclic on periodic
-                            axes, explicit end rows on open lines (reading A33) */
+                            axes, explicit end rows on open lines */
 } orc_params;
 
 typedef struct orc_solver orc_solver;

@@ -155,7 +155,7 @@ struct Phys {
   double alpha_d;            // alpha^D
   double mp_alpha, mp_beta, mp_eps;
   double kfac;               // kappa = mu * kfac, kfac = gamma / ((gamma - 1) Pr)
-  double dt_visc_fac;        // max(4/3, gamma/Pr) of the viscous time-step bound (reading A20)
+  double dt_visc_fac;        // max(4/3, gamma/Pr) of the viscous time-step bound
   int viscous, sutherland;
 };
 
@@ -273,7 +273,7 @@ GBR_HD double stencil_D_prod(const double* a, const double* b, long long e, long
 
 // ---------------------------------------------------------------------------
 // App. C on a wall-bounded (closed) axis of n cells, used for every cell of such an axis:
-// f' second-order one-sided at the end cells, fourth-order biased next to them (A22's index),
+// f' second-order one-sided at the end cells, fourth-order biased next to them (the printed stencil shifted back by one index),
 // fourth-order central third, E6 inside; f'' one-sided from f' at the two end cells, the
 // interior formula elsewhere; interface values: the wall interfaces take the boundary cell's
 // own state, the interfaces between the first (last) two cells the inner cell's state, the
@@ -645,7 +645,7 @@ GBR_HD void body_prim(const RhsArgsT<R>& A, int i, int j, int k) {
 // the primitives of its source cell found axis by axis -- periodic wrap, zero-gradient clamp,
 // slip-wall mirror, or the x-low inflow data -- which is exactly what the axis-by-axis ghost
 // copies of body_halo produce (corners included), with the same arithmetic per value.  A slip
-// wall (reading A36) mirrors cell g - 1 into ghost layer g and reflects the velocity about the
+// wall mirrors cell g - 1 into ghost layer g and reflects the velocity about the
 // unit normal of the wall interface; several walls reflect in axis order, each normal taken at
 // the cross-section the axis-by-axis filling sees (earlier axes' coordinates clamped to the
 // cells, later axes' at the source cell).
@@ -1221,7 +1221,7 @@ GBR_HD void face_unlimited(const RhsArgsT<R>& A, int d, int i, int j, int k, Fac
   C.inn = grsqrt(nn2);
   #pragma unroll
   for (int a = 0; a < ND; ++a) C.nu[a] = C.nh[a] * C.inn;
-  // face state of the eigenvectors: mean of rho and p of cells i, i+1 (reading A6)
+  // face state of the eigenvectors: mean of rho and p of cells i, i+1
   const R rb = R(0.5) * (P[pp[1]] + P[pp[2]]);
   const R pb = gfma(R(0.5), P[(NV - 1) * PC + pp[1]] + P[(NV - 1) * PC + pp[2]], A.pref_r);
   // a = sqrt(gamma p / rho): with t = 1/sqrt(gamma p rho), rho a = gamma p rho t, 1/(rho a) = t,
@@ -1339,7 +1339,7 @@ GBR_HD void face_flux(const RhsArgsT<R>& A, int d, int i, int j, int k, const Fa
   if (VISC) {
     // Sec. 5.2 alpha-damping on [u.., T].  gc2[v][e] = 2 d(phi_v)/d(xi_e) at the interface:
     // Eq. (AD-eqn1) along the sweep, the sum of the two cells' gradients across it (reading
-    // A11); the factor 1/2 is folded into mu, lambda and kappa below.
+    // the paper is silent on them); the factor 1/2 is folded into mu, lambda and kappa below.
     R gc2[ND + 1][ND];
     R phif[ND + 1];
     #pragma unroll
@@ -1578,7 +1578,7 @@ GBR_HD bool body_update(const UpdArgsT<R>& U, int i, int j, int k) {
 }
 
 // App. B: per-cell min over directions of 1/(|U| + c |grad xi|), plus the
-// viscous bound of reading A20.
+// viscous bound 1 / (nu_eff |grad xi|^2), nu_eff = max(4/3, gamma/Pr) mu / rho.
 struct DtArgs {
   Layout L;
   Phys ph;

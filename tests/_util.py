@@ -5,7 +5,7 @@ from paper_2303_10785_b300 import inputs as I
 
 
 def cancellation_scale(orc, q):
-    """Per conserved component: max over cells of J * sum_d (|G_{+1/2}| + |G_{-1/2}|) (reading A27)."""
+    """Per conserved component: max over cells of J * sum_d (|G_{+1/2}| + |G_{-1/2}|)."""
     nd = orc.nd
     _, det = orc.cell_metrics()
     acc = np.zeros(q.shape)

@@ -34,7 +34,7 @@ def _built():
 
 def test_dynamic_mesh_256_five_hundred_steps_fp64_and_mixed():
     # FP64: within 1e-10 after 100 steps; later, single cells where the App. E test resolves at
-    # round-off (reading A32) differ by up to ~1e-9 (measured 1.2e-9 at step 475) while the L1
+    # round-off differ by up to ~1e-9 (measured 1.2e-9 at step 475) while the L1
     # difference stays at round-off (4.6e-13 at step 500).  Mixed: within 1e-5 throughout.
     n, dt, steps = 256, 0.004, 500
     m = I.motion_dynamic_2d(n=n, L=10.0, amp=0.1)

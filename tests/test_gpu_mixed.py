@@ -9,7 +9,7 @@ hold p - p_ref (p_ref a pressure of the initial state, so that FP32 does not spe
 digits on the O(1/M^2) mean pressure), and the HLLC star correction S (Q*K - QK) is
 formed with (S* - U) factored out (no difference of two O(rho) states multiplied by S ~ c).
 Without them the error grows like 1/M.  Tolerances:
-* right-hand sides: 2e-6 of the cancellation scale (reading A27) -- about 30 FP32 ulps;
+* right-hand sides: 2e-6 of the cancellation scale -- about 30 FP32 ulps;
   the largest observed is ~2e-7, the same from M = 0.02 to M = 0.5;
 * states after many steps: L-infinity 1e-5 relative to max |Q| per component;
 * freestream: right-hand side 1e-6 of the cancellation scale, velocity 1e-6 of

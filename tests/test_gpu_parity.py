@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
 
 Tolerances (FP64): right-hand sides within 1e-12 of the cancellation scale of
-each conserved component (reading A27: the flux-difference scale, since the
+each conserved component (the flux-difference scale, since the
 freestream RHS is ~0); states within 1e-12 (relative to max |Q| per component)
 after one RK3 stage/step and 1e-10 after 100 steps of a smooth case.  Sizes are
 ragged (not multiples of the 128/256-thread blocks) and span many blocks.
@@ -457,7 +457,7 @@ def test_minimum_periodic_size():
 def test_nonphysical_reconstructed_states_match_oracle():
     # a sharp Sod slab drawn on the jittered centroids of a 28-degree skewed 378^2 mesh: rows that
     # cross the jump hold a cell-to-cell sawtooth, where the App. E bounds leave reconstructed
-    # states with negative density and pressure (reading A37); the sound speed must be the
+    # states with negative density and pressure; the sound speed must be the
     # formula's sqrt(gamma p / rho) there, as in the oracle
     n = (378, 378)
     case = I.case_params(2, n)

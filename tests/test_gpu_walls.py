@@ -1,5 +1,5 @@
-"""GPU: wall-bounded grids without ghost nodes (App. C metrics, reading A35) and slip walls
-(reading A36) against the oracle: metrics, right-hand sides (1e-12 of the cancellation scale),
+"""GPU: wall-bounded grids without ghost nodes (App. C metrics) and slip walls
+ against the oracle: metrics, right-hand sides (1e-12 of the cancellation scale),
 steps (1e-12), the mixed path (2e-5), and a batch member equal to the same grid alone."""
 import numpy as np
 import pytest

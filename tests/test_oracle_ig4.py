@@ -2,11 +2,11 @@
 
 IG4 is the compact implicit scheme
     alpha f'_{i-1} + f'_i + alpha f'_{i+1} = (2 + alpha)/3 (f_{i+1} - f_{i-1}) + (4 alpha - 1)/12 (f_{i+2} - f_{i-2})
-(read with differences, reading A2).  Pinned by what fixes it independently of the oracle's
+(read with differences).  Pinned by what fixes it independently of the oracle's
 solver: its exact response to Fourier modes on a periodic line (the modified wavenumber of
 the scheme, derived by inserting e^{i theta j}), a dense solve of the circulant system with
 numpy, exactness for quadratics on an open line (every row -- the explicit end rows of reading
-A33 and the IG4 rows -- is exact for them), fourth-order convergence, and, for the whole MIG4
+the end rows and the IG4 rows -- is exact for them), fourth-order convergence, and, for the whole MIG4
 right-hand side, freestream preservation and the fourth-order entropy-wave RHS.
 """
 import math

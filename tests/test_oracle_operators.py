@@ -3,8 +3,8 @@
 The paper prints (Sec. 6, freestream proof) the composite stencil of the
 averaged MEG6 interface derivative, 2282, -546, 89, -3, -1 over 2880, and the
 leading/trailing terms of the triple composite (xi_x)_{i+1/2} - (xi_x)_{i-1/2}
-over 23887872000 = 2880^3.  Reproducing them pins the E6 sign reading (A1), the
-1/12 van Leer factor (A3), the proof-sign reading (A5), the assembly of the
+over 23887872000 = 2880^3.  Reproducing them pins the E6 sign reading, the
+1/12 van Leer factor, the proof-sign reading, the assembly of the
 conservative metrics (Eq. GCL_metrics) and the interface interpolation.
 """
 import numpy as np

@@ -1,5 +1,5 @@
-"""Oracle pins of wall-bounded grids: App. C metrics (no ghost nodes, reading A35) and the slip
-wall (reading A36).
+"""Oracle pins of wall-bounded grids: App. C metrics (no ghost nodes) and the slip
+wall.
 
 * The App. C derivative is exact for linear data and second order at the walls (App. C calls its
   formulas low order); affine grids get exact metrics.
