@@ -601,22 +601,25 @@ __global__ void k_dt_f32(DtArgs D, float* mh32, float* mt32, float* jac32, Box b
 
 template <int ND, class R = double>
 __global__ void k_dt(DtArgs D, Box b, unsigned long long* minbits) {
+  // the minimum is taken in the path's type (exact: conversion to FP64 is monotone and exact),
+  // and converted once per block -- on the mixed path no FP64-pipe work per cell but the state's
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double v = 1.0e300;
+  R v = R(HUGE_VAL);
   if (t < box_size(b)) {
     int i, j, k;
     box_coord(b, t, i, j, k);
-    v = body_dt<ND, R>(D, i, j, k);
+    v = body_dt_r<ND, R>(D, i, j, k);
   }
+  // fmin (fminf for FP32, on the ALU pipe) passes over a NaN of a broken state as before
   for (int off = 16; off > 0; off >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, off));
-  __shared__ double wmin[kBlock / 32];
+  __shared__ R wmin[kBlock / 32];
   if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x < 32) {
-    double w = (threadIdx.x < blockDim.x / 32) ? wmin[threadIdx.x] : 1.0e300;
+    R w = (threadIdx.x < blockDim.x / 32) ? wmin[threadIdx.x] : R(HUGE_VAL);
     for (int off = 16; off > 0; off >>= 1) w = fmin(w, __shfl_xor_sync(0xffffffffu, w, off));
     // positive doubles order like their bit patterns
-    if (threadIdx.x == 0) atomicMin(minbits, (unsigned long long)__double_as_longlong(w));
+    if (threadIdx.x == 0) atomicMin(minbits, (unsigned long long)__double_as_longlong(fmin(1.0e300, double(w))));
   }
 }
 

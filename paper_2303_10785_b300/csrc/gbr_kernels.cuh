@@ -1605,7 +1605,7 @@ GBR_HD void body_dt_f32(const DtArgs& D, float* mh32, float* mt32, float* jac32,
 }
 
 template <int ND, class R = double>
-GBR_HD double body_dt(const DtArgs& D, int i, int j, int k) {
+GBR_HD R body_dt_r(const DtArgs& D, int i, int j, int k) {
   // evaluated in the path's type R (the mixed path's FP32 time step differs from the FP64 one by
   // FP32 round-off, far below the CFL number's own slack)
   constexpr int NV = ND + 2;
@@ -1648,7 +1648,13 @@ GBR_HD double body_dt(const DtArgs& D, int i, int j, int k) {
     worst = gmax(worst, gabs(Uc) + cs * gsqrt(g2));
     if (ph.viscous) worst = gmax(worst, nu_eff * g2);
   }
-  return gmin(1.0e300, double(R(1) / worst));
+  return R(1) / worst;  // +inf where nothing bounds the step
+}
+
+// the same as an FP64 number capped at 1e300 (the reduction's neutral value)
+template <int ND, class R = double>
+GBR_HD double body_dt(const DtArgs& D, int i, int j, int k) {
+  return gmin(1.0e300, double(body_dt_r<ND, R>(D, i, j, k)));
 }
 
 }  // namespace gbr
