@@ -145,24 +145,25 @@ __global__ void __launch_bounds__(kBlock, kStreamBlocks) kb_update(const BatchJo
 
 template <int ND, class R>
 __global__ void __launch_bounds__(kBlock) kb_dt(const BatchJob<R>* jobs, const WorkItem* items, int n, int total) {
-  __shared__ double wmin[kBlock / 32];
+  // the minimum in the path's type and one conversion per block, as in k_dt
+  __shared__ R wmin[kBlock / 32];
   for_work(items, n, total, [&](const WorkItem& it, int lb) {
     const BatchJob<R>& J = jobs[it.job];
     const long long t = (long long)lb * blockDim.x + threadIdx.x;
-    double v = 1.0e300;
+    R v = R(HUGE_VAL);
     if (t < box_size(J.inner)) {
       int i, j, k;
       box_coord(J.inner, t, i, j, k);
-      v = body_dt<ND, R>(J.D, i, j, k);
+      v = body_dt_r<ND, R>(J.D, i, j, k);
     }
     for (int off = 16; off > 0; off >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, off));
     __syncthreads();  // wmin of the previous block of this CTA has been read
     if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = v;
     __syncthreads();
     if (threadIdx.x < 32) {
-      double w = (threadIdx.x < blockDim.x / 32) ? wmin[threadIdx.x] : 1.0e300;
+      R w = (threadIdx.x < blockDim.x / 32) ? wmin[threadIdx.x] : R(HUGE_VAL);
       for (int off = 16; off > 0; off >>= 1) w = fmin(w, __shfl_xor_sync(0xffffffffu, w, off));
-      if (threadIdx.x == 0) atomicMin(J.dtbits, (unsigned long long)__double_as_longlong(w));
+      if (threadIdx.x == 0) atomicMin(J.dtbits, (unsigned long long)__double_as_longlong(fmin(1.0e300, double(w))));
     }
   });
 }
