@@ -105,11 +105,11 @@ __global__ void k_prim(RhsArgsT<R> A, Box b) {
 // per SM, 32 registers): the mixed 128^3 TGV step 4.7 % faster than at 42 / 54 registers.
 constexpr int kStreamBlocks = 8;
 
-template <int ND, class R = double>
+template <int ND, class R = double, bool SPECIAL = true>
 __global__ void __launch_bounds__(kBlock, kStreamBlocks) k_prim_halo(RhsArgsT<R> A, const double* q,
                                                                      const float* dq, Box b) {
   BOX_THREAD(b);
-  body_prim_halo<ND>(A, q, dq, i, j, k);
+  body_prim_halo<ND, R, SPECIAL>(A, q, dq, i, j, k);
 }
 
 template <int ND, class R = double>
@@ -1177,7 +1177,12 @@ gbr_status run_rhs_nd(gbr_ctx* c, const double* qs, const double* q0, double* ou
   const Box bi = B.inner;
   // primitives and all ghost layers in one pass over the padded box
   const Box pad = pad_box(L, H, H);
-  k_prim_halo<ND, R><<<grid_of(pad, kBlock), kBlock, 0, st>>>(A, qs, dq_in, pad);
+  bool special = false;  // an inflow or wall boundary on some non-periodic axis
+  for (int d = 0; d < ND; ++d)
+    if (!L.per[d])
+      special |= A.bc[d][0] == 2 || A.bc[d][0] == 3 || A.bc[d][1] == 3;
+  if (special) k_prim_halo<ND, R, true><<<grid_of(pad, kBlock), kBlock, 0, st>>>(A, qs, dq_in, pad);
+  else k_prim_halo<ND, R, false><<<grid_of(pad, kBlock), kBlock, 0, st>>>(A, qs, dq_in, pad);
   CKL("k_prim_halo");
   unsigned g1 = 0, g2 = 0;
   for (int e = 0; e < ND; ++e) {

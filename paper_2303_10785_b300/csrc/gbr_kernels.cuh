@@ -649,7 +649,9 @@ GBR_HD void body_prim(const RhsArgsT<R>& A, int i, int j, int k) {
 // unit normal of the wall interface; several walls reflect in axis order, each normal taken at
 // the cross-section the axis-by-axis filling sees (earlier axes' coordinates clamped to the
 // cells, later axes' at the source cell).
-template <int ND, class R>
+// SPECIAL = false: no inflow or wall boundary on this grid (every ghost cell is a periodic or
+// zero-gradient copy), so the FP64 ghost path is left out of the instantiation (registers)
+template <int ND, class R, bool SPECIAL = true>
 GBR_HD void body_prim_halo(const RhsArgsT<R>& A, const double* q, const float* dq, int i, int j, int k) {
   constexpr int NV = ND + 2;
   const Layout& L = A.L;
@@ -685,7 +687,7 @@ GBR_HD void body_prim_halo(const RhsArgsT<R>& A, const double* q, const float* d
   }
   const long long p = pidx(L, i, j, k);
   const long long PC = L.pcount;
-  if (!inflow && !(wall[0] | wall[1] | wall[2])) {
+  if (!SPECIAL || (!inflow && !(wall[0] | wall[1] | wall[2]))) {
     prim_store<ND>(A, q, dq, cidx(L, c[0], c[1], c[2]), p);
     return;
   }
