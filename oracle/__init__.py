@@ -7,7 +7,7 @@ no code with the CUDA library.  The only module both sides use is
 ``paper_2303_10785_b300.inputs`` (seeded grids and initial states).
 
 Parity unpinned: the face state of the eigenvectors, the MP-limiter constants, the
-Sutherland constants, the viscous time-step bound and the jet boundary/sponge forms.
+value of the jet's Sutherland constant S/T_ref and the jet boundary/sponge forms.
 """
 import ctypes
 import os
@@ -69,6 +69,8 @@ def _lib(counting=False):
     lib.orc_primitives.argtypes = [vp, _P, _P]
     lib.orc_dt.argtypes = [vp, _P, ctypes.c_double]
     lib.orc_dt.restype = ctypes.c_double
+    lib.orc_viscosity.argtypes = [vp, ctypes.c_double]
+    lib.orc_viscosity.restype = ctypes.c_double
     lib.orc_rk3.argtypes = [vp, _P, ctypes.c_double, ctypes.POINTER(_P), ctypes.POINTER(_P)]
     lib.orc_op1d.argtypes = [ctypes.c_int, ctypes.c_int, _P, _P]
     lib.orc_eigen.argtypes = [ctypes.c_int, _P, ctypes.c_double, ctypes.c_double, ctypes.c_double, _P, _P]
@@ -225,6 +227,10 @@ class Oracle:
     def dt(self, q, cfl):
         q = self._state(q)
         return float(self.lib.orc_dt(self.h, _ptr(q), float(cfl)))
+
+    def viscosity(self, T):
+        """Dynamic viscosity mu(T) (Sec. 2) of this grid's parameters."""
+        return float(self.lib.orc_viscosity(self.h, float(T)))
 
     def rk3(self, q, dt, stage_nodes=None, stage_vel=None):
         q = self._state(q).copy()

@@ -26,9 +26,10 @@
  *
  * Where the paper is silent or garbled, the reading taken is stated beside the code that uses it.
  * Parity unpinned (oracle-to-GPU parity only): the face state used for the
- * eigenvectors, the MP-limiter constants alpha = beta = 4, the
- * Sutherland constants, the viscous time-step term and the jet
- * boundary/sponge forms.
+ * eigenvectors, the MP-limiter constants alpha = beta = 4, the value of the
+ * Sutherland constant S/T_ref of the jet, and the jet boundary/sponge forms.
+ * (The time step, heat conduction and Sutherland's formula are pinned to closed
+ * forms by tests/test_oracle_closures.py.)
  */
 #include "orc.h"
 
@@ -1277,6 +1278,8 @@ double orc_dt(orc_solver* s, const double* q, double cfl) {
       }
   return Dbl(cfl * best);
 }
+
+double orc_viscosity(const orc_solver* s, double T) { return Dbl(s->viscosity(real(T))); }
 
 // App. B: three-stage SSP (TVD) Runge-Kutta, advancing Q with L(Q) = J (Res - (1/J)_t Q).
 int orc_rk3(orc_solver* s, double* q, double dt, const double* const* stage_nodes, const double* const* stage_vel) {

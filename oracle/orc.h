@@ -73,6 +73,8 @@ int  orc_residual(orc_solver* s, const double* q, double* res /*[nv][cells]*/);
 int  orc_face_flux(orc_solver* s, const double* q, int d, double* g /*[nv][faces]*/);
 int  orc_primitives(orc_solver* s, const double* q, double* prim /*[nv][cells]*/);
 double orc_dt(orc_solver* s, const double* q, double cfl);
+/* Sec. 2: dynamic viscosity mu(T) of the solver's parameters (T = p/rho units). */
+double orc_viscosity(const orc_solver* s, double T);
 /* One SSP-RK3 step in place.  stage_nodes/stage_vel: NULL for a static mesh,
    else 3 node sets (and velocities) at t, t+dt, t+dt/2. */
 int  orc_rk3(orc_solver* s, double* q, double dt,
