@@ -16,6 +16,14 @@ A step is one full SSP-RK3 step (three right-hand sides, stage combinations and,
 for tgv, the time step); the working sets (~3 GB, ~20 GB) are far larger than
 L2, so no flush is needed between steps.
 
+The default run (tgv, FP64, 128^3, one GPU) also measures, beside the headline and
+under the same rules: "mixed" (the same workload on the mixed-precision path, with
+its state against the FP64 path's after the same steps), "jet" (the 480 x 170 x 170
+jet-like box, FP64) and "serving" (a bounded 32-job sample of the serving stream,
+per-job FP64 against the continuous-batching server); --no-extras skips them.  The
+arithmetic roofline's peak is the FMA throughput measured on the same GPU first
+(gbr_alu_peak), with the unit-count figure and the nominal one beside it.
+
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload tgv|jet]
 Under torchrun (N > 1) each rank advances its own copy of the workload (the
 jobs are independent: replicas, weak scaling); rank 0 prints one JSON line.
@@ -39,12 +47,15 @@ CFL = 0.2
 JET_DT = 2e-3
 JET_SEED = 2303
 METRIC = "cell-RK-stage updates/s"
-# FP64 peak used as the roofline denominator of this ALU-bound path: 148 SMs x
-# 2 DFMA/clk/SM x 2 flop x 2.032 GHz = 1.20 TFLOP/s nominal at the maximum SM
-# clock; the pool's nominal FP64 figure, 1.25 TFLOP/s, is the one used.
-FP64_PEAK_TFLOPS = 1.25
-# FP32 FFMA peak, nominal: 148 SMs x 128 FMA/clk x 2 flop x 2.032 GHz
-FP32_PEAK_TFLOPS = 77.0
+# Arithmetic peaks of this ALU-bound path.  The roofline's denominator is the FMA throughput
+# measured live on the GPU that runs the kernels (gbr_alu_peak, before the timed region); beside it
+# the figures derived from unit counts and the maximum SM clock, and the nominal FP64 figure:
+# FP64 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz = 1.203 TFLOP/s (nominal 1.25),
+# FP32 148 SMs x 128 FFMA/clk x 2 flop x 2.032 GHz = 77.0 TFLOP/s.
+SM_MAX_GHZ = 2.032
+FP64_DERIVED_TFLOPS = 148 * 2 * 2 * SM_MAX_GHZ / 1e3
+FP32_DERIVED_TFLOPS = 148 * 128 * 2 * SM_MAX_GHZ / 1e3
+FP64_NOMINAL_TFLOPS = 1.25
 
 
 def measured_hbm_gbs():
@@ -336,23 +347,29 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
-def run_gpu(args, wl):
+def measure_peaks():
+    """FP64 and FP32 FMA throughput of this GPU (TFLOP/s), measured by the library's probe."""
+    from paper_2303_10785_b300 import gbr
+
+    f64, ms64 = gbr.alu_peak("fp64")
+    f32, ms32 = gbr.alu_peak("mixed")
+    return {"fp64_tflops": f64, "fp32_tflops": f32, "probe_ms": {"fp64": ms64, "fp32": ms32},
+            "fp64_derived_tflops": FP64_DERIVED_TFLOPS, "fp32_derived_tflops": FP32_DERIVED_TFLOPS,
+            "fp64_nominal_tflops": FP64_NOMINAL_TFLOPS}
+
+
+def measure(wl, dev, steps, warmup, e2e_steps, peaks, world, local, keep_state=False):
+    """Time `steps` SSP-RK3 steps of `wl` device-resident (after `warmup` steps), then `e2e_steps`
+    steps end to end through the C ABI from pinned host memory; the interface kernel's roofline
+    and the whole step's.  Returns a dict (the final device-resident state under "state" if asked)."""
     import torch
 
     from paper_2303_10785_b300 import gbr
 
-    world, rank, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     solver = gbr.Solver(wl.case, wl.nodes, device=dev)
     stream = solver.stream
     cells = wl.cells
-    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 10))
-    wl.attach(solver, args.warmup + args.steps + 2 + e2e_steps)
+    wl.attach(solver, warmup + steps + 2 + e2e_steps)
 
     def barrier():
         if world > 1:
@@ -363,7 +380,7 @@ def run_gpu(args, wl):
     # ---- device-resident throughput
     solver.set_state(wl.q)
     step = 0
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         wl.step(solver, step)
         step += 1
     solver.sync()
@@ -374,7 +391,7 @@ def run_gpu(args, wl):
     ev1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clocks:
         ev0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             wl.step(solver, step)
             step += 1
         ev1.record(stream)
@@ -384,10 +401,14 @@ def run_gpu(args, wl):
     face_ms, face_launches, launches = solver.profile(False)
     solver.sync()
     ms = dist_max(ms, dev)
-    value = world * 3 * cells * args.steps / (ms / 1e3)
+    value = world * 3 * cells * steps / (ms / 1e3)
+    out = {"value": value, "ms": ms, "launches": launches, "clocks": clocks.summary(),
+           "workspace_bytes": solver.workspace_bytes}
+    if keep_state:
+        out["state"] = solver.get_state()
 
     # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
-    e2e = None
+    out["e2e"] = None
     if e2e_steps:
         h_in = torch.from_numpy(np.ascontiguousarray(wl.q)).pin_memory()
         h_out = torch.empty_like(h_in).pin_memory()
@@ -412,8 +433,9 @@ def run_gpu(args, wl):
         solver.sync()
         e2e_s = dist_max(time.perf_counter() - t0, dev)
         nbytes = int(wl.q.size * 8)
-        e2e = {"value": world * 3 * cells * e2e_steps / e2e_s, "unit": METRIC, "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes, "steps": e2e_steps}
+        out["e2e"] = {"value": world * 3 * cells * e2e_steps / e2e_s, "unit": METRIC, "h2d_bytes_per_step": nbytes,
+                      "d2h_bytes_per_step": nbytes, "steps": e2e_steps}
+    solver.close()
 
     # ---- roofline of the interface-flux kernel and of the whole step
     counts = load_flops()[wl.flops_key]
@@ -421,7 +443,8 @@ def run_gpu(args, wl):
     faces_per_launch = wl.faces_per_rhs / 3.0
     avg_launch_s = (face_ms / 1e3) / max(face_launches, 1)
     mixed = wl.precision == "mixed"
-    fp_peak = FP32_PEAK_TFLOPS if mixed else FP64_PEAK_TFLOPS
+    fp_peak = peaks["fp32_tflops"] if mixed else peaks["fp64_tflops"]
+    fp_derived = FP32_DERIVED_TFLOPS if mixed else FP64_DERIVED_TFLOPS
     alg_bytes = face_alg_bytes(wl)
     t_alu = fl / (fp_peak * 1e12)
     t_hbm = alg_bytes / (HBM_PEAK_GBS * 1e9)
@@ -432,8 +455,12 @@ def run_gpu(args, wl):
         achieved = fl * faces_per_launch / avg_launch_s / 1e12
         roofline = dict({"bound": "alu", "achieved": achieved, "peak": fp_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp_peak}, **common)
-        roofline["peak_note"] = ("FP32 FFMA nominal from unit counts and the maximum SM clock" if mixed else
-                                 "FP64 derived from the pool's unit counts and clock (nominal 1.25 TFLOP/s)")
+        roofline["peak_note"] = ((
+            "FP32" if mixed else "FP64") + " FMA throughput measured on this GPU by gbr_alu_peak (of measured)")
+        roofline["peak_derived"] = fp_derived
+        roofline["frac_of_derived"] = achieved / fp_derived
+        if not mixed:
+            roofline["peak_nominal"] = FP64_NOMINAL_TFLOPS
     else:
         achieved = alg_bytes * faces_per_launch / avg_launch_s / 1e9
         roofline = dict({"bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
@@ -449,48 +476,85 @@ def run_gpu(args, wl):
     per_gpu = value / world
     t_flop = f_cell / (fp_peak * 1e12)
     t_byte = BYTES_PER_CELL_STAGE_3D / (HBM_PEAK_GBS * 1e9)
-    step_roofline = {"flops_per_cell_stage": f_cell, "bytes_per_cell_stage": BYTES_PER_CELL_STAGE_3D,
-                     "bound": "alu" if t_flop >= t_byte else "hbm", "achieved_tflops": f_cell * per_gpu / 1e12,
-                     "frac": max(t_flop, t_byte) * per_gpu, "fp_peak_tflops": fp_peak,
-                     "hbm_peak_gbs": HBM_PEAK_GBS}
+    out["roofline"] = roofline
+    out["step_roofline"] = {"flops_per_cell_stage": f_cell, "bytes_per_cell_stage": BYTES_PER_CELL_STAGE_3D,
+                            "bound": "alu" if t_flop >= t_byte else "hbm",
+                            "achieved_tflops": f_cell * per_gpu / 1e12, "frac": max(t_flop, t_byte) * per_gpu,
+                            "fp_peak_tflops": fp_peak, "hbm_peak_gbs": HBM_PEAK_GBS}
+    return out
+
+
+def sub_record(wl, r, steps):
+    """A workload measured beside the headline: its value, step time, end-to-end value and rooflines."""
+    return {"workload": wl.name, "config": wl.config, "precision": wl.precision, "value": r["value"],
+            "unit": METRIC, "steps": steps, "ms_per_step": r["ms"] / steps, "e2e": r["e2e"],
+            "gpu_launches": r["launches"], "roofline": r["roofline"], "step_roofline": r["step_roofline"],
+            "clocks": r["clocks"]}
+
+
+def run_gpu(args, wl):
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peaks = measure_peaks()
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 10))
+    extras = world == 1 and not args.no_extras and wl.kind == "tgv" and wl.precision == "fp64" \
+        and wl.scheme == "meg6" and args.edge == N_CELLS_EDGE
+    r = measure(wl, dev, args.steps, args.warmup, e2e_steps, peaks, world, local, keep_state=extras)
     if rank != 0:
-        solver.close()
         return
     line = {
-        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": r["value"], "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if wl.precision == "mixed" else "f64", "data": "synthetic",
         "config": dict({"workload": wl.name}, **wl.config, precision=wl.precision, gradients=wl.scheme,
                        parallelism=f"replicas{world}",
-                       l2=f"workspace {solver.workspace_bytes / 1e9:.1f} GB >> 126 MB L2, no flush"),
-        "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "step_roofline": step_roofline,
-        "clocks": clocks.summary(),
+                       l2=f"workspace {r['workspace_bytes'] / 1e9:.1f} GB >> 126 MB L2, no flush"),
+        "e2e": r["e2e"], "gpu_launches": r["launches"], "roofline": r["roofline"],
+        "step_roofline": r["step_roofline"], "clocks": r["clocks"], "alu_peaks": peaks,
     }
+    if extras:
+        # the same 128^3 Taylor-Green vortex on the mixed-precision path, and its state after the same
+        # number of steps against the FP64 path's (the tests bound both against the FP64 oracle)
+        wm = Workload("tgv", args.edge, "mixed", "meg6")
+        rm = measure(wm, dev, args.steps, args.warmup, e2e_steps, peaks, world, local, keep_state=True)
+        rec = sub_record(wm, rm, args.steps)
+        a, b = rm.pop("state"), r.pop("state")
+        nv = b.shape[0]
+        scale = np.abs(b).reshape(nv, -1).max(axis=1)
+        scale[1:nv - 1] = scale[1:nv - 1].max()
+        rec["linf_vs_fp64_path"] = float((np.abs(a - b).reshape(nv, -1).max(axis=1) / scale).max())
+        rec["linf_note"] = (f"state after {args.warmup + args.steps} CFL {CFL} steps against the FP64 path's, "
+                            "max |diff| / max |Q| per component")
+        rec["speedup_vs_fp64"] = rm["value"] / r["value"]
+        line["mixed"] = rec
+        # the 13.9 M-cell jet (FP64), the paper's largest grid shape, with its own rooflines
+        wj = Workload("jet")
+        js = min(args.steps, 10)
+        rj = measure(wj, dev, js, 3, min(e2e_steps, 3), peaks, world, local)
+        line["jet"] = sub_record(wj, rj, js)
+        # a bounded sample of the serving stream: per-job FP64 against the continuous-batching server
+        line["serving"] = serving_sample(args, local)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)
-    solver.close()
 
 
-def run_serving(args):
-    """The serving stream: jobs of mixed kinds, sizes and precisions with Poisson arrivals at an
-    offered load of `--load` x the measured FP64 per-job capacity, served (1) by the plain FP64
-    per-job form (one job at a time through gbr_rk_step), (2) by the continuous-batching server
-    with each job in its own precision (the line's value) and (3) by the server with every job in
-    mixed precision; aggregate cell-RK-stage updates/s and time-to-N-steps p50/p99 of each."""
+def serve_stream(specs, load, pool_gb, slots, chunk, local):
+    """Serve one stream three ways: (1) the plain FP64 per-job form (one job at a time through
+    gbr_rk_step), (2) the continuous-batching server with each job in its own precision and (3) the
+    server with every job in mixed precision.  Arrivals at `load` x the measured FP64 per-job
+    capacity (0: a burst, every job at t = 0).  Returns the three jobs lists and their statistics."""
     import torch
 
     from paper_2303_10785_b300 import inputs as I
     from paper_2303_10785_b300 import serving
-
-    world, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl")
-    # each rank serves its own stream of --jobs jobs (independent jobs: weak scaling)
-    specs = I.serving_stream(args.jobs, seed=args.seed + rank, rate=1.0)
 
     def jobs_at(rate, precision=None):
         out = []
@@ -518,14 +582,13 @@ def run_serving(args):
         s.close()
     capacity = work / secs
     mean_work = float(np.mean([I.serving_job_work(sp) for sp in specs]))
-    # --load 0: a burst (every job arrives at t = 0), which measures the capacity of each form
-    rate = args.load * capacity / mean_work if args.load > 0 else float("inf")
+    rate = load * capacity / mean_work if load > 0 else float("inf")
 
     base = jobs_at(rate, "fp64")
     serving.run_serial(base)
     st_base = serving.latency_stats(base)
-    pool = int(args.pool_gb * 1e9)
-    srv = serving.Server(pool, max_active=args.slots, chunk_steps=args.chunk)
+    pool = int(pool_gb * 1e9)
+    srv = serving.Server(pool, max_active=slots, chunk_steps=chunk)
     mix = jobs_at(rate)
     with ClockSampler(local) as clocks:
         srv.run(mix)
@@ -534,30 +597,81 @@ def run_serving(args):
     tuning = srv.batch.tuning()
     peak = {"active": srv.peak_active, "pool_bytes": srv.peak_pool}
     srv.close()
-    # the same stream with every job in mixed precision
-    srv = serving.Server(pool, max_active=args.slots, chunk_steps=args.chunk)
+    srv = serving.Server(pool, max_active=slots, chunk_steps=chunk)
     allmix = jobs_at(rate, "mixed")
     srv.run(allmix)
     st_allmix = serving.latency_stats(allmix)
     launches_allmix = srv.batch.info()["launches"]
     srv.close()
     errors = [j.error for j in mix + base + allmix if j.error]
+    return {"base": base, "mix": mix, "allmix": allmix, "st_base": st_base, "st_mix": st_mix,
+            "st_allmix": st_allmix, "capacity": capacity, "rate": rate, "tuning": tuning, "peak": peak,
+            "errors": errors, "launches": info["launches"] + launches_allmix, "clocks": clocks.summary()}
+
+
+def serving_summary(r, st_base, st_mix, st_allmix):
+    return {"batched_mixed": st_mix, "batched_all_mixed": st_allmix, "per_job_fp64": st_base,
+            "fp64_capacity_per_job": r["capacity"],
+            "all_mixed_throughput_ratio": st_allmix["cell_rk_stage_updates_per_s"]
+            / st_base["cell_rk_stage_updates_per_s"],
+            "arrival_rate_jobs_per_s": r["rate"] if r["rate"] != float("inf") else "burst",
+            "throughput_ratio": st_mix["cell_rk_stage_updates_per_s"] / st_base["cell_rk_stage_updates_per_s"],
+            "peak": r["peak"], "tuning": r["tuning"], "errors": r["errors"]}
+
+
+def serving_sample(args, local):
+    """The default line's serving record: a bounded sample of the serving stream (32 jobs, 2D edges
+    32-256, 3D edges 32-64, 50-150 steps, half of them mixed precision) arriving at once, served per
+    job in FP64 and by the continuous-batching server; the full stream is --workload serving."""
+    from paper_2303_10785_b300 import inputs as I
+
+    jobs = 32
+    specs = I.serving_stream(jobs, seed=args.seed, rate=1.0, edge2d=(32, 256), edge3d=(32, 64), steps=(50, 150))
+    r = serve_stream(specs, 0.0, 16.0, 32, 8, local)
+    out = serving_summary(r, r["st_base"], r["st_mix"], r["st_allmix"])
+    out["stream"] = (f"{jobs} jobs, burst, 2D edge 32-256 (vortex, Sod slab), 3D edge 32-64 (Taylor-Green), "
+                     "50-150 steps, FP64 or mixed per job (seed %d)" % args.seed)
+    out["gpu_launches"] = r["launches"]
+    out["clocks"] = r["clocks"]
+    return out
+
+
+def run_serving(args):
+    """The serving stream: jobs of mixed kinds, sizes and precisions with Poisson arrivals at an
+    offered load of `--load` x the measured FP64 per-job capacity, served (1) by the plain FP64
+    per-job form, (2) by the continuous-batching server with each job in its own precision (the
+    line's value) and (3) by the server with every job in mixed precision; aggregate
+    cell-RK-stage updates/s and time-to-N-steps p50/p99 of each."""
+    import torch
+
+    from paper_2303_10785_b300 import inputs as I
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    # each rank serves its own stream of --jobs jobs (independent jobs: weak scaling)
+    specs = I.serving_stream(args.jobs, seed=args.seed + rank, rate=1.0)
+    r = serve_stream(specs, args.load, args.pool_gb, args.slots, args.chunk, local)
+    st_base, st_mix, st_allmix, errors = r["st_base"], r["st_mix"], r["st_allmix"], r["errors"]
 
     def record(jobs, st):
         done = [j for j in jobs if j.finished is not None and j.error is None]
         return {"lat": [j.finished - j.arrival for j in done], "work": float(sum(j.work for j in done)),
                 "makespan": st["makespan_s"]}
 
-    recs = gather_objects({"mix": record(mix, st_mix), "base": record(base, st_base),
-                           "allmix": record(allmix, st_allmix), "errors": errors,
-                           "launches": info["launches"] + launches_allmix})
+    recs = gather_objects({"mix": record(r["mix"], st_mix), "base": record(r["base"], st_base),
+                           "allmix": record(r["allmix"], st_allmix), "errors": errors, "launches": r["launches"]})
     if world > 1:
-        st_mix = merge_serving([r["mix"] for r in recs])
-        st_base = merge_serving([r["base"] for r in recs])
-        st_allmix = merge_serving([r["allmix"] for r in recs])
-        errors = [e for r in recs for e in r["errors"]]
+        st_mix = merge_serving([x["mix"] for x in recs])
+        st_base = merge_serving([x["base"] for x in recs])
+        st_allmix = merge_serving([x["allmix"] for x in recs])
+        errors = [e for x in recs for e in x["errors"]]
     if rank != 0:
         return
+    summ = serving_summary(dict(r, errors=errors), st_base, st_mix, st_allmix)
     line = {
         "metric": METRIC, "value": st_mix["cell_rk_stage_updates_per_s"], "unit": METRIC, "n_gpus": world,
         "steps": None, "warmup": None, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
@@ -565,15 +679,7 @@ def run_serving(args):
         "config": {"workload": f"serving_stream_{args.jobs}_jobs_per_gpu", "seed": args.seed, "offered_load": args.load,
                    "pool_gb": args.pool_gb, "slots": args.slots, "chunk_steps": args.chunk,
                    "l2": "working sets of the large jobs >> 126 MB L2, no flush"},
-        "serving": {"batched_mixed": st_mix, "batched_all_mixed": st_allmix, "per_job_fp64": st_base,
-                    "fp64_capacity_per_job": capacity,
-                    "all_mixed_throughput_ratio": st_allmix["cell_rk_stage_updates_per_s"]
-                    / st_base["cell_rk_stage_updates_per_s"],
-                    "arrival_rate_jobs_per_s": rate if rate != float("inf") else "burst",
-                    "throughput_ratio": st_mix["cell_rk_stage_updates_per_s"]
-                    / st_base["cell_rk_stage_updates_per_s"], "peak": peak, "tuning": tuning,
-                    "errors": errors},
-        "gpu_launches": sum(r["launches"] for r in recs), "clocks": clocks.summary(),
+        "serving": summ, "gpu_launches": sum(x["launches"] for x in recs), "clocks": r["clocks"],
     }
     print(json.dumps(line), flush=True)
 
@@ -598,6 +704,8 @@ def main():
                     help="mixed: FP32 reconstruction and fluxes, FP64 state, metrics, GCL and RK accumulation")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default run only: skip the mixed-precision, jet and serving records beside the headline")
     ap.add_argument("--edge", type=int, default=N_CELLS_EDGE, help="tgv cells per edge (profiling runs use smaller grids)")
     args = ap.parse_args()
     if args.steps is None:

@@ -78,9 +78,9 @@ enum { GBR_GRAD_MEG6 = 0, GBR_GRAD_MIG4 = 1 };
 
 typedef struct {
   int ndim;            /* 2 or 3 */
-  int n[3];            /* cells per axis (n[2] = 1 in 2D) */
+  int n[3];            /* cells per axis, 1 .. 2^24 (n[2] = 1 in 2D) */
   int periodic[3];     /* 1 = periodic axis */
-  int ghost_nodes;     /* node layers supplied beyond each non-periodic side (>= 10), or 0: the
+  int ghost_nodes;     /* node layers supplied beyond each non-periodic side (10 .. 1024), or 0: the
                           non-periodic axes end at the grid's last nodes and their metrics near
                           the ends take the one-sided formulas of App. C (>= 12 cells; static
                           meshes only) */
@@ -214,6 +214,16 @@ gbr_status gbr_get_field(gbr_ctx* c, int which, int dir, double* host_out);
  * every face-flux launch from now on; 0 stops recording.  Out pointers may be NULL. */
 gbr_status gbr_profile(gbr_ctx* c, int enable, double* face_ms, long long* face_launches, long long* launches);
 
+/* Measurement hook (no counterpart in the paper): fused multiply-add throughput
+ * of the current device in TFLOP/s (2 flops per FMA) -- FP64 for precision =
+ * GBR_PREC_FP64, FP32 for GBR_PREC_MIXED -- the denominator of the arithmetic
+ * roofline of the kernels, measured where they run.  One wave of resident
+ * blocks, each thread running 8 independent FMA chains; the shortest of three
+ * launches after a warm-up, timed with CUDA events on `stream` (a
+ * cudaStream_t or NULL).  Synchronous.  tflops, ms (the timed launch's
+ * duration): out pointers, may be NULL.  Errors: EINVAL (precision), ECUDA. */
+gbr_status gbr_alu_peak(int precision, void* stream, double* tflops, double* ms);
+
 /* Self-check of the kernels' bounded waits (no counterpart in the paper).  The
  * MIG4 line solves wait for a TMA tile copy on an mbarrier with a bounded
  * number of polls; when they run out the block sets a sticky device flag and
@@ -245,7 +255,11 @@ gbr_status gbr_check_bounded_wait(gbr_ctx* c, int polls);
  * first call before any stream capture.  Calls share the array and it keeps
  * the last call's contents: calls whose work overlaps on the GPU (other
  * streams, other host threads) race and must be serialised by the caller.
- * Asynchronous on `stream` after the host-to-device copy of the nodes. */
+ * Asynchronous on `stream` after the host-to-device copy of the nodes.
+ * Unlike gbr_sync, this call does not report a non-finite result or a
+ * non-positive density (GBR_ENONFINITE): the device flag for them lives in the
+ * shared array and is never read back, so a caller who needs that check must
+ * test dqdt itself.  GBR_OK means that the work was enqueued. */
 gbr_status gbr_rhs_static(const gbr_params* p, const double* nodes, const double* node_vel, const double* q,
                           double* dqdt, void* stream, char* msg, size_t msg_len);
 

@@ -665,11 +665,17 @@ struct Sizes {
 
 Layout layout_of(const gbr_params* p);
 
+constexpr int kMaxAxisCells = 1 << 24;  // cells along one axis
+constexpr int kMaxGhostNodes = 1024;    // node layers beyond a non-periodic side
+
 bool valid_params(const gbr_params* p, std::string& why) {
   if (!p) { why = "null params"; return false; }
   if (p->ndim != 2 && p->ndim != 3) { why = "ndim must be 2 or 3"; return false; }
+  // bounds before any size arithmetic: padded extents n + 2 * (6 + 10) and node counts stay far inside int
+  if (p->ghost_nodes < 0 || p->ghost_nodes > kMaxGhostNodes) { why = "ghost_nodes out of range"; return false; }
   for (int d = 0; d < p->ndim; ++d) {
     if (p->n[d] < 1) { why = "empty axis"; return false; }
+    if (p->n[d] > kMaxAxisCells) { why = "axis too long"; return false; }
     if (p->periodic[d] && p->n[d] < H) { why = "a periodic axis needs at least 6 cells"; return false; }
     if (!p->periodic[d] && p->ghost_nodes != 0 && p->ghost_nodes < E) {
       why = "a non-periodic axis needs ghost_nodes >= 10, or 0 (walls, App. C metrics)";
@@ -1897,6 +1903,80 @@ gbr_status gbr_profile(gbr_ctx* c, int enable, double* face_ms, long long* face_
   return GBR_OK;
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Fused multiply-add throughput probe (gbr_alu_peak): the denominator of the
+// arithmetic roofline, measured on the device that runs the kernels.  Each
+// thread runs kProbeChains independent FMA chains a = a * x + y with runtime x
+// and y (nothing folds; |x| < 1 keeps every value finite), and stores its sum
+// only if it equals a value no chain produces, so no chain is dead code.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kProbeChains = 8;
+constexpr int kProbeUnroll = 16;
+constexpr int kProbeBlock = 256;
+
+template <class T>
+__global__ void __launch_bounds__(kProbeBlock) k_fma_probe(T x, T y, int iters, T never, T* sink) {
+  T a[kProbeChains];
+#pragma unroll
+  for (int c = 0; c < kProbeChains; ++c) a[c] = T(threadIdx.x + c);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < kProbeUnroll; ++u) {
+#pragma unroll
+      for (int c = 0; c < kProbeChains; ++c) a[c] = fma(a[c], x, y);
+    }
+  }
+  T s = T(0);
+#pragma unroll
+  for (int c = 0; c < kProbeChains; ++c) s += a[c];
+  if (s == never) sink[blockIdx.x] = s;
+}
+
+template <class T>
+gbr_status alu_probe(cudaStream_t st, int iters, double* tflops, double* ms_out) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fma_probe<T>, kProbeBlock, 0) != cudaSuccess)
+    return fail(nullptr, GBR_ECUDA, "alu probe: device query failed");
+  const int blocks = sms * std::max(per_sm, 1);  // one wave: every SM gets the same work
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return fail(nullptr, GBR_ECUDA, "alu probe: event");
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return fail(nullptr, GBR_ECUDA, "alu probe: event"); }
+  const T x = T(0.999), y = T(1.0e-3), never = T(-12345.0);
+  float best = 0.0f;
+  cudaError_t err = cudaSuccess;
+  for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {  // the first launch warms up
+    cudaEventRecord(e0, st);
+    k_fma_probe<T><<<blocks, kProbeBlock, 0, st>>>(x, y, iters, never, nullptr);
+    cudaEventRecord(e1, st);
+    err = cudaEventSynchronize(e1);
+    if (err == cudaSuccess) err = cudaGetLastError();
+    float ms = 0.0f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && err == cudaSuccess && (best == 0.0f || ms < best)) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return fail(nullptr, GBR_ECUDA, std::string("alu probe: ") + cudaGetErrorString(err));
+  const double flops = 2.0 * kProbeChains * kProbeUnroll * (double)iters * (double)blocks * kProbeBlock;
+  if (tflops) *tflops = flops / (best * 1e-3) / 1e12;
+  if (ms_out) *ms_out = best;
+  return GBR_OK;
+}
+}  // namespace
+
+extern "C" {
+
+gbr_status gbr_alu_peak(int precision, void* stream, double* tflops, double* ms) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == GBR_PREC_FP64) return alu_probe<double>(st, 1024, tflops, ms);
+  if (precision == GBR_PREC_MIXED) return alu_probe<float>(st, 32768, tflops, ms);
+  return fail(nullptr, GBR_EINVAL, "precision must be GBR_PREC_FP64 or GBR_PREC_MIXED");
+}
+
 gbr_status gbr_check_bounded_wait(gbr_ctx* c, int polls) {
   if (!c) return fail(nullptr, GBR_EINVAL, "null context");
   if (polls < 1 || polls > kTmaSpin) return fail(c, GBR_EINVAL, "polls out of range");
@@ -2133,6 +2213,10 @@ cudaError_t static_rhs_launches(gbr_ctx& c, const double* q, double* dqdt, cudaS
 extern "C" gbr_status gbr_rhs_static(const gbr_params* p, const double* nodes, const double* node_vel,
                                      const double* q, double* dqdt, void* stream, char* msg, size_t msg_len) {
   if (!p || !nodes || !q || !dqdt) return static_report(GBR_EINVAL, "null argument", msg, msg_len);
+  {  // the general checks first (axis and ghost-layer bounds, 32-bit offsets), then this call's own limits
+    std::string why;
+    if (!valid_params(p, why)) return static_report(GBR_EINVAL, why.c_str(), msg, msg_len);
+  }
   if (const char* why = static_param_error(p)) return static_report(GBR_EINVAL, why, msg, msg_len);
   if (node_vel && !p->moving) return static_report(GBR_EINVAL, "node velocities need params.moving = 1", msg, msg_len);
   const Layout L = layout_of(p);

@@ -92,6 +92,8 @@ def lib():
     L.gbr_get_field.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _P]
     L.gbr_profile.argtypes = [_vp, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     L.gbr_check_bounded_wait.argtypes = [_vp, ctypes.c_int]
+    L.gbr_alu_peak.argtypes = [ctypes.c_int, _vp, _P, _P]
+    L.gbr_alu_peak.restype = ctypes.c_int
     L.gbr_set_state_async.argtypes = [_vp, _vp, _vp]
     L.gbr_get_state_async.argtypes = [_vp, _vp, _vp]
     L.gbr_profile.restype = ctypes.c_int
@@ -138,12 +140,25 @@ def exported_symbols():
     return ["gbr_workspace_bytes", "gbr_create", "gbr_compute_metrics", "gbr_move_mesh", "gbr_set_motion",
             "gbr_set_state", "gbr_get_state", "gbr_set_inflow", "gbr_set_sponge", "gbr_rhs", "gbr_compute_dt",
             "gbr_set_state_async", "gbr_get_state_async", "gbr_rk_step", "gbr_sync", "gbr_get_time", "gbr_get_field",
-            "gbr_profile", "gbr_check_bounded_wait",
+            "gbr_profile", "gbr_check_bounded_wait", "gbr_alu_peak",
             "gbr_rhs_static",
             "gbr_batch_workspace_bytes", "gbr_batch_create", "gbr_batch_set_options", "gbr_batch_add",
             "gbr_batch_remove", "gbr_batch_step", "gbr_batch_sync", "gbr_batch_info", "gbr_batch_tuning",
             "gbr_batch_last_error", "gbr_batch_destroy", "gbr_arena_create", "gbr_arena_alloc", "gbr_arena_free",
             "gbr_arena_stats", "gbr_arena_destroy", "gbr_last_error", "gbr_last_global_error", "gbr_destroy"]
+
+
+def alu_peak(precision="fp64", stream=None):
+    """Measured FMA throughput of the current device: (TFLOP/s, ms of the timed launch)."""
+    L = lib()
+    tf = ctypes.c_double()
+    ms = ctypes.c_double()
+    st = None if stream is None else _vp(stream.cuda_stream)
+    rc = L.gbr_alu_peak({"fp64": GBR_PREC_FP64, "mixed": GBR_PREC_MIXED}[precision], st, ctypes.byref(tf),
+                        ctypes.byref(ms))
+    if rc:
+        raise GbrError(rc, L.gbr_last_global_error().decode())
+    return tf.value, ms.value
 
 
 def make_params(case):

@@ -107,3 +107,24 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.gbr_set_state_async(None, None, None) == gbr.GBR_EINVAL
     assert lib.gbr_get_state_async(None, None, None) == gbr.GBR_EINVAL
     lib.gbr_destroy(None)
+
+
+@pytest.mark.parametrize("bad", ["long_axis", "many_ghosts", "negative_ghosts"])
+def test_axis_and_ghost_bounds_rejected_before_size_arithmetic(lib, bad):
+    # an axis of 2^30 cells (with the others 1 wide the cell count alone would pass) or an absurd
+    # number of ghost node layers would overflow the padded extents; both are refused up front,
+    # by gbr_workspace_bytes, gbr_create and the allocation-free gbr_rhs_static alike
+    if bad == "long_axis":
+        case = I.case_params(2, (1 << 30, 6))
+    else:
+        case = I.case_params(2, (16, 16), periodic=(0, 1), ghost_nodes=5000 if bad == "many_ghosts" else -3)
+    p = gbr.make_params(case)
+    assert lib.gbr_workspace_bytes(ctypes.byref(p)) == 0
+    why = b"axis too long" if bad == "long_axis" else b"ghost_nodes out of range"
+    assert why in lib.gbr_last_global_error()
+    dummy = (ctypes.c_double * 8)()
+    msg = ctypes.create_string_buffer(128)
+    rc = lib.gbr_rhs_static(ctypes.byref(p), dummy, None, ctypes.c_void_p(256), ctypes.c_void_p(256), None, msg,
+                            ctypes.c_size_t(128))
+    assert rc == gbr.GBR_EINVAL
+    assert why in msg.value

@@ -77,3 +77,41 @@ def test_a_job_whose_state_goes_bad_fails_alone():
     st = serving.latency_stats(jobs)
     assert st["jobs"] == len(jobs) - 1 and st["failed"] == 1
     srv.close()
+
+
+def test_served_jobs_match_the_oracle():
+    """Served jobs of each precision and kind against the FP64 oracle after their steps: FP64 jobs
+    within L1 1e-8 (the Sod slabs' limiter is active at the waves) and, when smooth, 1e-10 of max |Q|;
+    mixed-precision jobs within 1e-5 (L-infinity)."""
+    import oracle as O
+    from test_gpu_parity import rel_state
+
+    jobs = small_stream(12, seed=5)
+    pool = int(3 * max(j.footprint() for j in jobs))
+    srv = serving.Server(pool, max_active=4, chunk_steps=3)
+    srv.run(jobs)
+    specs = {sp["id"]: sp for sp in I.serving_stream(12, seed=5, rate=400.0, edge2d=(24, 72), edge3d=(12, 24),
+                                                         steps=(3, 14))}
+    seen = set()
+    for j in jobs:
+        sp = specs[j.id]
+        key = (sp["kind"], sp["precision"])
+        if key in seen:
+            continue
+        seen.add(key)
+        assert j.error is None
+        orc = O.Oracle(dict(j.case, precision="fp64"), j.nodes)
+        qo = j.q.copy()
+        for _ in range(j.steps):
+            qo = orc.rk3(qo, orc.dt(qo, j.cfl))
+        nv = qo.shape[0]
+        if sp["precision"] == "mixed":
+            assert rel_state(j.result, qo) < 1e-5, key
+        else:
+            _, det = orc.cell_metrics()
+            l1 = (np.abs(j.result - qo) * det).reshape(nv, -1).sum(axis=1) / (np.abs(qo) * det).reshape(nv, -1).sum(axis=1)
+            assert l1.max() < 1e-8, key
+            if sp["kind"] != "sod":
+                assert rel_state(j.result, qo) < 1e-10, key
+    assert {k[1] for k in seen} == {"fp64", "mixed"}
+    srv.close()

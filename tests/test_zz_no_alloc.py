@@ -106,3 +106,33 @@ def test_static_scratch_rejects_oversize_grid():
     rc, msg = _static_rhs(case, nodes, q, q)
     assert rc == gbr.GBR_EINVAL
     assert "too large" in msg
+
+
+def test_static_scratch_rhs_open_axis_with_ghost_nodes():
+    """A non-periodic x axis with zero-gradient sides and 10 ghost node layers: exercises the ghost-node
+    offset of the node extension and the zero-gradient primitive ghosts of the allocation-free path."""
+    import torch
+
+    n = (26, 14, 12)
+    L = (3.0, 2.0, 2.0)
+    h = [Lx / m for Lx, m in zip(L, n)]
+
+    def f(i, j, k):
+        x, y, z = i * h[0], j * h[1], k * h[2]
+        s = 0.04 * np.sin(2 * np.pi * x / 3.0) * np.sin(2 * np.pi * y / 2.0) * np.sin(2 * np.pi * z / 2.0)
+        return x + s, y + 0.5 * s, z - s
+
+    nodes = I.nodes_from_functions(n, (0, 1, 1), 10, f)
+    case = I.case_params(3, n, periodic=(0, 1, 1), reynolds=400.0, ghost_nodes=10)
+    xc = I.centroids(nodes, n, (0, 1, 1))
+    P = I.tgv_prim(2 * np.pi * xc[0] / 3.0, np.pi * xc[1], np.pi * xc[2], mach=0.3)
+    P[0] = P[0] * (1.0 + 0.1 * np.tanh(4.0 * (xc[0] - 1.5)))  # a density ramp across the open axis
+    q = I.prim_to_cons(P, 1.4)
+    ref = _workspace_rhs(case, nodes, q)
+    scale = cancellation_scale(O.Oracle(case, nodes), q)
+    out = torch.empty(q.shape, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        out.fill_(float("nan"))
+        rc, msg = _static_rhs(case, nodes, torch.from_numpy(q).cuda(), out)
+        assert rc == gbr.GBR_OK, msg
+        assert _err(out.cpu().numpy(), ref, scale) < 1e-12
