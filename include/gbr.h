@@ -71,8 +71,12 @@ enum { GBR_PREC_FP64 = 0, GBR_PREC_MIXED = 1 };
  *                tridiagonal solve per grid line -- cyclic on periodic axes; on
  *                open axes over the padded line, whose three end points at each
  *                side take explicit rows (second-order one-sided, fourth-order
- *                biased, fourth-order central).  The metrics keep the E6-based
- *                operators of Sec. 6 (the paper builds them from IG4 for MIG4).
+ *                biased, fourth-order central).  The metric derivative and
+ *                interpolation of Sec. 6 use IG4 as well (step 2: the scheme's own
+ *                gradients): one solve per geometry line with the same end rows, on
+ *                periodic axes over the unwrapped line extended 64 cells beyond each
+ *                side (IG4 on the unbounded line to round-off); wall-bounded axes
+ *                without ghost nodes keep the App. C operators.
  *                Not available in gbr_rhs_static or in a batch. */
 enum { GBR_GRAD_MEG6 = 0, GBR_GRAD_MIG4 = 1 };
 

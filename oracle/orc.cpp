@@ -69,6 +69,11 @@ static int fail(const std::string& m) { g_err = m; return 1; }
 
 static const int H = 6;   // ghost layers of the primitive state
 static const int E = 10;  // geometry extension in cells beyond each side
+// MIG4: geometry extension beyond each side of a periodic axis (IG4 on the unbounded
+// unwrapped line, Sec. 6 step 2), and the margin kept to the ends of those lines for the
+// cell metrics that are interpolated to interfaces
+static const int kExtIG4 = 64;
+static const int kCellIG4 = kExtIG4 - 10;
 
 static inline real Min(real a, real b) { return (a < b) ? a : b; }
 static inline real Max(real a, real b) { return (a > b) ? a : b; }
@@ -322,6 +327,18 @@ static Field op_interp(const Field& f, int d, int scheme) {
 
 // Sec. 6 step 2: consistent metric derivative D = delta o interp (MEG6).
 static Field op_D(const Field& f, int d) { return op_delta(op_interp(f, d, 0), d); }
+
+// Sec. 6 steps 2-3 for MIG4: the same interpolation and derivative, with x' from the IG4
+// system (Eq. IG4_grads) solved over the field's whole line along d with the explicit end
+// rows.  On a periodic axis the geometry line is the unwrapped line extended kExtIG4 cells
+// beyond each side, so this is IG4 on the unbounded line: the inverse of the (alpha, 1, alpha)
+// operator decays by |r| = 0.4226 per cell, and the end rows reach the cells that are kept
+// below 1e-20 of their own size.
+static Field op_interp_ig4(const Field& f, int d) {
+  Field f1 = op_ig4(f, d, false, 0);
+  Field f2 = op_second(f, f1, d);
+  return op_face(f, f1, f2, d);
+}
 
 // ---------------------------------------------------------------------------
 // App. C: an axis bounded by walls on both sides (no ghost nodes).
@@ -710,9 +727,14 @@ int orc_solver::build_geometry(const Field* xc, const Field* vc) {
   ORC_PHASE(PH_GEOM);
   const int sch = p.metric_scheme;
   Field xd[3][3];  // xd[a][d] = d x_a / d xi_d
-  // Sec. 6 operators, App. C on wall-bounded axes
-  auto Dop = [&](const Field& f, int d) { return closed[d] ? op_delta(op_interp_c(f, d), d) : op_D(f, d); };
-  auto Iop = [&](const Field& f, int d) { return closed[d] ? op_interp_c(f, d) : op_interp(f, d, sch); };
+  // Sec. 6 operators built from the scheme's own gradients (step 2): E6 for MEG6, IG4 for MIG4;
+  // App. C on wall-bounded axes; the E4 operators of App. D for the non-conservative control
+  const bool ig4 = sch == 0 && p.gradient_scheme == 1;
+  auto Iop = [&](const Field& f, int d) {
+    if (closed[d]) return op_interp_c(f, d);
+    return ig4 ? op_interp_ig4(f, d) : op_interp(f, d, sch);
+  };
+  auto Dop = [&](const Field& f, int d) { return op_delta(Iop(f, d), d); };
   for (int a = 0; a < nd; ++a)
     for (int d = 0; d < nd; ++d) xd[a][d] = sch == 0 ? Dop(xc[a], d) : op_e4(xc[a], d);
 
@@ -1142,6 +1164,12 @@ int orc_create(const orc_params* prm, const double* nodes, const double* node_ve
     if (s->closed[d]) {  // geometry exists on the cells only
       s->ext.lo[d] = s->cellgeo.lo[d] = 0;
       s->ext.hi[d] = s->cellgeo.hi[d] = s->p.n[d];
+    } else if (s->p.periodic[d] && s->p.gradient_scheme == 1 && s->p.metric_scheme == 0) {
+      // MIG4 metrics: long unwrapped lines on periodic axes (see op_interp_ig4)
+      s->ext.lo[d] = -kExtIG4;
+      s->ext.hi[d] = s->p.n[d] + kExtIG4;
+      s->cellgeo.lo[d] = -kCellIG4;
+      s->cellgeo.hi[d] = s->p.n[d] + kCellIG4;
     }
   }
   s->inflow.assign((size_t)s->nv * s->p.n[1] * s->p.n[2], 0.0);

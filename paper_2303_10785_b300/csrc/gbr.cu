@@ -90,6 +90,109 @@ __global__ void k_face_metrics(GeoArgs G, Box b0, Box b1, Box b2) {
   body_face_metrics(G, d, i, j, k);
 }
 
+// ---- MIG4 metrics: one thread per geometry line (set-up work; Sec. 6 step 2 with IG4)
+__global__ void k_ig4_geo_factor(double* t, int m) { ig4_geo_factor(t, m); }
+
+// D_d of one direction on its own (the App. C closure of a wall-bounded axis of a MIG4 grid)
+__global__ void k_coordd1(GeoArgs G, int d, Box b) {
+  BOX_THREAD(b);
+  body_coord_derivative(G, d, i, j, k);
+}
+
+// xd[a][d] = D_d(x_a) on [-he + 5, n + he - 5) along d; xs: cross-section of the extended box
+__global__ void k_ig4_coordd(GeoArgs G, int d, Box xs, const double* t, double* w) {
+  BOX_THREAD(xs);
+  const Layout& L = G.L;
+  const long long base = line_base(L, d, i, j, k), st = L.es[d];
+  const int lo = -L.he[d], hi = L.n[d] + L.he[d];
+  const LineRef W{w + base, st};
+  for (int a = 0; a < L.nd; ++a) {
+    const double* x = G.xc + a * L.ecount + base;
+    auto f = [&](int m) { return x[m * st]; };
+    ig4_geo_solve(f, W, lo, hi, t);
+    double* out = G.xd + (a * 3 + d) * L.ecount + base;
+    double prev = ig4_geo_face(f, W, lo + 4);
+    for (int m = lo + 5; m < hi - 5; ++m) {
+      const double cur = ig4_geo_face(f, W, m);
+      out[m * st] = cur - prev;
+      prev = cur;
+    }
+  }
+}
+
+// Eq. (GCL_metrics), 3D, the derivatives along s: phase 0 stores, for e = s + 1, the term
+// D_s(x_b,f x_c) with f = s + 2; phase 1 subtracts, for e = s + 2, the term D_s(x_b,g x_c) with
+// g = s + 1 (b = a + 1, c = a + 2).  xs: cross-section of the cell-metric box.
+__global__ void k_ig4_metric_terms(GeoArgs G, int s, int phase, Box xs, const double* t, double* w) {
+  BOX_THREAD(xs);
+  const Layout& L = G.L;
+  const long long EC = L.ecount;
+  const long long base = line_base(L, s, i, j, k), st = L.es[s];
+  const int lo = -L.he[s], hi = L.n[s] + L.he[s];
+  const int olo = -L.cg[s], ohi = L.n[s] + L.cg[s];
+  const int e = phase == 0 ? (s + 1) % 3 : (s + 2) % 3;
+  const int inner = phase == 0 ? (s + 2) % 3 : (s + 1) % 3;  // the coordinate derivative in the product
+  const LineRef W{w + base, st};
+  for (int a = 0; a < 3; ++a) {
+    const int b = (a + 1) % 3, c = (a + 2) % 3;
+    const double* u = G.xd + (b * 3 + inner) * EC + base;
+    const double* v = G.xc + c * EC + base;
+    auto f = [&](int m) { return u[m * st] * v[m * st]; };
+    double* out = G.mh + (e * 3 + a) * EC + base;
+    if (L.closed[s]) {
+      for (int m = 0; m < L.n[s]; ++m) {
+        const double dv = appc_D(f, m, L.n[s]);
+        out[m * st] = phase == 0 ? dv : out[m * st] - dv;
+      }
+      continue;
+    }
+    ig4_geo_solve(f, W, lo, hi, t);
+    double prev = ig4_geo_face(f, W, olo - 1);
+    for (int m = olo; m < ohi; ++m) {
+      const double cur = ig4_geo_face(f, W, m);
+      const double dv = cur - prev;
+      out[m * st] = phase == 0 ? dv : out[m * st] - dv;
+      prev = cur;
+    }
+  }
+}
+
+// 1/J, unhatted and time metrics from the coordinate derivatives and the hat metrics
+__global__ void k_metrics_given(GeoArgs G, Box b) {
+  BOX_THREAD(b);
+  body_metrics(G, i, j, k, true);
+}
+
+// Sec. 6 step 3 with IG4: interface metrics of direction d, one line of the cell-metric box per
+// thread (xs: the cross-section of the interior)
+__global__ void k_ig4_face_metrics(GeoArgs G, int d, Box xs, const double* t, double* w) {
+  BOX_THREAD(xs);
+  const Layout& L = G.L;
+  const long long EC = L.ecount, FC = L.fcount[d];
+  const long long base = line_base(L, d, i, j, k), st = L.es[d];
+  const int lo = -L.cg[d], hi = L.n[d] + L.cg[d];
+  const int nd = L.nd;
+  const LineRef W{w + base, st};
+  int c0[3] = {i, j, k};
+  c0[d] = 0;
+  const long long f0 = fidx(L, d, c0[0], c0[1], c0[2]), fs = L.fs[d][d];  // interface 1/2; -1/2 at f0 - fs
+  auto interp = [&](const double* src, double* dst) {
+    const double* x = src + base;
+    auto f = [&](int m) { return x[m * st]; };
+    if (L.closed[d]) {
+      for (int m = -1; m < L.n[d]; ++m) dst[f0 + m * fs] = appc_face(f, m, L.n[d]);
+      return;
+    }
+    ig4_geo_solve(f, W, lo, hi, t);
+    for (int m = -1; m < L.n[d]; ++m) dst[f0 + m * fs] = ig4_geo_face(f, W, m);
+  };
+  for (int a = 0; a < nd; ++a) interp(G.mh + (d * 3 + a) * EC, G.fh[d] + a * FC);
+  if (G.viscous)
+    for (int ee = 0; ee < nd; ++ee)
+      for (int a = 0; a < nd; ++a) interp(G.mu + (ee * 3 + a) * EC, G.fu[d] + (ee * nd + a) * FC);
+  if (G.moving) interp(G.mt + d * EC, G.ft[d]);
+}
+
 __global__ void k_gcl(GeoArgs G, Box b) {
   BOX_THREAD(b);
   body_gcl(G, i, j, k);
@@ -656,7 +759,7 @@ struct Plan {
 enum Slot {
   SL_Q0, SL_Q1, SL_Q2, SL_PRIM, SL_TEMP, SL_G1, SL_G2, SL_FLUX, SL_NODES, SL_NVEL, SL_XC, SL_VC, SL_XD, SL_MH,
   SL_DET, SL_MU, SL_MT, SL_FH, SL_FU, SL_FT, SL_GCL, SL_JAC, SL_SIGMA, SL_INFLOW, SL_SCAL, SL_ERR, SL_IG4, SL_FH32, SL_FU32,
-  SL_FT32, SL_IG4F, SL_MH32, SL_MT32, SL_JAC32, SL_COUNT
+  SL_FT32, SL_IG4F, SL_MH32, SL_MT32, SL_JAC32, SL_GEOT, SL_GEOW, SL_COUNT
 };
 
 struct Sizes {
@@ -731,7 +834,9 @@ Layout layout_of(const gbr_params* p) {
   int n[3] = {p->n[0], p->n[1], p->ndim == 3 ? p->n[2] : 1};
   int closed[3];
   for (int d = 0; d < 3; ++d) closed[d] = (d < p->ndim && !p->periodic[d] && p->ghost_nodes == 0) ? 1 : 0;
-  return make_layout(p->ndim, n, p->periodic, closed);
+  int ig4_geo[3];
+  for (int d = 0; d < 3; ++d) ig4_geo[d] = p->gradient_scheme == GBR_GRAD_MIG4 ? 1 : 0;
+  return make_layout(p->ndim, n, p->periodic, closed, ig4_geo);
 }
 
 // bytes of one element of the arrays computed in the path's type
@@ -785,6 +890,14 @@ Plan plan_of(const gbr_params* p, const Layout& L) {
   P.add(f32 ? sizeof(float) * 9 * L.ncells : 0);               // SL_MH32: the time step's cell metrics
   P.add(f32 && mov ? sizeof(float) * 3 * L.ncells : 0);        // SL_MT32
   P.add(f32 ? sizeof(float) * L.ncells : 0);                   // SL_JAC32
+  // MIG4 metrics: Thomas factors of the extended and of the cell-metric lines per direction, and a
+  // work array for the line solves
+  const bool geo4 = p->gradient_scheme == GBR_GRAD_MIG4;
+  long long geot = 0;
+  if (geo4)
+    for (int d = 0; d < nd; ++d) geot += 2LL * (L.n[d] + 2 * L.he[d]) + 2LL * (L.n[d] + 2 * L.cg[d]);
+  P.add(D * geot);                                               // SL_GEOT
+  P.add(geo4 ? D * L.ecount : 0);                                // SL_GEOW
   P.total = (P.total + 255) & ~(size_t)255;
   return P;
 }
@@ -832,6 +945,9 @@ struct gbr_ctx {
   float *mh32, *mt32, *jac32;          // mixed path: FP32 copies of the cell metrics (time step)
   double *sigma, *inflow, *scal;
   double* ig4[3];  // MIG4 line-solve factors per direction (or null)
+  double* geot_ext[3];   // MIG4 metrics: Thomas factors of the extended lines per direction (or null)
+  double* geot_cell[3];  // ... and of the cell-metric lines
+  double* geow;          // ... work array of the line solves (extended-box layout)
   float* ig4f[3];  // mixed path: their FP32 copies (no conversions in the FP32 line solves)
   CUtensorMap ig4_tm[3][2];  // MIG4 y/z lines: TMA maps of the primitives and the temperature
   bool ig4_tma[3];           // the TMA form is used for this direction
@@ -994,22 +1110,29 @@ struct GeoBoxes {
 
 GeoBoxes geo_boxes(const Layout& L) {
   GeoBoxes B;
-  B.ext = pad_box(L, E, E);
+  int elo[3], ehi[3], mlo[3], mhi[3];
+  for (int e = 0; e < 3; ++e) {
+    elo[e] = -L.he[e];
+    ehi[e] = L.n[e] + L.he[e];
+    mlo[e] = -L.cg[e];
+    mhi[e] = L.n[e] + L.cg[e];
+  }
+  B.ext = make_box(L, elo, ehi);
   for (int d = 0; d < 3; ++d) {
     int lo[3], hi[3];
-    for (int e = 0; e < 3; ++e) { lo[e] = -E; hi[e] = L.n[e] + E; }
-    lo[d] = -5;
-    hi[d] = L.n[d] + 5;
+    for (int e = 0; e < 3; ++e) { lo[e] = elo[e]; hi[e] = ehi[e]; }
+    lo[d] = -L.he[d] + 5;
+    hi[d] = L.n[d] + L.he[d] - 5;
     B.coordd[d] = make_box(L, lo, hi);
     int flo[3] = {0, 0, 0}, fhi[3] = {L.n[0], L.n[1], L.n[2]};
     flo[d] = -1;
     fhi[d] = L.n[d];
     B.faces[d] = make_box(L, flo, fhi);
   }
-  B.metrics = pad_box(L, 5, 5);
+  B.metrics = make_box(L, mlo, mhi);
   B.inner = pad_box(L, 0, 0);
   int lo[3], hi[3];
-  for (int d = 0; d < 3; ++d) { lo[d] = -E; hi[d] = L.n[d] + E + 1; }
+  for (int d = 0; d < 3; ++d) { lo[d] = -L.he[d]; hi[d] = L.n[d] + L.he[d] + 1; }
   B.nodes = make_box(L, lo, hi);
   // closed (wall-bounded) axes: geometry exists on the cells only (App. C)
   for (int a = 0; a < L.nd; ++a) {
@@ -1064,6 +1187,45 @@ RhsBoxes rhs_boxes(const Layout& L) {
 
 DtArgs dt_args(gbr_ctx* c);
 
+// the box b with its extent along d reduced to the single index 0 (one thread per line along d)
+Box cross_section(Box b, int d) {
+  b.lo[d] = 0;
+  b.hi[d] = 1;
+  return b;
+}
+
+// MIG4 metrics (Sec. 6 steps 2-3 with IG4 line solves; App. C on wall-bounded axes)
+gbr_status run_geometry_ig4(gbr_ctx* c, const GeoArgs& G, const GeoBoxes& B) {
+  const Layout& L = c->L;
+  cudaStream_t st = c->stream;
+  constexpr int kLineBlock = 64;
+  for (int d = 0; d < L.nd; ++d) {
+    if (L.closed[d]) {
+      k_coordd1<<<grid_of(B.coordd[d], kBlock), kBlock, 0, st>>>(G, d, B.coordd[d]);
+      CKL("k_coordd1");
+    } else {
+      const Box xs = cross_section(B.ext, d);
+      k_ig4_coordd<<<grid_of(xs, kLineBlock), kLineBlock, 0, st>>>(G, d, xs, c->geot_ext[d], c->geow);
+      CKL("k_ig4_coordd");
+    }
+  }
+  if (L.nd == 3)
+    for (int phase = 0; phase < 2; ++phase)
+      for (int s = 0; s < 3; ++s) {
+        const Box xs = cross_section(B.metrics, s);
+        k_ig4_metric_terms<<<grid_of(xs, kLineBlock), kLineBlock, 0, st>>>(G, s, phase, xs, c->geot_ext[s], c->geow);
+        CKL("k_ig4_metric_terms");
+      }
+  k_metrics_given<<<grid_of(B.metrics, kBlock), kBlock, 0, st>>>(G, B.metrics);
+  CKL("k_metrics_given");
+  for (int d = 0; d < L.nd; ++d) {
+    const Box xs = cross_section(B.inner, d);
+    k_ig4_face_metrics<<<grid_of(xs, kLineBlock), kLineBlock, 0, st>>>(G, d, xs, c->geot_cell[d], c->geow);
+    CKL("k_ig4_face_metrics");
+  }
+  return GBR_OK;
+}
+
 gbr_status run_geometry(gbr_ctx* c) {
   const Layout& L = c->L;
   GeoArgs G = geo_args(c);
@@ -1071,16 +1233,21 @@ gbr_status run_geometry(gbr_ctx* c) {
   const GeoBoxes B = geo_boxes(L);
   k_centroid<<<grid_of(B.ext, kBlock), kBlock, 0, st>>>(G, B.ext);
   CKL("k_centroid");
-  unsigned gmax = 0;
-  for (int d = 0; d < L.nd; ++d) gmax = std::max(gmax, grid_of(B.coordd[d], kBlock));
-  k_coordd<<<dim3(gmax, L.nd), kBlock, 0, st>>>(G, B.coordd[0], B.coordd[1], B.coordd[2]);
-  CKL("k_coordd");
-  k_metrics<<<grid_of(B.metrics, kBlock), kBlock, 0, st>>>(G, B.metrics);
-  CKL("k_metrics");
-  gmax = 0;
-  for (int d = 0; d < L.nd; ++d) gmax = std::max(gmax, grid_of(B.faces[d], kBlock));
-  k_face_metrics<<<dim3(gmax, L.nd), kBlock, 0, st>>>(G, B.faces[0], B.faces[1], B.faces[2]);
-  CKL("k_face_metrics");
+  if (c->p.gradient_scheme == GBR_GRAD_MIG4) {
+    gbr_status s4 = run_geometry_ig4(c, G, B);
+    if (s4 != GBR_OK) return s4;
+  } else {
+    unsigned gmax = 0;
+    for (int d = 0; d < L.nd; ++d) gmax = std::max(gmax, grid_of(B.coordd[d], kBlock));
+    k_coordd<<<dim3(gmax, L.nd), kBlock, 0, st>>>(G, B.coordd[0], B.coordd[1], B.coordd[2]);
+    CKL("k_coordd");
+    k_metrics<<<grid_of(B.metrics, kBlock), kBlock, 0, st>>>(G, B.metrics);
+    CKL("k_metrics");
+    gmax = 0;
+    for (int d = 0; d < L.nd; ++d) gmax = std::max(gmax, grid_of(B.faces[d], kBlock));
+    k_face_metrics<<<dim3(gmax, L.nd), kBlock, 0, st>>>(G, B.faces[0], B.faces[1], B.faces[2]);
+    CKL("k_face_metrics");
+  }
   k_gcl<<<grid_of(B.inner, kBlock), kBlock, 0, st>>>(G, B.inner);
   CKL("k_gcl");
   if (c->p.precision == GBR_PREC_MIXED) {
@@ -1404,6 +1571,19 @@ void carve(gbr_ctx* c) {
       }
     }
   }
+  {
+    size_t goff = 0;
+    for (int d = 0; d < 3; ++d) {
+      c->geot_ext[d] = c->geot_cell[d] = nullptr;
+      if (d < L.nd && P.len[SL_GEOT]) {
+        c->geot_ext[d] = (double*)(c->ws + P.off[SL_GEOT]) + goff;
+        goff += 2 * (size_t)(L.n[d] + 2 * L.he[d]);
+        c->geot_cell[d] = (double*)(c->ws + P.off[SL_GEOT]) + goff;
+        goff += 2 * (size_t)(L.n[d] + 2 * L.cg[d]);
+      }
+    }
+    c->geow = ptr(SL_GEOW);
+  }
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link against the driver library)
@@ -1530,6 +1710,10 @@ gbr_status gbr_create(const gbr_params* p, const double* nodes, const double* no
   if (p->gradient_scheme == GBR_GRAD_MIG4) {
     ig4_encode_maps(c);
     for (int d = 0; d < L.nd; ++d) {
+      if (!L.closed[d]) {  // the metric line solves (extended lines, cell-metric lines)
+        k_ig4_geo_factor<<<1, 1, 0, c->stream>>>(c->geot_ext[d], L.n[d] + 2 * L.he[d]);
+        k_ig4_geo_factor<<<1, 1, 0, c->stream>>>(c->geot_cell[d], L.n[d] + 2 * L.cg[d]);
+      }
       k_ig4_factor<<<1, 1, 0, c->stream>>>(c->ig4[d], L.n[d], L.per[d]);
       if (c->ig4f[d]) {
         const long long n = ig4_table_len(L.n[d], L.per[d] != 0);

@@ -33,7 +33,9 @@ struct Layout {
   int pn[3];          // padded extents
   long long ps[3];    // padded strides
   long long pcount;
-  int he[3];          // geometry extension per axis (E on active axes)
+  int he[3];          // geometry extension per axis (E on active axes; kExtIG4 on periodic axes of a
+                      // MIG4 grid, whose metric operators solve IG4 over the unwrapped line)
+  int cg[3];          // cell metrics kept on [-cg, n + cg) (5; kExtIG4 - 10 with the long lines; 0 closed)
   int en[3];
   long long es[3];
   long long ecount;
@@ -47,7 +49,13 @@ struct Layout {
   int closed[3];      // wall-bounded axis without ghost nodes: no geometry extension, App. C operators
 };
 
-inline Layout make_layout(int nd, const int* n, const int* periodic, const int* closed) {
+// MIG4 geometry: extension of a periodic axis (IG4 on the unbounded unwrapped line: the inverse of the
+// (alpha, 1, alpha) operator decays by 0.4226 per cell, so the end rows of a line this long reach the
+// cells that are kept below 1e-20 of their own size)
+constexpr int kExtIG4 = 64;
+
+// ig4_geo: per axis, 1 when the metrics are built with IG4 on the long unwrapped line
+inline Layout make_layout(int nd, const int* n, const int* periodic, const int* closed, const int* ig4_geo) {
   Layout L;
   L.nd = nd;
   L.nv = nd + 2;
@@ -58,7 +66,8 @@ inline Layout make_layout(int nd, const int* n, const int* periodic, const int* 
     L.closed[d] = act && !periodic[d] && closed[d];
     L.hp[d] = act ? H : 0;
     L.pn[d] = L.n[d] + 2 * L.hp[d];
-    L.he[d] = (act && !L.closed[d]) ? E : 0;
+    L.he[d] = (act && !L.closed[d]) ? ((periodic[d] && ig4_geo[d]) ? kExtIG4 : E) : 0;
+    L.cg[d] = !act ? 0 : (L.closed[d] ? 0 : ((periodic[d] && ig4_geo[d]) ? kExtIG4 - 10 : 5));
     L.en[d] = L.n[d] + 2 * L.he[d];
     L.nn[d] = act ? L.n[d] + 2 * L.he[d] + 1 : 1;
   }
@@ -322,6 +331,77 @@ GBR_HD long long line_base(const Layout& L, int d, int i, int j, int k) {
 }
 
 // ---------------------------------------------------------------------------
+// MIG4 metric operators (Sec. 6 step 2: the metric derivative and interpolation use the scheme's
+// own gradients; for MIG4 x' is the IG4 system of Eq. IG4_grads).  A geometry line is solved as a
+// whole with the explicit end rows (second-order one-sided, fourth-order biased, fourth-order
+// central at the three end points of each side, IG4 rows between); on periodic axes the line is
+// the unwrapped line extended kExtIG4 cells beyond each side, i.e. IG4 on the unbounded line.
+// ---------------------------------------------------------------------------
+// Eq. IG4_grads: alpha = 5/14
+constexpr double kIg4Alpha = 5.0 / 14.0;
+
+// one line of an extended-box array: cell x of the line at p[x * s] (x may be negative)
+struct LineRef {
+  double* p;
+  long long s;
+  GBR_HD double& operator()(int x) const { return p[x * s]; }
+};
+
+// Thomas factors of the open-line system of m rows, the same for every line of that length:
+// t[r] = c'_r, t[m + r] = the pivot b_r - a_r c'_{r-1}
+GBR_HD void ig4_geo_factor(double* t, int m) {
+  double cp = 0.0;
+  for (int r = 0; r < m; ++r) {
+    const bool expl = r < 3 || r >= m - 3;
+    const double a = expl ? 0.0 : kIg4Alpha, c = expl ? 0.0 : kIg4Alpha;
+    const double den = 1.0 - (r > 0 ? a * cp : 0.0);
+    cp = c / den;
+    t[r] = cp;
+    t[m + r] = den;
+  }
+}
+
+// IG4 derivative w(x) of the line values f(x), x in [lo, hi), with the explicit end rows
+template <class F>
+GBR_HD void ig4_geo_solve(const F& f, const LineRef& w, int lo, int hi, const double* t) {
+  const int m = hi - lo, e = hi - 1;
+  const double al = kIg4Alpha;
+  const double c1 = (2.0 + al) / 3.0, c2 = (4.0 * al - 1.0) / 12.0;
+  double rp = 0.0;
+  for (int r = 0; r < m; ++r) {
+    const int x = lo + r;
+    double rhs;
+    if (r == 0) rhs = -1.5 * f(x) + 2.0 * f(x + 1) - 0.5 * f(x + 2);
+    else if (r == 1) rhs = -0.25 * f(x - 1) - (5.0 / 6.0) * f(x) + 1.5 * f(x + 1) - 0.5 * f(x + 2) + f(x + 3) / 12.0;
+    else if (r == 2) rhs = (2.0 / 3.0) * (f(x + 1) - f(x - 1)) - (f(x + 2) - f(x - 2)) / 12.0;
+    else if (x == e) rhs = 1.5 * f(e) - 2.0 * f(e - 1) + 0.5 * f(e - 2);
+    else if (x == e - 1)
+      rhs = 0.25 * f(e) + (5.0 / 6.0) * f(e - 1) - 1.5 * f(e - 2) + 0.5 * f(e - 3) - f(e - 4) / 12.0;
+    else if (x == e - 2) rhs = (2.0 / 3.0) * (f(e - 1) - f(e - 3)) - (f(e) - f(e - 4)) / 12.0;
+    else rhs = c1 * (f(x + 1) - f(x - 1)) + c2 * (f(x + 2) - f(x - 2));
+    const double a = (r < 3 || r >= m - 3) ? 0.0 : al;
+    rp = (rhs - a * rp) / t[m + r];
+    w(x) = rp;
+  }
+  double xn = 0.0;
+  for (int r = m - 1; r >= 0; --r) {
+    const int x = lo + r;
+    xn = (r == m - 1) ? w(x) : w(x) - t[r] * xn;
+    w(x) = xn;
+  }
+}
+
+// interface value at x + 1/2 (Eq. FP-interp, interp-formulae): the mean of the van Leer states of
+// cells x and x + 1 from f, its IG4 derivative w and f'' = 2 (f_{x+1} - 2 f_x + f_{x-1}) - (w_{x+1} - w_{x-1}) / 2
+template <class F>
+GBR_HD double ig4_geo_face(const F& f, const LineRef& w, int x) {
+  auto f2 = [&](int y) { return 2.0 * (f(y + 1) - 2.0 * f(y) + f(y - 1)) - 0.5 * (w(y + 1) - w(y - 1)); };
+  const double left = f(x) + 0.5 * w(x) + f2(x) / 12.0;
+  const double right = f(x + 1) - 0.5 * w(x + 1) + f2(x + 1) / 12.0;
+  return 0.5 * (left + right);
+}
+
+// ---------------------------------------------------------------------------
 // Geometry bodies (Sec. 3, Sec. 4, Sec. 6)
 // ---------------------------------------------------------------------------
 struct GeoArgs {
@@ -402,14 +482,18 @@ GBR_HD double metric_I(const Layout& L, const double* f, int d, int i, int j, in
 
 // Eq. (GCL_metrics) (3D) or its z = zeta reduction (2D), Eq. (Jac-matrix),
 // unhatted metrics (viscous) and Sec. 4 time metrics (moving).
-GBR_HD void body_metrics(const GeoArgs& G, int i, int j, int k) {
+// mh_given: the 3D hat metrics are already in G.mh (the MIG4 line kernels formed them)
+GBR_HD void body_metrics(const GeoArgs& G, int i, int j, int k, bool mh_given = false) {
   const Layout& L = G.L;
   const long long EC = L.ecount;
   const long long e = eidx(L, i, j, k);
   const int nd = L.nd;
   double m[3][3];
   double det;
-  if (nd == 3) {
+  if (nd == 3 && mh_given) {
+    for (int ee = 0; ee < 3; ++ee)
+      for (int a = 0; a < 3; ++a) m[ee][a] = G.mh[(ee * 3 + a) * EC + e];
+  } else if (nd == 3) {
     for (int ee = 0; ee < 3; ++ee) {
       const int f = (ee + 1) % 3, g = (ee + 2) % 3;
       for (int a = 0; a < 3; ++a) {
@@ -420,6 +504,8 @@ GBR_HD void body_metrics(const GeoArgs& G, int i, int j, int k) {
         m[ee][a] = t1 - t2;
       }
     }
+  }
+  if (nd == 3) {
     const double xx = G.xd[0 * EC + e], xe = G.xd[1 * EC + e], xz = G.xd[2 * EC + e];
     const double yx = G.xd[3 * EC + e], ye = G.xd[4 * EC + e], yz = G.xd[5 * EC + e];
     const double zx = G.xd[6 * EC + e], ze = G.xd[7 * EC + e], zz = G.xd[8 * EC + e];
@@ -833,7 +919,6 @@ GBR_HD void body_grad2(const RhsArgsT<R>& A, int e, int i, int j, int k) {
 // Table layout per direction (doubles): periodic: cp[n], inv[n], z[n], kinv, P[n];
 // open: cp[m], inv[m] with m = n + 2H.
 // ---------------------------------------------------------------------------
-constexpr double kIg4Alpha = 5.0 / 14.0;
 
 inline long long ig4_table_len(int n, bool periodic) { return periodic ? 4LL * n + 1 : 2LL * (n + 2 * H); }
 

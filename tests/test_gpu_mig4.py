@@ -2,9 +2,11 @@
 
 The CUDA path solves each grid line's tridiagonal IG4 system with factors computed once per
 direction (cyclic by Sherman-Morrison on periodic axes, explicit end rows on open axes); the
-oracle builds and solves each line's system on its own.  Same tolerances as the MEG6 parity
-tests: right-hand sides within 1e-12 of the cancellation scale, states within 1e-12 after a
-step; the mixed path within its own FP32 tolerance."""
+oracle builds and solves each line's system on its own.  The MIG4 metrics are built from IG4
+too (Sec. 6 step 2): one line solve per geometry line, on periodic axes over the unwrapped line
+extended 64 cells beyond each side.  Same tolerances as the MEG6 parity tests: metrics within
+1e-13 of their scale, right-hand sides within 1e-12 of the cancellation scale, states within
+1e-12 after a step; the mixed path within its own FP32 tolerance."""
 import numpy as np
 import pytest
 
@@ -31,6 +33,35 @@ def rhs_err(orc, s, q):
     Lg = s.rhs().cpu().numpy()
     Lo = orc.rhs(q)
     return (np.abs(Lg - Lo).reshape(q.shape[0], -1).max(axis=1) / cancellation_scale(orc, q)).max()
+
+
+@pytest.mark.parametrize("name", ["3d_tgv", "2d_moving", "3d_moving_viscous", "2d_vortex"])
+def test_mig4_metrics_match_oracle(name):
+    """Cell, interface and time metrics of MIG4 grids (IG4-based operators) against the oracle's."""
+    case, nodes, vel, q = CASES[name]()
+    orc = O.Oracle(mig4(case), nodes, vel)
+    s = gbr.Solver(mig4(case), nodes, vel)
+    nd = case["ndim"]
+    mh_o, det_o = orc.cell_metrics()
+    mh_g = s.field(gbr.GBR_FIELD_CELL_METRICS)
+    det_g = s.field(gbr.GBR_FIELD_CELL_DET)
+    assert np.abs(det_g - det_o).max() < 1e-13 * np.abs(det_o).max()
+    h = np.abs(det_o).max() ** (1.0 / nd)
+    mscale = max(np.abs(mh_o).max(), np.abs(nodes).max() * h ** (nd - 1))
+    assert np.abs(mh_g - mh_o).max() < 1e-13 * mscale
+    for d in range(nd):
+        fh_o, fu_o, ft_o = orc.face_metrics(d)
+        assert np.abs(s.field(gbr.GBR_FIELD_FACE_HAT, d) - fh_o).max() < 1e-13 * mscale
+        if case["reynolds"] > 0:
+            assert np.abs(s.field(gbr.GBR_FIELD_FACE_UNHAT, d) - fu_o).max() < 1e-12 * np.abs(fu_o).max()
+        if vel is not None:
+            assert np.abs(s.field(gbr.GBR_FIELD_FACE_TIME, d) - ft_o).max() < 1e-12 * np.abs(ft_o).max()
+    if vel is not None:
+        assert np.abs(s.field(gbr.GBR_FIELD_GCL) - orc.gcl()).max() < 1e-11 * np.abs(orc.gcl()).max()
+    # and they are not the E6-based metrics
+    _, meg6_det = O.Oracle(case, nodes, vel).cell_metrics()
+    assert np.abs(meg6_det - det_g).max() > 1e3 * 1e-13 * np.abs(det_o).max()
+    s.close()
 
 
 @pytest.mark.parametrize("name", sorted(CASES))

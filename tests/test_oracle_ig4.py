@@ -109,3 +109,68 @@ def test_mig4_open_axes_jet_like_case_runs_and_is_finite():
     # the quiescent state sees only that tail
     near = np.abs(L[:, :, :, :3]).max()
     assert np.abs(L[:, :, :, 14:]).max() < 0.42 ** 8 * near
+
+
+def _lambda1(th, scheme):
+    """f' / f for f = e^{i theta m}: IG4 (Eq. IG4_grads) or E6 (Eq. E6_grads)."""
+    if scheme == "mig4":
+        return 1j * (2 * C1 * np.sin(th) + 2 * C2 * np.sin(2 * th)) / (1 + 2 * AL * np.cos(th))
+    return 1j * (1.5 * np.sin(th) - 0.3 * np.sin(2 * th) + np.sin(3 * th) / 30.0)
+
+
+def _interface_and_derivative(th, scheme):
+    """Transfer functions of Sec. 6 for the cell mode f_m = e^{i theta (m + 1/2)}: the interface
+    value I (Eq. FP-interp / interp-formulae, with f'' = 2 (f_{i+1} - 2 f_i + f_{i-1}) - (f'_{i+1} -
+    f'_{i-1}) / 2) at i + 1/2 relative to f_i, and D = I_{i+1/2} - I_{i-1/2} (Eq. FP-interp2)
+    relative to f_i."""
+    l1 = _lambda1(th, scheme)
+    l2 = 4 * (np.cos(th) - 1) - 1j * np.sin(th) * l1
+    e = np.exp(1j * th)
+    icoef = 0.5 * ((1 + e) + 0.5 * l1 * (1 - e) + l2 * (1 + e) / 12.0)
+    return icoef, icoef * (1 - 1 / e)
+
+
+@pytest.mark.parametrize("scheme", ["mig4", "meg6"])
+def test_metrics_are_the_schemes_own_operators(scheme):
+    """Sec. 6 step 2: the metric derivative and interpolation use the scheme's own gradients (IG4 for
+    MIG4, E6 for MEG6).  Grid x = h i, y = h j + B sin(theta i) sin(theta j) (periodic, theta = 2 pi/n):
+    the centroid y_c = h (j + 1/2) + B c^2 s_i s_j with c = cos(theta/2), s_m = sin(theta (m + 1/2)), so
+    every metric and interface metric is a Fourier mode whose amplitude is the operator's transfer
+    function: y_xi = B c^2 Im(tD e^{i theta (i+1/2)}) s_j, y_eta likewise, xi^_x = y_eta,
+    eta^_x = -y_xi, xi^_y = 0, eta^_y = h, 1/J = h y_eta, and the interface values along each
+    direction through the interpolation's transfer function.  On the periodic axes the MIG4 lines
+    are the unwrapped lines (the x and y of this grid grow by n h per period)."""
+    n, h, B = 16, 0.3, 0.05
+    th = 2 * np.pi / n
+
+    def f(Ii, Jj):
+        return h * Ii, h * Jj + B * np.sin(th * Ii) * np.sin(th * Jj)
+
+    nodes = I.nodes_from_functions((n, n), (1, 1), 0, f)
+    orc = O.Oracle(I.case_params(2, (n, n), reynolds=100.0, gradient_scheme=scheme), nodes)
+    ti, tD = _interface_and_derivative(th, scheme)
+    m = np.arange(n)
+    c2 = np.cos(th / 2) ** 2
+    s = np.sin(th * (m + 0.5))
+    dmode = np.imag(tD * np.exp(1j * th * (m + 0.5)))   # D of s_m at cell m
+    imode = np.imag(ti * np.exp(1j * th * (m + 0.5)))   # I of s_m at interface m + 1/2
+    J_, I_ = np.meshgrid(m, m, indexing="ij")           # [j][i]
+    y_xi = B * c2 * dmode[I_] * s[J_]
+    y_eta = h + B * c2 * s[I_] * dmode[J_]
+    mh, det = orc.cell_metrics()
+    tol = 1e-14
+    assert np.abs(mh[0, 0] - y_eta).max() < tol and np.abs(mh[0, 1]).max() < tol
+    assert np.abs(mh[1, 0] + y_xi).max() < tol and np.abs(mh[1, 1] - h).max() < tol
+    assert np.abs(det - h * y_eta).max() < tol
+    # interface hat metrics: faces f = 0..n along xi hold i + 1/2 with i = f - 1 (periodic wrap)
+    fh0, _, _ = orc.face_metrics(0)
+    fh1, _, _ = orc.face_metrics(1)
+    fi = (np.arange(n + 1) - 1) % n
+    want0 = h + B * c2 * imode[fi][None, :] * dmode[:, None]   # I_xi(y_eta): [j][f]
+    want1 = -B * c2 * dmode[None, :] * imode[fi][:, None]      # I_eta(-y_xi): [f][i]
+    assert np.abs(fh0[0] - want0).max() < tol and np.abs(fh0[1]).max() < tol
+    assert np.abs(fh1[0] - want1).max() < tol and np.abs(fh1[1] - h).max() < tol
+    # the other scheme's transfer function is far away at this resolution
+    other = "meg6" if scheme == "mig4" else "mig4"
+    _, tD_o = _interface_and_derivative(th, other)
+    assert abs(tD_o - tD) * B * c2 > 1e3 * tol
