@@ -72,7 +72,7 @@ enum { GBR_PREC_FP64 = 0, GBR_PREC_MIXED = 1 };
  *                open axes over the padded line, whose three end points at each
  *                side take explicit rows (second-order one-sided, fourth-order
  *                biased, fourth-order central).  The metric derivative and
- *                interpolation of Sec. 6 use IG4 as well (step 2: the scheme's own
+ *                interpolation of Sec. 7 use IG4 as well (step 2: the scheme's own
  *                gradients): one solve per geometry line with the same end rows, on
  *                periodic axes over the unwrapped line extended 64 cells beyond each
  *                side (IG4 on the unbounded line to round-off); wall-bounded axes
@@ -102,7 +102,7 @@ typedef struct {
   int gradient_scheme; /* GBR_GRAD_MEG6 or GBR_GRAD_MIG4 */
 } gbr_params;
 
-/* Prescribed sinusoidal node motion (Sec. 7.2 families):
+/* Prescribed sinusoidal node motion (Sec. 8.2 families):
  * x_a(m, t) = origin_a + m_a h_a + amp_a sin(2 pi omega t) prod_b S_ab(m_b h_b),
  * S_ab(s) = sin(k_ab s) if k_ab != 0 else 1;  velocities are the analytic
  * time derivative.  m is the (unwrapped) node index. */
@@ -133,7 +133,7 @@ size_t gbr_workspace_bytes(const gbr_params* p);
 gbr_status gbr_create(const gbr_params* p, const double* nodes, const double* node_vel, void* d_workspace,
                       size_t ws_bytes, void* stream, gbr_ctx** out);
 
-/* Sec. 4 + Sec. 6: conservative metrics with the MEG6 interface derivative,
+/* Sec. 4 + Sec. 7: conservative metrics with the MEG6 interface derivative,
  * the Jacobian, their interface interpolation, and for a moving mesh the time
  * metrics xi_t = -(x_t xi_x + ...) and (1/J)_t of Eq. (Jacb2). */
 gbr_status gbr_compute_metrics(gbr_ctx* c);

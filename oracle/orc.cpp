@@ -19,7 +19,7 @@
  *            (App. A eigenvectors), van Leer states (Eq. legendre_polys), improved MP
  *            limiter (App. E), back-projection, HLLC (Sec. 5.1.1), flux difference
  *   Sec. 5.2 alpha-damping viscous flux, steps 1-5
- *   Sec. 6   consistent metric derivative (Eq. FP-interp, FP-interp2) and
+ *   Sec. 7   consistent metric derivative (Eq. FP-interp, FP-interp2) and
  *            interpolation (Eq. interp-formulae)
  *   App. B   SSP-RK3 and the CFL time step
  *   App. D   non-conservative metrics with the E4 derivative (negative control only)
@@ -70,7 +70,7 @@ static int fail(const std::string& m) { g_err = m; return 1; }
 static const int H = 6;   // ghost layers of the primitive state
 static const int E = 10;  // geometry extension in cells beyond each side
 // MIG4: geometry extension beyond each side of a periodic axis (IG4 on the unbounded
-// unwrapped line, Sec. 6 step 2), and the margin kept to the ends of those lines for the
+// unwrapped line, Sec. 7 step 2), and the margin kept to the ends of those lines for the
 // cell metrics that are interpolated to interfaces
 static const int kExtIG4 = 64;
 static const int kCellIG4 = kExtIG4 - 10;
@@ -153,7 +153,7 @@ struct Field {
       for (int i = (B).lo[0]; i < (B).hi[0]; ++i)
 
 // ---------------------------------------------------------------------------
-// One-dimensional operators along axis d (Sec. 5.1 step 1, Sec. 6, App. D)
+// One-dimensional operators along axis d (Sec. 5.1 step 1, Sec. 7, App. D)
 // ---------------------------------------------------------------------------
 
 // Eq. (E6_grads), read with differences:
@@ -317,7 +317,7 @@ static Field op_delta(const Field& fc, int d) {
   return o;
 }
 
-// Interpolation of a cell field to interfaces, Sec. 6 step 3 (scheme 0: E6
+// Interpolation of a cell field to interfaces, Sec. 7 step 3 (scheme 0: E6
 // gradients; scheme 1: the E4 gradients of App. D).
 static Field op_interp(const Field& f, int d, int scheme) {
   Field f1 = scheme ? op_e4(f, d) : op_e6(f, d);
@@ -325,10 +325,10 @@ static Field op_interp(const Field& f, int d, int scheme) {
   return op_face(f, f1, f2, d);
 }
 
-// Sec. 6 step 2: consistent metric derivative D = delta o interp (MEG6).
+// Sec. 7 step 2: consistent metric derivative D = delta o interp (MEG6).
 static Field op_D(const Field& f, int d) { return op_delta(op_interp(f, d, 0), d); }
 
-// Sec. 6 steps 2-3 for MIG4: the same interpolation and derivative, with x' from the IG4
+// Sec. 7 steps 2-3 for MIG4: the same interpolation and derivative, with x' from the IG4
 // system (Eq. IG4_grads) solved over the field's whole line along d with the explicit end
 // rows.  On a periodic axis the geometry line is the unwrapped line extended kExtIG4 cells
 // beyond each side, so this is IG4 on the unbounded line: the inverse of the (alpha, 1, alpha)
@@ -345,7 +345,7 @@ static Field op_interp_ig4(const Field& f, int d) {
 // The field's box along d is the n cells [lo, hi); the first and last three
 // cells take one-sided derivatives, the interfaces next to the walls one-sided
 // states, so that D = delta o interp is defined on every cell and is the same
-// operator in every line (the metric identities of Sec. 6 still hold).
+// operator in every line (the metric identities of Sec. 7 still hold).
 // ---------------------------------------------------------------------------
 // first derivative on the whole box
 static Field op_e6_c(const Field& f, int d) {
@@ -721,13 +721,13 @@ int orc_solver::centroids_from_nodes(const double* nodes, const double* vel, Fie
   return 0;
 }
 
-// Sec. 4 and Sec. 6: conservative metrics, Jacobian, time metrics, face
+// Sec. 4 and Sec. 7: conservative metrics, Jacobian, time metrics, face
 // interpolation and the GCL term.  xc/vc: centroids (velocities) on ext.
 int orc_solver::build_geometry(const Field* xc, const Field* vc) {
   ORC_PHASE(PH_GEOM);
   const int sch = p.metric_scheme;
   Field xd[3][3];  // xd[a][d] = d x_a / d xi_d
-  // Sec. 6 operators built from the scheme's own gradients (step 2): E6 for MEG6, IG4 for MIG4;
+  // Sec. 7 operators built from the scheme's own gradients (step 2): E6 for MEG6, IG4 for MIG4;
   // App. C on wall-bounded axes; the E4 operators of App. D for the non-conservative control
   const bool ig4 = sch == 0 && p.gradient_scheme == 1;
   auto Iop = [&](const Field& f, int d) {
@@ -806,7 +806,7 @@ int orc_solver::build_geometry(const Field* xc, const Field* vc) {
     }
   }
 
-  // Sec. 6 step 3: interpolate whole products (xi_x/J) to interfaces
+  // Sec. 7 step 3: interpolate whole products (xi_x/J) to interfaces
   for (int d = 0; d < nd; ++d) {
     Box fb = inner;
     fb.lo[d] = -1;

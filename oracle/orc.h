@@ -32,7 +32,7 @@ typedef struct {
                             one-sided formulas of App. C */
   int bc[3][2];          /* non-periodic sides: ORC_BC_ZEROGRAD, ORC_BC_INFLOW (x-low only) or
                             ORC_BC_WALL (slip wall) */
-  int metric_scheme;     /* 0 = conservative metrics with the MEG6 operator (Sec. 6),
+  int metric_scheme;     /* 0 = conservative metrics with the MEG6 operator (Sec. 7),
                             1 = non-conservative metrics with E4 (App. D, negative control) */
   double gamma, prandtl;
   double reynolds;       /* <= 0: Euler (no viscous flux); mu_ref = 1/reynolds */

@@ -90,7 +90,7 @@ __global__ void k_face_metrics(GeoArgs G, Box b0, Box b1, Box b2) {
   body_face_metrics(G, d, i, j, k);
 }
 
-// ---- MIG4 metrics: one thread per geometry line (set-up work; Sec. 6 step 2 with IG4)
+// ---- MIG4 metrics: one thread per geometry line (set-up work; Sec. 7 step 2 with IG4)
 __global__ void k_ig4_geo_factor(double* t, int m) { ig4_geo_factor(t, m); }
 
 // D_d of one direction on its own (the App. C closure of a wall-bounded axis of a MIG4 grid)
@@ -163,7 +163,7 @@ __global__ void k_metrics_given(GeoArgs G, Box b) {
   body_metrics(G, i, j, k, true);
 }
 
-// Sec. 6 step 3 with IG4: interface metrics of direction d, one line of the cell-metric box per
+// Sec. 7 step 3 with IG4: interface metrics of direction d, one line of the cell-metric box per
 // thread (xs: the cross-section of the interior)
 __global__ void k_ig4_face_metrics(GeoArgs G, int d, Box xs, const double* t, double* w) {
   BOX_THREAD(xs);
@@ -1194,7 +1194,7 @@ Box cross_section(Box b, int d) {
   return b;
 }
 
-// MIG4 metrics (Sec. 6 steps 2-3 with IG4 line solves; App. C on wall-bounded axes)
+// MIG4 metrics (Sec. 7 steps 2-3 with IG4 line solves; App. C on wall-bounded axes)
 gbr_status run_geometry_ig4(gbr_ctx* c, const GeoArgs& G, const GeoBoxes& B) {
   const Layout& L = c->L;
   cudaStream_t st = c->stream;

@@ -243,11 +243,11 @@ GBR_HD double gmax(double a, double b) { return bitsd(bmax(dbits(a), dbits(b)));
 GBR_HD double gabs(double x) { return bitsd(dbits(x) & kMag); }
 GBR_HD double minmod(double a, double b) { return bitsd(bminmod(dbits(a), dbits(b))); }
 
-// Composite stencils of the MEG6 interface operators (Sec. 6): the interface
+// Composite stencils of the MEG6 interface operators (Sec. 7): the interface
 // value I(f)_{i+1/2} = avg of the van Leer left/right states built from E6
 // gradients and the gradient-based second derivative, and the derivative
 // D(f)_i = I(f)_{i+1/2} - I(f)_{i-1/2}.  The D weights 2282, -546, 89, -3, -1
-// (over 2880) are the ones printed in the Sec. 6 proof; the I weights follow
+// (over 2880) are the ones printed in the Sec. 7 proof; the I weights follow
 // from the same three formulas: 1821, -461, 85, -4, -1 (over 2880) on
 // (f_i + f_{i+1}), (f_{i-1} + f_{i+2}), ... .
 constexpr double kD1 = 2282.0 / 2880.0, kD2 = -546.0 / 2880.0, kD3 = 89.0 / 2880.0, kD4 = -3.0 / 2880.0,
@@ -331,7 +331,7 @@ GBR_HD long long line_base(const Layout& L, int d, int i, int j, int k) {
 }
 
 // ---------------------------------------------------------------------------
-// MIG4 metric operators (Sec. 6 step 2: the metric derivative and interpolation use the scheme's
+// MIG4 metric operators (Sec. 7 step 2: the metric derivative and interpolation use the scheme's
 // own gradients; for MIG4 x' is the IG4 system of Eq. IG4_grads).  A geometry line is solved as a
 // whole with the explicit end rows (second-order one-sided, fourth-order biased, fourth-order
 // central at the three end points of each side, IG4 rows between); on periodic axes the line is
@@ -402,7 +402,7 @@ GBR_HD double ig4_geo_face(const F& f, const LineRef& w, int x) {
 }
 
 // ---------------------------------------------------------------------------
-// Geometry bodies (Sec. 3, Sec. 4, Sec. 6)
+// Geometry bodies (Sec. 3, Sec. 4, Sec. 7)
 // ---------------------------------------------------------------------------
 struct GeoArgs {
   Layout L;
@@ -444,7 +444,7 @@ GBR_HD void body_centroid(const GeoArgs& G, int i, int j, int k) {
   }
 }
 
-// Sec. 6 step 2: consistent derivative of the coordinates, xd[a][d] = D_d(x_a)
+// Sec. 7 step 2: consistent derivative of the coordinates, xd[a][d] = D_d(x_a)
 GBR_HD void body_coord_derivative(const GeoArgs& G, int d, int i, int j, int k) {
   const Layout& L = G.L;
   const long long e = eidx(L, i, j, k);
@@ -461,7 +461,7 @@ GBR_HD void body_coord_derivative(const GeoArgs& G, int d, int i, int j, int k) 
   }
 }
 
-// D along d of the product a * b (Sec. 6 step 2), App. C on a closed axis
+// D along d of the product a * b (Sec. 7 step 2), App. C on a closed axis
 GBR_HD double metric_D_prod(const Layout& L, const double* a, const double* b, int d, int i, int j, int k) {
   if (L.closed[d]) {
     const long long base = line_base(L, d, i, j, k), s = L.es[d];
@@ -470,7 +470,7 @@ GBR_HD double metric_D_prod(const Layout& L, const double* a, const double* b, i
   return stencil_D_prod(a, b, eidx(L, i, j, k), L.es[d]);
 }
 
-// interface value at i+1/2 along d of the cell field f (Sec. 6 step 3), App. C on a closed axis
+// interface value at i+1/2 along d of the cell field f (Sec. 7 step 3), App. C on a closed axis
 GBR_HD double metric_I(const Layout& L, const double* f, int d, int i, int j, int k) {
   if (L.closed[d]) {
     const long long base = line_base(L, d, i, j, k), s = L.es[d];
@@ -536,7 +536,7 @@ GBR_HD void body_metrics(const GeoArgs& G, int i, int j, int k, bool mh_given = 
   }
 }
 
-// Sec. 6 step 3: interface values of whole metric products, interface i+1/2 along d
+// Sec. 7 step 3: interface values of whole metric products, interface i+1/2 along d
 GBR_HD void body_face_metrics(const GeoArgs& G, int d, int i, int j, int k) {
   const Layout& L = G.L;
   const long long EC = L.ecount, FC = L.fcount[d];
@@ -567,7 +567,7 @@ GBR_HD void body_gcl(const GeoArgs& G, int i, int j, int k) {
   G.jac[c] = 1.0 / G.det[eidx(L, i, j, k)];
 }
 
-// Sec. 7.2 motion families evaluated at extended node index (i, j, k)
+// Sec. 8.2 motion families evaluated at extended node index (i, j, k)
 struct Motion {
   double origin[3], h[3], amp[3], omega, k[3][3];
 };

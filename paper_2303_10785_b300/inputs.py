@@ -117,7 +117,7 @@ def nodes_tgv_3d(n=128, amp_frac=0.1):
 
 
 def nodes_sinusoidal_3d(n=20, L=4.0):
-    """Sinusoidal freestream grid of the paper's 3D uniform-flow test (Sec. 7.1.1, node index = i - 1)."""
+    """Sinusoidal freestream grid of the paper's 3D uniform-flow test (Sec. 8.1.1, node index = i - 1)."""
     d0 = L / n
     xmin = -L / 2
 
@@ -170,7 +170,7 @@ def nodes_skewed_2d(n, lengths, skew_deg=20.0, jitter=0.1, seed=3):
 
 class SinusoidalMotion:
     """Prescribed node motion x_a = o_a + m_a h_a + A_a sin(2 pi w t) prod_b S_ab(m_b h_b),
-    where S_ab(s) = sin(k_ab s) when k_ab != 0 and 1 otherwise (Sec. 7.2 families)."""
+    where S_ab(s) = sin(k_ab s) when k_ab != 0 and 1 otherwise (Sec. 8.2 families)."""
 
     def __init__(self, n, h, amp, omega, k, origin=None):
         self.nd = len(n)
@@ -217,7 +217,7 @@ def motion_dynamic_2d(n=256, L=10.0, T=1.0, amp=0.1):
 
 
 def motion_deforming_3d(n=32, L=12.0, A=1.5, nw=4, omega=1.0):
-    """Sec. 7.2.1: x = xmin + dx0 [i + A sin(2 pi w t) sin(n pi j dy0/Ly) sin(n pi k dz0/Lz)], cyclic."""
+    """Sec. 8.2.1: x = xmin + dx0 [i + A sin(2 pi w t) sin(n pi j dy0/Ly) sin(n pi k dz0/Lz)], cyclic."""
     d0 = L / n
     kk = nw * np.pi / L
     k = ((0.0, kk, kk), (kk, 0.0, kk), (kk, kk, 0.0))

@@ -6,7 +6,7 @@ components share the momentum-vector scale).  Two 3D cases:
 * the viscous Taylor-Green vortex (Re = 1600, M = 0.1, constant mu) on the 0.1 h sinusoidally
   perturbed periodic mesh of the 3D workload, 32^3 cells, CFL 0.2 with the time step computed on
   each side every step (they must agree to round-off as well);
-* a viscous flow on the deforming mesh of Sec. 7.2.1 (16^3 cells, every node oscillating by
+* a viscous flow on the deforming mesh of Sec. 8.2.1 (16^3 cells, every node oscillating by
   1.5 cell widths), the geometry, time metrics and GCL term recomputed at every stage time,
   fixed dt = 0.01 for 100 steps (one full period of the motion).
 

@@ -3,7 +3,7 @@
 The CUDA path solves each grid line's tridiagonal IG4 system with factors computed once per
 direction (cyclic by Sherman-Morrison on periodic axes, explicit end rows on open axes); the
 oracle builds and solves each line's system on its own.  The MIG4 metrics are built from IG4
-too (Sec. 6 step 2): one line solve per geometry line, on periodic axes over the unwrapped line
+too (Sec. 7 step 2): one line solve per geometry line, on periodic axes over the unwrapped line
 extended 64 cells beyond each side.  Same tolerances as the MEG6 parity tests: metrics within
 1e-13 of their scale, right-hand sides within 1e-12 of the cancellation scale, states within
 1e-12 after a step; the mixed path within its own FP32 tolerance."""

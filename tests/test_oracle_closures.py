@@ -12,7 +12,7 @@ Sutherland's law (Sec. 2), each against a closed form computed here without the 
   energy right-hand side is div(kappa grad T) with kappa = mu gamma / ((gamma - 1) Pr):
   -kappa a k^2 sin(k y) for constant mu; with Sutherland's mu(T) the exact divergence is
   formed symbolically (sympy).  Fourth order on a uniform mesh (Sec. 5.2), second on the
-  wavy mesh (the interface metric/state product, Sec. 6 step 3), for several gamma and Pr;
+  wavy mesh (the interface metric/state product, Sec. 7 step 3), for several gamma and Pr;
   second order with Sutherland's mu, evaluated at a second-order interface temperature.
 * Sutherland's law in its textbook dimensional form mu/mu_ref = (T/T_ref)^(3/2) (T_ref + S)/(T + S)
   with air's S = 110.4 K, and its two asymptotes (mu ~ T^(3/2) for T << S, mu ~ T^(1/2) for T >> S).

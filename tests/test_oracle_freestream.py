@@ -1,4 +1,4 @@
-"""Oracle pins: freestream preservation on static and deforming meshes (Sec. 7.1.1, Sec. 7.2.1).
+"""Oracle pins: freestream preservation on static and deforming meshes (Sec. 8.1.1, Sec. 8.2.1).
 
 The paper reports machine-zero y/z-velocity errors with the conservative
 (freestream-preserving) metrics and 1e-3 (sinusoidal) / 1e-1 (random)

@@ -1,4 +1,4 @@
-"""Oracle pins: conservative metrics, metric identities, Jacobian and the GCL term (Sec. 4, Sec. 6, App. D)."""
+"""Oracle pins: conservative metrics, metric identities, Jacobian and the GCL term (Sec. 4, Sec. 7, App. D)."""
 import numpy as np
 import pytest
 

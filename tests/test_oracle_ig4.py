@@ -119,7 +119,7 @@ def _lambda1(th, scheme):
 
 
 def _interface_and_derivative(th, scheme):
-    """Transfer functions of Sec. 6 for the cell mode f_m = e^{i theta (m + 1/2)}: the interface
+    """Transfer functions of Sec. 7 for the cell mode f_m = e^{i theta (m + 1/2)}: the interface
     value I (Eq. FP-interp / interp-formulae, with f'' = 2 (f_{i+1} - 2 f_i + f_{i-1}) - (f'_{i+1} -
     f'_{i-1}) / 2) at i + 1/2 relative to f_i, and D = I_{i+1/2} - I_{i-1/2} (Eq. FP-interp2)
     relative to f_i."""
@@ -132,7 +132,7 @@ def _interface_and_derivative(th, scheme):
 
 @pytest.mark.parametrize("scheme", ["mig4", "meg6"])
 def test_metrics_are_the_schemes_own_operators(scheme):
-    """Sec. 6 step 2: the metric derivative and interpolation use the scheme's own gradients (IG4 for
+    """Sec. 7 step 2: the metric derivative and interpolation use the scheme's own gradients (IG4 for
     MIG4, E6 for MEG6).  Grid x = h i, y = h j + B sin(theta i) sin(theta j) (periodic, theta = 2 pi/n):
     the centroid y_c = h (j + 1/2) + B c^2 s_i s_j with c = cos(theta/2), s_m = sin(theta (m + 1/2)), so
     every metric and interface metric is a Fourier mode whose amplitude is the operator's transfer

@@ -1,6 +1,6 @@
-"""Oracle pins: the one-dimensional operators and the worked coefficients printed in Sec. 6.
+"""Oracle pins: the one-dimensional operators and the worked coefficients printed in Sec. 7.
 
-The paper prints (Sec. 6, freestream proof) the composite stencil of the
+The paper prints (Sec. 7, freestream proof) the composite stencil of the
 averaged MEG6 interface derivative, 2282, -546, 89, -3, -1 over 2880, and the
 leading/trailing terms of the triple composite (xi_x)_{i+1/2} - (xi_x)_{i-1/2}
 over 23887872000 = 2880^3.  Reproducing them pins the E6 sign reading, the
@@ -13,7 +13,7 @@ import pytest
 import oracle as O
 from paper_2303_10785_b300 import inputs as I
 
-PRINTED_D = {1: 2282, 2: -546, 3: 89, 4: -3, 5: -1}  # Sec. 6, coefficient of (y_{i+m} - y_{i-m}) / 2880
+PRINTED_D = {1: 2282, 2: -546, 3: 89, 4: -3, 5: -1}  # Sec. 7, coefficient of (y_{i+m} - y_{i-m}) / 2880
 
 
 def test_composite_derivative_stencil_matches_printed_coefficients():

@@ -7,7 +7,7 @@
   off (Sec. 5.1) and for the alpha-damping viscous term (Sec. 5.2) on uniform
   meshes; at least 2nd order on the wavy mesh, where the interface flux is the
   product of a reconstructed state and a separately interpolated metric (each
-  a flux-difference value exact only for linear data, Sec. 6 step 3), which
+  a flux-difference value exact only for linear data, Sec. 7 step 3), which
   costs an O(h^2) cross term.  The Taylor-Green initial energy decay rate
   -(3/4)/Re, and a Sod slab against the exact Riemann solution.
 """
