@@ -77,7 +77,7 @@ enum { GBR_PREC_FP64 = 0, GBR_PREC_MIXED = 1 };
  *                periodic axes over the unwrapped line extended 64 cells beyond each
  *                side (IG4 on the unbounded line to round-off); wall-bounded axes
  *                without ghost nodes keep the App. C operators.
- *                Not available in gbr_rhs_static or in a batch. */
+ *                Not available in gbr_rhs_static. */
 enum { GBR_GRAD_MEG6 = 0, GBR_GRAD_MIG4 = 1 };
 
 typedef struct {
@@ -270,14 +270,16 @@ gbr_status gbr_rhs_static(const gbr_params* p, const double* nodes, const double
 /* ---------------------------------------------------------------------------
  * Batched stepping (not in the paper, whose solver runs one job per GPU).
  * A batch advances many contexts together: per kind of member (ndim, viscous,
- * precision) every phase of an SSP-RK3 step is one launch over a
- * block -> (member, tile) work list, and the whole step (time steps on the
- * device, three stages, time advance) is captured as one CUDA graph, replayed
- * until the membership changes.  Each member keeps its own state, metrics, time
- * step and error flag; its results are bitwise those of gbr_rk_step on it alone.
- * Members must be static-mesh contexts created on the batch's stream; while a
- * member, a context is advanced only through the batch (other calls on it stay
- * in stream order).  Device tables live in a caller-owned workspace of
+ * precision, moving mesh, gradient scheme) every phase of an SSP-RK3 step is one
+ * launch over a block -> (member, tile) work list, and the whole step (time steps
+ * on the device, three stages, time advance) is captured as one CUDA graph,
+ * replayed until the membership changes.  Members with a prescribed motion
+ * (gbr_set_motion) recompute their geometry at every stage time with their own
+ * launches, and MIG4 members solve their gradient lines with their own launches,
+ * inside the same step.  Each member keeps its own state, metrics, time step and
+ * error flag; its results are bitwise those of gbr_rk_step on it alone.  Members
+ * must be contexts created on the batch's stream; while a member, a context is
+ * advanced only through the batch (other calls on it stay in stream order).  Device tables live in a caller-owned workspace of
  * gbr_batch_workspace_bytes(max_members) bytes (256-byte aligned).
  * Not thread-safe per batch. */
 typedef struct gbr_batch gbr_batch;
@@ -299,7 +301,9 @@ gbr_status gbr_batch_step(gbr_batch* b, int n_steps);
 /* Drain the stream (GBR_ETIMEOUT after timeout_s > 0) and check every member's
  * error flag: GBR_ENONFINITE names the first bad member (*bad_member, or -1). */
 gbr_status gbr_batch_sync(gbr_batch* b, double timeout_s, int* bad_member);
-/* Members, kinds, kernel launches per step and launches issued so far. */
+/* Members, kinds, kernel launches per step and launches issued so far.  Without
+ * graphs, a batch with moving-mesh or MIG4 members reports -1 launches per step
+ * until its first step has been enqueued. */
 gbr_status gbr_batch_info(gbr_batch* b, int* members, int* kinds, long long* launches_per_step, long long* launches);
 /* The chosen tuning of kind `kind` (0 .. kinds-1). */
 gbr_status gbr_batch_tuning(gbr_batch* b, int kind, int* nd, int* viscous, int* precision, int* face_block,

@@ -1195,9 +1195,8 @@ Box cross_section(Box b, int d) {
 }
 
 // MIG4 metrics (Sec. 7 steps 2-3 with IG4 line solves; App. C on wall-bounded axes)
-gbr_status run_geometry_ig4(gbr_ctx* c, const GeoArgs& G, const GeoBoxes& B) {
+gbr_status run_geometry_ig4(gbr_ctx* c, const GeoArgs& G, const GeoBoxes& B, cudaStream_t st) {
   const Layout& L = c->L;
-  cudaStream_t st = c->stream;
   constexpr int kLineBlock = 64;
   for (int d = 0; d < L.nd; ++d) {
     if (L.closed[d]) {
@@ -1226,15 +1225,14 @@ gbr_status run_geometry_ig4(gbr_ctx* c, const GeoArgs& G, const GeoBoxes& B) {
   return GBR_OK;
 }
 
-gbr_status run_geometry(gbr_ctx* c) {
+gbr_status run_geometry(gbr_ctx* c, cudaStream_t st) {
   const Layout& L = c->L;
   GeoArgs G = geo_args(c);
-  cudaStream_t st = c->stream;
   const GeoBoxes B = geo_boxes(L);
   k_centroid<<<grid_of(B.ext, kBlock), kBlock, 0, st>>>(G, B.ext);
   CKL("k_centroid");
   if (c->p.gradient_scheme == GBR_GRAD_MIG4) {
-    gbr_status s4 = run_geometry_ig4(c, G, B);
+    gbr_status s4 = run_geometry_ig4(c, G, B, st);
     if (s4 != GBR_OK) return s4;
   } else {
     unsigned gmax = 0;
@@ -1268,12 +1266,15 @@ gbr_status run_geometry(gbr_ctx* c) {
   return GBR_OK;
 }
 
-gbr_status run_motion(gbr_ctx* c, double stage_c) {
+gbr_status run_geometry(gbr_ctx* c) { return run_geometry(c, c->stream); }
+
+gbr_status run_motion(gbr_ctx* c, double stage_c, cudaStream_t st) {
   const Box bn = geo_boxes(c->L).nodes;
-  k_motion<<<grid_of(bn, kBlock), kBlock, 0, c->stream>>>(c->L, c->motion, c->scal, stage_c, c->nodes, c->nvel, bn);
+  k_motion<<<grid_of(bn, kBlock), kBlock, 0, st>>>(c->L, c->motion, c->scal, stage_c, c->nodes, c->nvel, bn);
   CKL("k_motion");
   return GBR_OK;
 }
+gbr_status run_motion(gbr_ctx* c, double stage_c) { return run_motion(c, stage_c, c->stream); }
 
 template <class R>
 RhsArgsT<R> rhs_args_r(gbr_ctx* c, const double* q) {
@@ -1338,6 +1339,55 @@ gbr_status launch_face(gbr_ctx* c, const RhsArgsT<R>& A, int d, const Box& b) {
   return GBR_OK;
 }
 
+// the shared-memory opt-in of the MIG4 line-solve kernels (above the 48 KB default), once per
+// instantiation; also called at gbr_create, so that no first launch sets it inside a graph capture
+template <int ND, class R>
+void ig4_attributes() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(k_ig4t<ND, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIg4SmemMax);
+  cudaFuncSetAttribute(k_ig4s<ND, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIg4SmemMax);
+  done = true;
+}
+
+// MIG4 first derivatives of every direction (Eq. IG4_grads): one line solve per grid line, on a
+// tile staged by TMA (y/z lines), by cp.async (x-lines and the fallback) or in global memory
+template <int ND, class R>
+gbr_status launch_ig4_grads(gbr_ctx* c, const RhsArgsT<R>& A, cudaStream_t st) {
+  ig4_attributes<ND, R>();
+  const Layout& L = c->L;
+  const RhsBoxes B = rhs_boxes(L);
+  const int nf = L.nv + (c->visc ? 1 : 0);
+  for (int e = 0; e < ND; ++e) {
+    Box lines = B.grad1[e];
+    lines.lo[e] = 0;
+    lines.hi[e] = 1;
+    const R* table;
+    if constexpr (sizeof(R) == sizeof(float)) table = c->ig4f[e];
+    else table = c->ig4[e];
+    const bool per = L.per[e] != 0;
+    const int tlen = (int)ig4_table_len(L.n[e], per);
+    const size_t smem = ig4_smem_bytes<R>(L.n[e], per);
+    if (c->ig4_tma[e]) {
+      const int bx = (e == 1) ? 2 : 1;
+      const int x0p = (lines.lo[0] + L.hp[0]) & ~3;
+      const int tiles = (lines.hi[0] + L.hp[0] - x0p + kIg4Lines - 1) / kIg4Lines;
+      const int nb = lines.hi[bx] - lines.lo[bx];
+      k_ig4t<ND, R><<<dim3((unsigned)(tiles * nb), nf), kIg4Lines, ig4t_smem_bytes<R>(L.n[e], per), st>>>(
+          A, e, lines, table, tlen, x0p, c->ig4_tm[e][0], c->ig4_tm[e][1], c->err);
+    } else if (smem <= kIg4SmemMax) {
+      const int a = (e == 0) ? 1 : 0, bx = 3 - e - a;
+      const int na = lines.hi[a] - lines.lo[a], nb = lines.hi[bx] - lines.lo[bx];
+      const unsigned tiles = (unsigned)((na + kIg4Lines - 1) / kIg4Lines) * (unsigned)nb;
+      k_ig4s<ND, R><<<dim3(tiles, nf), kIg4Lines, smem, st>>>(A, e, lines, table, ig4_srow(L.n[e]), tlen);
+    } else {
+      k_ig4<ND, R><<<dim3(grid_of(lines, 128), nf), 128, 0, st>>>(A, e, lines, table);
+    }
+    CKL("k_ig4");
+  }
+  return GBR_OK;
+}
+
 // one evaluation of L(qs [+ dq_in]): out = L (mode 0) or the RK combination (mode 1), the latter
 // in increments when dq_in / dq_out are given (mixed path, body_update)
 template <int ND, class R>
@@ -1363,44 +1413,8 @@ gbr_status run_rhs_nd(gbr_ctx* c, const double* qs, const double* q0, double* ou
     g2 = std::max(g2, grid_of(B.grad2[e], kBlock));
   }
   if (c->p.gradient_scheme == GBR_GRAD_MIG4) {
-    const int nf = L.nv + (c->visc ? 1 : 0);
-    for (int e = 0; e < ND; ++e) {
-      Box lines = B.grad1[e];
-      lines.lo[e] = 0;
-      lines.hi[e] = 1;
-      const R* table;
-      if constexpr (sizeof(R) == sizeof(float)) table = c->ig4f[e];
-      else table = c->ig4[e];
-      const bool per = L.per[e] != 0;
-      const int tlen = (int)ig4_table_len(L.n[e], per);
-      const size_t smem = ig4_smem_bytes<R>(L.n[e], per);
-      if (c->ig4_tma[e]) {
-        static bool attr_t = false;
-        if (!attr_t) {
-          cudaFuncSetAttribute(k_ig4t<ND, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIg4SmemMax);
-          attr_t = true;
-        }
-        const int bx = (e == 1) ? 2 : 1;
-        const int x0p = (lines.lo[0] + L.hp[0]) & ~3;
-        const int tiles = (lines.hi[0] + L.hp[0] - x0p + kIg4Lines - 1) / kIg4Lines;
-        const int nb = lines.hi[bx] - lines.lo[bx];
-        k_ig4t<ND, R><<<dim3((unsigned)(tiles * nb), nf), kIg4Lines, ig4t_smem_bytes<R>(L.n[e], per), st>>>(
-            A, e, lines, table, tlen, x0p, c->ig4_tm[e][0], c->ig4_tm[e][1], c->err);
-      } else if (smem <= kIg4SmemMax) {
-        static bool attr_set = false;  // one opt-in per instantiation (above the 48 KB default)
-        if (!attr_set) {
-          cudaFuncSetAttribute(k_ig4s<ND, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIg4SmemMax);
-          attr_set = true;
-        }
-        const int a = (e == 0) ? 1 : 0, bx = 3 - e - a;
-        const int na = lines.hi[a] - lines.lo[a], nb = lines.hi[bx] - lines.lo[bx];
-        const unsigned tiles = (unsigned)((na + kIg4Lines - 1) / kIg4Lines) * (unsigned)nb;
-        k_ig4s<ND, R><<<dim3(tiles, nf), kIg4Lines, smem, st>>>(A, e, lines, table, ig4_srow(L.n[e]), tlen);
-      } else {
-        k_ig4<ND, R><<<dim3(grid_of(lines, 128), nf), 128, 0, st>>>(A, e, lines, table);
-      }
-      CKL("k_ig4");
-    }
+    gbr_status sg = launch_ig4_grads<ND, R>(c, A, st);
+    if (sg != GBR_OK) return sg;
   } else {
     if constexpr (ND == 3 && sizeof(R) == sizeof(float)) {
       // one z-marching block per 32 x 8 tile of the union of the three boxes and chunk of planes
@@ -1708,6 +1722,13 @@ gbr_status gbr_create(const gbr_params* p, const double* nodes, const double* no
     return s;
   }
   if (p->gradient_scheme == GBR_GRAD_MIG4) {
+    if (L.nd == 3) {
+      if (p->precision == GBR_PREC_MIXED) ig4_attributes<3, float>();
+      else ig4_attributes<3, double>();
+    } else {
+      if (p->precision == GBR_PREC_MIXED) ig4_attributes<2, float>();
+      else ig4_attributes<2, double>();
+    }
     ig4_encode_maps(c);
     for (int d = 0; d < L.nd; ++d) {
       if (!L.closed[d]) {  // the metric line solves (extended lines, cell-metric lines)

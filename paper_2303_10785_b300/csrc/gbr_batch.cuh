@@ -6,9 +6,14 @@
 // gbr_rk_step on the member alone (same bodies, same data, same order).
 //
 // Design:
-// * Members are grouped by kind: (ndim, viscous, precision).  Per kind, each
+// * Members are grouped by kind: (ndim, viscous, precision, moving mesh, gradient
+//   scheme).  Per kind, each
 //   phase of an SSP-RK3 step is ONE launch over a work list of items
 //   (member, sub-box, first block, blocks): the block -> (member, tile) map.
+//   Moving-mesh members also recompute their geometry at each stage time (their
+//   own motion, metric and GCL launches, in gbr_rk_step's order), and MIG4
+//   members solve their IG4 lines with their own launches; the other phases of
+//   those kinds are batched as for the rest.
 // * Phase kernels are persistent: the grid is the number of co-resident CTAs (or
 //   fewer), and CTA b takes the contiguous block range [b*chunk, (b+1)*chunk)
 //   of the work list, finding its first item by binary search and walking on.
@@ -118,7 +123,7 @@ __global__ void __launch_bounds__(kBlock) kb_grad12(const BatchJob<R>* jobs, con
 // each work block's barriers); FP32 at 7 blocks of 128 threads per SM (as k_face), FP64 at 384
 // threads (at most 168 registers: 4 % faster than the unconstrained 234 on a batch of 64^3 TGV
 // and 256^2 vortex jobs).
-template <int ND, bool VISC, class R, int BS>
+template <int ND, bool VISC, bool MOV, class R, int BS>
 __global__ void __launch_bounds__(BS, sizeof(R) == 4 ? 896 / BS : (BS < 384 ? 384 / BS : 1))
     kb_face(const BatchJob<R>* jobs, const WorkItem* items, int n, int total) {
   __shared__ BoundSlot<ND, R> slots[BS];
@@ -129,17 +134,17 @@ __global__ void __launch_bounds__(BS, sizeof(R) == 4 ? 896 / BS : (BS < 384 ? 38
     const bool valid = t < box_size(J.faces[it.sub]);
     int i = 0, j = 0, k = 0;
     if (valid) box_coord(J.faces[it.sub], t, i, j, k);
-    face_block<ND, VISC, false>(J.A, it.sub, valid, i, j, k, slots, &count);
+    face_block<ND, VISC, MOV>(J.A, it.sub, valid, i, j, k, slots, &count);
   });
 }
 
-template <int ND, class R, bool SP>
+template <int ND, bool MOV, class R, bool SP>
 __global__ void __launch_bounds__(kBlock, kStreamBlocks) kb_update(const BatchJob<R>* jobs, const WorkItem* items, int n, int total,
                                                      int stage) {
   for_work(items, n, total, [&](const WorkItem& it, int lb) {
     const BatchJob<R>& J = jobs[it.job];
     BATCH_CELL(J.inner);
-    if (body_update<ND, false, R, SP>(J.U[stage], i, j, k)) atomicOr(J.err, 1);
+    if (body_update<ND, MOV, R, SP>(J.U[stage], i, j, k)) atomicOr(J.err, 1);
   });
 }
 
@@ -191,8 +196,10 @@ __global__ void kb_scalar(const BatchJob<R>* jobs, int n, int what) {
 constexpr int kFaceBlockOptions[3] = {64, 128, 256};
 
 struct KindKey {
-  int nd, visc, prec;
-  bool operator==(const KindKey& o) const { return nd == o.nd && visc == o.visc && prec == o.prec; }
+  int nd, visc, prec, mov, ig4;
+  bool operator==(const KindKey& o) const {
+    return nd == o.nd && visc == o.visc && prec == o.prec && mov == o.mov && ig4 == o.ig4;
+  }
 };
 
 struct Tuning {
@@ -297,9 +304,7 @@ BatchJob<R> make_job(gbr_ctx* c, double cfl) {
       U.mode = 0;
     }
   }
-  J.D = dt_args(c);
-  J.D.mt = nullptr;  // static members only
-  J.D.mt32 = nullptr;
+  J.D = dt_args(c);  // the time metrics of a moving member (null for a static one)
   for (int s = 0; s < 3; ++s) J.q[s] = c->q[s];
   if (rk_in_increments(c)) {
     // the same increment form as gbr_rk_step: Q_s = Q^n + D_s, D1 and D2 in the stage buffers
@@ -374,17 +379,41 @@ unsigned persistent_grid(gbr_batch* b, KernelT kernel, int block, int total) {
   return (unsigned)std::max(1, std::min(total, resident_ctas(b, kernel, block)));
 }
 
-template <int ND, bool VISC, class R, int BS>
+template <int ND, bool VISC, bool MOV, class R, int BS>
 gbr_status launch_face_kind(gbr_batch* b, const Kind& K, const BatchJob<R>* jobs) {
-  auto kern = kb_face<ND, VISC, R, BS>;
+  auto kern = kb_face<ND, VISC, MOV, R, BS>;
   const unsigned g = persistent_grid(b, kern, BS, K.total[WL_FACE]);
   kern<<<g, BS, 0, b->cur>>>(jobs, K.d_items[WL_FACE], (int)K.items[WL_FACE].size(), K.total[WL_FACE]);
   BK(cudaGetLastError(), "kb_face");
   return GBR_OK;
 }
 
+// work of one member launched on the batch's current stream (its geometry, its IG4 solves),
+// counted in `launches` through the member's own launch counter
+template <class Fn>
+gbr_status member_launches(gbr_batch* b, gbr_ctx* c, long long& launches, Fn fn) {
+  const long long before = c->launches;
+  const gbr_status s = fn();
+  launches += c->launches - before;
+  if (s != GBR_OK) return bfail(b, s, c->last_error);
+  return GBR_OK;
+}
+
+// the geometry of every member with a prescribed motion at the stage time t^n + stage_c dt
+gbr_status enqueue_geometry(gbr_batch* b, const Kind& K, double stage_c, long long& launches) {
+  for (gbr_ctx* c : K.members) {
+    if (!c->have_motion) continue;
+    gbr_status s = member_launches(b, c, launches, [&] {
+      gbr_status r = run_motion(c, stage_c, b->cur);
+      return r == GBR_OK ? run_geometry(c, b->cur) : r;
+    });
+    if (s != GBR_OK) return s;
+  }
+  return GBR_OK;
+}
+
 // the right-hand side of `stage` (0..3, 3 = autotuning evaluation) for one kind
-template <int ND, bool VISC, class R>
+template <int ND, bool VISC, bool MOV, class R>
 gbr_status enqueue_rhs(gbr_batch* b, const Kind& K, int stage, long long& launches) {
   const BatchJob<R>* jobs = reinterpret_cast<const BatchJob<R>*>(K.d_jobs);
   cudaStream_t st = b->cur;
@@ -395,7 +424,23 @@ gbr_status enqueue_rhs(gbr_batch* b, const Kind& K, int stage, long long& launch
         jobs, K.d_items[WL_PAD], (int)K.items[WL_PAD].size(), K.total[WL_PAD], qin);
     BK(cudaGetLastError(), "kb_prim_halo");
   }
-  if constexpr (kFaceFormsG2<R>) {
+  if (K.key.ig4) {
+    // MIG4: each member's line solves (their tiles and launch shapes are per member), then, on the
+    // FP64 path, the second derivatives of the whole kind in one launch
+    for (gbr_ctx* c : K.members) {
+      gbr_status s = member_launches(b, c, launches,
+                                     [&] { return launch_ig4_grads<ND, R>(c, rhs_args_r<R>(c, c->q[0]), st); });
+      if (s != GBR_OK) return s;
+    }
+    ++launches;
+    if constexpr (!kFaceFormsG2<R>) {
+      auto k2 = kb_grad2<ND, R>;
+      k2<<<persistent_grid(b, k2, kBlock, K.total[WL_GRAD2]), kBlock, 0, st>>>(
+          jobs, K.d_items[WL_GRAD2], (int)K.items[WL_GRAD2].size(), K.total[WL_GRAD2]);
+      BK(cudaGetLastError(), "kb_grad2");
+      ++launches;
+    }
+  } else if constexpr (kFaceFormsG2<R>) {
     // FP32: the interface kernel forms f'' itself
     auto k1 = kb_grad1<ND, R>;
     k1<<<persistent_grid(b, k1, kBlock, K.total[WL_GRAD1]), kBlock, 0, st>>>(
@@ -421,16 +466,16 @@ gbr_status enqueue_rhs(gbr_batch* b, const Kind& K, int stage, long long& launch
   }
   gbr_status s;
   switch (K.tune.face_block) {
-    case 64: s = launch_face_kind<ND, VISC, R, 64>(b, K, jobs); break;
-    case 256: s = launch_face_kind<ND, VISC, R, 256>(b, K, jobs); break;
-    default: s = launch_face_kind<ND, VISC, R, 128>(b, K, jobs); break;
+    case 64: s = launch_face_kind<ND, VISC, MOV, R, 64>(b, K, jobs); break;
+    case 256: s = launch_face_kind<ND, VISC, MOV, R, 256>(b, K, jobs); break;
+    default: s = launch_face_kind<ND, VISC, MOV, R, 128>(b, K, jobs); break;
   }
   if (s != GBR_OK) return s;
   {
     // the sponge-capable instantiation only when a member of the kind has a sponge
     bool sponge = false;
     for (gbr_ctx* m : K.members) sponge |= m->have_sponge;
-    auto kern = sponge ? kb_update<ND, R, true> : kb_update<ND, R, false>;
+    auto kern = sponge ? kb_update<ND, MOV, R, true> : kb_update<ND, MOV, R, false>;
     kern<<<persistent_grid(b, kern, kBlock, K.total[WL_INNER]), kBlock, 0, st>>>(
         jobs, K.d_items[WL_INNER], (int)K.items[WL_INNER].size(), K.total[WL_INNER], stage);
     BK(cudaGetLastError(), "kb_update");
@@ -439,12 +484,15 @@ gbr_status enqueue_rhs(gbr_batch* b, const Kind& K, int stage, long long& launch
   return GBR_OK;
 }
 
-template <int ND, bool VISC, class R>
+template <int ND, bool VISC, bool MOV, class R>
 gbr_status enqueue_step_kind(gbr_batch* b, const Kind& K, long long& launches) {
   const BatchJob<R>* jobs = reinterpret_cast<const BatchJob<R>*>(K.d_jobs);
   cudaStream_t st = b->cur;
   const int n = (int)K.members.size();
   const unsigned gs = (unsigned)((n + 127) / 128);
+  gbr_status sg;
+  // as gbr_rk_step: the geometry at t^n (moving members), then the time step from Q^n
+  if (MOV && (sg = enqueue_geometry(b, K, 0.0, launches)) != GBR_OK) return sg;
   kb_scalar<R><<<gs, 128, 0, st>>>(jobs, n, 0);
   BK(cudaGetLastError(), "kb_scalar");
   launches += 2;
@@ -457,8 +505,10 @@ gbr_status enqueue_step_kind(gbr_batch* b, const Kind& K, long long& launches) {
   }
   kb_scalar<R><<<gs, 128, 0, st>>>(jobs, n, 1);
   BK(cudaGetLastError(), "kb_scalar");
+  const double stage_c[3] = {0.0, 1.0, 0.5};  // stage times t^n + c dt of SSP-RK3
   for (int stage = 0; stage < 3; ++stage) {
-    gbr_status s = enqueue_rhs<ND, VISC, R>(b, K, stage, launches);
+    if (MOV && stage > 0 && (sg = enqueue_geometry(b, K, stage_c[stage], launches)) != GBR_OK) return sg;
+    gbr_status s = enqueue_rhs<ND, VISC, MOV, R>(b, K, stage, launches);
     if (s != GBR_OK) return s;
   }
   kb_scalar<R><<<gs, 128, 0, st>>>(jobs, n, 2);
@@ -468,37 +518,39 @@ gbr_status enqueue_step_kind(gbr_batch* b, const Kind& K, long long& launches) {
 }
 
 // dispatch on the kind's template parameters
+template <int ND, bool VISC, class Fn>
+gbr_status dispatch_mov(const KindKey& k, Fn& fn) {
+  if (k.mov) return k.prec ? fn.template run<ND, VISC, true, float>() : fn.template run<ND, VISC, true, double>();
+  return k.prec ? fn.template run<ND, VISC, false, float>() : fn.template run<ND, VISC, false, double>();
+}
+
 template <class Fn>
 gbr_status dispatch_kind(const KindKey& k, Fn fn) {
-  if (k.nd == 3) {
-    if (k.visc) return k.prec ? fn.template run<3, true, float>() : fn.template run<3, true, double>();
-    return k.prec ? fn.template run<3, false, float>() : fn.template run<3, false, double>();
-  }
-  if (k.visc) return k.prec ? fn.template run<2, true, float>() : fn.template run<2, true, double>();
-  return k.prec ? fn.template run<2, false, float>() : fn.template run<2, false, double>();
+  if (k.nd == 3) return k.visc ? dispatch_mov<3, true>(k, fn) : dispatch_mov<3, false>(k, fn);
+  return k.visc ? dispatch_mov<2, true>(k, fn) : dispatch_mov<2, false>(k, fn);
 }
 
 struct StepFn {
   gbr_batch* b;
   const Kind* K;
   long long* launches;
-  template <int ND, bool VISC, class R>
-  gbr_status run() { return enqueue_step_kind<ND, VISC, R>(b, *K, *launches); }
+  template <int ND, bool VISC, bool MOV, class R>
+  gbr_status run() { return enqueue_step_kind<ND, VISC, MOV, R>(b, *K, *launches); }
 };
 
 struct RhsFn {
   gbr_batch* b;
   const Kind* K;
   long long* launches;
-  template <int ND, bool VISC, class R>
-  gbr_status run() { return enqueue_rhs<ND, VISC, R>(b, *K, 3, *launches); }
+  template <int ND, bool VISC, bool MOV, class R>
+  gbr_status run() { return enqueue_rhs<ND, VISC, MOV, R>(b, *K, 3, *launches); }
 };
 
 struct UploadFn {
   gbr_batch* b;
   Kind* K;
   std::vector<char>* host;
-  template <int ND, bool VISC, class R>
+  template <int ND, bool VISC, bool MOV, class R>
   gbr_status run() {
     const size_t n = K->members.size();
     host->assign(n * sizeof(BatchJob<R>), 0);
@@ -511,7 +563,7 @@ struct UploadFn {
   }
 };
 
-int kind_code(const KindKey& k) { return (k.nd - 2) * 4 + k.visc * 2 + k.prec; }
+int kind_code(const KindKey& k) { return (k.nd - 2) * 16 + k.visc * 8 + k.prec * 4 + k.mov * 2 + k.ig4; }
 
 int size_class(long long cells) {
   int c = 0;
@@ -580,7 +632,8 @@ gbr_status autotune_kind(gbr_batch* b, Kind& K) {
   std::vector<char> host;
   for (int fb : kFaceBlockOptions) {
     // the gradient sweep is a choice of the FP64 path only (FP32 forms f'' in the interface kernel)
-    for (int fused = 0; fused < (K.key.prec == GBR_PREC_MIXED ? 1 : 2); ++fused) {
+    // (MIG4 kinds solve their first derivatives per member: no fused E6 sweep)
+    for (int fused = 0; fused < ((K.key.prec == GBR_PREC_MIXED || K.key.ig4) ? 1 : 2); ++fused) {
       K.tune.face_block = fb;
       K.tune.fused_grad = fused;
       build_items(K);
@@ -625,7 +678,8 @@ gbr_status rebuild(gbr_batch* b) {
   b->kinds.clear();
   for (size_t m = 0; m < b->members.size(); ++m) {
     gbr_ctx* c = b->members[m];
-    KindKey key{c->L.nd, c->visc ? 1 : 0, c->p.precision == GBR_PREC_MIXED ? 1 : 0};
+    KindKey key{c->L.nd, c->visc ? 1 : 0, c->p.precision == GBR_PREC_MIXED ? 1 : 0, c->mov ? 1 : 0,
+                c->p.gradient_scheme == GBR_GRAD_MIG4 ? 1 : 0};
     Kind* K = nullptr;
     for (Kind& x : b->kinds)
       if (x.key == key) K = &x;
@@ -702,8 +756,13 @@ gbr_status rebuild(gbr_batch* b) {
     b->graph = g;
     BK(cudaGraphInstantiate(&b->exec, b->graph, 0), "graph instantiate");
   } else {
-    // count the launches of one step without running it
+    // count the launches of one step without running it; a kind with per-member work (moving
+    // meshes, MIG4) is counted when its first step is enqueued (gbr_batch_step)
     for (const Kind& K : b->kinds) {
+      if (K.key.mov || K.key.ig4) {
+        launches = -1;
+        break;
+      }
       const int per_stage = (K.tune.fused_grad || K.key.prec == GBR_PREC_MIXED) ? 4 : 5;
       launches += 3 + (K.total[WL_DT] > 0 ? 1 : 0) + 3 * per_stage;
     }
@@ -757,8 +816,6 @@ gbr_status gbr_batch_add(gbr_batch* b, gbr_ctx* c, double cfl_or_neg_dt) {
   if (!(cfl_or_neg_dt != 0.0) || std::isnan(cfl_or_neg_dt)) return bfail(b, GBR_EINVAL, "cfl_or_neg_dt must be nonzero");
   if ((int)b->members.size() >= b->max_members) return bfail(b, GBR_ENOMEM, "batch is full");
   if (!c->metrics_ready) return bfail(b, GBR_ESTATE, "metrics not computed");
-  if (c->mov || c->have_motion) return bfail(b, GBR_EINVAL, "moving meshes are stepped with gbr_rk_step, not in a batch");
-  if (c->p.gradient_scheme != GBR_GRAD_MEG6) return bfail(b, GBR_EINVAL, "MIG4 contexts are stepped with gbr_rk_step, not in a batch");
   if (c->stream != b->stream) return bfail(b, GBR_EINVAL, "the context must use the batch's stream");
   for (gbr_ctx* x : b->members)
     if (x == c) return bfail(b, GBR_EINVAL, "context already in the batch");
@@ -789,12 +846,14 @@ gbr_status gbr_batch_step(gbr_batch* b, int n_steps) {
   for (int r = 0; r < n_steps; ++r) {
     if (b->exec) {
       BK(cudaGraphLaunch(b->exec, b->stream), "graph launch");
+      b->launches += b->launches_per_step;
     } else {
-      long long dummy = 0;
+      long long count = 0;
       b->cur = b->stream;
-      if ((s = enqueue_step(b, dummy)) != GBR_OK) return s;
+      if ((s = enqueue_step(b, count)) != GBR_OK) return s;
+      b->launches_per_step = count;
+      b->launches += count;
     }
-    b->launches += b->launches_per_step;
   }
   return GBR_OK;
 }

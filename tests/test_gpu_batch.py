@@ -130,21 +130,21 @@ def test_batch_membership_changes_between_steps():
         x.close()
 
 
-def test_batch_rejects_moving_mesh_and_foreign_stream():
+def test_batch_rejects_a_foreign_stream_and_duplicates():
     import torch
 
     b = gbr.Batch(2)
-    m = I.motion_dynamic_2d(n=32, L=10.0, amp=0.1)
-    mov = gbr.Solver(I.case_params(2, (32, 32), moving=1), m.nodes(0.0), m.velocity(0.0))
-    with pytest.raises(gbr.GbrError):
-        b.add(mov, 0.4)
     c, n, _, q = case_2d_vortex(32)
     other = gbr.Solver(c, n, stream=torch.cuda.Stream())
     with pytest.raises(gbr.GbrError):
         b.add(other, 0.4)
-    mov.close()
-    other.close()
+    mine = gbr.Solver(c, n)
+    b.add(mine, 0.4)
+    with pytest.raises(gbr.GbrError):
+        b.add(mine, 0.4)
     b.close()
+    mine.close()
+    other.close()
 
 
 def test_batch_reports_the_member_with_a_bad_state():
@@ -207,6 +207,73 @@ def test_batch_members_match_the_oracle():
         assert l1.max() < 1e-8, m
         if m in smooth:
             assert rel_state(qg, qo) < 1e-10, m
+    b.close()
+    for s in members:
+        s.close()
+
+
+def moving_and_mig4_jobs():
+    """Members with per-member work: prescribed motion (2D FP64, 3D viscous mixed), MIG4 (3D viscous
+    FP64, 2D mixed), a moving MIG4 member, and a static MEG6 member beside them."""
+    out = []
+    m2 = I.motion_dynamic_2d(n=40, L=10.0, amp=0.3)
+    c2 = I.case_params(2, (40, 40), moving=1)
+    xc = I.centroids(m2.nodes(0.0), (40, 40), (1, 1))
+    q2 = I.prim_to_cons(I.vortex_prim(xc[0], xc[1]), GAMMA)
+    out.append((c2, m2, q2, 0.4))
+    m3 = I.motion_deforming_3d(n=16, L=12.0)
+    c3 = I.case_params(3, (16, 16, 16), moving=1, reynolds=500.0, precision="mixed")
+    xc3 = I.centroids(m3.nodes(0.0), (16, 16, 16), (1, 1, 1))
+    s = 2 * np.pi / 12.0
+    q3 = I.prim_to_cons(I.tgv_prim(xc3[0] * s, xc3[1] * s, xc3[2] * s, mach=0.3), GAMMA)
+    out.append((c3, m3, q3, -0.01))
+    c, n, q = tgv(20)
+    out.append((dict(c, gradient_scheme="mig4"), n, q, 0.2))
+    c, n, _, q = case_2d_vortex(48)
+    out.append((dict(c, gradient_scheme="mig4", precision="mixed"), n, q, 0.4))
+    out.append((dict(c2, gradient_scheme="mig4"), m2, q2, -0.01))
+    out.append((c, n, q, 0.4))
+    return out
+
+
+def make_mv(job):
+    case, geo, q, _ = job
+    if isinstance(geo, np.ndarray):
+        s = gbr.Solver(case, geo)
+    else:
+        s = gbr.Solver(case, geo.nodes(0.0), geo.velocity(0.0))
+        s.set_motion(geo, 0.0)
+    s.set_state(q)
+    return s
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_moving_mesh_and_mig4_members_bitwise_equal_alone(use_graph):
+    """Members with prescribed motion recompute their geometry at every stage time inside the batched
+    step, MIG4 members solve their own gradient lines there; every member's state and time are bitwise
+    those of gbr_rk_step on it alone."""
+    js = moving_and_mig4_jobs()
+    steps = 4
+    refs = []
+    for j in js:
+        s = make_mv(j)
+        for _ in range(steps):
+            s.rk_step(j[3])
+        s.sync()
+        refs.append((s.get_state(), s.time()))
+        s.close()
+    b = gbr.Batch(len(js), use_graph=use_graph, autotune=False)
+    members = [make_mv(j) for j in js]
+    for s, j in zip(members, js):
+        b.add(s, j[3])
+    b.step(steps)
+    b.sync()
+    info = b.info()
+    assert info["members"] == len(js) and info["kinds"] == 6
+    assert info["launches_per_step"] > 0 and info["launches"] == steps * info["launches_per_step"]
+    for m, (s, (qref, tref)) in enumerate(zip(members, refs)):
+        assert np.array_equal(s.get_state(), qref), m
+        assert s.time() == tref, m
     b.close()
     for s in members:
         s.close()
