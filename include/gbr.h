@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define GBR_ABI_VERSION 2
+#define GBR_ABI_VERSION 3
 
 typedef struct gbr_ctx gbr_ctx;
 
@@ -286,11 +286,18 @@ typedef struct gbr_batch gbr_batch;
 
 size_t gbr_batch_workspace_bytes(int max_members);
 gbr_status gbr_batch_create(int max_members, void* d_workspace, size_t ws_bytes, void* stream, gbr_batch** out);
-/* use_graph: capture and replay each step as a CUDA graph (default 1); autotune:
- * per kind and size class (log2 of the kind's cells), time the candidate
- * interface-kernel block sizes (64, 128, 256 interfaces per tile) and gradient
- * sweeps (two passes, or one fused pass) on the live members' right-hand side
- * and keep the fastest (default 1; the members' states are not changed). */
+/* use_graph: capture and replay each step as a CUDA graph (default 1); autotune
+ * (0: the phase kernels, 128 interfaces per tile; 2: the fused stage kernel for
+ * every kind without per-member work, untimed; 1, the default:
+ * per kind and size class (log2 of the kind's cells), time the candidates on the
+ * live members' right-hand side and keep the fastest (default 1; the members'
+ * states are not changed): the phase kernels with 64, 128 or 256 interfaces per
+ * tile, and, for kinds without per-member work (static MEG6 members), the fused
+ * stage kernel -- every phase of a stage in one persistent cooperative launch,
+ * separated by grid-wide barriers (bounded waits: a barrier that does not
+ * complete makes the next gbr_batch_sync return GBR_ETIMEOUT); each with the
+ * gradient sweep in two passes or one fused pass (FP64 kinds)).  EINVAL for
+ * another autotune value. */
 gbr_status gbr_batch_set_options(gbr_batch* b, int use_graph, int autotune);
 /* cfl_or_neg_dt as for gbr_rk_step: > 0 CFL number, < 0 fixed step. */
 gbr_status gbr_batch_add(gbr_batch* b, gbr_ctx* c, double cfl_or_neg_dt);
@@ -298,16 +305,18 @@ gbr_status gbr_batch_remove(gbr_batch* b, gbr_ctx* c);
 /* Queue n_steps SSP-RK3 steps of every member (asynchronous; rebuilds the
  * tables, tuning and graph first when the membership changed). */
 gbr_status gbr_batch_step(gbr_batch* b, int n_steps);
-/* Drain the stream (GBR_ETIMEOUT after timeout_s > 0) and check every member's
- * error flag: GBR_ENONFINITE names the first bad member (*bad_member, or -1). */
+/* Drain the stream (GBR_ETIMEOUT after timeout_s > 0), check the fused stage
+ * kernels' barrier flags (GBR_ETIMEOUT) and every member's error flag:
+ * GBR_ENONFINITE names the first bad member (*bad_member, or -1). */
 gbr_status gbr_batch_sync(gbr_batch* b, double timeout_s, int* bad_member);
 /* Members, kinds, kernel launches per step and launches issued so far.  Without
  * graphs, a batch with moving-mesh or MIG4 members reports -1 launches per step
  * until its first step has been enqueued. */
 gbr_status gbr_batch_info(gbr_batch* b, int* members, int* kinds, long long* launches_per_step, long long* launches);
-/* The chosen tuning of kind `kind` (0 .. kinds-1). */
+/* The chosen tuning of kind `kind` (0 .. kinds-1): interfaces per tile, fused
+ * gradient sweep (0/1), fused stage kernel (0/1). */
 gbr_status gbr_batch_tuning(gbr_batch* b, int kind, int* nd, int* viscous, int* precision, int* face_block,
-                            int* fused_grad);
+                            int* fused_grad, int* fused_stage);
 const char* gbr_batch_last_error(const gbr_batch* b);
 void gbr_batch_destroy(gbr_batch* b);
 

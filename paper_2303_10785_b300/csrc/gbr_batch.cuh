@@ -148,6 +148,101 @@ __global__ void __launch_bounds__(kBlock, kStreamBlocks) kb_update(const BatchJo
   });
 }
 
+// ---------------------------------------------------------------------------
+// One persistent, fused right-hand side per kind and stage: the phases (primitives and ghost
+// layers, gradients, interface fluxes, update) of every member run in ONE cooperative launch
+// over the block -> (member, tile) work lists, separated by grid-wide barriers.  The launch is
+// cooperative, so every CTA is resident and each barrier completes once all CTAs arrive; the
+// wait is bounded all the same: a barrier that has not completed after kGridBarSpin polls sets
+// the kind's timeout flag (gbr_batch_sync reports GBR_ETIMEOUT) and the CTA goes on.
+// ---------------------------------------------------------------------------
+constexpr int kGridBarSpin = 1 << 22;
+constexpr int kFusedBlock = 128;
+
+struct GridBar {
+  unsigned* count;  // arrivals at the current barrier
+  unsigned* gen;    // completed barriers
+  int* timeout;
+};
+
+__device__ __forceinline__ void grid_barrier(const GridBar& G) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vg = G.gen;
+    const unsigned g = *vg;
+    __threadfence();
+    if (atomicAdd(G.count, 1u) == gridDim.x - 1) {
+      atomicExch(G.count, 0u);
+      __threadfence();
+      atomicAdd(G.gen, 1u);
+    } else {
+      int it = 0;
+      while (*vg == g && it < kGridBarSpin) {
+        __nanosleep(200);
+        ++it;
+      }
+      if (it >= kGridBarSpin) atomicOr(G.timeout, 1);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+struct StageLists {
+  const WorkItem* items[WL_COUNT];
+  int n[WL_COUNT], total[WL_COUNT];
+};
+
+template <int ND, bool VISC, class R, bool SP>
+__global__ void __launch_bounds__(kFusedBlock, sizeof(R) == 4 ? 896 / kFusedBlock : 384 / kFusedBlock)
+    kb_stage(const BatchJob<R>* jobs, StageLists W, int stage, int fused_grad, GridBar G) {
+  __shared__ BoundSlot<ND, R> slots[kFusedBlock];
+  __shared__ int count;
+  const int qin = stage == 3 ? 0 : stage;
+  for_work(W.items[WL_PAD], W.n[WL_PAD], W.total[WL_PAD], [&](const WorkItem& it, int lb) {
+    const BatchJob<R>& J = jobs[it.job];
+    BATCH_CELL(J.pad);
+    body_prim_halo<ND>(J.A, J.q[qin], J.dq[qin], i, j, k);
+  });
+  grid_barrier(G);
+  if (!kFaceFormsG2<R> && fused_grad) {
+    for_work(W.items[WL_GRAD1], W.n[WL_GRAD1], W.total[WL_GRAD1], [&](const WorkItem& it, int lb) {
+      const BatchJob<R>& J = jobs[it.job];
+      BATCH_CELL(J.grad1[it.sub]);
+      body_grad12<ND>(J.A, it.sub, J.grad2[it.sub], i, j, k);
+    });
+  } else {
+    for_work(W.items[WL_GRAD1], W.n[WL_GRAD1], W.total[WL_GRAD1], [&](const WorkItem& it, int lb) {
+      const BatchJob<R>& J = jobs[it.job];
+      BATCH_CELL(J.grad1[it.sub]);
+      body_grad1<ND>(J.A, it.sub, i, j, k);
+    });
+    if constexpr (!kFaceFormsG2<R>) {
+      grid_barrier(G);
+      for_work(W.items[WL_GRAD2], W.n[WL_GRAD2], W.total[WL_GRAD2], [&](const WorkItem& it, int lb) {
+        const BatchJob<R>& J = jobs[it.job];
+        BATCH_CELL(J.grad2[it.sub]);
+        body_grad2<ND>(J.A, it.sub, i, j, k);
+      });
+    }
+  }
+  grid_barrier(G);
+  for_work(W.items[WL_FACE], W.n[WL_FACE], W.total[WL_FACE], [&](const WorkItem& it, int lb) {
+    const BatchJob<R>& J = jobs[it.job];
+    const long long t = (long long)lb * blockDim.x + threadIdx.x;
+    const bool valid = t < box_size(J.faces[it.sub]);
+    int i = 0, j = 0, k = 0;
+    if (valid) box_coord(J.faces[it.sub], t, i, j, k);
+    face_block<ND, VISC, false>(J.A, it.sub, valid, i, j, k, slots, &count);
+  });
+  grid_barrier(G);
+  for_work(W.items[WL_INNER], W.n[WL_INNER], W.total[WL_INNER], [&](const WorkItem& it, int lb) {
+    const BatchJob<R>& J = jobs[it.job];
+    BATCH_CELL(J.inner);
+    if (body_update<ND, false, R, SP>(J.U[stage], i, j, k)) atomicOr(J.err, 1);
+  });
+}
+
 template <int ND, class R>
 __global__ void __launch_bounds__(kBlock) kb_dt(const BatchJob<R>* jobs, const WorkItem* items, int n, int total) {
   // the minimum in the path's type and one conversion per block, as in k_dt
@@ -205,6 +300,7 @@ struct KindKey {
 struct Tuning {
   int face_block = 128;  // interfaces per tile
   int fused_grad = 0;    // 1: one fused gradient sweep
+  int fused_stage = 0;   // 1: the whole right-hand side of a stage in one persistent cooperative launch
 };
 
 struct Kind {
@@ -218,6 +314,7 @@ struct Kind {
   int total[WL_COUNT] = {};
   long long cells = 0;
   Tuning tune;
+  unsigned* d_bar = nullptr;  // grid-barrier words of the fused stage kernel: count, generation, timeout
 };
 
 }  // namespace
@@ -264,9 +361,11 @@ gbr_status bfail(gbr_batch* b, gbr_status s, const std::string& m) {
 size_t batch_job_bytes() { return std::max(sizeof(BatchJob<double>), sizeof(BatchJob<float>)); }
 
 size_t batch_ws_bytes(int max_members) {
-  // per kind (at most 8) alignment slack, per member one job record and at most 1 + 3 + 3 + 3 + 1 + 1 items
+  // per kind (at most 32: dimension, viscosity, precision, moving mesh, gradient scheme) the alignment
+  // slack of its tables and its barrier words; per member one job record and at most
+  // 1 + 3 + 3 + 3 + 1 + 1 items
   const size_t per_member = ((batch_job_bytes() + 255) & ~(size_t)255) + 12 * sizeof(WorkItem);
-  return 8 * (size_t)WL_COUNT * 256 + 8 * 256 + (size_t)max_members * (per_member + 256);
+  return 32 * (size_t)(WL_COUNT + 2) * 256 + (size_t)max_members * (per_member + 256);
 }
 
 template <class R>
@@ -355,13 +454,16 @@ void build_items(Kind& K) {
     const Layout& L = c->L;
     const RhsBoxes B = rhs_boxes(L);
     const int jm = (int)m;
-    add_items(K.items[WL_PAD], K.total[WL_PAD], jm, 0, pad_box(L, H, H), kBlock);
+    // the fused stage kernel runs every phase with its one block size
+    const int sb = K.tune.fused_stage ? kFusedBlock : kBlock;
+    const int fb = K.tune.fused_stage ? kFusedBlock : K.tune.face_block;
+    add_items(K.items[WL_PAD], K.total[WL_PAD], jm, 0, pad_box(L, H, H), sb);
     for (int d = 0; d < L.nd; ++d) {
-      add_items(K.items[WL_GRAD1], K.total[WL_GRAD1], jm, d, B.grad1[d], kBlock);
-      add_items(K.items[WL_GRAD2], K.total[WL_GRAD2], jm, d, B.grad2[d], kBlock);
-      add_items(K.items[WL_FACE], K.total[WL_FACE], jm, d, B.faces[d], K.tune.face_block);
+      add_items(K.items[WL_GRAD1], K.total[WL_GRAD1], jm, d, B.grad1[d], sb);
+      add_items(K.items[WL_GRAD2], K.total[WL_GRAD2], jm, d, B.grad2[d], sb);
+      add_items(K.items[WL_FACE], K.total[WL_FACE], jm, d, B.faces[d], fb);
     }
-    add_items(K.items[WL_INNER], K.total[WL_INNER], jm, 0, B.inner, kBlock);
+    add_items(K.items[WL_INNER], K.total[WL_INNER], jm, 0, B.inner, sb);
     if (K.cfl[m] > 0.0) add_items(K.items[WL_DT], K.total[WL_DT], jm, 0, B.inner, kBlock);
   }
 }
@@ -412,11 +514,38 @@ gbr_status enqueue_geometry(gbr_batch* b, const Kind& K, double stage_c, long lo
   return GBR_OK;
 }
 
+// the fused stage kernel of a kind: one cooperative launch of as many CTAs as are resident
+template <int ND, bool VISC, class R, bool SP>
+gbr_status launch_stage_fused(gbr_batch* b, const Kind& K, const BatchJob<R>* jobs, int stage) {
+  auto kern = kb_stage<ND, VISC, R, SP>;
+  StageLists W;
+  for (int w = 0; w < WL_COUNT; ++w) {
+    W.items[w] = K.d_items[w];
+    W.n[w] = (int)K.items[w].size();
+    W.total[w] = K.total[w];
+  }
+  GridBar G{K.d_bar, K.d_bar + 1, reinterpret_cast<int*>(K.d_bar + 2)};
+  int fg = K.tune.fused_grad;
+  const int grid = resident_ctas(b, kern, kFusedBlock);
+  void* args[] = {(void*)&jobs, (void*)&W, (void*)&stage, (void*)&fg, (void*)&G};
+  BK(cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)grid), dim3(kFusedBlock), args, 0, b->cur), "kb_stage");
+  return GBR_OK;
+}
+
 // the right-hand side of `stage` (0..3, 3 = autotuning evaluation) for one kind
 template <int ND, bool VISC, bool MOV, class R>
 gbr_status enqueue_rhs(gbr_batch* b, const Kind& K, int stage, long long& launches) {
   const BatchJob<R>* jobs = reinterpret_cast<const BatchJob<R>*>(K.d_jobs);
   cudaStream_t st = b->cur;
+  if constexpr (!MOV) {
+    if (K.tune.fused_stage && !K.key.ig4) {
+      bool sponge = false;
+      for (gbr_ctx* m : K.members) sponge |= m->have_sponge;
+      ++launches;
+      return sponge ? launch_stage_fused<ND, VISC, R, true>(b, K, jobs, stage)
+                    : launch_stage_fused<ND, VISC, R, false>(b, K, jobs, stage);
+    }
+  }
   const int qin = stage == 3 ? 0 : stage;
   {
     auto kern = kb_prim_halo<ND, R>;
@@ -590,7 +719,9 @@ gbr_status upload_kinds(gbr_batch* b) {
     gbr_status s = dispatch_kind(K.key, up);
     if (s != GBR_OK) return s;
     K.d_jobs = take(K.job_bytes);
+    K.d_bar = reinterpret_cast<unsigned*>(take(4 * sizeof(unsigned)));
     if (off > b->ws_bytes) return bfail(b, GBR_ENOMEM, "batch workspace too small");
+    BK(cudaMemsetAsync(K.d_bar, 0, 4 * sizeof(unsigned), b->stream), "barrier words");
     BK(cudaMemcpyAsync(K.d_jobs, host.data(), K.job_bytes, cudaMemcpyHostToDevice, b->stream), "upload jobs");
     for (int w = 0; w < WL_COUNT; ++w) {
       const size_t bytes = std::max<size_t>(1, K.items[w].size()) * sizeof(WorkItem);
@@ -630,17 +761,25 @@ gbr_status autotune_kind(gbr_batch* b, Kind& K) {
   Tuning best;
   float best_ms = 1e30f;
   std::vector<char> host;
-  for (int fb : kFaceBlockOptions) {
-    // the gradient sweep is a choice of the FP64 path only (FP32 forms f'' in the interface kernel)
-    // (MIG4 kinds solve their first derivatives per member: no fused E6 sweep)
+  // candidates: the phase kernels with each interface tile size, and (static MEG6 kinds) the
+  // fused stage kernel; the gradient sweep is a choice of the FP64 path only (FP32 forms f'' in the
+  // interface kernel; MIG4 kinds solve their first derivatives per member)
+  const bool can_fuse = !K.key.mov && !K.key.ig4;
+  for (int cand = 0; cand < 4; ++cand) {
+    const int fb = cand < 3 ? kFaceBlockOptions[cand] : kFusedBlock;
+    const int stage_fused = cand == 3 ? 1 : 0;
+    if (stage_fused && !can_fuse) continue;
     for (int fused = 0; fused < ((K.key.prec == GBR_PREC_MIXED || K.key.ig4) ? 1 : 2); ++fused) {
       K.tune.face_block = fb;
       K.tune.fused_grad = fused;
+      K.tune.fused_stage = stage_fused;
       build_items(K);
-      // face work list for this block size
-      const size_t bytes = K.items[WL_FACE].size() * sizeof(WorkItem);
-      BK(cudaMemcpyAsync(K.d_items[WL_FACE], K.items[WL_FACE].data(), bytes, cudaMemcpyHostToDevice, b->stream),
-         "upload work list");
+      // the work lists of this candidate (their lengths do not depend on the block sizes)
+      for (int w = 0; w < WL_COUNT; ++w)
+        if (!K.items[w].empty())
+          BK(cudaMemcpyAsync(K.d_items[w], K.items[w].data(), K.items[w].size() * sizeof(WorkItem),
+                             cudaMemcpyHostToDevice, b->stream),
+             "upload work list");
       long long dummy = 0;
       RhsFn fn{b, &K, &dummy};
       b->cur = b->stream;
@@ -697,9 +836,16 @@ gbr_status rebuild(gbr_batch* b) {
     for (auto& e : b->tune_cache)
       if (e.first == key) K.tune = e.second;
   }
+  if (b->autotune == 2)  // the fused stage kernel wherever it applies, untimed
+    for (Kind& K : b->kinds)
+      if (!K.key.mov && !K.key.ig4) {
+        K.tune.fused_stage = 1;
+        K.tune.face_block = kFusedBlock;
+        K.tune.fused_grad = 0;
+      }
   gbr_status s = upload_kinds(b);
   if (s != GBR_OK) return s;
-  if (b->autotune) {
+  if (b->autotune == 1) {
     for (Kind& K : b->kinds)
       if ((s = autotune_kind(b, K)) != GBR_OK) return s;
     if ((s = upload_kinds(b)) != GBR_OK) return s;
@@ -763,7 +909,7 @@ gbr_status rebuild(gbr_batch* b) {
         launches = -1;
         break;
       }
-      const int per_stage = (K.tune.fused_grad || K.key.prec == GBR_PREC_MIXED) ? 4 : 5;
+      const int per_stage = K.tune.fused_stage ? 1 : ((K.tune.fused_grad || K.key.prec == GBR_PREC_MIXED) ? 4 : 5);
       launches += 3 + (K.total[WL_DT] > 0 ? 1 : 0) + 3 * per_stage;
     }
   }
@@ -805,8 +951,9 @@ gbr_status gbr_batch_create(int max_members, void* d_workspace, size_t ws_bytes,
 
 gbr_status gbr_batch_set_options(gbr_batch* b, int use_graph, int autotune) {
   if (!b) return bfail(b, GBR_EINVAL, "null batch");
+  if (autotune < 0 || autotune > 2) return bfail(b, GBR_EINVAL, "autotune must be 0, 1 or 2");
   b->use_graph = use_graph ? 1 : 0;
-  b->autotune = autotune ? 1 : 0;
+  b->autotune = autotune;
   b->dirty = true;
   return GBR_OK;
 }
@@ -870,6 +1017,12 @@ gbr_status gbr_batch_sync(gbr_batch* b, double timeout_s, int* bad_member) {
     if (timeout_s > 0.0 && el > timeout_s) return bfail(b, GBR_ETIMEOUT, "stream did not drain before the deadline");
     std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
+  for (const Kind& K : b->kinds) {
+    if (!K.d_bar) continue;
+    int tmo = 0;
+    BK(cudaMemcpy(&tmo, K.d_bar + 2, sizeof(int), cudaMemcpyDeviceToHost), "read timeout flag");
+    if (tmo) return bfail(b, GBR_ETIMEOUT, "a grid barrier of the fused stage kernel did not complete in time");
+  }
   for (size_t m = 0; m < b->members.size(); ++m) {
     int err = 0;
     BK(cudaMemcpy(&err, b->members[m]->err, sizeof(int), cudaMemcpyDeviceToHost), "read error flag");
@@ -895,7 +1048,7 @@ gbr_status gbr_batch_info(gbr_batch* b, int* members, int* kinds, long long* lau
 }
 
 gbr_status gbr_batch_tuning(gbr_batch* b, int kind, int* nd, int* viscous, int* precision, int* face_block,
-                            int* fused_grad) {
+                            int* fused_grad, int* fused_stage) {
   if (!b) return bfail(b, GBR_EINVAL, "null batch");
   if (kind < 0 || kind >= (int)b->kinds.size()) return bfail(b, GBR_EINVAL, "no such kind");
   const Kind& K = b->kinds[kind];
@@ -904,6 +1057,7 @@ gbr_status gbr_batch_tuning(gbr_batch* b, int kind, int* nd, int* viscous, int* 
   if (precision) *precision = K.key.prec;
   if (face_block) *face_block = K.tune.face_block;
   if (fused_grad) *fused_grad = K.tune.fused_grad;
+  if (fused_stage) *fused_stage = K.tune.fused_stage;
   return GBR_OK;
 }
 

@@ -110,7 +110,7 @@ def lib():
     L.gbr_batch_step.argtypes = [_vp, ctypes.c_int]
     L.gbr_batch_sync.argtypes = [_vp, ctypes.c_double, _ip]
     L.gbr_batch_info.argtypes = [_vp, _ip, _ip, ctypes.POINTER(_ll), ctypes.POINTER(_ll)]
-    L.gbr_batch_tuning.argtypes = [_vp, ctypes.c_int, _ip, _ip, _ip, _ip, _ip]
+    L.gbr_batch_tuning.argtypes = [_vp, ctypes.c_int, _ip, _ip, _ip, _ip, _ip, _ip]
     L.gbr_batch_last_error.argtypes = [_vp]
     L.gbr_batch_last_error.restype = ctypes.c_char_p
     L.gbr_batch_destroy.argtypes = [_vp]
@@ -443,9 +443,10 @@ class Batch:
     def tuning(self):
         out = []
         for kind in range(self.info()["kinds"]):
-            v = [ctypes.c_int() for _ in range(5)]
+            v = [ctypes.c_int() for _ in range(6)]
             self._check(self.L.gbr_batch_tuning(self.h, kind, *[ctypes.byref(x) for x in v]))
-            out.append(dict(zip(("ndim", "viscous", "mixed", "face_block", "fused_grad"), (x.value for x in v))))
+            out.append(dict(zip(("ndim", "viscous", "mixed", "face_block", "fused_grad", "fused_stage"),
+                                (x.value for x in v))))
         return out
 
     def close(self):

@@ -277,3 +277,37 @@ def test_batch_moving_mesh_and_mig4_members_bitwise_equal_alone(use_graph):
     b.close()
     for s in members:
         s.close()
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_fused_stage_kernel_bitwise_equal_to_members_alone(use_graph):
+    """The fused stage kernel (every phase of a stage in one persistent cooperative launch, grid-wide
+    barriers between the phases) on every kind of jobs(): each member's state and time bitwise those of
+    gbr_rk_step alone, as for the phase kernels."""
+    js = jobs()
+    steps = 3
+    refs = [alone(j, steps) for j in js]
+    b = gbr.Batch(len(js), use_graph=use_graph, autotune=2)
+    members = [make(j) for j in js]
+    for s, j in zip(members, js):
+        b.add(s, j[3])
+    b.step(steps)
+    b.sync()
+    info = b.info()
+    assert info["launches"] == steps * info["launches_per_step"]
+    assert all(t["fused_stage"] == 1 and t["face_block"] == 128 for t in b.tuning())
+    for s, (qref, tref) in zip(members, refs):
+        assert np.array_equal(s.get_state(), qref)
+        assert s.time() == tref
+    b.close()
+    for s in members:
+        s.close()
+    # fewer launches per step than the phase kernels
+    b0 = gbr.Batch(len(js), use_graph=use_graph, autotune=0)
+    m0 = [make(j) for j in js]
+    for s, j in zip(m0, js):
+        b0.add(s, j[3])
+    assert b0.info()["launches_per_step"] > info["launches_per_step"]
+    b0.close()
+    for s in m0:
+        s.close()
