@@ -320,6 +320,12 @@ def cpu_baseline(wl, seconds=10.0, max_samples=40):
     return out
 
 
+def config_of(wl, world):
+    """The workload description both arms report (identical for the GPU and the reference arm)."""
+    return dict({"workload": wl.name}, **wl.config, precision=wl.precision, gradients=wl.scheme,
+                parallelism=f"replicas{world}", l2="working set >> 126 MB L2, no flush")
+
+
 def run_reference(args, wl):
     """Reference arm: the CPU oracle as it stands, one RK stage of the workload's sample per step."""
     world, rank, _ = dist_env()
@@ -340,7 +346,7 @@ def run_reference(args, wl):
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict({"workload": wl.name}, **wl.config),
+        "config": config_of(wl, args.gpus),
         "cpu_baseline": {"value": value, "unit": METRIC, "cores": O.threads(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -513,9 +519,8 @@ def run_gpu(args, wl):
         "metric": METRIC, "value": r["value"], "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if wl.precision == "mixed" else "f64", "data": "synthetic",
-        "config": dict({"workload": wl.name}, **wl.config, precision=wl.precision, gradients=wl.scheme,
-                       parallelism=f"replicas{world}",
-                       l2=f"workspace {r['workspace_bytes'] / 1e9:.1f} GB >> 126 MB L2, no flush"),
+        "config": config_of(wl, world),
+        "workspace_gb": r["workspace_bytes"] / 1e9,
         "e2e": r["e2e"], "gpu_launches": r["launches"], "roofline": r["roofline"],
         "step_roofline": r["step_roofline"], "clocks": r["clocks"], "alu_peaks": peaks,
     }
