@@ -295,7 +295,8 @@ gbr_status gbr_batch_create(int max_members, void* d_workspace, size_t ws_bytes,
  * tile, and, for kinds without per-member work (static MEG6 members), the fused
  * stage kernel -- every phase of a stage in one persistent cooperative launch,
  * separated by grid-wide barriers (bounded waits: a barrier that does not
- * complete makes the next gbr_batch_sync return GBR_ETIMEOUT); each with the
+ * complete sets a sticky flag, and gbr_batch_sync returns GBR_ETIMEOUT from then
+ * on); each with the
  * gradient sweep in two passes or one fused pass (FP64 kinds)).  EINVAL for
  * another autotune value. */
 gbr_status gbr_batch_set_options(gbr_batch* b, int use_graph, int autotune);
@@ -317,6 +318,13 @@ gbr_status gbr_batch_info(gbr_batch* b, int* members, int* kinds, long long* lau
  * gradient sweep (0/1), fused stage kernel (0/1). */
 gbr_status gbr_batch_tuning(gbr_batch* b, int kind, int* nd, int* viscous, int* precision, int* face_block,
                             int* fused_grad, int* fused_stage);
+/* Self-check of the fused stage kernel's bounded grid barrier (no counterpart in
+ * the paper): one block waits, for `polls` polls (1 .. 2^22, each sleeping about
+ * 200 ns), at a barrier that no arrival completes, then sets the sticky timeout
+ * flag of the batch's first kind: the next gbr_batch_sync returns GBR_ETIMEOUT.
+ * Asynchronous.  Errors: EINVAL (null batch, polls out of range), ESTATE (no
+ * members). */
+gbr_status gbr_batch_check_barrier(gbr_batch* b, int polls);
 const char* gbr_batch_last_error(const gbr_batch* b);
 void gbr_batch_destroy(gbr_batch* b);
 

@@ -165,7 +165,7 @@ struct GridBar {
   int* timeout;
 };
 
-__device__ __forceinline__ void grid_barrier(const GridBar& G) {
+__device__ __forceinline__ void grid_barrier(const GridBar& G, int spins = kGridBarSpin) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* vg = G.gen;
@@ -177,15 +177,24 @@ __device__ __forceinline__ void grid_barrier(const GridBar& G) {
       atomicAdd(G.gen, 1u);
     } else {
       int it = 0;
-      while (*vg == g && it < kGridBarSpin) {
+      while (*vg == g && it < spins) {
         __nanosleep(200);
         ++it;
       }
-      if (it >= kGridBarSpin) atomicOr(G.timeout, 1);
+      if (it >= spins) atomicOr(G.timeout, 1);
     }
     __threadfence();
   }
   __syncthreads();
+}
+
+// The timeout path of the grid barrier, run on purpose: one CTA arrives at a barrier whose count
+// says that another arrival is still due (no other CTA exists), so the generation it waits on
+// never advances; after `spins` polls it sets the timeout flag and leaves.
+__global__ void kb_barrier_check(GridBar G, int spins) {
+  if (threadIdx.x == 0) *G.count = 1;  // one phantom arrival: this CTA is never the last
+  grid_barrier(G, spins);
+  if (threadIdx.x == 0) *G.count = 0;
 }
 
 struct StageLists {
@@ -1058,6 +1067,20 @@ gbr_status gbr_batch_tuning(gbr_batch* b, int kind, int* nd, int* viscous, int* 
   if (face_block) *face_block = K.tune.face_block;
   if (fused_grad) *fused_grad = K.tune.fused_grad;
   if (fused_stage) *fused_stage = K.tune.fused_stage;
+  return GBR_OK;
+}
+
+gbr_status gbr_batch_check_barrier(gbr_batch* b, int polls) {
+  if (!b) return bfail(b, GBR_EINVAL, "null batch");
+  if (polls < 1 || polls > kGridBarSpin) return bfail(b, GBR_EINVAL, "polls out of range");
+  if (b->dirty && !b->members.empty()) {
+    gbr_status s = rebuild(b);
+    if (s != GBR_OK) return s;
+  }
+  if (b->kinds.empty() || !b->kinds[0].d_bar) return bfail(b, GBR_ESTATE, "the batch has no members");
+  unsigned* w = b->kinds[0].d_bar;
+  kb_barrier_check<<<1, 32, 0, b->stream>>>(GridBar{w, w + 1, reinterpret_cast<int*>(w + 2)}, polls);
+  BK(cudaGetLastError(), "kb_barrier_check");
   return GBR_OK;
 }
 

@@ -111,6 +111,8 @@ def lib():
     L.gbr_batch_sync.argtypes = [_vp, ctypes.c_double, _ip]
     L.gbr_batch_info.argtypes = [_vp, _ip, _ip, ctypes.POINTER(_ll), ctypes.POINTER(_ll)]
     L.gbr_batch_tuning.argtypes = [_vp, ctypes.c_int, _ip, _ip, _ip, _ip, _ip, _ip]
+    L.gbr_batch_check_barrier.argtypes = [_vp, ctypes.c_int]
+    L.gbr_batch_check_barrier.restype = ctypes.c_int
     L.gbr_batch_last_error.argtypes = [_vp]
     L.gbr_batch_last_error.restype = ctypes.c_char_p
     L.gbr_batch_destroy.argtypes = [_vp]
@@ -144,7 +146,7 @@ def exported_symbols():
             "gbr_rhs_static",
             "gbr_batch_workspace_bytes", "gbr_batch_create", "gbr_batch_set_options", "gbr_batch_add",
             "gbr_batch_remove", "gbr_batch_step", "gbr_batch_sync", "gbr_batch_info", "gbr_batch_tuning",
-            "gbr_batch_last_error", "gbr_batch_destroy", "gbr_arena_create", "gbr_arena_alloc", "gbr_arena_free",
+            "gbr_batch_check_barrier", "gbr_batch_last_error", "gbr_batch_destroy", "gbr_arena_create", "gbr_arena_alloc", "gbr_arena_free",
             "gbr_arena_stats", "gbr_arena_destroy", "gbr_last_error", "gbr_last_global_error", "gbr_destroy"]
 
 
@@ -439,6 +441,10 @@ class Batch:
         self._check(self.L.gbr_batch_info(self.h, ctypes.byref(m), ctypes.byref(k), ctypes.byref(lps),
                                           ctypes.byref(lt)))
         return {"members": m.value, "kinds": k.value, "launches_per_step": lps.value, "launches": lt.value}
+
+    def check_barrier(self, polls=1000):
+        """Run the fused stage kernel's barrier timeout path on purpose (the next sync raises ETIMEOUT)."""
+        self._check(self.L.gbr_batch_check_barrier(self.h, int(polls)))
 
     def tuning(self):
         out = []

@@ -104,6 +104,7 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.gbr_rk_step(None, ctypes.c_double(0.4)) == gbr.GBR_EINVAL
     assert lib.gbr_sync(None, ctypes.c_double(1.0)) == gbr.GBR_EINVAL
     assert lib.gbr_check_bounded_wait(None, 64) == gbr.GBR_EINVAL
+    assert lib.gbr_batch_check_barrier(None, 64) == gbr.GBR_EINVAL
     assert lib.gbr_set_state_async(None, None, None) == gbr.GBR_EINVAL
     assert lib.gbr_get_state_async(None, None, None) == gbr.GBR_EINVAL
     lib.gbr_destroy(None)

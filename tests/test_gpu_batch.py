@@ -311,3 +311,26 @@ def test_fused_stage_kernel_bitwise_equal_to_members_alone(use_graph):
     b0.close()
     for s in m0:
         s.close()
+
+
+def test_fused_stage_barrier_timeout_is_reported():
+    """The grid barrier of the fused stage kernel waits a bounded number of polls: its timeout path,
+    run on purpose (a barrier no arrival completes, no fault), sets the batch's sticky flag and
+    gbr_batch_sync reports GBR_ETIMEOUT; the members' states are left as they were."""
+    js = jobs()[:2]
+    b = gbr.Batch(2, autotune=2)
+    members = [make(j) for j in js]
+    for s, j in zip(members, js):
+        b.add(s, j[3])
+    b.step(1)
+    b.sync()
+    before = [s.get_state() for s in members]
+    b.check_barrier(2000)
+    with pytest.raises(gbr.GbrError) as e:
+        b.sync()
+    assert e.value.status == gbr.GBR_ETIMEOUT
+    for s, q in zip(members, before):
+        assert np.array_equal(s.get_state(), q)
+    b.close()
+    for s in members:
+        s.close()
