@@ -632,13 +632,13 @@ struct BoundSlot {
 // in shared memory and the block's first threads compute all of their bounds (the same
 // arithmetic per interface), then every thread finishes its own flux.  No thread leaves before
 // the block's barriers.
-template <int ND, bool VISC, bool MOV, class R>
+template <int ND, bool VISC, bool MOV, class R, int DD = -1>
 __device__ __forceinline__ void face_block(const RhsArgsT<R>& A, int d, bool valid, int i, int j, int k,
                                            BoundSlot<ND, R>* slots, int* count) {
   constexpr int NV = ND + 2;
   FaceCtx<ND, R> C;
   C.limit = 0;
-  if (valid) face_unlimited<ND, MOV>(A, d, i, j, k, C);
+  if (valid) face_unlimited<ND, MOV, R, DD>(A, d, i, j, k, C);
   if (threadIdx.x == 0) *count = 0;
   __syncthreads();
   int slot = -1;
@@ -664,7 +664,7 @@ __device__ __forceinline__ void face_block(const RhsArgsT<R>& A, int d, bool val
   const int n = *count;
   for (int t = threadIdx.x; t < n; t += blockDim.x) {
     BoundSlot<ND, R>& S = slots[t];
-    face_bounds<ND>(A, d, S.nu, S.ra, S.a2, S.p1, S.limit, S.Wd, S.dL, S.dR);
+    face_bounds<ND, R, DD>(A, d, S.nu, S.ra, S.a2, S.p1, S.limit, S.Wd, S.dL, S.dR);
   }
   __syncthreads();
   if (slot >= 0) {
@@ -674,12 +674,12 @@ __device__ __forceinline__ void face_block(const RhsArgsT<R>& A, int d, bool val
       C.dR[c] = slots[slot].dR[c];
     }
   }
-  if (valid) face_flux<ND, VISC, MOV>(A, d, i, j, k, C);
+  if (valid) face_flux<ND, VISC, MOV, R, DD>(A, d, i, j, k, C);
 }
 
 // Bound work compacted over the block in both precisions (FP64: FP64-pipe bound, -7 % on the
 // 128^3 TGV; FP32, where the bounds form the four cells' f'': -5 % against one interface per thread)
-template <int ND, bool VISC, bool MOV, class R = double>
+template <int ND, bool VISC, bool MOV, class R = double, int DD = -1>
 __global__ void __launch_bounds__(GBR_FACE_BLOCK, sizeof(R) == 4 ? GBR_FACE_MIN_BLOCKS_F32 : GBR_FACE_MIN_BLOCKS)
     k_face(RhsArgsT<R> A, int d, Box b) {
   __shared__ BoundSlot<ND, R> slots[GBR_FACE_BLOCK];
@@ -688,7 +688,7 @@ __global__ void __launch_bounds__(GBR_FACE_BLOCK, sizeof(R) == 4 ? GBR_FACE_MIN_
   const bool valid = t < box_size(b);
   int i = 0, j = 0, k = 0;
   if (valid) box_coord(b, t, i, j, k);
-  face_block<ND, VISC, MOV>(A, d, valid, i, j, k, slots, &count);
+  face_block<ND, VISC, MOV, R, DD>(A, d, valid, i, j, k, slots, &count);
 }
 
 template <int ND, bool MOV, class R = double, bool SP = true>
@@ -1327,13 +1327,20 @@ gbr_status launch_face(gbr_ctx* c, const RhsArgsT<R>& A, int d, const Box& b) {
     gbr_status s0 = prof_event(c);
     if (s0 != GBR_OK) return s0;
   }
-  if (c->visc) {
-    if (c->mov) k_face<ND, true, true, R><<<g, kFaceBlock, 0, st>>>(A, d, b);
-    else k_face<ND, true, false, R><<<g, kFaceBlock, 0, st>>>(A, d, b);
-  } else {
-    if (c->mov) k_face<ND, false, true, R><<<g, kFaceBlock, 0, st>>>(A, d, b);
-    else k_face<ND, false, false, R><<<g, kFaceBlock, 0, st>>>(A, d, b);
-  }
+  // one instantiation per sweep direction (d fixed at compile time)
+  auto launch = [&](auto dd) {
+    constexpr int D = decltype(dd)::value;
+    if (c->visc) {
+      if (c->mov) k_face<ND, true, true, R, D><<<g, kFaceBlock, 0, st>>>(A, d, b);
+      else k_face<ND, true, false, R, D><<<g, kFaceBlock, 0, st>>>(A, d, b);
+    } else {
+      if (c->mov) k_face<ND, false, true, R, D><<<g, kFaceBlock, 0, st>>>(A, d, b);
+      else k_face<ND, false, false, R, D><<<g, kFaceBlock, 0, st>>>(A, d, b);
+    }
+  };
+  if (d == 0) launch(std::integral_constant<int, 0>{});
+  else if (d == 1) launch(std::integral_constant<int, 1>{});
+  else if constexpr (ND == 3) launch(std::integral_constant<int, 2>{});
   CKL("k_face");
   if (c->prof) return prof_event(c);
   return GBR_OK;
@@ -2350,8 +2357,10 @@ __global__ void k_extend_nodes(ExtendArgs X, Box b) {
 
 template <int ND, bool VISC, bool MOV>
 void static_face_launches(const RhsArgs& A, const RhsBoxes& B, cudaStream_t st) {
-  for (int d = 0; d < ND; ++d)
-    k_face<ND, VISC, MOV><<<grid_of(B.faces[d], kFaceBlock), kFaceBlock, 0, st>>>(A, d, B.faces[d]);
+  k_face<ND, VISC, MOV, double, 0><<<grid_of(B.faces[0], kFaceBlock), kFaceBlock, 0, st>>>(A, 0, B.faces[0]);
+  k_face<ND, VISC, MOV, double, 1><<<grid_of(B.faces[1], kFaceBlock), kFaceBlock, 0, st>>>(A, 1, B.faces[1]);
+  if constexpr (ND == 3)
+    k_face<ND, VISC, MOV, double, 2><<<grid_of(B.faces[2], kFaceBlock), kFaceBlock, 0, st>>>(A, 2, B.faces[2]);
 }
 
 // the launch sequence of one right-hand side (geometry first), errors as cudaError_t only

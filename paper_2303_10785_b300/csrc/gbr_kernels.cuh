@@ -1283,13 +1283,16 @@ struct FaceCtx {
   unsigned limit;       // bit c: left field c fails the App. E test; bit NV + c: right
 };
 
-template <int ND, bool MOV, class R>
-GBR_HD void face_unlimited(const RhsArgsT<R>& A, int d, int i, int j, int k, FaceCtx<ND, R>& C) {
+// DD: the sweep direction fixed at compile time (0 .. 2; the single-solver kernels, one launch per
+// direction), or -1 for d given at run time (the batch, whose launches mix directions)
+template <int ND, bool MOV, class R, int DD = -1>
+GBR_HD void face_unlimited(const RhsArgsT<R>& A, int d_in, int i, int j, int k, FaceCtx<ND, R>& C) {
   constexpr int NV = ND + 2;
+  const int d = DD >= 0 ? DD : d_in;
   const Layout& L = A.L;
   const PhysR<R>& ph = A.pr;
   using I = FaceIx<R>;
-  const I PC = (I)L.pcount, s = (I)L.ps[d];
+  const I PC = (I)L.pcount, s = DD == 0 ? I(1) : (I)L.ps[d];
   const I p1 = face_pidx<I>(L, i, j, k);
   const I pp[4] = {p1 - s, p1, p1 + s, p1 + 2 * s};
   const I FC = (I)L.fcount[d];
@@ -1370,13 +1373,14 @@ GBR_HD void face_unlimited(const RhsArgsT<R>& A, int d, int i, int j, int k, Fac
 // projected with the face's eigenvectors (only here), then each failing state is limited.
 // FP32 forms the four f'' here (keeping those of cells i and i+1 from face_unlimited instead
 // measured 3 % slower: more live registers); FP64 reads them from the f'' array.
-template <int ND, class R>
-GBR_HD void face_bounds(const RhsArgsT<R>& A, int d, const R* nu, R ra, R a2, FaceIx<R> p1, unsigned limit,
+template <int ND, class R, int DD = -1>
+GBR_HD void face_bounds(const RhsArgsT<R>& A, int d_in, const R* nu, R ra, R a2, FaceIx<R> p1, unsigned limit,
                         const R (*Wd)[ND + 2], R* dL, R* dR) {
   constexpr int NV = ND + 2;
+  const int d = DD >= 0 ? DD : d_in;
   const Layout& L = A.L;
   using I = FaceIx<R>;
-  const I PC = (I)L.pcount, s = (I)L.ps[d];
+  const I PC = (I)L.pcount, s = DD == 0 ? I(1) : (I)L.ps[d];
   const I pp[4] = {p1 - s, p1, p1 + s, p1 + 2 * s};
   R W2[4][NV];
   #pragma unroll
@@ -1398,13 +1402,14 @@ GBR_HD void face_bounds(const RhsArgsT<R>& A, int d, const R* nu, R ra, R a2, Fa
   }
 }
 
-template <int ND, bool VISC, bool MOV, class R>
-GBR_HD void face_flux(const RhsArgsT<R>& A, int d, int i, int j, int k, const FaceCtx<ND, R>& C) {
+template <int ND, bool VISC, bool MOV, class R, int DD = -1>
+GBR_HD void face_flux(const RhsArgsT<R>& A, int d_in, int i, int j, int k, const FaceCtx<ND, R>& C) {
   constexpr int NV = ND + 2;
+  const int d = DD >= 0 ? DD : d_in;
   const Layout& L = A.L;
   const PhysR<R>& ph = A.pr;
   using I = FaceIx<R>;
-  const I PC = (I)L.pcount, s = (I)L.ps[d];
+  const I PC = (I)L.pcount, s = DD == 0 ? I(1) : (I)L.ps[d];
   const I p1 = C.p1;
   const I pp[4] = {p1 - s, p1, p1 + s, p1 + 2 * s};
   const I FC = (I)L.fcount[d];
