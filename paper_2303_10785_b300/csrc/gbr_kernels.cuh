@@ -603,6 +603,7 @@ struct PhysR {
   R alpha_d;                 // alpha^D
   R mp_alpha, mp_beta, mp_eps;
   R kfac;
+  R hmu_ref, tmu_ref, hmk_ref;  // mu_ref / 2, -mu_ref / 3, mu_ref kfac / 2 (constant viscosity)
   int sutherland;
 };
 template <class R>
@@ -619,6 +620,9 @@ inline PhysR<R> phys_r(const Phys& ph) {
   r.mp_beta = R(ph.mp_beta);
   r.mp_eps = R(ph.mp_eps);
   r.kfac = R(ph.kfac);
+  r.hmu_ref = R(0.5) * r.mu_ref;  // the products face_flux forms from mu, in the path's type
+  r.tmu_ref = R(-1.0 / 3.0) * r.mu_ref;
+  r.hmk_ref = r.hmu_ref * r.kfac;
   r.sutherland = ph.sutherland;
   return r;
 }
@@ -634,7 +638,7 @@ struct RhsArgsT {
   R pref_r;             // the same in the path's type (the mixed path's offset is an FP32 number)
   R* temp;              // [pcount] T = p/rho (viscous)
   R* g1[3];             // [nv (+1 T)][pcount] first derivatives along d
-  R* g2[3];             // [nv][pcount] second derivatives along d
+  R* g2[3];             // [nv][pcount] second derivatives along d, as f'' / 12 (second_deriv_12)
   const R* fh[3];       // [nd][fcount] hat metrics n^ at interfaces (FP32 copies on the mixed path)
   const R* fu[3];       // [nd][nd][fcount] unhatted metrics d xi_e / d x_a at interfaces
   const R* ft[3];       // [fcount] hat xi_t at interfaces (moving)
@@ -873,24 +877,26 @@ GBR_HD void body_grad1(const RhsArgsT<R>& A, int e, int i, int j, int k) {
   if (A.viscous) A.g1[e][NV * PC + p] = stencil_E6(A.temp, p, s);
 }
 
-// Sec. 5.1 step 1: f''_i = 2 (f_{i+1} - 2 f_i + f_{i-1}) - 0.5 (f'_{i+1} - f'_{i-1})
-// The FP32 path forms f'' inside the interface kernel instead (from f and f' of the four cells
-// of the stencil, which it loads anyway): no f'' array and no pass.  The FP64 path stores f''
-// once per cell and direction, which costs fewer FP64 operations than forming it twice per
-// interface.
+// Sec. 5.1 step 1: f''_i = 2 (f_{i+1} - 2 f_i + f_{i-1}) - 0.5 (f'_{i+1} - f'_{i-1}), kept as
+// f''_i / 12: the scale at which the unlimited states use it (Eq. legendre_polys: f'/2 + f''/12,
+// one fused multiply-add per field instead of a multiply and one) and at which the App. E
+// curvatures d = W'' enter the bounds (mp_bound folds the factor 12 into constants it multiplies
+// anyway).  The FP32 path forms it inside the interface kernel (from f and f' of the four cells
+// of the stencil, which it loads anyway): no array and no pass.  The FP64 path stores it once per
+// cell and direction, which costs fewer FP64 operations than forming it twice per interface.
 template <class R>
 constexpr bool kFaceFormsG2 = sizeof(R) == sizeof(float);
 
 template <class R, class I>
-GBR_HD R second_deriv(const R* f, const R* f1, I p, I s) {
+GBR_HD R second_deriv_12(const R* f, const R* f1, I p, I s) {
   if constexpr (sizeof(R) == sizeof(double)) {
-    // FP64 (pipe-bound pass): five operations, 2 (f_{i+1} - 2 f_i + f_{i-1}) as one fused
-    // multiply-add on -0.5 (f'_{i+1} - f'_{i-1}) (-1.3 % step time)
+    // FP64 (pipe-bound pass): five operations, (f_{i+1} - 2 f_i + f_{i-1}) / 6 as one fused
+    // multiply-add on -(f'_{i+1} - f'_{i-1}) / 24
     const R c2 = gfma(R(-2), f[p], f[p + s]) + f[p - s];
-    return gfma(R(2), c2, R(-0.5) * (f1[p + s] - f1[p - s]));
+    return gfma(R(1.0 / 6.0), c2, R(-1.0 / 24.0) * (f1[p + s] - f1[p - s]));
   } else {
     // FP32 (inside the interface kernel, where the form above measured 1.3 % slower)
-    return R(2) * (f[p + s] - R(2) * f[p] + f[p - s]) - R(0.5) * (f1[p + s] - f1[p - s]);
+    return R(1.0 / 6.0) * (f[p + s] - R(2) * f[p] + f[p - s]) - R(1.0 / 24.0) * (f1[p + s] - f1[p - s]);
   }
 }
 
@@ -902,7 +908,7 @@ GBR_HD void body_grad2(const RhsArgsT<R>& A, int e, int i, int j, int k) {
   for (int c = 0; c < NV; ++c) {
     const R* f = A.prim + c * PC;
     const R* f1 = A.g1[e] + c * PC;
-    A.g2[e][c * PC + p] = second_deriv(f, f1, p, s);
+    A.g2[e][c * PC + p] = second_deriv_12(f, f1, p, s);
   }
 }
 
@@ -1101,7 +1107,7 @@ GBR_HD void body_grad12(const RhsArgsT<R>& A, int e, const Box& b2, int i, int j
     A.g1[e][c * PC + p] = stencil_E6(f, p, s);
     if (second) {
       const R f1p = stencil_E6(f, p + s, s), f1m = stencil_E6(f, p - s, s);
-      A.g2[e][c * PC + p] = gfma(R(2), gfma(R(-2), f[p], f[p + s]) + f[p - s], R(-0.5) * (f1p - f1m));  // as second_deriv
+      A.g2[e][c * PC + p] = gfma(R(1.0 / 6.0), gfma(R(-2), f[p], f[p + s]) + f[p - s], R(-1.0 / 24.0) * (f1p - f1m));  // as second_deriv_12
     }
   }
   if (A.viscous) A.g1[e][NV * PC + p] = stencil_E6(A.temp, p, s);
@@ -1112,30 +1118,29 @@ GBR_HD void body_grad12(const RhsArgsT<R>& A, int e, const Box& b2, int i, int j
 template <int ND, class R>
 GBR_HD void project(const R* nu, R ra, R a2, const R* x, R* W) {
   if (ND == 3) {
+    // rows U -/+ a: x_p -/+ (rho a) s, each one fused multiply-add
     const R s = gfma(nu[0], x[1], gfma(nu[1], x[2], nu[2] * x[3]));
-    const R t = ra * s;
     const R e = gfma(a2, x[0], -x[4]);
-    W[0] = x[4] - t;
+    W[0] = gfma(-ra, s, x[4]);
     W[1] = gfma(nu[0], e, gfma(nu[1], x[3], -nu[2] * x[2]));
     W[2] = gfma(nu[2], e, gfma(nu[0], x[2], -nu[1] * x[1]));
     W[3] = gfma(-nu[1], e, gfma(nu[0], x[3], -nu[2] * x[1]));
-    W[4] = x[4] + t;
+    W[4] = gfma(ra, s, x[4]);
   } else {
     const R s = gfma(nu[0], x[1], nu[1] * x[2]);
-    const R t = ra * s;
-    W[0] = x[3] - t;
+    W[0] = gfma(-ra, s, x[3]);
     W[1] = gfma(a2, x[0], -x[3]);
     W[2] = gfma(nu[0], x[2], -nu[1] * x[1]);
-    W[3] = x[3] + t;
+    W[3] = gfma(ra, s, x[3]);
   }
 }
 
-// App. A back-projection d -> R d
+// App. A back-projection d -> R d (hira = 1 / (2 rho a))
 template <int ND, class R>
-GBR_HD void back_project(const R* nu, R ira, R ia2, const R* dl, R* out) {
+GBR_HD void back_project(const R* nu, R hira, R ia2, const R* dl, R* out) {
   if (ND == 3) {
     const R h = R(0.5) * (dl[0] + dl[4]);
-    const R q = R(0.5) * (dl[4] - dl[0]) * ira;
+    const R q = (dl[4] - dl[0]) * hira;
     out[0] = ia2 * (h + gfma(nu[0], dl[1], gfma(nu[2], dl[2], -nu[1] * dl[3])));
     out[1] = gfma(nu[0], q, gfma(-nu[1], dl[2], -nu[2] * dl[3]));
     out[2] = gfma(nu[1], q, gfma(-nu[2], dl[1], nu[0] * dl[2]));
@@ -1143,7 +1148,7 @@ GBR_HD void back_project(const R* nu, R ira, R ia2, const R* dl, R* out) {
     out[4] = h;
   } else {
     const R h = R(0.5) * (dl[0] + dl[3]);
-    const R q = R(0.5) * (dl[3] - dl[0]) * ira;
+    const R q = (dl[3] - dl[0]) * hira;
     out[0] = ia2 * (h + dl[1]);
     out[1] = gfma(nu[0], q, -nu[1] * dl[2]);
     out[2] = gfma(nu[1], q, nu[0] * dl[2]);
@@ -1153,7 +1158,8 @@ GBR_HD void back_project(const R* nu, R ira, R ia2, const R* dl, R* out) {
 
 // App. E limiter written relative to the base cell value W_base:
 //   f  = W_face - W_base,  dm = W_base - W_up,  dp = W_down - W_base,
-//   du, db, dd = curvatures d of the up, base and down cells.
+//   du, db, dd = curvatures d / 12 of the up, base and down cells (the scale of the stored f''),
+//   so that W^MD - W_base = (dp - 12 d^M) / 2 and W^LC - W_base = 16 d^M + dm / 2.
 // mp_keep is the test (W^L - W_base)(W^L - W^MP) <= eps that leaves the state
 // unchanged; mp_bound returns the limited W_face - W_base when it fails.
 // FP64: the products and sums are FP64; every comparison, min, max, minmod and
@@ -1171,9 +1177,9 @@ GBR_HD double mp_bound(double f, double dm, double dp, double du, double db, dou
   const double dmp = bitsd(bminmod(dbits(db), dbits(dd)));  // d^M_{i+1/2}
   const double dmm = bitsd(bminmod(dbits(du), dbits(db)));  // d^M_{i-1/2}
   const long long bdp = dbits(dp), bf = dbits(f);
-  const long long md = dbits(0.5 * (dp - dmp));                // W^MD - W_base
+  const long long md = dbits(gfma(-6.0, dmp, 0.5 * dp));       // W^MD - W_base
   const long long ul = dbits(ph.mp_alpha * dm);                // W^UL - W_base
-  const long long lc = dbits(gfma(4.0 / 3.0, dmm, 0.5 * dm));  // W^LC - W_base
+  const long long lc = dbits(gfma(16.0, dmm, 0.5 * dm));       // W^LC - W_base
   // W^min, W^max relative to W_base (W_base itself maps to 0)
   const long long lo = bmax(bmin(bmin(0LL, bdp), md), bmin(bmin(0LL, ul), lc));
   const long long hi = bmin(bmax(bmax(0LL, bdp), md), bmax(bmax(0LL, ul), lc));
@@ -1188,9 +1194,9 @@ GBR_HD bool mp_keep(float f, float dm, float dp, const PhysR<float>& ph) {
 GBR_HD float mp_bound(float f, float dm, float dp, float du, float db, float dd, const PhysR<float>& ph) {
   const float dmp = minmod(db, dd);
   const float dmm = minmod(du, db);
-  const float md = 0.5f * (dp - dmp);
+  const float md = gfma(-6.0f, dmp, 0.5f * dp);
   const float ul = ph.mp_alpha * dm;
-  const float lc = gfma(4.0f / 3.0f, dmm, 0.5f * dm);
+  const float lc = gfma(16.0f, dmm, 0.5f * dm);
   const float lo = gmax(gmin(gmin(0.0f, dp), md), gmin(gmin(0.0f, ul), lc));
   const float hi = gmin(gmax(gmax(0.0f, dp), md), gmax(gmax(0.0f, ul), lc));
   return gmax(gmin(f, lo), gmin(gmax(f, lo), hi));
@@ -1277,7 +1283,7 @@ struct FaceCtx {
   FaceIx<R> p1, f;      // padded index of cell i, interface index
   R nh[ND], nu[ND];
   R nn2, inn, nt;
-  R ra, a2, ira, ia2;   // face state of the eigenvectors
+  R ra, a2, hira, ia2;  // face state of the eigenvectors (hira = 1 / (2 rho a))
   R Wd[3][NV];          // projected differences of cells i-1 .. i+2
   R dL[NV], dR[NV];     // W^L - W_i, W^R - W_{i+1}
   unsigned limit;       // bit c: left field c fails the App. E test; bit NV + c: right
@@ -1318,7 +1324,7 @@ GBR_HD void face_unlimited(const RhsArgsT<R>& A, int d_in, int i, int j, int k, 
   // a = gamma p t and 1/a = rho t -- one reciprocal square root, no division
   const R gp = ph.gamma * pb;
   const R t = grsqrt(gp * rb);
-  C.ira = t;
+  C.hira = R(0.5) * t;
   C.ra = gp * rb * t;
   const R a_ = gp * t;
   C.a2 = a_ * a_;
@@ -1343,8 +1349,8 @@ GBR_HD void face_unlimited(const RhsArgsT<R>& A, int d_in, int i, int j, int k, 
     for (int c = 0; c < NV; ++c) {
       const R* f = P + c * PC;
       const R* f1 = A.g1[d] + c * PC;
-      xl[c] = gfma(R(0.5), f1[pp[1]], second_deriv(f, f1, pp[1], s) * R(1.0 / 12.0));
-      xr[c] = gfma(R(-0.5), f1[pp[2]], second_deriv(f, f1, pp[2], s) * R(1.0 / 12.0));
+      xl[c] = gfma(R(0.5), f1[pp[1]], second_deriv_12(f, f1, pp[1], s));
+      xr[c] = gfma(R(-0.5), f1[pp[2]], second_deriv_12(f, f1, pp[2], s));
     }
     project<ND>(C.nu, C.ra, C.a2, xl, C.dL);
     project<ND>(C.nu, C.ra, C.a2, xr, C.dR);
@@ -1352,11 +1358,11 @@ GBR_HD void face_unlimited(const RhsArgsT<R>& A, int d_in, int i, int j, int k, 
     R x[NV];
     #pragma unroll
     for (int c = 0; c < NV; ++c)
-      x[c] = gfma(R(0.5), A.g1[d][c * PC + pp[1]], A.g2[d][c * PC + pp[1]] * R(1.0 / 12.0));
+      x[c] = gfma(R(0.5), A.g1[d][c * PC + pp[1]], A.g2[d][c * PC + pp[1]]);
     project<ND>(C.nu, C.ra, C.a2, x, C.dL);
     #pragma unroll
     for (int c = 0; c < NV; ++c)
-      x[c] = gfma(R(-0.5), A.g1[d][c * PC + pp[2]], A.g2[d][c * PC + pp[2]] * R(1.0 / 12.0));
+      x[c] = gfma(R(-0.5), A.g1[d][c * PC + pp[2]], A.g2[d][c * PC + pp[2]]);
     project<ND>(C.nu, C.ra, C.a2, x, C.dR);
   }
   // App. E test per field and side
@@ -1369,7 +1375,7 @@ GBR_HD void face_unlimited(const RhsArgsT<R>& A, int d_in, int i, int j, int k, 
   C.limit = limit;
 }
 
-// App. E bounds of the fields that failed the test: the curvatures d of cells i-1 .. i+2 are
+// App. E bounds of the fields that failed the test: the curvatures d / 12 of cells i-1 .. i+2 are
 // projected with the face's eigenvectors (only here), then each failing state is limited.
 // FP32 forms the four f'' here (keeping those of cells i and i+1 from face_unlimited instead
 // measured 3 % slower: more live registers); FP64 reads them from the f'' array.
@@ -1389,7 +1395,7 @@ GBR_HD void face_bounds(const RhsArgsT<R>& A, int d_in, const R* nu, R ra, R a2,
     #pragma unroll
     for (int c = 0; c < NV; ++c) {
       if constexpr (kFaceFormsG2<R>)
-        x[c] = second_deriv(A.prim + c * PC, A.g1[d] + c * PC, pp[m], s);
+        x[c] = second_deriv_12(A.prim + c * PC, A.g1[d] + c * PC, pp[m], s);
       else
         x[c] = A.g2[d][c * PC + pp[m]];
     }
@@ -1418,8 +1424,8 @@ GBR_HD void face_flux(const RhsArgsT<R>& A, int d_in, int i, int j, int k, const
   const R* nh = C.nh;
   const R nn2 = C.nn2, inn = C.inn, nt = C.nt;
   R PL[NV], PR[NV];
-  back_project<ND>(C.nu, C.ira, C.ia2, C.dL, PL);
-  back_project<ND>(C.nu, C.ira, C.ia2, C.dR, PR);
+  back_project<ND>(C.nu, C.hira, C.ia2, C.dL, PL);
+  back_project<ND>(C.nu, C.hira, C.ia2, C.dR, PR);
   #pragma unroll
   for (int c = 0; c < NV; ++c) {
     PL[c] += P[c * PC + pp[1]];
@@ -1475,18 +1481,21 @@ GBR_HD void face_flux(const RhsArgsT<R>& A, int d_in, int i, int j, int k, const
       m[e] = acc;
       sv[e] = acs;
     }
-    R mu = ph.mu_ref;
+    // mu / 2, -mu / 3 (lambda / 2) and mu kfac / 2: constants unless mu follows Sutherland's law
+    R hmu = ph.hmu_ref, tmu = ph.tmu_ref, hmk = ph.hmk_ref;
     if (ph.sutherland) {
       const R th = phif[ND] * ph.it_ref;
-      mu = ph.mu_ref * (th * gsqrt(th)) * ((R(1) + ph.suth_s) / (th + ph.suth_s));
+      const R mu = ph.mu_ref * (th * gsqrt(th)) * ((R(1) + ph.suth_s) / (th + ph.suth_s));
+      hmu = R(0.5) * mu;
+      tmu = R(-1.0 / 3.0) * mu;
+      hmk = hmu * ph.kfac;
     }
-    const R hmu = R(0.5) * mu;
     R div2 = R(0);
     #pragma unroll
     for (int a = 0; a < ND; ++a)
       #pragma unroll
       for (int e = 0; e < ND; ++e) div2 = gfma(xe[e][a], gc2[a][e], div2);
-    const R hlamdiv = R(-1.0 / 3.0) * mu * div2;  // lambda div u, lambda = -2/3 mu
+    const R hlamdiv = tmu * div2;  // lambda div u / 2, lambda = -2/3 mu
     R bn = R(0);
     #pragma unroll
     for (int a = 0; a < ND; ++a) {
@@ -1503,7 +1512,7 @@ GBR_HD void face_flux(const RhsArgsT<R>& A, int d_in, int i, int j, int k, const
     R gTn = R(0);
     #pragma unroll
     for (int e = 0; e < ND; ++e) gTn = gfma(m[e], gc2[ND][e], gTn);
-    F[NV - 1] -= gfma(R(0.5) * mu * ph.kfac, gTn, bn);
+    F[NV - 1] -= gfma(hmk, gTn, bn);
   }
   #pragma unroll
   for (int c = 0; c < NV; ++c) A.flux[d][c * FC + f] = F[c];
