@@ -90,6 +90,17 @@ __global__ void k_face_metrics(GeoArgs G, Box b0, Box b1, Box b2) {
   body_face_metrics(G, d, i, j, k);
 }
 
+// the FP64 path's interface geometry from the interface metrics (body_face_geo)
+struct FaceGeoOut {
+  double* fg[3];
+};
+__global__ void k_face_geo(GeoArgs G, FaceGeoOut O, Box b0, Box b1, Box b2) {
+  const int d = blockIdx.y;
+  const Box b = d == 0 ? b0 : (d == 1 ? b1 : b2);
+  BOX_THREAD(b);
+  body_face_geo(G, O.fg[d], d, i, j, k);
+}
+
 // ---- MIG4 metrics: one thread per geometry line (set-up work; Sec. 7 step 2 with IG4)
 __global__ void k_ig4_geo_factor(double* t, int m) { ig4_geo_factor(t, m); }
 
@@ -759,7 +770,7 @@ struct Plan {
 enum Slot {
   SL_Q0, SL_Q1, SL_Q2, SL_PRIM, SL_TEMP, SL_G1, SL_G2, SL_FLUX, SL_NODES, SL_NVEL, SL_XC, SL_VC, SL_XD, SL_MH,
   SL_DET, SL_MU, SL_MT, SL_FH, SL_FU, SL_FT, SL_GCL, SL_JAC, SL_SIGMA, SL_INFLOW, SL_SCAL, SL_ERR, SL_IG4, SL_FH32, SL_FU32,
-  SL_FT32, SL_IG4F, SL_MH32, SL_MT32, SL_JAC32, SL_GEOT, SL_GEOW, SL_COUNT
+  SL_FT32, SL_IG4F, SL_MH32, SL_MT32, SL_JAC32, SL_GEOT, SL_GEOW, SL_FG, SL_COUNT
 };
 
 struct Sizes {
@@ -898,6 +909,7 @@ Plan plan_of(const gbr_params* p, const Layout& L) {
     for (int d = 0; d < nd; ++d) geot += 2LL * (L.n[d] + 2 * L.he[d]) + 2LL * (L.n[d] + 2 * L.cg[d]);
   P.add(D * geot);                                               // SL_GEOT
   P.add(geo4 ? D * L.ecount : 0);                                // SL_GEOW
+  P.add(f32 ? 0 : D * fg_count(visc) * fsum);                    // SL_FG: FP64 interface geometry
   P.total = (P.total + 255) & ~(size_t)255;
   return P;
 }
@@ -941,6 +953,7 @@ struct gbr_ctx {
   double* q[3];
   void *prim, *temp, *g1[3], *g2[3], *flux[3];  // element type double (FP64) or float (mixed)
   double *nodes, *nvel, *xc, *vc, *xd, *mh, *det, *mu, *mt, *fh[3], *fu[3], *ft[3], *gcl, *jac;
+  double* fg[3];  // FP64 path: interface geometry derived from fh, fu (body_face_geo), or null
   float *fh32[3], *fu32[3], *ft32[3];  // mixed path: FP32 copies of the interface metrics
   float *mh32, *mt32, *jac32;          // mixed path: FP32 copies of the cell metrics (time step)
   double *sigma, *inflow, *scal;
@@ -1225,6 +1238,20 @@ gbr_status run_geometry_ig4(gbr_ctx* c, const GeoArgs& G, const GeoBoxes& B, cud
   return GBR_OK;
 }
 
+// FP64 path: the interface geometry of every direction, after the interface metrics
+gbr_status launch_face_geo(gbr_ctx* c, const GeoArgs& G, const GeoBoxes& B, cudaStream_t st) {
+  if (!c->fg[0]) return GBR_OK;
+  FaceGeoOut O;
+  unsigned gmax = 0;
+  for (int d = 0; d < 3; ++d) {
+    O.fg[d] = c->fg[d];
+    if (d < c->L.nd) gmax = std::max(gmax, grid_of(B.faces[d], kBlock));
+  }
+  k_face_geo<<<dim3(gmax, c->L.nd), kBlock, 0, st>>>(G, O, B.faces[0], B.faces[1], B.faces[2]);
+  CKL("k_face_geo");
+  return GBR_OK;
+}
+
 gbr_status run_geometry(gbr_ctx* c, cudaStream_t st) {
   const Layout& L = c->L;
   GeoArgs G = geo_args(c);
@@ -1245,6 +1272,10 @@ gbr_status run_geometry(gbr_ctx* c, cudaStream_t st) {
     for (int d = 0; d < L.nd; ++d) gmax = std::max(gmax, grid_of(B.faces[d], kBlock));
     k_face_metrics<<<dim3(gmax, L.nd), kBlock, 0, st>>>(G, B.faces[0], B.faces[1], B.faces[2]);
     CKL("k_face_metrics");
+  }
+  {
+    gbr_status sg = launch_face_geo(c, G, B, st);
+    if (sg != GBR_OK) return sg;
   }
   k_gcl<<<grid_of(B.inner, kBlock), kBlock, 0, st>>>(G, B.inner);
   CKL("k_gcl");
@@ -1298,6 +1329,8 @@ RhsArgsT<R> rhs_args_r(gbr_ctx* c, const double* q) {
       A.ft[d] = c->ft[d];
     }
     A.flux[d] = static_cast<R*>(c->flux[d]);
+    if constexpr (sizeof(R) == sizeof(double)) A.fg[d] = c->fg[d];
+    else A.fg[d] = nullptr;
   }
   A.inflow = c->inflow;
   for (int d = 0; d < 3; ++d)
@@ -1551,6 +1584,7 @@ void carve(gbr_ctx* c) {
     c->fh[d] = (d < nd) ? ptr(SL_FH) + (size_t)nd * foff : nullptr;
     c->fu[d] = (d < nd && c->visc) ? ptr(SL_FU) + (size_t)nd * nd * foff : nullptr;
     c->ft[d] = (d < nd && c->mov) ? ptr(SL_FT) + foff : nullptr;
+    c->fg[d] = (d < nd && P.len[SL_FG]) ? ptr(SL_FG) + (size_t)fg_count(c->visc) * foff : nullptr;
     auto fptr = [&](int slot, size_t elems) -> float* {
       return P.len[slot] ? (float*)(c->ws + P.off[slot]) + elems : nullptr;
     };
@@ -2377,6 +2411,9 @@ cudaError_t static_rhs_launches(gbr_ctx& c, const double* q, double* dqdt, cudaS
   gmax = 0;
   for (int d = 0; d < ND; ++d) gmax = std::max(gmax, grid_of(GB.faces[d], kBlock));
   k_face_metrics<<<dim3(gmax, ND), kBlock, 0, st>>>(G, GB.faces[0], GB.faces[1], GB.faces[2]);
+  FaceGeoOut O;
+  for (int d = 0; d < 3; ++d) O.fg[d] = c.fg[d];
+  k_face_geo<<<dim3(gmax, ND), kBlock, 0, st>>>(G, O, GB.faces[0], GB.faces[1], GB.faces[2]);
   k_gcl<<<grid_of(GB.inner, kBlock), kBlock, 0, st>>>(G, GB.inner);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -536,6 +536,39 @@ GBR_HD void body_metrics(const GeoArgs& G, int i, int j, int k, bool mh_given = 
   }
 }
 
+// Interface geometry the FP64 interface stages would otherwise form at every stage from fh and fu
+// (functions of the mesh alone), stored per interface in fg: the unit normal nu = n^/|n^|, |n^|^2,
+// 1/|n^|, |n^|, 1/|n^|^2 and, viscous, m_e = sum_b (d xi_e/d x_b) n^_b (the chain rule contracted
+// with n^, Sec. 5.2).  Each value is formed by the same operations in the same order as the
+// interface stages' own forms (face_unlimited, hllc, face_flux), so the fluxes are unchanged bit
+// for bit.
+enum { FG_NU = 0, FG_NN2 = 3, FG_INN = 4, FG_NN = 5, FG_INN2 = 6, FG_M = 7, FG_COUNT = 10 };
+inline int fg_count(bool viscous) { return viscous ? FG_COUNT : FG_M; }
+
+GBR_HD void body_face_geo(const GeoArgs& G, double* fg, int d, int i, int j, int k) {
+  const Layout& L = G.L;
+  const int nd = L.nd;
+  const long long FC = L.fcount[d], f = fidx(L, d, i, j, k);
+  double nh[3] = {0.0, 0.0, 0.0}, nn2 = 0.0;
+  for (int a = 0; a < nd; ++a) {
+    nh[a] = G.fh[d][a * FC + f];
+    nn2 = gfma(nh[a], nh[a], nn2);
+  }
+  const double inn = grsqrt(nn2);
+  for (int a = 0; a < 3; ++a) fg[(FG_NU + a) * FC + f] = nh[a] * inn;
+  fg[FG_NN2 * FC + f] = nn2;
+  fg[FG_INN * FC + f] = inn;
+  fg[FG_NN * FC + f] = nn2 * inn;
+  fg[FG_INN2 * FC + f] = inn * inn;
+  if (G.viscous)
+    for (int e = 0; e < nd; ++e) {
+      const double* fu = G.fu[d] + (e * nd) * FC + f;
+      double acc = fu[0] * nh[0];
+      for (int b = 1; b < nd; ++b) acc = gfma(fu[b * FC], nh[b], acc);
+      fg[(FG_M + e) * FC + f] = acc;
+    }
+}
+
 // Sec. 7 step 3: interface values of whole metric products, interface i+1/2 along d
 GBR_HD void body_face_metrics(const GeoArgs& G, int d, int i, int j, int k) {
   const Layout& L = G.L;
@@ -642,6 +675,7 @@ struct RhsArgsT {
   const R* fh[3];       // [nd][fcount] hat metrics n^ at interfaces (FP32 copies on the mixed path)
   const R* fu[3];       // [nd][nd][fcount] unhatted metrics d xi_e / d x_a at interfaces
   const R* ft[3];       // [fcount] hat xi_t at interfaces (moving)
+  const R* fg[3];       // [FG_COUNT][fcount] interface geometry derived from fh, fu (FP64 path; body_face_geo)
   R* flux[3];           // [nv][fcount] F^ - F^v at interfaces
   const double* inflow; // [nv][nk][nj]
   int bc[3][2];
@@ -886,6 +920,10 @@ GBR_HD void body_grad1(const RhsArgsT<R>& A, int e, int i, int j, int k) {
 // cell and direction, which costs fewer FP64 operations than forming it twice per interface.
 template <class R>
 constexpr bool kFaceFormsG2 = sizeof(R) == sizeof(float);
+// The FP64 interface stages read the mesh-only interface geometry from fg (body_face_geo); the FP32
+// ones, issue-bound, form it (fewer instructions than the loads and their addresses)
+template <class R>
+constexpr bool kFaceGeo = sizeof(R) == sizeof(double);
 
 template <class R, class I>
 GBR_HD R second_deriv_12(const R* f, const R* f1, I p, I s) {
@@ -1207,10 +1245,8 @@ GBR_HD float mp_bound(float f, float dm, float dp, float du, float db, float dd,
 // speeds, the energy and the energy flux; the pressure difference of S* and the momentum flux's
 // pressure term use p - pref (the dropped pref n^ has zero divergence by the metric identities).
 template <int ND, class R>
-GBR_HD void hllc(const R* PL, const R* PR, const R* nh, R nn2, R inn, R nt, const PhysR<R>& ph, R pref, R* F) {
+GBR_HD void hllc(const R* PL, const R* PR, const R* nh, R nn2, R nn, R inn2, R nt, const PhysR<R>& ph, R pref, R* F) {
   constexpr int NV = ND + 2;
-  const R nn = nn2 * inn;
-  const R inn2 = inn * inn;
   // left and right states (kept in scalars: no runtime-indexed arrays)
   const R rl = PL[0], rr = PR[0];
   const R dpl = PL[NV - 1], dpr = PR[NV - 1];
@@ -1306,17 +1342,24 @@ GBR_HD void face_unlimited(const RhsArgsT<R>& A, int d_in, int i, int j, int k, 
   const R* P = A.prim;
   C.p1 = p1;
   C.f = f;
-  R nn2 = R(0);
   #pragma unroll
-  for (int a = 0; a < ND; ++a) {
-    C.nh[a] = R(A.fh[d][a * FC + f]);
-    nn2 = gfma(C.nh[a], C.nh[a], nn2);
-  }
-  C.nn2 = nn2;
+  for (int a = 0; a < ND; ++a) C.nh[a] = R(A.fh[d][a * FC + f]);
   C.nt = MOV ? R(A.ft[d][f]) : R(0);
-  C.inn = grsqrt(nn2);
-  #pragma unroll
-  for (int a = 0; a < ND; ++a) C.nu[a] = C.nh[a] * C.inn;
+  if constexpr (kFaceGeo<R>) {
+    // FP64: |n^|^2 and the unit normal from the stored interface geometry
+    const R* g = A.fg[d] + f;
+    C.nn2 = g[FG_NN2 * FC];
+    #pragma unroll
+    for (int a = 0; a < ND; ++a) C.nu[a] = g[(FG_NU + a) * FC];
+  } else {
+    R nn2 = R(0);
+    #pragma unroll
+    for (int a = 0; a < ND; ++a) nn2 = gfma(C.nh[a], C.nh[a], nn2);
+    C.nn2 = nn2;
+    C.inn = grsqrt(nn2);
+    #pragma unroll
+    for (int a = 0; a < ND; ++a) C.nu[a] = C.nh[a] * C.inn;
+  }
   // face state of the eigenvectors: mean of rho and p of cells i, i+1
   const R rb = R(0.5) * (P[pp[1]] + P[pp[2]]);
   const R pb = gfma(R(0.5), P[(NV - 1) * PC + pp[1]] + P[(NV - 1) * PC + pp[2]], A.pref_r);
@@ -1422,7 +1465,15 @@ GBR_HD void face_flux(const RhsArgsT<R>& A, int d_in, int i, int j, int k, const
   const I f = C.f;
   const R* P = A.prim;
   const R* nh = C.nh;
-  const R nn2 = C.nn2, inn = C.inn, nt = C.nt;
+  const R nn2 = C.nn2, nt = C.nt;
+  R nn, inn2;  // |n^| and 1/|n^|^2
+  if constexpr (kFaceGeo<R>) {
+    nn = A.fg[d][FG_NN * FC + f];
+    inn2 = A.fg[d][FG_INN2 * FC + f];
+  } else {
+    nn = nn2 * C.inn;
+    inn2 = C.inn * C.inn;
+  }
   R PL[NV], PR[NV];
   back_project<ND>(C.nu, C.hira, C.ia2, C.dL, PL);
   back_project<ND>(C.nu, C.hira, C.ia2, C.dR, PR);
@@ -1432,7 +1483,7 @@ GBR_HD void face_flux(const RhsArgsT<R>& A, int d_in, int i, int j, int k, const
     PR[c] += P[c * PC + pp[2]];
   }
   R F[NV];
-  hllc<ND>(PL, PR, nh, nn2, inn, nt, ph, A.pref_r, F);
+  hllc<ND>(PL, PR, nh, nn2, nn, inn2, nt, ph, A.pref_r, F);
 
   if (VISC) {
     // Sec. 5.2 alpha-damping on [u.., T].  gc2[v][e] = 2 d(phi_v)/d(xi_e) at the interface:
@@ -1475,9 +1526,10 @@ GBR_HD void face_flux(const RhsArgsT<R>& A, int d_in, int i, int j, int k, const
       R acc = xe[e][0] * nh[0], acs = nh[0] * gc2[0][e];
       #pragma unroll
       for (int b = 1; b < ND; ++b) {
-        acc = gfma(xe[e][b], nh[b], acc);
+        if constexpr (!kFaceGeo<R>) acc = gfma(xe[e][b], nh[b], acc);
         acs = gfma(nh[b], gc2[b][e], acs);
       }
+      if constexpr (kFaceGeo<R>) acc = A.fg[d][(FG_M + e) * FC + f];  // stored (body_face_geo)
       m[e] = acc;
       sv[e] = acs;
     }
