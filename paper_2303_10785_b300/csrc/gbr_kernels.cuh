@@ -924,6 +924,9 @@ constexpr bool kFaceFormsG2 = sizeof(R) == sizeof(float);
 // ones, issue-bound, form it (fewer instructions than the loads and their addresses)
 template <class R>
 constexpr bool kFaceGeo = sizeof(R) == sizeof(double);
+// The stored pressures carry p - pref, and pref = 0 on the FP64 path
+template <class R>
+constexpr bool kPrefZero = sizeof(R) == sizeof(double);
 
 template <class R, class I>
 GBR_HD R second_deriv_12(const R* f, const R* f1, I p, I s) {
@@ -1244,13 +1247,13 @@ GBR_HD float mp_bound(float f, float dm, float dp, float du, float db, float dd,
 // The states carry p - pref (pref = 0 on the FP64 path): the absolute pressure enters the sound
 // speeds, the energy and the energy flux; the pressure difference of S* and the momentum flux's
 // pressure term use p - pref (the dropped pref n^ has zero divergence by the metric identities).
-template <int ND, class R>
+template <int ND, bool MOV, class R>
 GBR_HD void hllc(const R* PL, const R* PR, const R* nh, R nn2, R nn, R inn2, R nt, const PhysR<R>& ph, R pref, R* F) {
   constexpr int NV = ND + 2;
   // left and right states (kept in scalars: no runtime-indexed arrays)
   const R rl = PL[0], rr = PR[0];
   const R dpl = PL[NV - 1], dpr = PR[NV - 1];
-  const R pl = dpl + pref, pr = dpr + pref;
+  const R pl = kPrefZero<R> ? dpl : dpl + pref, pr = kPrefZero<R> ? dpr : dpr + pref;
   // t = 1/sqrt(gamma p rho) = 1/(rho c): c = gamma p t and 1/rho = gamma p t^2, no division
   const R gpl = ph.gamma * pl, gpr = ph.gamma * pr;
   const R tl = grsqrt(gpl * rl), tr = grsqrt(gpr * rr);
@@ -1282,7 +1285,8 @@ GBR_HD void hllc(const R* PL, const R* PR, const R* nh, R nn2, R nn, R inn2, R n
   F[0] = rs * Us;
   #pragma unroll
   for (int a = 0; a < ND; ++a) F[1 + a] = gfma(rs * us[a], Us, nh[a] * dps);
-  F[NV - 1] = gfma(Es + ps, Us, -nt * ps);
+  if constexpr (MOV) F[NV - 1] = gfma(Es + ps, Us, -nt * ps);
+  else F[NV - 1] = (Es + ps) * Us;  // xi_t = 0
   if (star) {
     // Q*K = rho (S - U)/(S - S*) [1, u + n^ (S* - U)/|n^|^2, E/rho + (S* - U)((S* - xi_t)/|n^|^2 + p/(rho (S - U)))]
     // The correction S (Q*K - QK) is formed with the factor (S* - U) taken out,
@@ -1301,7 +1305,7 @@ GBR_HD void hllc(const R* PL, const R* PR, const R* nh, R nn2, R nn, R inn2, R n
     F[0] = gfma(S * rs, dg, F[0]);
     #pragma unroll
     for (int a = 0; a < ND; ++a) F[1 + a] = gfma(S, gfma(rs * us[a], dg, fw * nh[a]), F[1 + a]);
-    F[NV - 1] = gfma(S * dS, gfma(fac, gfma(Ss - nt, inn2, p_rA), Es * g), F[NV - 1]);
+    F[NV - 1] = gfma(S * dS, gfma(fac, gfma(MOV ? Ss - nt : Ss, inn2, p_rA), Es * g), F[NV - 1]);
   }
 }
 
@@ -1360,18 +1364,23 @@ GBR_HD void face_unlimited(const RhsArgsT<R>& A, int d_in, int i, int j, int k, 
     #pragma unroll
     for (int a = 0; a < ND; ++a) C.nu[a] = C.nh[a] * C.inn;
   }
-  // face state of the eigenvectors: mean of rho and p of cells i, i+1
-  const R rb = R(0.5) * (P[pp[1]] + P[pp[2]]);
-  const R pb = gfma(R(0.5), P[(NV - 1) * PC + pp[1]] + P[(NV - 1) * PC + pp[2]], A.pref_r);
+  // face state of the eigenvectors: mean of rho and p of cells i, i+1, kept doubled
+  // (rb2 = 2 rho-bar, pb2 = 2 p-bar: the halvings fold into powers of two below)
+  const R rb2 = P[pp[1]] + P[pp[2]];
+  const R psum = P[(NV - 1) * PC + pp[1]] + P[(NV - 1) * PC + pp[2]];
+  const R pb2 = kPrefZero<R> ? psum : psum + R(2) * A.pref_r;
   // a = sqrt(gamma p / rho): with t = 1/sqrt(gamma p rho), rho a = gamma p rho t, 1/(rho a) = t,
-  // a = gamma p t and 1/a = rho t -- one reciprocal square root, no division
-  const R gp = ph.gamma * pb;
-  const R t = grsqrt(gp * rb);
-  C.hira = R(0.5) * t;
-  C.ra = gp * rb * t;
-  const R a_ = gp * t;
+  // a = gamma p t and 1/a = rho t -- one reciprocal square root, no division.  From the doubled
+  // state: g4 = 4 gamma p rho and t2 = 1/sqrt(g4) = t/2 (exact scalings by powers of two), so
+  // 1/(2 rho a) = t2, rho a = g4 t2 / 2, a = (2 gamma p) t2 and 1/a = (2 rho) t2.
+  const R gp2 = ph.gamma * pb2;
+  const R g4 = gp2 * rb2;
+  const R t2 = grsqrt(g4);
+  C.hira = t2;
+  C.ra = R(0.5) * (g4 * t2);
+  const R a_ = gp2 * t2;
   C.a2 = a_ * a_;
-  const R ia = rb * t;
+  const R ia = rb2 * t2;
   C.ia2 = ia * ia;
   // projected differences dW = R^-1 (P_{m+1} - P_m) of the four cells i-1 .. i+2
   #pragma unroll
@@ -1483,14 +1492,14 @@ GBR_HD void face_flux(const RhsArgsT<R>& A, int d_in, int i, int j, int k, const
     PR[c] += P[c * PC + pp[2]];
   }
   R F[NV];
-  hllc<ND>(PL, PR, nh, nn2, nn, inn2, nt, ph, A.pref_r, F);
+  hllc<ND, MOV>(PL, PR, nh, nn2, nn, inn2, nt, ph, A.pref_r, F);
 
   if (VISC) {
     // Sec. 5.2 alpha-damping on [u.., T].  gc2[v][e] = 2 d(phi_v)/d(xi_e) at the interface:
     // Eq. (AD-eqn1) along the sweep, the sum of the two cells' gradients across it (reading
     // the paper is silent on them); the factor 1/2 is folded into mu, lambda and kappa below.
     R gc2[ND + 1][ND];
-    R phif[ND + 1];
+    R phs[ND + 1];  // phi^L + phi^R = 2 x the interface value of [u.., T]
     #pragma unroll
     for (int v = 0; v <= ND; ++v) {
       const R* val = (v < ND) ? P + (1 + v) * PC : A.temp;
@@ -1506,7 +1515,7 @@ GBR_HD void face_flux(const RhsArgsT<R>& A, int d_in, int i, int j, int k, const
           gc2[v][e] = A.g1[e][gi * PC + pp[1]] + A.g1[e][gi * PC + pp[2]];
         }
       }
-      phif[v] = R(0.5) * (phiL + phiR);
+      phs[v] = phiL + phiR;
     }
     // The flux needs only tau n^ and beta . n^ (Eq. shear-str, thermal-work), so the chain rule
     // d/dx_a = sum_e (d xi_e/d x_a) d/d xi_e (Eq. AD-eqn3) is contracted with n^ first:
@@ -1536,7 +1545,7 @@ GBR_HD void face_flux(const RhsArgsT<R>& A, int d_in, int i, int j, int k, const
     // mu / 2, -mu / 3 (lambda / 2) and mu kfac / 2: constants unless mu follows Sutherland's law
     R hmu = ph.hmu_ref, tmu = ph.tmu_ref, hmk = ph.hmk_ref;
     if (ph.sutherland) {
-      const R th = phif[ND] * ph.it_ref;
+      const R th = R(0.5) * phs[ND] * ph.it_ref;
       const R mu = ph.mu_ref * (th * gsqrt(th)) * ((R(1) + ph.suth_s) / (th + ph.suth_s));
       hmu = R(0.5) * mu;
       tmu = R(-1.0 / 3.0) * mu;
@@ -1548,23 +1557,23 @@ GBR_HD void face_flux(const RhsArgsT<R>& A, int d_in, int i, int j, int k, const
       #pragma unroll
       for (int e = 0; e < ND; ++e) div2 = gfma(xe[e][a], gc2[a][e], div2);
     const R hlamdiv = tmu * div2;  // lambda div u / 2, lambda = -2/3 mu
-    R bn = R(0);
+    R bn = R(0);  // 2 beta . n^ minus its conduction part
     #pragma unroll
     for (int a = 0; a < ND; ++a) {
-      R t1 = R(0), t2 = R(0);
+      R t12 = R(0);  // (grad u n^)_a + (grad u^T n^)_a, one chain
       #pragma unroll
       for (int e = 0; e < ND; ++e) {
-        t1 = gfma(m[e], gc2[a][e], t1);
-        t2 = gfma(xe[e][a], sv[e], t2);
+        t12 = gfma(m[e], gc2[a][e], t12);
+        t12 = gfma(xe[e][a], sv[e], t12);
       }
-      const R taun = gfma(hmu, t1 + t2, hlamdiv * nh[a]);  // (tau n^)_a
+      const R taun = gfma(hmu, t12, hlamdiv * nh[a]);  // (tau n^)_a
       F[1 + a] -= taun;
-      bn = gfma(phif[a], taun, bn);
+      bn = gfma(phs[a], taun, bn);  // 2 u . (tau n^)
     }
     R gTn = R(0);
     #pragma unroll
     for (int e = 0; e < ND; ++e) gTn = gfma(m[e], gc2[ND][e], gTn);
-    F[NV - 1] -= gfma(hmk, gTn, bn);
+    F[NV - 1] -= gfma(hmk, gTn, R(0.5) * bn);
   }
   #pragma unroll
   for (int c = 0; c < NV; ++c) A.flux[d][c * FC + f] = F[c];
