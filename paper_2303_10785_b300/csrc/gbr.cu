@@ -28,15 +28,15 @@ using namespace gbr;
 namespace {
 
 // Launch shape of the interface kernel (tuning knobs, set at compile time).  The FP64
-// instantiations are FP64-pipe bound (one 128-thread block per SM's register share is
-// enough); the FP32 ones are issue- and latency-bound and run 7 blocks per SM (72 registers;
-// measured on the 128^3 TGV: 6 blocks / 80 registers 5 % slower, 8 / 64 spills, unconstrained
-// 128 registers 17 % slower).
+// instantiations are FP64-pipe bound and run 4 blocks of 128 threads per SM (at most 128
+// registers: unbounded, the viscous one takes 130-132 and only 3 blocks fit); the FP32 ones are
+// issue- and latency-bound and run 7 blocks per SM (72 registers; measured on the 128^3 TGV:
+// 6 blocks / 80 registers 5 % slower, 8 / 64 spills, unconstrained 128 registers 17 % slower).
 #ifndef GBR_FACE_BLOCK
 #define GBR_FACE_BLOCK 128
 #endif
 #ifndef GBR_FACE_MIN_BLOCKS
-#define GBR_FACE_MIN_BLOCKS 1
+#define GBR_FACE_MIN_BLOCKS 4
 #endif
 #ifndef GBR_FACE_MIN_BLOCKS_F32
 #define GBR_FACE_MIN_BLOCKS_F32 7

@@ -1176,24 +1176,26 @@ GBR_HD void project(const R* nu, R ra, R a2, const R* x, R* W) {
   }
 }
 
-// App. A back-projection d -> R d (hira = 1 / (2 rho a))
+// App. A back-projection onto a base state: out = base + R d (hira = 1 / (2 rho a)); the base
+// enters as the addend of each row's innermost fused multiply-add
 template <int ND, class R>
-GBR_HD void back_project(const R* nu, R hira, R ia2, const R* dl, R* out) {
+GBR_HD void back_project(const R* nu, R hira, R ia2, const R* dl, const R* base, R* out) {
   if (ND == 3) {
-    const R h = R(0.5) * (dl[0] + dl[4]);
+    const R s04 = dl[0] + dl[4];
     const R q = (dl[4] - dl[0]) * hira;
-    out[0] = ia2 * (h + gfma(nu[0], dl[1], gfma(nu[2], dl[2], -nu[1] * dl[3])));
-    out[1] = gfma(nu[0], q, gfma(-nu[1], dl[2], -nu[2] * dl[3]));
-    out[2] = gfma(nu[1], q, gfma(-nu[2], dl[1], nu[0] * dl[2]));
-    out[3] = gfma(nu[2], q, gfma(nu[1], dl[1], nu[0] * dl[3]));
-    out[4] = h;
+    const R x = gfma(nu[0], dl[1], gfma(nu[2], dl[2], -nu[1] * dl[3]));
+    out[0] = gfma(ia2, gfma(R(0.5), s04, x), base[0]);
+    out[1] = gfma(nu[0], q, gfma(-nu[1], dl[2], gfma(-nu[2], dl[3], base[1])));
+    out[2] = gfma(nu[1], q, gfma(-nu[2], dl[1], gfma(nu[0], dl[2], base[2])));
+    out[3] = gfma(nu[2], q, gfma(nu[1], dl[1], gfma(nu[0], dl[3], base[3])));
+    out[4] = gfma(R(0.5), s04, base[4]);
   } else {
-    const R h = R(0.5) * (dl[0] + dl[3]);
+    const R s03 = dl[0] + dl[3];
     const R q = (dl[3] - dl[0]) * hira;
-    out[0] = ia2 * (h + dl[1]);
-    out[1] = gfma(nu[0], q, -nu[1] * dl[2]);
-    out[2] = gfma(nu[1], q, nu[0] * dl[2]);
-    out[3] = h;
+    out[0] = gfma(ia2, gfma(R(0.5), s03, dl[1]), base[0]);
+    out[1] = gfma(nu[0], q, gfma(-nu[1], dl[2], base[1]));
+    out[2] = gfma(nu[1], q, gfma(nu[0], dl[2], base[2]));
+    out[3] = gfma(R(0.5), s03, base[3]);
   }
 }
 
@@ -1282,11 +1284,13 @@ GBR_HD void hllc(const R* PL, const R* PR, const R* nh, R nn2, R nn, R inn2, R n
   R us[ND];
   #pragma unroll
   for (int a = 0; a < ND; ++a) us[a] = left ? PL[1 + a] : PR[1 + a];
-  F[0] = rs * Us;
-  #pragma unroll
-  for (int a = 0; a < ND; ++a) F[1 + a] = gfma(rs * us[a], Us, nh[a] * dps);
-  if constexpr (MOV) F[NV - 1] = gfma(Es + ps, Us, -nt * ps);
-  else F[NV - 1] = (Es + ps) * Us;  // xi_t = 0
+  // The mass and momentum fluxes of the chosen branch, F^K or F^K + S (Q*K - QK), grouped by
+  // what they multiply: rho k1 and rho u_a k1 + n^_a k2, with k1 = U and k2 = p - pref outside the
+  // star region and k1 = U + S dg, k2 = p - pref + S fw inside it (dg, fw below)
+  R k1 = Us, k2 = dps;
+  R Fe;
+  if constexpr (MOV) Fe = gfma(Es + ps, Us, -nt * ps);
+  else Fe = (Es + ps) * Us;  // xi_t = 0
   if (star) {
     // Q*K = rho (S - U)/(S - S*) [1, u + n^ (S* - U)/|n^|^2, E/rho + (S* - U)((S* - xi_t)/|n^|^2 + p/(rho (S - U)))]
     // The correction S (Q*K - QK) is formed with the factor (S* - U) taken out,
@@ -1302,11 +1306,14 @@ GBR_HD void hllc(const R* PL, const R* PR, const R* nh, R nn2, R nn, R inn2, R n
     const R dS = Ss - Us;
     const R dg = dS * g;              // (S* - U) / (S - S*)
     const R fw = fac * dS * inn2;
-    F[0] = gfma(S * rs, dg, F[0]);
-    #pragma unroll
-    for (int a = 0; a < ND; ++a) F[1 + a] = gfma(S, gfma(rs * us[a], dg, fw * nh[a]), F[1 + a]);
-    F[NV - 1] = gfma(S * dS, gfma(fac, gfma(MOV ? Ss - nt : Ss, inn2, p_rA), Es * g), F[NV - 1]);
+    k1 = gfma(S, dg, Us);
+    k2 = gfma(S, fw, dps);
+    Fe = gfma(S * dS, gfma(fac, gfma(MOV ? Ss - nt : Ss, inn2, p_rA), Es * g), Fe);
   }
+  F[0] = rs * k1;
+  #pragma unroll
+  for (int a = 0; a < ND; ++a) F[1 + a] = gfma(rs * us[a], k1, nh[a] * k2);
+  F[NV - 1] = Fe;
 }
 
 // One interface i+1/2 along d: Sec. 5.1 steps 2-6 and Sec. 5.2 steps 1-4, in three stages so
@@ -1484,12 +1491,15 @@ GBR_HD void face_flux(const RhsArgsT<R>& A, int d_in, int i, int j, int k, const
     inn2 = C.inn * C.inn;
   }
   R PL[NV], PR[NV];
-  back_project<ND>(C.nu, C.hira, C.ia2, C.dL, PL);
-  back_project<ND>(C.nu, C.hira, C.ia2, C.dR, PR);
-  #pragma unroll
-  for (int c = 0; c < NV; ++c) {
-    PL[c] += P[c * PC + pp[1]];
-    PR[c] += P[c * PC + pp[2]];
+  {
+    R B1[NV], B2[NV];  // the base cells i, i+1
+    #pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      B1[c] = P[c * PC + pp[1]];
+      B2[c] = P[c * PC + pp[2]];
+    }
+    back_project<ND>(C.nu, C.hira, C.ia2, C.dL, B1, PL);
+    back_project<ND>(C.nu, C.hira, C.ia2, C.dR, B2, PR);
   }
   R F[NV];
   hllc<ND, MOV>(PL, PR, nh, nn2, nn, inn2, nt, ph, A.pref_r, F);
