@@ -120,11 +120,13 @@ __global__ void __launch_bounds__(kBlock) kb_grad12(const BatchJob<R>* jobs, con
 }
 
 // As k_face: the limiter's bound work compacted over the block (every thread takes part in
-// each work block's barriers); FP32 at 7 blocks of 128 threads per SM (as k_face), FP64 at 384
-// threads (at most 168 registers: 4 % faster than the unconstrained 234 on a batch of 64^3 TGV
-// and 256^2 vortex jobs).
+// each work block's barriers); FP32 at 896 threads per SM in 3D (7 blocks of 128, as k_face:
+// 72 registers, some spilled, measured faster than 768 or 640 threads without spills on a batch
+// of 48^3-64^3 mixed TGV jobs) and 768 in 2D (5 % faster than 896 on 96^2-160^2 vortex jobs),
+// FP64 at 384 threads (at most 168 registers: 4 % faster than the unconstrained 234 on a batch
+// of 64^3 TGV and 256^2 vortex jobs).
 template <int ND, bool VISC, bool MOV, class R, int BS>
-__global__ void __launch_bounds__(BS, sizeof(R) == 4 ? 896 / BS : (BS < 384 ? 384 / BS : 1))
+__global__ void __launch_bounds__(BS, sizeof(R) == 4 ? (ND == 3 ? 896 : 768) / BS : (BS < 384 ? 384 / BS : 1))
     kb_face(const BatchJob<R>* jobs, const WorkItem* items, int n, int total) {
   __shared__ BoundSlot<ND, R> slots[BS];
   __shared__ int count;
