@@ -713,7 +713,7 @@ __global__ void k_dt_f32(DtArgs D, float* mh32, float* mt32, float* jac32, Box b
   body_dt_f32(D, mh32, mt32, jac32, i, j, k);
 }
 
-template <int ND, class R = double>
+template <int ND, class R = double, bool GS = false>
 __global__ void k_dt(DtArgs D, Box b, unsigned long long* minbits) {
   // the minimum is taken in the path's type (exact: conversion to FP64 is monotone and exact),
   // and converted once per block -- on the mixed path no FP64-pipe work per cell but the state's
@@ -722,7 +722,7 @@ __global__ void k_dt(DtArgs D, Box b, unsigned long long* minbits) {
   if (t < box_size(b)) {
     int i, j, k;
     box_coord(b, t, i, j, k);
-    v = body_dt_r<ND, R>(D, i, j, k);
+    v = body_dt_r<ND, R, GS>(D, i, j, k);
   }
   // fmin (fminf for FP32, on the ALU pipe) passes over a NaN of a broken state as before
   for (int off = 16; off > 0; off >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, off));
@@ -770,7 +770,7 @@ struct Plan {
 enum Slot {
   SL_Q0, SL_Q1, SL_Q2, SL_PRIM, SL_TEMP, SL_G1, SL_G2, SL_FLUX, SL_NODES, SL_NVEL, SL_XC, SL_VC, SL_XD, SL_MH,
   SL_DET, SL_MU, SL_MT, SL_FH, SL_FU, SL_FT, SL_GCL, SL_JAC, SL_SIGMA, SL_INFLOW, SL_SCAL, SL_ERR, SL_IG4, SL_FH32, SL_FU32,
-  SL_FT32, SL_IG4F, SL_MH32, SL_MT32, SL_JAC32, SL_GEOT, SL_GEOW, SL_FG, SL_COUNT
+  SL_FT32, SL_IG4F, SL_MH32, SL_MT32, SL_JAC32, SL_GEOT, SL_GEOW, SL_FG, SL_GDT, SL_COUNT
 };
 
 struct Sizes {
@@ -910,6 +910,7 @@ Plan plan_of(const gbr_params* p, const Layout& L) {
   P.add(D * geot);                                               // SL_GEOT
   P.add(geo4 ? D * L.ecount : 0);                                // SL_GEOW
   P.add(f32 ? 0 : D * fg_count(visc) * fsum);                    // SL_FG: FP64 interface geometry
+  P.add(f32 || mov ? 0 : D * 2 * nd * L.ncells);                 // SL_GDT: FP64 time-step metric norms
   P.total = (P.total + 255) & ~(size_t)255;
   return P;
 }
@@ -954,6 +955,7 @@ struct gbr_ctx {
   void *prim, *temp, *g1[3], *g2[3], *flux[3];  // element type double (FP64) or float (mixed)
   double *nodes, *nvel, *xc, *vc, *xd, *mh, *det, *mu, *mt, *fh[3], *fu[3], *ft[3], *gcl, *jac;
   double* fg[3];  // FP64 path: interface geometry derived from fh, fu (body_face_geo), or null
+  double* gdt;    // FP64 path, static mesh: the time step's metric norms (body_dt_geo), or null
   float *fh32[3], *fu32[3], *ft32[3];  // mixed path: FP32 copies of the interface metrics
   float *mh32, *mt32, *jac32;          // mixed path: FP32 copies of the cell metrics (time step)
   double *sigma, *inflow, *scal;
@@ -1238,6 +1240,12 @@ gbr_status run_geometry_ig4(gbr_ctx* c, const GeoArgs& G, const GeoBoxes& B, cud
   return GBR_OK;
 }
 
+// FP64 path on a static mesh: the time step's metric norms (after J, k_gcl)
+__global__ void k_dt_geo(DtArgs D, double* gdt, Box b) {
+  BOX_THREAD(b);
+  body_dt_geo(D, gdt, i, j, k);
+}
+
 // FP64 path: the interface geometry of every direction, after the interface metrics
 gbr_status launch_face_geo(gbr_ctx* c, const GeoArgs& G, const GeoBoxes& B, cudaStream_t st) {
   if (!c->fg[0]) return GBR_OK;
@@ -1279,6 +1287,10 @@ gbr_status run_geometry(gbr_ctx* c, cudaStream_t st) {
   }
   k_gcl<<<grid_of(B.inner, kBlock), kBlock, 0, st>>>(G, B.inner);
   CKL("k_gcl");
+  if (c->gdt) {
+    k_dt_geo<<<grid_of(B.inner, kBlock), kBlock, 0, st>>>(dt_args(c), c->gdt, B.inner);
+    CKL("k_dt_geo");
+  }
   if (c->p.precision == GBR_PREC_MIXED) {
     // FP32 copies of the interface metrics (whole slots: all directions at once)
     const Plan& P = c->plan;
@@ -1539,6 +1551,7 @@ DtArgs dt_args(gbr_ctx* c) {
   D.mh32 = c->mh32;
   D.mt32 = c->mov ? c->mt32 : nullptr;
   D.jac32 = c->jac32;
+  D.gdt = c->gdt;
   return D;
 }
 
@@ -1555,8 +1568,13 @@ gbr_status run_dt(gbr_ctx* c, double cfl) {
     if (L.nd == 3) k_dt<3, float><<<g, kBlock, 0, st>>>(D, bi, bits);
     else k_dt<2, float><<<g, kBlock, 0, st>>>(D, bi, bits);
   } else {
-    if (L.nd == 3) k_dt<3, double><<<g, kBlock, 0, st>>>(D, bi, bits);
-    else k_dt<2, double><<<g, kBlock, 0, st>>>(D, bi, bits);
+    if (D.gdt) {
+      if (L.nd == 3) k_dt<3, double, true><<<g, kBlock, 0, st>>>(D, bi, bits);
+      else k_dt<2, double, true><<<g, kBlock, 0, st>>>(D, bi, bits);
+    } else {
+      if (L.nd == 3) k_dt<3, double><<<g, kBlock, 0, st>>>(D, bi, bits);
+      else k_dt<2, double><<<g, kBlock, 0, st>>>(D, bi, bits);
+    }
   }
   CKL("k_dt");
   k_dt_final<<<1, 1, 0, c->stream>>>(c->scal, bits, cfl);
@@ -1574,6 +1592,7 @@ void carve(gbr_ctx* c) {
   auto rptr = [&](int slot, size_t elems) -> void* { return P.len[slot] ? c->ws + P.off[slot] + ER * elems : nullptr; };
   c->prim = rptr(SL_PRIM, 0);
   c->temp = rptr(SL_TEMP, 0);
+  c->gdt = ptr(SL_GDT);
   const int nv = L.nv, nd = L.nd;
   const int n1 = nv + (c->visc ? 1 : 0);
   size_t foff = 0;

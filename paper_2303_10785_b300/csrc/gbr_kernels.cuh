@@ -1328,8 +1328,8 @@ template <int ND, class R>
 struct FaceCtx {
   static constexpr int NV = ND + 2;
   FaceIx<R> p1, f;      // padded index of cell i, interface index
-  R nh[ND], nu[ND];
-  R nn2, inn, nt;
+  R nh[ND], nu[ND];     // n^ and the unit normal
+  R nn2, inn, nt;       // |n^|^2, 1/|n^| (formed on the FP32 path only; FP64 reads fg), hat xi_t
   R ra, a2, hira, ia2;  // face state of the eigenvectors (hira = 1 / (2 rho a))
   R Wd[3][NV];          // projected differences of cells i-1 .. i+2
   R dL[NV], dR[NV];     // W^L - W_i, W^R - W_{i+1}
@@ -1763,7 +1763,29 @@ struct DtArgs {
   const float* mh32;
   const float* mt32;
   const float* jac32;
+  // FP64 path on a static mesh: |grad xi_e| and |grad xi_e|^2 per direction ([2 nd][cells],
+  // body_dt_geo), else null
+  const double* gdt;
 };
+
+// The time step's metric norms on a static mesh, once per mesh: g2_e = sum_a (mh_ea J)^2 and
+// sqrt(g2_e), by the operations and in the order of body_dt_r (which then reads them), so the
+// time step is unchanged bit for bit
+GBR_HD void body_dt_geo(const DtArgs& D, double* gdt, int i, int j, int k) {
+  const Layout& L = D.L;
+  const int nd = L.nd;
+  const long long c = cidx(L, i, j, k), NC = L.ncells, e = eidx(L, i, j, k), EC = L.ecount;
+  const double J = D.jac[c];
+  for (int ee = 0; ee < nd; ++ee) {
+    double g2 = 0.0;
+    for (int a = 0; a < nd; ++a) {
+      const double m = D.mh[(ee * 3 + a) * EC + e] * J;
+      g2 = gfma(m, m, g2);
+    }
+    gdt[ee * NC + c] = gsqrt(g2);
+    gdt[(nd + ee) * NC + c] = g2;
+  }
+}
 
 // FP32 copies of the cell metrics the mixed path's time step reads (interior cells)
 GBR_HD void body_dt_f32(const DtArgs& D, float* mh32, float* mt32, float* jac32, int i, int j, int k) {
@@ -1776,7 +1798,9 @@ GBR_HD void body_dt_f32(const DtArgs& D, float* mh32, float* mt32, float* jac32,
   jac32[c] = (float)D.jac[c];
 }
 
-template <int ND, class R = double>
+// GS: the metric norms are read from D.gdt (FP64, static mesh; the instantiation chosen on the
+// host); otherwise formed here (and read when D.gdt is set, a uniform run-time choice)
+template <int ND, class R = double, bool GS = false>
 GBR_HD R body_dt_r(const DtArgs& D, int i, int j, int k) {
   // evaluated in the path's type R (the mixed path's FP32 time step differs from the FP64 one by
   // FP32 round-off, far below the CFL number's own slack)
@@ -1808,6 +1832,7 @@ GBR_HD R body_dt_r(const DtArgs& D, int i, int j, int k) {
   // min over directions of 1/(|U| + c |grad xi|) and 1/(nu_eff |grad xi|^2) as one division by the
   // largest denominator: division is correctly rounded and monotone, so the result is the same value
   R worst = R(0);
+  const bool stored = GS || (!F32 && D.gdt != nullptr);
   for (int ee = 0; ee < ND; ++ee) {
     R Uc = D.mt ? ((F32 && D.mt32) ? R(D.mt32[ee * NC + c]) : R(D.mt[ee * EC + e])) * J : R(0);
     R g2 = R(0);
@@ -1815,9 +1840,16 @@ GBR_HD R body_dt_r(const DtArgs& D, int i, int j, int k) {
       const R mv = (F32 && D.mh32) ? R(D.mh32[(ee * 3 + a) * NC + c]) : R(D.mh[(ee * 3 + a) * EC + e]);
       const R m = mv * J;
       Uc = gfma(m, u[a], Uc);
-      g2 = gfma(m, m, g2);
+      if (!stored) g2 = gfma(m, m, g2);
     }
-    worst = gmax(worst, gabs(Uc) + cs * gsqrt(g2));
+    R gn;
+    if (stored) {
+      gn = R(D.gdt[ee * NC + c]);
+      g2 = R(D.gdt[(ND + ee) * NC + c]);
+    } else {
+      gn = gsqrt(g2);
+    }
+    worst = gmax(worst, gabs(Uc) + cs * gn);
     if (ph.viscous) worst = gmax(worst, nu_eff * g2);
   }
   return R(1) / worst;  // +inf where nothing bounds the step
