@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define GBR_ABI_VERSION 3
+#define GBR_ABI_VERSION 4
 
 typedef struct gbr_ctx gbr_ctx;
 
@@ -227,6 +227,18 @@ gbr_status gbr_profile(gbr_ctx* c, int enable, double* face_ms, long long* face_
  * cudaStream_t or NULL).  Synchronous.  tflops, ms (the timed launch's
  * duration): out pointers, may be NULL.  Errors: EINVAL (precision), ECUDA. */
 gbr_status gbr_alu_peak(int precision, void* stream, double* tflops, double* ms);
+
+/* Self-check of the FP64 reciprocal the kernels use in place of divisions (no
+ * counterpart in the paper): Newton's method for 1/x from the hardware's
+ * approximate reciprocal, meant to lie within one unit in the last place of the
+ * correctly rounded 1/x for finite, nonzero, normal x whose reciprocal is normal.
+ * Runs n such x on the device (SplitMix64 bit patterns of seed + index: random
+ * sign and mantissa, biased exponent 23 .. 2023) and returns in *max_ulp the
+ * largest distance, in units in the last place, between that reciprocal and the
+ * FP64 division 1.0 / x.  Synchronous on `stream` (a cudaStream_t or NULL); no
+ * allocation (one file-scope device counter, so concurrent calls share it).
+ * Errors: EINVAL (n outside 1 .. 2^34, null max_ulp), ECUDA. */
+gbr_status gbr_check_rcp(long long n, unsigned long long seed, void* stream, long long* max_ulp);
 
 /* Self-check of the kernels' bounded waits (no counterpart in the paper).  The
  * MIG4 line solves wait for a TMA tile copy on an mbarrier with a bounded

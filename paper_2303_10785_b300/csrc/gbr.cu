@@ -2242,6 +2242,48 @@ gbr_status gbr_alu_peak(int precision, void* stream, double* tflops, double* ms)
   return fail(nullptr, GBR_EINVAL, "precision must be GBR_PREC_FP64 or GBR_PREC_MIXED");
 }
 
+// ---------------------------------------------------------------------------
+// Self-check of grcp (gbr_check_rcp): its reciprocal against the FP64 division on
+// SplitMix64 bit patterns (Steele, Lea and Flood, "Fast splittable pseudorandom
+// number generators", OOPSLA 2014), the largest distance in units in the last place.
+// ---------------------------------------------------------------------------
+__device__ unsigned long long g_rcp_max_ulp;
+
+__global__ void k_rcp_check(long long n, unsigned long long seed) {
+  unsigned long long worst = 0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z = seed + (unsigned long long)(t + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const unsigned long long ef = 23 + (z >> 53) % 2001;  // x and 1/x normal
+    const unsigned long long b = ((unsigned long long)(t & 1) << 63) | (ef << 52) | (z & ((1ull << 52) - 1));
+    const double x = __longlong_as_double((long long)b);
+    const long long r1 = __double_as_longlong(grcp(x)), r2 = __double_as_longlong(1.0 / x);
+    const unsigned long long d = (unsigned long long)(r1 > r2 ? r1 - r2 : r2 - r1);
+    worst = d > worst ? d : worst;
+  }
+  atomicMax(&g_rcp_max_ulp, worst);
+}
+
+gbr_status gbr_check_rcp(long long n, unsigned long long seed, void* stream, long long* max_ulp) {
+  if (!max_ulp || n < 1 || n > (1LL << 34)) return fail(nullptr, GBR_EINVAL, "check_rcp: n outside 1 .. 2^34 or null max_ulp");
+  cudaStream_t st = (cudaStream_t)stream;
+  void* addr = nullptr;
+  if (cudaGetSymbolAddress(&addr, g_rcp_max_ulp) != cudaSuccess || cudaMemsetAsync(addr, 0, sizeof(unsigned long long), st) != cudaSuccess)
+    return fail(nullptr, GBR_ECUDA, "check_rcp: counter reset failed");
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return fail(nullptr, GBR_ECUDA, "check_rcp: device query failed");
+  k_rcp_check<<<sms * 8, 256, 0, st>>>(n, seed);
+  unsigned long long v = 0;
+  if (cudaGetLastError() != cudaSuccess || cudaMemcpyAsync(&v, addr, sizeof v, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(nullptr, GBR_ECUDA, "check_rcp: kernel or copy failed");
+  *max_ulp = (long long)v;
+  return GBR_OK;
+}
+
 gbr_status gbr_check_bounded_wait(gbr_ctx* c, int polls) {
   if (!c) return fail(nullptr, GBR_EINVAL, "null context");
   if (polls < 1 || polls > kTmaSpin) return fail(c, GBR_EINVAL, "polls out of range");

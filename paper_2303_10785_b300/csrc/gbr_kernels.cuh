@@ -178,6 +178,30 @@ GBR_HD double grsqrt(double x) {
   return 1.0 / std::sqrt(x);
 #endif
 }
+// 1/x by Newton's method for the reciprocal, y <- y + y (1 - x y), from the hardware's approximate
+// reciprocal (PTX rcp.approx.ftz.f64, relative error below 2^-22): the error squares at each step,
+// so two steps leave it below the FP64 rounding (within one unit in the last place of 1/x; the
+// FP64 division is correctly rounded).  Four FMAs against the division's longer sequence on the
+// FP64 pipe.  For finite, nonzero, normal x (densities, a Riemann fan's width, S - S*); gbr_check_rcp
+// measures it against the division.
+GBR_HD double grcp(double x) {
+#ifdef __CUDA_ARCH__
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+#else
+  return 1.0 / x;
+#endif
+}
+// FP32 (mixed path): the division (its FP32 sequence is short)
+GBR_HD float grcp(float x) { return 1.0f / x; }
+// a / b: FP64 as a times grcp(b), FP32 the division
+GBR_HD double gdiv(double a, double b) { return a * grcp(b); }
+GBR_HD float gdiv(float a, float b) { return a / b; }
+
 GBR_HD double gfma(double a, double b, double c) {
 #ifdef __CUDA_ARCH__
   return fma(a, b, c);
@@ -742,7 +766,7 @@ GBR_HD void prim_store(const RhsArgsT<R>& A, const double* q, const float* dq, l
   const Layout& L = A.L;
   const long long NC = L.ncells, PC = L.pcount;
   const R rho = dq ? R(q[c]) + R(dq[c]) : R(q[c]);
-  const R ir = R(1) / rho;
+  const R ir = grcp(rho);
   R ke = R(0);
   A.prim[p] = rho;
   for (int a = 0; a < ND; ++a) {
@@ -1275,7 +1299,7 @@ GBR_HD void hllc(const R* PL, const R* PR, const R* nh, R nn2, R nn, R inn2, R n
   const R SL = gmin(gfma(-cl, nn, Ul), gfma(-cr, nn, Ur));
   const R SR = gmax(gfma(cl, nn, Ul), gfma(cr, nn, Ur));
   const R aL = rl * (SL - Ul), aR = rr * (SR - Ur);
-  const R Ss = (aR * Ur - aL * Ul + (dpl - dpr) * nn2) / (aR - aL);
+  const R Ss = gdiv(aR * Ur - aL * Ul + (dpl - dpr) * nn2, aR - aL);
   // branches of Sec. 5.1.1: S^L >= 0 -> F^L; S^L < 0 <= S* -> F*L; S* < 0 < S^R -> F*R; else F^R
   const bool left = !is_neg(SL) || !is_neg(Ss);
   const bool star = is_neg(SL) && (left || is_pos(SR));
@@ -1299,7 +1323,7 @@ GBR_HD void hllc(const R* PL, const R* PR, const R* nh, R nn2, R nn, R inn2, R n
     // difference would lose a factor c/|U| of the working precision.
     const R rA = rs * (S - Us);
     const R B = S - Ss;
-    const R inv = R(1) / (rA * B);
+    const R inv = grcp(rA * B);
     const R g = rA * inv;             // 1 / (S - S*)
     const R fac = rA * g;             // rho (S - U) / (S - S*)
     const R p_rA = ps * B * inv;      // p / (rho (S - U))
@@ -1809,7 +1833,7 @@ GBR_HD R body_dt_r(const DtArgs& D, int i, int j, int k) {
   const Phys& ph = D.ph;
   const long long c = cidx(L, i, j, k), NC = L.ncells, e = eidx(L, i, j, k), EC = L.ecount;
   const R rho = R(D.q[c]);
-  const R ir = R(1) / rho;
+  const R ir = grcp(rho);
   R u[ND], ke = R(0);
   for (int a = 0; a < ND; ++a) {
     const R m = R(D.q[(1 + a) * NC + c]);

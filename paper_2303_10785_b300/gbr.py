@@ -94,6 +94,8 @@ def lib():
     L.gbr_check_bounded_wait.argtypes = [_vp, ctypes.c_int]
     L.gbr_alu_peak.argtypes = [ctypes.c_int, _vp, _P, _P]
     L.gbr_alu_peak.restype = ctypes.c_int
+    L.gbr_check_rcp.argtypes = [ctypes.c_longlong, ctypes.c_ulonglong, _vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.gbr_check_rcp.restype = ctypes.c_int
     L.gbr_set_state_async.argtypes = [_vp, _vp, _vp]
     L.gbr_get_state_async.argtypes = [_vp, _vp, _vp]
     L.gbr_profile.restype = ctypes.c_int
@@ -142,7 +144,7 @@ def exported_symbols():
     return ["gbr_workspace_bytes", "gbr_create", "gbr_compute_metrics", "gbr_move_mesh", "gbr_set_motion",
             "gbr_set_state", "gbr_get_state", "gbr_set_inflow", "gbr_set_sponge", "gbr_rhs", "gbr_compute_dt",
             "gbr_set_state_async", "gbr_get_state_async", "gbr_rk_step", "gbr_sync", "gbr_get_time", "gbr_get_field",
-            "gbr_profile", "gbr_check_bounded_wait", "gbr_alu_peak",
+            "gbr_profile", "gbr_check_bounded_wait", "gbr_alu_peak", "gbr_check_rcp",
             "gbr_rhs_static",
             "gbr_batch_workspace_bytes", "gbr_batch_create", "gbr_batch_set_options", "gbr_batch_add",
             "gbr_batch_remove", "gbr_batch_step", "gbr_batch_sync", "gbr_batch_info", "gbr_batch_tuning",
@@ -161,6 +163,17 @@ def alu_peak(precision="fp64", stream=None):
     if rc:
         raise GbrError(rc, L.gbr_last_global_error().decode())
     return tf.value, ms.value
+
+
+def check_rcp(n, seed=0, stream=None):
+    """Largest ulp distance between the kernels' FP64 reciprocal and the division over n random x."""
+    L = lib()
+    out = ctypes.c_longlong()
+    st = None if stream is None else _vp(stream.cuda_stream)
+    rc = L.gbr_check_rcp(int(n), int(seed), st, ctypes.byref(out))
+    if rc:
+        raise GbrError(rc, L.gbr_last_global_error().decode())
+    return out.value
 
 
 def make_params(case):
