@@ -760,6 +760,9 @@ GBR_HD R stencil_E6(const R* f, long long e, long long s) {
 // dq (mixed path, or null): the FP32 increment of the stage state over q, Q_s = q + dq (the
 // stage states of a step are kept as Q^n plus an FP32 increment, see body_update); added after
 // the rounding to FP32.
+// The stored pressures carry p - pref, and pref = 0 on the FP64 path
+template <class R>
+constexpr bool kPrefZero = sizeof(R) == sizeof(double);
 template <int ND, class R>
 GBR_HD void prim_store(const RhsArgsT<R>& A, const double* q, const float* dq, long long c, long long p) {
   constexpr int NV = ND + 2;
@@ -777,10 +780,12 @@ GBR_HD void prim_store(const RhsArgsT<R>& A, const double* q, const float* dq, l
     ke = gfma(m, u, ke);
   }
   const long long oE = (NV - 1) * NC + c;
-  const R Erel = dq ? R(q[oE] - A.pref * A.ph.igm1) + R(dq[oE]) : R(q[oE] - A.pref * A.ph.igm1);
+  // E - pref/(gamma - 1) (pref = 0 on the FP64 path: nothing to subtract)
+  const double Eoff = kPrefZero<R> ? q[oE] : q[oE] - A.pref * A.ph.igm1;
+  const R Erel = dq ? R(Eoff) + R(dq[oE]) : R(Eoff);
   const R prel = A.pr.gm1 * (Erel - R(0.5) * ke);  // p - pref
   A.prim[(NV - 1) * PC + p] = prel;
-  if (A.viscous) A.temp[p] = (prel + A.pref_r) * ir;
+  if (A.viscous) A.temp[p] = (kPrefZero<R> ? prel : prel + A.pref_r) * ir;
 }
 
 // primitives at interior cells
@@ -948,9 +953,6 @@ constexpr bool kFaceFormsG2 = sizeof(R) == sizeof(float);
 // ones, issue-bound, form it (fewer instructions than the loads and their addresses)
 template <class R>
 constexpr bool kFaceGeo = sizeof(R) == sizeof(double);
-// The stored pressures carry p - pref, and pref = 0 on the FP64 path
-template <class R>
-constexpr bool kPrefZero = sizeof(R) == sizeof(double);
 
 template <class R, class I>
 GBR_HD R second_deriv_12(const R* f, const R* f1, I p, I s) {
