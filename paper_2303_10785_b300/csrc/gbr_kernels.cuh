@@ -564,8 +564,8 @@ GBR_HD void body_metrics(const GeoArgs& G, int i, int j, int k, bool mh_given = 
 // (functions of the mesh alone), stored per interface in fg: the unit normal nu = n^/|n^|, |n^|^2,
 // 1/|n^|, |n^|, 1/|n^|^2 and, viscous, m_e = sum_b (d xi_e/d x_b) n^_b (the chain rule contracted
 // with n^, Sec. 5.2).  Each value is formed by the same operations in the same order as the
-// interface stages' own forms (face_unlimited, hllc, face_flux), so the fluxes are unchanged bit
-// for bit.
+// FP32 interface stages form them in place (face_unlimited, hllc, face_flux): the stored values
+// equal what the stages would form.
 enum { FG_NU = 0, FG_NN2 = 3, FG_INN = 4, FG_NN = 5, FG_INN2 = 6, FG_M = 7, FG_COUNT = 10 };
 inline int fg_count(bool viscous) { return viscous ? FG_COUNT : FG_M; }
 
@@ -1795,8 +1795,8 @@ struct DtArgs {
 };
 
 // The time step's metric norms on a static mesh, once per mesh: g2_e = sum_a (mh_ea J)^2 and
-// sqrt(g2_e), by the operations and in the order of body_dt_r (which then reads them), so the
-// time step is unchanged bit for bit
+// sqrt(g2_e), by the operations and in the order of body_dt_r's own form (which then reads them
+// instead): the stored values equal what it would form
 GBR_HD void body_dt_geo(const DtArgs& D, double* gdt, int i, int j, int k) {
   const Layout& L = D.L;
   const int nd = L.nd;
