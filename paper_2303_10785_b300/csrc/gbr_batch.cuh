@@ -53,9 +53,10 @@ struct WorkItem {
 
 enum { WL_PAD = 0, WL_GRAD1, WL_GRAD2, WL_FACE, WL_INNER, WL_DT, WL_COUNT };
 
-// Runs f(item, local block) for the contiguous block range of this CTA.
+// Runs f(item, local block) for the contiguous block range of this CTA.  The items may be a
+// sub-range of a longer list: `base` is the block offset its first item starts at.
 template <class F>
-__device__ __forceinline__ void for_work(const WorkItem* items, int n_items, int total, F f) {
+__device__ __forceinline__ void for_work(const WorkItem* items, int n_items, int total, F f, int base = 0) {
   const int chunk = (total + (int)gridDim.x - 1) / (int)gridDim.x;
   const int b0 = (int)blockIdx.x * chunk;
   const int b1 = min(total, b0 + chunk);
@@ -63,11 +64,11 @@ __device__ __forceinline__ void for_work(const WorkItem* items, int n_items, int
   int lo = 0, hi = n_items - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (items[mid].first <= b0) lo = mid;
+    if (items[mid].first <= b0 + base) lo = mid;
     else hi = mid - 1;
   }
   int m = lo;
-  for (int blk = b0; blk < b1; ++blk) {
+  for (int blk = b0 + base; blk < b1 + base; ++blk) {
     while (m + 1 < n_items && blk >= items[m].first + items[m].blocks) ++m;
     f(items[m], blk - items[m].first);
   }
@@ -125,19 +126,20 @@ __global__ void __launch_bounds__(kBlock) kb_grad12(const BatchJob<R>* jobs, con
 // of 48^3-64^3 mixed TGV jobs) and 768 in 2D (5 % faster than 896 on 96^2-160^2 vortex jobs),
 // FP64 at 384 threads (at most 168 registers: 4 % faster than the unconstrained 234 on a batch
 // of 64^3 TGV and 256^2 vortex jobs).
-template <int ND, bool VISC, bool MOV, class R, int BS>
+// DD: the one sweep direction of the launch's items (the per-direction instantiation, as k_face)
+template <int ND, bool VISC, bool MOV, class R, int BS, int DD>
 __global__ void __launch_bounds__(BS, sizeof(R) == 4 ? (ND == 3 ? 896 : 768) / BS : (BS < 384 ? 384 / BS : 1))
-    kb_face(const BatchJob<R>* jobs, const WorkItem* items, int n, int total) {
+    kb_face(const BatchJob<R>* jobs, const WorkItem* items, int n, int total, int base) {
   __shared__ BoundSlot<ND, R> slots[BS];
   __shared__ int count;
   for_work(items, n, total, [&](const WorkItem& it, int lb) {
     const BatchJob<R>& J = jobs[it.job];
     const long long t = (long long)lb * blockDim.x + threadIdx.x;
-    const bool valid = t < box_size(J.faces[it.sub]);
+    const bool valid = t < box_size(J.faces[DD]);
     int i = 0, j = 0, k = 0;
-    if (valid) box_coord(J.faces[it.sub], t, i, j, k);
-    face_block<ND, VISC, MOV>(J.A, it.sub, valid, i, j, k, slots, &count);
-  });
+    if (valid) box_coord(J.faces[DD], t, i, j, k);
+    face_block<ND, VISC, MOV, R, DD>(J.A, DD, valid, i, j, k, slots, &count);
+  }, base);
 }
 
 template <int ND, bool MOV, class R, bool SP>
@@ -323,6 +325,10 @@ struct Kind {
   WorkItem* d_items[WL_COUNT] = {};
   std::vector<WorkItem> items[WL_COUNT];
   int total[WL_COUNT] = {};
+  // the interface items ordered by direction: direction d is items[WL_FACE][face_start[d] ..
+  // face_start[d] + face_n[d]), blocks face_base[d] .. face_base[d] + face_total[d] of the list
+  int face_start[3] = {}, face_n[3] = {}, face_base[3] = {}, face_total[3] = {};
+  int face_dirs = 0;
   long long cells = 0;
   Tuning tune;
   unsigned* d_bar = nullptr;  // grid-barrier words of the fused stage kernel: count, generation, timeout
@@ -467,15 +473,27 @@ void build_items(Kind& K) {
     const int jm = (int)m;
     // the fused stage kernel runs every phase with its one block size
     const int sb = K.tune.fused_stage ? kFusedBlock : kBlock;
-    const int fb = K.tune.fused_stage ? kFusedBlock : K.tune.face_block;
     add_items(K.items[WL_PAD], K.total[WL_PAD], jm, 0, pad_box(L, H, H), sb);
     for (int d = 0; d < L.nd; ++d) {
       add_items(K.items[WL_GRAD1], K.total[WL_GRAD1], jm, d, B.grad1[d], sb);
       add_items(K.items[WL_GRAD2], K.total[WL_GRAD2], jm, d, B.grad2[d], sb);
-      add_items(K.items[WL_FACE], K.total[WL_FACE], jm, d, B.faces[d], fb);
     }
     add_items(K.items[WL_INNER], K.total[WL_INNER], jm, 0, B.inner, sb);
     if (K.cfl[m] > 0.0) add_items(K.items[WL_DT], K.total[WL_DT], jm, 0, B.inner, kBlock);
+  }
+  // interfaces: every member's x-sweep, then the y- and z-sweeps (one launch per direction)
+  const int fb = K.tune.fused_stage ? kFusedBlock : K.tune.face_block;
+  K.face_dirs = 0;
+  for (int d = 0; d < 3; ++d) {
+    K.face_start[d] = (int)K.items[WL_FACE].size();
+    K.face_base[d] = K.total[WL_FACE];
+    for (size_t m = 0; m < K.members.size(); ++m) {
+      const Layout& L = K.members[m]->L;
+      if (d < L.nd) add_items(K.items[WL_FACE], K.total[WL_FACE], (int)m, d, rhs_boxes(L).faces[d], fb);
+    }
+    K.face_n[d] = (int)K.items[WL_FACE].size() - K.face_start[d];
+    K.face_total[d] = K.total[WL_FACE] - K.face_base[d];
+    if (K.face_n[d] > 0) ++K.face_dirs;
   }
 }
 
@@ -492,13 +510,25 @@ unsigned persistent_grid(gbr_batch* b, KernelT kernel, int block, int total) {
   return (unsigned)std::max(1, std::min(total, resident_ctas(b, kernel, block)));
 }
 
+// one launch per sweep direction, each over that direction's range of the interface items
 template <int ND, bool VISC, bool MOV, class R, int BS>
-gbr_status launch_face_kind(gbr_batch* b, const Kind& K, const BatchJob<R>* jobs) {
-  auto kern = kb_face<ND, VISC, MOV, R, BS>;
-  const unsigned g = persistent_grid(b, kern, BS, K.total[WL_FACE]);
-  kern<<<g, BS, 0, b->cur>>>(jobs, K.d_items[WL_FACE], (int)K.items[WL_FACE].size(), K.total[WL_FACE]);
-  BK(cudaGetLastError(), "kb_face");
-  return GBR_OK;
+gbr_status launch_face_kind(gbr_batch* b, const Kind& K, const BatchJob<R>* jobs, long long& launches) {
+  auto one = [&](auto dd) -> gbr_status {
+    constexpr int D = decltype(dd)::value;
+    if (K.face_n[D] == 0) return GBR_OK;
+    auto kern = kb_face<ND, VISC, MOV, R, BS, D>;
+    const unsigned g = persistent_grid(b, kern, BS, K.face_total[D]);
+    kern<<<g, BS, 0, b->cur>>>(jobs, K.d_items[WL_FACE] + K.face_start[D], K.face_n[D], K.face_total[D],
+                               K.face_base[D]);
+    BK(cudaGetLastError(), "kb_face");
+    ++launches;
+    return GBR_OK;
+  };
+  gbr_status s = one(std::integral_constant<int, 0>{});
+  if (s == GBR_OK) s = one(std::integral_constant<int, 1>{});
+  if constexpr (ND == 3)
+    if (s == GBR_OK) s = one(std::integral_constant<int, 2>{});
+  return s;
 }
 
 // work of one member launched on the batch's current stream (its geometry, its IG4 solves),
@@ -606,9 +636,9 @@ gbr_status enqueue_rhs(gbr_batch* b, const Kind& K, int stage, long long& launch
   }
   gbr_status s;
   switch (K.tune.face_block) {
-    case 64: s = launch_face_kind<ND, VISC, MOV, R, 64>(b, K, jobs); break;
-    case 256: s = launch_face_kind<ND, VISC, MOV, R, 256>(b, K, jobs); break;
-    default: s = launch_face_kind<ND, VISC, MOV, R, 128>(b, K, jobs); break;
+    case 64: s = launch_face_kind<ND, VISC, MOV, R, 64>(b, K, jobs, launches); break;
+    case 256: s = launch_face_kind<ND, VISC, MOV, R, 256>(b, K, jobs, launches); break;
+    default: s = launch_face_kind<ND, VISC, MOV, R, 128>(b, K, jobs, launches); break;
   }
   if (s != GBR_OK) return s;
   {
@@ -620,7 +650,7 @@ gbr_status enqueue_rhs(gbr_batch* b, const Kind& K, int stage, long long& launch
         jobs, K.d_items[WL_INNER], (int)K.items[WL_INNER].size(), K.total[WL_INNER], stage);
     BK(cudaGetLastError(), "kb_update");
   }
-  launches += 2;
+  launches += 1;  // the update (launch_face_kind counted the interface launches)
   return GBR_OK;
 }
 
@@ -920,7 +950,9 @@ gbr_status rebuild(gbr_batch* b) {
         launches = -1;
         break;
       }
-      const int per_stage = K.tune.fused_stage ? 1 : ((K.tune.fused_grad || K.key.prec == GBR_PREC_MIXED) ? 4 : 5);
+      // phase kernels: primitives, gradients (one or two), one interface launch per direction, update
+      const int per_stage =
+          K.tune.fused_stage ? 1 : ((K.tune.fused_grad || K.key.prec == GBR_PREC_MIXED) ? 3 : 4) + K.face_dirs;
       launches += 3 + (K.total[WL_DT] > 0 ? 1 : 0) + 3 * per_stage;
     }
   }
