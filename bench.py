@@ -72,16 +72,16 @@ HBM_PEAK_GBS, HBM_PEAK_KIND = measured_hbm_gbs()
 BYTES_PER_CELL_STAGE_3D = 186.7
 # DRAM bytes (read + write) per interface of the 3D viscous interface kernel, from one ncu
 # capture of a launch of the current kernels (dram__bytes_read.sum + dram__bytes_write.sum):
-# FP64, 385.4 MB for the 893,952 interfaces of a 96^3 y-sweep; FP32 (mixed path), 327.9 MB for
+# FP64, 385.2 MB for the 893,952 interfaces of a 96^3 y-sweep; FP32 (mixed path), 327.9 MB for
 # the 2,113,536 of a 128^3 z-sweep.  Traffic grows in proportion to the interfaces of a launch.
-FACE_DRAM_BYTES_PER_INTERFACE = 385.36e6 / 893952
+FACE_DRAM_BYTES_PER_INTERFACE = 385.20e6 / 893952
 FACE_DRAM_BYTES_PER_INTERFACE_F32 = 327.90e6 / 2113536
 # FP64 operations (DFMA + DMUL + DADD thread-instructions) the FP64 interface kernel executes per
 # interface, from the same capture (smsp__sass_thread_inst_executed_op_{dfma,dmul,dadd}_pred_on:
-# 204.9 + 93.6 + 58.8): below the algorithmic flop count because the mesh-only interface geometry
+# 200.9 + 93.6 + 58.8): below the algorithmic flop count because the mesh-only interface geometry
 # is stored once per mesh and the algebra is restructured.  Each occupies one FP64 pipe slot, so
 # the pipe's rate is half the measured FMA peak in flop/s.
-FACE_FP64_OPS_PER_INTERFACE = 357.3
+FACE_FP64_OPS_PER_INTERFACE = 353.3
 
 
 def load_flops():
