@@ -257,7 +257,7 @@ __global__ void k_grad1(RhsArgsT<R> A, Box b0, Box b1, Box b2) {
 // plane suffices.  Every value is read from global memory about once per plane (the ring and the
 // chunk ends aside) instead of once per stencil point, and the three derivatives are stored with
 // consecutive threads on consecutive x.  Outputs and arithmetic are those of body_grad1 on the
-// three first-derivative boxes (each cell of a box gets exactly its stencil_E6 value).  The
+// three first-derivative boxes (each cell of a box gets exactly its stencil_E6x60 value).  The
 // per-cell kernel was issue-bound on index arithmetic (53 instructions per derivative, 62 % of
 // the issue slots busy); running pointers and one ring load per thread and plane take the 128^3
 // mixed step from 1.929 to 1.874 ms.
@@ -389,9 +389,9 @@ __global__ void __launch_bounds__(kG1TX * kG1TY) k_grad1t(RhsArgsT<R> A, Box U, 
 #pragma unroll
     for (int q = 0; q < FPB; ++q) {
       const R* pl = plane[buf][q];
-      if (zx) A.g1[0][fo[q] + p] = stencil_E6(pl + e, 0, 1);
-      if (zy) A.g1[1][fo[q] + p] = stencil_E6(pl + e, 0, kG1SX);
-      if (zz) A.g1[2][fo[q] + p] = stencil_E6(w[q], 3, 1);
+      if (zx) A.g1[0][fo[q] + p] = stencil_E6x60(pl + e, 0, 1);
+      if (zy) A.g1[1][fo[q] + p] = stencil_E6x60(pl + e, 0, kG1SX);
+      if (zz) A.g1[2][fo[q] + p] = stencil_E6x60(w[q], 3, 1);
 #pragma unroll
       for (int k = 0; k < 6; ++k) w[q][k] = w[q][k + 1];
 #pragma unroll
@@ -1324,7 +1324,8 @@ RhsArgsT<R> rhs_args_r(gbr_ctx* c, const double* q) {
   RhsArgsT<R> A;
   A.L = c->L;
   A.ph = c->ph;
-  A.pr = phys_r<R>(c->ph);
+  // the first derivatives carry kE6Scale with E6 (stencil_E6x60), 1 with IG4 (the line solves)
+  A.pr = phys_r<R>(c->ph, c->p.gradient_scheme == GBR_GRAD_MIG4 ? 1.0 : kE6Scale);
   A.q = q;
   A.prim = static_cast<R*>(c->prim);
   A.temp = static_cast<R*>(c->temp);

@@ -660,11 +660,17 @@ struct PhysR {
   R alpha_d;                 // alpha^D
   R mp_alpha, mp_beta, mp_eps;
   R kfac;
-  R hmu_ref, tmu_ref, hmk_ref;  // mu_ref / 2, -mu_ref / 3, mu_ref kfac / 2 (constant viscosity)
+  // The first derivatives are stored as K f' (K = kE6Scale with E6 gradients, 1 with IG4), and
+  // the constants that multiply them carry 1/K: gh = 1/(2K) (f'/2 of the unlimited states and of
+  // the alpha-damping states), sd = 1/(24 K) (the f' part of f''/12), alpha_k = K alpha^D (the
+  // damped interface gradients are kept in units of K f'), hk = 1/(2K) and tk = -1/(3K) (mu/2
+  // and lambda/2 per unit of mu on those gradients)
+  R gh, sd, alpha_k, hk, tk;
+  R hmu_ref, tmu_ref, hmk_ref;  // hk mu_ref, tk mu_ref, hk mu_ref kfac (constant viscosity)
   int sutherland;
 };
 template <class R>
-inline PhysR<R> phys_r(const Phys& ph) {
+inline PhysR<R> phys_r(const Phys& ph, double K) {
   PhysR<R> r;
   r.gamma = R(ph.gamma);
   r.gm1 = R(ph.gm1);
@@ -677,8 +683,13 @@ inline PhysR<R> phys_r(const Phys& ph) {
   r.mp_beta = R(ph.mp_beta);
   r.mp_eps = R(ph.mp_eps);
   r.kfac = R(ph.kfac);
-  r.hmu_ref = R(0.5) * r.mu_ref;  // the products face_flux forms from mu, in the path's type
-  r.tmu_ref = R(-1.0 / 3.0) * r.mu_ref;
+  r.gh = R(0.5 / K);
+  r.sd = R(1.0 / (24.0 * K));
+  r.alpha_k = R(ph.alpha_d * K);
+  r.hk = R(0.5 / K);
+  r.tk = R(-1.0 / (3.0 * K));
+  r.hmu_ref = r.hk * r.mu_ref;  // the products face_flux forms from mu, in the path's type
+  r.tmu_ref = r.tk * r.mu_ref;
   r.hmk_ref = r.hmu_ref * r.kfac;
   r.sutherland = ph.sutherland;
   return r;
@@ -742,12 +753,13 @@ GBR_HD float gsqrt(float x) {
 GBR_HD double gsqrt(double x) { return sqrt(x); }
 
 // E6 first derivative (Eq. E6_grads, read with differences)
+// Sixty times the E6 first derivative: 45 d1 - 9 d2 + d3 with d_m = f_{i+m} - f_{i-m}, five
+// operations against six for 3/4 d1 - 3/20 d2 + 1/60 d3; the stored first derivatives carry this
+// factor (kE6Scale) and their users fold 1/60 into constants they multiply by anyway (PhysR)
+constexpr double kE6Scale = 60.0;
 template <class R>
-GBR_HD R stencil_E6(const R* f, long long e, long long s) {
-  R r = R(3.0 / 4.0) * (f[e + s] - f[e - s]);
-  r = gfma(R(-3.0 / 20.0), f[e + 2 * s] - f[e - 2 * s], r);
-  r = gfma(R(1.0 / 60.0), f[e + 3 * s] - f[e - 3 * s], r);
-  return r;
+GBR_HD R stencil_E6x60(const R* f, long long e, long long s) {
+  return gfma(R(45), f[e + s] - f[e - s], gfma(R(-9), f[e + 2 * s] - f[e - 2 * s], f[e + 3 * s] - f[e - 3 * s]));
 }
 
 // Sec. 2: primitives P = [rho, u.., p] (and T = p/rho, R = 1) of state cell c stored at padded
@@ -936,8 +948,8 @@ GBR_HD void body_grad1(const RhsArgsT<R>& A, int e, int i, int j, int k) {
   constexpr int NV = ND + 2;
   const Layout& L = A.L;
   const long long PC = L.pcount, p = pidx(L, i, j, k), s = L.ps[e];
-  for (int c = 0; c < NV; ++c) A.g1[e][c * PC + p] = stencil_E6(A.prim + c * PC, p, s);
-  if (A.viscous) A.g1[e][NV * PC + p] = stencil_E6(A.temp, p, s);
+  for (int c = 0; c < NV; ++c) A.g1[e][c * PC + p] = stencil_E6x60(A.prim + c * PC, p, s);
+  if (A.viscous) A.g1[e][NV * PC + p] = stencil_E6x60(A.temp, p, s);
 }
 
 // Sec. 5.1 step 1: f''_i = 2 (f_{i+1} - 2 f_i + f_{i-1}) - 0.5 (f'_{i+1} - f'_{i-1}), kept as
@@ -954,16 +966,17 @@ constexpr bool kFaceFormsG2 = sizeof(R) == sizeof(float);
 template <class R>
 constexpr bool kFaceGeo = sizeof(R) == sizeof(double);
 
+// f1 holds K f' (PhysR): sd = 1/(24 K)
 template <class R, class I>
-GBR_HD R second_deriv_12(const R* f, const R* f1, I p, I s) {
+GBR_HD R second_deriv_12(const R* f, const R* f1, I p, I s, R sd) {
   if constexpr (sizeof(R) == sizeof(double)) {
     // FP64 (pipe-bound pass): five operations, (f_{i+1} - 2 f_i + f_{i-1}) / 6 as one fused
     // multiply-add on -(f'_{i+1} - f'_{i-1}) / 24
     const R c2 = gfma(R(-2), f[p], f[p + s]) + f[p - s];
-    return gfma(R(1.0 / 6.0), c2, R(-1.0 / 24.0) * (f1[p + s] - f1[p - s]));
+    return gfma(R(1.0 / 6.0), c2, -sd * (f1[p + s] - f1[p - s]));
   } else {
     // FP32 (inside the interface kernel, where the form above measured 1.3 % slower)
-    return R(1.0 / 6.0) * (f[p + s] - R(2) * f[p] + f[p - s]) - R(1.0 / 24.0) * (f1[p + s] - f1[p - s]);
+    return R(1.0 / 6.0) * (f[p + s] - R(2) * f[p] + f[p - s]) - sd * (f1[p + s] - f1[p - s]);
   }
 }
 
@@ -975,7 +988,7 @@ GBR_HD void body_grad2(const RhsArgsT<R>& A, int e, int i, int j, int k) {
   for (int c = 0; c < NV; ++c) {
     const R* f = A.prim + c * PC;
     const R* f1 = A.g1[e] + c * PC;
-    A.g2[e][c * PC + p] = second_deriv_12(f, f1, p, s);
+    A.g2[e][c * PC + p] = second_deriv_12(f, f1, p, s, A.pr.sd);
   }
 }
 
@@ -1171,13 +1184,13 @@ GBR_HD void body_grad12(const RhsArgsT<R>& A, int e, const Box& b2, int i, int j
                       k < b2.hi[2];
   for (int c = 0; c < NV; ++c) {
     const R* f = A.prim + c * PC;
-    A.g1[e][c * PC + p] = stencil_E6(f, p, s);
+    A.g1[e][c * PC + p] = stencil_E6x60(f, p, s);
     if (second) {
-      const R f1p = stencil_E6(f, p + s, s), f1m = stencil_E6(f, p - s, s);
-      A.g2[e][c * PC + p] = gfma(R(1.0 / 6.0), gfma(R(-2), f[p], f[p + s]) + f[p - s], R(-1.0 / 24.0) * (f1p - f1m));  // as second_deriv_12
+      const R f1p = stencil_E6x60(f, p + s, s), f1m = stencil_E6x60(f, p - s, s);
+      A.g2[e][c * PC + p] = gfma(R(1.0 / 6.0), gfma(R(-2), f[p], f[p + s]) + f[p - s], -A.pr.sd * (f1p - f1m));  // as second_deriv_12
     }
   }
-  if (A.viscous) A.g1[e][NV * PC + p] = stencil_E6(A.temp, p, s);
+  if (A.viscous) A.g1[e][NV * PC + p] = stencil_E6x60(A.temp, p, s);
 }
 
 // App. A projection x -> R^{-1} x for the face eigenvectors (unit normal nu,
@@ -1434,8 +1447,8 @@ GBR_HD void face_unlimited(const RhsArgsT<R>& A, int d_in, int i, int j, int k, 
     for (int c = 0; c < NV; ++c) {
       const R* f = P + c * PC;
       const R* f1 = A.g1[d] + c * PC;
-      xl[c] = gfma(R(0.5), f1[pp[1]], second_deriv_12(f, f1, pp[1], s));
-      xr[c] = gfma(R(-0.5), f1[pp[2]], second_deriv_12(f, f1, pp[2], s));
+      xl[c] = gfma(ph.gh, f1[pp[1]], second_deriv_12(f, f1, pp[1], s, ph.sd));
+      xr[c] = gfma(-ph.gh, f1[pp[2]], second_deriv_12(f, f1, pp[2], s, ph.sd));
     }
     project<ND>(C.nu, C.ra, C.a2, xl, C.dL);
     project<ND>(C.nu, C.ra, C.a2, xr, C.dR);
@@ -1443,11 +1456,11 @@ GBR_HD void face_unlimited(const RhsArgsT<R>& A, int d_in, int i, int j, int k, 
     R x[NV];
     #pragma unroll
     for (int c = 0; c < NV; ++c)
-      x[c] = gfma(R(0.5), A.g1[d][c * PC + pp[1]], A.g2[d][c * PC + pp[1]]);
+      x[c] = gfma(ph.gh, A.g1[d][c * PC + pp[1]], A.g2[d][c * PC + pp[1]]);
     project<ND>(C.nu, C.ra, C.a2, x, C.dL);
     #pragma unroll
     for (int c = 0; c < NV; ++c)
-      x[c] = gfma(R(-0.5), A.g1[d][c * PC + pp[2]], A.g2[d][c * PC + pp[2]]);
+      x[c] = gfma(-ph.gh, A.g1[d][c * PC + pp[2]], A.g2[d][c * PC + pp[2]]);
     project<ND>(C.nu, C.ra, C.a2, x, C.dR);
   }
   // App. E test per field and side
@@ -1480,7 +1493,7 @@ GBR_HD void face_bounds(const RhsArgsT<R>& A, int d_in, const R* nu, R ra, R a2,
     #pragma unroll
     for (int c = 0; c < NV; ++c) {
       if constexpr (kFaceFormsG2<R>)
-        x[c] = second_deriv_12(A.prim + c * PC, A.g1[d] + c * PC, pp[m], s);
+        x[c] = second_deriv_12(A.prim + c * PC, A.g1[d] + c * PC, pp[m], s, A.pr.sd);
       else
         x[c] = A.g2[d][c * PC + pp[m]];
     }
@@ -1531,9 +1544,10 @@ GBR_HD void face_flux(const RhsArgsT<R>& A, int d_in, int i, int j, int k, const
   hllc<ND, MOV>(PL, PR, nh, nn2, nn, inn2, nt, ph, A.pref_r, F);
 
   if (VISC) {
-    // Sec. 5.2 alpha-damping on [u.., T].  gc2[v][e] = 2 d(phi_v)/d(xi_e) at the interface:
-    // Eq. (AD-eqn1) along the sweep, the sum of the two cells' gradients across it (reading
-    // the paper is silent on them); the factor 1/2 is folded into mu, lambda and kappa below.
+    // Sec. 5.2 alpha-damping on [u.., T].  gc2[v][e] = 2 K d(phi_v)/d(xi_e) at the interface (the
+    // stored derivatives carry K, PhysR): Eq. (AD-eqn1) along the sweep, the sum of the two cells'
+    // gradients across it (reading: the paper is silent on them); the factor 1/(2K) is folded
+    // into mu, lambda and kappa below (hk, tk).
     R gc2[ND + 1][ND];
     R phs[ND + 1];  // phi^L + phi^R = 2 x the interface value of [u.., T]
     #pragma unroll
@@ -1541,12 +1555,12 @@ GBR_HD void face_flux(const RhsArgsT<R>& A, int d_in, int i, int j, int k, const
       const R* val = (v < ND) ? P + (1 + v) * PC : A.temp;
       const int gi = (v < ND) ? (1 + v) : NV;
       const R gd1 = A.g1[d][gi * PC + pp[1]], gd2 = A.g1[d][gi * PC + pp[2]];
-      const R phiL = gfma(R(0.5), gd1, val[pp[1]]);   // Eq. (AD-eqn2), beta^D = 0
-      const R phiR = gfma(R(-0.5), gd2, val[pp[2]]);
+      const R phiL = gfma(ph.gh, gd1, val[pp[1]]);   // Eq. (AD-eqn2), beta^D = 0 (gd: K f')
+      const R phiR = gfma(-ph.gh, gd2, val[pp[2]]);
       #pragma unroll
       for (int e = 0; e < ND; ++e) {
         if (e == d) {
-          gc2[v][e] = gfma(ph.alpha_d, phiR - phiL, gd1 + gd2);  // 2 x Eq. (AD-eqn1)
+          gc2[v][e] = gfma(ph.alpha_k, phiR - phiL, gd1 + gd2);  // 2 K x Eq. (AD-eqn1)
         } else {
           gc2[v][e] = A.g1[e][gi * PC + pp[1]] + A.g1[e][gi * PC + pp[2]];
         }
@@ -1583,8 +1597,8 @@ GBR_HD void face_flux(const RhsArgsT<R>& A, int d_in, int i, int j, int k, const
     if (ph.sutherland) {
       const R th = R(0.5) * phs[ND] * ph.it_ref;
       const R mu = ph.mu_ref * (th * gsqrt(th)) * ((R(1) + ph.suth_s) / (th + ph.suth_s));
-      hmu = R(0.5) * mu;
-      tmu = R(-1.0 / 3.0) * mu;
+      hmu = ph.hk * mu;
+      tmu = ph.tk * mu;
       hmk = hmu * ph.kfac;
     }
     R div2 = R(0);
