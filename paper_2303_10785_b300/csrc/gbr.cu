@@ -41,9 +41,32 @@ namespace {
 #ifndef GBR_FACE_MIN_BLOCKS_F32
 #define GBR_FACE_MIN_BLOCKS_F32 7
 #endif
+// The 3D x-sweep: its own block shape (the same by default; 256 threads x 2 blocks per SM measured
+// slower in both precisions), and its warps' interfaces.  Along x an extremum of the flow is a point,
+// so 32 consecutive x-interfaces hold a few interfaces that fail the App. E test, and every warp
+// pays for queueing them; with GBR_FACE_XT_WX = WX > 0 a warp holds WX consecutive x-interfaces of
+// 32 / WX consecutive y-lines instead, so that failing interfaces fill whole warps as they do in the
+// y- and z-sweeps, at the price of strided loads (each lane its own y-line).  FP64 (pipe-bound,
+// loads far from the bound): WX = 1, 128^3 TGV step 16.64 -> 16.38 ms (WX = 2: 16.41, 4: 16.62).
+// FP32 (issue- and latency-bound): the linear mapping (WX = 8 / 16 / 32: 1.83 / 1.88 / 1.99 ms
+// per step against 1.80).
+#ifndef GBR_FACE_BLOCK_X
+#define GBR_FACE_BLOCK_X GBR_FACE_BLOCK
+#endif
+#ifndef GBR_FACE_MIN_BLOCKS_X
+#define GBR_FACE_MIN_BLOCKS_X GBR_FACE_MIN_BLOCKS
+#endif
+#ifndef GBR_FACE_MIN_BLOCKS_F32_X
+#define GBR_FACE_MIN_BLOCKS_F32_X GBR_FACE_MIN_BLOCKS_F32
+#endif
+#ifndef GBR_FACE_XT_WX
+#define GBR_FACE_XT_WX 1
+#endif
+#ifndef GBR_FACE_XT_WX_F32
+#define GBR_FACE_XT_WX_F32 0
+#endif
 
 constexpr int kBlock = 256;
-constexpr int kFaceBlock = GBR_FACE_BLOCK;
 
 enum { S_DT = 0, S_T = 1, S_DTMIN = 2, S_NSCAL = 8 };
 
@@ -690,15 +713,55 @@ __device__ __forceinline__ void face_block(const RhsArgsT<R>& A, int d, bool val
 
 // Bound work compacted over the block in both precisions (FP64: FP64-pipe bound, -7 % on the
 // 128^3 TGV; FP32, where the bounds form the four cells' f'': -5 % against one interface per thread)
+template <int DD>
+__host__ __device__ constexpr int face_bs() { return DD == 0 ? GBR_FACE_BLOCK_X : GBR_FACE_BLOCK; }
+template <class R, int DD>
+__host__ __device__ constexpr int face_mb() {
+  return sizeof(R) == 4 ? (DD == 0 ? GBR_FACE_MIN_BLOCKS_F32_X : GBR_FACE_MIN_BLOCKS_F32)
+                        : (DD == 0 ? GBR_FACE_MIN_BLOCKS_X : GBR_FACE_MIN_BLOCKS);
+}
+template <class R, int ND, int DD>
+__host__ __device__ constexpr int face_xt() {
+  return (ND == 3 && DD == 0) ? (sizeof(R) == 4 ? GBR_FACE_XT_WX_F32 : GBR_FACE_XT_WX) : 0;
+}
+
+// The transposed x-sweep mapping (WX > 0, blocks of BS threads): a warp holds WX consecutive
+// x-interfaces of 32 / WX consecutive x-lines, the lines (j, k) numbered j fastest so that only the
+// box's last line group is ragged.  Blocks of a box, and the interface of thread `tid` of block `blk`
+// (false past the box).  int: the lines of a face box are below its interfaces, which the 32-bit
+// offset check keeps below 2^32 / 9.
+__host__ __device__ inline long long face_xt_blocks(const Box& b, int bs, int wx) {
+  const int BX = wx * (bs / 32), BY = 32 / wx;
+  const long long nx = b.hi[0] - b.lo[0], nl = (long long)(b.hi[1] - b.lo[1]) * (b.hi[2] - b.lo[2]);
+  return ((nx + BX - 1) / BX) * ((nl + BY - 1) / BY);
+}
+template <int BS, int WX>
+__device__ __forceinline__ bool face_xt_coord(const Box& b, int blk, int tid, int& i, int& j, int& k) {
+  constexpr int BX = WX * (BS / 32), BY = 32 / WX;
+  const int nx = b.hi[0] - b.lo[0], ny = b.hi[1] - b.lo[1], nl = ny * (b.hi[2] - b.lo[2]);
+  const int gx = (nx + BX - 1) / BX, lane = tid % 32;
+  const int line = (blk / gx) * BY + lane / WX;
+  i = b.lo[0] + (blk % gx) * BX + (tid / 32) * WX + lane % WX;
+  j = b.lo[1] + line % ny;
+  k = b.lo[2] + line / ny;
+  return i < b.hi[0] && line < nl;
+}
+
 template <int ND, bool VISC, bool MOV, class R = double, int DD = -1>
-__global__ void __launch_bounds__(GBR_FACE_BLOCK, sizeof(R) == 4 ? GBR_FACE_MIN_BLOCKS_F32 : GBR_FACE_MIN_BLOCKS)
+__global__ void __launch_bounds__(face_bs<DD>(), face_mb<R, DD>())
     k_face(RhsArgsT<R> A, int d, Box b) {
-  __shared__ BoundSlot<ND, R> slots[GBR_FACE_BLOCK];
+  constexpr int BS = face_bs<DD>();
+  __shared__ BoundSlot<ND, R> slots[BS];
   __shared__ int count;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = t < box_size(b);
+  bool valid;
   int i = 0, j = 0, k = 0;
-  if (valid) box_coord(b, t, i, j, k);
+  if constexpr (face_xt<R, ND, DD>() > 0) {
+    valid = face_xt_coord<BS, face_xt<R, ND, DD>()>(b, (int)blockIdx.x, (int)threadIdx.x, i, j, k);
+  } else {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    valid = t < box_size(b);
+    if (valid) box_coord(b, t, i, j, k);
+  }
   face_block<ND, VISC, MOV, R, DD>(A, d, valid, i, j, k, slots, &count);
 }
 
@@ -936,6 +999,18 @@ Box pad_box(const Layout& L, int lo_pad, int hi_pad) {
 unsigned grid_of(const Box& b, int block) {
   long long n = box_size(b);
   return (unsigned)((n + block - 1) / block);
+}
+
+// blocks of one interface launch: one per block-size run of the box, or with the transposed
+// x-sweep mapping one per (group of WX BS/32 x-interfaces, group of 32/WX x-lines)
+template <class R, int ND, int DD>
+unsigned face_grid(const Box& b) {
+  constexpr int BS = face_bs<DD>();
+  if constexpr (face_xt<R, ND, DD>() > 0) {
+    return (unsigned)face_xt_blocks(b, BS, face_xt<R, ND, DD>());
+  } else {
+    return grid_of(b, BS);
+  }
 }
 
 }  // namespace
@@ -1367,7 +1442,6 @@ gbr_status prof_event(gbr_ctx* c) {
 
 template <int ND, class R>
 gbr_status launch_face(gbr_ctx* c, const RhsArgsT<R>& A, int d, const Box& b) {
-  const unsigned g = grid_of(b, kFaceBlock);
   cudaStream_t st = c->stream;
   if (c->prof) {
     gbr_status s0 = prof_event(c);
@@ -1375,13 +1449,14 @@ gbr_status launch_face(gbr_ctx* c, const RhsArgsT<R>& A, int d, const Box& b) {
   }
   // one instantiation per sweep direction (d fixed at compile time)
   auto launch = [&](auto dd) {
-    constexpr int D = decltype(dd)::value;
+    constexpr int D = decltype(dd)::value, BS = face_bs<D>();
+    const unsigned g = face_grid<R, ND, D>(b);
     if (c->visc) {
-      if (c->mov) k_face<ND, true, true, R, D><<<g, kFaceBlock, 0, st>>>(A, d, b);
-      else k_face<ND, true, false, R, D><<<g, kFaceBlock, 0, st>>>(A, d, b);
+      if (c->mov) k_face<ND, true, true, R, D><<<g, BS, 0, st>>>(A, d, b);
+      else k_face<ND, true, false, R, D><<<g, BS, 0, st>>>(A, d, b);
     } else {
-      if (c->mov) k_face<ND, false, true, R, D><<<g, kFaceBlock, 0, st>>>(A, d, b);
-      else k_face<ND, false, false, R, D><<<g, kFaceBlock, 0, st>>>(A, d, b);
+      if (c->mov) k_face<ND, false, true, R, D><<<g, BS, 0, st>>>(A, d, b);
+      else k_face<ND, false, false, R, D><<<g, BS, 0, st>>>(A, d, b);
     }
   };
   if (d == 0) launch(std::integral_constant<int, 0>{});
@@ -2453,10 +2528,10 @@ __global__ void k_extend_nodes(ExtendArgs X, Box b) {
 
 template <int ND, bool VISC, bool MOV>
 void static_face_launches(const RhsArgs& A, const RhsBoxes& B, cudaStream_t st) {
-  k_face<ND, VISC, MOV, double, 0><<<grid_of(B.faces[0], kFaceBlock), kFaceBlock, 0, st>>>(A, 0, B.faces[0]);
-  k_face<ND, VISC, MOV, double, 1><<<grid_of(B.faces[1], kFaceBlock), kFaceBlock, 0, st>>>(A, 1, B.faces[1]);
+  k_face<ND, VISC, MOV, double, 0><<<face_grid<double, ND, 0>(B.faces[0]), face_bs<0>(), 0, st>>>(A, 0, B.faces[0]);
+  k_face<ND, VISC, MOV, double, 1><<<face_grid<double, ND, 1>(B.faces[1]), face_bs<1>(), 0, st>>>(A, 1, B.faces[1]);
   if constexpr (ND == 3)
-    k_face<ND, VISC, MOV, double, 2><<<grid_of(B.faces[2], kFaceBlock), kFaceBlock, 0, st>>>(A, 2, B.faces[2]);
+    k_face<ND, VISC, MOV, double, 2><<<face_grid<double, ND, 2>(B.faces[2]), face_bs<2>(), 0, st>>>(A, 2, B.faces[2]);
 }
 
 // the launch sequence of one right-hand side (geometry first), errors as cudaError_t only

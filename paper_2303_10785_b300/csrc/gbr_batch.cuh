@@ -125,19 +125,31 @@ __global__ void __launch_bounds__(kBlock) kb_grad12(const BatchJob<R>* jobs, con
 // 72 registers, some spilled, measured faster than 768 or 640 threads without spills on a batch
 // of 48^3-64^3 mixed TGV jobs) and 768 in 2D (5 % faster than 896 on 96^2-160^2 vortex jobs),
 // FP64 at 384 threads (at most 168 registers: 4 % faster than the unconstrained 234 on a batch
-// of 64^3 TGV and 256^2 vortex jobs).
+// of 64^3 TGV and 256^2 vortex jobs; 512 threads, 128 registers with ~200 B of spills: -0.4 % on
+// 48^3-64^3 TGV jobs, +3.3 % on 96^3).  The FP64 3D x-sweep takes k_face's transposed mapping
+// (-1.0 / -1.2 % per step on those batches).
 // DD: the one sweep direction of the launch's items (the per-direction instantiation, as k_face)
+#ifndef GBR_BATCH_FACE_FP64_THREADS
+#define GBR_BATCH_FACE_FP64_THREADS 384
+#endif
 template <int ND, bool VISC, bool MOV, class R, int BS, int DD>
-__global__ void __launch_bounds__(BS, sizeof(R) == 4 ? (ND == 3 ? 896 : 768) / BS : (BS < 384 ? 384 / BS : 1))
+__global__ void __launch_bounds__(BS, sizeof(R) == 4 ? (ND == 3 ? 896 : 768) / BS
+                                                     : (BS < GBR_BATCH_FACE_FP64_THREADS ? GBR_BATCH_FACE_FP64_THREADS / BS : 1))
     kb_face(const BatchJob<R>* jobs, const WorkItem* items, int n, int total, int base) {
   __shared__ BoundSlot<ND, R> slots[BS];
   __shared__ int count;
   for_work(items, n, total, [&](const WorkItem& it, int lb) {
     const BatchJob<R>& J = jobs[it.job];
-    const long long t = (long long)lb * blockDim.x + threadIdx.x;
-    const bool valid = t < box_size(J.faces[DD]);
+    bool valid;
     int i = 0, j = 0, k = 0;
-    if (valid) box_coord(J.faces[DD], t, i, j, k);
+    if constexpr (face_xt<R, ND, DD>() > 0) {
+      // the transposed x-sweep mapping of k_face (its blocks counted so by build_items)
+      valid = face_xt_coord<BS, face_xt<R, ND, DD>()>(J.faces[DD], lb, (int)threadIdx.x, i, j, k);
+    } else {
+      const long long t = (long long)lb * blockDim.x + threadIdx.x;
+      valid = t < box_size(J.faces[DD]);
+      if (valid) box_coord(J.faces[DD], t, i, j, k);
+    }
     face_block<ND, VISC, MOV, R, DD>(J.A, DD, valid, i, j, k, slots, &count);
   }, base);
 }
@@ -454,8 +466,9 @@ BatchJob<R> make_job(gbr_ctx* c, double cfl) {
   return J;
 }
 
-void add_items(std::vector<WorkItem>& v, int& total, int job, int sub, const Box& box, int block) {
-  const int blocks = (int)((box_size(box) + block - 1) / block);
+// xt > 0: the box's blocks under the transposed x-sweep mapping with WX = xt
+void add_items(std::vector<WorkItem>& v, int& total, int job, int sub, const Box& box, int block, int xt = 0) {
+  const int blocks = (int)(xt > 0 ? face_xt_blocks(box, block, xt) : (box_size(box) + block - 1) / block);
   if (blocks <= 0) return;
   v.push_back(WorkItem{job, sub, total, blocks});
   total += blocks;
@@ -483,13 +496,17 @@ void build_items(Kind& K) {
   }
   // interfaces: every member's x-sweep, then the y- and z-sweeps (one launch per direction)
   const int fb = K.tune.fused_stage ? kFusedBlock : K.tune.face_block;
+  // kb_face's 3D x-sweep mapping (the fused stage kernel keeps the linear one)
+  const int xt = (K.tune.fused_stage || K.key.nd != 3) ? 0
+                 : (K.key.prec == GBR_PREC_MIXED ? GBR_FACE_XT_WX_F32 : GBR_FACE_XT_WX);
   K.face_dirs = 0;
   for (int d = 0; d < 3; ++d) {
     K.face_start[d] = (int)K.items[WL_FACE].size();
     K.face_base[d] = K.total[WL_FACE];
     for (size_t m = 0; m < K.members.size(); ++m) {
       const Layout& L = K.members[m]->L;
-      if (d < L.nd) add_items(K.items[WL_FACE], K.total[WL_FACE], (int)m, d, rhs_boxes(L).faces[d], fb);
+      if (d < L.nd)
+        add_items(K.items[WL_FACE], K.total[WL_FACE], (int)m, d, rhs_boxes(L).faces[d], fb, d == 0 ? xt : 0);
     }
     K.face_n[d] = (int)K.items[WL_FACE].size() - K.face_start[d];
     K.face_total[d] = K.total[WL_FACE] - K.face_base[d];
