@@ -426,6 +426,164 @@ __global__ void __launch_bounds__(kG1TX * kG1TY) k_grad1t(RhsArgsT<R> A, Box U, 
   }
 }
 
+// The same derivatives (FP32) with four consecutive x-cells per thread, for layouts whose padded rows
+// are 16-byte aligned: a block of 8 x 16 threads owns a 32 x 16 tile of columns, keeps the seven
+// planes z-3 .. z+3 of its four cells as float4 registers (plus the next GBR_G1V_AHEAD planes in
+// flight), and puts each plane with a ring of one float4 column and three rows around the tile into
+// shared memory.  An x-derivative of four cells then takes two 16-byte shared loads, a y-derivative
+// six, and the stores go out as float4 where the four cells lie in the box.  The arithmetic per cell
+// is stencil_E6x60's, so every output equals k_grad1t's and body_grad1's.  128^3 mixed TGV: 0.066
+// against 0.075 ms per launch (39 M against 62 M warp instructions; 24 warps per SM, latency- and
+// barrier-stalled at 54 % issue, DRAM at 39 %).  Measured and not kept: one plane ahead (89
+// registers, 5 blocks per SM; +0.4 % per step) or three, 8 blocks per SM (64 registers), the z loop
+// unrolled over a register ring (no queue moves; +0.7 %), and the planes brought in by TMA into a
+// ring of nine shared slots with mbarriers (no registers for planes in flight, but 15 shared loads
+// per plane instead of 8: 45 M warp instructions, +0.3 %).
+constexpr int kGVX = 8, kGVY = 16;                // threads along x (four cells each) and y
+constexpr int kGVW = kGVX + 2, kGVR = kGVY + 6;   // float4 columns and rows of a plane tile
+constexpr int kGVHalo = 6 * kGVW + 2 * kGVY;      // 92 ring float4s per plane
+#ifndef GBR_G1V_BLOCKS
+#define GBR_G1V_BLOCKS 24                         // blocks per SM the z-chunks aim at
+#endif
+#ifndef GBR_G1V_AHEAD
+#define GBR_G1V_AHEAD 2                           // planes of loads in flight
+#endif
+#ifndef GBR_G1V_MINB
+#define GBR_G1V_MINB 6                            // launch bound: blocks per SM
+#endif
+
+__device__ __forceinline__ float4 g1v_ld(const float* p, bool ok) {
+  return ok ? *reinterpret_cast<const float4*>(p) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+__device__ __forceinline__ float g1v_c(const float4& v, int m) {
+  return m == 0 ? v.x : m == 1 ? v.y : m == 2 ? v.z : v.w;
+}
+// stencil_E6x60 of the 7 values a[m .. m + 6] of the 10 cells x - 3 .. x + 6 around a thread's four
+// cells x .. x + 3
+__device__ __forceinline__ float g1v_e6(const float* a, int m) { return stencil_E6x60(a + m, 3, 1); }
+
+__global__ void __launch_bounds__(kGVX * kGVY, GBR_G1V_MINB) k_grad1v(RhsArgsT<float> A, Box U, Box bx, Box by, Box bz, int tiles_x,
+                                                      int tiles_y, int zchunk) {
+  constexpr int NV = 5;
+  __shared__ float4 plane[2][kGVR * kGVW];
+  const Layout& L = A.L;
+  const int tid = threadIdx.x, tx = tid % kGVX, ty = tid / kGVX;
+  const int t = blockIdx.x;
+  const int tlx = t % tiles_x, tly = (t / tiles_x) % tiles_y, chunk = t / (tiles_x * tiles_y);
+  // the tile's first cell: x on a 16-byte boundary of the padded row (x + hp a multiple of 4)
+  const int x0 = -L.hp[0] + tlx * 4 * kGVX, y0 = U.lo[1] + tly * kGVY;
+  const int x = x0 + 4 * tx, y = y0 + ty;
+  const int zs = U.lo[2] + chunk * zchunk, ze = min(zs + zchunk, U.hi[2]);
+  const long long PC = L.pcount, sz = L.ps[2];
+  const int f = blockIdx.y;
+  const float* src = (f < NV) ? A.prim + f * PC : A.temp;
+  const long long fo = f * PC;
+  // a float4 of cells xq .. xq + 3 of row y is read where it lies in the padded box (outside it no
+  // output needs it); along z the planes read, zs - 3 .. ze + 2, lie in the padded range
+  auto inside = [&](int xq, int cy) {
+    return xq >= -L.hp[0] && xq + 4 <= L.n[0] + L.hp[0] && cy >= -L.hp[1] && cy < L.n[1] + L.hp[1];
+  };
+  const bool col = inside(x, y);
+  const long long pcol = col ? pidx(L, x, y, 0) : 0;
+  // the ring float4 this thread loads (threads 0 .. 91): its slot and padded offset
+  int h_slot = -1;
+  bool h_ok = false;
+  long long h_p = 0;
+  if (tid < kGVHalo) {
+    int r, c;
+    if (tid < 3 * kGVW) {
+      r = tid / kGVW;
+      c = tid % kGVW;
+    } else if (tid < 3 * kGVW + 2 * kGVY) {
+      const int q = tid - 3 * kGVW;
+      r = 3 + q / 2;
+      c = (q % 2) ? kGVW - 1 : 0;
+    } else {
+      const int q = tid - 3 * kGVW - 2 * kGVY;
+      r = 3 + kGVY + q / kGVW;
+      c = q % kGVW;
+    }
+    h_slot = r * kGVW + c;
+    const int xq = x0 - 4 + 4 * c, cy = y0 - 3 + r;
+    h_ok = inside(xq, cy);
+    h_p = h_ok ? pidx(L, xq, cy, 0) : 0;
+  }
+  const int e = (ty + 3) * kGVW + tx + 1;  // this thread's float4 in the plane tile
+  // the (x, y) tests of this thread's four cells against the three boxes
+  auto inb = [&](const Box& b, int m) { return x + m >= b.lo[0] && x + m < b.hi[0] && y >= b.lo[1] && y < b.hi[1]; };
+  bool in[3][4];
+  #pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    in[0][m] = inb(bx, m);
+    in[1][m] = inb(by, m);
+    in[2][m] = inb(bz, m);
+  }
+  // the planes z - 3 .. z + 3 of the column and, in flight, the next AH; the ring's plane z and the
+  // next AH (a plane is read only up to ze + 2, the ring's only below ze).  (The z loop unrolled over
+  // a register ring, so that no value moves, measured slower.)
+  constexpr int AH = GBR_G1V_AHEAD;
+  float4 w[7 + AH], hv[1 + AH];
+  #pragma unroll
+  for (int kq = 0; kq < 6 + AH; ++kq) w[kq] = g1v_ld(src + pcol + (long long)(zs - 3 + kq) * sz, col && zs - 3 + kq <= ze + 2);
+  #pragma unroll
+  for (int kq = 0; kq < AH; ++kq) hv[kq] = g1v_ld(src + h_p + (long long)(zs + kq) * sz, h_ok && zs + kq < ze);
+  long long p = pcol + (long long)zs * sz;
+  for (int z = zs; z < ze; ++z, p += sz) {
+    const int buf = (z - zs) & 1;
+    // the loads of the plane AH ahead, in flight while this plane is formed
+    w[6 + AH] = g1v_ld(src + p + (3 + AH) * sz, col && z + 3 + AH <= ze + 2);
+    hv[AH] = g1v_ld(src + h_p + (long long)(z + AH) * sz, h_ok && z + AH < ze);
+    plane[buf][e] = w[3];
+    if (h_slot >= 0) plane[buf][h_slot] = hv[0];
+    __syncthreads();
+    const float4* pl = plane[buf];
+    const bool zx = z >= bx.lo[2] && z < bx.hi[2], zy = z >= by.lo[2] && z < by.hi[2], zz = z >= bz.lo[2] && z < bz.hi[2];
+    float4 o[3];
+    {
+      const float4 l = pl[e - 1], r = pl[e + 1];
+      const float a[10] = {l.y, l.z, l.w, w[3].x, w[3].y, w[3].z, w[3].w, r.x, r.y, r.z};
+      o[0] = make_float4(g1v_e6(a, 0), g1v_e6(a, 1), g1v_e6(a, 2), g1v_e6(a, 3));
+    }
+    {
+      const float4 m3 = pl[e - 3 * kGVW], m2 = pl[e - 2 * kGVW], m1 = pl[e - kGVW];
+      const float4 p1 = pl[e + kGVW], p2 = pl[e + 2 * kGVW], p3 = pl[e + 3 * kGVW];
+      float v[4];
+      #pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const float c7[7] = {g1v_c(m3, m), g1v_c(m2, m), g1v_c(m1, m), g1v_c(w[3], m), g1v_c(p1, m), g1v_c(p2, m), g1v_c(p3, m)};
+        v[m] = stencil_E6x60(c7, 3, 1);
+      }
+      o[1] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    {
+      float v[4];
+      #pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const float c7[7] = {g1v_c(w[0], m), g1v_c(w[1], m), g1v_c(w[2], m), g1v_c(w[3], m), g1v_c(w[4], m), g1v_c(w[5], m), g1v_c(w[6], m)};
+        v[m] = stencil_E6x60(c7, 3, 1);
+      }
+      o[2] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    const bool zd[3] = {zx, zy, zz};
+    #pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (!zd[d]) continue;
+      float* out = A.g1[d] + fo + p;
+      if (in[d][0] && in[d][1] && in[d][2] && in[d][3]) {
+        *reinterpret_cast<float4*>(out) = o[d];
+      } else {
+        #pragma unroll
+        for (int m = 0; m < 4; ++m)
+          if (in[d][m]) out[m] = g1v_c(o[d], m);
+      }
+    }
+    #pragma unroll
+    for (int kq = 0; kq < 6 + AH; ++kq) w[kq] = w[kq + 1];
+    #pragma unroll
+    for (int kq = 0; kq < AH; ++kq) hv[kq] = hv[kq + 1];
+  }
+}
+
 // MIG4: one thread per (line, field); blockIdx.y is the field (primitives, then T)
 template <int ND, class R = double>
 __global__ void k_ig4(RhsArgsT<R> A, int e, Box lines, const R* table) {
@@ -1555,14 +1713,27 @@ gbr_status run_rhs_nd(gbr_ctx* c, const double* qs, const double* q0, double* ou
       const int nf = L.nv + (c->visc ? 1 : 0);
       const int tiles_x = (U.hi[0] - U.lo[0] + kG1TX - 1) / kG1TX, tiles_y = (U.hi[1] - U.lo[1] + kG1TY - 1) / kG1TY;
       const int nzu = U.hi[2] - U.lo[2];
-      // chunks of planes: about kG1Waves waves of resident blocks (8 per SM)
-      const int fb = (nf + kG1Fields - 1) / kG1Fields;  // field groups
-      const int pairs = tiles_x * tiles_y * fb;
-      const int chunks = std::max(1, std::min(nzu, (kG1Waves * device_sms() * 8 + pairs - 1) / pairs));
-      const int zchunk = (nzu + chunks - 1) / chunks;
-      const unsigned blocks = (unsigned)(tiles_x * tiles_y * ((nzu + zchunk - 1) / zchunk));
-      k_grad1t<R, kG1Fields><<<dim3(blocks, fb), kG1TX * kG1TY, 0, st>>>(A, U, B.grad1[0], B.grad1[1], B.grad1[2],
-                                                                         tiles_x, tiles_y, zchunk, nf);
+      // four cells per thread where the padded rows and the arrays sit on 16-byte boundaries
+      auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+      const bool vec = L.ps[1] % 4 == 0 && al16(A.prim) && (!c->visc || al16(A.temp)) && al16(A.g1[0]) &&
+                       al16(A.g1[1]) && al16(A.g1[2]);
+      if (vec) {
+        const int vtx = (U.hi[0] + L.hp[0] + 4 * kGVX - 1) / (4 * kGVX), vty = (U.hi[1] - U.lo[1] + kGVY - 1) / kGVY;
+        const int pairs = vtx * vty * nf;
+        const int chunks = std::max(1, std::min(nzu, (GBR_G1V_BLOCKS * device_sms() + pairs - 1) / pairs));
+        const int zchunk = (nzu + chunks - 1) / chunks;
+        const unsigned blocks = (unsigned)(vtx * vty * ((nzu + zchunk - 1) / zchunk));
+        k_grad1v<<<dim3(blocks, nf), kGVX * kGVY, 0, st>>>(A, U, B.grad1[0], B.grad1[1], B.grad1[2], vtx, vty, zchunk);
+      } else {
+        // chunks of planes: about kG1Waves waves of resident blocks (8 per SM)
+        const int fb = (nf + kG1Fields - 1) / kG1Fields;  // field groups
+        const int pairs = tiles_x * tiles_y * fb;
+        const int chunks = std::max(1, std::min(nzu, (kG1Waves * device_sms() * 8 + pairs - 1) / pairs));
+        const int zchunk = (nzu + chunks - 1) / chunks;
+        const unsigned blocks = (unsigned)(tiles_x * tiles_y * ((nzu + zchunk - 1) / zchunk));
+        k_grad1t<R, kG1Fields><<<dim3(blocks, fb), kG1TX * kG1TY, 0, st>>>(A, U, B.grad1[0], B.grad1[1], B.grad1[2],
+                                                                           tiles_x, tiles_y, zchunk, nf);
+      }
     } else {
       k_grad1<ND, R><<<g1 * ND, kBlock, 0, st>>>(A, B.grad1[0], B.grad1[1], B.grad1[2]);
     }
