@@ -82,6 +82,12 @@ FACE_DRAM_BYTES_PER_INTERFACE_F32 = 327.90e6 / 2113536
 # is stored once per mesh and the algebra is restructured.  Each occupies one FP64 pipe slot, so
 # the pipe's rate is half the measured FMA peak in flop/s.
 FACE_FP64_OPS_PER_INTERFACE = 353.3
+# Warp instructions the FP32 interface kernel issues per interface, from the 128^3 z-sweep capture
+# (smsp__inst_executed.sum 89.5 M for 2,113,536 interfaces; the x-sweep issues ~5 % more).  The
+# kernel is bound by instruction issue rather than HBM: each SM sub-partition issues one warp
+# instruction per clock, 4 per SM.
+FACE_F32_WARP_INSTR_PER_INTERFACE = 89.5e6 / 2113536
+ISSUE_PEAK_WARP_INSTR_PER_S = 148 * 4 * SM_MAX_GHZ * 1e9
 
 
 def load_flops():
@@ -490,6 +496,15 @@ def measure(wl, dev, steps, warmup, e2e_steps, peaks, world, local, keep_state=F
         roofline = dict({"bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
                          "frac": achieved / HBM_PEAK_GBS}, **common)
         roofline["peak_note"] = f"HBM copy bandwidth, {HBM_PEAK_KIND} (MEASURED_PEAKS.json)"
+        if mixed:
+            # the instructions the kernel issues against the GPU's issue rate at the maximum clock
+            issue_rate = FACE_F32_WARP_INSTR_PER_INTERFACE * faces_per_launch / avg_launch_s
+            roofline["warp_instr_per_face_executed"] = FACE_F32_WARP_INSTR_PER_INTERFACE
+            roofline["issue_frac"] = issue_rate / ISSUE_PEAK_WARP_INSTR_PER_S
+            roofline["frac_note"] = (
+                "the FP32 interface kernel is bound by instruction issue, not HBM (ncu: ~65 % of the "
+                "issue slots busy, DRAM at ~35 %); issue_frac is its executed warp instructions over "
+                "148 SMs x 4 issues per clock at the maximum SM clock")
     if mixed:
         roofline["traffic"] = FACE_DRAM_BYTES_PER_INTERFACE_F32 * faces_per_launch
         roofline["traffic_note"] = "bytes per launch, scaled from a 128^3 ncu capture by interfaces"
