@@ -86,6 +86,23 @@ def test_mixed_rhs_error_does_not_grow_at_low_mach(mach):
     s.close()
 
 
+@pytest.mark.parametrize("n", [(20, 18, 16), (21, 18, 16), (22, 17, 15)])
+def test_mixed_rhs_both_first_derivative_forms(n):
+    # the FP32 first derivatives take four x-cells per thread where the padded rows (n_x + 12
+    # cells) are 16-byte aligned, and one cell per thread elsewhere: both against the oracle
+    case = I.case_params(3, n, reynolds=1600.0)
+    nodes = I.nodes_random(n, (2 * np.pi,) * 3, frac=0.15)
+    xc = I.centroids(nodes, n, (1, 1, 1))
+    q = I.prim_to_cons(I.tgv_prim(*xc, mach=0.1), GAMMA)
+    orc, s = pair(case, nodes, None)
+    s.set_state(q)
+    Lg = s.rhs().cpu().numpy()
+    scale = cancellation_scale(orc, q)
+    err = (np.abs(Lg - orc.rhs(q)).reshape(5, -1).max(axis=1) / scale).max()
+    assert err < RHS_TOL, err
+    s.close()
+
+
 def test_mixed_workspace_is_smaller_than_fp64():
     case, nodes, vel, q = CASES["3d_tgv"]()
     s64 = gbr.Solver(case, nodes, vel)
