@@ -12,7 +12,8 @@ seconds to a minute, else through properties that hold at any size.
   unperturbed one: mass, momentum and energy totals conserved to round-off on both (~1e-14), and
   the two kinetic-energy histories agree to the scheme's truncation error (3.5e-10 relative at
   step 200); the mixed path follows the FP64 path within its tolerance.  And the right-hand side
-  of the perturbed case 20 steps in, every cell, against the oracle's (FP64 and mixed).
+  of the perturbed case 20 steps in, every cell, against the oracle's (MEG6 and MIG4, FP64 and
+  mixed).
 """
 import numpy as np
 import pytest
@@ -114,12 +115,15 @@ def test_full_jet_rhs_matches_oracle_on_the_inflow_block(precision):
     assert err < (1e-12 if precision == "fp64" else 2e-6)
 
 
+@pytest.mark.parametrize("scheme", ["meg6", "mig4"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_taylor_green_128_rhs_matches_oracle_after_twenty_steps(precision):
+def test_taylor_green_128_rhs_matches_oracle_after_twenty_steps(precision, scheme):
     # the bench's workload itself: 128^3 on the 0.1 h perturbed mesh, every cell of the
     # right-hand side of a state 20 CFL 0.2 steps in (the limiter active) against the oracle's
     n = 128
     case = I.case_params(3, (n, n, n), reynolds=1600.0)
+    if scheme == "mig4":
+        case = dict(case, gradient_scheme="mig4")
     nodes = I.nodes_tgv_3d(n, 0.1)
     xc = I.centroids(nodes, (n, n, n), (1, 1, 1))
     q = I.prim_to_cons(I.tgv_prim(*xc, mach=0.1), GAMMA)
@@ -133,7 +137,7 @@ def test_taylor_green_128_rhs_matches_oracle_after_twenty_steps(precision):
     orc = O.Oracle(case, nodes)
     Lo = orc.rhs(qs)
     err = (np.abs(Lg - Lo).reshape(5, -1).max(axis=1) / cancellation_scale(orc, qs)).max()
-    print("tgv 128^3", precision, err)
+    print("tgv 128^3", scheme, precision, err)
     assert err < (1e-12 if precision == "fp64" else 2e-6)
 
 
