@@ -7,7 +7,9 @@ seconds to a minute, else through properties that hold at any size.
   (FP64: maximum difference after 100 steps, L1 and maximum after 500).
 * Jet: the 480 x 170 x 170 stretched jet grid with inflow, sponge and Sutherland viscosity; the
   right-hand side of a perturbed state on the GPU against the oracle's right-hand side on the first
-  40 x-cells of the same grid (identical nodes; cells whose stencils do not reach the cut).
+  40 x-cells of the same grid (identical nodes; cells whose stencils do not reach the cut); and 100
+  steps from the quiescent state on the FP64 and the mixed path, the mixed state within its
+  tolerance of the FP64 one.
 * Taylor-Green vortex: 128^3, 200 steps at CFL 0.2 on the 0.1 h perturbed mesh and on the
   unperturbed one: mass, momentum and energy totals conserved to round-off on both (~1e-14), and
   the two kinetic-energy histories agree to the scheme's truncation error (3.5e-10 relative at
@@ -139,6 +141,30 @@ def test_taylor_green_128_rhs_matches_oracle_after_twenty_steps(precision, schem
     err = (np.abs(Lg - Lo).reshape(5, -1).max(axis=1) / cancellation_scale(orc, qs)).max()
     print("tgv 128^3", scheme, precision, err)
     assert err < (1e-12 if precision == "fp64" else 2e-6)
+
+
+def test_full_jet_mixed_follows_fp64_for_a_hundred_steps():
+    # the 13.9 M-cell jet from its quiescent state with the inflow and the sponge, 100 steps at
+    # the bench's fixed time step on the FP64 and on the mixed path: the jet enters, both stay
+    # finite, and the mixed state stays within its tolerance of the FP64 state
+    n, steps, dt = (480, 170, 170), 100, 2e-3
+    case, nodes, q, inflow, sigma, qamb = I.jet_case(n)
+    out = {}
+    for precision in ("fp64", "mixed"):
+        s = gbr.Solver(dict(case, precision=precision), nodes)
+        s.set_inflow(inflow)
+        s.set_sponge(sigma, qamb)
+        s.set_state(q)
+        for _ in range(steps):
+            s.rk_step(-dt)
+        out[precision] = s.get_state()
+        s.close()
+    qd, qm = out["fp64"], out["mixed"]
+    assert np.isfinite(qd).all() and np.isfinite(qm).all()
+    assert np.abs(qd - q).max() > 1e-2  # the jet has entered the box
+    err = rel_state(qm, qd)
+    print("jet mixed vs fp64 after", steps, "steps", err)
+    assert err < 1e-5
 
 
 def _totals(q, det):
