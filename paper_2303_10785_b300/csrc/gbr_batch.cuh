@@ -74,6 +74,37 @@ __device__ __forceinline__ void for_work(const WorkItem* items, int n_items, int
   }
 }
 
+// Runs f(item, local block) for block blockIdx.x + base of a list launched with one CTA per work
+// block (no loop: the interface kernels keep their registers for the interface)
+template <class F>
+__device__ __forceinline__ void one_work(const WorkItem* items, int n_items, F f, int base = 0) {
+  const int blk = (int)blockIdx.x + base;
+  int lo = 0, hi = n_items - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (items[mid].first <= blk) lo = mid;
+    else hi = mid - 1;
+  }
+  f(items[lo], blk - items[lo].first);
+}
+
+// the phase kernels' loop: one work block per CTA (GBR_BATCH_ONE, grid = the list's blocks), or
+// a persistent range of them per CTA.  One per CTA measured faster for every phase (batch steps of
+// twelve 48^3-64^3 TGV jobs / four 96^3, the interface kernels already one per CTA: FP64 18.99 ->
+// 18.49 ms / 28.84 -> 28.10 ms, mixed 2.784 -> 2.544 ms): the block scheduler balances the
+// uneven members' blocks better than fixed ranges, and no loop state takes registers.
+#ifndef GBR_BATCH_ONE
+#define GBR_BATCH_ONE 1
+#endif
+template <class F>
+__device__ __forceinline__ void phase_work(const WorkItem* items, int n_items, int total, F f) {
+  if constexpr (GBR_BATCH_ONE) {
+    if ((int)blockIdx.x < total && n_items > 0) one_work(items, n_items, f);
+  } else {
+    for_work(items, n_items, total, f);
+  }
+}
+
 #define BATCH_CELL(BOX)                                                        \
   const long long _t = (long long)lb * blockDim.x + threadIdx.x;              \
   if (_t >= box_size(BOX)) return;                                             \
@@ -83,7 +114,7 @@ __device__ __forceinline__ void for_work(const WorkItem* items, int n_items, int
 template <int ND, class R>
 __global__ void __launch_bounds__(kBlock, kStreamBlocks) kb_prim_halo(const BatchJob<R>* jobs, const WorkItem* items, int n,
                                                         int total, int stage) {
-  for_work(items, n, total, [&](const WorkItem& it, int lb) {
+  phase_work(items, n, total, [&](const WorkItem& it, int lb) {
     const BatchJob<R>& J = jobs[it.job];
     BATCH_CELL(J.pad);
     body_prim_halo<ND>(J.A, J.q[stage], J.dq[stage], i, j, k);
@@ -92,7 +123,7 @@ __global__ void __launch_bounds__(kBlock, kStreamBlocks) kb_prim_halo(const Batc
 
 template <int ND, class R>
 __global__ void __launch_bounds__(kBlock) kb_grad1(const BatchJob<R>* jobs, const WorkItem* items, int n, int total) {
-  for_work(items, n, total, [&](const WorkItem& it, int lb) {
+  phase_work(items, n, total, [&](const WorkItem& it, int lb) {
     const BatchJob<R>& J = jobs[it.job];
     BATCH_CELL(J.grad1[it.sub]);
     body_grad1<ND>(J.A, it.sub, i, j, k);
@@ -101,7 +132,7 @@ __global__ void __launch_bounds__(kBlock) kb_grad1(const BatchJob<R>* jobs, cons
 
 template <int ND, class R>
 __global__ void __launch_bounds__(kBlock) kb_grad2(const BatchJob<R>* jobs, const WorkItem* items, int n, int total) {
-  for_work(items, n, total, [&](const WorkItem& it, int lb) {
+  phase_work(items, n, total, [&](const WorkItem& it, int lb) {
     const BatchJob<R>& J = jobs[it.job];
     BATCH_CELL(J.grad2[it.sub]);
     body_grad2<ND>(J.A, it.sub, i, j, k);
@@ -113,7 +144,7 @@ __global__ void __launch_bounds__(kBlock) kb_grad2(const BatchJob<R>* jobs, cons
 template <int ND, class R>
 __global__ void __launch_bounds__(kBlock) kb_grad12(const BatchJob<R>* jobs, const WorkItem* items, int n,
                                                      int total) {
-  for_work(items, n, total, [&](const WorkItem& it, int lb) {
+  phase_work(items, n, total, [&](const WorkItem& it, int lb) {
     const BatchJob<R>& J = jobs[it.job];
     BATCH_CELL(J.grad1[it.sub]);
     body_grad12<ND>(J.A, it.sub, J.grad2[it.sub], i, j, k);
@@ -124,13 +155,19 @@ __global__ void __launch_bounds__(kBlock) kb_grad12(const BatchJob<R>* jobs, con
 // each work block's barriers); FP32 at 896 threads per SM in 3D (7 blocks of 128, as k_face:
 // 72 registers, some spilled, measured faster than 768 or 640 threads without spills on a batch
 // of 48^3-64^3 mixed TGV jobs) and 768 in 2D (5 % faster than 896 on 96^2-160^2 vortex jobs),
-// FP64 at 384 threads (at most 168 registers: 4 % faster than the unconstrained 234 on a batch
-// of 64^3 TGV and 256^2 vortex jobs; 512 threads, 128 registers with ~200 B of spills: -0.4 % on
-// 48^3-64^3 TGV jobs, +3.3 % on 96^3).  The FP64 3D x-sweep takes k_face's transposed mapping
-// (-1.0 / -1.2 % per step on those batches).
+// FP64 at 512 threads (4 blocks of 128 at 128 registers, as k_face).  Each CTA runs one work
+// block (GBR_BATCH_FACE_ONE: grid = the direction's blocks, the item found by a binary search)
+// instead of a persistent loop over a range of them: without the loop's state the FP64 kernel
+// fits 128 registers without spills (persistent it took 168, 3 blocks per SM, and spilled at
+// 128), and the FP32 one spills less.  Batch steps (twelve 48^3-64^3 TGV jobs / four 96^3):
+// FP64 20.49 -> 18.98 ms / 30.77 -> 28.84 ms, mixed 3.155 -> 2.788 ms.  The FP64 3D x-sweep takes
+// k_face's transposed mapping (-1.0 / -1.2 % per step on those batches).
 // DD: the one sweep direction of the launch's items (the per-direction instantiation, as k_face)
 #ifndef GBR_BATCH_FACE_FP64_THREADS
-#define GBR_BATCH_FACE_FP64_THREADS 384
+#define GBR_BATCH_FACE_FP64_THREADS 512
+#endif
+#ifndef GBR_BATCH_FACE_ONE
+#define GBR_BATCH_FACE_ONE 1
 #endif
 template <int ND, bool VISC, bool MOV, class R, int BS, int DD>
 __global__ void __launch_bounds__(BS, sizeof(R) == 4 ? (ND == 3 ? 896 : 768) / BS
@@ -138,7 +175,11 @@ __global__ void __launch_bounds__(BS, sizeof(R) == 4 ? (ND == 3 ? 896 : 768) / B
     kb_face(const BatchJob<R>* jobs, const WorkItem* items, int n, int total, int base) {
   __shared__ BoundSlot<ND, R> slots[BS];
   __shared__ int count;
-  for_work(items, n, total, [&](const WorkItem& it, int lb) {
+  auto work = [&](auto&& f) {
+    if constexpr (GBR_BATCH_FACE_ONE) one_work(items, n, f, base);
+    else for_work(items, n, total, f, base);
+  };
+  work([&](const WorkItem& it, int lb) {
     const BatchJob<R>& J = jobs[it.job];
     bool valid;
     int i = 0, j = 0, k = 0;
@@ -151,13 +192,13 @@ __global__ void __launch_bounds__(BS, sizeof(R) == 4 ? (ND == 3 ? 896 : 768) / B
       if (valid) box_coord(J.faces[DD], t, i, j, k);
     }
     face_block<ND, VISC, MOV, R, DD>(J.A, DD, valid, i, j, k, slots, &count);
-  }, base);
+  });
 }
 
 template <int ND, bool MOV, class R, bool SP>
 __global__ void __launch_bounds__(kBlock, kStreamBlocks) kb_update(const BatchJob<R>* jobs, const WorkItem* items, int n, int total,
                                                      int stage) {
-  for_work(items, n, total, [&](const WorkItem& it, int lb) {
+  phase_work(items, n, total, [&](const WorkItem& it, int lb) {
     const BatchJob<R>& J = jobs[it.job];
     BATCH_CELL(J.inner);
     if (body_update<ND, MOV, R, SP>(J.U[stage], i, j, k)) atomicOr(J.err, 1);
@@ -272,7 +313,7 @@ template <int ND, class R>
 __global__ void __launch_bounds__(kBlock) kb_dt(const BatchJob<R>* jobs, const WorkItem* items, int n, int total) {
   // the minimum in the path's type and one conversion per block, as in k_dt
   __shared__ R wmin[kBlock / 32];
-  for_work(items, n, total, [&](const WorkItem& it, int lb) {
+  phase_work(items, n, total, [&](const WorkItem& it, int lb) {
     const BatchJob<R>& J = jobs[it.job];
     const long long t = (long long)lb * blockDim.x + threadIdx.x;
     R v = R(HUGE_VAL);
@@ -527,6 +568,12 @@ unsigned persistent_grid(gbr_batch* b, KernelT kernel, int block, int total) {
   return (unsigned)std::max(1, std::min(total, resident_ctas(b, kernel, block)));
 }
 
+// the grid of a phase kernel (phase_work)
+template <class KernelT>
+unsigned phase_grid(gbr_batch* b, KernelT kernel, int block, int total) {
+  return GBR_BATCH_ONE ? (unsigned)std::max(1, total) : persistent_grid(b, kernel, block, total);
+}
+
 // one launch per sweep direction, each over that direction's range of the interface items
 template <int ND, bool VISC, bool MOV, class R, int BS>
 gbr_status launch_face_kind(gbr_batch* b, const Kind& K, const BatchJob<R>* jobs, long long& launches) {
@@ -534,7 +581,7 @@ gbr_status launch_face_kind(gbr_batch* b, const Kind& K, const BatchJob<R>* jobs
     constexpr int D = decltype(dd)::value;
     if (K.face_n[D] == 0) return GBR_OK;
     auto kern = kb_face<ND, VISC, MOV, R, BS, D>;
-    const unsigned g = persistent_grid(b, kern, BS, K.face_total[D]);
+    const unsigned g = GBR_BATCH_FACE_ONE ? (unsigned)K.face_total[D] : persistent_grid(b, kern, BS, K.face_total[D]);
     kern<<<g, BS, 0, b->cur>>>(jobs, K.d_items[WL_FACE] + K.face_start[D], K.face_n[D], K.face_total[D],
                                K.face_base[D]);
     BK(cudaGetLastError(), "kb_face");
@@ -607,7 +654,7 @@ gbr_status enqueue_rhs(gbr_batch* b, const Kind& K, int stage, long long& launch
   const int qin = stage == 3 ? 0 : stage;
   {
     auto kern = kb_prim_halo<ND, R>;
-    kern<<<persistent_grid(b, kern, kBlock, K.total[WL_PAD]), kBlock, 0, st>>>(
+    kern<<<phase_grid(b, kern, kBlock, K.total[WL_PAD]), kBlock, 0, st>>>(
         jobs, K.d_items[WL_PAD], (int)K.items[WL_PAD].size(), K.total[WL_PAD], qin);
     BK(cudaGetLastError(), "kb_prim_halo");
   }
@@ -622,7 +669,7 @@ gbr_status enqueue_rhs(gbr_batch* b, const Kind& K, int stage, long long& launch
     ++launches;
     if constexpr (!kFaceFormsG2<R>) {
       auto k2 = kb_grad2<ND, R>;
-      k2<<<persistent_grid(b, k2, kBlock, K.total[WL_GRAD2]), kBlock, 0, st>>>(
+      k2<<<phase_grid(b, k2, kBlock, K.total[WL_GRAD2]), kBlock, 0, st>>>(
           jobs, K.d_items[WL_GRAD2], (int)K.items[WL_GRAD2].size(), K.total[WL_GRAD2]);
       BK(cudaGetLastError(), "kb_grad2");
       ++launches;
@@ -630,23 +677,23 @@ gbr_status enqueue_rhs(gbr_batch* b, const Kind& K, int stage, long long& launch
   } else if constexpr (kFaceFormsG2<R>) {
     // FP32: the interface kernel forms f'' itself
     auto k1 = kb_grad1<ND, R>;
-    k1<<<persistent_grid(b, k1, kBlock, K.total[WL_GRAD1]), kBlock, 0, st>>>(
+    k1<<<phase_grid(b, k1, kBlock, K.total[WL_GRAD1]), kBlock, 0, st>>>(
         jobs, K.d_items[WL_GRAD1], (int)K.items[WL_GRAD1].size(), K.total[WL_GRAD1]);
     BK(cudaGetLastError(), "kb_grad1");
     launches += 2;
   } else if (K.tune.fused_grad) {
     auto kern = kb_grad12<ND, R>;
-    kern<<<persistent_grid(b, kern, kBlock, K.total[WL_GRAD1]), kBlock, 0, st>>>(
+    kern<<<phase_grid(b, kern, kBlock, K.total[WL_GRAD1]), kBlock, 0, st>>>(
         jobs, K.d_items[WL_GRAD1], (int)K.items[WL_GRAD1].size(), K.total[WL_GRAD1]);
     BK(cudaGetLastError(), "kb_grad12");
     launches += 2;
   } else {
     auto k1 = kb_grad1<ND, R>;
-    k1<<<persistent_grid(b, k1, kBlock, K.total[WL_GRAD1]), kBlock, 0, st>>>(
+    k1<<<phase_grid(b, k1, kBlock, K.total[WL_GRAD1]), kBlock, 0, st>>>(
         jobs, K.d_items[WL_GRAD1], (int)K.items[WL_GRAD1].size(), K.total[WL_GRAD1]);
     BK(cudaGetLastError(), "kb_grad1");
     auto k2 = kb_grad2<ND, R>;
-    k2<<<persistent_grid(b, k2, kBlock, K.total[WL_GRAD2]), kBlock, 0, st>>>(
+    k2<<<phase_grid(b, k2, kBlock, K.total[WL_GRAD2]), kBlock, 0, st>>>(
         jobs, K.d_items[WL_GRAD2], (int)K.items[WL_GRAD2].size(), K.total[WL_GRAD2]);
     BK(cudaGetLastError(), "kb_grad2");
     launches += 3;
@@ -663,7 +710,7 @@ gbr_status enqueue_rhs(gbr_batch* b, const Kind& K, int stage, long long& launch
     bool sponge = false;
     for (gbr_ctx* m : K.members) sponge |= m->have_sponge;
     auto kern = sponge ? kb_update<ND, MOV, R, true> : kb_update<ND, MOV, R, false>;
-    kern<<<persistent_grid(b, kern, kBlock, K.total[WL_INNER]), kBlock, 0, st>>>(
+    kern<<<phase_grid(b, kern, kBlock, K.total[WL_INNER]), kBlock, 0, st>>>(
         jobs, K.d_items[WL_INNER], (int)K.items[WL_INNER].size(), K.total[WL_INNER], stage);
     BK(cudaGetLastError(), "kb_update");
   }
@@ -685,7 +732,7 @@ gbr_status enqueue_step_kind(gbr_batch* b, const Kind& K, long long& launches) {
   launches += 2;
   if (K.total[WL_DT] > 0) {
     auto kern = kb_dt<ND, R>;
-    kern<<<persistent_grid(b, kern, kBlock, K.total[WL_DT]), kBlock, 0, st>>>(
+    kern<<<phase_grid(b, kern, kBlock, K.total[WL_DT]), kBlock, 0, st>>>(
         jobs, K.d_items[WL_DT], (int)K.items[WL_DT].size(), K.total[WL_DT]);
     BK(cudaGetLastError(), "kb_dt");
     ++launches;
