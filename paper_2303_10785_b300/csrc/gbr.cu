@@ -462,20 +462,23 @@ __device__ __forceinline__ float g1v_c(const float4& v, int m) {
 // cells x .. x + 3
 __device__ __forceinline__ float g1v_e6(const float* a, int m) { return stencil_E6x60(a + m, 3, 1); }
 
-__global__ void __launch_bounds__(kGVX * kGVY, GBR_G1V_MINB) k_grad1v(RhsArgsT<float> A, Box U, Box bx, Box by, Box bz, int tiles_x,
-                                                      int tiles_y, int zchunk) {
+// One block's tile t (tile in x, tile in y, chunk of planes; x fastest) of field f, through the
+// block's double-buffered plane tiles in shared memory.  A block may run several tiles in a row:
+// the barrier on entry lets every thread finish reading the previous tile's last plane before the
+// buffers are written again.
+__device__ __forceinline__ void grad1v_tile(const RhsArgsT<float>& A, const Box& U, const Box& bx, const Box& by,
+                                            const Box& bz, int tiles_x, int tiles_y, int zchunk, int t, int f,
+                                            float4 (*plane)[kGVR * kGVW]) {
   constexpr int NV = 5;
-  __shared__ float4 plane[2][kGVR * kGVW];
+  __syncthreads();
   const Layout& L = A.L;
   const int tid = threadIdx.x, tx = tid % kGVX, ty = tid / kGVX;
-  const int t = blockIdx.x;
   const int tlx = t % tiles_x, tly = (t / tiles_x) % tiles_y, chunk = t / (tiles_x * tiles_y);
   // the tile's first cell: x on a 16-byte boundary of the padded row (x + hp a multiple of 4)
   const int x0 = -L.hp[0] + tlx * 4 * kGVX, y0 = U.lo[1] + tly * kGVY;
   const int x = x0 + 4 * tx, y = y0 + ty;
   const int zs = U.lo[2] + chunk * zchunk, ze = min(zs + zchunk, U.hi[2]);
   const long long PC = L.pcount, sz = L.ps[2];
-  const int f = blockIdx.y;
   const float* src = (f < NV) ? A.prim + f * PC : A.temp;
   const long long fo = f * PC;
   // a float4 of cells xq .. xq + 3 of row y is read where it lies in the padded box (outside it no
@@ -582,6 +585,12 @@ __global__ void __launch_bounds__(kGVX * kGVY, GBR_G1V_MINB) k_grad1v(RhsArgsT<f
     #pragma unroll
     for (int kq = 0; kq < AH; ++kq) hv[kq] = hv[kq + 1];
   }
+}
+
+__global__ void __launch_bounds__(kGVX * kGVY, GBR_G1V_MINB) k_grad1v(RhsArgsT<float> A, Box U, Box bx, Box by, Box bz, int tiles_x,
+                                                      int tiles_y, int zchunk) {
+  __shared__ float4 plane[2][kGVR * kGVW];
+  grad1v_tile(A, U, bx, by, bz, tiles_x, tiles_y, zchunk, (int)blockIdx.x, (int)blockIdx.y, plane);
 }
 
 // MIG4: one thread per (line, field); blockIdx.y is the field (primitives, then T)
@@ -1433,6 +1442,42 @@ RhsBoxes rhs_boxes(const Layout& L) {
   return B;
 }
 
+// k_grad1v's launch shape for a layout: false where its rows or arrays are not 16-byte aligned
+// (k_grad1t is used then).  The union U of the three first-derivative boxes, tiles of 32 x 16
+// columns, chunks of zchunk planes: zchunk = 0 picks them so that the launch has about
+// GBR_G1V_BLOCKS blocks per SM, zchunk < 0 balances chunks of at most -zchunk planes.
+struct G1VPlan {
+  Box U;
+  int tiles_x, tiles_y, zchunk, chunks, nf;
+  long long blocks() const { return (long long)tiles_x * tiles_y * chunks * nf; }
+};
+bool g1v_plan(const Layout& L, const RhsBoxes& B, const void* prim, const void* temp, const void* const g1[3], bool visc,
+              int zchunk, G1VPlan& P) {
+  auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+  if (L.nd != 3 || L.ps[1] % 4 != 0 || !al16(prim) || (visc && !al16(temp)) || !al16(g1[0]) || !al16(g1[1]) ||
+      !al16(g1[2]))
+    return false;
+  for (int d = 0; d < 3; ++d) {
+    P.U.lo[d] = std::min(B.grad1[0].lo[d], std::min(B.grad1[1].lo[d], B.grad1[2].lo[d]));
+    P.U.hi[d] = std::max(B.grad1[0].hi[d], std::max(B.grad1[1].hi[d], B.grad1[2].hi[d]));
+  }
+  P.nf = L.nv + (visc ? 1 : 0);
+  P.tiles_x = (P.U.hi[0] + L.hp[0] + 4 * kGVX - 1) / (4 * kGVX);
+  P.tiles_y = (P.U.hi[1] - P.U.lo[1] + kGVY - 1) / kGVY;
+  const int nzu = P.U.hi[2] - P.U.lo[2];
+  if (zchunk < 0) {
+    const int chunks = (nzu - zchunk - 1) / -zchunk;
+    zchunk = (nzu + chunks - 1) / chunks;
+  } else if (zchunk == 0) {
+    const int pairs = P.tiles_x * P.tiles_y * P.nf;
+    const int chunks = std::max(1, std::min(nzu, (GBR_G1V_BLOCKS * device_sms() + pairs - 1) / pairs));
+    zchunk = (nzu + chunks - 1) / chunks;
+  }
+  P.zchunk = zchunk;
+  P.chunks = (nzu + zchunk - 1) / zchunk;
+  return true;
+}
+
 DtArgs dt_args(gbr_ctx* c);
 
 // the box b with its extent along d reduced to the single index 0 (one thread per line along d)
@@ -1714,16 +1759,11 @@ gbr_status run_rhs_nd(gbr_ctx* c, const double* qs, const double* q0, double* ou
       const int tiles_x = (U.hi[0] - U.lo[0] + kG1TX - 1) / kG1TX, tiles_y = (U.hi[1] - U.lo[1] + kG1TY - 1) / kG1TY;
       const int nzu = U.hi[2] - U.lo[2];
       // four cells per thread where the padded rows and the arrays sit on 16-byte boundaries
-      auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
-      const bool vec = L.ps[1] % 4 == 0 && al16(A.prim) && (!c->visc || al16(A.temp)) && al16(A.g1[0]) &&
-                       al16(A.g1[1]) && al16(A.g1[2]);
-      if (vec) {
-        const int vtx = (U.hi[0] + L.hp[0] + 4 * kGVX - 1) / (4 * kGVX), vty = (U.hi[1] - U.lo[1] + kGVY - 1) / kGVY;
-        const int pairs = vtx * vty * nf;
-        const int chunks = std::max(1, std::min(nzu, (GBR_G1V_BLOCKS * device_sms() + pairs - 1) / pairs));
-        const int zchunk = (nzu + chunks - 1) / chunks;
-        const unsigned blocks = (unsigned)(vtx * vty * ((nzu + zchunk - 1) / zchunk));
-        k_grad1v<<<dim3(blocks, nf), kGVX * kGVY, 0, st>>>(A, U, B.grad1[0], B.grad1[1], B.grad1[2], vtx, vty, zchunk);
+      const void* g1p[3] = {A.g1[0], A.g1[1], A.g1[2]};
+      G1VPlan P;
+      if (g1v_plan(L, B, A.prim, A.temp, g1p, c->visc, 0, P)) {
+        k_grad1v<<<dim3((unsigned)(P.tiles_x * P.tiles_y * P.chunks), P.nf), kGVX * kGVY, 0, st>>>(
+            A, P.U, B.grad1[0], B.grad1[1], B.grad1[2], P.tiles_x, P.tiles_y, P.zchunk);
       } else {
         // chunks of planes: about kG1Waves waves of resident blocks (8 per SM)
         const int fb = (nf + kG1Fields - 1) / kG1Fields;  // field groups

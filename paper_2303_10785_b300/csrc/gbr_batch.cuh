@@ -45,13 +45,18 @@ struct BatchJob {
   unsigned long long* dtbits;
   int* err;
   double cfl;           // > 0: CFL number; < 0: fixed time step -cfl
+  Box g1u;              // WL_G1V members: k_grad1v's box union and tiles_x, tiles_y, zchunk, chunks
+  int g1v[4];
 };
 
 struct WorkItem {
   int job, sub, first, blocks;  // blocks [first, first + blocks) of the launch cover sub-box `sub` of `job`
 };
 
-enum { WL_PAD = 0, WL_GRAD1, WL_GRAD2, WL_FACE, WL_INNER, WL_DT, WL_COUNT };
+// WL_G1V: FP32 3D MEG6 members whose rows are 16-byte aligned take their first derivatives by
+// k_grad1v's tiles (one item per member: its tiles x chunks x fields), the others cell by cell
+// (WL_GRAD1); the fused stage kernel keeps every member on WL_GRAD1
+enum { WL_PAD = 0, WL_GRAD1, WL_GRAD2, WL_FACE, WL_INNER, WL_DT, WL_G1V, WL_COUNT };
 
 // Runs f(item, local block) for the contiguous block range of this CTA.  The items may be a
 // sub-range of a longer list: `base` is the block offset its first item starts at.
@@ -141,6 +146,18 @@ __global__ void __launch_bounds__(kBlock) kb_grad2(const BatchJob<R>* jobs, cons
 
 // fused gradient sweep over the first-derivative box: f' everywhere, f'' where the
 // second-derivative box needs it, from f' of the neighbours recomputed in registers
+// the tiles of k_grad1v over the WL_G1V items (FP32 3D), one tile per CTA
+__global__ void __launch_bounds__(kGVX * kGVY, GBR_G1V_MINB) kb_grad1v(const BatchJob<float>* jobs, const WorkItem* items,
+                                                                    int n, int total) {
+  __shared__ float4 plane[2][kGVR * kGVW];
+  phase_work(items, n, total, [&](const WorkItem& it, int lb) {
+    const BatchJob<float>& J = jobs[it.job];
+    const int per_field = J.g1v[0] * J.g1v[1] * J.g1v[3];
+    grad1v_tile(J.A, J.g1u, J.grad1[0], J.grad1[1], J.grad1[2], J.g1v[0], J.g1v[1], J.g1v[2], lb % per_field,
+                lb / per_field, plane);
+  });
+}
+
 template <int ND, class R>
 __global__ void __launch_bounds__(kBlock) kb_grad12(const BatchJob<R>* jobs, const WorkItem* items, int n,
                                                      int total) {
@@ -436,9 +453,22 @@ size_t batch_job_bytes() { return std::max(sizeof(BatchJob<double>), sizeof(Batc
 size_t batch_ws_bytes(int max_members) {
   // per kind (at most 32: dimension, viscosity, precision, moving mesh, gradient scheme) the alignment
   // slack of its tables and its barrier words; per member one job record and at most
-  // 1 + 3 + 3 + 3 + 1 + 1 items
-  const size_t per_member = ((batch_job_bytes() + 255) & ~(size_t)255) + 12 * sizeof(WorkItem);
+  // 1 + 3 + 3 + 3 + 1 + 1 + 1 items (pad, first derivatives cell by cell, second, interfaces,
+  // inner, time step, first-derivative tiles: the capacities upload_kinds reserves)
+  const size_t per_member = ((batch_job_bytes() + 255) & ~(size_t)255) + 13 * sizeof(WorkItem);
   return 32 * (size_t)(WL_COUNT + 2) * 256 + (size_t)max_members * (per_member + 256);
+}
+
+// a member's k_grad1v tiles (FP32 3D MEG6, aligned rows), balanced chunks of at most
+// GBR_BATCH_G1V_CHUNK planes
+#ifndef GBR_BATCH_G1V_CHUNK
+#define GBR_BATCH_G1V_CHUNK 16
+#endif
+bool g1v_member(gbr_ctx* c, G1VPlan& P) {
+  if (c->p.precision != GBR_PREC_MIXED || c->L.nd != 3 || c->p.gradient_scheme == GBR_GRAD_MIG4) return false;
+  const RhsArgsT<float> A = rhs_args_r<float>(c, c->q[0]);
+  const void* g1p[3] = {A.g1[0], A.g1[1], A.g1[2]};
+  return g1v_plan(c->L, rhs_boxes(c->L), A.prim, A.temp, g1p, c->visc, -GBR_BATCH_G1V_CHUNK, P);
 }
 
 template <class R>
@@ -507,6 +537,16 @@ BatchJob<R> make_job(gbr_ctx* c, double cfl) {
   J.dtbits = reinterpret_cast<unsigned long long*>(c->scal + S_DTMIN);
   J.err = c->err;
   J.cfl = cfl;
+  if constexpr (sizeof(R) == sizeof(float)) {
+    G1VPlan P;
+    if (g1v_member(c, P)) {
+      J.g1u = P.U;
+      J.g1v[0] = P.tiles_x;
+      J.g1v[1] = P.tiles_y;
+      J.g1v[2] = P.zchunk;
+      J.g1v[3] = P.chunks;
+    }
+  }
   return J;
 }
 
@@ -531,8 +571,14 @@ void build_items(Kind& K) {
     // the fused stage kernel runs every phase with its one block size
     const int sb = K.tune.fused_stage ? kFusedBlock : kBlock;
     add_items(K.items[WL_PAD], K.total[WL_PAD], jm, 0, pad_box(L, H, H), sb);
+    G1VPlan P;
+    const bool tiles = !K.tune.fused_stage && g1v_member(c, P);
+    if (tiles) {
+      K.items[WL_G1V].push_back(WorkItem{jm, 0, K.total[WL_G1V], (int)P.blocks()});
+      K.total[WL_G1V] += (int)P.blocks();
+    }
     for (int d = 0; d < L.nd; ++d) {
-      add_items(K.items[WL_GRAD1], K.total[WL_GRAD1], jm, d, B.grad1[d], sb);
+      if (!tiles) add_items(K.items[WL_GRAD1], K.total[WL_GRAD1], jm, d, B.grad1[d], sb);
       add_items(K.items[WL_GRAD2], K.total[WL_GRAD2], jm, d, B.grad2[d], sb);
     }
     add_items(K.items[WL_INNER], K.total[WL_INNER], jm, 0, B.inner, sb);
@@ -678,12 +724,25 @@ gbr_status enqueue_rhs(gbr_batch* b, const Kind& K, int stage, long long& launch
       ++launches;
     }
   } else if constexpr (kFaceFormsG2<R>) {
-    // FP32: the interface kernel forms f'' itself
-    auto k1 = kb_grad1<ND, R>;
-    k1<<<phase_grid(b, k1, kBlock, K.total[WL_GRAD1]), kBlock, 0, st>>>(
-        jobs, K.d_items[WL_GRAD1], (int)K.items[WL_GRAD1].size(), K.total[WL_GRAD1]);
-    BK(cudaGetLastError(), "kb_grad1");
-    launches += 2;
+    // FP32: the interface kernel forms f'' itself; first derivatives cell by cell and, for the
+    // members on WL_G1V, by k_grad1v's tiles
+    ++launches;  // the primitive pass above
+    if (!K.items[WL_GRAD1].empty()) {
+      auto k1 = kb_grad1<ND, R>;
+      k1<<<phase_grid(b, k1, kBlock, K.total[WL_GRAD1]), kBlock, 0, st>>>(
+          jobs, K.d_items[WL_GRAD1], (int)K.items[WL_GRAD1].size(), K.total[WL_GRAD1]);
+      BK(cudaGetLastError(), "kb_grad1");
+      ++launches;
+    }
+    if constexpr (ND == 3 && sizeof(R) == sizeof(float)) {
+      if (!K.items[WL_G1V].empty()) {
+        auto kv = kb_grad1v;
+        kv<<<phase_grid(b, kv, kGVX * kGVY, K.total[WL_G1V]), kGVX * kGVY, 0, st>>>(
+            jobs, K.d_items[WL_G1V], (int)K.items[WL_G1V].size(), K.total[WL_G1V]);
+        BK(cudaGetLastError(), "kb_grad1v");
+        ++launches;
+      }
+    }
   } else if (K.tune.fused_grad) {
     auto kern = kb_grad12<ND, R>;
     kern<<<phase_grid(b, kern, kBlock, K.total[WL_GRAD1]), kBlock, 0, st>>>(
@@ -832,7 +891,12 @@ gbr_status upload_kinds(gbr_batch* b) {
     BK(cudaMemsetAsync(K.d_bar, 0, 4 * sizeof(unsigned), b->stream), "barrier words");
     BK(cudaMemcpyAsync(K.d_jobs, host.data(), K.job_bytes, cudaMemcpyHostToDevice, b->stream), "upload jobs");
     for (int w = 0; w < WL_COUNT; ++w) {
-      const size_t bytes = std::max<size_t>(1, K.items[w].size()) * sizeof(WorkItem);
+      // the autotuner's candidates reuse these buffers: a member's first derivatives are one
+      // WL_G1V item or nd WL_GRAD1 items, depending on the candidate
+      size_t cap = K.items[w].size();
+      if (w == WL_GRAD1) cap = std::max(cap, K.members.size() * (size_t)K.key.nd);
+      if (w == WL_G1V) cap = std::max(cap, K.members.size());
+      const size_t bytes = std::max<size_t>(1, cap) * sizeof(WorkItem);
       K.d_items[w] = reinterpret_cast<WorkItem*>(take(bytes));
       if (off > b->ws_bytes) return bfail(b, GBR_ENOMEM, "batch workspace too small");
       if (!K.items[w].empty())
@@ -1018,8 +1082,10 @@ gbr_status rebuild(gbr_batch* b) {
         break;
       }
       // phase kernels: primitives, gradients (one or two), one interface launch per direction, update
-      const int per_stage =
-          K.tune.fused_stage ? 1 : ((K.tune.fused_grad || K.key.prec == GBR_PREC_MIXED) ? 3 : 4) + K.face_dirs;
+      const int grads = K.key.prec == GBR_PREC_MIXED
+                            ? (K.items[WL_GRAD1].empty() ? 0 : 1) + (K.items[WL_G1V].empty() ? 0 : 1)
+                            : (K.tune.fused_grad ? 1 : 2);
+      const int per_stage = K.tune.fused_stage ? 1 : 2 + grads + K.face_dirs;
       launches += 3 + (K.total[WL_DT] > 0 ? 1 : 0) + 3 * per_stage;
     }
   }
